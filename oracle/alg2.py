@@ -1,0 +1,160 @@
+"""Algorithm 2 of the paper (Section IV-A), restated on Python integers (test infrastructure only).
+
+Steps, in the paper's order:
+
+* ``h = 1.25 * min(p, max(p_A, p_B)) + 192`` where ``p_M`` is the least precision that holds every
+  entry of ``M`` exactly (Algorithm 2, step 2).
+* Greedy extraction (Section IV-A): starting at the first unused inner index, append indices while
+  every row of ``A_s`` and every column of ``B_s`` still scales to integers of height below ``2^h``.
+* A block of fewer than 30 indices is widened to ``min(30, |S|)`` indices and done with dot products
+  (the basecase); otherwise ``T = (E_s A_s)(B_s F_s)`` over the integers, where ``E_s`` and ``F_s``
+  hold the optimal (minimal-height) power-of-two scalings of the rows of ``A_s`` and the columns of
+  ``B_s`` (Fig. 2), and ``E_s^-1 T F_s^-1`` is added to ``C``.
+
+Readings (each also used by the GPU planner):
+
+* "height of a row below 2^h" is ``max_k top(a_ik) - min_k bottom(a_ik) <= h`` over the nonzero
+  entries, where ``top`` is the exponent ``e`` with ``2^(e-1) <= |a| < 2^e`` and ``bottom`` the
+  exponent of the lowest set bit; the same for the columns of ``B``.
+* The greedy search stops before the first index that breaks the bound, but a block always holds at
+  least one index.
+* ``h`` is rounded down to an integer.
+* ``F_s`` scales column ``j`` (the figure's ``f_{i,s}`` index is read as ``f_{j,s}``).
+* All contributions to an entry are summed exactly and rounded once, so a product without basecase
+  blocks has the midpoint ``RNE_p(sum_k a_ik b_kj)``.
+"""
+from __future__ import annotations
+
+from .exact import FLAG_SIGN, FLAG_ZERO, limb_field
+
+BASECASE = 30
+
+
+def top_bottom(raw, i):
+    """``(top, bottom, signed_integer_mantissa, shift)`` of entry ``i``, or None if zero.
+
+    The value is ``mant * 2^shift`` with ``mant`` odd; ``bottom = shift`` and ``top`` is the exponent
+    of the entry."""
+    fl = int(raw.flags[i])
+    if fl & FLAG_ZERO:
+        return None
+    v = limb_field(raw, i)
+    tz = (v & -v).bit_length() - 1
+    mant = v >> tz
+    shift = int(raw.exp[i]) - 64 * raw.nlimbs + tz
+    if fl & FLAG_SIGN:
+        mant = -mant
+    return int(raw.exp[i]), shift, mant, shift
+
+
+def precision_of(raw, count):
+    """``p_M``: the largest ``top - bottom`` over the nonzero entries (0 for a zero matrix)."""
+    best = 0
+    for i in range(count):
+        tb = top_bottom(raw, i)
+        if tb is not None:
+            best = max(best, tb[0] - tb[1])
+    return best
+
+
+def height_bound(prec, pA, pB):
+    return (5 * min(prec, max(pA, pB))) // 4 + 192
+
+
+def plan(A, B, M, K, N, prec):
+    """Greedy block list ``[(start, stop, is_basecase)]`` over the inner dimension."""
+    pA = precision_of(A, M * K)
+    pB = precision_of(B, K * N)
+    h = height_bound(prec, pA, pB)
+    tbA = [[top_bottom(A, i * K + k) for k in range(K)] for i in range(M)]
+    tbB = [[top_bottom(B, k * N + j) for k in range(K)] for j in range(N)]
+    blocks = []
+    start = 0
+    while start < K:
+        stop = start + 1
+        hi_a = [None] * M
+        lo_a = [None] * M
+        hi_b = [None] * N
+        lo_b = [None] * N
+
+        def admit(k):
+            nha, nla, nhb, nlb = list(hi_a), list(lo_a), list(hi_b), list(lo_b)
+            for i in range(M):
+                tb = tbA[i][k]
+                if tb is not None:
+                    nha[i] = tb[0] if nha[i] is None else max(nha[i], tb[0])
+                    nla[i] = tb[1] if nla[i] is None else min(nla[i], tb[1])
+                    if nha[i] - nla[i] > h:
+                        return None
+            for j in range(N):
+                tb = tbB[j][k]
+                if tb is not None:
+                    nhb[j] = tb[0] if nhb[j] is None else max(nhb[j], tb[0])
+                    nlb[j] = tb[1] if nlb[j] is None else min(nlb[j], tb[1])
+                    if nhb[j] - nlb[j] > h:
+                        return None
+            return nha, nla, nhb, nlb
+
+        st = admit(start)
+        if st is None:  # a single index always forms a block
+            st = _force(tbA, tbB, start, M, N)
+        hi_a, lo_a, hi_b, lo_b = st
+        while stop < K:
+            st = admit(stop)
+            if st is None:
+                break
+            hi_a, lo_a, hi_b, lo_b = st
+            stop += 1
+        if stop - start < BASECASE:
+            stop = start + min(BASECASE, K - start)
+            blocks.append((start, stop, True))
+        else:
+            blocks.append((start, stop, False))
+        start = stop
+    return h, blocks
+
+
+def _force(tbA, tbB, k, M, N):
+    hi_a = [tbA[i][k][0] if tbA[i][k] else None for i in range(M)]
+    lo_a = [tbA[i][k][1] if tbA[i][k] else None for i in range(M)]
+    hi_b = [tbB[j][k][0] if tbB[j][k] else None for j in range(N)]
+    lo_b = [tbB[j][k][1] if tbB[j][k] else None for j in range(N)]
+    return hi_a, lo_a, hi_b, lo_b
+
+
+def scaled_block(A, B, M, K, N, start, stop):
+    """``(e, f, X, Y)``: row exponents ``e_i``, column exponents ``f_j`` and the integer matrices
+    ``X = E_s A_s`` (M x |s|) and ``Y = B_s F_s`` (|s| x N) of block ``[start, stop)`` (Fig. 2)."""
+    e = []
+    X = []
+    for i in range(M):
+        row = [top_bottom(A, i * K + k) for k in range(start, stop)]
+        lows = [tb[1] for tb in row if tb is not None]
+        ei = -min(lows) if lows else 0
+        e.append(ei)
+        X.append([0 if tb is None else tb[2] << (tb[3] + ei) for tb in row])
+    f = []
+    cols = []
+    for j in range(N):
+        col = [top_bottom(B, k * N + j) for k in range(start, stop)]
+        lows = [tb[1] for tb in col if tb is not None]
+        fj = -min(lows) if lows else 0
+        f.append(fj)
+        cols.append([0 if tb is None else tb[2] << (tb[3] + fj) for tb in col])
+    Y = [[cols[j][kk] for j in range(N)] for kk in range(stop - start)]
+    return e, f, X, Y
+
+
+def int_matmul(X, Y):
+    """Textbook integer matrix product on Python integers."""
+    n_in = len(Y)
+    N = len(Y[0]) if n_in else 0
+    return [[sum(row[k] * Y[k][j] for k in range(n_in)) for j in range(N)] for row in X]
+
+
+def int_matmul_entry(X, Y, i, j):
+    return sum(X[i][k] * Y[k][j] for k in range(len(Y)))
+
+
+def height(v: int) -> int:
+    return abs(v).bit_length()

@@ -1,0 +1,150 @@
+"""Pins for the Algorithm 2 restatement (``oracle.alg2``): the block decomposition must reproduce the
+exact product (checked with ``fractions.Fraction`` arithmetic), the integer product must agree with
+numpy's integer matmul, the scalings must be minimal, the greedy blocks maximal, and the height bound
+must follow the paper's formula."""
+from __future__ import annotations
+
+import math
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+from oracle import alg2
+from oracle import exact as X
+from synth import random_balls
+from synth.workloads import matmul_uniform
+from tests.ballmake import ball_values, make_balls
+
+
+def exact_product(A, B, M, K, N):
+    out = [[Fraction(0)] * N for _ in range(M)]
+    for i in range(M):
+        for j in range(N):
+            out[i][j] = sum(ball_values(A, i * K + k)[0] * ball_values(B, k * N + j)[0]
+                            for k in range(K))
+    return out
+
+
+def recombined(A, B, M, K, N, prec):
+    h, blocks = alg2.plan(A, B, M, K, N, prec)
+    C = [[Fraction(0)] * N for _ in range(M)]
+    for start, stop, base in blocks:
+        if base:
+            for i in range(M):
+                for j in range(N):
+                    C[i][j] += sum(ball_values(A, i * K + k)[0] * ball_values(B, k * N + j)[0]
+                                   for k in range(start, stop))
+        else:
+            e, f, Xs, Ys = alg2.scaled_block(A, B, M, K, N, start, stop)
+            T = alg2.int_matmul(Xs, Ys)
+            for i in range(M):
+                for j in range(N):
+                    C[i][j] += Fraction(T[i][j]) * Fraction(2) ** (-e[i] - f[j])
+    return h, blocks, C
+
+
+@pytest.mark.parametrize("kind", ["uniform", "badly_scaled", "zeros", "short"])
+def test_blocks_reproduce_exact_product(kind):
+    rng = np.random.default_rng(hash(kind) % 2**32)
+    if kind == "uniform":
+        M, K, N, p = 3, 40, 4, 128
+        A = random_balls(rng, M * K, 2, 128, -20, 20)
+        B = random_balls(rng, K * N, 2, 128, -20, 20)
+    elif kind == "badly_scaled":
+        M, K, N, p = 3, 70, 2, 64
+        ea = rng.integers(-5, 5, size=M * K)
+        ea[np.arange(M) * K + 35] += 900  # column 35 of A is 2^900 larger: forces a split
+        A = random_balls(rng, M * K, 1, 64, exps=ea)
+        B = random_balls(rng, K * N, 1, 64, -5, 5)
+    elif kind == "zeros":
+        M, K, N, p = 2, 35, 3, 64
+        A = random_balls(rng, M * K, 1, 64, -5, 5, zero_frac=0.4)
+        B = random_balls(rng, K * N, 1, 64, -5, 5, zero_frac=0.4)
+        A.flags[0:K] = X.FLAG_ZERO  # row 0 of A entirely zero
+        A.limbs[:, 0:K] = 0
+    else:
+        M, K, N, p = 2, 12, 2, 64
+        A = random_balls(rng, M * K, 1, 64, -5, 5)
+        B = random_balls(rng, K * N, 1, 64, -5, 5)
+    h, blocks, C = recombined(A, B, M, K, N, p)
+    assert C == exact_product(A, B, M, K, N)
+    # the blocks tile [0, K) in order
+    assert blocks[0][0] == 0 and blocks[-1][1] == K
+    assert all(blocks[t][1] == blocks[t + 1][0] for t in range(len(blocks) - 1))
+    if kind == "uniform":
+        assert blocks == [(0, K, False)]
+    if kind == "short":
+        assert blocks == [(0, K, True)]
+    if kind == "badly_scaled":
+        assert len(blocks) >= 2
+
+
+def test_height_bound_formula():
+    for p, pa, pb in [(256, 256, 256), (128, 128, 128), (53, 53, 53), (1024, 300, 2000),
+                      (106, 53, 64)]:
+        assert alg2.height_bound(p, pa, pb) == math.floor(1.25 * min(p, max(pa, pb)) + 192)
+    assert alg2.height_bound(256, 256, 256) == 512
+    assert alg2.height_bound(128, 128, 128) == 352
+
+
+def test_precision_of_matrix():
+    A = make_balls([Fraction(3, 4), Fraction(1, 2**10), Fraction(5)])
+    # 3/4 = 11b * 2^-2 -> 2 bits; 2^-10 -> 1 bit; 5 = 101b -> 3 bits
+    assert alg2.precision_of(A, 3) == 3
+
+
+def test_scaling_is_minimal_and_integral():
+    rng = np.random.default_rng(2)
+    M, K, N = 4, 33, 3
+    A = random_balls(rng, M * K, 2, 100, -30, 30)
+    B = random_balls(rng, K * N, 2, 100, -30, 30)
+    e, f, Xs, Ys = alg2.scaled_block(A, B, M, K, N, 0, K)
+    for i in range(M):
+        assert any(v & 1 for v in Xs[i])  # minimal: some entry odd
+        for k in range(K):
+            assert Fraction(Xs[i][k]) == ball_values(A, i * K + k)[0] * Fraction(2) ** e[i]
+    for j in range(N):
+        assert any(Ys[k][j] & 1 for k in range(K))
+        for k in range(K):
+            assert Fraction(Ys[k][j]) == ball_values(B, k * N + j)[0] * Fraction(2) ** f[j]
+
+
+def test_greedy_blocks_are_within_height_and_maximal():
+    rng = np.random.default_rng(3)
+    M, K, N, p = 2, 150, 2, 64
+    ea = rng.integers(-200, 200, size=M * K)
+    A = random_balls(rng, M * K, 1, 64, exps=ea)
+    B = random_balls(rng, K * N, 1, 64, -3, 3)
+    h, blocks = alg2.plan(A, B, M, K, N, p)
+
+    def height_ok(start, stop):
+        for i in range(M):
+            tbs = [alg2.top_bottom(A, i * K + k) for k in range(start, stop)]
+            if max(t[0] for t in tbs) - min(t[1] for t in tbs) > h:
+                return False
+        for j in range(N):
+            tbs = [alg2.top_bottom(B, k * N + j) for k in range(start, stop)]
+            if max(t[0] for t in tbs) - min(t[1] for t in tbs) > h:
+                return False
+        return True
+
+    for start, stop, base in blocks:
+        if not base:
+            assert height_ok(start, stop)
+            if stop < K:
+                assert not height_ok(start, stop + 1)
+
+
+def test_int_matmul_vs_numpy():
+    rng = np.random.default_rng(4)
+    Xm = rng.integers(-2**20, 2**20, size=(5, 7))
+    Ym = rng.integers(-2**20, 2**20, size=(7, 3))
+    T = alg2.int_matmul(Xm.tolist(), Ym.tolist())
+    assert T == (Xm.astype(np.int64) @ Ym.astype(np.int64)).tolist()
+
+
+def test_uniform_workload_is_one_block():
+    case = matmul_uniform(9, 40, 256, -20, 20, rad_bits=250)
+    h, blocks = alg2.plan(case.A[0], case.B[0], 40, 40, 40, 256)
+    assert h == 512 and blocks == [(0, 40, False)]
