@@ -1,0 +1,187 @@
+/*
+ * arbgpu -- arbitrary-precision real and complex ball dot products and matrix multiplication on a
+ * GB300 GPU (sm_103a), after F. Johansson, "Faster arbitrary-precision dot product and matrix
+ * multiplication" (arXiv 1901.04289).
+ *
+ * Plain C ABI: device pointers, sizes and a CUDA stream passed as `void *`; no C++ or framework
+ * types.  Every call is asynchronous on the given stream unless stated otherwise.  The caller owns
+ * every buffer (inputs, outputs, workspace); the library never allocates device memory on these
+ * paths and never falls back to the CPU.
+ *
+ * ---------------------------------------------------------------------------------------------
+ * Ball layout (Section III-A).  An array of `count` balls is five device arrays:
+ *
+ *   limbs   uint64  limb k (0 = least significant) of entry i at limbs[k * limb_stride + i],
+ *                   k < nlimbs ("limb planes").  A nonzero finite midpoint is
+ *                   m = (-1)^sign * 2^exp * sum_k limbs[k] * 2^(64 (k - nlimbs))      (eq. 1)
+ *                   with bit 63 of limb nlimbs-1 set; low limbs may be zero.
+ *   exp     int64   2^(exp-1) <= |m| < 2^exp.
+ *   flags   uint32  bit 0 sign, bit 1 zero (limbs must then be zero), bit 2 infinity, bit 3 NaN,
+ *                   bit 4 infinite radius; bits 8..15: n, the number of limbs from the top down to
+ *                   the lowest nonzero limb (1 <= n <= nlimbs) -- the "limb count" of eq. 1.
+ *   rad_man uint32  radius r = rad_man * 2^(rad_exp - 30), rad_man = 0 or 2^29 <= rad_man < 2^30
+ *   rad_exp int64   (a 30-bit "mag", p_rad = 30).
+ *
+ * Exponents must satisfy |exp| < 2^60 (and |rad_exp| < 2^60 for nonzero radii); NaN, infinities
+ * and larger exponents are reported as ARBGPU_ERR_UNSUPPORTED_VALUE (where the paper leaves the
+ * fixed-point path for a fallback, Section III-C) and the affected outputs are set to
+ * [NaN +- inf] (flags = NaN | infinite radius).
+ *
+ * Outputs are written with the output array's own nlimbs (>= ceil(p/64)): the midpoint rounded to
+ * nearest (ties to even) at p bits, top-aligned, and a radius rounded up.
+ * ---------------------------------------------------------------------------------------------
+ */
+#ifndef ARBGPU_H
+#define ARBGPU_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  ARBGPU_OK = 0,
+  ARBGPU_ERR_INVALID = 1,           /* bad argument (returned synchronously) */
+  ARBGPU_ERR_UNSUPPORTED_VALUE = 2, /* NaN / infinity / |exponent| >= 2^60 in an input */
+  ARBGPU_ERR_WORKSPACE = 3,         /* workspace missing or too small */
+  ARBGPU_ERR_CUDA = 4,              /* a CUDA runtime call failed */
+  ARBGPU_ERR_TIMEOUT = 5,           /* a bounded device-side wait gave up */
+  ARBGPU_ERR_LIMIT = 6              /* a per-call size hint (max precision / length) exceeded */
+} arbgpu_status;
+
+/* Flag bits of the layout above. */
+#define ARBGPU_FLAG_SIGN 1u
+#define ARBGPU_FLAG_ZERO 2u
+#define ARBGPU_FLAG_INF 4u
+#define ARBGPU_FLAG_NAN 8u
+#define ARBGPU_FLAG_RAD_INF 16u
+#define ARBGPU_NSIG_SHIFT 8
+
+/* One ball array (all pointers device memory, caller-owned). */
+typedef struct {
+  uint64_t *limbs;
+  int64_t limb_stride; /* elements between limb planes, >= count */
+  int32_t nlimbs;      /* limbs per midpoint, 1..64 */
+  int64_t *exp;
+  uint32_t *flags;
+  uint32_t *rad_man;
+  int64_t *rad_exp;
+  int64_t count;
+} arbgpu_balls;
+
+typedef struct arbgpu_ctx arbgpu_ctx;
+
+/* Library context for one device: holds the device status word.  Create before use, on the host
+ * thread that will use it; one context per host thread.  `device` is a CUDA device ordinal.
+ * Allocates a few bytes of device memory once (here, not on the compute paths). */
+arbgpu_status arbgpu_create(arbgpu_ctx **ctx, int device);
+arbgpu_status arbgpu_destroy(arbgpu_ctx *ctx);
+
+/* Synchronises `stream`, returns the first device-side error recorded since the previous call
+ * (ARBGPU_OK if none) and clears it. */
+arbgpu_status arbgpu_get_status(arbgpu_ctx *ctx, void *stream);
+
+/* Human-readable name of a status code (static string). */
+const char *arbgpu_status_string(arbgpu_status s);
+
+/* Library version as major*10000 + minor*100 + patch. */
+int arbgpu_version(void);
+
+/*
+ * Batched ball dot products: Algorithm 1 (Section III), the counterpart of arb_dot / acb_dot:
+ *
+ *   res[b]  contains  initial[b] + (-1)^sub[b] * sum_{i < len[b]} x[xoff[b] + i*xstep[b]]
+ *                                                               * y[yoff[b] + i*ystep[b]]
+ *
+ * computed at precision prec[b] >= 2 (bits).  One warp evaluates one dot: a setup pass over the
+ * terms (exponent bounds, accumulator size), exact limb products accumulated in a two's-complement
+ * fixed-point window of n_s limbs, a ulp error counter and a fixed-point radius accumulator, then
+ * one rounding to p bits (round to nearest, ties to even) and an upward-rounded radius.
+ *
+ *   res      output balls, entry b written (res->nlimbs >= ceil(prec[b]/64)); must not alias inputs
+ *   initial  optional (NULL): entry b is added with a plus sign
+ *   sub      optional (NULL = all 0) device uint8[batch]
+ *   x, y     input ball arrays; xoff/xstep/yoff/ystep/len device int64[batch] (strides may be
+ *            negative or zero; every index touched must lie in [0, count))
+ *   prec     device int32[batch]
+ *   prec_max, len_max  host-side upper bounds of prec[] and len[] over the batch, used to choose
+ *            the kernel; a dot exceeding them is written as [NaN +- inf] with ARBGPU_ERR_LIMIT
+ *            (prec_max <= 1024; larger precisions return ARBGPU_ERR_INVALID)
+ *   complex_mode  0: real.  1: complex -- res, initial, x and y each point to TWO arbgpu_balls
+ *            (real part, imaginary part); each part of the result is a real dot of length 2N
+ *            (Section III-F).
+ *   workspace, ws_bytes  unused (may be NULL / 0)
+ *   stream   cudaStream_t
+ * Errors: argument errors return synchronously; value errors through arbgpu_get_status.
+ */
+arbgpu_status arbgpu_dot(arbgpu_ctx *ctx, const arbgpu_balls *res, const arbgpu_balls *initial,
+                         const uint8_t *sub, const arbgpu_balls *x, const int64_t *xoff,
+                         const int64_t *xstep, const arbgpu_balls *y, const int64_t *yoff,
+                         const int64_t *ystep, const int64_t *len, const int32_t *prec,
+                         int64_t batch, int32_t prec_max, int64_t len_max, int complex_mode,
+                         void *workspace, size_t ws_bytes, void *stream);
+
+/* Algorithm selection for arbgpu_mat_mul. */
+#define ARBGPU_ALG_AUTO 0
+#define ARBGPU_ALG_DOT 1   /* classical: M*N dot products (Section IV, first paragraph) */
+#define ARBGPU_ALG_BLOCK 2 /* scaled integer blocks (Algorithm 2, Section IV-A) */
+
+/* Flags for arbgpu_mat_mul. */
+#define ARBGPU_MM_COMPLEX_3M 1u /* complex midpoints by eq. 3 (three real products) */
+
+/*
+ * Ball matrix product C = A * B (C contains the exact product of every choice of points in the
+ * input balls).  A is M x K, B is K x N, C is M x N, all row-major with leading dimensions
+ * lda, ldb, ldc (entry (i, k) of A is index i*lda + k of its ball array).  Precision prec >= 2.
+ *
+ *   ARBGPU_ALG_DOT    every entry is one Algorithm-1 dot (warp per entry).
+ *   ARBGPU_ALG_BLOCK  Algorithm 2: the inner dimension is cut greedily into blocks in which every
+ *                     row of A and column of B scales to integers of height <= h
+ *                     (h = 1.25 min(p, max(p_A, p_B)) + 192); each block's scaled integer matrices
+ *                     are split into signed 8-bit digits and multiplied exactly on the tensor cores
+ *                     (BF16 digits, FP32 accumulation kept below 2^24, so every product is exact);
+ *                     blocks shorter than 30 indices are done by dot products.  All contributions
+ *                     to an entry are summed exactly and rounded once.  Radii:
+ *                     |A| R_B + R_A (|B| + R_B) from exact integer products of magnitudes rounded
+ *                     up to 8*S_r-bit windows.
+ *   ARBGPU_ALG_AUTO   picks by size and precision.
+ *
+ *   complex_mode  0 real; 1 complex: C, A, B each point to TWO arbgpu_balls (real, imaginary)
+ *   workspace     device memory of at least arbgpu_mat_mul_workspace_size() bytes (BLOCK/AUTO)
+ * The block path reads back its plan (a few bytes per block) with one stream synchronisation.
+ */
+arbgpu_status arbgpu_mat_mul(arbgpu_ctx *ctx, const arbgpu_balls *C, const arbgpu_balls *A,
+                             const arbgpu_balls *B, int64_t M, int64_t K, int64_t N, int64_t lda,
+                             int64_t ldb, int64_t ldc, int32_t prec, int complex_mode, int alg,
+                             uint32_t flags, void *workspace, size_t ws_bytes, void *stream);
+
+/* Workspace bytes arbgpu_mat_mul needs for these sizes (host-only, synchronous).  `a_nlimbs` and
+ * `b_nlimbs` are the input arrays' limb counts. */
+arbgpu_status arbgpu_mat_mul_workspace_size(arbgpu_ctx *ctx, int64_t M, int64_t K, int64_t N,
+                                            int32_t prec, int32_t a_nlimbs, int32_t b_nlimbs,
+                                            int complex_mode, int alg, uint32_t flags,
+                                            size_t *bytes);
+
+/*
+ * Exact integer matrix product T = X * Y over Z, reduced modulo 2^(64 t_limbs): the engine behind
+ * the block path (it replaces the paper's FLINT fmpz_mat_mul, Section IV).  Signed integers in
+ * two's complement limb planes: X[k * (M*K) + i*K + kk] is limb k (little-endian) of X[i][kk],
+ * x_limbs limbs per entry; likewise Y (K x N, y_limbs) and T (M x N, t_limbs).  The operands are
+ * split into balanced signed base-256 digits and every digit product is formed exactly on the
+ * tensor cores.  `workspace` must hold arbgpu_int_mat_mul_workspace_size() bytes.
+ */
+arbgpu_status arbgpu_int_mat_mul(arbgpu_ctx *ctx, uint64_t *T, int32_t t_limbs, const uint64_t *X,
+                                 int32_t x_limbs, const uint64_t *Y, int32_t y_limbs, int64_t M,
+                                 int64_t K, int64_t N, void *workspace, size_t ws_bytes,
+                                 void *stream);
+
+arbgpu_status arbgpu_int_mat_mul_workspace_size(arbgpu_ctx *ctx, int32_t x_limbs, int32_t y_limbs,
+                                                int64_t M, int64_t K, int64_t N, size_t *bytes);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ARBGPU_H */

@@ -1,0 +1,219 @@
+"""arbgpu: ball (midpoint-radius) dot products and matrix multiplication on a GB300 GPU.
+
+Thin Python layer over the C ABI in ``include/arbgpu.h``: ``Balls`` keeps one ball array in device
+memory (torch tensors used as plain buffers) and the functions below pass raw pointers, sizes and
+the current CUDA stream to ``libarbgpu.so``.  All arithmetic happens in the library's CUDA kernels.
+"""
+from __future__ import annotations
+
+import ctypes as C
+
+import numpy as np
+import torch
+
+from . import _lib
+from ._lib import (ALG_AUTO, ALG_BLOCK, ALG_DOT, MM_COMPLEX_3M, ArbgpuError, CBalls)
+
+__all__ = ["Balls", "Context", "dot", "mat_mul", "int_mat_mul", "ALG_AUTO", "ALG_DOT",
+           "ALG_BLOCK", "MM_COMPLEX_3M", "ArbgpuError"]
+
+
+class Balls:
+    """One array of ``count`` balls in device memory, in the layout of ``include/arbgpu.h``.
+
+    ``limbs`` is an int64 tensor ``[nlimbs, count]`` (bit patterns of the uint64 limbs), ``exp`` and
+    ``rad_exp`` int64 ``[count]``, ``flags`` and ``rad_man`` int32 ``[count]`` (uint32 bit patterns).
+    """
+
+    def __init__(self, limbs, exp, flags, rad_man, rad_exp):
+        self.limbs, self.exp, self.flags, self.rad_man, self.rad_exp = limbs, exp, flags, rad_man, \
+            rad_exp
+        self.nlimbs = int(limbs.shape[0])
+        self.count = int(exp.shape[0])
+
+    @staticmethod
+    def empty(count, nlimbs, device="cuda"):
+        return Balls(torch.zeros((nlimbs, count), dtype=torch.int64, device=device),
+                     torch.zeros(count, dtype=torch.int64, device=device),
+                     torch.zeros(count, dtype=torch.int32, device=device),
+                     torch.zeros(count, dtype=torch.int32, device=device),
+                     torch.zeros(count, dtype=torch.int64, device=device))
+
+    @staticmethod
+    def from_raw(raw, device="cuda", pin=False):
+        """Copy a host ball array (numpy fields: limbs, exp, flags, rad_man, rad_exp)."""
+        def t(a, dt):
+            x = torch.from_numpy(np.ascontiguousarray(a).view(dt))
+            return x.pin_memory() if pin else x.to(device)
+        return Balls(t(raw.limbs, np.int64), t(raw.exp, np.int64), t(raw.flags, np.int32),
+                     t(raw.rad_man, np.int32), t(raw.rad_exp, np.int64))
+
+    def to_host(self):
+        """(limbs uint64, exp int64, flags uint32, rad_man uint32, rad_exp int64) numpy arrays."""
+        return (self.limbs.cpu().numpy().view(np.uint64), self.exp.cpu().numpy(),
+                self.flags.cpu().numpy().view(np.uint32), self.rad_man.cpu().numpy().view(np.uint32),
+                self.rad_exp.cpu().numpy())
+
+    def copy_from_(self, other, non_blocking=False):
+        for a, b in ((self.limbs, other.limbs), (self.exp, other.exp), (self.flags, other.flags),
+                     (self.rad_man, other.rad_man), (self.rad_exp, other.rad_exp)):
+            a.copy_(b, non_blocking=non_blocking)
+        return self
+
+    def tensors(self):
+        return (self.limbs, self.exp, self.flags, self.rad_man, self.rad_exp)
+
+    def nbytes(self):
+        return sum(t.numel() * t.element_size() for t in self.tensors())
+
+    def cstruct(self) -> CBalls:
+        return CBalls(self.limbs.data_ptr(), self.count, self.nlimbs, self.exp.data_ptr(),
+                      self.flags.data_ptr(), self.rad_man.data_ptr(), self.rad_exp.data_ptr(),
+                      self.count)
+
+
+class Context:
+    """An ``arbgpu_ctx`` for one device (owns the device status word)."""
+
+    def __init__(self, device=None):
+        dev = torch.cuda.current_device() if device is None else int(device)
+        self.device = dev
+        h = C.c_void_p()
+        rc = _lib.lib().arbgpu_create(C.byref(h), dev)
+        if rc != 0:
+            raise ArbgpuError(rc, "arbgpu_create")
+        self.handle = h
+        self._ws = None
+
+    def close(self):
+        if self.handle is not None:
+            _lib.lib().arbgpu_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def status(self, stream=None) -> int:
+        """Synchronise the stream and return (and clear) the device-side status code."""
+        s = _stream_ptr(stream)
+        return int(_lib.lib().arbgpu_get_status(self.handle, s))
+
+    def check(self, stream=None):
+        rc = self.status(stream)
+        if rc != 0:
+            raise ArbgpuError(rc, "device status")
+
+    def workspace(self, nbytes):
+        """A cached device buffer of at least ``nbytes`` bytes."""
+        if nbytes == 0:
+            return None
+        if self._ws is None or self._ws.numel() < nbytes:
+            self._ws = torch.empty(int(nbytes), dtype=torch.uint8, device=f"cuda:{self.device}")
+        return self._ws
+
+
+_default = {}
+
+
+def default_context(device=None) -> Context:
+    dev = torch.cuda.current_device() if device is None else int(device)
+    if dev not in _default:
+        _default[dev] = Context(dev)
+    return _default[dev]
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return C.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+
+
+def _pair(b):
+    if isinstance(b, (list, tuple)):
+        return list(b)
+    return [b]
+
+
+def _arr(structs):
+    A = CBalls * len(structs)
+    return A(*structs)
+
+
+def _ptr(t):
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+def dot(res, x, y, xoff, xstep, yoff, ystep, length, prec, *, prec_max, len_max, sub=None,
+        initial=None, ctx=None, stream=None):
+    """Batched ball dots (``arbgpu_dot``).  ``res``, ``x``, ``y``, ``initial``: a ``Balls`` (real)
+    or a pair ``(re, im)`` (complex).  Index arrays: int64 device tensors; ``prec`` int32; ``sub``
+    uint8 or None."""
+    ctx = ctx or default_context()
+    cplx = isinstance(x, (list, tuple))
+    r, xs, ys = _pair(res), _pair(x), _pair(y)
+    init = _pair(initial) if initial is not None else None
+    batch = int(length.shape[0])
+    rc = _lib.lib().arbgpu_dot(
+        ctx.handle, _arr([b.cstruct() for b in r]),
+        _arr([b.cstruct() for b in init]) if init else None, _ptr(sub),
+        _arr([b.cstruct() for b in xs]), _ptr(xoff), _ptr(xstep), _arr([b.cstruct() for b in ys]),
+        _ptr(yoff), _ptr(ystep), _ptr(length), _ptr(prec), batch, int(prec_max), int(len_max),
+        1 if cplx else 0, None, 0, _stream_ptr(stream))
+    if rc != 0:
+        raise ArbgpuError(rc, "arbgpu_dot")
+
+
+def mat_mul_workspace_size(M, K, N, prec, a_nlimbs, b_nlimbs, complex_mode=False, alg=ALG_AUTO,
+                           flags=0, ctx=None):
+    ctx = ctx or default_context()
+    n = C.c_size_t(0)
+    rc = _lib.lib().arbgpu_mat_mul_workspace_size(ctx.handle, M, K, N, prec, a_nlimbs, b_nlimbs,
+                                                  1 if complex_mode else 0, alg, flags,
+                                                  C.byref(n))
+    if rc != 0:
+        raise ArbgpuError(rc, "arbgpu_mat_mul_workspace_size")
+    return int(n.value)
+
+
+def mat_mul(C_out, A, B, M, K, N, prec, *, alg=ALG_AUTO, flags=0, lda=None, ldb=None, ldc=None,
+            workspace=None, ctx=None, stream=None):
+    """Ball matrix product ``C = A * B`` (``arbgpu_mat_mul``); complex when A is a pair."""
+    ctx = ctx or default_context()
+    cplx = isinstance(A, (list, tuple))
+    cs, As, Bs = _pair(C_out), _pair(A), _pair(B)
+    lda = K if lda is None else lda
+    ldb = N if ldb is None else ldb
+    ldc = N if ldc is None else ldc
+    if workspace is None:
+        need = mat_mul_workspace_size(M, K, N, prec, As[0].nlimbs, Bs[0].nlimbs, cplx, alg, flags,
+                                      ctx)
+        workspace = ctx.workspace(need)
+    wsp = _ptr(workspace)
+    wsb = 0 if workspace is None else workspace.numel() * workspace.element_size()
+    rc = _lib.lib().arbgpu_mat_mul(ctx.handle, _arr([b.cstruct() for b in cs]),
+                                   _arr([b.cstruct() for b in As]), _arr([b.cstruct() for b in Bs]),
+                                   M, K, N, lda, ldb, ldc, prec, 1 if cplx else 0, alg, flags, wsp,
+                                   wsb, _stream_ptr(stream))
+    if rc != 0:
+        raise ArbgpuError(rc, "arbgpu_mat_mul")
+
+
+def int_mat_mul(T, t_limbs, X, x_limbs, Y, y_limbs, M, K, N, *, workspace=None, ctx=None,
+                stream=None):
+    """Exact integer matrix product over limb planes (``arbgpu_int_mat_mul``)."""
+    ctx = ctx or default_context()
+    if workspace is None:
+        n = C.c_size_t(0)
+        rc = _lib.lib().arbgpu_int_mat_mul_workspace_size(ctx.handle, x_limbs, y_limbs, M, K, N,
+                                                          C.byref(n))
+        if rc != 0:
+            raise ArbgpuError(rc, "arbgpu_int_mat_mul_workspace_size")
+        workspace = ctx.workspace(int(n.value))
+    wsb = 0 if workspace is None else workspace.numel() * workspace.element_size()
+    rc = _lib.lib().arbgpu_int_mat_mul(ctx.handle, _ptr(T), t_limbs, _ptr(X), x_limbs, _ptr(Y),
+                                       y_limbs, M, K, N, _ptr(workspace), wsb, _stream_ptr(stream))
+    if rc != 0:
+        raise ArbgpuError(rc, "arbgpu_int_mat_mul")

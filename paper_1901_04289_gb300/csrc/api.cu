@@ -1,0 +1,200 @@
+// The C ABI of the arbgpu library: context, status word, argument checks and dispatch.
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+
+#include "internal.h"
+
+using namespace arbgpu;
+
+namespace {
+
+bool balls_ok(const arbgpu_balls &b) {
+  if (b.count < 0 || b.nlimbs < 1 || b.nlimbs > 64) return false;
+  if (b.count == 0) return true;
+  if (!b.limbs || !b.exp || !b.flags || !b.rad_man || !b.rad_exp) return false;
+  if (b.limb_stride < b.count) return false;
+  return true;
+}
+
+bool overlaps(const void *a, size_t na, const void *b, size_t nb) {
+  const char *pa = (const char *)a, *pb = (const char *)b;
+  return pa < pb + nb && pb < pa + na;
+}
+
+// True if any array of `out` shares memory with any array of `in`.
+bool balls_alias(const arbgpu_balls &out, const arbgpu_balls &in) {
+  if (out.count == 0 || in.count == 0) return false;
+  const void *op[5] = {out.limbs, out.exp, out.flags, out.rad_man, out.rad_exp};
+  const size_t on[5] = {(size_t)out.limb_stride * out.nlimbs * 8, (size_t)out.count * 8,
+                        (size_t)out.count * 4, (size_t)out.count * 4, (size_t)out.count * 8};
+  const void *ip[5] = {in.limbs, in.exp, in.flags, in.rad_man, in.rad_exp};
+  const size_t in_[5] = {(size_t)in.limb_stride * in.nlimbs * 8, (size_t)in.count * 8,
+                         (size_t)in.count * 4, (size_t)in.count * 4, (size_t)in.count * 8};
+  for (int i = 0; i < 5; ++i)
+    for (int j = 0; j < 5; ++j)
+      if (overlaps(op[i], on[i], ip[j], in_[j])) return true;
+  return false;
+}
+
+}  // namespace
+
+extern "C" {
+
+int arbgpu_version(void) { return 100; }
+
+const char *arbgpu_status_string(arbgpu_status s) {
+  switch (s) {
+    case ARBGPU_OK: return "ok";
+    case ARBGPU_ERR_INVALID: return "invalid argument";
+    case ARBGPU_ERR_UNSUPPORTED_VALUE: return "unsupported value (NaN, infinity or huge exponent)";
+    case ARBGPU_ERR_WORKSPACE: return "workspace too small";
+    case ARBGPU_ERR_CUDA: return "CUDA error";
+    case ARBGPU_ERR_TIMEOUT: return "device wait timed out";
+    case ARBGPU_ERR_LIMIT: return "size limit exceeded";
+  }
+  return "unknown status";
+}
+
+arbgpu_status arbgpu_create(arbgpu_ctx **ctx, int device) {
+  if (!ctx) return ARBGPU_ERR_INVALID;
+  *ctx = nullptr;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev)
+    return ARBGPU_ERR_CUDA;
+  int prev = 0;
+  cudaGetDevice(&prev);
+  if (cudaSetDevice(device) != cudaSuccess) return ARBGPU_ERR_CUDA;
+  arbgpu_ctx *c = new (std::nothrow) arbgpu_ctx();
+  if (!c) return ARBGPU_ERR_INVALID;
+  c->device = device;
+  cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, device);
+  if (cudaMalloc(&c->status, sizeof(int)) != cudaSuccess ||
+      cudaMemset(c->status, 0, sizeof(int)) != cudaSuccess) {
+    delete c;
+    cudaSetDevice(prev);
+    return ARBGPU_ERR_CUDA;
+  }
+  cudaDeviceSynchronize();
+  cudaSetDevice(prev);
+  *ctx = c;
+  return ARBGPU_OK;
+}
+
+arbgpu_status arbgpu_destroy(arbgpu_ctx *ctx) {
+  if (!ctx) return ARBGPU_ERR_INVALID;
+  cudaFree(ctx->status);
+  delete ctx;
+  return ARBGPU_OK;
+}
+
+arbgpu_status arbgpu_get_status(arbgpu_ctx *ctx, void *stream) {
+  if (!ctx) return ARBGPU_ERR_INVALID;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (cudaStreamSynchronize(s) != cudaSuccess) return ARBGPU_ERR_CUDA;
+  int v = 0;
+  if (cudaMemcpy(&v, ctx->status, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
+    return ARBGPU_ERR_CUDA;
+  if (v != 0) cudaMemset(ctx->status, 0, sizeof(int));
+  return (arbgpu_status)v;
+}
+
+arbgpu_status arbgpu_dot(arbgpu_ctx *ctx, const arbgpu_balls *res, const arbgpu_balls *initial,
+                         const uint8_t *sub, const arbgpu_balls *x, const int64_t *xoff,
+                         const int64_t *xstep, const arbgpu_balls *y, const int64_t *yoff,
+                         const int64_t *ystep, const int64_t *len, const int32_t *prec,
+                         int64_t batch, int32_t prec_max, int64_t len_max, int complex_mode,
+                         void *workspace, size_t ws_bytes, void *stream) {
+  (void)workspace;
+  (void)ws_bytes;
+  if (!ctx || !res || !x || !y || batch < 0) return ARBGPU_ERR_INVALID;
+  if (batch == 0) return ARBGPU_OK;
+  if (!xoff || !xstep || !yoff || !ystep || !len || !prec) return ARBGPU_ERR_INVALID;
+  if (prec_max < 2 || prec_max > 1024 || len_max < 0 || len_max > ((int64_t)1 << 40))
+    return ARBGPU_ERR_INVALID;
+  const int parts = complex_mode ? 2 : 1;
+  for (int q = 0; q < parts; ++q) {
+    if (!balls_ok(res[q]) || !balls_ok(x[q]) || !balls_ok(y[q])) return ARBGPU_ERR_INVALID;
+    if (initial && !balls_ok(initial[q])) return ARBGPU_ERR_INVALID;
+    if (res[q].count < batch) return ARBGPU_ERR_INVALID;
+    if (initial && initial[q].count < batch) return ARBGPU_ERR_INVALID;
+    if ((int64_t)res[q].nlimbs * 64 < prec_max) return ARBGPU_ERR_INVALID;
+    for (int r = 0; r < parts; ++r) {
+      if (balls_alias(res[q], x[r]) || balls_alias(res[q], y[r])) return ARBGPU_ERR_INVALID;
+      if (initial && balls_alias(res[q], initial[r])) return ARBGPU_ERR_INVALID;
+      if (r != q && balls_alias(res[q], res[r])) return ARBGPU_ERR_INVALID;
+    }
+  }
+  if (cudaSetDevice(ctx->device) != cudaSuccess) return ARBGPU_ERR_CUDA;
+  return launch_batched_dot(ctx, res, initial, sub, x, xoff, xstep, y, yoff, ystep, len, prec,
+                            batch, prec_max, len_max, complex_mode, (cudaStream_t)stream);
+}
+
+arbgpu_status arbgpu_mat_mul_workspace_size(arbgpu_ctx *ctx, int64_t M, int64_t K, int64_t N,
+                                            int32_t prec, int32_t a_nlimbs, int32_t b_nlimbs,
+                                            int complex_mode, int alg, uint32_t flags,
+                                            size_t *bytes) {
+  (void)ctx;
+  (void)M;
+  (void)K;
+  (void)N;
+  (void)prec;
+  (void)a_nlimbs;
+  (void)b_nlimbs;
+  (void)complex_mode;
+  (void)flags;
+  if (!bytes) return ARBGPU_ERR_INVALID;
+  *bytes = 0;
+  if (alg == ARBGPU_ALG_DOT) return ARBGPU_OK;
+  return ARBGPU_ERR_INVALID;  // the block path is added with its kernels
+}
+
+arbgpu_status arbgpu_mat_mul(arbgpu_ctx *ctx, const arbgpu_balls *C, const arbgpu_balls *A,
+                             const arbgpu_balls *B, int64_t M, int64_t K, int64_t N, int64_t lda,
+                             int64_t ldb, int64_t ldc, int32_t prec, int complex_mode, int alg,
+                             uint32_t flags, void *workspace, size_t ws_bytes, void *stream) {
+  (void)flags;
+  (void)workspace;
+  (void)ws_bytes;
+  if (!ctx || !C || !A || !B || M < 0 || K < 0 || N < 0) return ARBGPU_ERR_INVALID;
+  if (prec < 2 || prec > 1024) return ARBGPU_ERR_INVALID;
+  if (M == 0 || N == 0) return ARBGPU_OK;
+  if (lda < K || ldb < N || ldc < N) return ARBGPU_ERR_INVALID;
+  const int parts = complex_mode ? 2 : 1;
+  for (int q = 0; q < parts; ++q) {
+    if (!balls_ok(C[q]) || !balls_ok(A[q]) || !balls_ok(B[q])) return ARBGPU_ERR_INVALID;
+    if (K > 0 && (A[q].count < (M - 1) * lda + K || B[q].count < (K - 1) * ldb + N))
+      return ARBGPU_ERR_INVALID;
+    if (C[q].count < (M - 1) * ldc + N) return ARBGPU_ERR_INVALID;
+    if ((int64_t)C[q].nlimbs * 64 < prec) return ARBGPU_ERR_INVALID;
+    for (int r = 0; r < parts; ++r) {
+      if (balls_alias(C[q], A[r]) || balls_alias(C[q], B[r])) return ARBGPU_ERR_INVALID;
+      if (r != q && balls_alias(C[q], C[r])) return ARBGPU_ERR_INVALID;
+    }
+  }
+  if (cudaSetDevice(ctx->device) != cudaSuccess) return ARBGPU_ERR_CUDA;
+  if (alg == ARBGPU_ALG_DOT || alg == ARBGPU_ALG_AUTO)
+    return launch_matmul_dot(ctx, C, A, B, M, K, N, lda, ldb, ldc, prec, complex_mode,
+                             (cudaStream_t)stream);
+  return ARBGPU_ERR_INVALID;
+}
+
+arbgpu_status arbgpu_int_mat_mul(arbgpu_ctx *ctx, uint64_t *T, int32_t t_limbs, const uint64_t *X,
+                                 int32_t x_limbs, const uint64_t *Y, int32_t y_limbs, int64_t M,
+                                 int64_t K, int64_t N, void *workspace, size_t ws_bytes,
+                                 void *stream) {
+  (void)ctx; (void)T; (void)t_limbs; (void)X; (void)x_limbs; (void)Y; (void)y_limbs;
+  (void)M; (void)K; (void)N; (void)workspace; (void)ws_bytes; (void)stream;
+  return ARBGPU_ERR_INVALID;
+}
+
+arbgpu_status arbgpu_int_mat_mul_workspace_size(arbgpu_ctx *ctx, int32_t x_limbs, int32_t y_limbs,
+                                                int64_t M, int64_t K, int64_t N, size_t *bytes) {
+  (void)ctx; (void)x_limbs; (void)y_limbs; (void)M; (void)K; (void)N;
+  if (!bytes) return ARBGPU_ERR_INVALID;
+  *bytes = 0;
+  return ARBGPU_ERR_INVALID;
+}
+
+}  // extern "C"

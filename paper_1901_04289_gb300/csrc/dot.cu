@@ -1,0 +1,198 @@
+// Term sources for kernel (a) and their launchers: batched dots (arb_dot / acb_dot counterparts,
+// Section III) and the classical matrix product as M*N dots (Section IV).
+#include "dot_eval.cuh"
+#include "internal.h"
+
+namespace arbgpu {
+
+// Batched dots: dot b reads x[xoff[b] + i*xstep[b]] and y[yoff[b] + i*ystep[b]], i < len[b].
+// A complex dot b is two virtual real dots (2b: real part, 2b+1: imaginary part) of length 2N:
+// re = sum a c - b d, im = sum a d + b c (Section III-F).
+struct BatchDotSrc {
+  BallsView x[2], y[2], init[2];
+  BallsOut out[2];
+  const int64_t *xoff, *xstep, *yoff, *ystep, *len;
+  const int32_t *precs;
+  const uint8_t *subs;
+  int64_t batch;
+  int cplx;
+  bool has_init;
+  int prec_max;
+  int64_t len_max;
+
+  __device__ int64_t ndots() const { return cplx ? 2 * batch : batch; }
+  __device__ int64_t b_of(int64_t d) const { return cplx ? (d >> 1) : d; }
+  __device__ int part(int64_t d) const { return cplx ? (int)(d & 1) : 0; }
+  __device__ int64_t nterms(int64_t d) const {
+    const int64_t n = __ldg(len + b_of(d));
+    return cplx ? 2 * n : n;
+  }
+  __device__ int64_t len_of(int64_t d) const { return __ldg(len + b_of(d)); }
+  __device__ TermLoc term(int64_t d, int64_t t) const {
+    const int64_t b = b_of(d);
+    const bool sb = subs ? (__ldg(subs + b) != 0) : false;
+    if (!cplx) return TermLoc{0, __ldg(xoff + b) + t * __ldg(xstep + b), 0,
+                              __ldg(yoff + b) + t * __ldg(ystep + b), sb};
+    const int64_t i = t >> 1;
+    const int w = (int)(t & 1);
+    const int64_t xi = __ldg(xoff + b) + i * __ldg(xstep + b);
+    const int64_t yi = __ldg(yoff + b) + i * __ldg(ystep + b);
+    if (part(d) == 0) return w == 0 ? TermLoc{0, xi, 0, yi, sb} : TermLoc{1, xi, 1, yi, !sb};
+    return w == 0 ? TermLoc{0, xi, 1, yi, sb} : TermLoc{1, xi, 0, yi, sb};
+  }
+  __device__ const BallsView &xview(int a) const { return x[a]; }
+  __device__ const BallsView &yview(int a) const { return y[a]; }
+  __device__ bool has_initial(int64_t) const { return has_init; }
+  __device__ const BallsView &initial_view(int64_t d) const { return init[part(d)]; }
+  __device__ int64_t initial_index(int64_t d) const { return b_of(d); }
+  __device__ const BallsOut &out_view(int64_t d) const { return out[part(d)]; }
+  __device__ int64_t out_index(int64_t d) const { return b_of(d); }
+  __device__ int prec(int64_t d) const { return __ldg(precs + b_of(d)); }
+};
+
+// Classical product: entry (i, j) is the dot of row i of A and column j of B.  Consecutive warps
+// take consecutive j, so the lanes' reads of B rows are shared through L1.
+struct MatDotSrc {
+  BallsView A[2], B[2];
+  BallsOut C[2];
+  int64_t M, K, N, lda, ldb, ldc;
+  int prec_v;
+  int cplx;
+  int prec_max;
+  int64_t len_max;
+
+  __device__ int64_t ndots() const { return (cplx ? 2 : 1) * M * N; }
+  __device__ int part(int64_t d) const { return cplx ? (int)(d & 1) : 0; }
+  __device__ int64_t ent(int64_t d) const { return cplx ? (d >> 1) : d; }
+  __device__ int64_t nterms(int64_t) const { return cplx ? 2 * K : K; }
+  __device__ TermLoc term(int64_t d, int64_t t) const {
+    const int64_t e = ent(d);
+    const int64_t i = e / N, j = e - (e / N) * N;
+    if (!cplx) return TermLoc{0, i * lda + t, 0, t * ldb + j, false};
+    const int64_t k = t >> 1;
+    const int w = (int)(t & 1);
+    const int64_t xi = i * lda + k, yi = k * ldb + j;
+    if (part(d) == 0) return w == 0 ? TermLoc{0, xi, 0, yi, false} : TermLoc{1, xi, 1, yi, true};
+    return w == 0 ? TermLoc{0, xi, 1, yi, false} : TermLoc{1, xi, 0, yi, false};
+  }
+  __device__ const BallsView &xview(int a) const { return A[a]; }
+  __device__ const BallsView &yview(int a) const { return B[a]; }
+  __device__ bool has_initial(int64_t) const { return false; }
+  __device__ const BallsView &initial_view(int64_t) const { return A[0]; }
+  __device__ int64_t initial_index(int64_t) const { return 0; }
+  __device__ const BallsOut &out_view(int64_t d) const { return C[part(d)]; }
+  __device__ int64_t out_index(int64_t d) const {
+    const int64_t e = ent(d);
+    const int64_t i = e / N, j = e - i * N;
+    return i * ldc + j;
+  }
+  __device__ int prec(int64_t) const { return prec_v; }
+};
+
+int dot_class_for_problem(int prec, int64_t max_terms, int max_nlimbs) {
+  const int ns = dot_ns(prec, max_terms, max_terms);
+  int nx = max_nlimbs < ns + 1 ? max_nlimbs : ns + 1;
+  if (nx < 1) nx = 1;
+  return dot_class_for(nx, ns);
+}
+
+template <class Src>
+static arbgpu_status launch_dot_src(arbgpu_ctx *ctx, const Src &src, int64_t ndots, int cmax,
+                                    cudaStream_t stream) {
+  if (ndots <= 0) return ARBGPU_OK;
+  const int threads = 256;
+  int64_t blocks = (ndots + 7) / 8;
+  const int64_t cap = (int64_t)ctx->sm_count * 16;
+  if (blocks > cap) blocks = cap;
+  switch (cmax) {
+    case 0: dot_kernel<0, Src><<<(unsigned)blocks, threads, 0, stream>>>(src, ctx->status); break;
+    case 1: dot_kernel<1, Src><<<(unsigned)blocks, threads, 0, stream>>>(src, ctx->status); break;
+    case 2: dot_kernel<2, Src><<<(unsigned)blocks, threads, 0, stream>>>(src, ctx->status); break;
+    case 3: dot_kernel<3, Src><<<(unsigned)blocks, threads, 0, stream>>>(src, ctx->status); break;
+    case 4: dot_kernel<4, Src><<<(unsigned)blocks, threads, 0, stream>>>(src, ctx->status); break;
+    case 5: dot_kernel<5, Src><<<(unsigned)blocks, threads, 0, stream>>>(src, ctx->status); break;
+    case 6: dot_kernel<6, Src><<<(unsigned)blocks, threads, 0, stream>>>(src, ctx->status); break;
+    case 7: dot_kernel<7, Src><<<(unsigned)blocks, threads, 0, stream>>>(src, ctx->status); break;
+    default: return ARBGPU_ERR_INVALID;
+  }
+  return cudaGetLastError() == cudaSuccess ? ARBGPU_OK : ARBGPU_ERR_CUDA;
+}
+
+arbgpu_status launch_batched_dot(arbgpu_ctx *ctx, const arbgpu_balls *res,
+                                 const arbgpu_balls *initial, const uint8_t *sub,
+                                 const arbgpu_balls *x, const int64_t *xoff, const int64_t *xstep,
+                                 const arbgpu_balls *y, const int64_t *yoff, const int64_t *ystep,
+                                 const int64_t *len, const int32_t *prec, int64_t batch,
+                                 int32_t prec_max, int64_t len_max, int complex_mode,
+                                 cudaStream_t stream) {
+  const int parts = complex_mode ? 2 : 1;
+  BatchDotSrc s{};
+  int maxnl = 1;
+  for (int q = 0; q < parts; ++q) {
+    s.x[q] = view_of(x[q]);
+    s.y[q] = view_of(y[q]);
+    s.out[q] = out_of(res[q]);
+    s.init[q] = initial ? view_of(initial[q]) : view_of(x[q]);
+    maxnl = x[q].nlimbs > maxnl ? x[q].nlimbs : maxnl;
+    maxnl = y[q].nlimbs > maxnl ? y[q].nlimbs : maxnl;
+    if (initial) maxnl = initial[q].nlimbs > maxnl ? initial[q].nlimbs : maxnl;
+  }
+  if (!complex_mode) {
+    s.x[1] = s.x[0];
+    s.y[1] = s.y[0];
+    s.out[1] = s.out[0];
+    s.init[1] = s.init[0];
+  }
+  s.xoff = xoff;
+  s.xstep = xstep;
+  s.yoff = yoff;
+  s.ystep = ystep;
+  s.len = len;
+  s.precs = prec;
+  s.subs = sub;
+  s.batch = batch;
+  s.cplx = complex_mode ? 1 : 0;
+  s.has_init = initial != nullptr;
+  s.prec_max = prec_max;
+  const int64_t terms_max = (complex_mode ? 2 * len_max : len_max);
+  s.len_max = terms_max;
+  const int cmax = dot_class_for_problem(prec_max, terms_max + 1, maxnl);
+  if (cmax < 0) return ARBGPU_ERR_INVALID;
+  return launch_dot_src(ctx, s, s.cplx ? 2 * batch : batch, cmax, stream);
+}
+
+arbgpu_status launch_matmul_dot(arbgpu_ctx *ctx, const arbgpu_balls *C, const arbgpu_balls *A,
+                                const arbgpu_balls *B, int64_t M, int64_t K, int64_t N,
+                                int64_t lda, int64_t ldb, int64_t ldc, int32_t prec,
+                                int complex_mode, cudaStream_t stream) {
+  const int parts = complex_mode ? 2 : 1;
+  MatDotSrc s{};
+  int maxnl = 1;
+  for (int q = 0; q < parts; ++q) {
+    s.A[q] = view_of(A[q]);
+    s.B[q] = view_of(B[q]);
+    s.C[q] = out_of(C[q]);
+    maxnl = A[q].nlimbs > maxnl ? A[q].nlimbs : maxnl;
+    maxnl = B[q].nlimbs > maxnl ? B[q].nlimbs : maxnl;
+  }
+  if (!complex_mode) {
+    s.A[1] = s.A[0];
+    s.B[1] = s.B[0];
+    s.C[1] = s.C[0];
+  }
+  s.M = M;
+  s.K = K;
+  s.N = N;
+  s.lda = lda;
+  s.ldb = ldb;
+  s.ldc = ldc;
+  s.prec_v = prec;
+  s.cplx = complex_mode ? 1 : 0;
+  s.prec_max = prec;
+  s.len_max = complex_mode ? 2 * K : K;
+  const int cmax = dot_class_for_problem(prec, s.len_max, maxnl);
+  if (cmax < 0) return ARBGPU_ERR_INVALID;
+  return launch_dot_src(ctx, s, (complex_mode ? 2 : 1) * M * N, cmax, stream);
+}
+
+}  // namespace arbgpu

@@ -1,0 +1,36 @@
+// Host-side declarations shared by the translation units of the arbgpu library.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "arbgpu.h"
+
+struct arbgpu_ctx {
+  int device;
+  int sm_count;
+  int *status;  // device int: first recorded error code
+};
+
+namespace arbgpu {
+
+// Kernel (a): batched dots (real or complex).
+arbgpu_status launch_batched_dot(arbgpu_ctx *ctx, const arbgpu_balls *res,
+                                 const arbgpu_balls *initial, const uint8_t *sub,
+                                 const arbgpu_balls *x, const int64_t *xoff, const int64_t *xstep,
+                                 const arbgpu_balls *y, const int64_t *yoff, const int64_t *ystep,
+                                 const int64_t *len, const int32_t *prec, int64_t batch,
+                                 int32_t prec_max, int64_t len_max, int complex_mode,
+                                 cudaStream_t stream);
+
+// Kernel (a) over rows x columns: the classical matrix product, one warp per output entry.
+arbgpu_status launch_matmul_dot(arbgpu_ctx *ctx, const arbgpu_balls *C, const arbgpu_balls *A,
+                                const arbgpu_balls *B, int64_t M, int64_t K, int64_t N,
+                                int64_t lda, int64_t ldb, int64_t ldc, int32_t prec,
+                                int complex_mode, cudaStream_t stream);
+
+// Dot-kernel size class for a precision, a maximal term count and operand limb counts (-1: none).
+int dot_class_for_problem(int prec, int64_t max_terms, int max_nlimbs);
+
+}  // namespace arbgpu
