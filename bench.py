@@ -1,0 +1,345 @@
+"""Benchmark: effective ball multiply-add rate of the real ball matrix product at N=512.
+
+Workload (default): real ball matrices A, B of size 512 x 512, uniform random 256-bit mantissas,
+exponents uniform in [-20, 20], radii 2^-250 relative, multiplied at p = 256 with the library's
+default algorithm (the block algorithm of Section IV-A once available, else the classical
+dot-product algorithm).  The same inputs with 128-bit mantissas are timed at p = 128, and both
+precisions are also timed with the classical warp-per-dot algorithm, so the line reports the
+block-versus-dot speedup at p = 128 and p = 256.
+
+One step = one complete ``arbgpu_mat_mul`` call (every kernel of the path) on inputs resident in
+device memory; L2 is flushed (512 MiB write) before each timed step and the step is timed with CUDA
+events on the launching stream.  ``e2e`` repeats the measurement through the same public call with
+the inputs copied from pinned host memory and the result copied back inside the timed region.
+
+``--impl reference`` times the CPU oracle (exact rational dot products on Python integers, then one
+rounding) on a bounded sample of output entries of the same workload.
+
+Usage: python bench.py [--gpus N --steps K --warmup W] [--impl ours|reference]
+       (N > 1 under torchrun: every rank runs its own replica; weak scaling)
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0,
+                  "sm_max_mhz": 2070.0}
+METRIC = "ball matmul eff. GMAC/s at p=128/256 vs plain dot path; INT8 TC % of peak"
+UNIT = "GMAC/s"
+N_DEFAULT = 512
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        d["_source"] = "measured"
+        return d
+    d = dict(PEAKS_FALLBACK)
+    d["_source"] = "fallback"
+    return d
+
+
+def workload_name(n, prec):
+    return (f"real ball matmul N={n} p={prec}: uniform {prec}-bit mantissas, exponents U[-20,20], "
+            f"radii 2^-250 relative")
+
+
+# --------------------------------------------------------------------------- clocks
+
+class ClockSampler:
+    """Samples nvidia-smi clocks and throttle reasons every 200 ms while active."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.QUERY}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        sms, maxs, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sms.append(float(f[1]))
+                maxs.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sms:
+            return None
+        top = max(sms)
+        load = [s for s in sms if s >= 0.5 * top] or sms
+        return {"sm_mhz": statistics.median(load), "sm_max_mhz": max(maxs) if maxs else None,
+                "reasons": sorted(reasons), "samples": len(sms)}
+
+
+# --------------------------------------------------------------------------- oracle arm
+
+def oracle_sample(case, prec, entries, seconds):
+    """Time the oracle's exact definition on sampled output entries; returns (MAC/s, entries)."""
+    from oracle import exact as X
+    import numpy as np
+    rng = np.random.default_rng(0)
+    K, N = case.K, case.N
+    done = 0
+    macs = 0
+    t0 = time.perf_counter()
+    while done < entries and (time.perf_counter() - t0) < seconds:
+        i, j = int(rng.integers(case.M)), int(rng.integers(N))
+        terms = X.matmul_entry_terms(case.A[0], case.B[0], K, N, i, j)
+        X.result_exact(terms, prec, (prec + 63) // 64)
+        done += 1
+        macs += K
+    dt = time.perf_counter() - t0
+    return macs / dt, done, dt
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    from synth.workloads import block_matmul_n512
+    case = block_matmul_n512(prec=args.prec)
+    for _ in range(args.warmup):
+        oracle_sample(case, args.prec, 1, 5.0)
+    rates = []
+    ents = 0
+    secs = 0.0
+    for _ in range(args.steps):
+        r, n, dt = oracle_sample(case, args.prec, args.ref_entries, 30.0)
+        rates.append(r)
+        ents += n
+        secs += dt
+    value = statistics.mean(rates) / 1e9
+    sample = (f"{ents} output entries of the {case.N}x{case.N} product ({case.K} terms each), "
+              f"{args.steps} steps, {secs:.1f} s")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 0,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * secs / max(args.steps, 1), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "exact (python int)",
+            "data": "synthetic", "config": {"workload": workload_name(case.N, args.prec),
+                                            "l2": "n/a (CPU)"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# --------------------------------------------------------------------------- GPU arm
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--prec", type=int, default=256)
+    ap.add_argument("--n", type=int, default=N_DEFAULT)
+    ap.add_argument("--alg", default="auto", choices=["auto", "dot", "block"])
+    ap.add_argument("--no-compare", action="store_true", help="skip the p=128 / dot-path lines")
+    ap.add_argument("--ref-entries", type=int, default=48)
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+
+    import torch
+    import torch.distributed as dist
+
+    import paper_1901_04289_gb300 as arb
+    from synth.workloads import block_matmul_n512, matmul_uniform
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device(f"cuda:{local}"))
+    torch.cuda.set_device(local)
+    dev = f"cuda:{local}"
+    ctx = arb.default_context(local)
+    peaks = load_peaks()
+    algs = {"auto": arb.ALG_AUTO, "dot": arb.ALG_DOT, "block": arb.ALG_BLOCK}
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def make(prec):
+        if args.n == N_DEFAULT:
+            return block_matmul_n512(prec=prec)
+        return matmul_uniform(1901042893, args.n, prec, -20, 20, rad_bits=250)
+
+    def timed(case, prec, alg, steps, warmup, e2e=False, trace=False):
+        n = case.N
+        nl = (prec + 63) // 64
+        A = arb.Balls.from_raw(case.A[0], device=dev)
+        B = arb.Balls.from_raw(case.B[0], device=dev)
+        C = arb.Balls.empty(case.M * n, nl, device=dev)
+        hA = hB = hC = None
+        if e2e:
+            hA = arb.Balls.from_raw(case.A[0], pin=True)
+            hB = arb.Balls.from_raw(case.B[0], pin=True)
+            hC = arb.Balls(*(torch.empty_like(t, device="cpu").pin_memory() for t in C.tensors()))
+        need = arb.mat_mul_workspace_size(case.M, case.K, n, prec, A.nlimbs, B.nlimbs, False, alg)
+        ws = torch.empty(max(need, 1), dtype=torch.uint8, device=dev)
+
+        def step():
+            if e2e:
+                A.copy_from_(hA, non_blocking=True)
+                B.copy_from_(hB, non_blocking=True)
+            arb.mat_mul(C, A, B, case.M, case.K, n, prec, alg=alg, workspace=ws, ctx=ctx)
+            if e2e:
+                hC.copy_from_(C, non_blocking=True)
+
+        for _ in range(warmup):
+            step()
+        ctx.check()
+        stream = torch.cuda.current_stream()
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(steps)]
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        l0 = ctx.launch_count()
+        if trace:
+            ctx.trace(True)
+        for k in range(steps):
+            flush.zero_()
+            evs[k][0].record(stream)
+            step()
+            evs[k][1].record(stream)
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        launches = ctx.launch_count() - l0
+        recs = ctx.trace_read() if trace else []
+        ctx.trace(False)
+        ctx.check()
+        ms = sum(a.elapsed_time(b) for a, b in evs)
+        h2d = (A.nbytes() + B.nbytes()) if e2e else 0
+        d2h = C.nbytes() if e2e else 0
+        return ms, launches, recs, h2d, d2h
+
+    prec = args.prec
+    alg = algs[args.alg]
+    case = make(prec)
+    macs = case.M * case.K * case.N
+    sampler = ClockSampler(local)
+    sampler.start()
+    ms, launches, recs, _, _ = timed(case, prec, alg, args.steps, args.warmup, trace=True)
+    clocks = sampler.stop()
+    # max over ranks
+    tot = torch.tensor([ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(tot, op=dist.ReduceOp.MAX)
+    ms_max = float(tot.item())
+    value = world * macs * args.steps / (ms_max * 1e-3) / 1e9
+    e2e_ms, _, _, h2d, d2h = timed(case, prec, alg, args.steps, 2, e2e=True)
+    e2e_value = macs * args.steps / (e2e_ms * 1e-3) / 1e9
+
+    # roofline of the dominant kernel, from the library's per-launch events
+    per = {}
+    for name, kms, units in recs:
+        d = per.setdefault(name, [0.0, 0, 0])
+        d[0] += kms
+        d[1] += 1
+        d[2] += units
+    dom = max(per.items(), key=lambda kv: kv[1][0]) if per else None
+    roofline = None
+    if dom:
+        name, (kms, cnt, units) = dom
+        avg_s = kms / cnt * 1e-3
+        sm_mhz = (clocks or {}).get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
+        if name == "dot_kernel":
+            n_l = (prec + 63) // 64
+            # 4 32x32-bit multiplies per 64x64-bit limb product, n_l^2 limb products per MAC
+            mults = 4 * n_l * n_l * units / cnt
+            peak = 152 * 64 * sm_mhz * 1e6 / 1e12  # IMAD issue: 64 / clk / SM, Tmul/s
+            achieved = mults / avg_s / 1e12
+            roofline = {"bound": "alu", "kernel": name, "achieved": achieved, "peak": peak,
+                        "unit": "T int32-mul/s", "frac": achieved / peak, "traffic": None,
+                        "peak_source": f"derived: 152 SMs x 64 IMAD/clk x {sm_mhz:.0f} MHz"}
+        else:
+            roofline = {"kernel": name, "ms_avg": kms / cnt}
+        roofline["share_of_step"] = kms / ms if ms else None
+
+    compare = {}
+    if not args.no_compare and args.n == N_DEFAULT:
+        for p in (128, 256):
+            c = case if p == prec else make(p)
+            for nm, a in (("auto", arb.ALG_AUTO), ("dot", arb.ALG_DOT)):
+                if p == prec and a == alg:
+                    compare[f"{nm}_p{p}"] = value / world
+                    continue
+                t, _, _, _, _ = timed(c, p, a, 3, 1)
+                compare[f"{nm}_p{p}"] = c.M * c.K * c.N * 3 / (t * 1e-3) / 1e9
+        for p in (128, 256):
+            compare[f"speedup_vs_dot_p{p}"] = compare[f"auto_p{p}"] / compare[f"dot_p{p}"]
+
+    cpu = None
+    if rank == 0 and world == 1:
+        r, n_ent, dt = oracle_sample(case, prec, 10**9, args.cpu_seconds)
+        cpu = {"value": r / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"{n_ent} output entries x {case.K} terms in {dt:.1f} s (exact "
+                         f"Python-integer dot, one rounding)"}
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "int64 limbs / exact integer products", "data": "synthetic",
+                "config": {"workload": workload_name(case.N, prec), "alg": args.alg,
+                           "l2": "flushed (512 MiB write) before every timed step",
+                           "parallelism": f"replicas x{world}"},
+                "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
+                        "d2h_bytes_per_step": d2h},
+                "gpu_launches": launches, "roofline": roofline, "cpu_baseline": cpu,
+                "clocks": clocks, "compare": compare, "peaks_source": peaks["_source"]}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

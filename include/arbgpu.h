@@ -89,6 +89,25 @@ const char *arbgpu_status_string(arbgpu_status s);
 /* Library version as major*10000 + minor*100 + patch. */
 int arbgpu_version(void);
 
+/* Tracing (host-side, no effect on results).
+ * arbgpu_launch_count: number of kernels launched through `ctx` so far.
+ * arbgpu_trace_enable: when on, every kernel launch is bracketed by a pair of CUDA events recorded
+ *   on its stream (a few microseconds of overhead per launch).
+ * arbgpu_trace_read: waits for the recorded launches, writes up to `max_entries` records (kernel
+ *   name -- a static string --, device time in ms, and the algorithmic work units the launch
+ *   processed: dot_kernel counts dots for arbgpu_dot and M*N*K multiply-adds for arbgpu_mat_mul)
+ *   and clears the record list. */
+typedef struct {
+  const char *name;
+  float ms;
+  int64_t units;
+} arbgpu_trace_entry;
+
+arbgpu_status arbgpu_launch_count(arbgpu_ctx *ctx, int64_t *count);
+arbgpu_status arbgpu_trace_enable(arbgpu_ctx *ctx, int enable);
+arbgpu_status arbgpu_trace_read(arbgpu_ctx *ctx, arbgpu_trace_entry *out, int32_t max_entries,
+                                int32_t *n_entries);
+
 /*
  * Batched ball dot products: Algorithm 1 (Section III), the counterpart of arb_dot / acb_dot:
  *

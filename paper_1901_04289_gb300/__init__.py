@@ -106,6 +106,23 @@ class Context:
         if rc != 0:
             raise ArbgpuError(rc, "device status")
 
+    def launch_count(self) -> int:
+        n = C.c_int64(0)
+        _lib.lib().arbgpu_launch_count(self.handle, C.byref(n))
+        return int(n.value)
+
+    def trace(self, enable=True):
+        _lib.lib().arbgpu_trace_enable(self.handle, 1 if enable else 0)
+
+    def trace_read(self, max_entries=4096):
+        """[(kernel name, device ms, work units)] of the launches traced since the last read."""
+        buf = (_lib.CTrace * max_entries)()
+        n = C.c_int32(0)
+        rc = _lib.lib().arbgpu_trace_read(self.handle, buf, max_entries, C.byref(n))
+        if rc != 0:
+            raise ArbgpuError(rc, "arbgpu_trace_read")
+        return [(buf[i].name.decode(), float(buf[i].ms), int(buf[i].units)) for i in range(n.value)]
+
     def workspace(self, nbytes):
         """A cached device buffer of at least ``nbytes`` bytes."""
         if nbytes == 0:

@@ -45,6 +45,10 @@ class CBalls(C.Structure):
     ]
 
 
+class CTrace(C.Structure):
+    _fields_ = [("name", C.c_char_p), ("ms", C.c_float), ("units", C.c_int64)]
+
+
 class ArbgpuError(RuntimeError):
     def __init__(self, code, what=""):
         self.code = code
@@ -79,7 +83,11 @@ def lib():
         L.arbgpu_int_mat_mul.argtypes = [vp, vp, i32, vp, i32, vp, i32, i64, i64, i64, vp, sz, vp]
         L.arbgpu_int_mat_mul_workspace_size.argtypes = [vp, i32, i32, i64, i64, i64,
                                                         C.POINTER(C.c_size_t)]
-        for name in ("arbgpu_create", "arbgpu_destroy", "arbgpu_get_status", "arbgpu_dot",
+        L.arbgpu_launch_count.argtypes = [vp, C.POINTER(C.c_int64)]
+        L.arbgpu_trace_enable.argtypes = [vp, C.c_int]
+        L.arbgpu_trace_read.argtypes = [vp, C.POINTER(CTrace), i32, C.POINTER(C.c_int32)]
+        for name in ("arbgpu_launch_count", "arbgpu_trace_enable", "arbgpu_trace_read",
+                     "arbgpu_create", "arbgpu_destroy", "arbgpu_get_status", "arbgpu_dot",
                      "arbgpu_mat_mul", "arbgpu_mat_mul_workspace_size", "arbgpu_int_mat_mul",
                      "arbgpu_int_mat_mul_workspace_size"):
             getattr(L, name).restype = C.c_int
@@ -97,5 +105,6 @@ def status_string(code) -> str:
 def exported_symbols():
     """Names the shared library must export (every function declared in include/arbgpu.h)."""
     return ["arbgpu_create", "arbgpu_destroy", "arbgpu_get_status", "arbgpu_status_string",
-            "arbgpu_version", "arbgpu_dot", "arbgpu_mat_mul", "arbgpu_mat_mul_workspace_size",
+            "arbgpu_version", "arbgpu_launch_count", "arbgpu_trace_enable", "arbgpu_trace_read",
+            "arbgpu_dot", "arbgpu_mat_mul", "arbgpu_mat_mul_workspace_size",
             "arbgpu_int_mat_mul", "arbgpu_int_mat_mul_workspace_size"]

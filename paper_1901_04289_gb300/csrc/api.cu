@@ -40,7 +40,71 @@ bool balls_alias(const arbgpu_balls &out, const arbgpu_balls &in) {
 
 }  // namespace
 
+namespace arbgpu {
+
+static cudaEvent_t pool_event(arbgpu_ctx *c) {
+  if (!c->event_pool.empty()) {
+    cudaEvent_t e = c->event_pool.back();
+    c->event_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+
+LaunchScope::LaunchScope(arbgpu_ctx *c, cudaStream_t s, const char *name, int64_t units)
+    : ctx(c), stream(s), idx(-1) {
+  ctx->launches += 1;
+  if (ctx->trace) {
+    arbgpu_trace_rec r{name, pool_event(ctx), pool_event(ctx), units};
+    cudaEventRecord(r.start, stream);
+    ctx->recs.push_back(r);
+    idx = (int)ctx->recs.size() - 1;
+  }
+}
+
+LaunchScope::~LaunchScope() {
+  if (idx >= 0) cudaEventRecord(ctx->recs[idx].stop, stream);
+}
+
+}  // namespace arbgpu
+
 extern "C" {
+
+arbgpu_status arbgpu_launch_count(arbgpu_ctx *ctx, int64_t *count) {
+  if (!ctx || !count) return ARBGPU_ERR_INVALID;
+  *count = ctx->launches;
+  return ARBGPU_OK;
+}
+
+arbgpu_status arbgpu_trace_enable(arbgpu_ctx *ctx, int enable) {
+  if (!ctx) return ARBGPU_ERR_INVALID;
+  ctx->trace = enable != 0;
+  return ARBGPU_OK;
+}
+
+arbgpu_status arbgpu_trace_read(arbgpu_ctx *ctx, arbgpu_trace_entry *out, int32_t max_entries,
+                                int32_t *n_entries) {
+  if (!ctx || !n_entries || (max_entries > 0 && !out)) return ARBGPU_ERR_INVALID;
+  int32_t n = 0;
+  for (auto &r : ctx->recs) {
+    if (cudaEventSynchronize(r.stop) != cudaSuccess) return ARBGPU_ERR_CUDA;
+    if (n < max_entries) {
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, r.start, r.stop);
+      out[n].name = r.name;
+      out[n].ms = ms;
+      out[n].units = r.units;
+      ++n;
+    }
+    ctx->event_pool.push_back(r.start);
+    ctx->event_pool.push_back(r.stop);
+  }
+  ctx->recs.clear();
+  *n_entries = n;
+  return ARBGPU_OK;
+}
 
 int arbgpu_version(void) { return 100; }
 
@@ -69,6 +133,8 @@ arbgpu_status arbgpu_create(arbgpu_ctx **ctx, int device) {
   arbgpu_ctx *c = new (std::nothrow) arbgpu_ctx();
   if (!c) return ARBGPU_ERR_INVALID;
   c->device = device;
+  c->launches = 0;
+  c->trace = false;
   cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, device);
   if (cudaMalloc(&c->status, sizeof(int)) != cudaSuccess ||
       cudaMemset(c->status, 0, sizeof(int)) != cudaSuccess) {
@@ -84,6 +150,11 @@ arbgpu_status arbgpu_create(arbgpu_ctx **ctx, int device) {
 
 arbgpu_status arbgpu_destroy(arbgpu_ctx *ctx) {
   if (!ctx) return ARBGPU_ERR_INVALID;
+  for (auto &r : ctx->recs) {
+    cudaEventDestroy(r.start);
+    cudaEventDestroy(r.stop);
+  }
+  for (auto e : ctx->event_pool) cudaEventDestroy(e);
   cudaFree(ctx->status);
   delete ctx;
   return ARBGPU_OK;

@@ -48,6 +48,8 @@ struct BatchDotSrc {
   __device__ const BallsOut &out_view(int64_t d) const { return out[part(d)]; }
   __device__ int64_t out_index(int64_t d) const { return b_of(d); }
   __device__ int prec(int64_t d) const { return __ldg(precs + b_of(d)); }
+  int64_t units() const { return ndots_host; }
+  int64_t ndots_host;
 };
 
 // Classical product: entry (i, j) is the dot of row i of A and column j of B.  Consecutive warps
@@ -87,6 +89,7 @@ struct MatDotSrc {
     return i * ldc + j;
   }
   __device__ int prec(int64_t) const { return prec_v; }
+  int64_t units() const { return M * N * K; }
 };
 
 int dot_class_for_problem(int prec, int64_t max_terms, int max_nlimbs) {
@@ -104,6 +107,7 @@ static arbgpu_status launch_dot_src(arbgpu_ctx *ctx, const Src &src, int64_t ndo
   int64_t blocks = (ndots + 7) / 8;
   const int64_t cap = (int64_t)ctx->sm_count * 16;
   if (blocks > cap) blocks = cap;
+  LaunchScope scope(ctx, stream, "dot_kernel", src.units());
   switch (cmax) {
     case 0: dot_kernel<0, Src><<<(unsigned)blocks, threads, 0, stream>>>(src, ctx->status); break;
     case 1: dot_kernel<1, Src><<<(unsigned)blocks, threads, 0, stream>>>(src, ctx->status); break;
@@ -156,6 +160,7 @@ arbgpu_status launch_batched_dot(arbgpu_ctx *ctx, const arbgpu_balls *res,
   s.prec_max = prec_max;
   const int64_t terms_max = (complex_mode ? 2 * len_max : len_max);
   s.len_max = terms_max;
+  s.ndots_host = s.cplx ? 2 * batch : batch;
   const int cmax = dot_class_for_problem(prec_max, terms_max + 1, maxnl);
   if (cmax < 0) return ARBGPU_ERR_INVALID;
   return launch_dot_src(ctx, s, s.cplx ? 2 * batch : batch, cmax, stream);

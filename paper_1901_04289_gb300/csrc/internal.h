@@ -4,14 +4,39 @@
 #include <cstddef>
 #include <cstdint>
 #include <cuda_runtime.h>
+#include <vector>
 
 #include "arbgpu.h"
+
+// One traced kernel launch: a pair of events recorded around it on its stream.
+struct arbgpu_trace_rec {
+  const char *name;
+  cudaEvent_t start, stop;
+  int64_t units;  // algorithmic work units the launch processes (caller-defined per kernel)
+};
 
 struct arbgpu_ctx {
   int device;
   int sm_count;
-  int *status;  // device int: first recorded error code
+  int *status;       // device int: first recorded error code
+  int64_t launches;  // kernels launched through this context
+  bool trace;
+  std::vector<arbgpu_trace_rec> recs;
+  std::vector<cudaEvent_t> event_pool;
 };
+
+namespace arbgpu {
+
+// Bracket a kernel launch: counts it and, when tracing is on, records events around it.
+struct LaunchScope {
+  arbgpu_ctx *ctx;
+  cudaStream_t stream;
+  int idx;
+  LaunchScope(arbgpu_ctx *c, cudaStream_t s, const char *name, int64_t units = 0);
+  ~LaunchScope();
+};
+
+}  // namespace arbgpu
 
 namespace arbgpu {
 
