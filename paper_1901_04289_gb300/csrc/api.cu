@@ -217,7 +217,7 @@ arbgpu_status arbgpu_mat_mul_workspace_size(arbgpu_ctx *ctx, int64_t M, int64_t 
   (void)flags;
   if (!bytes) return ARBGPU_ERR_INVALID;
   *bytes = 0;
-  if (alg == ARBGPU_ALG_DOT) return ARBGPU_OK;
+  if (alg == ARBGPU_ALG_DOT || alg == ARBGPU_ALG_AUTO) return ARBGPU_OK;
   return ARBGPU_ERR_INVALID;  // the block path is added with its kernels
 }
 
