@@ -251,21 +251,4 @@ arbgpu_status arbgpu_mat_mul(arbgpu_ctx *ctx, const arbgpu_balls *C, const arbgp
   return ARBGPU_ERR_INVALID;
 }
 
-arbgpu_status arbgpu_int_mat_mul(arbgpu_ctx *ctx, uint64_t *T, int32_t t_limbs, const uint64_t *X,
-                                 int32_t x_limbs, const uint64_t *Y, int32_t y_limbs, int64_t M,
-                                 int64_t K, int64_t N, void *workspace, size_t ws_bytes,
-                                 void *stream) {
-  (void)ctx; (void)T; (void)t_limbs; (void)X; (void)x_limbs; (void)Y; (void)y_limbs;
-  (void)M; (void)K; (void)N; (void)workspace; (void)ws_bytes; (void)stream;
-  return ARBGPU_ERR_INVALID;
-}
-
-arbgpu_status arbgpu_int_mat_mul_workspace_size(arbgpu_ctx *ctx, int32_t x_limbs, int32_t y_limbs,
-                                                int64_t M, int64_t K, int64_t N, size_t *bytes) {
-  (void)ctx; (void)x_limbs; (void)y_limbs; (void)M; (void)K; (void)N;
-  if (!bytes) return ARBGPU_ERR_INVALID;
-  *bytes = 0;
-  return ARBGPU_ERR_INVALID;
-}
-
 }  // extern "C"

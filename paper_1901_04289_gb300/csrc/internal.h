@@ -55,6 +55,28 @@ arbgpu_status launch_matmul_dot(arbgpu_ctx *ctx, const arbgpu_balls *C, const ar
                                 int64_t lda, int64_t ldb, int64_t ldc, int32_t prec,
                                 int complex_mode, cudaStream_t stream);
 
+// Tensor-core digit GEMM (tc_gemm.cu): T = X * Y over Z from balanced base-256 digit planes.
+//   A: BF16 [SA][M][Kp], B: BF16 [SB][N][Kp] (both K contiguous, Kp a multiple of 64, zero padded)
+//   digits: uint8 [SA+SB-1][Mp][Np], carries: int32 [groups][Mp][Np] with Mp, Np = M, N rounded
+//   up to 128.  T[i][j] = sum_d digits[d][i][j] 256^d + sum_g carries[g][i][j] 256^dend(g), where
+//   dend(g) is the end of group g's diagonal range (digit_gemm_group_ends).
+struct DigitGemmArgs {
+  const void *A;
+  const void *B;
+  int M, N;
+  int64_t Kp;
+  int SA, SB;
+  int groups;
+  uint8_t *digits;
+  int32_t *carries;
+  const char *name;
+};
+arbgpu_status launch_digit_gemm(arbgpu_ctx *ctx, const DigitGemmArgs &a, cudaStream_t stream);
+int digit_gemm_groups(arbgpu_ctx *ctx, int M, int N, int ND);
+bool digit_gemm_fits(int SA, int SB, int64_t Kp);
+// The diagonal ranges the launcher uses: ends[g] = first diagonal after group g (g < groups).
+void digit_gemm_group_ends(int SA, int SB, int groups, int *ends);
+
 // Dot-kernel size class for a precision, a maximal term count and operand limb counts (-1: none).
 int dot_class_for_problem(int prec, int64_t max_terms, int max_nlimbs);
 

@@ -1,0 +1,335 @@
+// Host side of the tensor-core digit GEMM: TMA descriptors, diagonal-group schedule, launch.
+#include <cstdio>
+#include <mutex>
+
+#include "internal.h"
+#include "tc_gemm.cuh"
+
+namespace arbgpu {
+
+// ------------------------------------------------------------------------------ the kernel
+
+struct TgShared {
+  uint64_t full[TG_STAGES];
+  uint64_t empty[TG_STAGES];
+  uint64_t accf[2];
+  uint64_t acce[2];
+  uint64_t done;
+  uint32_t tmem_base;
+  int abort;
+};
+
+__global__ void __launch_bounds__(TG_THREADS, 1)
+    digit_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                      const __grid_constant__ DigitGemmParams P) {
+  extern __shared__ __align__(1024) uint8_t smem_raw[];
+  uint8_t *tiles = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  uint8_t *sA = tiles;
+  uint8_t *sB = tiles + (size_t)TG_STAGES * TG_TILE_BYTES;
+  TgShared *sh = (TgShared *)(tiles + (size_t)TG_STAGES * 2 * TG_TILE_BYTES);
+
+  const int warp = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31;
+  const int ntiles = P.tiles_m * P.tiles_n;
+  const int tile = blockIdx.x % ntiles;
+  const int group = blockIdx.x / ntiles;
+  const int mt = tile / P.tiles_n, nt = tile % P.tiles_n;
+  const int m0 = mt * TG_BM, n0 = nt * TG_BN;
+  const int d0 = P.dstart[group], d1 = P.dstart[group + 1];
+  const int nkb = P.Kp / TG_BK;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < TG_STAGES; ++s) {
+      mbar_init(&sh->full[s], 1);
+      mbar_init(&sh->empty[s], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&sh->accf[b], 1);
+      mbar_init(&sh->acce[b], TG_EPI_WARPS);
+    }
+    mbar_init(&sh->done, 1);
+    sh->abort = 0;
+    fence_mbar_init();
+  }
+  if (warp == 1) {
+    tmem_alloc(&sh->tmem_base, TG_TMEM_COLS);
+    tmem_relinquish();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = sh->tmem_base;
+  volatile int *abort = &sh->abort;
+
+  auto give_up = [&]() {
+    *abort = 1;
+    set_status(P.status, ARBGPU_ERR_TIMEOUT);
+  };
+
+  if (warp == 0) {
+    // ------------------------------------------------------------ TMA producer
+    if (lane == 0) {
+      tma_prefetch_desc(&tmA);
+      tma_prefetch_desc(&tmB);
+      uint32_t item = 0;
+      bool ok = true;
+      for (int d = d0; d < d1 && ok; ++d) {
+        const int jlo = max(0, d - (P.SB - 1)), jhi = min(d, P.SA - 1);
+        for (int j = jlo; j <= jhi && ok; ++j) {
+          const int l = d - j;
+          for (int kb = 0; kb < nkb; ++kb, ++item) {
+            const int s = item % TG_STAGES;
+            const uint32_t ph = (item / TG_STAGES) & 1;
+            if (!mbar_wait(&sh->empty[s], ph ^ 1, abort)) {
+              give_up();
+              ok = false;
+              break;
+            }
+            mbar_arrive_expect_tx(&sh->full[s], 2 * TG_TILE_BYTES);
+            tma_load_3d(sA + (size_t)s * TG_TILE_BYTES, &tmA, &sh->full[s], kb * TG_BK, m0, j);
+            tma_load_3d(sB + (size_t)s * TG_TILE_BYTES, &tmB, &sh->full[s], kb * TG_BK, n0, l);
+          }
+        }
+      }
+      // before leaving, let every load this thread issued land (bounded)
+      const uint32_t first = item > (uint32_t)TG_STAGES ? item - TG_STAGES : 0;
+      for (uint32_t it = first; it < item; ++it)
+        mbar_wait(&sh->full[it % TG_STAGES], (it / TG_STAGES) & 1, abort);
+    }
+  } else if (warp == 1) {
+    // ------------------------------------------------------------ MMA issuer
+    if (lane == 0) {
+      const uint32_t idesc = idesc_bf16_f32(TG_BM, TG_BN);
+      uint32_t item = 0, chain = 0;
+      bool ok = true;
+      for (int d = d0; d < d1 && ok; ++d) {
+        const int jlo = max(0, d - (P.SB - 1)), jhi = min(d, P.SA - 1);
+        int kbc = 0;
+        for (int j = jlo; j <= jhi && ok; ++j) {
+          for (int kb = 0; kb < nkb; ++kb, ++item) {
+            const uint32_t buf = chain & 1;
+            if (kbc == 0) {  // start of a chain: the accumulator must have been drained
+              if (!mbar_wait(&sh->acce[buf], ((chain >> 1) & 1) ^ 1, abort)) {
+                give_up();
+                ok = false;
+                break;
+              }
+              tc_fence_after();
+            }
+            const int s = item % TG_STAGES;
+            if (!mbar_wait(&sh->full[s], (item / TG_STAGES) & 1, abort)) {
+              give_up();
+              ok = false;
+              break;
+            }
+            tc_fence_after();
+            const uint64_t ad = sw128_desc(smem_u32(sA + (size_t)s * TG_TILE_BYTES));
+            const uint64_t bd = sw128_desc(smem_u32(sB + (size_t)s * TG_TILE_BYTES));
+#pragma unroll
+            for (int kk = 0; kk < TG_BK / 16; ++kk)
+              umma_bf16(tmem + buf * TG_BN, ad + 2 * kk, bd + 2 * kk, idesc,
+                        (kbc > 0 || kk > 0) ? 1u : 0u);
+            umma_commit(&sh->empty[s]);
+            ++kbc;
+            const bool diag_end = (j == jhi) && (kb == nkb - 1);
+            if (kbc == TG_CHAIN_KB || diag_end) {
+              umma_commit(&sh->accf[buf]);
+              ++chain;
+              kbc = 0;
+            }
+          }
+        }
+      }
+      umma_commit(&sh->done);
+      mbar_wait(&sh->done, 0, abort);
+    }
+  } else {
+    // ------------------------------------------------------------ drain / carry epilogue
+    const int q = warp & 3;             // TMEM lane quadrant this warp may access
+    const int half = (warp - 2) >> 2;   // which 64 of the tile's 128 columns
+    const int row = 32 * q + lane;
+    const uint32_t lane_addr = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(half * 64);
+    int32_t R[64];
+#pragma unroll
+    for (int c = 0; c < 64; ++c) R[c] = 0;
+    const int64_t gm = m0 + row;
+    const int64_t gcol = n0 + half * 64;
+    uint32_t chain = 0;
+    bool ok = true;
+    for (int d = d0; d < d1 && ok; ++d) {
+      const int jlo = max(0, d - (P.SB - 1)), jhi = min(d, P.SA - 1);
+      const int nchains_d = ((jhi - jlo + 1) * nkb + TG_CHAIN_KB - 1) / TG_CHAIN_KB;
+      // chains never straddle a pair boundary when nkb is a multiple of TG_CHAIN_KB; in general a
+      // chain ends every TG_CHAIN_KB k-blocks or at the end of the diagonal
+      for (int cc = 0; cc < nchains_d; ++cc, ++chain) {
+        const uint32_t buf = chain & 1;
+        // every lane waits, then the warp agrees, so the .sync.aligned TMEM loads run converged
+        const bool got = __all_sync(0xffffffffu, mbar_wait(&sh->accf[buf], (chain >> 1) & 1, abort));
+        if (!got) {
+          if (lane == 0) give_up();
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        uint32_t v[32];
+        tmem_ld32(lane_addr + buf * TG_BN, v);
+        tmem_wait_ld();
+#pragma unroll
+        for (int c = 0; c < 32; ++c)
+          R[c] += (int32_t)(__float_as_uint(__uint_as_float(v[c]) + TG_MAGIC) - TG_MAGIC_BITS);
+        tmem_ld32(lane_addr + buf * TG_BN + 32, v);
+        tmem_wait_ld();
+#pragma unroll
+        for (int c = 0; c < 32; ++c)
+          R[32 + c] +=
+              (int32_t)(__float_as_uint(__uint_as_float(v[c]) + TG_MAGIC) - TG_MAGIC_BITS);
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&sh->acce[buf]);
+      }
+      if (!ok) break;
+      // digit d of T: the low byte of R; carry the rest
+      uint32_t packed[16];
+#pragma unroll
+      for (int c = 0; c < 16; ++c) {
+        packed[c] = ((uint32_t)(R[4 * c] & 255)) | ((uint32_t)(R[4 * c + 1] & 255) << 8) |
+                    ((uint32_t)(R[4 * c + 2] & 255) << 16) | ((uint32_t)(R[4 * c + 3] & 255) << 24);
+      }
+#pragma unroll
+      for (int c = 0; c < 64; ++c) R[c] >>= 8;
+      uint4 *dst = (uint4 *)(P.digits + ((int64_t)d * P.Mp + gm) * P.Np + gcol);
+#pragma unroll
+      for (int c = 0; c < 4; ++c)
+        dst[c] = make_uint4(packed[4 * c], packed[4 * c + 1], packed[4 * c + 2], packed[4 * c + 3]);
+    }
+    int4 *cdst = (int4 *)(P.carries + ((int64_t)group * P.Mp + gm) * P.Np + gcol);
+#pragma unroll
+    for (int c = 0; c < 16; ++c) cdst[c] = make_int4(R[4 * c], R[4 * c + 1], R[4 * c + 2], R[4 * c + 3]);
+  }
+
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 1) {
+    __syncwarp();
+    tmem_dealloc(tmem, TG_TMEM_COLS);
+  }
+}
+
+typedef CUresult (*PFN_tmapEncodeTiled)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
+                                        const cuuint64_t *, const cuuint64_t *, const cuuint32_t *,
+                                        const cuuint32_t *, CUtensorMapInterleave,
+                                        CUtensorMapSwizzle, CUtensorMapL2promotion,
+                                        CUtensorMapFloatOOBfill);
+
+static PFN_tmapEncodeTiled encode_fn() {
+  static PFN_tmapEncodeTiled fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, []() {
+    cudaDriverEntryPointQueryResult q;
+    void *p = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (PFN_tmapEncodeTiled)p;
+  });
+  return fn;
+}
+
+// 3-D map over digit planes [planes][rows][Kp] of BF16, box = 64 (k) x 128 (rows) x 1 plane.
+static bool make_plane_map(CUtensorMap *tm, const void *base, int64_t Kp, int64_t rows,
+                           int64_t planes) {
+  PFN_tmapEncodeTiled enc = encode_fn();
+  if (!enc) return false;
+  cuuint64_t dims[3] = {(cuuint64_t)Kp, (cuuint64_t)rows, (cuuint64_t)planes};
+  cuuint64_t strides[2] = {(cuuint64_t)(Kp * 2), (cuuint64_t)(Kp * 2 * rows)};
+  cuuint32_t box[3] = {(cuuint32_t)TG_BK, (cuuint32_t)TG_BM, 1};
+  cuuint32_t estr[3] = {1, 1, 1};
+  CUresult r = enc(tm, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void *>(base), dims, strides,
+                   box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
+int digit_gemm_groups(arbgpu_ctx *ctx, int M, int N, int ND) {
+  const int tiles = ((M + TG_BM - 1) / TG_BM) * ((N + TG_BN - 1) / TG_BN);
+  int g = ctx->sm_count / tiles;  // one wave of CTAs (one CTA per SM)
+  if (g < 1) g = 1;
+  if (g > ND) g = ND;
+  if (g > TG_MAXG) g = TG_MAXG;
+  return g;
+}
+
+// Largest |running sum| bound of the drain: pairs * Kp * 2^14 plus the carried part.
+bool digit_gemm_fits(int SA, int SB, int64_t Kp) {
+  const int64_t pairs = SA < SB ? SA : SB;
+  return pairs * Kp * 16384 + (1 << 24) < ((int64_t)1 << 31);
+}
+
+// Split the SA + SB - 1 diagonals into `groups` contiguous ranges of about equal pair counts (every
+// range non-empty); ends[g] is the first diagonal after range g.
+void digit_gemm_group_ends(int SA, int SB, int groups, int *ends) {
+  const int ND = SA + SB - 1;
+  auto pairs = [&](int d) {
+    const int jlo = d - (SB - 1) > 0 ? d - (SB - 1) : 0;
+    const int jhi = d < SA - 1 ? d : SA - 1;
+    return (int64_t)(jhi - jlo + 1);
+  };
+  int64_t total = 0;
+  for (int d = 0; d < ND; ++d) total += pairs(d);
+  int64_t acc = 0;
+  int g = 0;
+  for (int d = 0; d < ND && g + 1 < groups; ++d) {
+    acc += pairs(d);
+    const int rest_d = ND - (d + 1), rest_g = groups - (g + 1);
+    if (acc * groups >= total * (int64_t)(g + 1) || rest_d == rest_g) ends[g++] = d + 1;
+  }
+  ends[groups - 1] = ND;
+}
+
+arbgpu_status launch_digit_gemm(arbgpu_ctx *ctx, const DigitGemmArgs &a, cudaStream_t stream) {
+  if (a.M <= 0 || a.N <= 0 || a.Kp <= 0 || (a.Kp % TG_BK) != 0 || a.SA < 1 || a.SB < 1)
+    return ARBGPU_ERR_INVALID;
+  if (!digit_gemm_fits(a.SA, a.SB, a.Kp)) return ARBGPU_ERR_LIMIT;
+  DigitGemmParams P{};
+  P.M = a.M;
+  P.N = a.N;
+  P.Kp = a.Kp;
+  P.SA = a.SA;
+  P.SB = a.SB;
+  P.ND = a.SA + a.SB - 1;
+  P.tiles_m = (a.M + TG_BM - 1) / TG_BM;
+  P.tiles_n = (a.N + TG_BN - 1) / TG_BN;
+  P.Mp = (int64_t)P.tiles_m * TG_BM;
+  P.Np = (int64_t)P.tiles_n * TG_BN;
+  P.digits = a.digits;
+  P.carries = a.carries;
+  P.status = ctx->status;
+  const int G = a.groups;
+  if (G < 1 || G > TG_MAXG || G > P.ND) return ARBGPU_ERR_INVALID;
+  P.groups = G;
+  int ends[TG_MAXG];
+  digit_gemm_group_ends(a.SA, a.SB, G, ends);
+  P.dstart[0] = 0;
+  for (int t = 0; t < G; ++t) P.dstart[t + 1] = ends[t];
+  for (int t = 0; t < G; ++t)
+    if (P.dstart[t + 1] <= P.dstart[t]) return ARBGPU_ERR_INVALID;
+
+  CUtensorMap tmA, tmB;
+  if (!make_plane_map(&tmA, a.A, a.Kp, a.M, a.SA) || !make_plane_map(&tmB, a.B, a.Kp, a.N, a.SB))
+    return ARBGPU_ERR_CUDA;
+  static bool attr_set = false;
+  if (!attr_set) {
+    if (cudaFuncSetAttribute(digit_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)TG_SMEM_BYTES) != cudaSuccess)
+      return ARBGPU_ERR_CUDA;
+    attr_set = true;
+  }
+  const int grid = P.tiles_m * P.tiles_n * G;
+  LaunchScope scope(ctx, stream, a.name ? a.name : "digit_gemm",
+                    (int64_t)(a.SA) * a.SB * (int64_t)a.M * a.N * a.Kp);
+  digit_gemm_kernel<<<grid, TG_THREADS, TG_SMEM_BYTES, stream>>>(tmA, tmB, P);
+  return cudaGetLastError() == cudaSuccess ? ARBGPU_OK : ARBGPU_ERR_CUDA;
+}
+
+}  // namespace arbgpu
