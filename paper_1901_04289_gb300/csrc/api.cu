@@ -202,23 +202,27 @@ arbgpu_status arbgpu_dot(arbgpu_ctx *ctx, const arbgpu_balls *res, const arbgpu_
                             batch, prec_max, len_max, complex_mode, (cudaStream_t)stream);
 }
 
+// AUTO: the block algorithm from this size on (the paper's default cutoff lies at N = 40..60).
+static bool auto_uses_block(int64_t M, int64_t K, int64_t N) {
+  return M >= 48 && N >= 48 && K >= 48;
+}
+
 arbgpu_status arbgpu_mat_mul_workspace_size(arbgpu_ctx *ctx, int64_t M, int64_t K, int64_t N,
                                             int32_t prec, int32_t a_nlimbs, int32_t b_nlimbs,
                                             int complex_mode, int alg, uint32_t flags,
                                             size_t *bytes) {
-  (void)ctx;
-  (void)M;
-  (void)K;
-  (void)N;
-  (void)prec;
   (void)a_nlimbs;
   (void)b_nlimbs;
-  (void)complex_mode;
   (void)flags;
-  if (!bytes) return ARBGPU_ERR_INVALID;
+  if (!ctx || !bytes || M < 0 || K < 0 || N < 0 || prec < 2 || prec > 1024)
+    return ARBGPU_ERR_INVALID;
   *bytes = 0;
-  if (alg == ARBGPU_ALG_DOT || alg == ARBGPU_ALG_AUTO) return ARBGPU_OK;
-  return ARBGPU_ERR_INVALID;  // the block path is added with its kernels
+  if (alg == ARBGPU_ALG_DOT) return ARBGPU_OK;
+  if (alg != ARBGPU_ALG_BLOCK && alg != ARBGPU_ALG_AUTO) return ARBGPU_ERR_INVALID;
+  if (complex_mode) return ARBGPU_OK;  // complex products use the dot kernel for now
+  if (alg == ARBGPU_ALG_AUTO && !auto_uses_block(M, K, N)) return ARBGPU_OK;
+  *bytes = block_workspace_size(ctx, M, K, N, prec);
+  return ARBGPU_OK;
 }
 
 arbgpu_status arbgpu_mat_mul(arbgpu_ctx *ctx, const arbgpu_balls *C, const arbgpu_balls *A,
@@ -245,10 +249,19 @@ arbgpu_status arbgpu_mat_mul(arbgpu_ctx *ctx, const arbgpu_balls *C, const arbgp
     }
   }
   if (cudaSetDevice(ctx->device) != cudaSuccess) return ARBGPU_ERR_CUDA;
-  if (alg == ARBGPU_ALG_DOT || alg == ARBGPU_ALG_AUTO)
-    return launch_matmul_dot(ctx, C, A, B, M, K, N, lda, ldb, ldc, prec, complex_mode,
-                             (cudaStream_t)stream);
-  return ARBGPU_ERR_INVALID;
+  if (alg != ARBGPU_ALG_DOT && alg != ARBGPU_ALG_BLOCK && alg != ARBGPU_ALG_AUTO)
+    return ARBGPU_ERR_INVALID;
+  const bool try_block = !complex_mode && (alg == ARBGPU_ALG_BLOCK ||
+                                           (alg == ARBGPU_ALG_AUTO && auto_uses_block(M, K, N)));
+  if (try_block && K > 0) {
+    bool used = false;
+    arbgpu_status st = block_matmul_real(ctx, C[0], A[0], B[0], M, K, N, lda, ldb, ldc, prec,
+                                         workspace, ws_bytes, (cudaStream_t)stream, &used);
+    if (used || st != ARBGPU_ERR_LIMIT) return st;
+    // not a single exponent block (or special values): the classical algorithm handles it
+  }
+  return launch_matmul_dot(ctx, C, A, B, M, K, N, lda, ldb, ldc, prec, complex_mode,
+                           (cudaStream_t)stream);
 }
 
 }  // extern "C"

@@ -77,6 +77,14 @@ bool digit_gemm_fits(int SA, int SB, int64_t Kp);
 // The diagonal ranges the launcher uses: ends[g] = first diagonal after group g (g < groups).
 void digit_gemm_group_ends(int SA, int SB, int groups, int *ends);
 
+// Block algorithm (block.cu).  block_matmul_real returns ARBGPU_ERR_LIMIT (and *used_block =
+// false) when the inputs are not a single exponent block or hold special values.
+size_t block_workspace_size(arbgpu_ctx *ctx, int64_t M, int64_t K, int64_t N, int prec);
+arbgpu_status block_matmul_real(arbgpu_ctx *ctx, const arbgpu_balls &C, const arbgpu_balls &A,
+                                const arbgpu_balls &B, int64_t M, int64_t K, int64_t N,
+                                int64_t lda, int64_t ldb, int64_t ldc, int prec, void *workspace,
+                                size_t ws_bytes, cudaStream_t s, bool *used_block);
+
 // Dot-kernel size class for a precision, a maximal term count and operand limb counts (-1: none).
 int dot_class_for_problem(int prec, int64_t max_terms, int max_nlimbs);
 
