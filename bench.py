@@ -286,6 +286,8 @@ def main():
         d[0] += kms
         d[1] += 1
         d[2] += units
+    kernels = {k: {"launches": v[1], "ms_total": round(v[0], 4),
+                   "share": round(v[0] / ms, 4) if ms else None} for k, v in per.items()}
     dom = max(per.items(), key=lambda kv: kv[1][0]) if per else None
     roofline = None
     if dom:
@@ -334,7 +336,8 @@ def main():
                            "parallelism": f"replicas x{world}"},
                 "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
                         "d2h_bytes_per_step": d2h},
-                "gpu_launches": launches, "roofline": roofline, "cpu_baseline": cpu,
+                "gpu_launches": launches, "roofline": roofline, "kernels": kernels,
+                "cpu_baseline": cpu,
                 "clocks": clocks, "compare": compare, "peaks_source": peaks["_source"]}
         print(json.dumps(line), flush=True)
     if world > 1:

@@ -422,7 +422,7 @@ __global__ void block_round_kernel(const RoundArgs a) {
       const uint64_t w1 = (li + 1 >= 0 && li + 1 < nw) ? T[li + 1] : 0;
       const uint64_t f = bi ? ((w0 >> bi) | (w1 << (64 - bi))) : w0;
       C.limbs[(int64_t)q * C.stride + oi] = f;
-      if (f) nsig = nl - q;
+      if (f && nsig == 0) nsig = nl - q;  // lowest nonzero limb fixes the limb count
     }
     oexp = sigma + L;
     fl = (neg ? ARBGPU_FLAG_SIGN : 0u) | ((uint32_t)nsig << ARBGPU_NSIG_SHIFT);
