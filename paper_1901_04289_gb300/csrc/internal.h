@@ -85,6 +85,13 @@ arbgpu_status block_matmul_real(arbgpu_ctx *ctx, const arbgpu_balls &C, const ar
                                 int64_t lda, int64_t ldb, int64_t ldc, int prec, void *workspace,
                                 size_t ws_bytes, cudaStream_t s, bool *used_block);
 
+// Integer matrix product on a caller-provided workspace (intmm.cu); ctx->device must be current.
+arbgpu_status int_mat_mul_run(arbgpu_ctx *ctx, uint64_t *T, int32_t t_limbs, const uint64_t *X,
+                              int32_t x_limbs, const uint64_t *Y, int32_t y_limbs, int64_t M,
+                              int64_t K, int64_t N, void *workspace, size_t ws_bytes,
+                              cudaStream_t s);
+size_t int_mat_mul_workspace(arbgpu_ctx *ctx, int xl, int yl, int64_t M, int64_t K, int64_t N);
+
 // Dot-kernel size class for a precision, a maximal term count and operand limb counts (-1: none).
 int dot_class_for_problem(int prec, int64_t max_terms, int max_nlimbs);
 

@@ -122,28 +122,22 @@ IntWs int_ws_layout(arbgpu_ctx *ctx, int xl, int yl, int64_t M, int64_t K, int64
 
 }  // namespace
 
-extern "C" {
+namespace arbgpu {
 
-arbgpu_status arbgpu_int_mat_mul_workspace_size(arbgpu_ctx *ctx, int32_t x_limbs, int32_t y_limbs,
-                                                int64_t M, int64_t K, int64_t N, size_t *bytes) {
-  if (!ctx || !bytes || x_limbs < 1 || y_limbs < 1 || x_limbs > IM_MAX_LIMBS ||
-      y_limbs > IM_MAX_LIMBS || M < 0 || K < 0 || N < 0)
-    return ARBGPU_ERR_INVALID;
-  *bytes = int_ws_layout(ctx, x_limbs, y_limbs, M, K, N).total;
-  return ARBGPU_OK;
+size_t int_mat_mul_workspace(arbgpu_ctx *ctx, int xl, int yl, int64_t M, int64_t K, int64_t N) {
+  return int_ws_layout(ctx, xl, yl, M, K, N).total;
 }
 
-arbgpu_status arbgpu_int_mat_mul(arbgpu_ctx *ctx, uint64_t *T, int32_t t_limbs, const uint64_t *X,
-                                 int32_t x_limbs, const uint64_t *Y, int32_t y_limbs, int64_t M,
-                                 int64_t K, int64_t N, void *workspace, size_t ws_bytes,
-                                 void *stream) {
+arbgpu_status int_mat_mul_run(arbgpu_ctx *ctx, uint64_t *T, int32_t t_limbs, const uint64_t *X,
+                              int32_t x_limbs, const uint64_t *Y, int32_t y_limbs, int64_t M,
+                              int64_t K, int64_t N, void *workspace, size_t ws_bytes,
+                              cudaStream_t s) {
   if (!ctx || x_limbs < 1 || y_limbs < 1 || x_limbs > IM_MAX_LIMBS || y_limbs > IM_MAX_LIMBS ||
       t_limbs < 1 || t_limbs > 2 * IM_MAX_LIMBS + 4 || M < 0 || K < 0 || N < 0)
     return ARBGPU_ERR_INVALID;
   if (M == 0 || N == 0) return ARBGPU_OK;
   if (!T || (K > 0 && (!X || !Y))) return ARBGPU_ERR_INVALID;
   if (M > (1 << 30) || N > (1 << 30) || K > (1 << 30)) return ARBGPU_ERR_INVALID;
-  cudaStream_t s = (cudaStream_t)stream;
   if (cudaSetDevice(ctx->device) != cudaSuccess) return ARBGPU_ERR_CUDA;
   if (K == 0) {
     return cudaMemsetAsync(T, 0, sizeof(uint64_t) * t_limbs * M * N, s) == cudaSuccess
@@ -182,6 +176,27 @@ arbgpu_status arbgpu_int_mat_mul(arbgpu_ctx *ctx, uint64_t *T, int32_t t_limbs, 
         digits, carries, w.ND, w.G, ends, M, N, w.Mp, w.Np, T, t_limbs);
   }
   return cudaGetLastError() == cudaSuccess ? ARBGPU_OK : ARBGPU_ERR_CUDA;
+}
+
+}  // namespace arbgpu
+
+extern "C" {
+
+arbgpu_status arbgpu_int_mat_mul_workspace_size(arbgpu_ctx *ctx, int32_t x_limbs, int32_t y_limbs,
+                                                int64_t M, int64_t K, int64_t N, size_t *bytes) {
+  if (!ctx || !bytes || x_limbs < 1 || y_limbs < 1 || x_limbs > IM_MAX_LIMBS ||
+      y_limbs > IM_MAX_LIMBS || M < 0 || K < 0 || N < 0)
+    return ARBGPU_ERR_INVALID;
+  *bytes = int_ws_layout(ctx, x_limbs, y_limbs, M, K, N).total;
+  return ARBGPU_OK;
+}
+
+arbgpu_status arbgpu_int_mat_mul(arbgpu_ctx *ctx, uint64_t *T, int32_t t_limbs, const uint64_t *X,
+                                 int32_t x_limbs, const uint64_t *Y, int32_t y_limbs, int64_t M,
+                                 int64_t K, int64_t N, void *workspace, size_t ws_bytes,
+                                 void *stream) {
+  return arbgpu::int_mat_mul_run(ctx, T, t_limbs, X, x_limbs, Y, y_limbs, M, K, N, workspace,
+                                 ws_bytes, (cudaStream_t)stream);
 }
 
 }  // extern "C"

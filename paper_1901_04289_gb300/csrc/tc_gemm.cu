@@ -318,12 +318,13 @@ arbgpu_status launch_digit_gemm(arbgpu_ctx *ctx, const DigitGemmArgs &a, cudaStr
   CUtensorMap tmA, tmB;
   if (!make_plane_map(&tmA, a.A, a.Kp, a.M, a.SA) || !make_plane_map(&tmB, a.B, a.Kp, a.N, a.SB))
     return ARBGPU_ERR_CUDA;
-  static bool attr_set = false;
-  if (!attr_set) {
+  static bool attr_set[256] = {};
+  const int dev = ctx->device & 255;
+  if (!attr_set[dev]) {  // per device: the attribute applies to the current device
     if (cudaFuncSetAttribute(digit_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)TG_SMEM_BYTES) != cudaSuccess)
       return ARBGPU_ERR_CUDA;
-    attr_set = true;
+    attr_set[dev] = true;
   }
   const int grid = P.tiles_m * P.tiles_n * G;
   LaunchScope scope(ctx, stream, a.name ? a.name : "digit_gemm",
