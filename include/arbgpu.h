@@ -199,6 +199,30 @@ arbgpu_status arbgpu_int_mat_mul(arbgpu_ctx *ctx, uint64_t *T, int32_t t_limbs, 
 arbgpu_status arbgpu_int_mat_mul_workspace_size(arbgpu_ctx *ctx, int32_t x_limbs, int32_t y_limbs,
                                                 int64_t M, int64_t K, int64_t N, size_t *bytes);
 
+/*
+ * Allocation-free integer product.  The paper has no counterpart: this is a convenience of this
+ * library for callers that cannot call cudaMalloc -- for example a host program whose device
+ * memory is entirely held by another allocator's pool, or a thread that must not enter the CUDA
+ * allocator at all.  It computes exactly what arbgpu_int_mat_mul computes (same argument meaning
+ * and layout) but allocates nothing and needs no context: its scratch space is one device array of
+ * ARBGPU_NOALLOC_SCRATCH_BYTES inside the library, which every GPU that loads the library keeps
+ * until the process exits.
+ *   - Runs on the current device and on `stream`.  The first call on each device looks up the
+ *     array's device address (cudaGetSymbolAddress with that device current); make that first
+ *     call before any stream capture.
+ *   - Sizes whose scratch would exceed ARBGPU_NOALLOC_SCRATCH_BYTES are rejected synchronously
+ *     with ARBGPU_ERR_LIMIT (arbgpu_int_mat_mul_workspace_size gives the scratch a size needs).
+ *   - Every call shares the one array, which keeps the last call's contents: calls whose GPU work
+ *     overlaps (other streams, other host threads) race; order them on one stream.
+ *   - status: optional device int (NULL allowed); the call sets it to 0 and the kernels record
+ *     the first device-side error (ARBGPU_ERR_TIMEOUT) there.
+ */
+#define ARBGPU_NOALLOC_SCRATCH_BYTES ((size_t)32 << 20)
+arbgpu_status arbgpu_int_mat_mul_noalloc(uint64_t *T, int32_t t_limbs, const uint64_t *X,
+                                         int32_t x_limbs, const uint64_t *Y, int32_t y_limbs,
+                                         int64_t M, int64_t K, int64_t N, int *status,
+                                         void *stream);
+
 #ifdef __cplusplus
 }
 #endif

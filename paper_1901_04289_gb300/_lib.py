@@ -83,6 +83,8 @@ def lib():
         L.arbgpu_int_mat_mul.argtypes = [vp, vp, i32, vp, i32, vp, i32, i64, i64, i64, vp, sz, vp]
         L.arbgpu_int_mat_mul_workspace_size.argtypes = [vp, i32, i32, i64, i64, i64,
                                                         C.POINTER(C.c_size_t)]
+        L.arbgpu_int_mat_mul_noalloc.argtypes = [vp, i32, vp, i32, vp, i32, i64, i64, i64, vp, vp]
+        L.arbgpu_int_mat_mul_noalloc.restype = C.c_int
         L.arbgpu_launch_count.argtypes = [vp, C.POINTER(C.c_int64)]
         L.arbgpu_trace_enable.argtypes = [vp, C.c_int]
         L.arbgpu_trace_read.argtypes = [vp, C.POINTER(CTrace), i32, C.POINTER(C.c_int32)]
@@ -107,4 +109,5 @@ def exported_symbols():
     return ["arbgpu_create", "arbgpu_destroy", "arbgpu_get_status", "arbgpu_status_string",
             "arbgpu_version", "arbgpu_launch_count", "arbgpu_trace_enable", "arbgpu_trace_read",
             "arbgpu_dot", "arbgpu_mat_mul", "arbgpu_mat_mul_workspace_size",
-            "arbgpu_int_mat_mul", "arbgpu_int_mat_mul_workspace_size"]
+            "arbgpu_int_mat_mul", "arbgpu_int_mat_mul_workspace_size",
+            "arbgpu_int_mat_mul_noalloc"]
