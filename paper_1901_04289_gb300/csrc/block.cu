@@ -13,6 +13,7 @@
 //   round  C_ij = RNE_p(T_ij 2^(-e_i - f_j)) (one rounding of the exact entry) and
 //          R_ij >= eps_round + P1 2^(...) + P2 2^(...), rounded up to a 30-bit radius.
 #include <cstring>
+#include <vector>
 
 #include "internal.h"
 #include "tc_gemm.cuh"
@@ -71,15 +72,35 @@ __device__ __forceinline__ EntryScan scan_entry(const BallsView &v, int64_t idx)
   return s;
 }
 
-// One warp per row of A (lanes over k): row top / bottom / radius top.
+// Inner-dimension range of scan launch row blockIdx.y: the whole of [0, K) when `blocks` is null,
+// else block blockIdx.y of the plan ([start, stop, basecase] triples).  Returns false for a
+// basecase block (nothing to scan).
+__device__ __forceinline__ bool scan_range(const int32_t *blocks, int64_t K, int64_t &k0,
+                                           int64_t &k1) {
+  if (!blocks) {
+    k0 = 0;
+    k1 = K;
+    return true;
+  }
+  const int b = blockIdx.y;
+  k0 = blocks[3 * b];
+  k1 = blocks[3 * b + 1];
+  return blocks[3 * b + 2] == 0;
+}
+
+// One warp per row of A (lanes over k): row top / bottom / radius top over the scan range.
 __global__ void scan_rows_kernel(const BallsView A, int64_t M, int64_t K, int64_t lda,
-                                 int64_t *rtop, int64_t *rbot, int64_t *rrad, BlockStats *st) {
+                                 const int32_t *blocks, int64_t *rtop, int64_t *rbot,
+                                 int64_t *rrad, BlockStats *st) {
   const int lane = threadIdx.x & 31;
   const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  if (i >= M) return;
+  int64_t k0, k1;
+  if (i >= M || !scan_range(blocks, K, k0, k1)) return;
+  const int64_t ob = (int64_t)blockIdx.y * M;
+  st += blockIdx.y;
   int64_t top = INT64_MIN, bot = INT64_MAX, rad = INT64_MIN, pm = 0;
   bool special = false, anyrad = false;
-  for (int64_t k = lane; k < K; k += 32) {
+  for (int64_t k = k0 + lane; k < k1; k += 32) {
     EntryScan e = scan_entry(A, i * lda + k);
     special |= e.special;
     if (e.nz) {
@@ -102,9 +123,9 @@ __global__ void scan_rows_kernel(const BallsView A, int64_t M, int64_t K, int64_
   special = __any_sync(0xffffffffu, special);
   anyrad = __any_sync(0xffffffffu, anyrad);
   if (lane == 0) {
-    rtop[i] = top;
-    rbot[i] = bot;
-    rrad[i] = rad;
+    rtop[ob + i] = top;
+    rbot[ob + i] = bot;
+    rrad[ob + i] = rad;
     if (top != INT64_MIN) atomic_max_i64(&st->hA, top - bot);
     atomic_max_i64(&st->pA, pm);
     if (special) atomicOr(&st->special, 1);
@@ -114,16 +135,20 @@ __global__ void scan_rows_kernel(const BallsView A, int64_t M, int64_t K, int64_
 
 // Columns of B: block (32 columns) x (32 k-slices); reads coalesced along the row.
 __global__ void scan_cols_kernel(const BallsView B, int64_t K, int64_t N, int64_t ldb,
-                                 int64_t *ctop, int64_t *cbot, int64_t *crad, int64_t *cplus,
-                                 BlockStats *st) {
+                                 const int32_t *blocks, int64_t *ctop, int64_t *cbot,
+                                 int64_t *crad, int64_t *cplus, BlockStats *st) {
   __shared__ int64_t s_top[32][33], s_bot[32][33], s_rad[32][33], s_pm[32][33];
   __shared__ int s_flags[32][33];
+  int64_t k0, k1;
+  if (!scan_range(blocks, K, k0, k1)) return;  // uniform over the CTA
+  const int64_t ob = (int64_t)blockIdx.y * N;
+  st += blockIdx.y;
   const int tx = threadIdx.x, ty = threadIdx.y;
   const int64_t j = (int64_t)blockIdx.x * 32 + tx;
   int64_t top = INT64_MIN, bot = INT64_MAX, rad = INT64_MIN, pm = 0;
   int flags = 0;
   if (j < N) {
-    for (int64_t k = ty; k < K; k += 32) {
+    for (int64_t k = k0 + ty; k < k1; k += 32) {
       EntryScan e = scan_entry(B, k * ldb + j);
       if (e.special) flags |= 1;
       if (e.nz) {
@@ -151,12 +176,12 @@ __global__ void scan_cols_kernel(const BallsView B, int64_t K, int64_t N, int64_
       pm = max((long long)pm, (long long)s_pm[y][tx]);
       flags |= s_flags[y][tx];
     }
-    ctop[j] = top;
-    cbot[j] = bot;
-    crad[j] = rad;
+    ctop[ob + j] = top;
+    cbot[ob + j] = bot;
+    crad[ob + j] = rad;
     // |b| + r_b < 2^(max(top, rexp) + 1)
     const int64_t mx = top > rad ? top : rad;
-    cplus[j] = mx == INT64_MIN ? INT64_MIN : mx + 1;
+    cplus[ob + j] = mx == INT64_MIN ? INT64_MIN : mx + 1;
     if (top != INT64_MIN) atomic_max_i64(&st->hB, top - bot);
     atomic_max_i64(&st->pB, pm);
     if (flags & 1) atomicOr(&st->special, 1);
@@ -244,8 +269,9 @@ struct SplitOut {
 // Split A (rows = M, row-major lda) or B (rows = N, read transposed from K x N, ldb).
 //   A: mid = E A; r1 = U(|A|) under rowtop; r2 = U(R_A) under rowrad.
 //   B: mid = B F; r1 = V(R_B) under colrad; r2 = V(|B| + R_B) under colplus.
-__global__ void split_kernel(const BallsView X, bool is_b, int64_t rows, int64_t K, int64_t Kp,
-                             int64_t ld, int S, const int64_t *bot, const int64_t *top,
+//   Columns [k0, k0 + K) of the operand form the block; columns K..Kp of the planes are zero.
+__global__ void split_kernel(const BallsView X, bool is_b, int64_t rows, int64_t k0, int64_t K,
+                             int64_t Kp, int64_t ld, int S, const int64_t *bot, const int64_t *top,
                              const int64_t *radtop, const int64_t *plustop, SplitOut o) {
   const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= rows * Kp) return;
@@ -259,7 +285,7 @@ __global__ void split_kernel(const BallsView X, bool is_b, int64_t rows, int64_t
     if (o.r2) o.r2[off] = o.r2[plane + off] = z;
     return;
   }
-  const int64_t e = is_b ? (k * ld + r) : (r * ld + k);
+  const int64_t e = is_b ? ((k0 + k) * ld + r) : (r * ld + k0 + k);
   const uint32_t fl = __ldg(X.flags + e);
   const bool nz = !(fl & (ARBGPU_FLAG_ZERO | SPECIAL_MASK));
   const int64_t ex = __ldg(X.exp + e);
@@ -343,14 +369,11 @@ __device__ __forceinline__ Mag product_mag(const IntProduct &p, int64_t i, int64
   return mag_from_u64(acc[0], base);
 }
 
-__global__ void block_round_kernel(const RoundArgs a) {
-  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= a.M * a.N) return;
-  const int64_t i = idx / a.N, j = idx - (idx / a.N) * a.N;
-  uint64_t T[RD_MAXW];
-  const int nw = assemble(a.mid, i, j, a.Mp, a.Np, T);
-  const bool rowz = a.rtop[i] == INT64_MIN, colz = a.ctop[j] == INT64_MIN;
-  const int64_t sigma = (rowz ? 0 : a.rbot[i]) + (colz ? 0 : a.cbot[j]);  // T * 2^sigma
+// Round the two's-complement integer T[0..nw) times 2^sigma to p bits (nearest, ties to even) and
+// store it into entry oi of C with radius >= |rounded - T 2^sigma| + extra * 2^sigma + rad.
+// T is clobbered.
+__device__ void round_store(uint64_t *T, int nw, int64_t sigma, uint64_t extra, Mag rad, int prec,
+                            const BallsOut &C, int64_t oi) {
   const bool neg = (T[nw - 1] >> 63) != 0;
   if (neg) {
     u128 c = 1;
@@ -366,25 +389,23 @@ __global__ void block_round_kernel(const RoundArgs a) {
       top = k;
       break;
     }
-  const BallsOut &C = a.C;
-  const int64_t oi = i * a.ldc + j;
   const int nl = C.nlimbs;
-  uint64_t E[RD_MAXW];
-  for (int k = 0; k < nw; ++k) E[k] = 0;
-  bool zero = top < 0;
+  uint64_t E[RD_MAXW + 1];
+  for (int k = 0; k <= nw; ++k) E[k] = 0;
   uint32_t fl = ARBGPU_FLAG_ZERO;
   int64_t oexp = 0;
-  if (!zero) {
+  if (top >= 0) {
     int64_t L = 64LL * top + bitlen64(T[top]);
-    const int64_t k = L > a.prec ? L - a.prec : 0;
+    const int64_t k = L > prec ? L - prec : 0;
     if (k > 0) {
-      // round to nearest, ties to even, at bit k; E = |rounded - T|
+      // round at bit k; E = |rounded - T|
       auto bit = [&](int64_t pos) -> bool {
         return pos >= 0 && pos < 64LL * nw && ((T[pos >> 6] >> (pos & 63)) & 1);
       };
       bool sticky = false;
       for (int64_t w = 0; w < ((k - 1) >> 6) && !sticky; ++w) sticky = T[w] != 0;
-      if (!sticky && ((k - 1) & 63)) sticky = (T[(k - 1) >> 6] & ((((uint64_t)1) << ((k - 1) & 63)) - 1)) != 0;
+      if (!sticky && ((k - 1) & 63))
+        sticky = (T[(k - 1) >> 6] & ((((uint64_t)1) << ((k - 1) & 63)) - 1)) != 0;
       const bool up = bit(k - 1) && (sticky || bit(k));
       uint64_t rem[RD_MAXW];
       for (int w = 0; w < nw; ++w) {
@@ -393,7 +414,6 @@ __global__ void block_round_kernel(const RoundArgs a) {
         T[w] ^= rem[w];
       }
       if (up) {
-        for (int w = 0; w < nw; ++w) E[w] = 0;
         E[k >> 6] = ((uint64_t)1) << (k & 63);
         uint64_t borrow = 0;
         for (int w = 0; w < nw; ++w) {
@@ -431,24 +451,296 @@ __global__ void block_round_kernel(const RoundArgs a) {
   }
   C.exp[oi] = oexp;
   C.flags[oi] = fl;
-  // radius: eps_round * 2^sigma + P1 2^(top_i + crad_j - 2W) + P2 2^(rrad_i + cplus_j - 2W)
-  Mag r = mag_from_limbs(E, nw, sigma);
-  if (a.rp1.ND && a.rtop[i] != INT64_MIN && a.crad[j] != INT64_MIN)
-    r = mag_add_up(r, product_mag(a.rp1, i, j, a.Mp, a.Np, a.rtop[i] + a.crad[j] - 2 * BL_W));
-  if (a.rp2.ND && a.rrad[i] != INT64_MIN && a.cplus[j] != INT64_MIN)
-    r = mag_add_up(r, product_mag(a.rp2, i, j, a.Mp, a.Np, a.rrad[i] + a.cplus[j] - 2 * BL_W));
+  // E += extra
+  {
+    u128 c = extra;
+    for (int w = 0; w <= nw && c; ++w) {
+      c += E[w];
+      E[w] = (uint64_t)c;
+      c >>= 64;
+    }
+  }
+  const Mag r = mag_add_up(mag_from_limbs(E, nw + 1, sigma), rad);
   C.rad_man[oi] = r.man;
   C.rad_exp[oi] = r.man ? r.exp : 0;
+}
+
+// Radius bound of one block product at entry (i, j): P1 2^(top_i + crad_j - 2W) and
+// P2 2^(rrad_i + cplus_j - 2W), each rounded up, summed rounded up.
+__device__ __forceinline__ Mag block_radius(const IntProduct &rp1, const IntProduct &rp2,
+                                            const int64_t *rtop, const int64_t *rrad,
+                                            const int64_t *crad, const int64_t *cplus, int64_t i,
+                                            int64_t j, int64_t Mp, int64_t Np) {
+  Mag r{0u, 0};
+  if (rp1.ND && rtop[i] != INT64_MIN && crad[j] != INT64_MIN)
+    r = mag_add_up(r, product_mag(rp1, i, j, Mp, Np, rtop[i] + crad[j] - 2 * BL_W));
+  if (rp2.ND && rrad[i] != INT64_MIN && cplus[j] != INT64_MIN)
+    r = mag_add_up(r, product_mag(rp2, i, j, Mp, Np, rrad[i] + cplus[j] - 2 * BL_W));
+  return r;
+}
+
+__global__ void block_round_kernel(const RoundArgs a) {
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= a.M * a.N) return;
+  const int64_t i = idx / a.N, j = idx - (idx / a.N) * a.N;
+  uint64_t T[RD_MAXW];
+  const int nw = assemble(a.mid, i, j, a.Mp, a.Np, T);
+  const bool rowz = a.rtop[i] == INT64_MIN, colz = a.ctop[j] == INT64_MIN;
+  const int64_t sigma = (rowz ? 0 : a.rbot[i]) + (colz ? 0 : a.cbot[j]);  // T * 2^sigma
+  const Mag rad = block_radius(a.rp1, a.rp2, a.rtop, a.rrad, a.crad, a.cplus, i, j, a.Mp, a.Np);
+  round_store(T, nw, sigma, 0, rad, a.prec, a.C, i * a.ldc + j);
+}
+
+// ------------------------------------------------------------------------- several blocks
+
+// Per-entry top / bottom exponents (INT64_MIN / INT64_MAX for zeros) for the planner.
+__global__ void entry_tb_kernel(const BallsView X, int64_t rows, int64_t cols, int64_t ld,
+                                int64_t *top, int64_t *bot) {
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= rows * cols) return;
+  const int64_t r = idx / cols, c = idx - (idx / cols) * cols;
+  EntryScan e = scan_entry(X, r * ld + c);
+  top[idx] = e.nz ? e.top : INT64_MIN;
+  bot[idx] = e.nz ? e.bot : INT64_MAX;
+}
+
+// Greedy extraction of Algorithm 2 (one CTA): from the current start, every line (row of A, column
+// of B) walks the inner index until its height would exceed h; the block ends at the first such
+// index over all lines (a block holds at least one index); blocks shorter than the basecase size
+// are widened to min(30, remaining) and marked for dot products.  Writes [start, stop, basecase]
+// triples and their count.
+__global__ void __launch_bounds__(1024)
+    plan_kernel(const int64_t *tA, const int64_t *bA, const int64_t *tB, const int64_t *bB, int64_t M,
+                int64_t K, int64_t N, int64_t h, int32_t *blocks, int32_t *nblocks, int maxb) {
+  __shared__ int s_end, s_start, s_nb;
+  if (threadIdx.x == 0) {
+    s_start = 0;
+    s_nb = 0;
+  }
+  __syncthreads();
+  const int64_t lines = M + N;
+  while (true) {
+    const int start = s_start;
+    if (start >= K) break;
+    __syncthreads();
+    if (threadIdx.x == 0) s_end = (int)K;
+    __syncthreads();
+    for (int64_t L = threadIdx.x; L < lines; L += blockDim.x) {
+      const int64_t *tp = L < M ? tA + L * K : tB + (L - M);
+      const int64_t *bp = L < M ? bA + L * K : bB + (L - M);
+      const int64_t stride = L < M ? 1 : N;
+      int64_t hi = INT64_MIN, lo = INT64_MAX;
+      bool stop = false;
+      for (int64_t k = start; !stop && k < *(volatile int *)&s_end; k += 8) {
+        int64_t tt[8], bb[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const bool in = k + u < K;
+          tt[u] = in ? tp[(k + u) * stride] : INT64_MIN;
+          bb[u] = in ? bp[(k + u) * stride] : INT64_MAX;
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          if (stop || tt[u] == INT64_MIN) continue;
+          hi = max((long long)hi, (long long)tt[u]);
+          lo = min((long long)lo, (long long)bb[u]);
+          if (hi - lo > h) {
+            atomicMin(&s_end, (int)(k + u));
+            stop = true;
+          }
+        }
+      }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      int end = s_end;
+      if (end <= start) end = start + 1;
+      int base = 0;
+      if (end - start < BL_BASECASE) {
+        end = start + (int)min((int64_t)BL_BASECASE, K - start);
+        base = 1;
+      }
+      const int b = s_nb;
+      if (b < maxb) {
+        blocks[3 * b] = start;
+        blocks[3 * b + 1] = end;
+        blocks[3 * b + 2] = base;
+      }
+      s_nb = b + 1;
+      s_start = end;
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *nblocks = s_nb;
+}
+
+// Per-entry windowed accumulator over several blocks, Algorithm 1 style: nacc limbs of two's
+// complement at 2^base with base = top_i + top_j + bc(K) + 2 - 64 nacc (so the sum of all blocks
+// fits), a count of ulps lost below the window, and a 30-bit radius.
+struct AccView {
+  uint64_t *acc;  // [nacc][M*N]
+  uint32_t *err;  // [M*N]
+  uint32_t *rman;
+  int64_t *rexp;
+  int nacc;
+  int bcK;
+  const int64_t *ftop_r, *ftop_c;  // whole-range row / column tops
+};
+
+__device__ __forceinline__ int64_t acc_base(const AccView &v, int64_t i, int64_t j) {
+  return v.ftop_r[i] + v.ftop_c[j] + v.bcK + 2 - 64LL * v.nacc;
+}
+
+struct AccArgs {
+  IntProduct mid, rp1, rp2;
+  const int64_t *rtop, *rbot, *rrad, *ctop, *cbot, *crad, *cplus;  // this block's lines
+  AccView v;
+  int64_t M, N, Mp, Np;
+};
+
+constexpr int ACC_MAX = 24;
+
+// acc += T_s 2^sigma_s (bits below the window truncated toward zero, one ulp each time),
+// rad += this block's radius bound.
+__global__ void accumulate_kernel(const AccArgs a) {
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= a.M * a.N) return;
+  const int64_t i = idx / a.N, j = idx - (idx / a.N) * a.N;
+  const int64_t MN = a.M * a.N;
+  const AccView &v = a.v;
+  if (a.rtop[i] != INT64_MIN && a.ctop[j] != INT64_MIN && v.ftop_r[i] != INT64_MIN &&
+      v.ftop_c[j] != INT64_MIN) {
+    uint64_t T[RD_MAXW];
+    const int nw = assemble(a.mid, i, j, a.Mp, a.Np, T);
+    const bool neg = (T[nw - 1] >> 63) != 0;
+    if (neg) {
+      u128 c = 1;
+      for (int k = 0; k < nw; ++k) {
+        c += (u128)(~T[k]);
+        T[k] = (uint64_t)c;
+        c >>= 64;
+      }
+    }
+    const int64_t sh = a.rbot[i] + a.cbot[j] - acc_base(v, i, j);  // T's bit 0 sits at bit sh
+    uint64_t W[ACC_MAX];
+    bool lost = false;
+    for (int q = 0; q < v.nacc; ++q) {
+      // bits [64q - sh, 64q - sh + 64) of |T|
+      const int64_t lo = 64LL * q - sh;
+      const int64_t li = lo >= 0 ? (lo >> 6) : -((-lo + 63) >> 6);
+      const int bi = (int)(lo - li * 64);
+      const uint64_t w0 = (li >= 0 && li < nw) ? T[li] : 0;
+      const uint64_t w1 = (li + 1 >= 0 && li + 1 < nw) ? T[li + 1] : 0;
+      W[q] = bi ? ((w0 >> bi) | (w1 << (64 - bi))) : w0;
+    }
+    if (sh < 0) {  // bits of |T| below the window
+      const int64_t cut = -sh;
+      for (int64_t w = 0; w < (cut >> 6) && w < nw && !lost; ++w) lost = T[w] != 0;
+      if (!lost && (cut & 63) && (cut >> 6) < nw)
+        lost = (T[cut >> 6] & ((((uint64_t)1) << (cut & 63)) - 1)) != 0;
+    }
+    const uint64_t flip = neg ? ~(uint64_t)0 : 0;
+    u128 c = neg ? 1 : 0;
+    for (int q = 0; q < v.nacc; ++q) {
+      const int64_t o = (int64_t)q * MN + idx;
+      c += (u128)v.acc[o] + (W[q] ^ flip);
+      v.acc[o] = (uint64_t)c;
+      c >>= 64;
+    }
+    if (lost) v.err[idx] += 1;
+  }
+  const Mag r = block_radius(a.rp1, a.rp2, a.rtop, a.rrad, a.crad, a.cplus, i, j, a.Mp, a.Np);
+  if (r.man) {
+    const Mag cur{v.rman[idx], v.rexp[idx]};
+    const Mag nr = mag_add_up(cur, r);
+    v.rman[idx] = nr.man;
+    v.rexp[idx] = nr.exp;
+  }
+}
+
+// Final rounding of the accumulator (no basecase blocks).
+__global__ void acc_round_kernel(const AccView v, BallsOut C, int64_t M, int64_t N, int64_t ldc,
+                                 int prec) {
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= M * N) return;
+  const int64_t i = idx / N, j = idx - (idx / N) * N;
+  uint64_t T[RD_MAXW];
+  const int64_t MN = M * N;
+  for (int q = 0; q < v.nacc; ++q) T[q] = v.acc[(int64_t)q * MN + idx];
+  T[v.nacc] = (T[v.nacc - 1] >> 63) ? ~(uint64_t)0 : 0;  // one limb of sign extension
+  const bool live = v.ftop_r[i] != INT64_MIN && v.ftop_c[j] != INT64_MIN;
+  const int64_t base = live ? acc_base(v, i, j) : 0;
+  round_store(T, v.nacc + 1, base, live ? v.err[idx] : 0, Mag{v.rman[idx], v.rexp[idx]}, prec, C,
+              i * ldc + j);
+}
+
+// Accumulator -> an exact ball (nacc + 1 limbs, radius = lost ulps + block radii): the `initial`
+// term of the dot products that finish the basecase blocks.
+__global__ void acc_to_ball_kernel(const AccView v, BallsOut I, int64_t M, int64_t N) {
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= M * N) return;
+  const int64_t i = idx / N, j = idx - (idx / N) * N;
+  const int64_t MN = M * N;
+  const int nw = v.nacc;
+  uint64_t T[ACC_MAX];
+  for (int q = 0; q < nw; ++q) T[q] = v.acc[(int64_t)q * MN + idx];
+  const bool neg = (T[nw - 1] >> 63) != 0;
+  if (neg) {
+    u128 c = 1;
+    for (int k = 0; k < nw; ++k) {
+      c += (u128)(~T[k]);
+      T[k] = (uint64_t)c;
+      c >>= 64;
+    }
+  }
+  int top = -1;
+  for (int k = nw - 1; k >= 0; --k)
+    if (T[k]) {
+      top = k;
+      break;
+    }
+  const bool live = v.ftop_r[i] != INT64_MIN && v.ftop_c[j] != INT64_MIN;
+  const int64_t base = live ? acc_base(v, i, j) : 0;
+  const int nl = I.nlimbs;  // nacc + 1
+  if (top < 0) {
+    for (int q = 0; q < nl; ++q) I.limbs[(int64_t)q * I.stride + idx] = 0;
+    I.exp[idx] = 0;
+    I.flags[idx] = ARBGPU_FLAG_ZERO;
+  } else {
+    const int64_t L = 64LL * top + bitlen64(T[top]);
+    int nsig = 0;
+    for (int q = 0; q < nl; ++q) {
+      const int64_t lo = 64LL * q + (L - 64LL * nl);
+      const int64_t li = lo >= 0 ? (lo >> 6) : -((-lo + 63) >> 6);
+      const int bi = (int)(lo - li * 64);
+      const uint64_t w0 = (li >= 0 && li < nw) ? T[li] : 0;
+      const uint64_t w1 = (li + 1 >= 0 && li + 1 < nw) ? T[li + 1] : 0;
+      const uint64_t f = bi ? ((w0 >> bi) | (w1 << (64 - bi))) : w0;
+      I.limbs[(int64_t)q * I.stride + idx] = f;
+      if (f && nsig == 0) nsig = nl - q;
+    }
+    I.exp[idx] = base + L;
+    I.flags[idx] = (neg ? ARBGPU_FLAG_SIGN : 0u) | ((uint32_t)nsig << ARBGPU_NSIG_SHIFT);
+  }
+  Mag r{v.rman[idx], v.rexp[idx]};
+  if (live && v.err[idx]) r = mag_add_up(r, mag_from_u64(v.err[idx], base));
+  I.rad_man[idx] = r.man;
+  I.rad_exp[idx] = r.man ? r.exp : 0;
 }
 
 // ------------------------------------------------------------------------- workspace and driver
 
 struct BlockWs {
+  // whole-range scan
   size_t stats, rtop, rbot, rrad, ctop, cbot, crad, cplus;
-  size_t dA, dB, rA1, rA2, rB1, rB2;
-  size_t mdig, mcar, r1dig, r1car, r2dig, r2car;
+  // operands and products of one block
+  size_t dA, dB, rA1, rA2, rB1, rB2, mdig, mcar, r1dig, r1car, r2dig, r2car;
+  // several blocks: planner input, plan, per-block line statistics, accumulator, initial balls
+  size_t tA, bA, tB, bB, blocks, nblocks, bstats;
+  size_t brtop, brbot, brrad, bctop, bcbot, bcrad, bcplus;
+  size_t acc, err, rman, rexp, ilimbs, iexp, iflags, irman, irexp, bk;
   size_t total;
-  int Smax, NDmax, Gmax, Gr;
+  int Smax, NDmax, Gmax, Gr, maxb, nacc;
   int64_t Kp, Mp, Np;
 };
 
@@ -462,6 +754,8 @@ static BlockWs block_ws(arbgpu_ctx *ctx, int64_t M, int64_t K, int64_t N, int pr
   w.Np = (N + TG_BN - 1) / TG_BN * TG_BN;
   w.Gmax = digit_gemm_groups(ctx, (int)M, (int)N, w.NDmax);
   w.Gr = digit_gemm_groups(ctx, (int)M, (int)N, 2 * BL_SR - 1);
+  w.maxb = (int)(K / BL_BASECASE) + 2;  // every block but the last holds >= 30 indices
+  w.nacc = (prec + 63) / 64 + 3;
   auto al = [](size_t v) { return (v + 255) / 256 * 256; };
   size_t off = 0;
   auto take = [&](size_t bytes) {
@@ -469,6 +763,7 @@ static BlockWs block_ws(arbgpu_ctx *ctx, int64_t M, int64_t K, int64_t N, int pr
     off += al(bytes);
     return o;
   };
+  const size_t MN = (size_t)M * N;
   w.stats = take(sizeof(BlockStats));
   w.rtop = take(8 * M);
   w.rbot = take(8 * M);
@@ -489,6 +784,30 @@ static BlockWs block_ws(arbgpu_ctx *ctx, int64_t M, int64_t K, int64_t N, int pr
   w.r1car = take((size_t)w.Gr * w.Mp * w.Np * 4);
   w.r2dig = take((size_t)(2 * BL_SR - 1) * w.Mp * w.Np);
   w.r2car = take((size_t)w.Gr * w.Mp * w.Np * 4);
+  w.tA = take(8 * (size_t)M * K);
+  w.bA = take(8 * (size_t)M * K);
+  w.tB = take(8 * (size_t)K * N);
+  w.bB = take(8 * (size_t)K * N);
+  w.blocks = take(12 * (size_t)w.maxb);
+  w.nblocks = take(8);
+  w.bstats = take(sizeof(BlockStats) * (size_t)w.maxb);
+  w.brtop = take(8 * (size_t)w.maxb * M);
+  w.brbot = take(8 * (size_t)w.maxb * M);
+  w.brrad = take(8 * (size_t)w.maxb * M);
+  w.bctop = take(8 * (size_t)w.maxb * N);
+  w.bcbot = take(8 * (size_t)w.maxb * N);
+  w.bcrad = take(8 * (size_t)w.maxb * N);
+  w.bcplus = take(8 * (size_t)w.maxb * N);
+  w.acc = take(8 * (size_t)w.nacc * MN);
+  w.err = take(4 * MN);
+  w.rman = take(4 * MN);
+  w.rexp = take(8 * MN);
+  w.ilimbs = take(8 * (size_t)(w.nacc + 1) * MN);
+  w.iexp = take(8 * MN);
+  w.iflags = take(4 * MN);
+  w.irman = take(4 * MN);
+  w.irexp = take(8 * MN);
+  w.bk = take(4 * (size_t)K);
   w.total = off;
   return w;
 }
@@ -498,8 +817,84 @@ size_t block_workspace_size(arbgpu_ctx *ctx, int64_t M, int64_t K, int64_t N, in
   return block_ws(ctx, M, K, N, prec).total;
 }
 
-// Real block product.  Returns ARBGPU_ERR_LIMIT when the inputs need more than one block or hold
-// special values (the caller then uses the classical algorithm).
+// Line statistics of one block (pointers into the whole-range or the per-block arrays).
+struct Lines {
+  const int64_t *rtop, *rbot, *rrad, *ctop, *cbot, *crad, *cplus;
+};
+
+// Split the block [k0, k0 + Kb) and run its products: T = (E A)(B F), and the radius products
+// P1 = U(|A|) V(R_B) (when B has radii), P2 = U(R_A) V(|B| + R_B) (when A has radii).
+static arbgpu_status run_block(arbgpu_ctx *ctx, const BlockWs &w, uint8_t *ws, const BallsView &Av,
+                               const BallsView &Bv, int64_t M, int64_t N, int64_t lda,
+                               int64_t ldb, int64_t k0, int64_t Kb, int SA, int SB, bool radA,
+                               bool radB, const Lines &ln, cudaStream_t s, IntProduct *mid,
+                               IntProduct *rp1, IntProduct *rp2) {
+  const int64_t Kp = (Kb + TG_BK - 1) / TG_BK * TG_BK;
+  if (SA > w.Smax || SB > w.Smax || !digit_gemm_fits(SA, SB, Kp)) return ARBGPU_ERR_LIMIT;
+  __nv_bfloat16 *dA = (__nv_bfloat16 *)(ws + w.dA), *dB = (__nv_bfloat16 *)(ws + w.dB);
+  __nv_bfloat16 *rA1 = (__nv_bfloat16 *)(ws + w.rA1), *rA2 = (__nv_bfloat16 *)(ws + w.rA2);
+  __nv_bfloat16 *rB1 = (__nv_bfloat16 *)(ws + w.rB1), *rB2 = (__nv_bfloat16 *)(ws + w.rB2);
+  {
+    const int64_t n = M * Kp;
+    SplitOut o{dA, radB ? rA1 : nullptr, radA ? rA2 : nullptr};
+    LaunchScope sc(ctx, s, "split_a", n);
+    split_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(Av, false, M, k0, Kb, Kp, lda, SA,
+                                                             ln.rbot, ln.rtop, ln.rrad, nullptr, o);
+  }
+  {
+    const int64_t n = N * Kp;
+    SplitOut o{dB, radB ? rB1 : nullptr, radA ? rB2 : nullptr};
+    LaunchScope sc(ctx, s, "split_b", n);
+    split_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(Bv, true, N, k0, Kb, Kp, ldb, SB,
+                                                             ln.cbot, ln.ctop, ln.crad, ln.cplus, o);
+  }
+  if (cudaGetLastError() != cudaSuccess) return ARBGPU_ERR_CUDA;
+  const int ND = SA + SB - 1;
+  const int G = digit_gemm_groups(ctx, (int)M, (int)N, ND);
+  if (G > w.Gmax) return ARBGPU_ERR_LIMIT;
+  {
+    DigitGemmArgs g{dA, dB, (int)M, (int)N, Kp, SA, SB, G, ws + w.mdig, (int32_t *)(ws + w.mcar),
+                    "digit_gemm_mid"};
+    arbgpu_status stg = launch_digit_gemm(ctx, g, s);
+    if (stg != ARBGPU_OK) return stg;
+    *mid = IntProduct{ws + w.mdig, (int32_t *)(ws + w.mcar), ND, G, {}};
+    digit_gemm_group_ends(SA, SB, G, mid->ends.e);
+  }
+  const int NDr = 2 * BL_SR - 1;
+  *rp1 = IntProduct{};
+  *rp2 = IntProduct{};
+  if (radB) {
+    DigitGemmArgs g{rA1, rB1, (int)M, (int)N, Kp, BL_SR, BL_SR, w.Gr, ws + w.r1dig,
+                    (int32_t *)(ws + w.r1car), "digit_gemm_rad"};
+    arbgpu_status stg = launch_digit_gemm(ctx, g, s);
+    if (stg != ARBGPU_OK) return stg;
+    *rp1 = IntProduct{ws + w.r1dig, (int32_t *)(ws + w.r1car), NDr, w.Gr, {}};
+    digit_gemm_group_ends(BL_SR, BL_SR, w.Gr, rp1->ends.e);
+  }
+  if (radA) {
+    DigitGemmArgs g{rA2, rB2, (int)M, (int)N, Kp, BL_SR, BL_SR, w.Gr, ws + w.r2dig,
+                    (int32_t *)(ws + w.r2car), "digit_gemm_rad"};
+    arbgpu_status stg = launch_digit_gemm(ctx, g, s);
+    if (stg != ARBGPU_OK) return stg;
+    *rp2 = IntProduct{ws + w.r2dig, (int32_t *)(ws + w.r2car), NDr, w.Gr, {}};
+    digit_gemm_group_ends(BL_SR, BL_SR, w.Gr, rp2->ends.e);
+  }
+  return ARBGPU_OK;
+}
+
+static int digits_for_height(int64_t h) { return h < 0 ? 1 : (int)((h + 2 + 7) / 8); }
+
+static int bit_length(int64_t v) {
+  int b = 0;
+  while (v > 0) {
+    ++b;
+    v >>= 1;
+  }
+  return b;
+}
+
+// Real product by Algorithm 2.  Returns ARBGPU_ERR_LIMIT when the inputs hold special values or
+// exceed the path's limits (the caller then uses the classical algorithm).
 arbgpu_status block_matmul_real(arbgpu_ctx *ctx, const arbgpu_balls &C, const arbgpu_balls &A,
                                 const arbgpu_balls &B, int64_t M, int64_t K, int64_t N,
                                 int64_t lda, int64_t ldb, int64_t ldc, int prec, void *workspace,
@@ -511,10 +906,9 @@ arbgpu_status block_matmul_real(arbgpu_ctx *ctx, const arbgpu_balls &C, const ar
   if (!workspace || ws_bytes < w.total) return ARBGPU_ERR_WORKSPACE;
   uint8_t *ws = (uint8_t *)workspace;
   BlockStats *st = (BlockStats *)(ws + w.stats);
-  int64_t *rtop = (int64_t *)(ws + w.rtop), *rbot = (int64_t *)(ws + w.rbot);
-  int64_t *rrad = (int64_t *)(ws + w.rrad);
-  int64_t *ctop = (int64_t *)(ws + w.ctop), *cbot = (int64_t *)(ws + w.cbot);
-  int64_t *crad = (int64_t *)(ws + w.crad), *cplus = (int64_t *)(ws + w.cplus);
+  const Lines full{(int64_t *)(ws + w.rtop), (int64_t *)(ws + w.rbot), (int64_t *)(ws + w.rrad),
+                   (int64_t *)(ws + w.ctop), (int64_t *)(ws + w.cbot), (int64_t *)(ws + w.crad),
+                   (int64_t *)(ws + w.cplus)};
   BlockStats init{};
   init.hA = init.hB = INT64_MIN;
   if (cudaMemcpyAsync(st, &init, sizeof(init), cudaMemcpyHostToDevice, s) != cudaSuccess)
@@ -522,13 +916,14 @@ arbgpu_status block_matmul_real(arbgpu_ctx *ctx, const arbgpu_balls &C, const ar
   const BallsView Av = view_of(A), Bv = view_of(B);
   {
     LaunchScope sc(ctx, s, "scan_rows", M * K);
-    scan_rows_kernel<<<(unsigned)((M * 32 + 255) / 256), 256, 0, s>>>(Av, M, K, lda, rtop, rbot,
-                                                                        rrad, st);
+    scan_rows_kernel<<<(unsigned)((M * 32 + 255) / 256), 256, 0, s>>>(
+        Av, M, K, lda, nullptr, (int64_t *)full.rtop, (int64_t *)full.rbot, (int64_t *)full.rrad, st);
   }
   {
     LaunchScope sc(ctx, s, "scan_cols", K * N);
-    scan_cols_kernel<<<(unsigned)((N + 31) / 32), dim3(32, 32), 0, s>>>(Bv, K, N, ldb, ctop, cbot,
-                                                                         crad, cplus, st);
+    scan_cols_kernel<<<(unsigned)((N + 31) / 32), dim3(32, 32), 0, s>>>(
+        Bv, K, N, ldb, nullptr, (int64_t *)full.ctop, (int64_t *)full.cbot, (int64_t *)full.crad,
+        (int64_t *)full.cplus, st);
   }
   BlockStats hs{};
   if (cudaMemcpyAsync(&hs, st, sizeof(hs), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
@@ -537,78 +932,152 @@ arbgpu_status block_matmul_real(arbgpu_ctx *ctx, const arbgpu_balls &C, const ar
   if (hs.special) return ARBGPU_ERR_LIMIT;
   const int64_t pmax = hs.pA > hs.pB ? hs.pA : hs.pB;
   const int64_t h = (5 * (prec < pmax ? (int64_t)prec : pmax)) / 4 + 192;
-  if (hs.hA > h || hs.hB > h) return ARBGPU_ERR_LIMIT;  // needs several blocks
-  const int SA = hs.hA < 0 ? 1 : (int)((hs.hA + 2 + 7) / 8);
-  const int SB = hs.hB < 0 ? 1 : (int)((hs.hB + 2 + 7) / 8);
-  if (SA > w.Smax || SB > w.Smax || !digit_gemm_fits(SA, SB, w.Kp)) return ARBGPU_ERR_LIMIT;
-  const bool radB = hs.radB != 0, radA = hs.radA != 0;
-  __nv_bfloat16 *dA = (__nv_bfloat16 *)(ws + w.dA), *dB = (__nv_bfloat16 *)(ws + w.dB);
-  __nv_bfloat16 *rA1 = (__nv_bfloat16 *)(ws + w.rA1), *rA2 = (__nv_bfloat16 *)(ws + w.rA2);
-  __nv_bfloat16 *rB1 = (__nv_bfloat16 *)(ws + w.rB1), *rB2 = (__nv_bfloat16 *)(ws + w.rB2);
+
+  if (hs.hA <= h && hs.hB <= h) {
+    // ---- one block: exact product, one rounding per entry
+    RoundArgs ra{};
+    arbgpu_status st1 = run_block(ctx, w, ws, Av, Bv, M, N, lda, ldb, 0, K,
+                                  digits_for_height(hs.hA), digits_for_height(hs.hB),
+                                  hs.radA != 0, hs.radB != 0, full, s, &ra.mid, &ra.rp1, &ra.rp2);
+    if (st1 != ARBGPU_OK) return st1;
+    ra.rtop = full.rtop;
+    ra.rbot = full.rbot;
+    ra.rrad = full.rrad;
+    ra.ctop = full.ctop;
+    ra.cbot = full.cbot;
+    ra.crad = full.crad;
+    ra.cplus = full.cplus;
+    ra.C = out_of(C);
+    ra.M = M;
+    ra.N = N;
+    ra.ldc = ldc;
+    ra.Mp = w.Mp;
+    ra.Np = w.Np;
+    ra.prec = prec;
+    {
+      LaunchScope sc(ctx, s, "block_round", M * N);
+      block_round_kernel<<<(unsigned)((M * N + 127) / 128), 128, 0, s>>>(ra);
+    }
+    *used_block = true;
+    return cudaGetLastError() == cudaSuccess ? ARBGPU_OK : ARBGPU_ERR_CUDA;
+  }
+
+  // ---- several blocks: greedy plan on the device
+  int64_t *tA = (int64_t *)(ws + w.tA), *bA = (int64_t *)(ws + w.bA);
+  int64_t *tB = (int64_t *)(ws + w.tB), *bB = (int64_t *)(ws + w.bB);
+  int32_t *blocks = (int32_t *)(ws + w.blocks), *nblocks = (int32_t *)(ws + w.nblocks);
   {
-    const int64_t n = M * w.Kp;
-    SplitOut o{dA, radB ? rA1 : nullptr, radA ? rA2 : nullptr};
-    LaunchScope sc(ctx, s, "split_a", n);
-    split_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(Av, false, M, K, w.Kp, lda, SA, rbot,
-                                                             rtop, rrad, nullptr, o);
+    LaunchScope sc(ctx, s, "entry_tb", M * K + K * N);
+    entry_tb_kernel<<<(unsigned)((M * K + 255) / 256), 256, 0, s>>>(Av, M, K, lda, tA, bA);
+    entry_tb_kernel<<<(unsigned)((K * N + 255) / 256), 256, 0, s>>>(Bv, K, N, ldb, tB, bB);
   }
   {
-    const int64_t n = N * w.Kp;
-    SplitOut o{dB, radB ? rB1 : nullptr, radA ? rB2 : nullptr};
-    LaunchScope sc(ctx, s, "split_b", n);
-    split_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(Bv, true, N, K, w.Kp, ldb, SB, cbot,
-                                                             ctop, crad, cplus, o);
+    LaunchScope sc(ctx, s, "plan", M + N);
+    plan_kernel<<<1, 1024, 0, s>>>(tA, bA, tB, bB, M, K, N, h, blocks, nblocks, w.maxb);
+  }
+  int32_t hnb = 0;
+  if (cudaMemcpyAsync(&hnb, nblocks, 4, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess)
+    return ARBGPU_ERR_CUDA;
+  if (hnb < 1 || hnb > w.maxb) return ARBGPU_ERR_LIMIT;
+  std::vector<int32_t> hb(3 * (size_t)hnb);
+  std::vector<BlockStats> hbs((size_t)hnb, init);
+  BlockStats *bst = (BlockStats *)(ws + w.bstats);
+  if (cudaMemcpyAsync(hb.data(), blocks, 12 * (size_t)hnb, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaMemcpyAsync(bst, hbs.data(), sizeof(BlockStats) * hnb, cudaMemcpyHostToDevice, s) !=
+          cudaSuccess)
+    return ARBGPU_ERR_CUDA;
+  const Lines per{(int64_t *)(ws + w.brtop), (int64_t *)(ws + w.brbot), (int64_t *)(ws + w.brrad),
+                  (int64_t *)(ws + w.bctop), (int64_t *)(ws + w.bcbot), (int64_t *)(ws + w.bcrad),
+                  (int64_t *)(ws + w.bcplus)};
+  {
+    LaunchScope sc(ctx, s, "scan_rows", M * K);
+    scan_rows_kernel<<<dim3((unsigned)((M * 32 + 255) / 256), (unsigned)hnb), 256, 0, s>>>(
+        Av, M, K, lda, blocks, (int64_t *)per.rtop, (int64_t *)per.rbot, (int64_t *)per.rrad, bst);
+  }
+  {
+    LaunchScope sc(ctx, s, "scan_cols", K * N);
+    scan_cols_kernel<<<dim3((unsigned)((N + 31) / 32), (unsigned)hnb), dim3(32, 32), 0, s>>>(
+        Bv, K, N, ldb, blocks, (int64_t *)per.ctop, (int64_t *)per.cbot, (int64_t *)per.crad,
+        (int64_t *)per.cplus, bst);
+  }
+  if (cudaMemcpyAsync(hbs.data(), bst, sizeof(BlockStats) * hnb, cudaMemcpyDeviceToHost, s) !=
+          cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess)
+    return ARBGPU_ERR_CUDA;
+
+  // accumulator
+  AccView av{(uint64_t *)(ws + w.acc), (uint32_t *)(ws + w.err), (uint32_t *)(ws + w.rman),
+             (int64_t *)(ws + w.rexp), w.nacc, bit_length(K), full.rtop, full.ctop};
+  const size_t MN = (size_t)M * N;
+  if (cudaMemsetAsync(av.acc, 0, 8 * (size_t)w.nacc * MN, s) != cudaSuccess ||
+      cudaMemsetAsync(av.err, 0, 4 * MN, s) != cudaSuccess ||
+      cudaMemsetAsync(av.rman, 0, 4 * MN, s) != cudaSuccess ||
+      cudaMemsetAsync(av.rexp, 0, 8 * MN, s) != cudaSuccess)
+    return ARBGPU_ERR_CUDA;
+  std::vector<int32_t> basek;
+  for (int b = 0; b < hnb; ++b) {
+    const int64_t k0 = hb[3 * b], k1 = hb[3 * b + 1];
+    if (hb[3 * b + 2]) {
+      for (int64_t k = k0; k < k1; ++k) basek.push_back((int32_t)k);
+      continue;
+    }
+    const Lines lb{per.rtop + (int64_t)b * M, per.rbot + (int64_t)b * M, per.rrad + (int64_t)b * M,
+                   per.ctop + (int64_t)b * N, per.cbot + (int64_t)b * N, per.crad + (int64_t)b * N,
+                   per.cplus + (int64_t)b * N};
+    AccArgs aa{};
+    arbgpu_status st1 = run_block(ctx, w, ws, Av, Bv, M, N, lda, ldb, k0, k1 - k0,
+                                  digits_for_height(hbs[b].hA), digits_for_height(hbs[b].hB),
+                                  hbs[b].radA != 0, hbs[b].radB != 0, lb, s, &aa.mid, &aa.rp1,
+                                  &aa.rp2);
+    if (st1 != ARBGPU_OK) return st1;
+    aa.rtop = lb.rtop;
+    aa.rbot = lb.rbot;
+    aa.rrad = lb.rrad;
+    aa.ctop = lb.ctop;
+    aa.cbot = lb.cbot;
+    aa.crad = lb.crad;
+    aa.cplus = lb.cplus;
+    aa.v = av;
+    aa.M = M;
+    aa.N = N;
+    aa.Mp = w.Mp;
+    aa.Np = w.Np;
+    LaunchScope sc(ctx, s, "accumulate", M * N);
+    accumulate_kernel<<<(unsigned)((M * N + 127) / 128), 128, 0, s>>>(aa);
   }
   if (cudaGetLastError() != cudaSuccess) return ARBGPU_ERR_CUDA;
-  RoundArgs ra{};
-  const int ND = SA + SB - 1;
-  const int G = digit_gemm_groups(ctx, (int)M, (int)N, ND);
-  if (G > w.Gmax) return ARBGPU_ERR_LIMIT;
+  if (basek.empty()) {
+    LaunchScope sc(ctx, s, "acc_round", M * N);
+    acc_round_kernel<<<(unsigned)((M * N + 127) / 128), 128, 0, s>>>(av, out_of(C), M, N, ldc,
+                                                                     prec);
+    *used_block = true;
+    return cudaGetLastError() == cudaSuccess ? ARBGPU_OK : ARBGPU_ERR_CUDA;
+  }
+  // basecase blocks: dot products with the accumulated blocks as their initial term
+  arbgpu_balls ib{};
+  ib.limbs = (uint64_t *)(ws + w.ilimbs);
+  ib.limb_stride = (int64_t)MN;
+  ib.nlimbs = w.nacc + 1;
+  ib.exp = (int64_t *)(ws + w.iexp);
+  ib.flags = (uint32_t *)(ws + w.iflags);
+  ib.rad_man = (uint32_t *)(ws + w.irman);
+  ib.rad_exp = (int64_t *)(ws + w.irexp);
+  ib.count = (int64_t)MN;
   {
-    DigitGemmArgs g{dA, dB, (int)M, (int)N, w.Kp, SA, SB, G, ws + w.mdig,
-                    (int32_t *)(ws + w.mcar), "digit_gemm_mid"};
-    arbgpu_status stg = launch_digit_gemm(ctx, g, s);
-    if (stg != ARBGPU_OK) return stg;
-    ra.mid = IntProduct{ws + w.mdig, (int32_t *)(ws + w.mcar), ND, G, {}};
-    digit_gemm_group_ends(SA, SB, G, ra.mid.ends.e);
+    LaunchScope sc(ctx, s, "acc_to_ball", M * N);
+    acc_to_ball_kernel<<<(unsigned)((M * N + 127) / 128), 128, 0, s>>>(av, out_of(ib), M, N);
   }
-  const int NDr = 2 * BL_SR - 1;
-  if (radB) {
-    DigitGemmArgs g{rA1, rB1, (int)M, (int)N, w.Kp, BL_SR, BL_SR, w.Gr, ws + w.r1dig,
-                    (int32_t *)(ws + w.r1car), "digit_gemm_rad"};
-    arbgpu_status stg = launch_digit_gemm(ctx, g, s);
-    if (stg != ARBGPU_OK) return stg;
-    ra.rp1 = IntProduct{ws + w.r1dig, (int32_t *)(ws + w.r1car), NDr, w.Gr, {}};
-    digit_gemm_group_ends(BL_SR, BL_SR, w.Gr, ra.rp1.ends.e);
-  }
-  if (radA) {
-    DigitGemmArgs g{rA2, rB2, (int)M, (int)N, w.Kp, BL_SR, BL_SR, w.Gr, ws + w.r2dig,
-                    (int32_t *)(ws + w.r2car), "digit_gemm_rad"};
-    arbgpu_status stg = launch_digit_gemm(ctx, g, s);
-    if (stg != ARBGPU_OK) return stg;
-    ra.rp2 = IntProduct{ws + w.r2dig, (int32_t *)(ws + w.r2car), NDr, w.Gr, {}};
-    digit_gemm_group_ends(BL_SR, BL_SR, w.Gr, ra.rp2.ends.e);
-  }
-  ra.rtop = rtop;
-  ra.rbot = rbot;
-  ra.rrad = rrad;
-  ra.ctop = ctop;
-  ra.cbot = cbot;
-  ra.crad = crad;
-  ra.cplus = cplus;
-  ra.C = out_of(C);
-  ra.M = M;
-  ra.N = N;
-  ra.ldc = ldc;
-  ra.Mp = w.Mp;
-  ra.Np = w.Np;
-  ra.prec = prec;
-  {
-    LaunchScope sc(ctx, s, "block_round", M * N);
-    block_round_kernel<<<(unsigned)((M * N + 127) / 128), 128, 0, s>>>(ra);
-  }
-  *used_block = true;
-  return cudaGetLastError() == cudaSuccess ? ARBGPU_OK : ARBGPU_ERR_CUDA;
+  int32_t *bk = (int32_t *)(ws + w.bk);
+  if (cudaMemcpyAsync(bk, basek.data(), 4 * basek.size(), cudaMemcpyHostToDevice, s) !=
+      cudaSuccess)
+    return ARBGPU_ERR_CUDA;
+  arbgpu_status st2 = launch_basecase_dot(ctx, C, A, B, ib, bk, (int64_t)basek.size(), M, N, lda,
+                                          ldb, ldc, prec, s);
+  if (st2 == ARBGPU_OK) *used_block = true;
+  // the host list must outlive the copy: wait for it before `basek` goes out of scope
+  if (cudaStreamSynchronize(s) != cudaSuccess) return ARBGPU_ERR_CUDA;
+  return st2;
 }
 
 }  // namespace arbgpu

@@ -92,6 +92,38 @@ struct MatDotSrc {
   int64_t units() const { return M * N * K; }
 };
 
+// The basecase of Algorithm 2: entry (i, j) sums A[i, k] B[k, j] over the inner indices k listed in
+// bk (the basecase blocks), starting from the accumulated block products as `initial`.
+struct BasecaseSrc {
+  BallsView A, B, init;
+  BallsOut C;
+  const int32_t *bk;
+  int64_t nbk, M, N, lda, ldb, ldc;
+  int prec_v;
+  int prec_max;
+  int64_t len_max;
+
+  __device__ int64_t ndots() const { return M * N; }
+  __device__ int64_t nterms(int64_t) const { return nbk; }
+  __device__ TermLoc term(int64_t d, int64_t t) const {
+    const int64_t i = d / N, j = d - (d / N) * N;
+    const int64_t k = __ldg(bk + t);
+    return TermLoc{0, i * lda + k, 0, k * ldb + j, false};
+  }
+  __device__ const BallsView &xview(int) const { return A; }
+  __device__ const BallsView &yview(int) const { return B; }
+  __device__ bool has_initial(int64_t) const { return true; }
+  __device__ const BallsView &initial_view(int64_t) const { return init; }
+  __device__ int64_t initial_index(int64_t d) const { return d; }
+  __device__ const BallsOut &out_view(int64_t) const { return C; }
+  __device__ int64_t out_index(int64_t d) const {
+    const int64_t i = d / N, j = d - i * N;
+    return i * ldc + j;
+  }
+  __device__ int prec(int64_t) const { return prec_v; }
+  int64_t units() const { return M * N * nbk; }
+};
+
 int dot_class_for_problem(int prec, int64_t max_terms, int max_nlimbs) {
   const int ns = dot_ns(prec, max_terms, max_terms);
   int nx = max_nlimbs < ns + 1 ? max_nlimbs : ns + 1;
@@ -198,6 +230,33 @@ arbgpu_status launch_matmul_dot(arbgpu_ctx *ctx, const arbgpu_balls *C, const ar
   const int cmax = dot_class_for_problem(prec, s.len_max, maxnl);
   if (cmax < 0) return ARBGPU_ERR_INVALID;
   return launch_dot_src(ctx, s, (complex_mode ? 2 : 1) * M * N, cmax, stream);
+}
+
+arbgpu_status launch_basecase_dot(arbgpu_ctx *ctx, const arbgpu_balls &C, const arbgpu_balls &A,
+                                  const arbgpu_balls &B, const arbgpu_balls &initial,
+                                  const int32_t *bk, int64_t nbk, int64_t M, int64_t N,
+                                  int64_t lda, int64_t ldb, int64_t ldc, int32_t prec,
+                                  cudaStream_t stream) {
+  BasecaseSrc s{};
+  s.A = view_of(A);
+  s.B = view_of(B);
+  s.init = view_of(initial);
+  s.C = out_of(C);
+  s.bk = bk;
+  s.nbk = nbk;
+  s.M = M;
+  s.N = N;
+  s.lda = lda;
+  s.ldb = ldb;
+  s.ldc = ldc;
+  s.prec_v = prec;
+  s.prec_max = prec;
+  s.len_max = nbk;
+  int maxnl = A.nlimbs > B.nlimbs ? A.nlimbs : B.nlimbs;
+  if (initial.nlimbs > maxnl) maxnl = initial.nlimbs;
+  const int cmax = dot_class_for_problem(prec, nbk + 1, maxnl);
+  if (cmax < 0) return ARBGPU_ERR_INVALID;
+  return launch_dot_src(ctx, s, M * N, cmax, stream);
 }
 
 }  // namespace arbgpu

@@ -92,6 +92,14 @@ arbgpu_status int_mat_mul_run(arbgpu_ctx *ctx, uint64_t *T, int32_t t_limbs, con
                               cudaStream_t s);
 size_t int_mat_mul_workspace(arbgpu_ctx *ctx, int xl, int yl, int64_t M, int64_t K, int64_t N);
 
+// Dot products that finish the basecase blocks of Algorithm 2 (dot.cu): entry (i, j) of C is
+// initial[i*N + j] + sum over k in bk[0..nbk) of A[i*lda + k] * B[k*ldb + j].
+arbgpu_status launch_basecase_dot(arbgpu_ctx *ctx, const arbgpu_balls &C, const arbgpu_balls &A,
+                                  const arbgpu_balls &B, const arbgpu_balls &initial,
+                                  const int32_t *bk, int64_t nbk, int64_t M, int64_t N,
+                                  int64_t lda, int64_t ldb, int64_t ldc, int32_t prec,
+                                  cudaStream_t stream);
+
 // Dot-kernel size class for a precision, a maximal term count and operand limb counts (-1: none).
 int dot_class_for_problem(int prec, int64_t max_terms, int max_nlimbs);
 

@@ -114,24 +114,75 @@ def test_block_n512_p128_sampled(arb):
     check_entries(out, case.A[0], case.B[0], 512, 512, 512, 128, ents, 2)
 
 
-def test_block_falls_back_when_several_blocks_are_needed(arb):
-    """Column 35 of A is 2^900 larger than the rest: Algorithm 2 needs several blocks; the library
-    then uses the classical algorithm, whose output matches the Algorithm 1 restatement."""
-    rng = np.random.default_rng(4)
-    M, K, N, p = 8, 70, 6, 64
+def check_bounds(out, A, B, M, K, N, prec, entries):
+    """Containment and the accuracy bound |m - S| <= 2^-p sum |a b| for every listed entry."""
+    worst = 0.0
+    for i, j in entries:
+        S, Sabs, R = X.dot_terms_exact(X.matmul_entry_terms(A, B, K, N, i, j))
+        idx = i * N + j
+        m, r = X.mid(out, idx), X.rad(out, idx)
+        assert X.contains(m, r, S, R), (i, j)
+        worst = max(worst, X.accuracy_ratio(m, S, Sabs, prec))
+    assert worst <= 1.0, worst
+    return worst
+
+
+def jump_case(seed, M, K, N, jumps, p, nl=1, rad=None):
+    """Columns listed in `jumps` of A are 2^900 larger than the rest: Algorithm 2 cuts there."""
+    rng = np.random.default_rng(seed)
     ea = rng.integers(-5, 5, size=M * K)
-    ea[np.arange(M) * K + 35] += 900
-    A = random_balls(rng, M * K, 1, 64, exps=ea)
-    B = random_balls(rng, K * N, 1, 64, -5, 5)
-    assert len(alg2.plan(A, B, M, K, N, p)[1]) > 1
-    out, _ = run_mm(arb, A, B, M, K, N, p, arb.ALG_BLOCK)
-    for i in range(M):
-        for j in range(N):
-            ref = alg1.matmul_entry(A, B, K, N, i, j, p, 1)
-            idx = i * N + j
-            got = ([int(out.limbs[0, idx])], int(out.exp[idx]), int(out.flags[idx]),
-                   int(out.rad_man[idx]), int(out.rad_exp[idx]))
-            assert got == (ref["limbs"], ref["exp"], ref["flags"], ref["rad_man"], ref["rad_exp"])
+    for k in jumps:
+        ea[np.arange(M) * K + k] += 900
+    A = random_balls(rng, M * K, nl, 64 * nl, exps=ea, rad_bits=rad, rad_zero_frac=0.5)
+    B = random_balls(rng, K * N, nl, 64 * nl, -5, 5, rad_bits=rad, rad_zero_frac=0.5)
+    return A, B
+
+
+def test_several_blocks_with_basecase(arb):
+    """Column 35 of A jumps by 2^900: blocks [0, 35), a one-column block widened to a 30-column
+    basecase, then the rest; the block part is accumulated and the basecase done by dots."""
+    M, K, N, p = 24, 100, 20, 64
+    A, B = jump_case(4, M, K, N, [35], p, rad=60)
+    h, blocks = alg2.plan(A, B, M, K, N, p)
+    assert any(b[2] for b in blocks) and any(not b[2] for b in blocks)
+    out, names = run_mm(arb, A, B, M, K, N, p, arb.ALG_BLOCK, trace=True)
+    assert "accumulate" in names and "dot_kernel" in names and "plan" in names
+    check_bounds(out, A, B, M, K, N, p, [(i, j) for i in range(M) for j in range(N)])
+
+
+def test_several_blocks_without_basecase(arb):
+    """Jumps at 60 and 120 in a 180-wide inner dimension: three full blocks, no basecase."""
+    M, K, N, p = 40, 180, 36, 128
+    A, B = jump_case(5, M, K, N, [60, 120], p, nl=2, rad=120)
+    h, blocks = alg2.plan(A, B, M, K, N, p)
+    assert len(blocks) >= 3 and not any(b[2] for b in blocks)
+    out, names = run_mm(arb, A, B, M, K, N, p, arb.ALG_BLOCK, trace=True)
+    assert "acc_round" in names and "dot_kernel" not in names
+    assert names.count("accumulate") == len(blocks)
+    rng = np.random.default_rng(2)
+    check_bounds(out, A, B, M, K, N, p, [(int(a), int(b)) for a, b in
+                                         zip(rng.integers(0, M, 200), rng.integers(0, N, 200))])
+
+
+def test_structured_laplace_blocks(arb):
+    """Exponents c_k + U[-4, 4] with c_k ~ Laplace(40) along the inner index (the structured complex
+    workload's real part at a small size): many blocks of the plan, exact accumulation, bounds."""
+    rng = np.random.default_rng(7)
+    n, p = 160, 128
+    c = np.clip(np.rint(rng.laplace(0, 40, size=n)), -200, 200).astype(np.int64)
+    ea = np.clip(c[None, :] + rng.integers(-4, 4, size=(n, n), endpoint=True), -200, 200)
+    eb = np.clip(c[:, None] + rng.integers(-4, 4, size=(n, n), endpoint=True), -200, 200)
+    A = random_balls(rng, n * n, 2, 128, exps=ea.reshape(-1), rad_bits=120)
+    B = random_balls(rng, n * n, 2, 128, exps=eb.reshape(-1), rad_bits=120)
+    h, blocks = alg2.plan(A, B, n, n, n, p)
+    assert len(blocks) >= 2
+    out, names = run_mm(arb, A, B, n, n, n, p, arb.ALG_BLOCK, trace=True)
+    assert "plan" in names
+    # one accumulation per full block of the oracle's plan: the device planner agrees with it
+    assert names.count("accumulate") == sum(1 for b in blocks if not b[2])
+    rng2 = np.random.default_rng(3)
+    check_bounds(out, A, B, n, n, n, p, [(int(a), int(b)) for a, b in
+                                         zip(rng2.integers(0, n, 150), rng2.integers(0, n, 150))])
 
 
 def test_identity_times_matrix(arb):
