@@ -219,9 +219,8 @@ arbgpu_status arbgpu_mat_mul_workspace_size(arbgpu_ctx *ctx, int64_t M, int64_t 
   *bytes = 0;
   if (alg == ARBGPU_ALG_DOT) return ARBGPU_OK;
   if (alg != ARBGPU_ALG_BLOCK && alg != ARBGPU_ALG_AUTO) return ARBGPU_ERR_INVALID;
-  if (complex_mode) return ARBGPU_OK;  // complex products use the dot kernel for now
   if (alg == ARBGPU_ALG_AUTO && !auto_uses_block(M, K, N)) return ARBGPU_OK;
-  *bytes = block_workspace_size(ctx, M, K, N, prec);
+  *bytes = block_workspace_size(ctx, M, K, N, prec, complex_mode != 0);
   return ARBGPU_OK;
 }
 
@@ -251,12 +250,12 @@ arbgpu_status arbgpu_mat_mul(arbgpu_ctx *ctx, const arbgpu_balls *C, const arbgp
   if (cudaSetDevice(ctx->device) != cudaSuccess) return ARBGPU_ERR_CUDA;
   if (alg != ARBGPU_ALG_DOT && alg != ARBGPU_ALG_BLOCK && alg != ARBGPU_ALG_AUTO)
     return ARBGPU_ERR_INVALID;
-  const bool try_block = !complex_mode && (alg == ARBGPU_ALG_BLOCK ||
-                                           (alg == ARBGPU_ALG_AUTO && auto_uses_block(M, K, N)));
+  const bool try_block =
+      alg == ARBGPU_ALG_BLOCK || (alg == ARBGPU_ALG_AUTO && auto_uses_block(M, K, N));
   if (try_block && K > 0) {
     bool used = false;
-    arbgpu_status st = block_matmul_real(ctx, C[0], A[0], B[0], M, K, N, lda, ldb, ldc, prec,
-                                         workspace, ws_bytes, (cudaStream_t)stream, &used);
+    arbgpu_status st = block_matmul(ctx, C, A, B, M, K, N, lda, ldb, ldc, prec, complex_mode != 0,
+                                    workspace, ws_bytes, (cudaStream_t)stream, &used);
     if (used || st != ARBGPU_ERR_LIMIT) return st;
     // not a single exponent block (or special values): the classical algorithm handles it
   }

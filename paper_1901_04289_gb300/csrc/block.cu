@@ -583,12 +583,26 @@ struct AccView {
   uint32_t *rman;
   int64_t *rexp;
   int nacc;
-  int bcK;
-  const int64_t *ftop_r, *ftop_c;  // whole-range row / column tops
+  int bcK;                                  // bit length bound of the number of summed products
+  const int64_t *ftop_r[2], *ftop_c[2];     // whole-range row / column tops of the products summed
 };
 
-__device__ __forceinline__ int64_t acc_base(const AccView &v, int64_t i, int64_t j) {
-  return v.ftop_r[i] + v.ftop_c[j] + v.bcK + 2 - 64LL * v.nacc;
+// Exponent bound of the accumulated sum at (i, j); false when every product is zero there.
+__device__ __forceinline__ bool acc_top(const AccView &v, int64_t i, int64_t j, int64_t &top) {
+  bool live = false;
+  top = INT64_MIN;
+  for (int q = 0; q < 2; ++q) {
+    if (!v.ftop_r[q]) continue;
+    const int64_t a = v.ftop_r[q][i], b = v.ftop_c[q][j];
+    if (a == INT64_MIN || b == INT64_MIN) continue;
+    live = true;
+    top = a + b > top ? a + b : top;
+  }
+  return live;
+}
+
+__device__ __forceinline__ int64_t acc_base_of(const AccView &v, int64_t top) {
+  return top + v.bcK + 2 - 64LL * v.nacc;
 }
 
 struct AccArgs {
@@ -596,6 +610,7 @@ struct AccArgs {
   const int64_t *rtop, *rbot, *rrad, *ctop, *cbot, *crad, *cplus;  // this block's lines
   AccView v;
   int64_t M, N, Mp, Np;
+  int negate;  // subtract the product (the -B D part of a complex real part)
 };
 
 constexpr int ACC_MAX = 24;
@@ -608,12 +623,13 @@ __global__ void accumulate_kernel(const AccArgs a) {
   const int64_t i = idx / a.N, j = idx - (idx / a.N) * a.N;
   const int64_t MN = a.M * a.N;
   const AccView &v = a.v;
-  if (a.rtop[i] != INT64_MIN && a.ctop[j] != INT64_MIN && v.ftop_r[i] != INT64_MIN &&
-      v.ftop_c[j] != INT64_MIN) {
+  int64_t vtop;
+  if (a.rtop[i] != INT64_MIN && a.ctop[j] != INT64_MIN && acc_top(v, i, j, vtop)) {
     uint64_t T[RD_MAXW];
     const int nw = assemble(a.mid, i, j, a.Mp, a.Np, T);
-    const bool neg = (T[nw - 1] >> 63) != 0;
-    if (neg) {
+    const bool tneg = (T[nw - 1] >> 63) != 0;
+    const bool neg = tneg != (a.negate != 0);
+    if (tneg) {
       u128 c = 1;
       for (int k = 0; k < nw; ++k) {
         c += (u128)(~T[k]);
@@ -621,7 +637,7 @@ __global__ void accumulate_kernel(const AccArgs a) {
         c >>= 64;
       }
     }
-    const int64_t sh = a.rbot[i] + a.cbot[j] - acc_base(v, i, j);  // T's bit 0 sits at bit sh
+    const int64_t sh = a.rbot[i] + a.cbot[j] - acc_base_of(v, vtop);  // T's bit 0 at bit sh
     uint64_t W[ACC_MAX];
     bool lost = false;
     for (int q = 0; q < v.nacc; ++q) {
@@ -668,8 +684,9 @@ __global__ void acc_round_kernel(const AccView v, BallsOut C, int64_t M, int64_t
   const int64_t MN = M * N;
   for (int q = 0; q < v.nacc; ++q) T[q] = v.acc[(int64_t)q * MN + idx];
   T[v.nacc] = (T[v.nacc - 1] >> 63) ? ~(uint64_t)0 : 0;  // one limb of sign extension
-  const bool live = v.ftop_r[i] != INT64_MIN && v.ftop_c[j] != INT64_MIN;
-  const int64_t base = live ? acc_base(v, i, j) : 0;
+  int64_t vtop;
+  const bool live = acc_top(v, i, j, vtop);
+  const int64_t base = live ? acc_base_of(v, vtop) : 0;
   round_store(T, v.nacc + 1, base, live ? v.err[idx] : 0, Mag{v.rman[idx], v.rexp[idx]}, prec, C,
               i * ldc + j);
 }
@@ -699,8 +716,9 @@ __global__ void acc_to_ball_kernel(const AccView v, BallsOut I, int64_t M, int64
       top = k;
       break;
     }
-  const bool live = v.ftop_r[i] != INT64_MIN && v.ftop_c[j] != INT64_MIN;
-  const int64_t base = live ? acc_base(v, i, j) : 0;
+  int64_t vtop;
+  const bool live = acc_top(v, i, j, vtop);
+  const int64_t base = live ? acc_base_of(v, vtop) : 0;
   const int nl = I.nlimbs;  // nacc + 1
   if (top < 0) {
     for (int q = 0; q < nl; ++q) I.limbs[(int64_t)q * I.stride + idx] = 0;
@@ -731,20 +749,21 @@ __global__ void acc_to_ball_kernel(const AccView v, BallsOut I, int64_t M, int64
 // ------------------------------------------------------------------------- workspace and driver
 
 struct BlockWs {
-  // whole-range scan
-  size_t stats, rtop, rbot, rrad, ctop, cbot, crad, cplus;
+  // whole-range scans of the operand parts: rows of A_re / A_im, columns of B_re / B_im
+  size_t pstats, prtop[2], prbot[2], prrad[2], pctop[2], pcbot[2], pcrad[2], pcplus[2];
   // operands and products of one block
   size_t dA, dB, rA1, rA2, rB1, rB2, mdig, mcar, r1dig, r1car, r2dig, r2car;
-  // several blocks: planner input, plan, per-block line statistics, accumulator, initial balls
+  // several blocks: planner input, plan, per-block line statistics
   size_t tA, bA, tB, bB, blocks, nblocks, bstats;
   size_t brtop, brbot, brrad, bctop, bcbot, bcrad, bcplus;
-  size_t acc, err, rman, rexp, ilimbs, iexp, iflags, irman, irexp, bk;
+  // per output part: accumulator, initial balls, basecase index list
+  size_t acc[2], err[2], rman[2], rexp[2], ilimbs[2], iexp[2], iflags[2], irman[2], irexp[2], bk[2];
   size_t total;
   int Smax, NDmax, Gmax, Gr, maxb, nacc;
   int64_t Kp, Mp, Np;
 };
 
-static BlockWs block_ws(arbgpu_ctx *ctx, int64_t M, int64_t K, int64_t N, int prec) {
+static BlockWs block_ws(arbgpu_ctx *ctx, int64_t M, int64_t K, int64_t N, int prec, bool cplx) {
   BlockWs w{};
   const int64_t hmax = (5LL * prec) / 4 + 192;
   w.Smax = (int)((hmax + 2 + 7) / 8);
@@ -764,14 +783,17 @@ static BlockWs block_ws(arbgpu_ctx *ctx, int64_t M, int64_t K, int64_t N, int pr
     return o;
   };
   const size_t MN = (size_t)M * N;
-  w.stats = take(sizeof(BlockStats));
-  w.rtop = take(8 * M);
-  w.rbot = take(8 * M);
-  w.rrad = take(8 * M);
-  w.ctop = take(8 * N);
-  w.cbot = take(8 * N);
-  w.crad = take(8 * N);
-  w.cplus = take(8 * N);
+  const int parts = cplx ? 2 : 1;
+  w.pstats = take(sizeof(BlockStats) * 4);
+  for (int q = 0; q < parts; ++q) {
+    w.prtop[q] = take(8 * M);
+    w.prbot[q] = take(8 * M);
+    w.prrad[q] = take(8 * M);
+    w.pctop[q] = take(8 * N);
+    w.pcbot[q] = take(8 * N);
+    w.pcrad[q] = take(8 * N);
+    w.pcplus[q] = take(8 * N);
+  }
   w.dA = take((size_t)w.Smax * M * w.Kp * 2);
   w.dB = take((size_t)w.Smax * N * w.Kp * 2);
   w.rA1 = take((size_t)BL_SR * M * w.Kp * 2);
@@ -798,23 +820,26 @@ static BlockWs block_ws(arbgpu_ctx *ctx, int64_t M, int64_t K, int64_t N, int pr
   w.bcbot = take(8 * (size_t)w.maxb * N);
   w.bcrad = take(8 * (size_t)w.maxb * N);
   w.bcplus = take(8 * (size_t)w.maxb * N);
-  w.acc = take(8 * (size_t)w.nacc * MN);
-  w.err = take(4 * MN);
-  w.rman = take(4 * MN);
-  w.rexp = take(8 * MN);
-  w.ilimbs = take(8 * (size_t)(w.nacc + 1) * MN);
-  w.iexp = take(8 * MN);
-  w.iflags = take(4 * MN);
-  w.irman = take(4 * MN);
-  w.irexp = take(8 * MN);
-  w.bk = take(4 * (size_t)K);
+  for (int q = 0; q < parts; ++q) {
+    w.acc[q] = take(8 * (size_t)w.nacc * MN);
+    w.err[q] = take(4 * MN);
+    w.rman[q] = take(4 * MN);
+    w.rexp[q] = take(8 * MN);
+    w.ilimbs[q] = take(8 * (size_t)(w.nacc + 1) * MN);
+    w.iexp[q] = take(8 * MN);
+    w.iflags[q] = take(4 * MN);
+    w.irman[q] = take(4 * MN);
+    w.irexp[q] = take(8 * MN);
+    w.bk[q] = take(4 * 2 * (size_t)K);
+  }
   w.total = off;
   return w;
 }
 
-size_t block_workspace_size(arbgpu_ctx *ctx, int64_t M, int64_t K, int64_t N, int prec) {
+size_t block_workspace_size(arbgpu_ctx *ctx, int64_t M, int64_t K, int64_t N, int prec,
+                            bool cplx) {
   if (M <= 0 || N <= 0 || K <= 0) return 0;
-  return block_ws(ctx, M, K, N, prec).total;
+  return block_ws(ctx, M, K, N, prec, cplx).total;
 }
 
 // Line statistics of one block (pointers into the whole-range or the per-block arrays).
@@ -893,140 +918,102 @@ static int bit_length(int64_t v) {
   return b;
 }
 
-// Real product by Algorithm 2.  Returns ARBGPU_ERR_LIMIT when the inputs hold special values or
-// exceed the path's limits (the caller then uses the classical algorithm).
-arbgpu_status block_matmul_real(arbgpu_ctx *ctx, const arbgpu_balls &C, const arbgpu_balls &A,
-                                const arbgpu_balls &B, int64_t M, int64_t K, int64_t N,
-                                int64_t lda, int64_t ldb, int64_t ldc, int prec, void *workspace,
-                                size_t ws_bytes, cudaStream_t s, bool *used_block) {
-  *used_block = false;
-  if (A.nlimbs > BL_MAX_NL || B.nlimbs > BL_MAX_NL) return ARBGPU_ERR_LIMIT;
-  if (K < BL_BASECASE) return ARBGPU_ERR_LIMIT;
-  BlockWs w = block_ws(ctx, M, K, N, prec);
-  if (!workspace || ws_bytes < w.total) return ARBGPU_ERR_WORKSPACE;
-  uint8_t *ws = (uint8_t *)workspace;
-  BlockStats *st = (BlockStats *)(ws + w.stats);
-  const Lines full{(int64_t *)(ws + w.rtop), (int64_t *)(ws + w.rbot), (int64_t *)(ws + w.rrad),
-                   (int64_t *)(ws + w.ctop), (int64_t *)(ws + w.cbot), (int64_t *)(ws + w.crad),
-                   (int64_t *)(ws + w.cplus)};
+// Statistics of one real product X * Y from the whole-range scans of its parts.
+static BlockStats merge_stats(const BlockStats &rows, const BlockStats &cols) {
+  BlockStats m{};
+  m.pA = rows.pA;
+  m.hA = rows.hA;
+  m.radA = rows.radA;
+  m.pB = cols.pB;
+  m.hB = cols.hB;
+  m.radB = cols.radB;
+  m.special = rows.special | cols.special;
+  return m;
+}
+
+static int64_t height_bound(int prec, const BlockStats &hs) {
+  const int64_t pmax = hs.pA > hs.pB ? hs.pA : hs.pB;
+  return (5 * (prec < pmax ? (int64_t)prec : pmax)) / 4 + 192;
+}
+
+// Add (-1)^negate X Y to the accumulator by Algorithm 2: plan the blocks of this product, run the
+// products of the full blocks and accumulate them; append the basecase indices, tagged with
+// `combo`, to `basek`.
+static arbgpu_status accumulate_product(arbgpu_ctx *ctx, const BlockWs &w, uint8_t *ws,
+                                        const BallsView &Xv, const BallsView &Yv, int64_t M,
+                                        int64_t K, int64_t N, int64_t ldx, int64_t ldy, int prec,
+                                        const Lines &full, const BlockStats &hs, bool negate,
+                                        int combo, const AccView &av, cudaStream_t s,
+                                        std::vector<int32_t> &basek) {
+  const int64_t h = height_bound(prec, hs);
+  std::vector<int32_t> hb;
+  std::vector<BlockStats> hbs;
+  Lines per = full;
+  int hnb = 1;
   BlockStats init{};
   init.hA = init.hB = INT64_MIN;
-  if (cudaMemcpyAsync(st, &init, sizeof(init), cudaMemcpyHostToDevice, s) != cudaSuccess)
-    return ARBGPU_ERR_CUDA;
-  const BallsView Av = view_of(A), Bv = view_of(B);
-  {
-    LaunchScope sc(ctx, s, "scan_rows", M * K);
-    scan_rows_kernel<<<(unsigned)((M * 32 + 255) / 256), 256, 0, s>>>(
-        Av, M, K, lda, nullptr, (int64_t *)full.rtop, (int64_t *)full.rbot, (int64_t *)full.rrad, st);
-  }
-  {
-    LaunchScope sc(ctx, s, "scan_cols", K * N);
-    scan_cols_kernel<<<(unsigned)((N + 31) / 32), dim3(32, 32), 0, s>>>(
-        Bv, K, N, ldb, nullptr, (int64_t *)full.ctop, (int64_t *)full.cbot, (int64_t *)full.crad,
-        (int64_t *)full.cplus, st);
-  }
-  BlockStats hs{};
-  if (cudaMemcpyAsync(&hs, st, sizeof(hs), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
-      cudaStreamSynchronize(s) != cudaSuccess)
-    return ARBGPU_ERR_CUDA;
-  if (hs.special) return ARBGPU_ERR_LIMIT;
-  const int64_t pmax = hs.pA > hs.pB ? hs.pA : hs.pB;
-  const int64_t h = (5 * (prec < pmax ? (int64_t)prec : pmax)) / 4 + 192;
-
   if (hs.hA <= h && hs.hB <= h) {
-    // ---- one block: exact product, one rounding per entry
-    RoundArgs ra{};
-    arbgpu_status st1 = run_block(ctx, w, ws, Av, Bv, M, N, lda, ldb, 0, K,
-                                  digits_for_height(hs.hA), digits_for_height(hs.hB),
-                                  hs.radA != 0, hs.radB != 0, full, s, &ra.mid, &ra.rp1, &ra.rp2);
-    if (st1 != ARBGPU_OK) return st1;
-    ra.rtop = full.rtop;
-    ra.rbot = full.rbot;
-    ra.rrad = full.rrad;
-    ra.ctop = full.ctop;
-    ra.cbot = full.cbot;
-    ra.crad = full.crad;
-    ra.cplus = full.cplus;
-    ra.C = out_of(C);
-    ra.M = M;
-    ra.N = N;
-    ra.ldc = ldc;
-    ra.Mp = w.Mp;
-    ra.Np = w.Np;
-    ra.prec = prec;
+    hb = {0, (int32_t)K, 0};
+    hbs = {hs};
+  } else {
+    int64_t *tA = (int64_t *)(ws + w.tA), *bA = (int64_t *)(ws + w.bA);
+    int64_t *tB = (int64_t *)(ws + w.tB), *bB = (int64_t *)(ws + w.bB);
+    int32_t *blocks = (int32_t *)(ws + w.blocks), *nblocks = (int32_t *)(ws + w.nblocks);
     {
-      LaunchScope sc(ctx, s, "block_round", M * N);
-      block_round_kernel<<<(unsigned)((M * N + 127) / 128), 128, 0, s>>>(ra);
+      LaunchScope sc(ctx, s, "entry_tb", M * K + K * N);
+      entry_tb_kernel<<<(unsigned)((M * K + 255) / 256), 256, 0, s>>>(Xv, M, K, ldx, tA, bA);
+      entry_tb_kernel<<<(unsigned)((K * N + 255) / 256), 256, 0, s>>>(Yv, K, N, ldy, tB, bB);
     }
-    *used_block = true;
-    return cudaGetLastError() == cudaSuccess ? ARBGPU_OK : ARBGPU_ERR_CUDA;
+    {
+      LaunchScope sc(ctx, s, "plan", M + N);
+      plan_kernel<<<1, 1024, 0, s>>>(tA, bA, tB, bB, M, K, N, h, blocks, nblocks, w.maxb);
+    }
+    int32_t nb = 0;
+    if (cudaMemcpyAsync(&nb, nblocks, 4, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+      return ARBGPU_ERR_CUDA;
+    if (nb < 1 || nb > w.maxb) return ARBGPU_ERR_LIMIT;
+    hnb = nb;
+    hb.assign(3 * (size_t)hnb, 0);
+    hbs.assign((size_t)hnb, init);
+    BlockStats *bst = (BlockStats *)(ws + w.bstats);
+    if (cudaMemcpyAsync(hb.data(), blocks, 12 * (size_t)hnb, cudaMemcpyDeviceToHost, s) !=
+            cudaSuccess ||
+        cudaMemcpyAsync(bst, hbs.data(), sizeof(BlockStats) * hnb, cudaMemcpyHostToDevice, s) !=
+            cudaSuccess)
+      return ARBGPU_ERR_CUDA;
+    per = Lines{(int64_t *)(ws + w.brtop), (int64_t *)(ws + w.brbot), (int64_t *)(ws + w.brrad),
+                (int64_t *)(ws + w.bctop), (int64_t *)(ws + w.bcbot), (int64_t *)(ws + w.bcrad),
+                (int64_t *)(ws + w.bcplus)};
+    {
+      LaunchScope sc(ctx, s, "scan_rows", M * K);
+      scan_rows_kernel<<<dim3((unsigned)((M * 32 + 255) / 256), (unsigned)hnb), 256, 0, s>>>(
+          Xv, M, K, ldx, blocks, (int64_t *)per.rtop, (int64_t *)per.rbot, (int64_t *)per.rrad,
+          bst);
+    }
+    {
+      LaunchScope sc(ctx, s, "scan_cols", K * N);
+      scan_cols_kernel<<<dim3((unsigned)((N + 31) / 32), (unsigned)hnb), dim3(32, 32), 0, s>>>(
+          Yv, K, N, ldy, blocks, (int64_t *)per.ctop, (int64_t *)per.cbot, (int64_t *)per.crad,
+          (int64_t *)per.cplus, bst);
+    }
+    if (cudaMemcpyAsync(hbs.data(), bst, sizeof(BlockStats) * hnb, cudaMemcpyDeviceToHost, s) !=
+            cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+      return ARBGPU_ERR_CUDA;
   }
-
-  // ---- several blocks: greedy plan on the device
-  int64_t *tA = (int64_t *)(ws + w.tA), *bA = (int64_t *)(ws + w.bA);
-  int64_t *tB = (int64_t *)(ws + w.tB), *bB = (int64_t *)(ws + w.bB);
-  int32_t *blocks = (int32_t *)(ws + w.blocks), *nblocks = (int32_t *)(ws + w.nblocks);
-  {
-    LaunchScope sc(ctx, s, "entry_tb", M * K + K * N);
-    entry_tb_kernel<<<(unsigned)((M * K + 255) / 256), 256, 0, s>>>(Av, M, K, lda, tA, bA);
-    entry_tb_kernel<<<(unsigned)((K * N + 255) / 256), 256, 0, s>>>(Bv, K, N, ldb, tB, bB);
-  }
-  {
-    LaunchScope sc(ctx, s, "plan", M + N);
-    plan_kernel<<<1, 1024, 0, s>>>(tA, bA, tB, bB, M, K, N, h, blocks, nblocks, w.maxb);
-  }
-  int32_t hnb = 0;
-  if (cudaMemcpyAsync(&hnb, nblocks, 4, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
-      cudaStreamSynchronize(s) != cudaSuccess)
-    return ARBGPU_ERR_CUDA;
-  if (hnb < 1 || hnb > w.maxb) return ARBGPU_ERR_LIMIT;
-  std::vector<int32_t> hb(3 * (size_t)hnb);
-  std::vector<BlockStats> hbs((size_t)hnb, init);
-  BlockStats *bst = (BlockStats *)(ws + w.bstats);
-  if (cudaMemcpyAsync(hb.data(), blocks, 12 * (size_t)hnb, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
-      cudaMemcpyAsync(bst, hbs.data(), sizeof(BlockStats) * hnb, cudaMemcpyHostToDevice, s) !=
-          cudaSuccess)
-    return ARBGPU_ERR_CUDA;
-  const Lines per{(int64_t *)(ws + w.brtop), (int64_t *)(ws + w.brbot), (int64_t *)(ws + w.brrad),
-                  (int64_t *)(ws + w.bctop), (int64_t *)(ws + w.bcbot), (int64_t *)(ws + w.bcrad),
-                  (int64_t *)(ws + w.bcplus)};
-  {
-    LaunchScope sc(ctx, s, "scan_rows", M * K);
-    scan_rows_kernel<<<dim3((unsigned)((M * 32 + 255) / 256), (unsigned)hnb), 256, 0, s>>>(
-        Av, M, K, lda, blocks, (int64_t *)per.rtop, (int64_t *)per.rbot, (int64_t *)per.rrad, bst);
-  }
-  {
-    LaunchScope sc(ctx, s, "scan_cols", K * N);
-    scan_cols_kernel<<<dim3((unsigned)((N + 31) / 32), (unsigned)hnb), dim3(32, 32), 0, s>>>(
-        Bv, K, N, ldb, blocks, (int64_t *)per.ctop, (int64_t *)per.cbot, (int64_t *)per.crad,
-        (int64_t *)per.cplus, bst);
-  }
-  if (cudaMemcpyAsync(hbs.data(), bst, sizeof(BlockStats) * hnb, cudaMemcpyDeviceToHost, s) !=
-          cudaSuccess ||
-      cudaStreamSynchronize(s) != cudaSuccess)
-    return ARBGPU_ERR_CUDA;
-
-  // accumulator
-  AccView av{(uint64_t *)(ws + w.acc), (uint32_t *)(ws + w.err), (uint32_t *)(ws + w.rman),
-             (int64_t *)(ws + w.rexp), w.nacc, bit_length(K), full.rtop, full.ctop};
-  const size_t MN = (size_t)M * N;
-  if (cudaMemsetAsync(av.acc, 0, 8 * (size_t)w.nacc * MN, s) != cudaSuccess ||
-      cudaMemsetAsync(av.err, 0, 4 * MN, s) != cudaSuccess ||
-      cudaMemsetAsync(av.rman, 0, 4 * MN, s) != cudaSuccess ||
-      cudaMemsetAsync(av.rexp, 0, 8 * MN, s) != cudaSuccess)
-    return ARBGPU_ERR_CUDA;
-  std::vector<int32_t> basek;
+  const bool planned = per.rtop != full.rtop;
   for (int b = 0; b < hnb; ++b) {
     const int64_t k0 = hb[3 * b], k1 = hb[3 * b + 1];
     if (hb[3 * b + 2]) {
-      for (int64_t k = k0; k < k1; ++k) basek.push_back((int32_t)k);
+      for (int64_t k = k0; k < k1; ++k) basek.push_back((int32_t)((k << 2) | combo));
       continue;
     }
-    const Lines lb{per.rtop + (int64_t)b * M, per.rbot + (int64_t)b * M, per.rrad + (int64_t)b * M,
-                   per.ctop + (int64_t)b * N, per.cbot + (int64_t)b * N, per.crad + (int64_t)b * N,
-                   per.cplus + (int64_t)b * N};
+    const int64_t oM = planned ? (int64_t)b * M : 0, oN = planned ? (int64_t)b * N : 0;
+    const Lines lb{per.rtop + oM, per.rbot + oM, per.rrad + oM, per.ctop + oN,
+                   per.cbot + oN, per.crad + oN, per.cplus + oN};
     AccArgs aa{};
-    arbgpu_status st1 = run_block(ctx, w, ws, Av, Bv, M, N, lda, ldb, k0, k1 - k0,
+    arbgpu_status st1 = run_block(ctx, w, ws, Xv, Yv, M, N, ldx, ldy, k0, k1 - k0,
                                   digits_for_height(hbs[b].hA), digits_for_height(hbs[b].hB),
                                   hbs[b].radA != 0, hbs[b].radB != 0, lb, s, &aa.mid, &aa.rp1,
                                   &aa.rp2);
@@ -1043,41 +1030,177 @@ arbgpu_status block_matmul_real(arbgpu_ctx *ctx, const arbgpu_balls &C, const ar
     aa.N = N;
     aa.Mp = w.Mp;
     aa.Np = w.Np;
+    aa.negate = negate ? 1 : 0;
     LaunchScope sc(ctx, s, "accumulate", M * N);
     accumulate_kernel<<<(unsigned)((M * N + 127) / 128), 128, 0, s>>>(aa);
   }
-  if (cudaGetLastError() != cudaSuccess) return ARBGPU_ERR_CUDA;
-  if (basek.empty()) {
-    LaunchScope sc(ctx, s, "acc_round", M * N);
-    acc_round_kernel<<<(unsigned)((M * N + 127) / 128), 128, 0, s>>>(av, out_of(C), M, N, ldc,
-                                                                     prec);
-    *used_block = true;
-    return cudaGetLastError() == cudaSuccess ? ARBGPU_OK : ARBGPU_ERR_CUDA;
-  }
-  // basecase blocks: dot products with the accumulated blocks as their initial term
-  arbgpu_balls ib{};
-  ib.limbs = (uint64_t *)(ws + w.ilimbs);
-  ib.limb_stride = (int64_t)MN;
-  ib.nlimbs = w.nacc + 1;
-  ib.exp = (int64_t *)(ws + w.iexp);
-  ib.flags = (uint32_t *)(ws + w.iflags);
-  ib.rad_man = (uint32_t *)(ws + w.irman);
-  ib.rad_exp = (int64_t *)(ws + w.irexp);
-  ib.count = (int64_t)MN;
-  {
-    LaunchScope sc(ctx, s, "acc_to_ball", M * N);
-    acc_to_ball_kernel<<<(unsigned)((M * N + 127) / 128), 128, 0, s>>>(av, out_of(ib), M, N);
-  }
-  int32_t *bk = (int32_t *)(ws + w.bk);
-  if (cudaMemcpyAsync(bk, basek.data(), 4 * basek.size(), cudaMemcpyHostToDevice, s) !=
-      cudaSuccess)
+  return cudaGetLastError() == cudaSuccess ? ARBGPU_OK : ARBGPU_ERR_CUDA;
+}
+
+// Ball matrix product by Algorithm 2 (real, or complex by four real products, Section IV-C).
+// Returns ARBGPU_ERR_LIMIT when the inputs hold special values or exceed the path's limits (the
+// caller then uses the classical algorithm).
+arbgpu_status block_matmul(arbgpu_ctx *ctx, const arbgpu_balls *C, const arbgpu_balls *A,
+                           const arbgpu_balls *B, int64_t M, int64_t K, int64_t N, int64_t lda,
+                           int64_t ldb, int64_t ldc, int prec, bool cplx, void *workspace,
+                           size_t ws_bytes, cudaStream_t s, bool *used_block) {
+  *used_block = false;
+  const int parts = cplx ? 2 : 1;
+  for (int q = 0; q < parts; ++q)
+    if (A[q].nlimbs > BL_MAX_NL || B[q].nlimbs > BL_MAX_NL) return ARBGPU_ERR_LIMIT;
+  if (K < BL_BASECASE) return ARBGPU_ERR_LIMIT;
+  BlockWs w = block_ws(ctx, M, K, N, prec, cplx);
+  if (!workspace || ws_bytes < w.total) return ARBGPU_ERR_WORKSPACE;
+  uint8_t *ws = (uint8_t *)workspace;
+  // whole-range scans: rows of each A part (stats 0, 1), columns of each B part (stats 2, 3)
+  BlockStats *pst = (BlockStats *)(ws + w.pstats);
+  BlockStats init{};
+  init.hA = init.hB = INT64_MIN;
+  BlockStats inits[4] = {init, init, init, init};
+  if (cudaMemcpyAsync(pst, inits, sizeof(inits), cudaMemcpyHostToDevice, s) != cudaSuccess)
     return ARBGPU_ERR_CUDA;
-  arbgpu_status st2 = launch_basecase_dot(ctx, C, A, B, ib, bk, (int64_t)basek.size(), M, N, lda,
-                                          ldb, ldc, prec, s);
-  if (st2 == ARBGPU_OK) *used_block = true;
-  // the host list must outlive the copy: wait for it before `basek` goes out of scope
+  BallsView Av[2], Bv[2];
+  Lines rowsL[2], colsL[2];
+  for (int q = 0; q < parts; ++q) {
+    Av[q] = view_of(A[q]);
+    Bv[q] = view_of(B[q]);
+    rowsL[q] = Lines{(int64_t *)(ws + w.prtop[q]), (int64_t *)(ws + w.prbot[q]),
+                     (int64_t *)(ws + w.prrad[q]), nullptr, nullptr, nullptr, nullptr};
+    colsL[q] = Lines{nullptr, nullptr, nullptr, (int64_t *)(ws + w.pctop[q]),
+                     (int64_t *)(ws + w.pcbot[q]), (int64_t *)(ws + w.pcrad[q]),
+                     (int64_t *)(ws + w.pcplus[q])};
+    {
+      LaunchScope sc(ctx, s, "scan_rows", M * K);
+      scan_rows_kernel<<<(unsigned)((M * 32 + 255) / 256), 256, 0, s>>>(
+          Av[q], M, K, lda, nullptr, (int64_t *)rowsL[q].rtop, (int64_t *)rowsL[q].rbot,
+          (int64_t *)rowsL[q].rrad, pst + q);
+    }
+    {
+      LaunchScope sc(ctx, s, "scan_cols", K * N);
+      scan_cols_kernel<<<(unsigned)((N + 31) / 32), dim3(32, 32), 0, s>>>(
+          Bv[q], K, N, ldb, nullptr, (int64_t *)colsL[q].ctop, (int64_t *)colsL[q].cbot,
+          (int64_t *)colsL[q].crad, (int64_t *)colsL[q].cplus, pst + 2 + q);
+    }
+  }
+  BlockStats hst[4];
+  if (cudaMemcpyAsync(hst, pst, sizeof(hst), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess)
+    return ARBGPU_ERR_CUDA;
+  for (int q = 0; q < parts; ++q)
+    if (hst[q].special || hst[2 + q].special) return ARBGPU_ERR_LIMIT;
+  auto lines_of = [&](int xa, int yb) {
+    return Lines{rowsL[xa].rtop, rowsL[xa].rbot, rowsL[xa].rrad, colsL[yb].ctop,
+                 colsL[yb].cbot, colsL[yb].crad, colsL[yb].cplus};
+  };
+
+  if (!cplx) {
+    const BlockStats hs = merge_stats(hst[0], hst[2]);
+    const int64_t h = height_bound(prec, hs);
+    if (hs.hA <= h && hs.hB <= h) {
+      // ---- one block: exact product, one rounding per entry
+      const Lines full = lines_of(0, 0);
+      RoundArgs ra{};
+      arbgpu_status st1 = run_block(ctx, w, ws, Av[0], Bv[0], M, N, lda, ldb, 0, K,
+                                    digits_for_height(hs.hA), digits_for_height(hs.hB),
+                                    hs.radA != 0, hs.radB != 0, full, s, &ra.mid, &ra.rp1,
+                                    &ra.rp2);
+      if (st1 != ARBGPU_OK) return st1;
+      ra.rtop = full.rtop;
+      ra.rbot = full.rbot;
+      ra.rrad = full.rrad;
+      ra.ctop = full.ctop;
+      ra.cbot = full.cbot;
+      ra.crad = full.crad;
+      ra.cplus = full.cplus;
+      ra.C = out_of(C[0]);
+      ra.M = M;
+      ra.N = N;
+      ra.ldc = ldc;
+      ra.Mp = w.Mp;
+      ra.Np = w.Np;
+      ra.prec = prec;
+      {
+        LaunchScope sc(ctx, s, "block_round", M * N);
+        block_round_kernel<<<(unsigned)((M * N + 127) / 128), 128, 0, s>>>(ra);
+      }
+      *used_block = true;
+      return cudaGetLastError() == cudaSuccess ? ARBGPU_OK : ARBGPU_ERR_CUDA;
+    }
+  }
+
+  // ---- accumulate every real product into its output part, then finish each part
+  // real: C = A B.  complex: Re C = Ar Br - Ai Bi, Im C = Ar Bi + Ai Br (four real products).
+  struct Prod {
+    int part, xa, yb, combo;
+    bool neg;
+  };
+  const Prod real_prods[1] = {{0, 0, 0, 0, false}};
+  const Prod cplx_prods[4] = {{0, 0, 0, 0, false}, {0, 1, 1, 1, true},
+                              {1, 0, 1, 2, false}, {1, 1, 0, 3, false}};
+  const Prod *prods = cplx ? cplx_prods : real_prods;
+  const int nprods = cplx ? 4 : 1;
+  const size_t MN = (size_t)M * N;
+  AccView av[2];
+  std::vector<int32_t> basek[2];
+  for (int q = 0; q < parts; ++q) {
+    av[q] = AccView{(uint64_t *)(ws + w.acc[q]), (uint32_t *)(ws + w.err[q]),
+                    (uint32_t *)(ws + w.rman[q]), (int64_t *)(ws + w.rexp[q]), w.nacc,
+                    bit_length(K) + (cplx ? 1 : 0), {nullptr, nullptr}, {nullptr, nullptr}};
+    int np = 0;
+    for (int t = 0; t < nprods; ++t)
+      if (prods[t].part == q) {
+        av[q].ftop_r[np] = rowsL[prods[t].xa].rtop;
+        av[q].ftop_c[np] = colsL[prods[t].yb].ctop;
+        ++np;
+      }
+    if (cudaMemsetAsync(av[q].acc, 0, 8 * (size_t)w.nacc * MN, s) != cudaSuccess ||
+        cudaMemsetAsync(av[q].err, 0, 4 * MN, s) != cudaSuccess ||
+        cudaMemsetAsync(av[q].rman, 0, 4 * MN, s) != cudaSuccess ||
+        cudaMemsetAsync(av[q].rexp, 0, 8 * MN, s) != cudaSuccess)
+      return ARBGPU_ERR_CUDA;
+  }
+  for (int t = 0; t < nprods; ++t) {
+    const Prod &pr = prods[t];
+    const BlockStats hs = merge_stats(hst[pr.xa], hst[2 + pr.yb]);
+    arbgpu_status st1 = accumulate_product(ctx, w, ws, Av[pr.xa], Bv[pr.yb], M, K, N, lda, ldb,
+                                           prec, lines_of(pr.xa, pr.yb), hs, pr.neg, pr.combo,
+                                           av[pr.part], s, basek[pr.part]);
+    if (st1 != ARBGPU_OK) return st1;
+  }
+  for (int q = 0; q < parts; ++q) {
+    if (basek[q].empty()) {
+      LaunchScope sc(ctx, s, "acc_round", M * N);
+      acc_round_kernel<<<(unsigned)((M * N + 127) / 128), 128, 0, s>>>(av[q], out_of(C[q]), M, N,
+                                                                       ldc, prec);
+      continue;
+    }
+    // basecase blocks: dot products with the accumulated blocks as their initial term
+    arbgpu_balls ib{};
+    ib.limbs = (uint64_t *)(ws + w.ilimbs[q]);
+    ib.limb_stride = (int64_t)MN;
+    ib.nlimbs = w.nacc + 1;
+    ib.exp = (int64_t *)(ws + w.iexp[q]);
+    ib.flags = (uint32_t *)(ws + w.iflags[q]);
+    ib.rad_man = (uint32_t *)(ws + w.irman[q]);
+    ib.rad_exp = (int64_t *)(ws + w.irexp[q]);
+    ib.count = (int64_t)MN;
+    {
+      LaunchScope sc(ctx, s, "acc_to_ball", M * N);
+      acc_to_ball_kernel<<<(unsigned)((M * N + 127) / 128), 128, 0, s>>>(av[q], out_of(ib), M, N);
+    }
+    int32_t *bk = (int32_t *)(ws + w.bk[q]);
+    if (cudaMemcpyAsync(bk, basek[q].data(), 4 * basek[q].size(), cudaMemcpyHostToDevice, s) !=
+        cudaSuccess)
+      return ARBGPU_ERR_CUDA;
+    arbgpu_status st2 = launch_basecase_dot(ctx, C[q], A, B, cplx, ib, bk,
+                                            (int64_t)basek[q].size(), M, N, lda, ldb, ldc, prec,
+                                            s);
+    if (st2 != ARBGPU_OK) return st2;
+  }
+  *used_block = true;
+  // the host-side index lists must outlive their copies
   if (cudaStreamSynchronize(s) != cudaSuccess) return ARBGPU_ERR_CUDA;
-  return st2;
+  return cudaGetLastError() == cudaSuccess ? ARBGPU_OK : ARBGPU_ERR_CUDA;
 }
 
 }  // namespace arbgpu

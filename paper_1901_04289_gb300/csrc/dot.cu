@@ -92,10 +92,11 @@ struct MatDotSrc {
   int64_t units() const { return M * N * K; }
 };
 
-// The basecase of Algorithm 2: entry (i, j) sums A[i, k] B[k, j] over the inner indices k listed in
-// bk (the basecase blocks), starting from the accumulated block products as `initial`.
+// The basecase of Algorithm 2: entry (i, j) sums +- X[i, k] Y[k, j] over the tagged inner indices
+// in bk (the basecase blocks of each real product), starting from the accumulated block products
+// as `initial`.
 struct BasecaseSrc {
-  BallsView A, B, init;
+  BallsView A[2], B[2], init;
   BallsOut C;
   const int32_t *bk;
   int64_t nbk, M, N, lda, ldb, ldc;
@@ -107,11 +108,15 @@ struct BasecaseSrc {
   __device__ int64_t nterms(int64_t) const { return nbk; }
   __device__ TermLoc term(int64_t d, int64_t t) const {
     const int64_t i = d / N, j = d - (d / N) * N;
-    const int64_t k = __ldg(bk + t);
-    return TermLoc{0, i * lda + k, 0, k * ldb + j, false};
+    const int32_t e = __ldg(bk + t);
+    const int64_t k = e >> 2;
+    const int combo = e & 3;
+    const int xa = (combo == 1 || combo == 3) ? 1 : 0;
+    const int yb = (combo == 1 || combo == 2) ? 1 : 0;
+    return TermLoc{xa, i * lda + k, yb, k * ldb + j, combo == 1};
   }
-  __device__ const BallsView &xview(int) const { return A; }
-  __device__ const BallsView &yview(int) const { return B; }
+  __device__ const BallsView &xview(int a) const { return A[a]; }
+  __device__ const BallsView &yview(int b) const { return B[b]; }
   __device__ bool has_initial(int64_t) const { return true; }
   __device__ const BallsView &initial_view(int64_t) const { return init; }
   __device__ int64_t initial_index(int64_t d) const { return d; }
@@ -232,14 +237,21 @@ arbgpu_status launch_matmul_dot(arbgpu_ctx *ctx, const arbgpu_balls *C, const ar
   return launch_dot_src(ctx, s, (complex_mode ? 2 : 1) * M * N, cmax, stream);
 }
 
-arbgpu_status launch_basecase_dot(arbgpu_ctx *ctx, const arbgpu_balls &C, const arbgpu_balls &A,
-                                  const arbgpu_balls &B, const arbgpu_balls &initial,
+arbgpu_status launch_basecase_dot(arbgpu_ctx *ctx, const arbgpu_balls &C, const arbgpu_balls *A,
+                                  const arbgpu_balls *B, bool cplx, const arbgpu_balls &initial,
                                   const int32_t *bk, int64_t nbk, int64_t M, int64_t N,
                                   int64_t lda, int64_t ldb, int64_t ldc, int32_t prec,
                                   cudaStream_t stream) {
   BasecaseSrc s{};
-  s.A = view_of(A);
-  s.B = view_of(B);
+  const int parts = cplx ? 2 : 1;
+  int maxnl = initial.nlimbs;
+  for (int q = 0; q < 2; ++q) {
+    const int src = q < parts ? q : 0;
+    s.A[q] = view_of(A[src]);
+    s.B[q] = view_of(B[src]);
+    maxnl = A[src].nlimbs > maxnl ? A[src].nlimbs : maxnl;
+    maxnl = B[src].nlimbs > maxnl ? B[src].nlimbs : maxnl;
+  }
   s.init = view_of(initial);
   s.C = out_of(C);
   s.bk = bk;
@@ -252,8 +264,6 @@ arbgpu_status launch_basecase_dot(arbgpu_ctx *ctx, const arbgpu_balls &C, const 
   s.prec_v = prec;
   s.prec_max = prec;
   s.len_max = nbk;
-  int maxnl = A.nlimbs > B.nlimbs ? A.nlimbs : B.nlimbs;
-  if (initial.nlimbs > maxnl) maxnl = initial.nlimbs;
   const int cmax = dot_class_for_problem(prec, nbk + 1, maxnl);
   if (cmax < 0) return ARBGPU_ERR_INVALID;
   return launch_dot_src(ctx, s, M * N, cmax, stream);

@@ -77,13 +77,25 @@ bool digit_gemm_fits(int SA, int SB, int64_t Kp);
 // The diagonal ranges the launcher uses: ends[g] = first diagonal after group g (g < groups).
 void digit_gemm_group_ends(int SA, int SB, int groups, int *ends);
 
-// Block algorithm (block.cu).  block_matmul_real returns ARBGPU_ERR_LIMIT (and *used_block =
-// false) when the inputs are not a single exponent block or hold special values.
-size_t block_workspace_size(arbgpu_ctx *ctx, int64_t M, int64_t K, int64_t N, int prec);
-arbgpu_status block_matmul_real(arbgpu_ctx *ctx, const arbgpu_balls &C, const arbgpu_balls &A,
-                                const arbgpu_balls &B, int64_t M, int64_t K, int64_t N,
-                                int64_t lda, int64_t ldb, int64_t ldc, int prec, void *workspace,
-                                size_t ws_bytes, cudaStream_t s, bool *used_block);
+// Block algorithm (block.cu): real or complex (C, A, B point to one or two arbgpu_balls).  Returns
+// ARBGPU_ERR_LIMIT (and *used_block = false) when the inputs hold special values or exceed the
+// path's limits.
+size_t block_workspace_size(arbgpu_ctx *ctx, int64_t M, int64_t K, int64_t N, int prec,
+                            bool cplx);
+arbgpu_status block_matmul(arbgpu_ctx *ctx, const arbgpu_balls *C, const arbgpu_balls *A,
+                           const arbgpu_balls *B, int64_t M, int64_t K, int64_t N, int64_t lda,
+                           int64_t ldb, int64_t ldc, int prec, bool cplx, void *workspace,
+                           size_t ws_bytes, cudaStream_t s, bool *used_block);
+
+// Dot products that finish the basecase blocks of Algorithm 2 (dot.cu): entry (i, j) of C is
+// initial[i*N + j] + sum over the tagged indices e = bk[t] (k = e >> 2, combo = e & 3) of
+// +- X[i*lda + k] * Y[k*ldb + j] with (X, Y, sign) = (A0, B0, +), (A1, B1, -), (A0, B1, +),
+// (A1, B0, +) for combo 0..3 (A1, B1: imaginary parts, used when cplx).
+arbgpu_status launch_basecase_dot(arbgpu_ctx *ctx, const arbgpu_balls &C, const arbgpu_balls *A,
+                                  const arbgpu_balls *B, bool cplx, const arbgpu_balls &initial,
+                                  const int32_t *bk, int64_t nbk, int64_t M, int64_t N,
+                                  int64_t lda, int64_t ldb, int64_t ldc, int32_t prec,
+                                  cudaStream_t stream);
 
 // Integer matrix product on a caller-provided workspace (intmm.cu); ctx->device must be current.
 arbgpu_status int_mat_mul_run(arbgpu_ctx *ctx, uint64_t *T, int32_t t_limbs, const uint64_t *X,
@@ -91,14 +103,6 @@ arbgpu_status int_mat_mul_run(arbgpu_ctx *ctx, uint64_t *T, int32_t t_limbs, con
                               int64_t K, int64_t N, void *workspace, size_t ws_bytes,
                               cudaStream_t s);
 size_t int_mat_mul_workspace(arbgpu_ctx *ctx, int xl, int yl, int64_t M, int64_t K, int64_t N);
-
-// Dot products that finish the basecase blocks of Algorithm 2 (dot.cu): entry (i, j) of C is
-// initial[i*N + j] + sum over k in bk[0..nbk) of A[i*lda + k] * B[k*ldb + j].
-arbgpu_status launch_basecase_dot(arbgpu_ctx *ctx, const arbgpu_balls &C, const arbgpu_balls &A,
-                                  const arbgpu_balls &B, const arbgpu_balls &initial,
-                                  const int32_t *bk, int64_t nbk, int64_t M, int64_t N,
-                                  int64_t lda, int64_t ldb, int64_t ldc, int32_t prec,
-                                  cudaStream_t stream);
 
 // Dot-kernel size class for a precision, a maximal term count and operand limb counts (-1: none).
 int dot_class_for_problem(int prec, int64_t max_terms, int max_nlimbs);

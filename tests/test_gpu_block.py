@@ -138,6 +138,17 @@ def jump_case(seed, M, K, N, jumps, p, nl=1, rad=None):
     return A, B
 
 
+def band_case(seed, M, K, N, lo, hi, nl=1, rad=None):
+    """Columns lo..hi-1 of A are 2^900 larger than the rest: three full blocks."""
+    rng = np.random.default_rng(seed)
+    ea = rng.integers(-5, 5, size=M * K)
+    for k in range(lo, hi):
+        ea[np.arange(M) * K + k] += 900
+    A = random_balls(rng, M * K, nl, 64 * nl, exps=ea, rad_bits=rad, rad_zero_frac=0.5)
+    B = random_balls(rng, K * N, nl, 64 * nl, -5, 5, rad_bits=rad, rad_zero_frac=0.5)
+    return A, B
+
+
 def test_several_blocks_with_basecase(arb):
     """Column 35 of A jumps by 2^900: blocks [0, 35), a one-column block widened to a 30-column
     basecase, then the rest; the block part is accumulated and the basecase done by dots."""
@@ -151,9 +162,9 @@ def test_several_blocks_with_basecase(arb):
 
 
 def test_several_blocks_without_basecase(arb):
-    """Jumps at 60 and 120 in a 180-wide inner dimension: three full blocks, no basecase."""
+    """Columns 60..119 of A sit 2^900 higher: three full blocks, no basecase."""
     M, K, N, p = 40, 180, 36, 128
-    A, B = jump_case(5, M, K, N, [60, 120], p, nl=2, rad=120)
+    A, B = band_case(5, M, K, N, 60, 120, nl=2, rad=120)
     h, blocks = alg2.plan(A, B, M, K, N, p)
     assert len(blocks) >= 3 and not any(b[2] for b in blocks)
     out, names = run_mm(arb, A, B, M, K, N, p, arb.ALG_BLOCK, trace=True)
@@ -202,3 +213,60 @@ def test_identity_times_matrix(arb):
     for idx in range(0, n * n, 13):
         assert X.dy_cmp(X.mid(out, idx), X.mid(A, idx)) == 0
         assert int(out.rad_man[idx]) == 0
+
+
+def run_cmm(arb, A2, B2, M, K, N, prec, alg, trace=False):
+    nl = (prec + 63) // 64
+    ctx = arb.default_context()
+    C2 = [arb.Balls.empty(M * N, nl), arb.Balls.empty(M * N, nl)]
+    if trace:
+        ctx.trace(True)
+    arb.mat_mul(C2, [arb.Balls.from_raw(a) for a in A2], [arb.Balls.from_raw(b) for b in B2], M, K,
+                N, prec, alg=alg)
+    st = ctx.status()
+    names = [r[0] for r in ctx.trace_read()] if trace else []
+    ctx.trace(False)
+    assert st == 0
+    return [to_raw(c) for c in C2], names
+
+
+def check_complex(outs, A2, B2, M, K, N, prec, entries):
+    worst = 0.0
+    for i, j in entries:
+        re, im = X.complex_dot_terms(A2, [i * K + k for k in range(K)], B2,
+                                     [k * N + j for k in range(K)])
+        for part, terms in ((0, re), (1, im)):
+            S, Sabs, R = X.dot_terms_exact(terms)
+            idx = i * N + j
+            m, r = X.mid(outs[part], idx), X.rad(outs[part], idx)
+            assert X.contains(m, r, S, R), (part, i, j)
+            worst = max(worst, X.accuracy_ratio(m, S, Sabs, prec))
+    assert worst <= 1.0, worst
+
+
+def test_complex_block_uniform(arb):
+    """Uniformly scaled complex matrices: four single-block real products, Re = ArBr - AiBi and
+    Im = ArBi + AiBr accumulated exactly (Section IV-C)."""
+    rng = np.random.default_rng(21)
+    n, p = 96, 128
+    A2 = [random_balls(rng, n * n, 2, 128, -10, 10, rad_bits=120, rad_zero_frac=0.5) for _ in "ri"]
+    B2 = [random_balls(rng, n * n, 2, 128, -10, 10, rad_bits=120, rad_zero_frac=0.5) for _ in "ri"]
+    outs, names = run_cmm(arb, A2, B2, n, n, n, p, arb.ALG_BLOCK, trace=True)
+    assert names.count("accumulate") == 4 and "digit_gemm_mid" in names
+    rng2 = np.random.default_rng(4)
+    check_complex(outs, A2, B2, n, n, n, p, [(int(a), int(b)) for a, b in
+                                             zip(rng2.integers(0, n, 80), rng2.integers(0, n, 80))])
+
+
+@pytest.mark.parametrize("structured", [True, False])
+def test_complex_laplace_small(arb, structured):
+    """The complex Laplace(40) workload at N = 128: structured (blocks along the inner index) and
+    literal (i.i.d. exponents: mostly basecase blocks)."""
+    from synth.workloads import complex_matmul_laplace
+    case = complex_matmul_laplace(n=128, structured=structured)
+    outs, names = run_cmm(arb, case.A, case.B, 128, 128, 128, 128, arb.ALG_BLOCK, trace=True)
+    assert "plan" in names
+    rng2 = np.random.default_rng(5)
+    check_complex(outs, case.A, case.B, 128, 128, 128, 128,
+                  [(int(a), int(b)) for a, b in zip(rng2.integers(0, 128, 60),
+                                                    rng2.integers(0, 128, 60))])
