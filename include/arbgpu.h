@@ -176,6 +176,30 @@ arbgpu_status arbgpu_mat_mul(arbgpu_ctx *ctx, const arbgpu_balls *C, const arbgp
                              int64_t ldb, int64_t ldc, int32_t prec, int complex_mode, int alg,
                              uint32_t flags, void *workspace, size_t ws_bytes, void *stream);
 
+/*
+ * Grouped batch of independent ball matrix products (the same operation as arbgpu_mat_mul, item by
+ * item).  `descs` is a HOST array of `count` descriptors (device pointers inside).  Items that use
+ * the classical algorithm (ARBGPU_ALG_DOT, or ARBGPU_ALG_AUTO below the block size) run together
+ * in ONE launch of the dot kernel over a device work list (one warp per output entry, each item at
+ * its own precision); the other items run the block algorithm one after the other on `stream`,
+ * sharing the workspace.  Workspace: arbgpu_mat_mul_batched_workspace_size().
+ */
+typedef struct {
+  arbgpu_balls C[2], A[2], B[2]; /* [1] is the imaginary part when complex_mode */
+  int64_t M, K, N, lda, ldb, ldc;
+  int32_t prec;
+  int32_t complex_mode;
+  int32_t alg;
+  uint32_t flags;
+} arbgpu_matmul_desc;
+
+arbgpu_status arbgpu_mat_mul_batched(arbgpu_ctx *ctx, const arbgpu_matmul_desc *descs,
+                                     int32_t count, void *workspace, size_t ws_bytes,
+                                     void *stream);
+arbgpu_status arbgpu_mat_mul_batched_workspace_size(arbgpu_ctx *ctx,
+                                                    const arbgpu_matmul_desc *descs,
+                                                    int32_t count, size_t *bytes);
+
 /* Workspace bytes arbgpu_mat_mul needs for these sizes (host-only, synchronous).  `a_nlimbs` and
  * `b_nlimbs` are the input arrays' limb counts. */
 arbgpu_status arbgpu_mat_mul_workspace_size(arbgpu_ctx *ctx, int64_t M, int64_t K, int64_t N,

@@ -218,6 +218,43 @@ def mat_mul(C_out, A, B, M, K, N, prec, *, alg=ALG_AUTO, flags=0, lda=None, ldb=
         raise ArbgpuError(rc, "arbgpu_mat_mul")
 
 
+def mat_mul_batched(items, *, workspace=None, ctx=None, stream=None):
+    """Grouped batch of ball matrix products (``arbgpu_mat_mul_batched``).  ``items``: list of
+    dicts with keys C, A, B (Balls or (re, im) pairs), M, K, N, prec and optional alg, lda, ldb,
+    ldc.  Small classical items run in one grouped launch, the others by the block algorithm."""
+    ctx = ctx or default_context()
+    arr = (_lib.CMatmulDesc * len(items))()
+    for q, it in enumerate(items):
+        cs, As, Bs = _pair(it["C"]), _pair(it["A"]), _pair(it["B"])
+        cplx = len(As) == 2
+        d = arr[q]
+        for r in range(2):
+            src = r if cplx else 0
+            d.C[r] = cs[src].cstruct()
+            d.A[r] = As[src].cstruct()
+            d.B[r] = Bs[src].cstruct()
+        d.M, d.K, d.N = it["M"], it["K"], it["N"]
+        d.lda = it.get("lda", it["K"])
+        d.ldb = it.get("ldb", it["N"])
+        d.ldc = it.get("ldc", it["N"])
+        d.prec = it["prec"]
+        d.complex_mode = 1 if cplx else 0
+        d.alg = it.get("alg", ALG_AUTO)
+        d.flags = it.get("flags", 0)
+    if workspace is None:
+        n = C.c_size_t(0)
+        rc = _lib.lib().arbgpu_mat_mul_batched_workspace_size(ctx.handle, arr, len(items),
+                                                              C.byref(n))
+        if rc != 0:
+            raise ArbgpuError(rc, "arbgpu_mat_mul_batched_workspace_size")
+        workspace = ctx.workspace(int(n.value))
+    wsb = 0 if workspace is None else workspace.numel() * workspace.element_size()
+    rc = _lib.lib().arbgpu_mat_mul_batched(ctx.handle, arr, len(items), _ptr(workspace), wsb,
+                                           _stream_ptr(stream))
+    if rc != 0:
+        raise ArbgpuError(rc, "arbgpu_mat_mul_batched")
+
+
 def int_mat_mul(T, t_limbs, X, x_limbs, Y, y_limbs, M, K, N, *, workspace=None, ctx=None,
                 stream=None):
     """Exact integer matrix product over limb planes (``arbgpu_int_mat_mul``)."""

@@ -45,6 +45,13 @@ class CBalls(C.Structure):
     ]
 
 
+class CMatmulDesc(C.Structure):
+    _fields_ = [("C", CBalls * 2), ("A", CBalls * 2), ("B", CBalls * 2), ("M", C.c_int64),
+                ("K", C.c_int64), ("N", C.c_int64), ("lda", C.c_int64), ("ldb", C.c_int64),
+                ("ldc", C.c_int64), ("prec", C.c_int32), ("complex_mode", C.c_int32),
+                ("alg", C.c_int32), ("flags", C.c_uint32)]
+
+
 class CTrace(C.Structure):
     _fields_ = [("name", C.c_char_p), ("ms", C.c_float), ("units", C.c_int64)]
 
@@ -85,6 +92,11 @@ def lib():
                                                         C.POINTER(C.c_size_t)]
         L.arbgpu_int_mat_mul_noalloc.argtypes = [vp, i32, vp, i32, vp, i32, i64, i64, i64, vp, vp]
         L.arbgpu_int_mat_mul_noalloc.restype = C.c_int
+        L.arbgpu_mat_mul_batched.argtypes = [vp, C.POINTER(CMatmulDesc), i32, vp, sz, vp]
+        L.arbgpu_mat_mul_batched.restype = C.c_int
+        L.arbgpu_mat_mul_batched_workspace_size.argtypes = [vp, C.POINTER(CMatmulDesc), i32,
+                                                            C.POINTER(C.c_size_t)]
+        L.arbgpu_mat_mul_batched_workspace_size.restype = C.c_int
         L.arbgpu_launch_count.argtypes = [vp, C.POINTER(C.c_int64)]
         L.arbgpu_trace_enable.argtypes = [vp, C.c_int]
         L.arbgpu_trace_read.argtypes = [vp, C.POINTER(CTrace), i32, C.POINTER(C.c_int32)]
@@ -110,4 +122,5 @@ def exported_symbols():
             "arbgpu_version", "arbgpu_launch_count", "arbgpu_trace_enable", "arbgpu_trace_read",
             "arbgpu_dot", "arbgpu_mat_mul", "arbgpu_mat_mul_workspace_size",
             "arbgpu_int_mat_mul", "arbgpu_int_mat_mul_workspace_size",
-            "arbgpu_int_mat_mul_noalloc"]
+            "arbgpu_int_mat_mul_noalloc", "arbgpu_mat_mul_batched",
+            "arbgpu_mat_mul_batched_workspace_size"]

@@ -264,3 +264,138 @@ arbgpu_status arbgpu_mat_mul(arbgpu_ctx *ctx, const arbgpu_balls *C, const arbgp
 }
 
 }  // extern "C"
+
+namespace {
+
+bool matmul_args_ok(const arbgpu_balls *C, const arbgpu_balls *A, const arbgpu_balls *B, int64_t M,
+                    int64_t K, int64_t N, int64_t lda, int64_t ldb, int64_t ldc, int32_t prec,
+                    int complex_mode) {
+  if (!C || !A || !B || M < 0 || K < 0 || N < 0 || prec < 2 || prec > 1024) return false;
+  if (M == 0 || N == 0) return true;
+  if (lda < K || ldb < N || ldc < N) return false;
+  const int parts = complex_mode ? 2 : 1;
+  for (int q = 0; q < parts; ++q) {
+    if (!balls_ok(C[q]) || !balls_ok(A[q]) || !balls_ok(B[q])) return false;
+    if (K > 0 && (A[q].count < (M - 1) * lda + K || B[q].count < (K - 1) * ldb + N)) return false;
+    if (C[q].count < (M - 1) * ldc + N) return false;
+    if ((int64_t)C[q].nlimbs * 64 < prec) return false;
+    for (int r = 0; r < parts; ++r) {
+      if (balls_alias(C[q], A[r]) || balls_alias(C[q], B[r])) return false;
+      if (r != q && balls_alias(C[q], C[r])) return false;
+    }
+  }
+  return true;
+}
+
+bool item_uses_block(const arbgpu_matmul_desc &d) {
+  if (d.M == 0 || d.N == 0 || d.K == 0) return false;
+  return d.alg == ARBGPU_ALG_BLOCK || (d.alg == ARBGPU_ALG_AUTO && auto_uses_block(d.M, d.K, d.N));
+}
+
+size_t al256(size_t v) { return (v + 255) / 256 * 256; }
+
+}  // namespace
+
+extern "C" {
+
+arbgpu_status arbgpu_mat_mul_batched_workspace_size(arbgpu_ctx *ctx,
+                                                    const arbgpu_matmul_desc *descs,
+                                                    int32_t count, size_t *bytes) {
+  if (!ctx || !bytes || count < 0 || (count > 0 && !descs)) return ARBGPU_ERR_INVALID;
+  size_t grouped = al256(sizeof(GroupItem) * (size_t)count) + al256(8 * (size_t)count);
+  size_t blk = 0;
+  for (int32_t q = 0; q < count; ++q) {
+    const arbgpu_matmul_desc &d = descs[q];
+    if (!item_uses_block(d)) continue;
+    const size_t b = block_workspace_size(ctx, d.M, d.K, d.N, d.prec, d.complex_mode != 0);
+    blk = b > blk ? b : blk;
+  }
+  *bytes = grouped + blk;
+  return ARBGPU_OK;
+}
+
+arbgpu_status arbgpu_mat_mul_batched(arbgpu_ctx *ctx, const arbgpu_matmul_desc *descs,
+                                     int32_t count, void *workspace, size_t ws_bytes,
+                                     void *stream) {
+  if (!ctx || count < 0 || (count > 0 && !descs)) return ARBGPU_ERR_INVALID;
+  if (count == 0) return ARBGPU_OK;
+  for (int32_t q = 0; q < count; ++q) {
+    const arbgpu_matmul_desc &d = descs[q];
+    if (d.alg != ARBGPU_ALG_AUTO && d.alg != ARBGPU_ALG_DOT && d.alg != ARBGPU_ALG_BLOCK)
+      return ARBGPU_ERR_INVALID;
+    if (!matmul_args_ok(d.C, d.A, d.B, d.M, d.K, d.N, d.lda, d.ldb, d.ldc, d.prec,
+                        d.complex_mode))
+      return ARBGPU_ERR_INVALID;
+  }
+  size_t need = 0;
+  arbgpu_status st = arbgpu_mat_mul_batched_workspace_size(ctx, descs, count, &need);
+  if (st != ARBGPU_OK) return st;
+  if (ws_bytes < need || (need && !workspace)) return ARBGPU_ERR_WORKSPACE;
+  if (cudaSetDevice(ctx->device) != cudaSuccess) return ARBGPU_ERR_CUDA;
+  cudaStream_t s = (cudaStream_t)stream;
+  uint8_t *ws = (uint8_t *)workspace;
+  const size_t items_off = 0, ends_off = al256(sizeof(GroupItem) * (size_t)count);
+  const size_t blk_off = ends_off + al256(8 * (size_t)count);
+  // 1. every classical item in one launch of the dot kernel
+  std::vector<GroupItem> items;
+  std::vector<int64_t> ends;
+  std::vector<int32_t> block_items;
+  int64_t total = 0, kmax = 0;
+  int pmax = 2, nlmax = 1;
+  for (int32_t q = 0; q < count; ++q) {
+    const arbgpu_matmul_desc &d = descs[q];
+    if (d.M == 0 || d.N == 0) continue;
+    if (item_uses_block(d)) {
+      block_items.push_back(q);
+      continue;
+    }
+    GroupItem it{};
+    const int parts = d.complex_mode ? 2 : 1;
+    for (int r = 0; r < 2; ++r) {
+      const int src = r < parts ? r : 0;
+      it.A[r] = view_of(d.A[src]);
+      it.B[r] = view_of(d.B[src]);
+      it.C[r] = out_of(d.C[src]);
+      nlmax = d.A[src].nlimbs > nlmax ? d.A[src].nlimbs : nlmax;
+      nlmax = d.B[src].nlimbs > nlmax ? d.B[src].nlimbs : nlmax;
+    }
+    it.M = d.M;
+    it.N = d.N;
+    it.K = d.K;
+    it.lda = d.lda;
+    it.ldb = d.ldb;
+    it.ldc = d.ldc;
+    it.prec = d.prec;
+    it.cplx = d.complex_mode ? 1 : 0;
+    total += (int64_t)parts * d.M * d.N;
+    items.push_back(it);
+    ends.push_back(total);
+    pmax = d.prec > pmax ? d.prec : pmax;
+    kmax = d.K > kmax ? d.K : kmax;
+  }
+  if (!items.empty()) {
+    GroupItem *ditems = (GroupItem *)(ws + items_off);
+    int64_t *dends = (int64_t *)(ws + ends_off);
+    if (cudaMemcpyAsync(ditems, items.data(), sizeof(GroupItem) * items.size(),
+                        cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        cudaMemcpyAsync(dends, ends.data(), 8 * ends.size(), cudaMemcpyHostToDevice, s) !=
+            cudaSuccess)
+      return ARBGPU_ERR_CUDA;
+    st = launch_grouped_dot(ctx, ditems, dends, (int32_t)items.size(), total, pmax, kmax, nlmax, s);
+    if (st != ARBGPU_OK) return st;
+  }
+  // 2. the block items, one after the other, sharing the rest of the workspace
+  for (int32_t q : block_items) {
+    const arbgpu_matmul_desc &d = descs[q];
+    bool used = false;
+    st = block_matmul(ctx, d.C, d.A, d.B, d.M, d.K, d.N, d.lda, d.ldb, d.ldc, d.prec,
+                      d.complex_mode != 0, ws + blk_off, ws_bytes - blk_off, s, &used);
+    if (!used && st == ARBGPU_ERR_LIMIT)
+      st = launch_matmul_dot(ctx, d.C, d.A, d.B, d.M, d.K, d.N, d.lda, d.ldb, d.ldc, d.prec,
+                             d.complex_mode, s);
+    if (st != ARBGPU_OK) return st;
+  }
+  return ARBGPU_OK;
+}
+
+}  // extern "C"

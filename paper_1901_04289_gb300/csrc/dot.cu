@@ -129,6 +129,72 @@ struct BasecaseSrc {
   int64_t units() const { return M * N * nbk; }
 };
 
+// Grouped classical products: virtual dot d belongs to the item q with ends[q-1] <= d < ends[q]
+// (binary search over a device work list); inside the item it is entry (i, j) (and, for complex
+// items, its part).  View slot 4q + {0, 1, 2, 3} is A_re, A_im, B_re, B_im of item q.
+struct GroupedDotSrc {
+  const GroupItem *items;
+  const int64_t *ends;
+  int32_t count;
+  int64_t total;
+  int prec_max;
+  int64_t len_max;
+
+  __device__ int item(int64_t d) const {
+    int lo = 0, hi = count - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi) >> 1;
+      if (__ldg(ends + mid) > d) hi = mid;
+      else lo = mid + 1;
+    }
+    return lo;
+  }
+  __device__ int64_t local(int64_t d, int q) const { return d - (q ? __ldg(ends + q - 1) : 0); }
+  __device__ int64_t ndots() const { return total; }
+  __device__ int64_t nterms(int64_t d) const {
+    const GroupItem &D = items[item(d)];
+    return D.cplx ? 2 * D.K : D.K;
+  }
+  __device__ TermLoc term(int64_t d, int64_t t) const {
+    const int q = item(d);
+    const GroupItem &D = items[q];
+    const int64_t e0 = local(d, q);
+    const int part = D.cplx ? (int)(e0 & 1) : 0;
+    const int64_t e = D.cplx ? (e0 >> 1) : e0;
+    const int64_t i = e / D.N, j = e - (e / D.N) * D.N;
+    const int base = 4 * q;
+    if (!D.cplx) return TermLoc{base + 0, i * D.lda + t, base + 2, t * D.ldb + j, false};
+    const int64_t k = t >> 1;
+    const int w = (int)(t & 1);
+    const int64_t xi = i * D.lda + k, yi = k * D.ldb + j;
+    if (part == 0)
+      return w == 0 ? TermLoc{base + 0, xi, base + 2, yi, false}
+                    : TermLoc{base + 1, xi, base + 3, yi, true};
+    return w == 0 ? TermLoc{base + 0, xi, base + 3, yi, false}
+                  : TermLoc{base + 1, xi, base + 2, yi, false};
+  }
+  __device__ const BallsView &xview(int a) const { return items[a >> 2].A[a & 1]; }
+  __device__ const BallsView &yview(int b) const { return items[b >> 2].B[(b & 3) - 2]; }
+  __device__ bool has_initial(int64_t) const { return false; }
+  __device__ const BallsView &initial_view(int64_t) const { return items[0].A[0]; }
+  __device__ int64_t initial_index(int64_t) const { return 0; }
+  __device__ const BallsOut &out_view(int64_t d) const {
+    const int q = item(d);
+    const GroupItem &D = items[q];
+    return D.C[D.cplx ? (int)(local(d, q) & 1) : 0];
+  }
+  __device__ int64_t out_index(int64_t d) const {
+    const int q = item(d);
+    const GroupItem &D = items[q];
+    const int64_t e0 = local(d, q);
+    const int64_t e = D.cplx ? (e0 >> 1) : e0;
+    const int64_t i = e / D.N, j = e - i * D.N;
+    return i * D.ldc + j;
+  }
+  __device__ int prec(int64_t d) const { return items[item(d)].prec; }
+  int64_t units() const { return total; }
+};
+
 int dot_class_for_problem(int prec, int64_t max_terms, int max_nlimbs) {
   const int ns = dot_ns(prec, max_terms, max_terms);
   int nx = max_nlimbs < ns + 1 ? max_nlimbs : ns + 1;
@@ -267,6 +333,16 @@ arbgpu_status launch_basecase_dot(arbgpu_ctx *ctx, const arbgpu_balls &C, const 
   const int cmax = dot_class_for_problem(prec, nbk + 1, maxnl);
   if (cmax < 0) return ARBGPU_ERR_INVALID;
   return launch_dot_src(ctx, s, M * N, cmax, stream);
+}
+
+arbgpu_status launch_grouped_dot(arbgpu_ctx *ctx, const GroupItem *dev_items,
+                                 const int64_t *dev_ends, int32_t count, int64_t total_dots,
+                                 int prec_max, int64_t k_max, int max_nlimbs,
+                                 cudaStream_t stream) {
+  GroupedDotSrc s{dev_items, dev_ends, count, total_dots, prec_max, 2 * k_max};
+  const int cmax = dot_class_for_problem(prec_max, 2 * k_max + 1, max_nlimbs);
+  if (cmax < 0) return ARBGPU_ERR_INVALID;
+  return launch_dot_src(ctx, s, total_dots, cmax, stream);
 }
 
 }  // namespace arbgpu

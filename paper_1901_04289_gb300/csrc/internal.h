@@ -7,6 +7,7 @@
 #include <vector>
 
 #include "arbgpu.h"
+#include "common.cuh"
 
 // One traced kernel launch: a pair of events recorded around it on its stream.
 struct arbgpu_trace_rec {
@@ -103,6 +104,18 @@ arbgpu_status int_mat_mul_run(arbgpu_ctx *ctx, uint64_t *T, int32_t t_limbs, con
                               int64_t K, int64_t N, void *workspace, size_t ws_bytes,
                               cudaStream_t s);
 size_t int_mat_mul_workspace(arbgpu_ctx *ctx, int xl, int yl, int64_t M, int64_t K, int64_t N);
+
+// Grouped classical products (dot.cu): one launch over the items of a device work list; `ends`
+// holds the running totals of virtual dots (item q owns dots [ends[q-1], ends[q])).
+struct GroupItem {
+  BallsView A[2], B[2];
+  BallsOut C[2];
+  int64_t M, N, K, lda, ldb, ldc;
+  int32_t prec, cplx;
+};
+arbgpu_status launch_grouped_dot(arbgpu_ctx *ctx, const GroupItem *dev_items,
+                                 const int64_t *dev_ends, int32_t count, int64_t total_dots,
+                                 int prec_max, int64_t k_max, int max_nlimbs, cudaStream_t stream);
 
 // Dot-kernel size class for a precision, a maximal term count and operand limb counts (-1: none).
 int dot_class_for_problem(int prec, int64_t max_terms, int max_nlimbs);
