@@ -12,6 +12,7 @@
 //   gemm   T = (E A)(B F) exactly on the tensor cores; P1 = U(|A|) V(R_B), P2 = U(R_A) V(|B|+R_B).
 //   round  C_ij = RNE_p(T_ij 2^(-e_i - f_j)) (one rounding of the exact entry) and
 //          R_ij >= eps_round + P1 2^(...) + P2 2^(...), rounded up to a 30-bit radius.
+#include <cstdlib>
 #include <cstring>
 #include <vector>
 
@@ -315,18 +316,122 @@ struct Ends {
   int e[TG_MAXG];
 };
 
-struct IntProduct {  // one exact integer product in digit + carry form
+// Device copies of a CrtPlan's tables (in the workspace).
+struct CrtTables {
+  const uint32_t *mods;
+  const uint64_t *inv;
+  const uint32_t *pow16;
+  const uint64_t *W;
+  const uint64_t *M;
+  const uint64_t *halfM;
+  int NM, NMW, NCHP;
+};
+
+// One exact integer product.  kind 0: digit + carry form of T itself.  kind 1 (multimodular): for
+// every modulus t, digits [t][3][Mp][Np] and carries [t][Mp][Np] of P_t = sum_k r_ik s_kj over
+// the residues, from which T follows by the Chinese remainder theorem.
+struct IntProduct {
   const uint8_t *digits;
   const int32_t *carries;
   int ND, groups;
   Ends ends;
+  int kind;
+  CrtTables crt;
 };
 
 constexpr int RD_MAXW = 48;  // limbs of the assembled product (ND <= 8 * 46)
 
+// x mod m for x < 2^63 with inv = floor((2^64 - 1) / m) (Barrett reduction).
+__device__ __forceinline__ uint32_t barrett_mod(uint64_t x, uint32_t m, uint64_t inv) {
+  const uint64_t q = __umul64hi(x, inv);
+  uint64_t r = x - q * m;
+  while (r >= m) r -= m;
+  return (uint32_t)r;
+}
+
+// T_ij from its residues: sum_t r_t W_t reduced mod M and centred into (-M/2, M/2).
+__device__ int crt_assemble(const IntProduct &p, int64_t i, int64_t j, int64_t Mp, int64_t Np,
+                            uint64_t *T) {
+  const CrtTables &c = p.crt;
+  const int nw = c.NMW + 1;
+  for (int k = 0; k < nw; ++k) T[k] = 0;
+  const int64_t pl = Mp * Np, o = i * Np + j;
+  for (int t = 0; t < c.NM; ++t) {
+    const uint8_t *dg = p.digits + (int64_t)t * 3 * pl + o;
+    int64_t P = (int64_t)dg[0] | ((int64_t)dg[pl] << 8) | ((int64_t)dg[2 * pl] << 16);
+    P += (int64_t)p.carries[(int64_t)t * pl + o] * (int64_t)(1 << 24);
+    const uint32_t m = c.mods[t];
+    uint32_t r = P >= 0 ? barrett_mod((uint64_t)P, m, c.inv[t])
+                        : (m - barrett_mod((uint64_t)(-P), m, c.inv[t])) % m;
+    if (r == 0) continue;
+    const uint64_t *W = c.W + (int64_t)t * c.NMW;
+    u128 cy = 0;
+    for (int k = 0; k < c.NMW; ++k) {
+      cy += (u128)W[k] * r + T[k];
+      T[k] = (uint64_t)cy;
+      cy >>= 64;
+    }
+    T[c.NMW] += (uint64_t)cy;
+  }
+  // q ~ floor(T / M) (< NM 2^16) from the leading limbs; then correct
+  const int n = c.NMW;
+  const double sc = 18446744073709551616.0;  // 2^64
+  const double tt = ((double)T[n] * sc + (double)T[n - 1]) * sc + (double)T[n - 2];
+  const double mm = (double)c.M[n - 1] * sc + (double)c.M[n - 2];
+  double qd = floor(tt / mm) - 2.0;
+  uint64_t q = qd > 0 ? (uint64_t)qd : 0;
+  if (q) {
+    u128 cy = 0;
+    uint64_t borrow = 0;
+    for (int k = 0; k <= n; ++k) {
+      cy += (u128)(k < n ? c.M[k] : 0) * q;
+      const uint64_t sub = (uint64_t)cy;
+      cy >>= 64;
+      const u128 d = (u128)T[k] - sub - borrow;
+      T[k] = (uint64_t)d;
+      borrow = (uint64_t)(d >> 64) & 1;
+    }
+  }
+  for (int it = 0; it < 8; ++it) {  // while T >= M: T -= M
+    bool ge = T[n] != 0;
+    if (!ge) {
+      ge = true;
+      for (int k = n - 1; k >= 0; --k)
+        if (T[k] != c.M[k]) {
+          ge = T[k] > c.M[k];
+          break;
+        }
+    }
+    if (!ge) break;
+    uint64_t borrow = 0;
+    for (int k = 0; k <= n; ++k) {
+      const u128 d = (u128)T[k] - (k < n ? c.M[k] : 0) - borrow;
+      T[k] = (uint64_t)d;
+      borrow = (uint64_t)(d >> 64) & 1;
+    }
+  }
+  // centre: T > (M - 1) / 2  ->  T - M (two's complement)
+  bool gt = false;
+  for (int k = n - 1; k >= 0; --k)
+    if (T[k] != c.halfM[k]) {
+      gt = T[k] > c.halfM[k];
+      break;
+    }
+  if (gt) {
+    uint64_t borrow = 0;
+    for (int k = 0; k <= n; ++k) {
+      const u128 d = (u128)T[k] - (k < n ? c.M[k] : 0) - borrow;
+      T[k] = (uint64_t)d;
+      borrow = (uint64_t)(d >> 64) & 1;
+    }
+  }
+  return nw;
+}
+
 // Assemble T_ij (two's complement, nw limbs) from its digits and carries.
 __device__ __forceinline__ int assemble(const IntProduct &p, int64_t i, int64_t j, int64_t Mp,
                                         int64_t Np, uint64_t *acc) {
+  if (p.kind == 1) return crt_assemble(p, i, j, Mp, Np, acc);
   const int nw = (8 * p.ND + 32 + 63) / 64 + 1;
   for (int k = 0; k < nw; ++k) acc[k] = 0;
   const uint8_t *dp = p.digits + i * Np + j;
@@ -349,6 +454,71 @@ __device__ __forceinline__ int assemble(const IntProduct &p, int64_t i, int64_t 
     }
   }
   return nw;
+}
+
+// Residues of the scaled integers for the multimodular engine: X = (-1)^neg L 2^sh (as in the
+// digit split), r_t = X mod m_t in balanced form, split into two balanced bytes r_t = 256 h + l,
+// written to planes [2t] (l) and [2t + 1] (h) of [2 NM][rows][Kp].
+__global__ void residue_split_kernel(const BallsView X, bool is_b, int64_t rows, int64_t k0,
+                                     int64_t K, int64_t Kp, int64_t ld, const int64_t *bot,
+                                     const int64_t *top, const uint32_t *mods, const uint64_t *inv,
+                                     const uint32_t *pow16, int NM, int NCHP,
+                                     __nv_bfloat16 *out) {
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= rows * Kp) return;
+  const int64_t r = idx / Kp, k = idx - (idx / Kp) * Kp;
+  const int64_t plane = rows * Kp;
+  __nv_bfloat16 *o = out + r * Kp + k;
+  const __nv_bfloat16 z = __int2bfloat16_rn(0);
+  bool nz = false, neg = false;
+  int64_t e = 0, ex = 0;
+  if (k < K) {
+    e = is_b ? ((k0 + k) * ld + r) : (r * ld + k0 + k);
+    const uint32_t fl = __ldg(X.flags + e);
+    nz = !(fl & (ARBGPU_FLAG_ZERO | SPECIAL_MASK));
+    neg = (fl & ARBGPU_FLAG_SIGN) != 0;
+    ex = __ldg(X.exp + e);
+  }
+  if (!nz) {
+    for (int t = 0; t < 2 * NM; ++t) o[(int64_t)t * plane] = z;
+    return;
+  }
+  // 16-bit chunks of |X| = L 2^sh
+  uint64_t L[BL_MAX_NL];
+  const int nl = X.nlimbs;
+  for (int q = 0; q < nl; ++q) L[q] = __ldg(X.limbs + (int64_t)q * X.stride + e);
+  const int64_t sh = ex - 64LL * nl - bot[r];
+  int nch = (int)((top[r] - bot[r] + 15) / 16) + 1;
+  if (nch > NCHP) nch = NCHP;
+  uint32_t ch[CRT_MAX_CHUNKS];
+  for (int c = 0; c < nch; ++c) {
+    const int64_t pos = 16LL * c - sh;
+    uint32_t v = 0;
+    if (pos > -16 && pos < 64LL * nl) {
+      if (pos >= 0) {
+        const int li = (int)(pos >> 6), bi = (int)(pos & 63);
+        uint64_t w = L[li] >> bi;
+        if (bi > 48 && li + 1 < nl) w |= L[li + 1] << (64 - bi);
+        v = (uint32_t)(w & 0xFFFFu);
+      } else {
+        v = (uint32_t)((L[0] << (-pos)) & 0xFFFFu);
+      }
+    }
+    ch[c] = v;
+  }
+  for (int t = 0; t < NM; ++t) {
+    const uint32_t *pw = pow16 + (int64_t)t * NCHP;
+    uint64_t acc = 0;
+    for (int c = 0; c < nch; ++c) acc += (uint64_t)ch[c] * __ldg(pw + c);
+    const uint32_t m = __ldg(mods + t);
+    int32_t res = (int32_t)barrett_mod(acc, m, __ldg(inv + t));
+    if (res > (int32_t)(m >> 1)) res -= (int32_t)m;
+    if (neg) res = -res;
+    const int32_t lo = ((res + 128) & 255) - 128;
+    const int32_t hi = (res - lo) >> 8;
+    o[(int64_t)(2 * t) * plane] = __int2bfloat16_rn(lo);
+    o[(int64_t)(2 * t + 1) * plane] = __int2bfloat16_rn(hi);
+  }
 }
 
 struct RoundArgs {
@@ -758,8 +928,10 @@ struct BlockWs {
   size_t brtop, brbot, brrad, bctop, bcbot, bcrad, bcplus;
   // per output part: accumulator, initial balls, basecase index list
   size_t acc[2], err[2], rman[2], rexp[2], ilimbs[2], iexp[2], iflags[2], irman[2], irexp[2], bk[2];
+  // multimodular engine: residue planes, residue products, tables
+  size_t resA, resB, cdig, ccar, cmods, cinv, cpow, cW, cM, chalf;
   size_t total;
-  int Smax, NDmax, Gmax, Gr, maxb, nacc;
+  int Smax, NDmax, Gmax, Gr, maxb, nacc, NMmax, NMWmax;
   int64_t Kp, Mp, Np;
 };
 
@@ -775,6 +947,12 @@ static BlockWs block_ws(arbgpu_ctx *ctx, int64_t M, int64_t K, int64_t N, int pr
   w.Gr = digit_gemm_groups(ctx, (int)M, (int)N, 2 * BL_SR - 1);
   w.maxb = (int)(K / BL_BASECASE) + 2;  // every block but the last holds >= 30 indices
   w.nacc = (prec + 63) / 64 + 3;
+  {
+    int bk = 0;
+    for (int64_t v = K; v > 0; v >>= 1) ++bk;
+    w.NMmax = crt_moduli_for_bits((int)(2 * (hmax + 1) + bk + 2));
+    w.NMWmax = (16 * w.NMmax + 63) / 64 + 1;
+  }
   auto al = [](size_t v) { return (v + 255) / 256 * 256; };
   size_t off = 0;
   auto take = [&](size_t bytes) {
@@ -832,6 +1010,16 @@ static BlockWs block_ws(arbgpu_ctx *ctx, int64_t M, int64_t K, int64_t N, int pr
     w.irexp[q] = take(8 * MN);
     w.bk[q] = take(4 * 2 * (size_t)K);
   }
+  w.resA = take((size_t)2 * w.NMmax * M * w.Kp * 2);
+  w.resB = take((size_t)2 * w.NMmax * N * w.Kp * 2);
+  w.cdig = take((size_t)3 * w.NMmax * w.Mp * w.Np);
+  w.ccar = take((size_t)4 * w.NMmax * w.Mp * w.Np);
+  w.cmods = take(4 * (size_t)w.NMmax);
+  w.cinv = take(8 * (size_t)w.NMmax);
+  w.cpow = take(4 * (size_t)w.NMmax * CRT_MAX_CHUNKS);
+  w.cW = take(8 * (size_t)w.NMmax * w.NMWmax);
+  w.cM = take(8 * (size_t)w.NMWmax);
+  w.chalf = take(8 * (size_t)w.NMWmax);
   w.total = off;
   return w;
 }
@@ -847,42 +1035,117 @@ struct Lines {
   const int64_t *rtop, *rbot, *rrad, *ctop, *cbot, *crad, *cplus;
 };
 
+static int digits_for_height(int64_t h) { return h < 0 ? 1 : (int)((h + 2 + 7) / 8); }
+
+static int bit_length(int64_t v) {
+  int b = 0;
+  while (v > 0) {
+    ++b;
+    v >>= 1;
+  }
+  return b;
+}
+
+// The integer engine for a block: digits (S_A x S_B digit products) or multimodular (NM residue
+// products of 2 x 2 digits each, then the Chinese remainder theorem).  ARBGPU_ENGINE=digits|crt
+// forces one; otherwise the cheaper by digit-product count.
+static bool choose_crt(int SA, int SB, int NM) {
+  const char *e = getenv("ARBGPU_ENGINE");
+  if (e && !strcmp(e, "digits")) return false;
+  if (e && !strcmp(e, "crt")) return true;
+  return 4 * NM + 16 < SA * SB;
+}
+
 // Split the block [k0, k0 + Kb) and run its products: T = (E A)(B F), and the radius products
-// P1 = U(|A|) V(R_B) (when B has radii), P2 = U(R_A) V(|B| + R_B) (when A has radii).
+// P1 = U(|A|) V(R_B) (when B has radii), P2 = U(R_A) V(|B| + R_B) (when A has radii).  hA, hB: the
+// largest row / column heights in the block.
 static arbgpu_status run_block(arbgpu_ctx *ctx, const BlockWs &w, uint8_t *ws, const BallsView &Av,
                                const BallsView &Bv, int64_t M, int64_t N, int64_t lda,
-                               int64_t ldb, int64_t k0, int64_t Kb, int SA, int SB, bool radA,
-                               bool radB, const Lines &ln, cudaStream_t s, IntProduct *mid,
-                               IntProduct *rp1, IntProduct *rp2) {
+                               int64_t ldb, int64_t k0, int64_t Kb, int64_t hA, int64_t hB,
+                               bool radA, bool radB, const Lines &ln, cudaStream_t s,
+                               IntProduct *mid, IntProduct *rp1, IntProduct *rp2) {
   const int64_t Kp = (Kb + TG_BK - 1) / TG_BK * TG_BK;
-  if (SA > w.Smax || SB > w.Smax || !digit_gemm_fits(SA, SB, Kp)) return ARBGPU_ERR_LIMIT;
+  const int SA = digits_for_height(hA), SB = digits_for_height(hB);
+  const int NM = crt_moduli_for_bits((int)((hA > 0 ? hA : 0) + (hB > 0 ? hB : 0) +
+                                           bit_length(Kb) + 2));
+  const CrtPlan *plan = nullptr;
+  if (choose_crt(SA, SB, NM) && NM <= w.NMmax) {
+    plan = crt_plan(NM);
+    if (plan && plan->NMW + 1 > RD_MAXW) plan = nullptr;
+  }
+  if (!plan && (SA > w.Smax || SB > w.Smax || !digit_gemm_fits(SA, SB, Kp)))
+    return ARBGPU_ERR_LIMIT;
   __nv_bfloat16 *dA = (__nv_bfloat16 *)(ws + w.dA), *dB = (__nv_bfloat16 *)(ws + w.dB);
   __nv_bfloat16 *rA1 = (__nv_bfloat16 *)(ws + w.rA1), *rA2 = (__nv_bfloat16 *)(ws + w.rA2);
   __nv_bfloat16 *rB1 = (__nv_bfloat16 *)(ws + w.rB1), *rB2 = (__nv_bfloat16 *)(ws + w.rB2);
-  {
+  // radius operands (and the digit planes when the digit engine runs)
+  if (!plan || radA || radB) {
     const int64_t n = M * Kp;
     SplitOut o{dA, radB ? rA1 : nullptr, radA ? rA2 : nullptr};
     LaunchScope sc(ctx, s, "split_a", n);
-    split_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(Av, false, M, k0, Kb, Kp, lda, SA,
-                                                             ln.rbot, ln.rtop, ln.rrad, nullptr, o);
+    split_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(Av, false, M, k0, Kb, Kp, lda,
+                                                             plan ? 0 : SA, ln.rbot, ln.rtop,
+                                                             ln.rrad, nullptr, o);
   }
-  {
+  if (!plan || radA || radB) {
     const int64_t n = N * Kp;
     SplitOut o{dB, radB ? rB1 : nullptr, radA ? rB2 : nullptr};
     LaunchScope sc(ctx, s, "split_b", n);
-    split_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(Bv, true, N, k0, Kb, Kp, ldb, SB,
-                                                             ln.cbot, ln.ctop, ln.crad, ln.cplus, o);
+    split_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(Bv, true, N, k0, Kb, Kp, ldb,
+                                                             plan ? 0 : SB, ln.cbot, ln.ctop,
+                                                             ln.crad, ln.cplus, o);
   }
   if (cudaGetLastError() != cudaSuccess) return ARBGPU_ERR_CUDA;
-  const int ND = SA + SB - 1;
-  const int G = digit_gemm_groups(ctx, (int)M, (int)N, ND);
-  if (G > w.Gmax) return ARBGPU_ERR_LIMIT;
-  {
+  if (plan) {
+    // ---- multimodular: residues, NM batched residue products, CRT in the consumer
+    CrtTables ct{(const uint32_t *)(ws + w.cmods), (const uint64_t *)(ws + w.cinv),
+                 (const uint32_t *)(ws + w.cpow),  (const uint64_t *)(ws + w.cW),
+                 (const uint64_t *)(ws + w.cM),    (const uint64_t *)(ws + w.chalf),
+                 plan->NM, plan->NMW, plan->NCHP};
+    if (cudaMemcpyAsync(ws + w.cmods, plan->mods.data(), 4 * plan->mods.size(),
+                        cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        cudaMemcpyAsync(ws + w.cinv, plan->inv.data(), 8 * plan->inv.size(),
+                        cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        cudaMemcpyAsync(ws + w.cpow, plan->pow16.data(), 4 * plan->pow16.size(),
+                        cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        cudaMemcpyAsync(ws + w.cW, plan->W.data(), 8 * plan->W.size(), cudaMemcpyHostToDevice,
+                        s) != cudaSuccess ||
+        cudaMemcpyAsync(ws + w.cM, plan->M.data(), 8 * plan->M.size(), cudaMemcpyHostToDevice,
+                        s) != cudaSuccess ||
+        cudaMemcpyAsync(ws + w.chalf, plan->halfM.data(), 8 * plan->halfM.size(),
+                        cudaMemcpyHostToDevice, s) != cudaSuccess)
+      return ARBGPU_ERR_CUDA;
+    __nv_bfloat16 *resA = (__nv_bfloat16 *)(ws + w.resA), *resB = (__nv_bfloat16 *)(ws + w.resB);
+    {
+      const int64_t n = M * Kp;
+      LaunchScope sc(ctx, s, "residues_a", n);
+      residue_split_kernel<<<(unsigned)((n + 127) / 128), 128, 0, s>>>(
+          Av, false, M, k0, Kb, Kp, lda, ln.rbot, ln.rtop, ct.mods, ct.inv, ct.pow16, NM,
+          plan->NCHP, resA);
+    }
+    {
+      const int64_t n = N * Kp;
+      LaunchScope sc(ctx, s, "residues_b", n);
+      residue_split_kernel<<<(unsigned)((n + 127) / 128), 128, 0, s>>>(
+          Bv, true, N, k0, Kb, Kp, ldb, ln.cbot, ln.ctop, ct.mods, ct.inv, ct.pow16, NM,
+          plan->NCHP, resB);
+    }
+    if (cudaGetLastError() != cudaSuccess) return ARBGPU_ERR_CUDA;
+    DigitGemmArgs g{resA, resB, (int)M, (int)N, Kp, 2, 2, 1, ws + w.cdig,
+                    (int32_t *)(ws + w.ccar), "crt_gemm", NM};
+    arbgpu_status stg = launch_digit_gemm(ctx, g, s);
+    if (stg != ARBGPU_OK) return stg;
+    *mid = IntProduct{ws + w.cdig, (int32_t *)(ws + w.ccar), 3, 1, {}, 1, ct};
+    mid->ends.e[0] = 3;
+  } else {
+    const int ND = SA + SB - 1;
+    const int G = digit_gemm_groups(ctx, (int)M, (int)N, ND);
+    if (G > w.Gmax) return ARBGPU_ERR_LIMIT;
     DigitGemmArgs g{dA, dB, (int)M, (int)N, Kp, SA, SB, G, ws + w.mdig, (int32_t *)(ws + w.mcar),
                     "digit_gemm_mid"};
     arbgpu_status stg = launch_digit_gemm(ctx, g, s);
     if (stg != ARBGPU_OK) return stg;
-    *mid = IntProduct{ws + w.mdig, (int32_t *)(ws + w.mcar), ND, G, {}};
+    *mid = IntProduct{ws + w.mdig, (int32_t *)(ws + w.mcar), ND, G, {}, 0, {}};
     digit_gemm_group_ends(SA, SB, G, mid->ends.e);
   }
   const int NDr = 2 * BL_SR - 1;
@@ -893,7 +1156,7 @@ static arbgpu_status run_block(arbgpu_ctx *ctx, const BlockWs &w, uint8_t *ws, c
                     (int32_t *)(ws + w.r1car), "digit_gemm_rad"};
     arbgpu_status stg = launch_digit_gemm(ctx, g, s);
     if (stg != ARBGPU_OK) return stg;
-    *rp1 = IntProduct{ws + w.r1dig, (int32_t *)(ws + w.r1car), NDr, w.Gr, {}};
+    *rp1 = IntProduct{ws + w.r1dig, (int32_t *)(ws + w.r1car), NDr, w.Gr, {}, 0, {}};
     digit_gemm_group_ends(BL_SR, BL_SR, w.Gr, rp1->ends.e);
   }
   if (radA) {
@@ -901,21 +1164,10 @@ static arbgpu_status run_block(arbgpu_ctx *ctx, const BlockWs &w, uint8_t *ws, c
                     (int32_t *)(ws + w.r2car), "digit_gemm_rad"};
     arbgpu_status stg = launch_digit_gemm(ctx, g, s);
     if (stg != ARBGPU_OK) return stg;
-    *rp2 = IntProduct{ws + w.r2dig, (int32_t *)(ws + w.r2car), NDr, w.Gr, {}};
+    *rp2 = IntProduct{ws + w.r2dig, (int32_t *)(ws + w.r2car), NDr, w.Gr, {}, 0, {}};
     digit_gemm_group_ends(BL_SR, BL_SR, w.Gr, rp2->ends.e);
   }
   return ARBGPU_OK;
-}
-
-static int digits_for_height(int64_t h) { return h < 0 ? 1 : (int)((h + 2 + 7) / 8); }
-
-static int bit_length(int64_t v) {
-  int b = 0;
-  while (v > 0) {
-    ++b;
-    v >>= 1;
-  }
-  return b;
 }
 
 // Statistics of one real product X * Y from the whole-range scans of its parts.
@@ -1013,10 +1265,9 @@ static arbgpu_status accumulate_product(arbgpu_ctx *ctx, const BlockWs &w, uint8
     const Lines lb{per.rtop + oM, per.rbot + oM, per.rrad + oM, per.ctop + oN,
                    per.cbot + oN, per.crad + oN, per.cplus + oN};
     AccArgs aa{};
-    arbgpu_status st1 = run_block(ctx, w, ws, Xv, Yv, M, N, ldx, ldy, k0, k1 - k0,
-                                  digits_for_height(hbs[b].hA), digits_for_height(hbs[b].hB),
-                                  hbs[b].radA != 0, hbs[b].radB != 0, lb, s, &aa.mid, &aa.rp1,
-                                  &aa.rp2);
+    arbgpu_status st1 = run_block(ctx, w, ws, Xv, Yv, M, N, ldx, ldy, k0, k1 - k0, hbs[b].hA,
+                                  hbs[b].hB, hbs[b].radA != 0, hbs[b].radB != 0, lb, s, &aa.mid,
+                                  &aa.rp1, &aa.rp2);
     if (st1 != ARBGPU_OK) return st1;
     aa.rtop = lb.rtop;
     aa.rbot = lb.rbot;
@@ -1100,8 +1351,7 @@ arbgpu_status block_matmul(arbgpu_ctx *ctx, const arbgpu_balls *C, const arbgpu_
       // ---- one block: exact product, one rounding per entry
       const Lines full = lines_of(0, 0);
       RoundArgs ra{};
-      arbgpu_status st1 = run_block(ctx, w, ws, Av[0], Bv[0], M, N, lda, ldb, 0, K,
-                                    digits_for_height(hs.hA), digits_for_height(hs.hB),
+      arbgpu_status st1 = run_block(ctx, w, ws, Av[0], Bv[0], M, N, lda, ldb, 0, K, hs.hA, hs.hB,
                                     hs.radA != 0, hs.radB != 0, full, s, &ra.mid, &ra.rp1,
                                     &ra.rp2);
       if (st1 != ARBGPU_OK) return st1;

@@ -1,0 +1,134 @@
+// Host side of the multimodular integer engine: the moduli (primes just below 2^16), their Barrett
+// reciprocals, the tables 2^(16c) mod m_t, and the Chinese-remainder weights
+// W_t = (M / m_t) * ((M / m_t)^-1 mod m_t), M = prod m_t, all computed once per modulus count and
+// cached.  (The paper's integer products use FLINT's multimodular algorithm, Section IV.)
+#include <cmath>
+#include <map>
+#include <memory>
+#include <mutex>
+
+#include "internal.h"
+
+namespace arbgpu {
+
+namespace {
+
+// Primes below 2^16 in decreasing order (sieve of Eratosthenes).
+const std::vector<uint32_t> &primes_desc() {
+  static std::vector<uint32_t> p;
+  static std::once_flag once;
+  std::call_once(once, []() {
+    const uint32_t n = 1u << 16;
+    std::vector<char> comp(n, 0);
+    for (uint32_t i = 2; i * i < n; ++i)
+      if (!comp[i])
+        for (uint32_t j = i * i; j < n; j += i) comp[j] = 1;
+    for (uint32_t i = n - 1; i >= 3; --i)
+      if (!comp[i]) p.push_back(i);
+  });
+  return p;
+}
+
+// little-endian multi-limb helpers
+void mul_small(std::vector<uint64_t> &a, uint32_t m) {
+  u128 c = 0;
+  for (auto &w : a) {
+    c += (u128)w * m;
+    w = (uint64_t)c;
+    c >>= 64;
+  }
+  if (c) a.push_back((uint64_t)c);
+}
+
+int bit_length(const std::vector<uint64_t> &a) {
+  for (int k = (int)a.size() - 1; k >= 0; --k)
+    if (a[k]) return 64 * k + 64 - __builtin_clzll(a[k]);
+  return 0;
+}
+
+uint32_t inv_mod(uint32_t a, uint32_t m) {  // a^-1 mod m (gcd(a, m) = 1)
+  int64_t t = 0, nt = 1, r = m, nr = a % m;
+  while (nr) {
+    const int64_t q = r / nr;
+    int64_t tmp = t - q * nt;
+    t = nt;
+    nt = tmp;
+    tmp = r - q * nr;
+    r = nr;
+    nr = tmp;
+  }
+  if (t < 0) t += m;
+  return (uint32_t)t;
+}
+
+std::mutex g_mu;
+std::map<int, std::unique_ptr<CrtPlan>> g_plans;
+
+std::unique_ptr<CrtPlan> build_plan(int NM) {
+  const auto &pr = primes_desc();
+  auto P = std::make_unique<CrtPlan>();
+  P->NM = NM;
+  P->mods.assign(pr.begin(), pr.begin() + NM);
+  std::vector<uint64_t> M{1};
+  for (uint32_t m : P->mods) mul_small(M, m);
+  P->NMW = (bit_length(M) + 63) / 64;
+  if (P->NMW < 2) P->NMW = 2;
+  M.resize(P->NMW, 0);
+  P->M = M;
+  // (M - 1) / 2 (M is odd)
+  P->halfM = M;
+  P->halfM[0] -= 1;
+  for (int k = 0; k < P->NMW; ++k) {
+    const uint64_t hi = k + 1 < P->NMW ? P->halfM[k + 1] : 0;
+    P->halfM[k] = (P->halfM[k] >> 1) | (hi << 63);
+  }
+  P->inv.resize(NM);
+  P->W.assign((size_t)NM * P->NMW, 0);
+  for (int t = 0; t < NM; ++t) {
+    const uint32_t m = P->mods[t];
+    P->inv[t] = ~(uint64_t)0 / m;
+    std::vector<uint64_t> Q{1};
+    uint64_t qmod = 1;
+    for (int s = 0; s < NM; ++s)
+      if (s != t) {
+        mul_small(Q, P->mods[s]);
+        qmod = qmod * (P->mods[s] % m) % m;
+      }
+    mul_small(Q, inv_mod((uint32_t)qmod, m));
+    for (int k = 0; k < P->NMW && k < (int)Q.size(); ++k) P->W[(size_t)t * P->NMW + k] = Q[k];
+  }
+  P->NCHP = CRT_MAX_CHUNKS;
+  P->pow16.resize((size_t)NM * P->NCHP);
+  for (int t = 0; t < NM; ++t) {
+    uint64_t v = 1;
+    for (int c = 0; c < P->NCHP; ++c) {
+      P->pow16[(size_t)t * P->NCHP + c] = (uint32_t)v;
+      v = (v << 16) % P->mods[t];
+    }
+  }
+  return P;
+}
+
+}  // namespace
+
+// Number of moduli whose product exceeds 2^bits (so signed integers of `bits` bits, sign
+// included, are recovered uniquely from their residues).
+int crt_moduli_for_bits(int bits) {
+  const auto &pr = primes_desc();
+  double acc = 0;
+  int n = 0;
+  while (n < (int)pr.size() && acc < bits + 1.0) acc += std::log2((double)pr[n++]);
+  return n < 5 ? 5 : n;
+}
+
+const CrtPlan *crt_plan(int NM) {
+  std::lock_guard<std::mutex> lock(g_mu);
+  auto it = g_plans.find(NM);
+  if (it != g_plans.end()) return it->second.get();
+  auto P = build_plan(NM);
+  const CrtPlan *r = P.get();
+  g_plans[NM] = std::move(P);
+  return r;
+}
+
+}  // namespace arbgpu

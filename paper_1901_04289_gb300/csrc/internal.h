@@ -71,6 +71,7 @@ struct DigitGemmArgs {
   uint8_t *digits;
   int32_t *carries;
   const char *name;
+  int batch = 1;  // independent products sharing the plane layout (item b: planes b*SA.., b*SB..)
 };
 arbgpu_status launch_digit_gemm(arbgpu_ctx *ctx, const DigitGemmArgs &a, cudaStream_t stream);
 int digit_gemm_groups(arbgpu_ctx *ctx, int M, int N, int ND);
@@ -116,6 +117,19 @@ struct GroupItem {
 arbgpu_status launch_grouped_dot(arbgpu_ctx *ctx, const GroupItem *dev_items,
                                  const int64_t *dev_ends, int32_t count, int64_t total_dots,
                                  int prec_max, int64_t k_max, int max_nlimbs, cudaStream_t stream);
+
+// Multimodular engine (crt.cu): moduli = the NM largest primes below 2^16.
+constexpr int CRT_MAX_CHUNKS = 100;  // 16-bit chunks of a scaled integer (1600 bits)
+struct CrtPlan {
+  int NM, NMW, NCHP;              // moduli, limbs of M, columns of pow16
+  std::vector<uint32_t> mods;     // m_t
+  std::vector<uint64_t> inv;      // floor((2^64 - 1) / m_t)
+  std::vector<uint32_t> pow16;    // [NM][NCHP]: 2^(16c) mod m_t
+  std::vector<uint64_t> W;        // [NM][NMW]: (M / m_t) * ((M / m_t)^-1 mod m_t)
+  std::vector<uint64_t> M, halfM; // M and (M - 1) / 2
+};
+int crt_moduli_for_bits(int bits);
+const CrtPlan *crt_plan(int NM);
 
 // Dot-kernel size class for a precision, a maximal term count and operand limb counts (-1: none).
 int dot_class_for_problem(int prec, int64_t max_terms, int max_nlimbs);

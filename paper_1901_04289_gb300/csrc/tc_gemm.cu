@@ -32,7 +32,11 @@ __global__ void __launch_bounds__(TG_THREADS, 1)
   const int lane = threadIdx.x & 31;
   const int ntiles = P.tiles_m * P.tiles_n;
   const int tile = blockIdx.x % ntiles;
-  const int group = blockIdx.x / ntiles;
+  const int group = (blockIdx.x / ntiles) % P.groups;
+  const int bidx = blockIdx.x / (ntiles * P.groups);  // batch item
+  const int zA = bidx * P.SA, zB = bidx * P.SB;       // its first digit plane
+  uint8_t *const out_digits = P.digits + (int64_t)bidx * P.ND * P.Mp * P.Np;
+  int32_t *const out_carries = P.carries + (int64_t)bidx * P.groups * P.Mp * P.Np;
   const int mt = tile / P.tiles_n, nt = tile % P.tiles_n;
   const int m0 = mt * TG_BM, n0 = nt * TG_BN;
   const int d0 = P.dstart[group], d1 = P.dstart[group + 1];
@@ -86,8 +90,10 @@ __global__ void __launch_bounds__(TG_THREADS, 1)
               break;
             }
             mbar_arrive_expect_tx(&sh->full[s], 2 * TG_TILE_BYTES);
-            tma_load_3d(sA + (size_t)s * TG_TILE_BYTES, &tmA, &sh->full[s], kb * TG_BK, m0, j);
-            tma_load_3d(sB + (size_t)s * TG_TILE_BYTES, &tmB, &sh->full[s], kb * TG_BK, n0, l);
+            tma_load_3d(sA + (size_t)s * TG_TILE_BYTES, &tmA, &sh->full[s], kb * TG_BK, m0,
+                        zA + j);
+            tma_load_3d(sB + (size_t)s * TG_TILE_BYTES, &tmB, &sh->full[s], kb * TG_BK, n0,
+                        zB + l);
           }
         }
       }
@@ -197,12 +203,12 @@ __global__ void __launch_bounds__(TG_THREADS, 1)
       }
 #pragma unroll
       for (int c = 0; c < 64; ++c) R[c] >>= 8;
-      uint4 *dst = (uint4 *)(P.digits + ((int64_t)d * P.Mp + gm) * P.Np + gcol);
+      uint4 *dst = (uint4 *)(out_digits + ((int64_t)d * P.Mp + gm) * P.Np + gcol);
 #pragma unroll
       for (int c = 0; c < 4; ++c)
         dst[c] = make_uint4(packed[4 * c], packed[4 * c + 1], packed[4 * c + 2], packed[4 * c + 3]);
     }
-    int4 *cdst = (int4 *)(P.carries + ((int64_t)group * P.Mp + gm) * P.Np + gcol);
+    int4 *cdst = (int4 *)(out_carries + ((int64_t)group * P.Mp + gm) * P.Np + gcol);
 #pragma unroll
     for (int c = 0; c < 16; ++c) cdst[c] = make_int4(R[4 * c], R[4 * c + 1], R[4 * c + 2], R[4 * c + 3]);
   }
@@ -304,6 +310,7 @@ arbgpu_status launch_digit_gemm(arbgpu_ctx *ctx, const DigitGemmArgs &a, cudaStr
   P.Np = (int64_t)P.tiles_n * TG_BN;
   P.digits = a.digits;
   P.carries = a.carries;
+  P.batch = a.batch > 0 ? a.batch : 1;
   P.status = ctx->status;
   const int G = a.groups;
   if (G < 1 || G > TG_MAXG || G > P.ND) return ARBGPU_ERR_INVALID;
@@ -316,7 +323,8 @@ arbgpu_status launch_digit_gemm(arbgpu_ctx *ctx, const DigitGemmArgs &a, cudaStr
     if (P.dstart[t + 1] <= P.dstart[t]) return ARBGPU_ERR_INVALID;
 
   CUtensorMap tmA, tmB;
-  if (!make_plane_map(&tmA, a.A, a.Kp, a.M, a.SA) || !make_plane_map(&tmB, a.B, a.Kp, a.N, a.SB))
+  if (!make_plane_map(&tmA, a.A, a.Kp, a.M, (int64_t)a.SA * P.batch) ||
+      !make_plane_map(&tmB, a.B, a.Kp, a.N, (int64_t)a.SB * P.batch))
     return ARBGPU_ERR_CUDA;
   static bool attr_set[256] = {};
   const int dev = ctx->device & 255;
@@ -326,10 +334,11 @@ arbgpu_status launch_digit_gemm(arbgpu_ctx *ctx, const DigitGemmArgs &a, cudaStr
       return ARBGPU_ERR_CUDA;
     attr_set[dev] = true;
   }
-  const int grid = P.tiles_m * P.tiles_n * G;
+  const int64_t grid = (int64_t)P.tiles_m * P.tiles_n * G * P.batch;
+  if (grid > 0x7fffffff) return ARBGPU_ERR_LIMIT;
   LaunchScope scope(ctx, stream, a.name ? a.name : "digit_gemm",
-                    (int64_t)(a.SA) * a.SB * (int64_t)a.M * a.N * a.Kp);
-  digit_gemm_kernel<<<grid, TG_THREADS, TG_SMEM_BYTES, stream>>>(tmA, tmB, P);
+                    (int64_t)(a.SA) * a.SB * (int64_t)a.M * a.N * a.Kp * P.batch);
+  digit_gemm_kernel<<<(unsigned)grid, TG_THREADS, TG_SMEM_BYTES, stream>>>(tmA, tmB, P);
   return cudaGetLastError() == cudaSuccess ? ARBGPU_OK : ARBGPU_ERR_CUDA;
 }
 

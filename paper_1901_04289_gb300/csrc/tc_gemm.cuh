@@ -52,6 +52,8 @@ struct DigitGemmParams {
   uint8_t *digits;          // [ND][Mp][Np] digit bytes of T
   int32_t *carries;         // [groups][Mp][Np] carry out of each group's last diagonal
   int64_t Mp, Np;           // padded leading sizes (multiples of the tile)
+  int batch;                // independent products: item b uses planes [b*SA, (b+1)*SA) of A,
+                            // [b*SB, (b+1)*SB) of B, and its own digits / carries
   int *status;
 };
 

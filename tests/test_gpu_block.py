@@ -270,3 +270,59 @@ def test_complex_laplace_small(arb, structured):
     check_complex(outs, case.A, case.B, 128, 128, 128, 128,
                   [(int(a), int(b)) for a, b in zip(rng2.integers(0, 128, 60),
                                                     rng2.integers(0, 128, 60))])
+
+
+def _run_engine(arb, engine, A, B, M, K, N, prec, cplx=False):
+    import os
+    old = os.environ.get("ARBGPU_ENGINE")
+    os.environ["ARBGPU_ENGINE"] = engine
+    try:
+        if cplx:
+            outs, names = run_cmm(arb, A, B, M, K, N, prec, arb.ALG_BLOCK, trace=True)
+        else:
+            out, names = run_mm(arb, A, B, M, K, N, prec, arb.ALG_BLOCK, trace=True)
+            outs = [out]
+    finally:
+        if old is None:
+            del os.environ["ARBGPU_ENGINE"]
+        else:
+            os.environ["ARBGPU_ENGINE"] = old
+    return outs, names
+
+
+@pytest.mark.parametrize("kind", ["single", "several", "complex"])
+def test_digit_and_multimodular_engines_agree_bit_for_bit(arb, kind):
+    """The exact block integers T are the same whichever engine forms them (digit products or
+    residues + Chinese remainder theorem), so every output field must agree."""
+    rng = np.random.default_rng(40)
+    if kind == "single":
+        M, K, N, p = 130, 192, 120, 256
+        A = random_balls(rng, M * K, 4, 256, -20, 20, rad_bits=250, rad_zero_frac=0.3)
+        B = random_balls(rng, K * N, 4, 256, -20, 20, rad_bits=250, rad_zero_frac=0.3)
+    elif kind == "several":
+        M, K, N, p = 40, 180, 36, 128
+        A, B = band_case(5, M, K, N, 60, 120, nl=2, rad=120)
+    else:
+        M = K = N = 80
+        p = 128
+        A = [random_balls(rng, M * K, 2, 128, -10, 10, rad_bits=120) for _ in "ri"]
+        B = [random_balls(rng, K * N, 2, 128, -10, 10, rad_bits=120) for _ in "ri"]
+    od, nd = _run_engine(arb, "digits", A, B, M, K, N, p, cplx=(kind == "complex"))
+    oc, nc = _run_engine(arb, "crt", A, B, M, K, N, p, cplx=(kind == "complex"))
+    assert "crt_gemm" in nc and "crt_gemm" not in nd
+    for a, b in zip(od, oc):
+        for f in ("limbs", "exp", "flags", "rad_man", "rad_exp"):
+            assert np.array_equal(getattr(a, f), getattr(b, f)), f
+
+
+def test_multimodular_p1024(arb):
+    """p = 1024: 1024-bit mantissas, about 190 moduli; midpoints are the exactly rounded values."""
+    rng = np.random.default_rng(41)
+    M, K, N, p = 48, 64, 40, 1024
+    A = random_balls(rng, M * K, 16, 1024, -50, 50, rad_bits=1016, rad_zero_frac=0.5)
+    B = random_balls(rng, K * N, 16, 1024, -50, 50, rad_bits=1016, rad_zero_frac=0.5)
+    out, names = run_mm(arb, A, B, M, K, N, p, arb.ALG_BLOCK, trace=True)
+    assert "crt_gemm" in names
+    rng2 = np.random.default_rng(2)
+    check_entries(out, A, B, M, K, N, p, [(int(a), int(b)) for a, b in
+                                         zip(rng2.integers(0, M, 40), rng2.integers(0, N, 40))], 16)
