@@ -70,7 +70,7 @@ def test_block_small_exact_rounding(arb, M, K, N, prec, spread, rad):
     h, blocks = alg2.plan(A, B, M, K, N, prec)
     assert blocks == [(0, K, False)]  # a single exponent block
     out, names = run_mm(arb, A, B, M, K, N, prec, arb.ALG_BLOCK, trace=True)
-    assert any(n.startswith("digit_gemm") for n in names)
+    assert any(n.startswith("digit_gemm") or n == "crt_gemm" for n in names)
     rng2 = np.random.default_rng(1)
     ents = [(int(a), int(b)) for a, b in zip(rng2.integers(0, M, 150), rng2.integers(0, N, 150))]
     loose = check_entries(out, A, B, M, K, N, prec, ents, nl)
@@ -98,7 +98,7 @@ def test_block_exact_inputs_give_exact_results(arb):
 def test_block_n512_p256_sampled(arb):
     case = block_matmul_n512(prec=256)
     out, names = run_mm(arb, case.A[0], case.B[0], 512, 512, 512, 256, arb.ALG_AUTO, trace=True)
-    assert "digit_gemm_mid" in names
+    assert "crt_gemm" in names  # the multimodular engine is the default at this size
     rng = np.random.default_rng(5)
     ents = [(int(a), int(b)) for a, b in zip(rng.integers(0, 512, 120), rng.integers(0, 512, 120))]
     loose = check_entries(out, case.A[0], case.B[0], 512, 512, 512, 256, ents, 4)
@@ -252,7 +252,7 @@ def test_complex_block_uniform(arb):
     A2 = [random_balls(rng, n * n, 2, 128, -10, 10, rad_bits=120, rad_zero_frac=0.5) for _ in "ri"]
     B2 = [random_balls(rng, n * n, 2, 128, -10, 10, rad_bits=120, rad_zero_frac=0.5) for _ in "ri"]
     outs, names = run_cmm(arb, A2, B2, n, n, n, p, arb.ALG_BLOCK, trace=True)
-    assert names.count("accumulate") == 4 and "digit_gemm_mid" in names
+    assert names.count("accumulate") == 4 and "crt_gemm" in names
     rng2 = np.random.default_rng(4)
     check_complex(outs, A2, B2, n, n, n, p, [(int(a), int(b)) for a, b in
                                              zip(rng2.integers(0, n, 80), rng2.integers(0, n, 80))])
