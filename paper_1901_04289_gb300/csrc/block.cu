@@ -14,6 +14,7 @@
 //          R_ij >= eps_round + P1 2^(...) + P2 2^(...), rounded up to a 30-bit radius.
 #include <cstdlib>
 #include <cstring>
+#include <mutex>
 #include <vector>
 
 #include "internal.h"
@@ -316,15 +317,18 @@ struct Ends {
   int e[TG_MAXG];
 };
 
-// Device copies of a CrtPlan's tables (in the workspace).
+// Per-modulus constants (the first CRT_MAX_MODULI primes below 2^16), loaded once per device:
+// m_t, floor((2^64 - 1) / m_t) and 2^(16c) mod m_t.
+__constant__ uint32_t c_mods[CRT_MAX_MODULI];
+__constant__ uint64_t c_inv[CRT_MAX_MODULI];
+__constant__ uint16_t c_pow16[CRT_MAX_MODULI * CRT_MAX_CHUNKS];
+
+// Device copies of the tables of one modulus count (in the workspace).
 struct CrtTables {
-  const uint32_t *mods;
-  const uint64_t *inv;
-  const uint32_t *pow16;
-  const uint64_t *W;
+  const uint32_t *W32;  // [NM][NW32P]
   const uint64_t *M;
   const uint64_t *halfM;
-  int NM, NMW, NCHP;
+  int NM, NMW, NW32P;
 };
 
 // One exact integer product.  kind 0: digit + carry form of T itself.  kind 1 (multimodular): for
@@ -349,29 +353,48 @@ __device__ __forceinline__ uint32_t barrett_mod(uint64_t x, uint32_t m, uint64_t
   return (uint32_t)r;
 }
 
-// T_ij from its residues: sum_t r_t W_t reduced mod M and centred into (-M/2, M/2).
+// T_ij from its residues: sum_t r_t W_t reduced mod M and centred into (-M/2, M/2).  The sum is
+// formed in 32-bit limbs, sixteen at a time in 64-bit register accumulators (each < NM 2^48).
 __device__ int crt_assemble(const IntProduct &p, int64_t i, int64_t j, int64_t Mp, int64_t Np,
                             uint64_t *T) {
   const CrtTables &c = p.crt;
   const int nw = c.NMW + 1;
-  for (int k = 0; k < nw; ++k) T[k] = 0;
   const int64_t pl = Mp * Np, o = i * Np + j;
+  uint32_t rr[CRT_MAX_MODULI];
   for (int t = 0; t < c.NM; ++t) {
     const uint8_t *dg = p.digits + (int64_t)t * 3 * pl + o;
     int64_t P = (int64_t)dg[0] | ((int64_t)dg[pl] << 8) | ((int64_t)dg[2 * pl] << 16);
     P += (int64_t)p.carries[(int64_t)t * pl + o] * (int64_t)(1 << 24);
-    const uint32_t m = c.mods[t];
-    uint32_t r = P >= 0 ? barrett_mod((uint64_t)P, m, c.inv[t])
-                        : (m - barrett_mod((uint64_t)(-P), m, c.inv[t])) % m;
-    if (r == 0) continue;
-    const uint64_t *W = c.W + (int64_t)t * c.NMW;
-    u128 cy = 0;
-    for (int k = 0; k < c.NMW; ++k) {
-      cy += (u128)W[k] * r + T[k];
-      T[k] = (uint64_t)cy;
-      cy >>= 64;
+    const uint32_t m = c_mods[t];
+    rr[t] = P >= 0 ? barrett_mod((uint64_t)P, m, c_inv[t])
+                   : (m - barrett_mod((uint64_t)(-P), m, c_inv[t])) % m;
+  }
+  uint64_t carry = 0;
+  for (int l0 = 0; l0 < c.NW32P; l0 += 16) {
+    uint64_t acc[16];
+#pragma unroll
+    for (int q = 0; q < 16; ++q) acc[q] = 0;
+    for (int t = 0; t < c.NM; ++t) {
+      const uint32_t r = rr[t];
+      const uint4 *w4 = (const uint4 *)(c.W32 + (int64_t)t * c.NW32P + l0);
+#pragma unroll
+      for (int q4 = 0; q4 < 4; ++q4) {
+        const uint4 w = __ldg(w4 + q4);
+        acc[4 * q4 + 0] += (uint64_t)r * w.x;
+        acc[4 * q4 + 1] += (uint64_t)r * w.y;
+        acc[4 * q4 + 2] += (uint64_t)r * w.z;
+        acc[4 * q4 + 3] += (uint64_t)r * w.w;
+      }
     }
-    T[c.NMW] += (uint64_t)cy;
+#pragma unroll
+    for (int q = 0; q < 16; q += 2) {
+      const uint64_t v0 = acc[q] + carry;
+      const uint64_t lo = (uint32_t)v0;
+      const uint64_t v1 = acc[q + 1] + (v0 >> 32);
+      const int k = (l0 + q) >> 1;
+      if (k < nw) T[k] = lo | ((uint64_t)(uint32_t)v1 << 32);
+      carry = v1 >> 32;
+    }
   }
   // q ~ floor(T / M) (< NM 2^16) from the leading limbs; then correct
   const int n = c.NMW;
@@ -458,11 +481,11 @@ __device__ __forceinline__ int assemble(const IntProduct &p, int64_t i, int64_t 
 
 // Residues of the scaled integers for the multimodular engine: X = (-1)^neg L 2^sh (as in the
 // digit split), r_t = X mod m_t in balanced form, split into two balanced bytes r_t = 256 h + l,
-// written to planes [2t] (l) and [2t + 1] (h) of [2 NM][rows][Kp].
+// written to planes [2t] (l) and [2t + 1] (h) of [2 NM][rows][Kp].  NCH (a bound on the number of
+// 16-bit chunks of |X|) is a template argument so that the chunks stay in registers.
+template <int NCH>
 __global__ void residue_split_kernel(const BallsView X, bool is_b, int64_t rows, int64_t k0,
-                                     int64_t K, int64_t Kp, int64_t ld, const int64_t *bot,
-                                     const int64_t *top, const uint32_t *mods, const uint64_t *inv,
-                                     const uint32_t *pow16, int NM, int NCHP,
+                                     int64_t K, int64_t Kp, int64_t ld, const int64_t *bot, int NM,
                                      __nv_bfloat16 *out) {
   const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= rows * Kp) return;
@@ -483,15 +506,14 @@ __global__ void residue_split_kernel(const BallsView X, bool is_b, int64_t rows,
     for (int t = 0; t < 2 * NM; ++t) o[(int64_t)t * plane] = z;
     return;
   }
-  // 16-bit chunks of |X| = L 2^sh
+  // 16-bit chunks of |X| = L 2^sh (chunks past NCH are zero by the choice of NCH)
   uint64_t L[BL_MAX_NL];
   const int nl = X.nlimbs;
   for (int q = 0; q < nl; ++q) L[q] = __ldg(X.limbs + (int64_t)q * X.stride + e);
   const int64_t sh = ex - 64LL * nl - bot[r];
-  int nch = (int)((top[r] - bot[r] + 15) / 16) + 1;
-  if (nch > NCHP) nch = NCHP;
-  uint32_t ch[CRT_MAX_CHUNKS];
-  for (int c = 0; c < nch; ++c) {
+  uint32_t ch[NCH];
+#pragma unroll
+  for (int c = 0; c < NCH; ++c) {
     const int64_t pos = 16LL * c - sh;
     uint32_t v = 0;
     if (pos > -16 && pos < 64LL * nl) {
@@ -507,11 +529,12 @@ __global__ void residue_split_kernel(const BallsView X, bool is_b, int64_t rows,
     ch[c] = v;
   }
   for (int t = 0; t < NM; ++t) {
-    const uint32_t *pw = pow16 + (int64_t)t * NCHP;
+    const uint16_t *pw = c_pow16 + t * CRT_MAX_CHUNKS;
     uint64_t acc = 0;
-    for (int c = 0; c < nch; ++c) acc += (uint64_t)ch[c] * __ldg(pw + c);
-    const uint32_t m = __ldg(mods + t);
-    int32_t res = (int32_t)barrett_mod(acc, m, __ldg(inv + t));
+#pragma unroll
+    for (int c = 0; c < NCH; ++c) acc += (uint64_t)ch[c] * (uint32_t)pw[c];
+    const uint32_t m = c_mods[t];
+    int32_t res = (int32_t)barrett_mod(acc, m, c_inv[t]);
     if (res > (int32_t)(m >> 1)) res -= (int32_t)m;
     if (neg) res = -res;
     const int32_t lo = ((res + 128) & 255) - 128;
@@ -519,6 +542,41 @@ __global__ void residue_split_kernel(const BallsView X, bool is_b, int64_t rows,
     o[(int64_t)(2 * t) * plane] = __int2bfloat16_rn(lo);
     o[(int64_t)(2 * t + 1) * plane] = __int2bfloat16_rn(hi);
   }
+}
+
+static const int kChunkClasses[] = {12, 20, 28, 40, 56, 72, CRT_MAX_CHUNKS};
+
+static void launch_residues(int nch, unsigned grid, cudaStream_t s, const BallsView &X, bool is_b,
+                            int64_t rows, int64_t k0, int64_t K, int64_t Kp, int64_t ld,
+                            const int64_t *bot, int NM, __nv_bfloat16 *out) {
+#define ARB_RES(NCH_)                                                                      \
+  residue_split_kernel<NCH_><<<grid, 128, 0, s>>>(X, is_b, rows, k0, K, Kp, ld, bot, NM, out)
+  if (nch <= 12) ARB_RES(12);
+  else if (nch <= 20) ARB_RES(20);
+  else if (nch <= 28) ARB_RES(28);
+  else if (nch <= 40) ARB_RES(40);
+  else if (nch <= 56) ARB_RES(56);
+  else if (nch <= 72) ARB_RES(72);
+  else ARB_RES(CRT_MAX_CHUNKS);
+#undef ARB_RES
+}
+
+// Load the per-modulus constants into this device's constant memory (once per device).
+static arbgpu_status ensure_crt_constants(int device) {
+  static bool done[256] = {};
+  static std::mutex mu;
+  std::lock_guard<std::mutex> lock(mu);
+  if (done[device & 255]) return ARBGPU_OK;
+  const CrtPlan *full = crt_plan(CRT_MAX_MODULI);
+  if (!full) return ARBGPU_ERR_CUDA;
+  std::vector<uint16_t> pw((size_t)CRT_MAX_MODULI * CRT_MAX_CHUNKS);
+  for (size_t q = 0; q < pw.size(); ++q) pw[q] = (uint16_t)full->pow16[q];
+  if (cudaMemcpyToSymbol(c_mods, full->mods.data(), 4 * CRT_MAX_MODULI) != cudaSuccess ||
+      cudaMemcpyToSymbol(c_inv, full->inv.data(), 8 * CRT_MAX_MODULI) != cudaSuccess ||
+      cudaMemcpyToSymbol(c_pow16, pw.data(), 2 * pw.size()) != cudaSuccess)
+    return ARBGPU_ERR_CUDA;
+  done[device & 255] = true;
+  return ARBGPU_OK;
 }
 
 struct RoundArgs {
@@ -1017,7 +1075,7 @@ static BlockWs block_ws(arbgpu_ctx *ctx, int64_t M, int64_t K, int64_t N, int pr
   w.cmods = take(4 * (size_t)w.NMmax);
   w.cinv = take(8 * (size_t)w.NMmax);
   w.cpow = take(4 * (size_t)w.NMmax * CRT_MAX_CHUNKS);
-  w.cW = take(8 * (size_t)w.NMmax * w.NMWmax);
+  w.cW = take(4 * (size_t)w.NMmax * ((2 * w.NMWmax + 2 + 15) / 16 * 16));
   w.cM = take(8 * (size_t)w.NMWmax);
   w.chalf = take(8 * (size_t)w.NMWmax);
   w.total = off;
@@ -1098,18 +1156,11 @@ static arbgpu_status run_block(arbgpu_ctx *ctx, const BlockWs &w, uint8_t *ws, c
   if (cudaGetLastError() != cudaSuccess) return ARBGPU_ERR_CUDA;
   if (plan) {
     // ---- multimodular: residues, NM batched residue products, CRT in the consumer
-    CrtTables ct{(const uint32_t *)(ws + w.cmods), (const uint64_t *)(ws + w.cinv),
-                 (const uint32_t *)(ws + w.cpow),  (const uint64_t *)(ws + w.cW),
-                 (const uint64_t *)(ws + w.cM),    (const uint64_t *)(ws + w.chalf),
-                 plan->NM, plan->NMW, plan->NCHP};
-    if (cudaMemcpyAsync(ws + w.cmods, plan->mods.data(), 4 * plan->mods.size(),
+    if (ensure_crt_constants(ctx->device) != ARBGPU_OK) return ARBGPU_ERR_CUDA;
+    CrtTables ct{(const uint32_t *)(ws + w.cW), (const uint64_t *)(ws + w.cM),
+                 (const uint64_t *)(ws + w.chalf), plan->NM, plan->NMW, plan->NW32P};
+    if (cudaMemcpyAsync(ws + w.cW, plan->W32.data(), 4 * plan->W32.size(),
                         cudaMemcpyHostToDevice, s) != cudaSuccess ||
-        cudaMemcpyAsync(ws + w.cinv, plan->inv.data(), 8 * plan->inv.size(),
-                        cudaMemcpyHostToDevice, s) != cudaSuccess ||
-        cudaMemcpyAsync(ws + w.cpow, plan->pow16.data(), 4 * plan->pow16.size(),
-                        cudaMemcpyHostToDevice, s) != cudaSuccess ||
-        cudaMemcpyAsync(ws + w.cW, plan->W.data(), 8 * plan->W.size(), cudaMemcpyHostToDevice,
-                        s) != cudaSuccess ||
         cudaMemcpyAsync(ws + w.cM, plan->M.data(), 8 * plan->M.size(), cudaMemcpyHostToDevice,
                         s) != cudaSuccess ||
         cudaMemcpyAsync(ws + w.chalf, plan->halfM.data(), 8 * plan->halfM.size(),
@@ -1119,16 +1170,14 @@ static arbgpu_status run_block(arbgpu_ctx *ctx, const BlockWs &w, uint8_t *ws, c
     {
       const int64_t n = M * Kp;
       LaunchScope sc(ctx, s, "residues_a", n);
-      residue_split_kernel<<<(unsigned)((n + 127) / 128), 128, 0, s>>>(
-          Av, false, M, k0, Kb, Kp, lda, ln.rbot, ln.rtop, ct.mods, ct.inv, ct.pow16, NM,
-          plan->NCHP, resA);
+      launch_residues((int)((hA + 2 + 15) / 16) + 1, (unsigned)((n + 127) / 128), s, Av, false,
+                      M, k0, Kb, Kp, lda, ln.rbot, NM, resA);
     }
     {
       const int64_t n = N * Kp;
       LaunchScope sc(ctx, s, "residues_b", n);
-      residue_split_kernel<<<(unsigned)((n + 127) / 128), 128, 0, s>>>(
-          Bv, true, N, k0, Kb, Kp, ldb, ln.cbot, ln.ctop, ct.mods, ct.inv, ct.pow16, NM,
-          plan->NCHP, resB);
+      launch_residues((int)((hB + 2 + 15) / 16) + 1, (unsigned)((n + 127) / 128), s, Bv, true,
+                      N, k0, Kb, Kp, ldb, ln.cbot, NM, resB);
     }
     if (cudaGetLastError() != cudaSuccess) return ARBGPU_ERR_CUDA;
     DigitGemmArgs g{resA, resB, (int)M, (int)N, Kp, 2, 2, 1, ws + w.cdig,

@@ -97,6 +97,14 @@ std::unique_ptr<CrtPlan> build_plan(int NM) {
     mul_small(Q, inv_mod((uint32_t)qmod, m));
     for (int k = 0; k < P->NMW && k < (int)Q.size(); ++k) P->W[(size_t)t * P->NMW + k] = Q[k];
   }
+  P->NW32P = (2 * P->NMW + 2 + 15) / 16 * 16;
+  P->W32.assign((size_t)NM * P->NW32P, 0);
+  for (int t = 0; t < NM; ++t)
+    for (int k = 0; k < P->NMW; ++k) {
+      const uint64_t v = P->W[(size_t)t * P->NMW + k];
+      P->W32[(size_t)t * P->NW32P + 2 * k] = (uint32_t)v;
+      P->W32[(size_t)t * P->NW32P + 2 * k + 1] = (uint32_t)(v >> 32);
+    }
   P->NCHP = CRT_MAX_CHUNKS;
   P->pow16.resize((size_t)NM * P->NCHP);
   for (int t = 0; t < NM; ++t) {
@@ -122,6 +130,7 @@ int crt_moduli_for_bits(int bits) {
 }
 
 const CrtPlan *crt_plan(int NM) {
+  if (NM < 1 || NM > CRT_MAX_MODULI) return nullptr;
   std::lock_guard<std::mutex> lock(g_mu);
   auto it = g_plans.find(NM);
   if (it != g_plans.end()) return it->second.get();

@@ -120,12 +120,14 @@ arbgpu_status launch_grouped_dot(arbgpu_ctx *ctx, const GroupItem *dev_items,
 
 // Multimodular engine (crt.cu): moduli = the NM largest primes below 2^16.
 constexpr int CRT_MAX_CHUNKS = 100;  // 16-bit chunks of a scaled integer (1600 bits)
+constexpr int CRT_MAX_MODULI = 256;
 struct CrtPlan {
-  int NM, NMW, NCHP;              // moduli, limbs of M, columns of pow16
+  int NM, NMW, NCHP, NW32P;       // moduli, limbs of M, columns of pow16, columns of W32
   std::vector<uint32_t> mods;     // m_t
   std::vector<uint64_t> inv;      // floor((2^64 - 1) / m_t)
   std::vector<uint32_t> pow16;    // [NM][NCHP]: 2^(16c) mod m_t
   std::vector<uint64_t> W;        // [NM][NMW]: (M / m_t) * ((M / m_t)^-1 mod m_t)
+  std::vector<uint32_t> W32;      // [NM][NW32P]: W in 32-bit limbs, zero padded
   std::vector<uint64_t> M, halfM; // M and (M - 1) / 2
 };
 int crt_moduli_for_bits(int bits);
