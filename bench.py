@@ -116,6 +116,54 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sms)}
 
 
+# --------------------------------------------------------------------------- rooflines
+
+IMAD_PER_CLK_PER_SM = 64  # 32-bit integer multiply(-add) issue rate per SM per clock
+SMS = 152
+
+
+def kernel_summary(recs, step_ms_total):
+    per = {}
+    for name, kms, units in recs:
+        d = per.setdefault(name, [0.0, 0, 0])
+        d[0] += kms
+        d[1] += 1
+        d[2] += units
+    return {k: {"launches": v[1], "ms_total": round(v[0], 4),
+                "share": round(v[0] / step_ms_total, 4) if step_ms_total else None,
+                "units": v[2]} for k, v in per.items()}
+
+
+def roofline_of(name, k, peaks, sm_mhz, limb_n=None):
+    """Roofline entry of one kernel from its trace totals (ms_total, launches, units)."""
+    avg_s = k["ms_total"] / k["launches"] * 1e-3
+    units = k["units"] / k["launches"]
+    alu_peak = SMS * IMAD_PER_CLK_PER_SM * sm_mhz * 1e6 / 1e12
+    if name in ("crt_gemm", "digit_gemm", "digit_gemm_mid", "digit_gemm_rad"):
+        achieved = 2.0 * units / avg_s / 1e12
+        peak = peaks.get("bf16_tflops", 1900.0)
+        return {"bound": "tensor", "kernel": name, "achieved": achieved, "peak": peak,
+                "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                "note": "exact BF16 digit products (1 digit MAC = 2 flops) vs the measured "
+                        "dense BF16 burst peak (no INT8 tcgen05 on sm_103a)"}
+    if name == "dot_kernel" and limb_n:
+        mults = 4 * limb_n * limb_n * units
+        achieved = mults / avg_s / 1e12
+        return {"bound": "alu", "kernel": name, "achieved": achieved, "peak": alu_peak,
+                "unit": "T int32-mul/s", "frac": achieved / alu_peak, "traffic": None,
+                "peak_source": f"derived: {SMS} SMs x {IMAD_PER_CLK_PER_SM} IMAD/clk x "
+                               f"{sm_mhz:.0f} MHz"}
+    if name in ("block_round", "residues_a", "residues_b"):
+        achieved = units / avg_s / 1e12
+        return {"bound": "alu", "kernel": name, "achieved": achieved, "peak": alu_peak,
+                "unit": "T int32-mul/s", "frac": achieved / alu_peak, "traffic": None,
+                "peak_source": f"derived: {SMS} SMs x {IMAD_PER_CLK_PER_SM} IMAD/clk x "
+                               f"{sm_mhz:.0f} MHz",
+                "work": "CRT sums (block_round) / residue chunks (residues): 32-bit "
+                        "multiply-adds per launch"}
+    return {"kernel": name, "ms_avg": avg_s * 1e3}
+
+
 # --------------------------------------------------------------------------- oracle arm
 
 def oracle_sample(case, prec, entries, seconds):
@@ -169,6 +217,183 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+# --------------------------------------------------------------------------- other workloads
+
+def run_workload(args):
+    """One JSON line for one of the non-headline workloads (single GPU)."""
+    import numpy as np
+    import torch
+
+    import paper_1901_04289_gb300 as arb
+    from oracle import exact as X
+    from synth import SEED_BASE
+    from synth.workloads import (batched_dots, complex_matmul_laplace, dot_matmul_n32_p128,
+                                 grouped_matmuls)
+    from tests.gpu_util import batch_tensors
+
+    torch.cuda.set_device(0)
+    ctx = arb.default_context(0)
+    peaks = load_peaks()
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    wl = args.workload
+    cpu_fn = None
+    if wl == "n32dots":
+        case = dot_matmul_n32_p128()
+        A, B = arb.Balls.from_raw(case.A[0]), arb.Balls.from_raw(case.B[0])
+        C = arb.Balls.empty(32 * 32, 2)
+
+        def step():
+            arb.mat_mul(C, A, B, 32, 32, 32, 128, alg=arb.ALG_DOT, ctx=ctx)
+        macs, prec, name = 32 ** 3, 128, "real ball matmul N=32 p=128 by dots (exact balls)"
+        inbytes, outbytes = A.nbytes() + B.nbytes(), C.nbytes()
+
+        def cpu_fn(limit):
+            return _oracle_entries(lambda i, j: X.matmul_entry_terms(case.A[0], case.B[0], 32,
+                                                                      32, i, j), 32, 32, 32,
+                                   128, limit)
+    elif wl == "dots":
+        bt = batched_dots()
+        x, y = arb.Balls.from_raw(bt.x), arb.Balls.from_raw(bt.y)
+        res = arb.Balls.empty(len(bt.length), 3)
+        t = batch_tensors(bt)
+        pmax, lmax = int(bt.prec.max()), int(bt.length.max())
+
+        def step():
+            arb.dot(res, x, y, t["xoff"], t["xstep"], t["yoff"], t["ystep"], t["length"],
+                    t["prec"], prec_max=pmax, len_max=lmax, ctx=ctx)
+        macs, prec = int(bt.length.sum()), 192
+        name = bt.name
+        inbytes, outbytes = x.nbytes() + y.nbytes(), res.nbytes()
+
+        def cpu_fn(limit):
+            rng = np.random.default_rng(0)
+            done = terms = 0
+            t0 = time.perf_counter()
+            while time.perf_counter() - t0 < limit:
+                b = int(rng.integers(len(bt.length)))
+                idx = range(int(bt.xoff[b]), int(bt.xoff[b] + bt.length[b]))
+                X.result_exact(X.real_dot_terms(bt.x, idx, bt.y, idx), int(bt.prec[b]), 3)
+                done += 1
+                terms += int(bt.length[b])
+            dt = time.perf_counter() - t0
+            return terms / dt, f"{done} dots ({terms} terms) in {dt:.1f} s", dt
+    elif wl.startswith("complex2048"):
+        case = complex_matmul_laplace(structured=(wl == "complex2048"))
+        n = case.N
+        A = [arb.Balls.from_raw(a) for a in case.A]
+        B = [arb.Balls.from_raw(b) for b in case.B]
+        C = [arb.Balls.empty(n * n, 2), arb.Balls.empty(n * n, 2)]
+        need = arb.mat_mul_workspace_size(n, n, n, 128, 2, 2, True, arb.ALG_AUTO)
+        ws = torch.empty(max(need, 1), dtype=torch.uint8, device="cuda")
+
+        def step():
+            arb.mat_mul(C, A, B, n, n, n, 128, workspace=ws, ctx=ctx)
+        macs, prec, name = n ** 3, 128, case.name
+        inbytes = sum(b.nbytes() for b in A + B)
+        outbytes = sum(c.nbytes() for c in C)
+
+        def cpu_fn(limit):
+            rng = np.random.default_rng(0)
+            done = 0
+            t0 = time.perf_counter()
+            while time.perf_counter() - t0 < limit:
+                i, j = int(rng.integers(n)), int(rng.integers(n))
+                re, im = X.complex_dot_terms(case.A, [i * n + k for k in range(n)], case.B,
+                                             [k * n + j for k in range(n)])
+                X.result_exact(re, 128, 2)
+                X.result_exact(im, 128, 2)
+                done += 1
+            dt = time.perf_counter() - t0
+            return done * n / dt, f"{done} complex entries x {n} terms in {dt:.1f} s", dt
+    else:  # grouped
+        cases = grouped_matmuls()
+        items = []
+        inbytes = outbytes = 0
+        for c in cases:
+            A, B = arb.Balls.from_raw(c.A[0]), arb.Balls.from_raw(c.B[0])
+            Cc = arb.Balls.empty(c.N * c.N, (c.prec + 63) // 64)
+            items.append(dict(C=Cc, A=A, B=B, M=c.M, K=c.K, N=c.N, prec=c.prec))
+            inbytes += A.nbytes() + B.nbytes()
+            outbytes += Cc.nbytes()
+
+        def step():
+            arb.mat_mul_batched(items, ctx=ctx)
+        macs = sum(c.M * c.K * c.N for c in cases)
+        prec = 1024
+        name = ("grouped batch of 256 real ball matmuls, N U[16,512], p in {64..1024}, "
+                "exponents U[-50,50], radii 2^-(p-8)")
+
+        def cpu_fn(limit):
+            rng = np.random.default_rng(0)
+            done = terms = 0
+            t0 = time.perf_counter()
+            while time.perf_counter() - t0 < limit:
+                c = cases[int(rng.integers(len(cases)))]
+                i, j = int(rng.integers(c.N)), int(rng.integers(c.N))
+                X.result_exact(X.matmul_entry_terms(c.A[0], c.B[0], c.K, c.N, i, j), c.prec,
+                               (c.prec + 63) // 64)
+                done += 1
+                terms += c.K
+            dt = time.perf_counter() - t0
+            return terms / dt, f"{done} entries of random items ({terms} terms) in {dt:.1f} s", dt
+    for _ in range(args.warmup):
+        step()
+    ctx.check()
+    stream = torch.cuda.current_stream()
+    sampler = ClockSampler(0)
+    sampler.start()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(args.steps)]
+    torch.cuda.synchronize()
+    l0 = ctx.launch_count()
+    ctx.trace(True)
+    for k in range(args.steps):
+        flush.zero_()
+        evs[k][0].record(stream)
+        step()
+        evs[k][1].record(stream)
+    torch.cuda.synchronize()
+    launches = ctx.launch_count() - l0
+    recs = ctx.trace_read()
+    ctx.trace(False)
+    clocks = sampler.stop()
+    ctx.check()
+    ms = sum(a.elapsed_time(b) for a, b in evs)
+    value = macs * args.steps / (ms * 1e-3) / 1e9
+    kernels = kernel_summary(recs, ms)
+    sm_mhz = (clocks or {}).get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
+    roofline = None
+    if kernels:
+        dom = max(kernels.items(), key=lambda kv: kv[1]["ms_total"])
+        roofline = roofline_of(dom[0], dom[1], peaks, sm_mhz, limb_n=(prec + 63) // 64)
+        roofline["share_of_step"] = dom[1]["share"]
+    r, sample, _dt = cpu_fn(args.cpu_seconds)
+    line = {"metric": "ball multiply-adds per second (complex MACs for complex)",
+            "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "int64 limbs / exact integer products",
+            "data": "synthetic", "config": {"workload": name, "l2": "flushed before every step"},
+            "gpu_launches": launches, "roofline": roofline, "kernels": kernels,
+            "cpu_baseline": {"value": r / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": sample},
+            "io_bytes": {"in": inbytes, "out": outbytes}, "clocks": clocks}
+    print(json.dumps(line), flush=True)
+
+
+def _oracle_entries(terms_of, M, K, N, prec, limit):
+    import numpy as np
+    from oracle import exact as X
+    rng = np.random.default_rng(0)
+    done = 0
+    t0 = time.perf_counter()
+    while time.perf_counter() - t0 < limit:
+        i, j = int(rng.integers(M)), int(rng.integers(N))
+        X.result_exact(terms_of(i, j), prec, (prec + 63) // 64)
+        done += 1
+    dt = time.perf_counter() - t0
+    return done * K / dt, f"{done} entries x {K} terms in {dt:.1f} s", dt
+
+
 # --------------------------------------------------------------------------- GPU arm
 
 def main():
@@ -183,9 +408,17 @@ def main():
     ap.add_argument("--no-compare", action="store_true", help="skip the p=128 / dot-path lines")
     ap.add_argument("--ref-entries", type=int, default=48)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--workload", default="n512",
+                    choices=["n512", "n32dots", "dots", "complex2048", "complex2048_literal",
+                             "grouped"],
+                    help="n512 (default): the headline; the others are the remaining synthetic "
+                         "workloads, one JSON line each")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
+        return
+    if args.workload != "n512":
+        run_workload(args)
         return
 
     import torch
@@ -279,33 +512,21 @@ def main():
     e2e_ms, _, _, h2d, d2h = timed(case, prec, alg, args.steps, 2, e2e=True)
     e2e_value = macs * args.steps / (e2e_ms * 1e-3) / 1e9
 
-    # roofline of the dominant kernel, from the library's per-launch events
-    per = {}
-    for name, kms, units in recs:
-        d = per.setdefault(name, [0.0, 0, 0])
-        d[0] += kms
-        d[1] += 1
-        d[2] += units
-    kernels = {k: {"launches": v[1], "ms_total": round(v[0], 4),
-                   "share": round(v[0] / ms, 4) if ms else None} for k, v in per.items()}
-    dom = max(per.items(), key=lambda kv: kv[1][0]) if per else None
+    # roofline of the dominant kernel (and of the tensor-core kernel), from the library's
+    # per-launch events
+    kernels = kernel_summary(recs, ms)
+    sm_mhz = (clocks or {}).get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
     roofline = None
-    if dom:
-        name, (kms, cnt, units) = dom
-        avg_s = kms / cnt * 1e-3
-        sm_mhz = (clocks or {}).get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
-        if name == "dot_kernel":
-            n_l = (prec + 63) // 64
-            # 4 32x32-bit multiplies per 64x64-bit limb product, n_l^2 limb products per MAC
-            mults = 4 * n_l * n_l * units / cnt
-            peak = 152 * 64 * sm_mhz * 1e6 / 1e12  # IMAD issue: 64 / clk / SM, Tmul/s
-            achieved = mults / avg_s / 1e12
-            roofline = {"bound": "alu", "kernel": name, "achieved": achieved, "peak": peak,
-                        "unit": "T int32-mul/s", "frac": achieved / peak, "traffic": None,
-                        "peak_source": f"derived: 152 SMs x 64 IMAD/clk x {sm_mhz:.0f} MHz"}
-        else:
-            roofline = {"kernel": name, "ms_avg": kms / cnt}
-        roofline["share_of_step"] = kms / ms if ms else None
+    tensor = None
+    if kernels:
+        dom = max(kernels.items(), key=lambda kv: kv[1]["ms_total"])
+        roofline = roofline_of(dom[0], dom[1], peaks, sm_mhz, limb_n=(prec + 63) // 64)
+        roofline["share_of_step"] = dom[1]["share"]
+        for tn in ("crt_gemm", "digit_gemm_mid"):
+            if tn in kernels:
+                tensor = roofline_of(tn, kernels[tn], peaks, sm_mhz)
+                tensor["share_of_step"] = kernels[tn]["share"]
+                break
 
     compare = {}
     if not args.no_compare and args.n == N_DEFAULT:
@@ -336,7 +557,8 @@ def main():
                            "parallelism": f"replicas x{world}"},
                 "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
                         "d2h_bytes_per_step": d2h},
-                "gpu_launches": launches, "roofline": roofline, "kernels": kernels,
+                "gpu_launches": launches, "roofline": roofline, "tensor_core": tensor,
+                "kernels": kernels,
                 "cpu_baseline": cpu,
                 "clocks": clocks, "compare": compare, "peaks_source": peaks["_source"]}
         print(json.dumps(line), flush=True)

@@ -1169,13 +1169,13 @@ static arbgpu_status run_block(arbgpu_ctx *ctx, const BlockWs &w, uint8_t *ws, c
     __nv_bfloat16 *resA = (__nv_bfloat16 *)(ws + w.resA), *resB = (__nv_bfloat16 *)(ws + w.resB);
     {
       const int64_t n = M * Kp;
-      LaunchScope sc(ctx, s, "residues_a", n);
+      LaunchScope sc(ctx, s, "residues_a", n * NM * ((hA + 2 + 15) / 16 + 1));
       launch_residues((int)((hA + 2 + 15) / 16) + 1, (unsigned)((n + 127) / 128), s, Av, false,
                       M, k0, Kb, Kp, lda, ln.rbot, NM, resA);
     }
     {
       const int64_t n = N * Kp;
-      LaunchScope sc(ctx, s, "residues_b", n);
+      LaunchScope sc(ctx, s, "residues_b", n * NM * ((hB + 2 + 15) / 16 + 1));
       launch_residues((int)((hB + 2 + 15) / 16) + 1, (unsigned)((n + 127) / 128), s, Bv, true,
                       N, k0, Kb, Kp, ldb, ln.cbot, NM, resB);
     }
@@ -1419,7 +1419,10 @@ arbgpu_status block_matmul(arbgpu_ctx *ctx, const arbgpu_balls *C, const arbgpu_
       ra.Np = w.Np;
       ra.prec = prec;
       {
-        LaunchScope sc(ctx, s, "block_round", M * N);
+        // work units: 32-bit multiply-adds of the CRT sums (multimodular), else entries
+      const int64_t units =
+          ra.mid.kind == 1 ? M * N * ra.mid.crt.NM * (int64_t)ra.mid.crt.NW32P : M * N;
+      LaunchScope sc(ctx, s, "block_round", units);
         block_round_kernel<<<(unsigned)((M * N + 127) / 128), 128, 0, s>>>(ra);
       }
       *used_block = true;
