@@ -482,82 +482,109 @@ __device__ __forceinline__ int assemble(const IntProduct &p, int64_t i, int64_t 
 // Residues of the scaled integers for the multimodular engine: X = (-1)^neg L 2^sh (as in the
 // digit split), r_t = X mod m_t in balanced form, split into two balanced bytes r_t = 256 h + l,
 // written to planes [2t] (l) and [2t + 1] (h) of [2 NM][rows][Kp].  NCH (a bound on the number of
-// 16-bit chunks of |X|) is a template argument so that the chunks stay in registers.
-template <int NCH>
-__global__ void residue_split_kernel(const BallsView X, bool is_b, int64_t rows, int64_t k0,
-                                     int64_t K, int64_t Kp, int64_t ld, const int64_t *bot, int NM,
-                                     __nv_bfloat16 *out) {
-  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= rows * Kp) return;
-  const int64_t r = idx / Kp, k = idx - (idx / Kp) * Kp;
-  const int64_t plane = rows * Kp;
-  __nv_bfloat16 *o = out + r * Kp + k;
-  const __nv_bfloat16 z = __int2bfloat16_rn(0);
-  bool nz = false, neg = false;
-  int64_t e = 0, ex = 0;
-  if (k < K) {
-    e = is_b ? ((k0 + k) * ld + r) : (r * ld + k0 + k);
-    const uint32_t fl = __ldg(X.flags + e);
-    nz = !(fl & (ARBGPU_FLAG_ZERO | SPECIAL_MASK));
-    neg = (fl & ARBGPU_FLAG_SIGN) != 0;
-    ex = __ldg(X.exp + e);
-  }
-  if (!nz) {
-    for (int t = 0; t < 2 * NM; ++t) o[(int64_t)t * plane] = z;
-    return;
-  }
-  // 16-bit chunks of |X| = L 2^sh (chunks past NCH are zero by the choice of NCH)
-  uint64_t L[BL_MAX_NL];
+// 16-bit chunks of |X|) is a template argument so that the chunks stay in registers; each thread
+// takes RE consecutive entries of one row, sharing the loads of the table 2^(16c) mod m_t.
+
+__device__ __forceinline__ void residue_chunks(const BallsView &X, int64_t e, int64_t sh,
+                                               uint32_t *ch, int nch) {
   const int nl = X.nlimbs;
-  for (int q = 0; q < nl; ++q) L[q] = __ldg(X.limbs + (int64_t)q * X.stride + e);
-  const int64_t sh = ex - 64LL * nl - bot[r];
-  uint32_t ch[NCH];
-#pragma unroll
-  for (int c = 0; c < NCH; ++c) {
+  for (int c = 0; c < nch; ++c) {
     const int64_t pos = 16LL * c - sh;
     uint32_t v = 0;
     if (pos > -16 && pos < 64LL * nl) {
       if (pos >= 0) {
         const int li = (int)(pos >> 6), bi = (int)(pos & 63);
-        uint64_t w = L[li] >> bi;
-        if (bi > 48 && li + 1 < nl) w |= L[li + 1] << (64 - bi);
+        uint64_t w = __ldg(X.limbs + (int64_t)li * X.stride + e) >> bi;
+        if (bi > 48 && li + 1 < nl) w |= __ldg(X.limbs + (int64_t)(li + 1) * X.stride + e) << (64 - bi);
         v = (uint32_t)(w & 0xFFFFu);
       } else {
-        v = (uint32_t)((L[0] << (-pos)) & 0xFFFFu);
+        v = (uint32_t)((__ldg(X.limbs + e) << (-pos)) & 0xFFFFu);
       }
     }
     ch[c] = v;
   }
+}
+
+template <int NCH, int RE>
+__global__ void residue_split_kernel(const BallsView X, bool is_b, int64_t rows, int64_t k0,
+                                     int64_t K, int64_t Kp, int64_t ld, const int64_t *bot, int NM,
+                                     __nv_bfloat16 *out) {
+  constexpr int RES_E = RE;
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;  // group of RES_E entries
+  const int64_t kq = Kp / RES_E;                                        // Kp is a multiple of 64
+  if (idx >= rows * kq) return;
+  const int64_t r = idx / kq, kb = (idx - (idx / kq) * kq) * RES_E;
+  const int64_t plane = rows * Kp;
+  __nv_bfloat16 *o = out + r * Kp + kb;
+  uint32_t ch[RES_E][NCH];
+  bool live[RES_E], neg[RES_E];
+  bool any = false;
+#pragma unroll
+  for (int u = 0; u < RES_E; ++u) {
+    const int64_t k = kb + u;
+    live[u] = false;
+    neg[u] = false;
+#pragma unroll
+    for (int c = 0; c < NCH; ++c) ch[u][c] = 0;
+    if (k < K) {
+      const int64_t e = is_b ? ((k0 + k) * ld + r) : (r * ld + k0 + k);
+      const uint32_t fl = __ldg(X.flags + e);
+      if (!(fl & (ARBGPU_FLAG_ZERO | SPECIAL_MASK))) {
+        live[u] = true;
+        neg[u] = (fl & ARBGPU_FLAG_SIGN) != 0;
+        const int64_t sh = __ldg(X.exp + e) - 64LL * X.nlimbs - bot[r];
+        residue_chunks(X, e, sh, ch[u], NCH);
+        any = true;
+      }
+    }
+  }
+  const __nv_bfloat16 z = __int2bfloat16_rn(0);
+  if (!any) {
+    for (int t = 0; t < 2 * NM; ++t)
+#pragma unroll
+      for (int u = 0; u < RES_E; ++u) o[(int64_t)t * plane + u] = z;
+    return;
+  }
   for (int t = 0; t < NM; ++t) {
     const uint16_t *pw = c_pow16 + t * CRT_MAX_CHUNKS;
-    uint64_t acc = 0;
+    uint64_t acc[RES_E];
 #pragma unroll
-    for (int c = 0; c < NCH; ++c) acc += (uint64_t)ch[c] * (uint32_t)pw[c];
+    for (int u = 0; u < RES_E; ++u) acc[u] = 0;
+#pragma unroll
+    for (int c = 0; c < NCH; ++c) {
+      const uint32_t w = pw[c];
+#pragma unroll
+      for (int u = 0; u < RES_E; ++u) acc[u] += (uint64_t)ch[u][c] * w;
+    }
     const uint32_t m = c_mods[t];
-    int32_t res = (int32_t)barrett_mod(acc, m, c_inv[t]);
-    if (res > (int32_t)(m >> 1)) res -= (int32_t)m;
-    if (neg) res = -res;
-    const int32_t lo = ((res + 128) & 255) - 128;
-    const int32_t hi = (res - lo) >> 8;
-    o[(int64_t)(2 * t) * plane] = __int2bfloat16_rn(lo);
-    o[(int64_t)(2 * t + 1) * plane] = __int2bfloat16_rn(hi);
+    const uint64_t iv = c_inv[t];
+#pragma unroll
+    for (int u = 0; u < RES_E; ++u) {
+      int32_t res = (int32_t)barrett_mod(acc[u], m, iv);
+      if (res > (int32_t)(m >> 1)) res -= (int32_t)m;
+      if (neg[u]) res = -res;
+      if (!live[u]) res = 0;
+      const int32_t lo = ((res + 128) & 255) - 128;
+      const int32_t hi = (res - lo) >> 8;
+      o[(int64_t)(2 * t) * plane + u] = __int2bfloat16_rn(lo);
+      o[(int64_t)(2 * t + 1) * plane + u] = __int2bfloat16_rn(hi);
+    }
   }
 }
 
-static const int kChunkClasses[] = {12, 20, 28, 40, 56, 72, CRT_MAX_CHUNKS};
-
-static void launch_residues(int nch, unsigned grid, cudaStream_t s, const BallsView &X, bool is_b,
+static void launch_residues(int nch, int64_t n, cudaStream_t s, const BallsView &X, bool is_b,
                             int64_t rows, int64_t k0, int64_t K, int64_t Kp, int64_t ld,
                             const int64_t *bot, int NM, __nv_bfloat16 *out) {
-#define ARB_RES(NCH_)                                                                      \
-  residue_split_kernel<NCH_><<<grid, 128, 0, s>>>(X, is_b, rows, k0, K, Kp, ld, bot, NM, out)
-  if (nch <= 12) ARB_RES(12);
-  else if (nch <= 20) ARB_RES(20);
-  else if (nch <= 28) ARB_RES(28);
-  else if (nch <= 40) ARB_RES(40);
-  else if (nch <= 56) ARB_RES(56);
-  else if (nch <= 72) ARB_RES(72);
-  else ARB_RES(CRT_MAX_CHUNKS);
+#define ARB_RES(NCH_, RE_)                                                                  \
+  residue_split_kernel<NCH_, RE_><<<(unsigned)((n / RE_ + 127) / 128), 128, 0, s>>>(         \
+      X, is_b, rows, k0, K, Kp, ld, bot, NM, out)
+  if (nch <= 12) ARB_RES(12, 4);
+  else if (nch <= 20) ARB_RES(20, 4);
+  else if (nch <= 28) ARB_RES(28, 2);
+  else if (nch <= 40) ARB_RES(40, 2);
+  else if (nch <= 56) ARB_RES(56, 1);
+  else if (nch <= 72) ARB_RES(72, 1);
+  else ARB_RES(CRT_MAX_CHUNKS, 1);
 #undef ARB_RES
 }
 
@@ -1106,12 +1133,23 @@ static int bit_length(int64_t v) {
 
 // The integer engine for a block: digits (S_A x S_B digit products) or multimodular (NM residue
 // products of 2 x 2 digits each, then the Chinese remainder theorem).  ARBGPU_ENGINE=digits|crt
-// forces one; otherwise the cheaper by digit-product count.
-static bool choose_crt(int SA, int SB, int NM) {
+// forces one; otherwise the cheaper by a cost model whose constants are the measured costs of the
+// kernels on GB300: a tensor-core digit multiply-add, a 32-bit multiply-add of the CRT epilogue
+// (per output entry), a 16-bit multiply-add of the residue kernel (per input entry), and a digit
+// byte of the digit epilogue (per output entry).
+static bool choose_crt(int SA, int SB, int NM, int64_t M, int64_t N, int64_t Kp, int64_t hA,
+                       int64_t hB) {
   const char *e = getenv("ARBGPU_ENGINE");
   if (e && !strcmp(e, "digits")) return false;
   if (e && !strcmp(e, "crt")) return true;
-  return 4 * NM + 16 < SA * SB;
+  const double t_mma = 2.6e-15, t_crt = 7e-13, t_res = 2.2e-13, t_dig = 4e-12;
+  const double MN = (double)M * (double)N;
+  const double nw32 = 2.0 * ((16.0 * NM + 63) / 64 + 1);
+  const double nch = (double)((hA > hB ? hA : hB) + 2) / 16 + 1;
+  const double digits = t_mma * SA * SB * (double)Kp * MN + t_dig * (SA + SB) * MN;
+  const double crt = t_mma * 4.0 * NM * (double)Kp * MN + t_crt * NM * nw32 * MN +
+                     t_res * NM * nch * (double)Kp * (double)(M + N);
+  return crt < digits;
 }
 
 // Split the block [k0, k0 + Kb) and run its products: T = (E A)(B F), and the radius products
@@ -1127,7 +1165,7 @@ static arbgpu_status run_block(arbgpu_ctx *ctx, const BlockWs &w, uint8_t *ws, c
   const int NM = crt_moduli_for_bits((int)((hA > 0 ? hA : 0) + (hB > 0 ? hB : 0) +
                                            bit_length(Kb) + 2));
   const CrtPlan *plan = nullptr;
-  if (choose_crt(SA, SB, NM) && NM <= w.NMmax) {
+  if (choose_crt(SA, SB, NM, M, N, Kp, hA, hB) && NM <= w.NMmax) {
     plan = crt_plan(NM);
     if (plan && plan->NMW + 1 > RD_MAXW) plan = nullptr;
   }
@@ -1170,13 +1208,13 @@ static arbgpu_status run_block(arbgpu_ctx *ctx, const BlockWs &w, uint8_t *ws, c
     {
       const int64_t n = M * Kp;
       LaunchScope sc(ctx, s, "residues_a", n * NM * ((hA + 2 + 15) / 16 + 1));
-      launch_residues((int)((hA + 2 + 15) / 16) + 1, (unsigned)((n + 127) / 128), s, Av, false,
+      launch_residues((int)((hA + 2 + 15) / 16) + 1, n, s, Av, false,
                       M, k0, Kb, Kp, lda, ln.rbot, NM, resA);
     }
     {
       const int64_t n = N * Kp;
       LaunchScope sc(ctx, s, "residues_b", n * NM * ((hB + 2 + 15) / 16 + 1));
-      launch_residues((int)((hB + 2 + 15) / 16) + 1, (unsigned)((n + 127) / 128), s, Bv, true,
+      launch_residues((int)((hB + 2 + 15) / 16) + 1, n, s, Bv, true,
                       N, k0, Kb, Kp, ldb, ln.cbot, NM, resB);
     }
     if (cudaGetLastError() != cudaSuccess) return ARBGPU_ERR_CUDA;
