@@ -578,10 +578,10 @@ static void launch_residues(int nch, int64_t n, cudaStream_t s, const BallsView 
 #define ARB_RES(NCH_, RE_)                                                                  \
   residue_split_kernel<NCH_, RE_><<<(unsigned)((n / RE_ + 127) / 128), 128, 0, s>>>(         \
       X, is_b, rows, k0, K, Kp, ld, bot, NM, out)
-  if (nch <= 12) ARB_RES(12, 4);
-  else if (nch <= 20) ARB_RES(20, 4);
-  else if (nch <= 28) ARB_RES(28, 2);
-  else if (nch <= 40) ARB_RES(40, 2);
+  if (nch <= 12) ARB_RES(12, 2);
+  else if (nch <= 20) ARB_RES(20, 1);
+  else if (nch <= 28) ARB_RES(28, 1);
+  else if (nch <= 40) ARB_RES(40, 1);
   else if (nch <= 56) ARB_RES(56, 1);
   else if (nch <= 72) ARB_RES(72, 1);
   else ARB_RES(CRT_MAX_CHUNKS, 1);

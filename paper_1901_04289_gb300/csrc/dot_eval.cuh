@@ -265,6 +265,7 @@ __device__ __forceinline__ void limbs_shift(const uint64_t *a, int n, int64_t sh
 template <int NS>
 __device__ void dot_finalise(const LaneAcc<NS> &acc, const DotSetup &su, int prec,
                              const BallsOut &out, int64_t oi, int lane) {
+  if (lane != 0) return;  // every lane holds the reduced sums; one finishes the dot
   uint64_t a[NS + 1];
   for (int k = 0; k < NS; ++k) a[k] = acc.s[k];
   a[NS] = 0;

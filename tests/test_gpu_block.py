@@ -252,7 +252,8 @@ def test_complex_block_uniform(arb):
     A2 = [random_balls(rng, n * n, 2, 128, -10, 10, rad_bits=120, rad_zero_frac=0.5) for _ in "ri"]
     B2 = [random_balls(rng, n * n, 2, 128, -10, 10, rad_bits=120, rad_zero_frac=0.5) for _ in "ri"]
     outs, names = run_cmm(arb, A2, B2, n, n, n, p, arb.ALG_BLOCK, trace=True)
-    assert names.count("accumulate") == 4 and "crt_gemm" in names
+    assert names.count("accumulate") == 4
+    assert "crt_gemm" in names or "digit_gemm_mid" in names
     rng2 = np.random.default_rng(4)
     check_complex(outs, A2, B2, n, n, n, p, [(int(a), int(b)) for a, b in
                                              zip(rng2.integers(0, n, 80), rng2.integers(0, n, 80))])
