@@ -322,8 +322,9 @@ def test_multimodular_p1024(arb):
     M, K, N, p = 48, 64, 40, 1024
     A = random_balls(rng, M * K, 16, 1024, -50, 50, rad_bits=1016, rad_zero_frac=0.5)
     B = random_balls(rng, K * N, 16, 1024, -50, 50, rad_bits=1016, rad_zero_frac=0.5)
-    out, names = run_mm(arb, A, B, M, K, N, p, arb.ALG_BLOCK, trace=True)
-    assert "crt_gemm" in names
     rng2 = np.random.default_rng(2)
-    check_entries(out, A, B, M, K, N, p, [(int(a), int(b)) for a, b in
-                                         zip(rng2.integers(0, M, 40), rng2.integers(0, N, 40))], 16)
+    sample = [(int(a), int(b)) for a, b in zip(rng2.integers(0, M, 40), rng2.integers(0, N, 40))]
+    for engine, kernel in (("crt", "crt_gemm"), ("digits", "digit_gemm_mid")):
+        (out,), names = _run_engine(arb, engine, A, B, M, K, N, p)
+        assert kernel in names
+        check_entries(out, A, B, M, K, N, p, sample, 16)
