@@ -134,7 +134,7 @@ def kernel_summary(recs, step_ms_total):
                 "units": v[2]} for k, v in per.items()}
 
 
-def roofline_of(name, k, peaks, sm_mhz, limb_n=None):
+def roofline_of(name, k, peaks, sm_mhz):
     """Roofline entry of one kernel from its trace totals (ms_total, launches, units)."""
     avg_s = k["ms_total"] / k["launches"] * 1e-3
     units = k["units"] / k["launches"]
@@ -146,13 +146,6 @@ def roofline_of(name, k, peaks, sm_mhz, limb_n=None):
                 "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
                 "note": "exact BF16 digit products (1 digit MAC = 2 flops) vs the measured "
                         "dense BF16 burst peak (no INT8 tcgen05 on sm_103a)"}
-    if name == "dot_kernel" and limb_n:
-        mults = 4 * limb_n * limb_n * units
-        achieved = mults / avg_s / 1e12
-        return {"bound": "alu", "kernel": name, "achieved": achieved, "peak": alu_peak,
-                "unit": "T int32-mul/s", "frac": achieved / alu_peak, "traffic": None,
-                "peak_source": f"derived: {SMS} SMs x {IMAD_PER_CLK_PER_SM} IMAD/clk x "
-                               f"{sm_mhz:.0f} MHz"}
     if name in ("block_round", "residues_a", "residues_b"):
         achieved = units / avg_s / 1e12
         return {"bound": "alu", "kernel": name, "achieved": achieved, "peak": alu_peak,
@@ -162,6 +155,49 @@ def roofline_of(name, k, peaks, sm_mhz, limb_n=None):
                 "work": "CRT sums (block_round) / residue chunks (residues): 32-bit "
                         "multiply-adds per launch"}
     return {"kernel": name, "ms_avg": avg_s * 1e3}
+
+
+def dot_work(terms_by_n, unique_bytes=None):
+    """Algorithmic work of a dot-path call: terms_by_n maps limbs read per factor (n) to the number
+    of terms.  mults = 4 n^2 32-bit multiplies per term (n^2 64x64->128-bit limb products);
+    bytes = every input byte the terms need, once: 2 (8n + 24) per term for independent dots, or
+    `unique_bytes` when entries are shared between dots (a matrix product)."""
+    terms = sum(terms_by_n.values())
+    mults = sum(4 * n * n * t for n, t in terms_by_n.items())
+    byts = unique_bytes if unique_bytes is not None else sum(
+        2 * (8 * n + 24) * t for n, t in terms_by_n.items())
+    return {"terms": terms, "mults": mults, "bytes": byts}
+
+
+def dot_roofline(kernels, work, calls, peaks, sm_mhz):
+    """Roofline of the dot path over the timed region: one setup launch and one launch per size
+    class each call.  The bound is whichever of HBM bytes or integer multiplies takes longer at
+    peak; `achieved` divides the work of one call by the device time of one call."""
+    t_eval = kernels.get("dot_eval", {}).get("ms_total", 0.0) * 1e-3 / calls
+    t_set = kernels.get("dot_setup", {}).get("ms_total", 0.0) * 1e-3 / calls
+    t_all = t_eval + t_set
+    if t_all <= 0:
+        return None
+    alu_peak = SMS * IMAD_PER_CLK_PER_SM * sm_mhz * 1e6 / 1e12
+    hbm_peak = peaks.get("hbm_gbs", 6800.0)
+    t_hbm = work["bytes"] / (hbm_peak * 1e9)
+    t_alu = work["mults"] / (alu_peak * 1e12)
+    base = {"kernel": "dot_setup + dot_eval", "ms_per_call": t_all * 1e3,
+            "eval_ms_per_call": t_eval * 1e3, "terms_per_call": work["terms"],
+            "traffic": None}
+    if t_hbm >= t_alu:
+        achieved = work["bytes"] / t_all / 1e9
+        base.update({"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                     "frac": achieved / hbm_peak, "bytes_per_call": work["bytes"],
+                     "peak_source": "measured copy bandwidth"})
+    else:
+        achieved = work["mults"] / t_eval / 1e12
+        base.update({"bound": "alu", "achieved": achieved, "peak": alu_peak,
+                     "unit": "T int32-mul/s", "frac": achieved / alu_peak,
+                     "mults_per_call": work["mults"],
+                     "peak_source": f"derived: {SMS} SMs x {IMAD_PER_CLK_PER_SM} IMAD/clk x "
+                                    f"{sm_mhz:.0f} MHz"})
+    return base
 
 
 # --------------------------------------------------------------------------- oracle arm
@@ -237,6 +273,7 @@ def run_workload(args):
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     wl = args.workload
     cpu_fn = None
+    work = None
     if wl == "n32dots":
         case = dot_matmul_n32_p128()
         A, B = arb.Balls.from_raw(case.A[0]), arb.Balls.from_raw(case.B[0])
@@ -246,6 +283,7 @@ def run_workload(args):
             arb.mat_mul(C, A, B, 32, 32, 32, 128, alg=arb.ALG_DOT, ctx=ctx)
         macs, prec, name = 32 ** 3, 128, "real ball matmul N=32 p=128 by dots (exact balls)"
         inbytes, outbytes = A.nbytes() + B.nbytes(), C.nbytes()
+        work = dot_work({2: macs}, unique_bytes=3 * 32 * 32 * (8 * 2 + 24))
 
         def cpu_fn(limit):
             return _oracle_entries(lambda i, j: X.matmul_entry_terms(case.A[0], case.B[0], 32,
@@ -264,6 +302,8 @@ def run_workload(args):
         macs, prec = int(bt.length.sum()), 192
         name = bt.name
         inbytes, outbytes = x.nbytes() + y.nbytes(), res.nbytes()
+        nd = (bt.prec.astype(np.int64) + 63) // 64
+        work = dot_work({int(n): int(bt.length[nd == n].sum()) for n in np.unique(nd)})
 
         def cpu_fn(limit):
             rng = np.random.default_rng(0)
@@ -365,8 +405,13 @@ def run_workload(args):
     roofline = None
     if kernels:
         dom = max(kernels.items(), key=lambda kv: kv[1]["ms_total"])
-        roofline = roofline_of(dom[0], dom[1], peaks, sm_mhz, limb_n=(prec + 63) // 64)
-        roofline["share_of_step"] = dom[1]["share"]
+        if dom[0] in ("dot_setup", "dot_eval") and work is not None:
+            roofline = dot_roofline(kernels, work, args.steps, peaks, sm_mhz)
+            roofline["share_of_step"] = round(sum(
+                kernels.get(k, {}).get("share", 0) or 0 for k in ("dot_setup", "dot_eval")), 4)
+        else:
+            roofline = roofline_of(dom[0], dom[1], peaks, sm_mhz)
+            roofline["share_of_step"] = dom[1]["share"]
     r, sample, _dt = cpu_fn(args.cpu_seconds)
     line = {"metric": "ball multiply-adds per second (complex MACs for complex)",
             "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
@@ -520,8 +565,16 @@ def main():
     tensor = None
     if kernels:
         dom = max(kernels.items(), key=lambda kv: kv[1]["ms_total"])
-        roofline = roofline_of(dom[0], dom[1], peaks, sm_mhz, limb_n=(prec + 63) // 64)
-        roofline["share_of_step"] = dom[1]["share"]
+        if dom[0] in ("dot_setup", "dot_eval"):
+            n = (prec + 63) // 64
+            ent = (case.M * case.K + case.K * case.N + case.M * case.N) * (8 * n + 24)
+            roofline = dot_roofline(kernels, dot_work({n: macs}, unique_bytes=ent), args.steps,
+                                    peaks, sm_mhz)
+            roofline["share_of_step"] = round(sum(
+                kernels.get(k, {}).get("share", 0) or 0 for k in ("dot_setup", "dot_eval")), 4)
+        else:
+            roofline = roofline_of(dom[0], dom[1], peaks, sm_mhz)
+            roofline["share_of_step"] = dom[1]["share"]
         for tn in ("crt_gemm", "digit_gemm_mid"):
             if tn in kernels:
                 tensor = roofline_of(tn, kernels[tn], peaks, sm_mhz)

@@ -19,37 +19,44 @@ struct BatchDotSrc {
   bool has_init;
   int prec_max;
   int64_t len_max;
+  int64_t ndots_host;
 
+  struct Cursor {
+    int64_t b, xo, xs, yo, ys, n;
+    int part;
+    bool sub;
+  };
   __device__ int64_t ndots() const { return cplx ? 2 * batch : batch; }
-  __device__ int64_t b_of(int64_t d) const { return cplx ? (d >> 1) : d; }
-  __device__ int part(int64_t d) const { return cplx ? (int)(d & 1) : 0; }
-  __device__ int64_t nterms(int64_t d) const {
-    const int64_t n = __ldg(len + b_of(d));
-    return cplx ? 2 * n : n;
+  __device__ Cursor cursor(int64_t d) const {
+    Cursor c;
+    c.b = cplx ? (d >> 1) : d;
+    c.part = cplx ? (int)(d & 1) : 0;
+    c.xo = __ldg(xoff + c.b);
+    c.xs = __ldg(xstep + c.b);
+    c.yo = __ldg(yoff + c.b);
+    c.ys = __ldg(ystep + c.b);
+    c.n = __ldg(len + c.b);
+    c.sub = subs ? (__ldg(subs + c.b) != 0) : false;
+    return c;
   }
-  __device__ int64_t len_of(int64_t d) const { return __ldg(len + b_of(d)); }
-  __device__ TermLoc term(int64_t d, int64_t t) const {
-    const int64_t b = b_of(d);
-    const bool sb = subs ? (__ldg(subs + b) != 0) : false;
-    if (!cplx) return TermLoc{0, __ldg(xoff + b) + t * __ldg(xstep + b), 0,
-                              __ldg(yoff + b) + t * __ldg(ystep + b), sb};
+  __device__ int64_t nterms(const Cursor &c) const { return cplx ? 2 * c.n : c.n; }
+  __device__ TermLoc term(const Cursor &c, int64_t t) const {
+    if (!cplx) return TermLoc{0, c.xo + t * c.xs, 0, c.yo + t * c.ys, c.sub};
     const int64_t i = t >> 1;
     const int w = (int)(t & 1);
-    const int64_t xi = __ldg(xoff + b) + i * __ldg(xstep + b);
-    const int64_t yi = __ldg(yoff + b) + i * __ldg(ystep + b);
-    if (part(d) == 0) return w == 0 ? TermLoc{0, xi, 0, yi, sb} : TermLoc{1, xi, 1, yi, !sb};
-    return w == 0 ? TermLoc{0, xi, 1, yi, sb} : TermLoc{1, xi, 0, yi, sb};
+    const int64_t xi = c.xo + i * c.xs, yi = c.yo + i * c.ys;
+    if (c.part == 0) return w == 0 ? TermLoc{0, xi, 0, yi, c.sub} : TermLoc{1, xi, 1, yi, !c.sub};
+    return w == 0 ? TermLoc{0, xi, 1, yi, c.sub} : TermLoc{1, xi, 0, yi, c.sub};
   }
-  __device__ const BallsView &xview(int a) const { return x[a]; }
-  __device__ const BallsView &yview(int a) const { return y[a]; }
-  __device__ bool has_initial(int64_t) const { return has_init; }
-  __device__ const BallsView &initial_view(int64_t d) const { return init[part(d)]; }
-  __device__ int64_t initial_index(int64_t d) const { return b_of(d); }
-  __device__ const BallsOut &out_view(int64_t d) const { return out[part(d)]; }
-  __device__ int64_t out_index(int64_t d) const { return b_of(d); }
-  __device__ int prec(int64_t d) const { return __ldg(precs + b_of(d)); }
+  __device__ const BallsView &xview(const Cursor &, int a) const { return x[a]; }
+  __device__ const BallsView &yview(const Cursor &, int a) const { return y[a]; }
+  __device__ bool has_initial() const { return has_init; }
+  __device__ const BallsView &initial_view(const Cursor &c) const { return init[c.part]; }
+  __device__ int64_t initial_index(const Cursor &c) const { return c.b; }
+  __device__ const BallsOut &out_view(const Cursor &c) const { return out[c.part]; }
+  __device__ int64_t out_index(const Cursor &c) const { return c.b; }
+  __device__ int prec(const Cursor &c) const { return __ldg(precs + c.b); }
   int64_t units() const { return ndots_host; }
-  int64_t ndots_host;
 };
 
 // Classical product: entry (i, j) is the dot of row i of A and column j of B.  Consecutive warps
@@ -63,32 +70,38 @@ struct MatDotSrc {
   int prec_max;
   int64_t len_max;
 
+  struct Cursor {
+    int64_t xrow, j, oi;
+    int part;
+  };
   __device__ int64_t ndots() const { return (cplx ? 2 : 1) * M * N; }
-  __device__ int part(int64_t d) const { return cplx ? (int)(d & 1) : 0; }
-  __device__ int64_t ent(int64_t d) const { return cplx ? (d >> 1) : d; }
-  __device__ int64_t nterms(int64_t) const { return cplx ? 2 * K : K; }
-  __device__ TermLoc term(int64_t d, int64_t t) const {
-    const int64_t e = ent(d);
-    const int64_t i = e / N, j = e - (e / N) * N;
-    if (!cplx) return TermLoc{0, i * lda + t, 0, t * ldb + j, false};
+  __device__ Cursor cursor(int64_t d) const {
+    Cursor c;
+    const int64_t e = cplx ? (d >> 1) : d;
+    c.part = cplx ? (int)(d & 1) : 0;
+    const int64_t i = e / N;
+    c.j = e - i * N;
+    c.xrow = i * lda;
+    c.oi = i * ldc + c.j;
+    return c;
+  }
+  __device__ int64_t nterms(const Cursor &) const { return cplx ? 2 * K : K; }
+  __device__ TermLoc term(const Cursor &c, int64_t t) const {
+    if (!cplx) return TermLoc{0, c.xrow + t, 0, t * ldb + c.j, false};
     const int64_t k = t >> 1;
     const int w = (int)(t & 1);
-    const int64_t xi = i * lda + k, yi = k * ldb + j;
-    if (part(d) == 0) return w == 0 ? TermLoc{0, xi, 0, yi, false} : TermLoc{1, xi, 1, yi, true};
+    const int64_t xi = c.xrow + k, yi = k * ldb + c.j;
+    if (c.part == 0) return w == 0 ? TermLoc{0, xi, 0, yi, false} : TermLoc{1, xi, 1, yi, true};
     return w == 0 ? TermLoc{0, xi, 1, yi, false} : TermLoc{1, xi, 0, yi, false};
   }
-  __device__ const BallsView &xview(int a) const { return A[a]; }
-  __device__ const BallsView &yview(int a) const { return B[a]; }
-  __device__ bool has_initial(int64_t) const { return false; }
-  __device__ const BallsView &initial_view(int64_t) const { return A[0]; }
-  __device__ int64_t initial_index(int64_t) const { return 0; }
-  __device__ const BallsOut &out_view(int64_t d) const { return C[part(d)]; }
-  __device__ int64_t out_index(int64_t d) const {
-    const int64_t e = ent(d);
-    const int64_t i = e / N, j = e - i * N;
-    return i * ldc + j;
-  }
-  __device__ int prec(int64_t) const { return prec_v; }
+  __device__ const BallsView &xview(const Cursor &, int a) const { return A[a]; }
+  __device__ const BallsView &yview(const Cursor &, int a) const { return B[a]; }
+  __device__ bool has_initial() const { return false; }
+  __device__ const BallsView &initial_view(const Cursor &) const { return A[0]; }
+  __device__ int64_t initial_index(const Cursor &) const { return 0; }
+  __device__ const BallsOut &out_view(const Cursor &c) const { return C[c.part]; }
+  __device__ int64_t out_index(const Cursor &c) const { return c.oi; }
+  __device__ int prec(const Cursor &) const { return prec_v; }
   int64_t units() const { return M * N * K; }
 };
 
@@ -104,34 +117,42 @@ struct BasecaseSrc {
   int prec_max;
   int64_t len_max;
 
+  struct Cursor {
+    int64_t d, xrow, j, oi;
+  };
   __device__ int64_t ndots() const { return M * N; }
-  __device__ int64_t nterms(int64_t) const { return nbk; }
-  __device__ TermLoc term(int64_t d, int64_t t) const {
-    const int64_t i = d / N, j = d - (d / N) * N;
+  __device__ Cursor cursor(int64_t d) const {
+    Cursor c;
+    const int64_t i = d / N;
+    c.d = d;
+    c.j = d - i * N;
+    c.xrow = i * lda;
+    c.oi = i * ldc + c.j;
+    return c;
+  }
+  __device__ int64_t nterms(const Cursor &) const { return nbk; }
+  __device__ TermLoc term(const Cursor &c, int64_t t) const {
     const int32_t e = __ldg(bk + t);
     const int64_t k = e >> 2;
     const int combo = e & 3;
     const int xa = (combo == 1 || combo == 3) ? 1 : 0;
     const int yb = (combo == 1 || combo == 2) ? 1 : 0;
-    return TermLoc{xa, i * lda + k, yb, k * ldb + j, combo == 1};
+    return TermLoc{xa, c.xrow + k, yb, k * ldb + c.j, combo == 1};
   }
-  __device__ const BallsView &xview(int a) const { return A[a]; }
-  __device__ const BallsView &yview(int b) const { return B[b]; }
-  __device__ bool has_initial(int64_t) const { return true; }
-  __device__ const BallsView &initial_view(int64_t) const { return init; }
-  __device__ int64_t initial_index(int64_t d) const { return d; }
-  __device__ const BallsOut &out_view(int64_t) const { return C; }
-  __device__ int64_t out_index(int64_t d) const {
-    const int64_t i = d / N, j = d - i * N;
-    return i * ldc + j;
-  }
-  __device__ int prec(int64_t) const { return prec_v; }
+  __device__ const BallsView &xview(const Cursor &, int a) const { return A[a]; }
+  __device__ const BallsView &yview(const Cursor &, int b) const { return B[b]; }
+  __device__ bool has_initial() const { return true; }
+  __device__ const BallsView &initial_view(const Cursor &) const { return init; }
+  __device__ int64_t initial_index(const Cursor &c) const { return c.d; }
+  __device__ const BallsOut &out_view(const Cursor &) const { return C; }
+  __device__ int64_t out_index(const Cursor &c) const { return c.oi; }
+  __device__ int prec(const Cursor &) const { return prec_v; }
   int64_t units() const { return M * N * nbk; }
 };
 
 // Grouped classical products: virtual dot d belongs to the item q with ends[q-1] <= d < ends[q]
 // (binary search over a device work list); inside the item it is entry (i, j) (and, for complex
-// items, its part).  View slot 4q + {0, 1, 2, 3} is A_re, A_im, B_re, B_im of item q.
+// items, its part).
 struct GroupedDotSrc {
   const GroupItem *items;
   const int64_t *ends;
@@ -140,6 +161,11 @@ struct GroupedDotSrc {
   int prec_max;
   int64_t len_max;
 
+  struct Cursor {
+    const GroupItem *it;
+    int64_t xrow, j, oi;
+    int part;
+  };
   __device__ int item(int64_t d) const {
     int lo = 0, hi = count - 1;
     while (lo < hi) {
@@ -149,49 +175,40 @@ struct GroupedDotSrc {
     }
     return lo;
   }
-  __device__ int64_t local(int64_t d, int q) const { return d - (q ? __ldg(ends + q - 1) : 0); }
   __device__ int64_t ndots() const { return total; }
-  __device__ int64_t nterms(int64_t d) const {
-    const GroupItem &D = items[item(d)];
-    return D.cplx ? 2 * D.K : D.K;
-  }
-  __device__ TermLoc term(int64_t d, int64_t t) const {
+  __device__ Cursor cursor(int64_t d) const {
+    Cursor c;
     const int q = item(d);
-    const GroupItem &D = items[q];
-    const int64_t e0 = local(d, q);
-    const int part = D.cplx ? (int)(e0 & 1) : 0;
-    const int64_t e = D.cplx ? (e0 >> 1) : e0;
-    const int64_t i = e / D.N, j = e - (e / D.N) * D.N;
-    const int base = 4 * q;
-    if (!D.cplx) return TermLoc{base + 0, i * D.lda + t, base + 2, t * D.ldb + j, false};
+    c.it = items + q;
+    const int64_t e0 = d - (q ? __ldg(ends + q - 1) : 0);
+    const bool cx = c.it->cplx != 0;
+    c.part = cx ? (int)(e0 & 1) : 0;
+    const int64_t e = cx ? (e0 >> 1) : e0;
+    const int64_t N = c.it->N;
+    const int64_t i = e / N;
+    c.j = e - i * N;
+    c.xrow = i * c.it->lda;
+    c.oi = i * c.it->ldc + c.j;
+    return c;
+  }
+  __device__ int64_t nterms(const Cursor &c) const { return c.it->cplx ? 2 * c.it->K : c.it->K; }
+  __device__ TermLoc term(const Cursor &c, int64_t t) const {
+    const int64_t ldb = c.it->ldb;
+    if (!c.it->cplx) return TermLoc{0, c.xrow + t, 0, t * ldb + c.j, false};
     const int64_t k = t >> 1;
     const int w = (int)(t & 1);
-    const int64_t xi = i * D.lda + k, yi = k * D.ldb + j;
-    if (part == 0)
-      return w == 0 ? TermLoc{base + 0, xi, base + 2, yi, false}
-                    : TermLoc{base + 1, xi, base + 3, yi, true};
-    return w == 0 ? TermLoc{base + 0, xi, base + 3, yi, false}
-                  : TermLoc{base + 1, xi, base + 2, yi, false};
+    const int64_t xi = c.xrow + k, yi = k * ldb + c.j;
+    if (c.part == 0) return w == 0 ? TermLoc{0, xi, 0, yi, false} : TermLoc{1, xi, 1, yi, true};
+    return w == 0 ? TermLoc{0, xi, 1, yi, false} : TermLoc{1, xi, 0, yi, false};
   }
-  __device__ const BallsView &xview(int a) const { return items[a >> 2].A[a & 1]; }
-  __device__ const BallsView &yview(int b) const { return items[b >> 2].B[(b & 3) - 2]; }
-  __device__ bool has_initial(int64_t) const { return false; }
-  __device__ const BallsView &initial_view(int64_t) const { return items[0].A[0]; }
-  __device__ int64_t initial_index(int64_t) const { return 0; }
-  __device__ const BallsOut &out_view(int64_t d) const {
-    const int q = item(d);
-    const GroupItem &D = items[q];
-    return D.C[D.cplx ? (int)(local(d, q) & 1) : 0];
-  }
-  __device__ int64_t out_index(int64_t d) const {
-    const int q = item(d);
-    const GroupItem &D = items[q];
-    const int64_t e0 = local(d, q);
-    const int64_t e = D.cplx ? (e0 >> 1) : e0;
-    const int64_t i = e / D.N, j = e - i * D.N;
-    return i * D.ldc + j;
-  }
-  __device__ int prec(int64_t d) const { return items[item(d)].prec; }
+  __device__ const BallsView &xview(const Cursor &c, int a) const { return c.it->A[a]; }
+  __device__ const BallsView &yview(const Cursor &c, int b) const { return c.it->B[b]; }
+  __device__ bool has_initial() const { return false; }
+  __device__ const BallsView &initial_view(const Cursor &c) const { return c.it->A[0]; }
+  __device__ int64_t initial_index(const Cursor &) const { return 0; }
+  __device__ const BallsOut &out_view(const Cursor &c) const { return c.it->C[c.part]; }
+  __device__ int64_t out_index(const Cursor &c) const { return c.oi; }
+  __device__ int prec(const Cursor &c) const { return c.it->prec; }
   int64_t units() const { return total; }
 };
 
@@ -202,27 +219,44 @@ int dot_class_for_problem(int prec, int64_t max_terms, int max_nlimbs) {
   return dot_class_for(nx, ns);
 }
 
+template <int C, class Src>
+static void launch_eval(const Src &src, unsigned blocks, cudaStream_t stream) {
+  dot_eval_kernel<C, Src><<<blocks, 256, 0, stream>>>(src);
+}
+
+// Setup launch, then one evaluation launch per size class up to cmax.
 template <class Src>
 static arbgpu_status launch_dot_src(arbgpu_ctx *ctx, const Src &src, int64_t ndots, int cmax,
                                     cudaStream_t stream) {
   if (ndots <= 0) return ARBGPU_OK;
   const int threads = 256;
-  int64_t blocks = (ndots + 7) / 8;
   const int64_t cap = (int64_t)ctx->sm_count * 16;
-  if (blocks > cap) blocks = cap;
-  LaunchScope scope(ctx, stream, "dot_kernel", src.units());
-  switch (cmax) {
-    case 0: dot_kernel<0, Src><<<(unsigned)blocks, threads, 0, stream>>>(src, ctx->status); break;
-    case 1: dot_kernel<1, Src><<<(unsigned)blocks, threads, 0, stream>>>(src, ctx->status); break;
-    case 2: dot_kernel<2, Src><<<(unsigned)blocks, threads, 0, stream>>>(src, ctx->status); break;
-    case 3: dot_kernel<3, Src><<<(unsigned)blocks, threads, 0, stream>>>(src, ctx->status); break;
-    case 4: dot_kernel<4, Src><<<(unsigned)blocks, threads, 0, stream>>>(src, ctx->status); break;
-    case 5: dot_kernel<5, Src><<<(unsigned)blocks, threads, 0, stream>>>(src, ctx->status); break;
-    case 6: dot_kernel<6, Src><<<(unsigned)blocks, threads, 0, stream>>>(src, ctx->status); break;
-    case 7: dot_kernel<7, Src><<<(unsigned)blocks, threads, 0, stream>>>(src, ctx->status); break;
-    default: return ARBGPU_ERR_INVALID;
+  {
+    int64_t blocks = (ndots + 7) / 8;
+    if (blocks > cap) blocks = cap;
+    LaunchScope scope(ctx, stream, "dot_setup", src.units());
+    dot_setup_kernel<Src><<<(unsigned)blocks, threads, 0, stream>>>(src, cmax, ctx->status);
+    if (cudaGetLastError() != cudaSuccess) return ARBGPU_ERR_CUDA;
   }
-  return cudaGetLastError() == cudaSuccess ? ARBGPU_OK : ARBGPU_ERR_CUDA;
+  const int64_t chunks = (ndots + DOT_CHUNK - 1) / DOT_CHUNK;
+  int64_t blocks = (chunks + 7) / 8;
+  if (blocks > cap) blocks = cap;
+  for (int c = 0; c <= cmax; ++c) {
+    LaunchScope scope(ctx, stream, "dot_eval", c == cmax ? src.units() : 0);
+    switch (c) {
+      case 0: launch_eval<0>(src, (unsigned)blocks, stream); break;
+      case 1: launch_eval<1>(src, (unsigned)blocks, stream); break;
+      case 2: launch_eval<2>(src, (unsigned)blocks, stream); break;
+      case 3: launch_eval<3>(src, (unsigned)blocks, stream); break;
+      case 4: launch_eval<4>(src, (unsigned)blocks, stream); break;
+      case 5: launch_eval<5>(src, (unsigned)blocks, stream); break;
+      case 6: launch_eval<6>(src, (unsigned)blocks, stream); break;
+      case 7: launch_eval<7>(src, (unsigned)blocks, stream); break;
+      default: return ARBGPU_ERR_INVALID;
+    }
+    if (cudaGetLastError() != cudaSuccess) return ARBGPU_ERR_CUDA;
+  }
+  return ARBGPU_OK;
 }
 
 arbgpu_status launch_batched_dot(arbgpu_ctx *ctx, const arbgpu_balls *res,

@@ -1,22 +1,32 @@
-// Kernel (a): one warp evaluates one ball dot product by Algorithm 1 of the paper (Section III).
+// Kernel (a): ball dot products by Algorithm 1 of the paper (Section III), in two launches.
 //
-//   setup      (Section III-C)  lanes scan the terms' flags and exponents; warp max/sum reductions
-//                               give e_max, e_rad, N_nonzero and the accumulator size n_s.
-//   evaluation (Section III-D)  every lane multiplies its terms' leading limbs exactly
+//   setup      (Section III-C)  one warp per dot: lanes scan the terms' flags and exponents; warp
+//              max/sum reductions give e_max, e_rad, N_nonzero and the accumulator size n_s.  Dots
+//              that are finished here (special values, [0 +- 0]) are written out; for the others
+//              the setup is parked in the dot's own output entry (exp = e_s, rad_exp = e_rad,
+//              flags = PENDING | size class | n_s | limbs to read), so no workspace is needed.
+//   evaluate   one launch per size class (NX limbs read per factor, NS accumulator limbs), each
+//              compiled for its own register budget, so a warp never mixes code paths and the
+//              instruction cache holds one class at a time.  Warps scan chunks of dots for the
+//              entries of their class and evaluate them:
+//     products (Section III-D)  every lane multiplies its terms' leading limbs exactly
 //                               (64x64->128-bit products), aligns each product to the accumulator
 //                               and adds or subtracts it in two's complement; bits falling below
 //                               the accumulator, cut factors and skipped terms add one ulp to err.
-//   radius     (Section III-E)  30-bit upper bounds of |m| r', |m'| r, r r' summed in a 64-bit
+//     radius   (Section III-E)  30-bit upper bounds of |m| r', |m'| r, r r' summed in a 64-bit
 //                               fixed-point integer srad.
-//   reduction                   the lanes' n_s-limb accumulators, err and srad are added with a
+//     reduction                 the lanes' n_s-limb accumulators, err and srad are added with a
 //                               butterfly of warp shuffles; integer addition modulo 2^(64 NS) is
 //                               associative, so the result equals the sequential sum bit for bit.
-//   finalise   (Algorithm 1, step 4) negate if negative, round to p bits (nearest, ties to even),
-//                               radius = eps_round + err ulps + srad, rounded up to 30 bits.
+//     finalise (Algorithm 1, step 4) negate if negative, round to p bits (nearest, ties to even),
+//                               radius = eps_round + err ulps + srad, rounded up to 30 bits; all
+//                               in registers (fixed-size limb arrays, runtime bit positions).
 //
 // The accumulator and the product live in registers: every operand is held top-aligned in a
 // fixed-size array of NX limbs (unread low limbs are zero), so the 2NX-limb product sits at a fixed
-// position and one runtime offset F = 64 n_s - shift places it in the accumulator frame.
+// position and one runtime offset F = 64 n_s - shift places it in the accumulator frame.  A dot
+// may run in any class at least as large as its own (NX >= limbs read, NS >= n_s): the class only
+// sizes the register arrays, the arithmetic is fixed by n_s.
 #pragma once
 
 #include "common.cuh"
@@ -88,6 +98,15 @@ __device__ __forceinline__ Opnd load_opnd(const BallsView &v, int64_t i) {
   o.rexp = __ldg(v.rad_exp + i);
   return o;
 }
+// Midpoint fields only (for dots without radius products the radius fields are never needed).
+__device__ __forceinline__ Opnd load_opnd_mid(const BallsView &v, int64_t i) {
+  Opnd o;
+  o.flags = __ldg(v.flags + i);
+  o.e = __ldg(v.exp + i);
+  o.rman = 0;
+  o.rexp = 0;
+  return o;
+}
 
 // The exact ball [1 +- 0]: the second factor of the `initial` term.
 __device__ __forceinline__ Opnd one_opnd() { return Opnd{1u << ARBGPU_NSIG_SHIFT, 1, 0u, 0}; }
@@ -109,6 +128,26 @@ struct DotSetup {
   int nx;  // limbs to read per factor (at most)
   bool has_mid, has_rad;
 };
+
+// The setup parked in the output entry's flags word (bit 31 never appears in a finished entry).
+constexpr uint32_t DOT_PENDING = 1u << 31;
+__device__ __forceinline__ uint32_t pack_setup(int cls, const DotSetup &su) {
+  return DOT_PENDING | (uint32_t)cls | ((uint32_t)su.n_s << 4) | ((uint32_t)su.nx << 10) |
+         (su.has_mid ? (1u << 16) : 0u) | (su.has_rad ? (1u << 17) : 0u);
+}
+__device__ __forceinline__ int pending_class(uint32_t f) {
+  return (f & DOT_PENDING) ? (int)(f & 15u) : -1;
+}
+__device__ __forceinline__ DotSetup unpack_setup(uint32_t f, int64_t e_s, int64_t e_rad) {
+  DotSetup su;
+  su.e_s = e_s;
+  su.e_rad = e_rad;
+  su.n_s = (int)((f >> 4) & 63u);
+  su.nx = (int)((f >> 10) & 63u);
+  su.has_mid = (f >> 16) & 1u;
+  su.has_rad = (f >> 17) & 1u;
+  return su;
+}
 
 __device__ __forceinline__ int64_t warp_max_i64(int64_t v) {
 #pragma unroll
@@ -232,132 +271,179 @@ __device__ __forceinline__ void acc_term(LaneAcc<NS> &acc, const uint64_t (&xa)[
   }
 }
 
-// ---------------------------------------------------------------- multi-limb helpers (finalise)
+// ---------------------------------------------------------------- finalise (registers only)
 
-__device__ __forceinline__ bool limbs_bit(const uint64_t *a, int n, int64_t pos) {
-  if (pos < 0 || pos >= 64LL * n) return false;
-  return (a[pos >> 6] >> (pos & 63)) & 1;
+// Smallest 30-bit mag >= v * 2^base for a fixed-size limb array (the same value as
+// mag_from_limbs, without dynamically indexed arrays).
+template <int N>
+__device__ __forceinline__ Mag mag_up_regs(const uint64_t (&v)[N], int64_t base) {
+  int top = -1;
+#pragma unroll
+  for (int k = 0; k < N; ++k)
+    if (v[k]) top = k;
+  if (top < 0) return Mag{0u, 0};
+  uint64_t hi = 0, lo = 0;
+  bool rest = false;
+#pragma unroll
+  for (int k = 0; k < N; ++k) {
+    if (k == top) hi = v[k];
+    if (k == top - 1) lo = v[k];
+    if (k < top - 1) rest |= v[k] != 0;
+  }
+  const int lb = bitlen64(hi);
+  const int64_t L = (int64_t)top * 64 + lb;
+  if (L <= 64) return mag_from_u64(hi, base);
+  const uint64_t w = (lb == 64) ? hi : ((hi << (64 - lb)) | (lo >> lb));
+  const bool sticky = rest || ((lb == 64) ? (lo != 0) : ((lo << (64 - lb)) != 0));
+  uint64_t b = w >> 34;
+  if ((w & ((((uint64_t)1) << 34) - 1)) || sticky) b += 1;
+  int64_t e = base + L;
+  if (b == ((uint64_t)1 << P_RAD)) {
+    b >>= 1;
+    e += 1;
+  }
+  return Mag{(uint32_t)b, e};
 }
-__device__ __forceinline__ bool limbs_any_below(const uint64_t *a, int n, int64_t pos) {
-  if (pos <= 0) return false;
-  int64_t lim = pos >> 6;
-  for (int k = 0; k < n && k < lim; ++k)
-    if (a[k]) return true;
-  int rb = pos & 63;
-  if (rb && lim < n) return (a[lim] & ((((uint64_t)1) << rb) - 1)) != 0;
-  return false;
-}
-// out[0..nout) = floor(a * 2^-sh) mod 2^(64 nout) for sh >= 0, or a * 2^(-sh) for sh < 0.
-__device__ __forceinline__ void limbs_shift(const uint64_t *a, int n, int64_t sh, uint64_t *out,
-                                            int nout) {
-  for (int k = 0; k < nout; ++k) {
-    // bits [64k + sh, 64k + sh + 64) of a
-    int64_t lo = 64LL * k + sh;
-    int64_t li = lo >= 0 ? (lo >> 6) : -((-lo + 63) >> 6);
-    int bi = (int)(lo - li * 64);
-    uint64_t w0 = (li >= 0 && li < n) ? a[li] : 0;
-    uint64_t w1 = (li + 1 >= 0 && li + 1 < n) ? a[li + 1] : 0;
-    out[k] = bi ? ((w0 >> bi) | (w1 << (64 - bi))) : w0;
+
+// v <<= 64 q for 0 <= q < N (a barrel shifter over limbs: log2 N rounds of selects).
+template <int N>
+__device__ __forceinline__ void limbs_shift_up(uint64_t (&v)[N], int q) {
+#pragma unroll
+  for (int b = 1; b < N; b <<= 1) {
+    const bool on = (q & b) != 0;
+#pragma unroll
+    for (int j = N - 1; j >= 0; --j) v[j] = on ? (j >= b ? v[j - b] : 0) : v[j];
   }
 }
 
-// Finalise a reduced accumulator (Algorithm 1, step 4) and write output entry `oi`.
+// Round the reduced accumulator to p bits and write output entry `oi` (Algorithm 1, step 4).
+// Every lane holds the reduced sums and computes the same values; the output limbs are written by
+// the lanes in parallel, the scalar fields by lane 0.
 template <int NS>
 __device__ void dot_finalise(const LaneAcc<NS> &acc, const DotSetup &su, int prec,
                              const BallsOut &out, int64_t oi, int lane) {
-  if (lane != 0) return;  // every lane holds the reduced sums; one finishes the dot
-  uint64_t a[NS + 1];
-  for (int k = 0; k < NS; ++k) a[k] = acc.s[k];
-  a[NS] = 0;
-  bool neg = (a[NS - 1] >> 63) != 0;
-  if (neg) {
-    u128 c = 1;
+  constexpr int NT = NS + 1;  // the top-aligned frame
+  uint64_t a[NS];
+  const bool neg = (acc.s[NS - 1] >> 63) != 0;
+  {
+    const uint64_t flip = neg ? ~(uint64_t)0 : 0;
+    u128 c = neg ? 1 : 0;
+#pragma unroll
     for (int k = 0; k < NS; ++k) {
-      c += (u128)(~a[k]);
+      c += (u128)(acc.s[k] ^ flip);
       a[k] = (uint64_t)c;
       c >>= 64;
     }
   }
-  int top = -1;
-  for (int k = NS - 1; k >= 0; --k)
-    if (a[k]) {
-      top = k;
-      break;
-    }
+  int L = 0;  // bit length of |sum|
+#pragma unroll
+  for (int k = 0; k < NS; ++k)
+    if (a[k]) L = 64 * k + bitlen64(a[k]);
   const int64_t ulp_e = su.e_s - 64LL * su.n_s;
-  uint64_t E[NS + 2];  // eps_round + err, in accumulator ulps
-  for (int k = 0; k < NS + 2; ++k) E[k] = 0;
-  const int nl = out.nlimbs;
-  uint64_t field[64];
+  const bool zero = (L == 0) || !su.has_mid;
+  uint64_t ta[NT];
+  Mag r1{0u, 0};
   int64_t oexp = 0;
-  bool zero = (top < 0) || !su.has_mid;
   if (!zero) {
-    int64_t L = 64LL * top + bitlen64(a[top]);
-    int64_t k = L > prec ? L - prec : 0;
-    if (k > 0) {
-      bool rbit = limbs_bit(a, NS, k - 1);
-      bool sticky = limbs_any_below(a, NS, k - 1);
-      bool up = rbit && (sticky || limbs_bit(a, NS, k));
-      // rem = a mod 2^k
-      uint64_t rem[NS + 1];
-      for (int j = 0; j < NS + 1; ++j) {
-        int64_t lo = 64LL * j;
-        rem[j] = (lo + 64 <= k) ? a[j] : (lo < k ? (a[j] & ((((uint64_t)1) << (k - lo)) - 1)) : 0);
+    // ta = |sum| * 2^s0, top bit at 64 NT - 1 (s0 >= 65 since |sum| < 2^(64 NS - 1))
+    const int s0 = 64 * NT - L;
+    const int bs = s0 & 63;
+    ta[0] = a[0] << bs;
+#pragma unroll
+    for (int j = 1; j < NS; ++j) ta[j] = shl_funnel(a[j], a[j - 1], bs);
+    ta[NS] = shl_funnel(0, a[NS - 1], bs);
+    limbs_shift_up<NT>(ta, s0 >> 6);
+    // keep the top p bits: cut at bit c of ta (bits below c are the rounding remainder)
+    const int c = 64 * NT - prec;
+    const int cl = c >> 6, cb = c & 63;
+    const int rl = (c - 1) >> 6, rb = (c - 1) & 63;
+    uint64_t rem[NT];
+    uint64_t rword = 0, lword = 0;
+    bool sticky = false;
+#pragma unroll
+    for (int j = 0; j < NT; ++j) {
+      const uint64_t low = j < cl ? ~(uint64_t)0 : (j == cl ? ((((uint64_t)1) << cb) - 1) : 0);
+      rem[j] = ta[j] & low;
+      ta[j] &= ~low;
+      if (j == rl) rword = rem[j];
+      if (j == cl) lword = ta[j];
+      const uint64_t below_r = j < rl ? ~(uint64_t)0 : (j == rl ? ((((uint64_t)1) << rb) - 1) : 0);
+      sticky |= (rem[j] & below_r) != 0;
+    }
+    const bool rbit = (rword >> rb) & 1;
+    const bool lsb = (lword >> cb) & 1;
+    const bool up = rbit && (sticky || lsb);
+    // eps = |rounded - sum| in units of ta: 2^c - rem when rounding up, else rem
+    uint64_t E[NT + 1];
+    if (up) {
+      u128 cc = 0;
+      uint64_t borrow = 0;
+#pragma unroll
+      for (int j = 0; j < NT; ++j) {
+        const uint64_t unit = j == cl ? (((uint64_t)1) << cb) : 0;
+        cc += (u128)ta[j] + unit;
+        ta[j] = (uint64_t)cc;
+        cc >>= 64;
+        const u128 dlt = (u128)unit - rem[j] - borrow;
+        E[j] = (uint64_t)dlt;
+        borrow = (uint64_t)(dlt >> 64) & 1;
       }
-      // clear the low k bits of a
-      for (int j = 0; j < NS + 1; ++j) a[j] ^= rem[j];
-      if (up) {
-        // eps = 2^k - rem (0 < rem < 2^k here), then a += 2^k
-        for (int j = 0; j < NS + 1; ++j) E[j] = 0;
-        E[k >> 6] = ((uint64_t)1) << (k & 63);
-        uint64_t borrow = 0;
-        for (int j = 0; j < NS + 1; ++j) {
-          u128 dlt = (u128)E[j] - rem[j] - borrow;
-          E[j] = (uint64_t)dlt;
-          borrow = (uint64_t)(dlt >> 64) & 1;
-        }
-        int64_t pos = k;
-        u128 cc = ((u128)1) << (pos & 63);
-        for (int j = (int)(pos >> 6); j < NS + 1; ++j) {
-          cc += a[j];
-          a[j] = (uint64_t)cc;
-          cc >>= 64;
-        }
-        if (limbs_bit(a, NS + 1, L)) L += 1;
-      } else {
-        for (int j = 0; j < NS + 1; ++j) E[j] = rem[j];
+      if ((uint64_t)cc) {  // rounded up to 2^(64 NT): one bit longer
+#pragma unroll
+        for (int j = 0; j < NT; ++j) ta[j] = 0;
+        ta[NT - 1] = ((uint64_t)1) << 63;
+        L += 1;
+      }
+    } else {
+#pragma unroll
+      for (int j = 0; j < NT; ++j) E[j] = rem[j];
+    }
+    E[NT] = 0;
+    // E += err * 2^s0 (err counts accumulator ulps)
+    {
+      const int q = s0 >> 6;
+      const uint64_t lo = acc.err << bs;
+      const uint64_t hi = bs ? (acc.err >> (64 - bs)) : 0;
+      u128 cc = 0;
+#pragma unroll
+      for (int j = 0; j < NT + 1; ++j) {
+        const uint64_t add = (j == q) ? lo : ((j == q + 1) ? hi : 0);
+        cc += (u128)E[j] + add;
+        E[j] = (uint64_t)cc;
+        cc >>= 64;
       }
     }
-    // field = top-aligned mantissa in nl limbs: a * 2^(64 nl - L)
-    limbs_shift(a, NS + 1, L - 64LL * nl, field, nl);
+    r1 = mag_up_regs<NT + 1>(E, ulp_e - s0);
     oexp = ulp_e + L;
+  } else if (su.has_mid) {
+    r1 = mag_from_u64(acc.err, ulp_e);
   }
-  // E += err
-  {
-    u128 c = acc.err;
-    for (int j = 0; j < NS + 2; ++j) {
-      c += E[j];
-      E[j] = (uint64_t)c;
-      c >>= 64;
+  const Mag r2 = su.has_rad ? mag_from_u64(acc.srad, su.e_rad - P_RAD) : Mag{0u, 0};
+  const Mag r = mag_add_up(r1, r2);
+  const int nl = out.nlimbs;
+  // output limb nl-1-m is ta[NT-1-m] (m < NT), zero below
+  for (int m = lane; m < nl; m += 32) {
+    uint64_t v = 0;
+    if (!zero) {
+#pragma unroll
+      for (int j = 0; j < NT; ++j)
+        if (m == NT - 1 - j) v = ta[j];
     }
+    out.limbs[(int64_t)(nl - 1 - m) * out.stride + oi] = v;
   }
-  Mag r1 = su.has_mid ? mag_from_limbs(E, NS + 2, ulp_e) : Mag{0u, 0};
-  Mag r2 = su.has_rad ? mag_from_u64(acc.srad, su.e_rad - P_RAD) : Mag{0u, 0};
-  Mag r = mag_add_up(r1, r2);
   if (lane == 0) {
     uint32_t fl;
     if (zero) {
-      for (int j = 0; j < nl; ++j) out.limbs[(int64_t)j * out.stride + oi] = 0;
       out.exp[oi] = 0;
       fl = ARBGPU_FLAG_ZERO;
     } else {
-      int nsig = 0;
-      for (int j = 0; j < nl; ++j) {
-        out.limbs[(int64_t)j * out.stride + oi] = field[j];
-        if (nsig == 0 && field[j]) nsig = nl - j;
-      }
+      // significant limbs: from the top limb down to the lowest nonzero one
+      int jmin = NT - 1;
+#pragma unroll
+      for (int j = NT - 1; j >= 0; --j)
+        if (ta[j] && NT - 1 - j < nl) jmin = j;
       out.exp[oi] = oexp;
-      fl = (neg ? ARBGPU_FLAG_SIGN : 0u) | ((uint32_t)nsig << ARBGPU_NSIG_SHIFT);
+      fl = (neg ? ARBGPU_FLAG_SIGN : 0u) | ((uint32_t)(NT - jmin) << ARBGPU_NSIG_SHIFT);
     }
     out.flags[oi] = fl;
     out.rad_man[oi] = r.man;
@@ -366,10 +452,20 @@ __device__ void dot_finalise(const LaneAcc<NS> &acc, const DotSetup &su, int pre
 }
 
 __device__ __forceinline__ void write_special(const BallsOut &out, int64_t oi, int lane) {
+  for (int j = lane; j < out.nlimbs; j += 32) out.limbs[(int64_t)j * out.stride + oi] = 0;
   if (lane == 0) {
-    for (int j = 0; j < out.nlimbs; ++j) out.limbs[(int64_t)j * out.stride + oi] = 0;
     out.exp[oi] = 0;
     out.flags[oi] = ARBGPU_FLAG_NAN | ARBGPU_FLAG_RAD_INF;
+    out.rad_man[oi] = 0;
+    out.rad_exp[oi] = 0;
+  }
+}
+
+__device__ __forceinline__ void write_zero(const BallsOut &out, int64_t oi, int lane) {
+  for (int j = lane; j < out.nlimbs; j += 32) out.limbs[(int64_t)j * out.stride + oi] = 0;
+  if (lane == 0) {
+    out.exp[oi] = 0;
+    out.flags[oi] = ARBGPU_FLAG_ZERO;
     out.rad_man[oi] = 0;
     out.rad_exp[oi] = 0;
   }
@@ -385,9 +481,13 @@ struct TermLoc {
   bool neg;
 };
 
-// Evaluate dot d of `src` with one warp in size class C.
+// A term source provides, per dot d, a cursor (the dot's row/column/offsets, computed once) and
+// through it: nterms, term(t), the optional `initial` entry, the output entry and the precision.
+
+// Evaluate the dot under cursor `cur` with one warp in size class C.
 template <int C, class Src>
-__device__ void dot_eval_class(const Src &src, int64_t d, const DotSetup &su, int prec, int lane) {
+__device__ void dot_eval_class(const Src &src, const typename Src::Cursor &cur,
+                               const DotSetup &su, int prec, int lane) {
   constexpr int NX = DotClass<C>::NX;
   constexpr int NS = DotClass<C>::NS;
   LaneAcc<NS> acc;
@@ -395,9 +495,10 @@ __device__ void dot_eval_class(const Src &src, int64_t d, const DotSetup &su, in
   for (int k = 0; k < NS; ++k) acc.s[k] = 0;
   acc.err = 0;
   acc.srad = 0;
-  const int64_t nt = src.nterms(d);
-  const bool has_init = src.has_initial(d);
+  const int64_t nt = src.nterms(cur);
+  const bool has_init = src.has_initial();
   const int64_t width = 64LL * su.n_s;
+  const bool rad = su.has_rad;
   for (int64_t t = lane; t < nt + (has_init ? 1 : 0); t += 32) {
     Opnd x, y;
     const BallsView *xv = nullptr;
@@ -405,18 +506,18 @@ __device__ void dot_eval_class(const Src &src, int64_t d, const DotSetup &su, in
     int64_t xi = 0, yi = 0;
     bool negate = false;
     if (t < nt) {
-      TermLoc tl = src.term(d, t);
-      xv = &src.xview(tl.xa);
-      yv = &src.yview(tl.ya);
+      const TermLoc tl = src.term(cur, t);
+      xv = &src.xview(cur, tl.xa);
+      yv = &src.yview(cur, tl.ya);
       xi = tl.xi;
       yi = tl.yi;
       negate = tl.neg;
-      x = load_opnd(*xv, xi);
-      y = load_opnd(*yv, yi);
+      x = rad ? load_opnd(*xv, xi) : load_opnd_mid(*xv, xi);
+      y = rad ? load_opnd(*yv, yi) : load_opnd_mid(*yv, yi);
     } else {
-      xv = &src.initial_view(d);
-      xi = src.initial_index(d);
-      x = load_opnd(*xv, xi);
+      xv = &src.initial_view(cur);
+      xi = src.initial_index(cur);
+      x = rad ? load_opnd(*xv, xi) : load_opnd_mid(*xv, xi);
       y = one_opnd();
     }
     const bool xz = opnd_zero(x), yz = opnd_zero(y);
@@ -447,7 +548,7 @@ __device__ void dot_eval_class(const Src &src, int64_t d, const DotSetup &su, in
         acc_term<NX, NS>(acc, xa, ya, F, negative);
       }
     }
-    if (su.has_rad && (x.rman || y.rman)) {
+    if (rad && (x.rman || y.rman)) {
       if (!xz && xtop == 0) xtop = __ldg(xv->limbs + (int64_t)(xv->nlimbs - 1) * xv->stride + xi);
       if (!yz && ytop == 0)
         ytop = yv ? __ldg(yv->limbs + (int64_t)(yv->nlimbs - 1) * yv->stride + yi)
@@ -469,24 +570,25 @@ __device__ void dot_eval_class(const Src &src, int64_t d, const DotSetup &su, in
     acc.err += __shfl_xor_sync(0xffffffffu, acc.err, o);
     acc.srad += __shfl_xor_sync(0xffffffffu, acc.srad, o);
   }
-  dot_finalise<NS>(acc, su, prec, src.out_view(d), src.out_index(d), lane);
+  dot_finalise<NS>(acc, su, prec, src.out_view(cur), src.out_index(cur), lane);
 }
 
-// Whole dot: setup pass, class dispatch, evaluation.  CMAX bounds the classes compiled in.
-template <int CMAX, class Src>
-__device__ void dot_run(const Src &src, int64_t d, int lane, int *status) {
-  const int prec = src.prec(d);
-  const int64_t nt = src.nterms(d);
-  const bool has_init = src.has_initial(d);
-  const BallsOut &out = src.out_view(d);
-  const int64_t oi = src.out_index(d);
+// Setup pass of dot d (Section III-C): finishes the dot (special values, limits, [0 +- 0]) or
+// parks its setup in the output entry.  CMAX bounds the classes the launch will evaluate.
+template <class Src>
+__device__ void dot_setup(const Src &src, int64_t d, int cmax, int lane, int *status) {
+  const typename Src::Cursor cur = src.cursor(d);
+  const int prec = src.prec(cur);
+  const int64_t nt = src.nterms(cur);
+  const bool has_init = src.has_initial();
+  const BallsOut &out = src.out_view(cur);
+  const int64_t oi = src.out_index(cur);
   if (prec < 2 || prec > src.prec_max || nt < 0 || nt > src.len_max ||
       (int64_t)out.nlimbs * 64 < prec) {
-    set_status(status, ARBGPU_ERR_LIMIT);
+    if (lane == 0) set_status(status, ARBGPU_ERR_LIMIT);
     write_special(out, oi, lane);
     return;
   }
-  // ---- setup pass (Section III-C)
   bool special = false;
   int64_t nnz = 0;
   int64_t e_max = INT64_MIN, e_rad = INT64_MIN;
@@ -494,11 +596,11 @@ __device__ void dot_run(const Src &src, int64_t d, int lane, int *status) {
   for (int64_t t = lane; t < nt + (has_init ? 1 : 0); t += 32) {
     Opnd x, y;
     if (t < nt) {
-      TermLoc tl = src.term(d, t);
-      x = load_opnd(src.xview(tl.xa), tl.xi);
-      y = load_opnd(src.yview(tl.ya), tl.yi);
+      const TermLoc tl = src.term(cur, t);
+      x = load_opnd(src.xview(cur, tl.xa), tl.xi);
+      y = load_opnd(src.yview(cur, tl.ya), tl.yi);
     } else {
-      x = load_opnd(src.initial_view(d), src.initial_index(d));
+      x = load_opnd(src.initial_view(cur), src.initial_index(cur));
       y = one_opnd();
     }
     if (opnd_special(x) || opnd_special(y)) {
@@ -512,9 +614,8 @@ __device__ void dot_run(const Src &src, int64_t d, int lane, int *status) {
     }
     e_rad = term_rad_exp_max(x, y, e_rad);
   }
-  special = __any_sync(0xffffffffu, special);
-  if (special) {
-    set_status(status, ARBGPU_ERR_UNSUPPORTED_VALUE);
+  if (__any_sync(0xffffffffu, special)) {
+    if (lane == 0) set_status(status, ARBGPU_ERR_UNSUPPORTED_VALUE);
     write_special(out, oi, lane);
     return;
   }
@@ -526,13 +627,7 @@ __device__ void dot_run(const Src &src, int64_t d, int lane, int *status) {
   su.has_mid = e_max != INT64_MIN;
   su.has_rad = e_rad != INT64_MIN;
   if (!su.has_mid && !su.has_rad) {  // [0 +- 0]
-    if (lane == 0) {
-      for (int j = 0; j < out.nlimbs; ++j) out.limbs[(int64_t)j * out.stride + oi] = 0;
-      out.exp[oi] = 0;
-      out.flags[oi] = ARBGPU_FLAG_ZERO;
-      out.rad_man[oi] = 0;
-      out.rad_exp[oi] = 0;
-    }
+    write_zero(out, oi, lane);
     return;
   }
   const int64_t ntot = nt + (has_init ? 1 : 0);
@@ -543,31 +638,61 @@ __device__ void dot_run(const Src &src, int64_t d, int lane, int *status) {
   su.nx = min(nsig_max, su.n_s + 1);
   if (su.nx < 1) su.nx = 1;
   const int c = dot_class_for(su.nx, su.n_s);
-  if (c < 0 || c > CMAX) {
-    set_status(status, ARBGPU_ERR_LIMIT);
+  if (c < 0 || c > cmax) {
+    if (lane == 0) set_status(status, ARBGPU_ERR_LIMIT);
     write_special(out, oi, lane);
     return;
   }
-  switch (c) {
-    case 0: if constexpr (CMAX >= 0) dot_eval_class<0>(src, d, su, prec, lane); break;
-    case 1: if constexpr (CMAX >= 1) dot_eval_class<1>(src, d, su, prec, lane); break;
-    case 2: if constexpr (CMAX >= 2) dot_eval_class<2>(src, d, su, prec, lane); break;
-    case 3: if constexpr (CMAX >= 3) dot_eval_class<3>(src, d, su, prec, lane); break;
-    case 4: if constexpr (CMAX >= 4) dot_eval_class<4>(src, d, su, prec, lane); break;
-    case 5: if constexpr (CMAX >= 5) dot_eval_class<5>(src, d, su, prec, lane); break;
-    case 6: if constexpr (CMAX >= 6) dot_eval_class<6>(src, d, su, prec, lane); break;
-    case 7: if constexpr (CMAX >= 7) dot_eval_class<7>(src, d, su, prec, lane); break;
-    default: break;
+  if (lane == 0) {
+    out.exp[oi] = su.e_s;
+    out.rad_exp[oi] = su.e_rad;
+    out.flags[oi] = pack_setup(c, su);
   }
 }
 
-template <int CMAX, class Src>
-__global__ void __launch_bounds__(256) dot_kernel(const __grid_constant__ Src src, int *status) {
+template <class Src>
+__global__ void __launch_bounds__(256) dot_setup_kernel(const __grid_constant__ Src src, int cmax,
+                                                        int *status) {
   const int lane = threadIdx.x & 31;
   const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   const int64_t nd = src.ndots();
-  for (int64_t d = warp; d < nd; d += nwarps) dot_run<CMAX>(src, d, lane, status);
+  for (int64_t d = warp; d < nd; d += nwarps) dot_setup(src, d, cmax, lane, status);
+}
+
+// Dots scanned per warp step of an evaluation launch.
+constexpr int DOT_CHUNK = 8;
+
+// Evaluation of every pending dot of class C: a warp reads the parked flags of DOT_CHUNK dots and
+// evaluates those of its class one after the other.
+template <int C, class Src>
+__global__ void __launch_bounds__(256) dot_eval_kernel(const __grid_constant__ Src src) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const int64_t nd = src.ndots();
+  const int64_t nchunks = (nd + DOT_CHUNK - 1) / DOT_CHUNK;
+  for (int64_t ch = warp; ch < nchunks; ch += nwarps) {
+    const int64_t d0 = ch * DOT_CHUNK;
+    typename Src::Cursor cur{};
+    uint32_t f = 0;
+    if (lane < DOT_CHUNK && d0 + lane < nd) {
+      cur = src.cursor(d0 + lane);
+      f = __ldg(src.out_view(cur).flags + src.out_index(cur));
+    }
+    unsigned mask = __ballot_sync(0xffffffffu, pending_class(f) == C);
+    while (mask) {
+      const int l = __ffs(mask) - 1;
+      mask &= mask - 1;
+      const int64_t d = d0 + l;
+      const typename Src::Cursor cd = src.cursor(d);
+      const BallsOut &out = src.out_view(cd);
+      const int64_t oi = src.out_index(cd);
+      const uint32_t fd = __shfl_sync(0xffffffffu, f, l);
+      const DotSetup su = unpack_setup(fd, __ldg(out.exp + oi), __ldg(out.rad_exp + oi));
+      dot_eval_class<C>(src, cd, su, src.prec(cd), lane);
+    }
+  }
 }
 
 }  // namespace arbgpu

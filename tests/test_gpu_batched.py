@@ -46,7 +46,7 @@ def test_grouped_batch_mixed(arb):
     assert ctx.status() == 0
     names = [r[0] for r in ctx.trace_read()]
     ctx.trace(False)
-    assert names.count("dot_kernel") == 1  # every classical item in one grouped launch
+    assert names.count("dot_setup") == 1  # every classical item in one grouped launch
     rng2 = np.random.default_rng(2)
     for A, B, C, n, p, cplx in raws:
         outs = [to_raw(c) for c in C]
