@@ -1,0 +1,57 @@
+// Kernel (a) for batched dots (arbgpu_dot).
+#include "dot_src.cuh"
+
+namespace arbgpu {
+
+int dot_class_for_problem(int prec, int64_t max_terms, int max_nlimbs) {
+  const int ns = dot_ns(prec, max_terms, max_terms);
+  int nx = max_nlimbs < ns + 1 ? max_nlimbs : ns + 1;
+  if (nx < 1) nx = 1;
+  return dot_class_for(nx, ns);
+}
+
+arbgpu_status launch_batched_dot(arbgpu_ctx *ctx, const arbgpu_balls *res,
+                                 const arbgpu_balls *initial, const uint8_t *sub,
+                                 const arbgpu_balls *x, const int64_t *xoff, const int64_t *xstep,
+                                 const arbgpu_balls *y, const int64_t *yoff, const int64_t *ystep,
+                                 const int64_t *len, const int32_t *prec, int64_t batch,
+                                 int32_t prec_max, int64_t len_max, int complex_mode,
+                                 cudaStream_t stream) {
+  const int parts = complex_mode ? 2 : 1;
+  BatchDotSrc s{};
+  int maxnl = 1;
+  for (int q = 0; q < parts; ++q) {
+    s.x[q] = view_of(x[q]);
+    s.y[q] = view_of(y[q]);
+    s.out[q] = out_of(res[q]);
+    s.init[q] = initial ? view_of(initial[q]) : view_of(x[q]);
+    maxnl = x[q].nlimbs > maxnl ? x[q].nlimbs : maxnl;
+    maxnl = y[q].nlimbs > maxnl ? y[q].nlimbs : maxnl;
+    if (initial) maxnl = initial[q].nlimbs > maxnl ? initial[q].nlimbs : maxnl;
+  }
+  if (!complex_mode) {
+    s.x[1] = s.x[0];
+    s.y[1] = s.y[0];
+    s.out[1] = s.out[0];
+    s.init[1] = s.init[0];
+  }
+  s.xoff = xoff;
+  s.xstep = xstep;
+  s.yoff = yoff;
+  s.ystep = ystep;
+  s.len = len;
+  s.precs = prec;
+  s.subs = sub;
+  s.batch = batch;
+  s.cplx = complex_mode ? 1 : 0;
+  s.has_init = initial != nullptr;
+  s.prec_max = prec_max;
+  const int64_t terms_max = (complex_mode ? 2 * len_max : len_max);
+  s.len_max = terms_max;
+  s.ndots_host = s.cplx ? 2 * batch : batch;
+  const int cmax = dot_class_for_problem(prec_max, terms_max + 1, maxnl);
+  if (cmax < 0) return ARBGPU_ERR_INVALID;
+  return launch_dot_src(ctx, s, s.cplx ? 2 * batch : batch, cmax, dot_group_batched(terms_max), stream);
+}
+
+}  // namespace arbgpu

@@ -165,6 +165,29 @@ __device__ __forceinline__ int64_t warp_sum_i64(int64_t v) {
 
 __device__ __forceinline__ int64_t imax64(int64_t a, int64_t b) { return a > b ? a : b; }
 
+// Lane groups: a warp evaluates 32 / G dots at once, G consecutive lanes per dot.  Shuffles name
+// only the group's lanes, so groups may take different paths; offsets stay below G.
+template <int G>
+__device__ __forceinline__ unsigned group_mask(int lane) {
+  if constexpr (G == 32)
+    return 0xffffffffu;
+  else
+    return ((1u << G) - 1u) << (lane & ~(G - 1));
+}
+template <int G>
+__device__ __forceinline__ int64_t group_max_i64(int64_t v, unsigned gm) {
+#pragma unroll
+  for (int o = G / 2; o > 0; o >>= 1) v = imax64(v, __shfl_xor_sync(gm, v, o));
+  return v;
+}
+template <int G>
+__device__ __forceinline__ int64_t group_sum_i64(int64_t v, unsigned gm) {
+#pragma unroll
+  for (int o = G / 2; o > 0; o >>= 1) v += __shfl_xor_sync(gm, v, o);
+  return v;
+}
+__device__ __forceinline__ bool group_any(bool p, unsigned gm) { return __ballot_sync(gm, p) != 0; }
+
 // Radius exponents of the nonzero products |m| r', |m'| r, r r' of one term (Section III-C 5c).
 __device__ __forceinline__ int64_t term_rad_exp_max(const Opnd &x, const Opnd &y, int64_t cur) {
   bool xz = opnd_zero(x), yz = opnd_zero(y);
@@ -317,11 +340,11 @@ __device__ __forceinline__ void limbs_shift_up(uint64_t (&v)[N], int q) {
 }
 
 // Round the reduced accumulator to p bits and write output entry `oi` (Algorithm 1, step 4).
-// Every lane holds the reduced sums and computes the same values; the output limbs are written by
-// the lanes in parallel, the scalar fields by lane 0.
-template <int NS>
+// Every lane of the group holds the reduced sums and computes the same values; the output limbs are
+// written by the group's lanes in parallel, the scalar fields by its first lane.
+template <int NS, int G>
 __device__ void dot_finalise(const LaneAcc<NS> &acc, const DotSetup &su, int prec,
-                             const BallsOut &out, int64_t oi, int lane) {
+                             const BallsOut &out, int64_t oi, int gl) {
   constexpr int NT = NS + 1;  // the top-aligned frame
   uint64_t a[NS];
   const bool neg = (acc.s[NS - 1] >> 63) != 0;
@@ -422,7 +445,7 @@ __device__ void dot_finalise(const LaneAcc<NS> &acc, const DotSetup &su, int pre
   const Mag r = mag_add_up(r1, r2);
   const int nl = out.nlimbs;
   // output limb nl-1-m is ta[NT-1-m] (m < NT), zero below
-  for (int m = lane; m < nl; m += 32) {
+  for (int m = gl; m < nl; m += G) {
     uint64_t v = 0;
     if (!zero) {
 #pragma unroll
@@ -431,7 +454,7 @@ __device__ void dot_finalise(const LaneAcc<NS> &acc, const DotSetup &su, int pre
     }
     out.limbs[(int64_t)(nl - 1 - m) * out.stride + oi] = v;
   }
-  if (lane == 0) {
+  if (gl == 0) {
     uint32_t fl;
     if (zero) {
       out.exp[oi] = 0;
@@ -451,9 +474,10 @@ __device__ void dot_finalise(const LaneAcc<NS> &acc, const DotSetup &su, int pre
   }
 }
 
-__device__ __forceinline__ void write_special(const BallsOut &out, int64_t oi, int lane) {
-  for (int j = lane; j < out.nlimbs; j += 32) out.limbs[(int64_t)j * out.stride + oi] = 0;
-  if (lane == 0) {
+template <int G>
+__device__ __forceinline__ void write_special(const BallsOut &out, int64_t oi, int gl) {
+  for (int j = gl; j < out.nlimbs; j += G) out.limbs[(int64_t)j * out.stride + oi] = 0;
+  if (gl == 0) {
     out.exp[oi] = 0;
     out.flags[oi] = ARBGPU_FLAG_NAN | ARBGPU_FLAG_RAD_INF;
     out.rad_man[oi] = 0;
@@ -461,9 +485,10 @@ __device__ __forceinline__ void write_special(const BallsOut &out, int64_t oi, i
   }
 }
 
-__device__ __forceinline__ void write_zero(const BallsOut &out, int64_t oi, int lane) {
-  for (int j = lane; j < out.nlimbs; j += 32) out.limbs[(int64_t)j * out.stride + oi] = 0;
-  if (lane == 0) {
+template <int G>
+__device__ __forceinline__ void write_zero(const BallsOut &out, int64_t oi, int gl) {
+  for (int j = gl; j < out.nlimbs; j += G) out.limbs[(int64_t)j * out.stride + oi] = 0;
+  if (gl == 0) {
     out.exp[oi] = 0;
     out.flags[oi] = ARBGPU_FLAG_ZERO;
     out.rad_man[oi] = 0;
@@ -484,99 +509,141 @@ struct TermLoc {
 // A term source provides, per dot d, a cursor (the dot's row/column/offsets, computed once) and
 // through it: nterms, term(t), the optional `initial` entry, the output entry and the precision.
 
-// Evaluate the dot under cursor `cur` with one warp in size class C.
-template <int C, class Src>
+// Terms a lane takes per step of the evaluation loop.  The scalar fields and the leading limbs of
+// all of them are requested together (the limbs speculatively, min(NX, n) of them, masked once the
+// flags and exponents are in), so a step waits for one memory round trip.
+template <int NX>
+struct TermsPerStep {
+  static constexpr int U = NX <= 2 ? 2 : 1;
+};
+
+// Load the leading min(NX, n) limbs of entry i top-aligned into a[NX] (zeros below).
+template <int NX>
+__device__ __forceinline__ void load_top(const BallsView &v, int64_t i, uint64_t (&a)[NX]) {
+  const uint64_t *base = v.limbs + (int64_t)(v.nlimbs - 1) * v.stride + i;
+#pragma unroll
+  for (int j = 0; j < NX; ++j) a[NX - 1 - j] = j < v.nlimbs ? __ldg(base - (int64_t)j * v.stride) : 0;
+}
+
+// Keep the r leading limbs of a top-aligned operand.
+template <int NX>
+__device__ __forceinline__ void keep_leading(uint64_t (&a)[NX], int r) {
+#pragma unroll
+  for (int j = 0; j < NX; ++j)
+    if (j >= r) a[NX - 1 - j] = 0;
+}
+
+// Evaluate the dot under cursor `cur` with a group of G lanes in size class C.
+template <int C, int G, class Src>
 __device__ void dot_eval_class(const Src &src, const typename Src::Cursor &cur,
-                               const DotSetup &su, int prec, int lane) {
+                               const DotSetup &su, int prec, int gl, unsigned gm) {
   constexpr int NX = DotClass<C>::NX;
   constexpr int NS = DotClass<C>::NS;
+  constexpr int U = TermsPerStep<NX>::U;
   LaneAcc<NS> acc;
 #pragma unroll
   for (int k = 0; k < NS; ++k) acc.s[k] = 0;
   acc.err = 0;
   acc.srad = 0;
   const int64_t nt = src.nterms(cur);
-  const bool has_init = src.has_initial();
+  const int64_t ntot = nt + (src.has_initial() ? 1 : 0);
   const int64_t width = 64LL * su.n_s;
   const bool rad = su.has_rad;
-  for (int64_t t = lane; t < nt + (has_init ? 1 : 0); t += 32) {
-    Opnd x, y;
-    const BallsView *xv = nullptr;
-    const BallsView *yv = nullptr;
-    int64_t xi = 0, yi = 0;
-    bool negate = false;
-    if (t < nt) {
-      const TermLoc tl = src.term(cur, t);
-      xv = &src.xview(cur, tl.xa);
-      yv = &src.yview(cur, tl.ya);
-      xi = tl.xi;
-      yi = tl.yi;
-      negate = tl.neg;
-      x = rad ? load_opnd(*xv, xi) : load_opnd_mid(*xv, xi);
-      y = rad ? load_opnd(*yv, yi) : load_opnd_mid(*yv, yi);
-    } else {
-      xv = &src.initial_view(cur);
-      xi = src.initial_index(cur);
-      x = rad ? load_opnd(*xv, xi) : load_opnd_mid(*xv, xi);
-      y = one_opnd();
-    }
-    const bool xz = opnd_zero(x), yz = opnd_zero(y);
-    uint64_t xtop = 0, ytop = 0;
-    if (!xz && !yz) {
-      const int64_t shift = su.e_s - (x.e + y.e);
-      if (shift >= width) {
-        acc.err += 1;
-      } else {
-        const int F = (int)(width - shift);
-        const int n2 = (F + 63) / 64 + 1;
-        const int nx = min((int)nsig_of(x.flags), xv->nlimbs);
-        const int ny = yv ? min((int)nsig_of(y.flags), yv->nlimbs) : 1;
-        if (nx > n2 || ny > n2) acc.err += 1;
-        const int rx = min(nx, n2), ry = min(ny, n2);
-        uint64_t xa[NX], ya[NX];
-        load_leading<NX>(*xv, xi, rx, xa);
-        if (yv) {
-          load_leading<NX>(*yv, yi, ry, ya);
-        } else {
+  for (int64_t t0 = gl; t0 < ntot; t0 += G * U) {
+    Opnd x[U], y[U];
+    const BallsView *xv[U];
+    const BallsView *yv[U];
+    int64_t xi[U], yi[U];
+    bool negate[U], valid[U];
+    // scalar fields and leading limbs of U terms
+    uint64_t xa[U][NX], ya[U][NX];
 #pragma unroll
-          for (int j = 0; j < NX; ++j) ya[j] = 0;
-          ya[NX - 1] = (uint64_t)1 << 63;
-        }
-        xtop = xa[NX - 1];
-        ytop = ya[NX - 1];
-        const bool negative = (((x.flags ^ y.flags) & ARBGPU_FLAG_SIGN) != 0) != negate;
-        acc_term<NX, NS>(acc, xa, ya, F, negative);
+    for (int u = 0; u < U; ++u) {
+      const int64_t t = t0 + G * u;
+      valid[u] = t < ntot;
+      xv[u] = nullptr;
+      yv[u] = nullptr;
+      xi[u] = yi[u] = 0;
+      negate[u] = false;
+      x[u] = y[u] = Opnd{ARBGPU_FLAG_ZERO, 0, 0u, 0};
+#pragma unroll
+      for (int j = 0; j < NX; ++j) xa[u][j] = ya[u][j] = 0;
+      if (t < nt) {
+        const TermLoc tl = src.term(cur, t);
+        xv[u] = &src.xview(cur, tl.xa);
+        yv[u] = &src.yview(cur, tl.ya);
+        xi[u] = tl.xi;
+        yi[u] = tl.yi;
+        negate[u] = tl.neg;
+        x[u] = rad ? load_opnd(*xv[u], xi[u]) : load_opnd_mid(*xv[u], xi[u]);
+        y[u] = rad ? load_opnd(*yv[u], yi[u]) : load_opnd_mid(*yv[u], yi[u]);
+        load_top<NX>(*xv[u], xi[u], xa[u]);
+        load_top<NX>(*yv[u], yi[u], ya[u]);
+      } else if (valid[u]) {
+        xv[u] = &src.initial_view(cur);
+        xi[u] = src.initial_index(cur);
+        x[u] = rad ? load_opnd(*xv[u], xi[u]) : load_opnd_mid(*xv[u], xi[u]);
+        y[u] = one_opnd();
+        load_top<NX>(*xv[u], xi[u], xa[u]);
+        ya[u][NX - 1] = (uint64_t)1 << 63;
       }
     }
-    if (rad && (x.rman || y.rman)) {
-      if (!xz && xtop == 0) xtop = __ldg(xv->limbs + (int64_t)(xv->nlimbs - 1) * xv->stride + xi);
-      if (!yz && ytop == 0)
-        ytop = yv ? __ldg(yv->limbs + (int64_t)(yv->nlimbs - 1) * yv->stride + yi)
-                  : ((uint64_t)1 << 63);
-      term_radius(acc.srad, x, xtop, y, ytop, su.e_rad);
+    // which terms reach the accumulator, and how many limbs of each factor they use
+    int F[U];
+    bool live[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      live[u] = false;
+      F[u] = 0;
+      if (valid[u] && !opnd_zero(x[u]) && !opnd_zero(y[u])) {
+        const int64_t shift = su.e_s - (x[u].e + y[u].e);
+        if (shift >= width) {
+          acc.err += 1;
+        } else {
+          live[u] = true;
+          F[u] = (int)(width - shift);
+          const int n2 = (F[u] + 63) / 64 + 1;
+          const int nx = min((int)nsig_of(x[u].flags), xv[u]->nlimbs);
+          const int ny = yv[u] ? min((int)nsig_of(y[u].flags), yv[u]->nlimbs) : 1;
+          if (nx > n2 || ny > n2) acc.err += 1;
+          keep_leading<NX>(xa[u], min(nx, n2));
+          keep_leading<NX>(ya[u], min(ny, n2));
+        }
+      }
+    }
+    // products and radii
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      if (live[u]) {
+        const bool negative =
+            (((x[u].flags ^ y[u].flags) & ARBGPU_FLAG_SIGN) != 0) != negate[u];
+        acc_term<NX, NS>(acc, xa[u], ya[u], F[u], negative);
+      }
+      if (rad && valid[u] && (x[u].rman || y[u].rman))
+        term_radius(acc.srad, x[u], xa[u][NX - 1], y[u], ya[u][NX - 1], su.e_rad);
     }
   }
-  // butterfly reduction: every lane ends with the full sums
+  // butterfly reduction over the group: every lane ends with the full sums
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
+  for (int o = G / 2; o > 0; o >>= 1) {
     u128 c = 0;
 #pragma unroll
     for (int k = 0; k < NS; ++k) {
-      uint64_t v = __shfl_xor_sync(0xffffffffu, acc.s[k], o);
+      uint64_t v = __shfl_xor_sync(gm, acc.s[k], o);
       c += (u128)acc.s[k] + v;
       acc.s[k] = (uint64_t)c;
       c >>= 64;
     }
-    acc.err += __shfl_xor_sync(0xffffffffu, acc.err, o);
-    acc.srad += __shfl_xor_sync(0xffffffffu, acc.srad, o);
+    acc.err += __shfl_xor_sync(gm, acc.err, o);
+    acc.srad += __shfl_xor_sync(gm, acc.srad, o);
   }
-  dot_finalise<NS>(acc, su, prec, src.out_view(cur), src.out_index(cur), lane);
+  dot_finalise<NS, G>(acc, su, prec, src.out_view(cur), src.out_index(cur), gl);
 }
 
 // Setup pass of dot d (Section III-C): finishes the dot (special values, limits, [0 +- 0]) or
 // parks its setup in the output entry.  CMAX bounds the classes the launch will evaluate.
-template <class Src>
-__device__ void dot_setup(const Src &src, int64_t d, int cmax, int lane, int *status) {
+template <int G, class Src>
+__device__ void dot_setup(const Src &src, int64_t d, int cmax, int gl, unsigned gm, int *status) {
   const typename Src::Cursor cur = src.cursor(d);
   const int prec = src.prec(cur);
   const int64_t nt = src.nterms(cur);
@@ -585,52 +652,64 @@ __device__ void dot_setup(const Src &src, int64_t d, int cmax, int lane, int *st
   const int64_t oi = src.out_index(cur);
   if (prec < 2 || prec > src.prec_max || nt < 0 || nt > src.len_max ||
       (int64_t)out.nlimbs * 64 < prec) {
-    if (lane == 0) set_status(status, ARBGPU_ERR_LIMIT);
-    write_special(out, oi, lane);
+    if (gl == 0) set_status(status, ARBGPU_ERR_LIMIT);
+    write_special<G>(out, oi, gl);
     return;
   }
   bool special = false;
   int64_t nnz = 0;
   int64_t e_max = INT64_MIN, e_rad = INT64_MIN;
   int nsig_max = 0;
-  for (int64_t t = lane; t < nt + (has_init ? 1 : 0); t += 32) {
-    Opnd x, y;
-    if (t < nt) {
-      const TermLoc tl = src.term(cur, t);
-      x = load_opnd(src.xview(cur, tl.xa), tl.xi);
-      y = load_opnd(src.yview(cur, tl.ya), tl.yi);
-    } else {
-      x = load_opnd(src.initial_view(cur), src.initial_index(cur));
-      y = one_opnd();
+  constexpr int U = 4;  // terms per lane per step, loads issued together
+  const int64_t ntot = nt + (has_init ? 1 : 0);
+  for (int64_t t0 = gl; t0 < ntot; t0 += G * U) {
+    Opnd x[U], y[U];
+    bool valid[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int64_t t = t0 + G * u;
+      valid[u] = t < ntot;
+      x[u] = y[u] = Opnd{ARBGPU_FLAG_ZERO, 0, 0u, 0};
+      if (t < nt) {
+        const TermLoc tl = src.term(cur, t);
+        x[u] = load_opnd(src.xview(cur, tl.xa), tl.xi);
+        y[u] = load_opnd(src.yview(cur, tl.ya), tl.yi);
+      } else if (valid[u]) {
+        x[u] = load_opnd(src.initial_view(cur), src.initial_index(cur));
+        y[u] = one_opnd();
+      }
     }
-    if (opnd_special(x) || opnd_special(y)) {
-      special = true;
-      continue;
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      if (!valid[u]) continue;
+      if (opnd_special(x[u]) || opnd_special(y[u])) {
+        special = true;
+        continue;
+      }
+      if (!opnd_zero(x[u]) && !opnd_zero(y[u])) {
+        ++nnz;
+        e_max = imax64(e_max, x[u].e + y[u].e);
+        nsig_max = max(nsig_max, (int)max(nsig_of(x[u].flags), nsig_of(y[u].flags)));
+      }
+      e_rad = term_rad_exp_max(x[u], y[u], e_rad);
     }
-    if (!opnd_zero(x) && !opnd_zero(y)) {
-      ++nnz;
-      e_max = imax64(e_max, x.e + y.e);
-      nsig_max = max(nsig_max, (int)max(nsig_of(x.flags), nsig_of(y.flags)));
-    }
-    e_rad = term_rad_exp_max(x, y, e_rad);
   }
-  if (__any_sync(0xffffffffu, special)) {
-    if (lane == 0) set_status(status, ARBGPU_ERR_UNSUPPORTED_VALUE);
-    write_special(out, oi, lane);
+  if (group_any(special, gm)) {
+    if (gl == 0) set_status(status, ARBGPU_ERR_UNSUPPORTED_VALUE);
+    write_special<G>(out, oi, gl);
     return;
   }
-  nnz = warp_sum_i64(nnz);
-  e_max = warp_max_i64(e_max);
-  e_rad = warp_max_i64(e_rad);
-  nsig_max = (int)warp_max_i64(nsig_max);
+  nnz = group_sum_i64<G>(nnz, gm);
+  e_max = group_max_i64<G>(e_max, gm);
+  e_rad = group_max_i64<G>(e_rad, gm);
+  nsig_max = (int)group_max_i64<G>(nsig_max, gm);
   DotSetup su;
   su.has_mid = e_max != INT64_MIN;
   su.has_rad = e_rad != INT64_MIN;
   if (!su.has_mid && !su.has_rad) {  // [0 +- 0]
-    write_zero(out, oi, lane);
+    write_zero<G>(out, oi, gl);
     return;
   }
-  const int64_t ntot = nt + (has_init ? 1 : 0);
   const int extend = bc64(nnz) + 1;
   su.n_s = dot_ns(prec, ntot, nnz);
   su.e_s = su.has_mid ? e_max + extend : 0;
@@ -639,58 +718,80 @@ __device__ void dot_setup(const Src &src, int64_t d, int cmax, int lane, int *st
   if (su.nx < 1) su.nx = 1;
   const int c = dot_class_for(su.nx, su.n_s);
   if (c < 0 || c > cmax) {
-    if (lane == 0) set_status(status, ARBGPU_ERR_LIMIT);
-    write_special(out, oi, lane);
+    if (gl == 0) set_status(status, ARBGPU_ERR_LIMIT);
+    write_special<G>(out, oi, gl);
     return;
   }
-  if (lane == 0) {
+  if (gl == 0) {
     out.exp[oi] = su.e_s;
     out.rad_exp[oi] = su.e_rad;
     out.flags[oi] = pack_setup(c, su);
   }
 }
 
-template <class Src>
+template <int G, class Src>
 __global__ void __launch_bounds__(256) dot_setup_kernel(const __grid_constant__ Src src, int cmax,
                                                         int *status) {
+  constexpr int DPW = 32 / G;  // dots per warp step
   const int lane = threadIdx.x & 31;
+  const int gl = lane & (G - 1);
+  const unsigned gm = group_mask<G>(lane);
   const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   const int64_t nd = src.ndots();
-  for (int64_t d = warp; d < nd; d += nwarps) dot_setup(src, d, cmax, lane, status);
+  for (int64_t d0 = warp * DPW; d0 < nd; d0 += nwarps * DPW) {
+    const int64_t d = d0 + lane / G;
+    if (d < nd) dot_setup<G>(src, d, cmax, gl, gm, status);
+  }
 }
 
-// Dots scanned per warp step of an evaluation launch.
-constexpr int DOT_CHUNK = 8;
+// Largest number of dots a warp scans per step of an evaluation launch.
+constexpr int DOT_CHUNK = 32;
 
-// Evaluation of every pending dot of class C: a warp reads the parked flags of DOT_CHUNK dots and
-// evaluates those of its class one after the other.
-template <int C, class Src>
-__global__ void __launch_bounds__(256) dot_eval_kernel(const __grid_constant__ Src src) {
+// Resident 256-thread blocks per SM the register budget of each class is sized for.
+template <int C>
+struct DotClassBlocks {
+  static constexpr int B = C <= 4 ? 2 : 1;
+};
+
+// Evaluation of every pending dot of class C: a warp reads the parked flags of `chunk` dots and
+// evaluates those of its class, 32 / G at a time (one per lane group).
+template <int C, int G, class Src>
+__global__ void __launch_bounds__(256, DotClassBlocks<C>::B)
+    dot_eval_kernel(const __grid_constant__ Src src, int chunk) {
+  constexpr int DPW = 32 / G;
   const int lane = threadIdx.x & 31;
+  const int g = lane / G, gl = lane & (G - 1);
+  const unsigned gm = group_mask<G>(lane);
   const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   const int64_t nd = src.ndots();
-  const int64_t nchunks = (nd + DOT_CHUNK - 1) / DOT_CHUNK;
+  const int64_t nchunks = (nd + chunk - 1) / chunk;
   for (int64_t ch = warp; ch < nchunks; ch += nwarps) {
-    const int64_t d0 = ch * DOT_CHUNK;
-    typename Src::Cursor cur{};
+    const int64_t d0 = ch * chunk;
     uint32_t f = 0;
-    if (lane < DOT_CHUNK && d0 + lane < nd) {
-      cur = src.cursor(d0 + lane);
-      f = __ldg(src.out_view(cur).flags + src.out_index(cur));
+    if (lane < chunk && d0 + lane < nd) {
+      const typename Src::Cursor c = src.cursor(d0 + lane);
+      f = __ldg(src.out_view(c).flags + src.out_index(c));
     }
     unsigned mask = __ballot_sync(0xffffffffu, pending_class(f) == C);
     while (mask) {
-      const int l = __ffs(mask) - 1;
-      mask &= mask - 1;
-      const int64_t d = d0 + l;
-      const typename Src::Cursor cd = src.cursor(d);
-      const BallsOut &out = src.out_view(cd);
-      const int64_t oi = src.out_index(cd);
-      const uint32_t fd = __shfl_sync(0xffffffffu, f, l);
-      const DotSetup su = unpack_setup(fd, __ldg(out.exp + oi), __ldg(out.rad_exp + oi));
-      dot_eval_class<C>(src, cd, su, src.prec(cd), lane);
+      // group g takes the g-th remaining dot of the chunk
+      unsigned m = mask;
+      for (int k = 0; k < g; ++k) m &= m - 1;
+      const int pos = m ? __ffs(m) - 1 : 0;
+      const bool has = m != 0;
+#pragma unroll
+      for (int k = 0; k < DPW; ++k) mask &= mask - 1;
+      const uint32_t fd = __shfl_sync(0xffffffffu, f, pos);
+      if (has) {
+        const typename Src::Cursor cd = src.cursor(d0 + pos);
+        const BallsOut &out = src.out_view(cd);
+        const int64_t oi = src.out_index(cd);
+        const DotSetup su = unpack_setup(fd, __ldg(out.exp + oi), __ldg(out.rad_exp + oi));
+        dot_eval_class<C, G>(src, cd, su, src.prec(cd), gl, gm);
+      }
+      __syncwarp();
     }
   }
 }

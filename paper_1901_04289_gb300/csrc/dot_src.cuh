@@ -1,5 +1,9 @@
-// Term sources for kernel (a) and their launchers: batched dots (arb_dot / acb_dot counterparts,
-// Section III) and the classical matrix product as M*N dots (Section IV).
+// Term sources of kernel (a) and the launch sequence shared by its callers: batched dots (arb_dot /
+// acb_dot counterparts, Section III), the classical matrix product as M*N dots (Section IV), the
+// basecase blocks of Algorithm 2 and grouped classical products.  Each source is compiled in its
+// own translation unit (dot_*.cu).
+#pragma once
+
 #include "dot_eval.cuh"
 #include "internal.h"
 
@@ -212,46 +216,55 @@ struct GroupedDotSrc {
   int64_t units() const { return total; }
 };
 
-int dot_class_for_problem(int prec, int64_t max_terms, int max_nlimbs) {
-  const int ns = dot_ns(prec, max_terms, max_terms);
-  int nx = max_nlimbs < ns + 1 ? max_nlimbs : ns + 1;
-  if (nx < 1) nx = 1;
-  return dot_class_for(nx, ns);
+// Lanes per dot.  Matrix-shaped sources take 4 lanes per entry: a warp then evaluates eight
+// neighbouring entries of a row of C at once, and at every step their groups read neighbouring
+// entries of a row of B (coalesced) and the same entries of A.  Batched dots with unit strides are
+// coalesced within a group, so they take whole warps unless they are short.
+inline int dot_group_matrix() { return 4; }
+inline int dot_group_batched(int64_t terms) {
+  return terms >= 128 ? 32 : (terms >= 64 ? 16 : (terms >= 32 ? 8 : 4));
 }
 
-template <int C, class Src>
-static void launch_eval(const Src &src, unsigned blocks, cudaStream_t stream) {
-  dot_eval_kernel<C, Src><<<blocks, 256, 0, stream>>>(src);
+template <int C, int G, class Src>
+static void launch_eval(const Src &src, unsigned blocks, int chunk, cudaStream_t stream) {
+  dot_eval_kernel<C, G, Src><<<blocks, 256, 0, stream>>>(src, chunk);
 }
 
-// Setup launch, then one evaluation launch per size class up to cmax.
-template <class Src>
-static arbgpu_status launch_dot_src(arbgpu_ctx *ctx, const Src &src, int64_t ndots, int cmax,
-                                    cudaStream_t stream) {
-  if (ndots <= 0) return ARBGPU_OK;
+// Evaluation launches of classes 0..cmax; the classes of long products (5 and up) always take
+// whole warps.
+template <int G, class Src>
+static arbgpu_status launch_dot_group(arbgpu_ctx *ctx, const Src &src, int64_t ndots, int cmax,
+                                      cudaStream_t stream) {
+  constexpr int DPW = 32 / G;
   const int threads = 256;
   const int64_t cap = (int64_t)ctx->sm_count * 16;
   {
-    int64_t blocks = (ndots + 7) / 8;
+    int64_t blocks = (ndots + 8 * DPW - 1) / (8 * DPW);
     if (blocks > cap) blocks = cap;
     LaunchScope scope(ctx, stream, "dot_setup", src.units());
-    dot_setup_kernel<Src><<<(unsigned)blocks, threads, 0, stream>>>(src, cmax, ctx->status);
+    dot_setup_kernel<G, Src><<<(unsigned)blocks, threads, 0, stream>>>(src, cmax, ctx->status);
     if (cudaGetLastError() != cudaSuccess) return ARBGPU_ERR_CUDA;
   }
-  const int64_t chunks = (ndots + DOT_CHUNK - 1) / DOT_CHUNK;
+  // chunks of DPW to 8 DPW dots per warp step (at most DOT_CHUNK): as many as keeps every SM busy
+  const int64_t most = 8 * DPW < DOT_CHUNK ? 8 * DPW : DOT_CHUNK;
+  int64_t chunk = ndots / ((int64_t)ctx->sm_count * 32);
+  chunk = chunk < DPW ? DPW : (chunk > most ? most : chunk);
+  const int64_t chunks = (ndots + chunk - 1) / chunk;
   int64_t blocks = (chunks + 7) / 8;
   if (blocks > cap) blocks = cap;
+  const unsigned b = (unsigned)blocks;
+  const int ck = (int)chunk;
   for (int c = 0; c <= cmax; ++c) {
     LaunchScope scope(ctx, stream, "dot_eval", c == cmax ? src.units() : 0);
     switch (c) {
-      case 0: launch_eval<0>(src, (unsigned)blocks, stream); break;
-      case 1: launch_eval<1>(src, (unsigned)blocks, stream); break;
-      case 2: launch_eval<2>(src, (unsigned)blocks, stream); break;
-      case 3: launch_eval<3>(src, (unsigned)blocks, stream); break;
-      case 4: launch_eval<4>(src, (unsigned)blocks, stream); break;
-      case 5: launch_eval<5>(src, (unsigned)blocks, stream); break;
-      case 6: launch_eval<6>(src, (unsigned)blocks, stream); break;
-      case 7: launch_eval<7>(src, (unsigned)blocks, stream); break;
+      case 0: launch_eval<0, G>(src, b, ck, stream); break;
+      case 1: launch_eval<1, G>(src, b, ck, stream); break;
+      case 2: launch_eval<2, G>(src, b, ck, stream); break;
+      case 3: launch_eval<3, G>(src, b, ck, stream); break;
+      case 4: launch_eval<4, G>(src, b, ck, stream); break;
+      case 5: launch_eval<5, 32>(src, b, ck, stream); break;
+      case 6: launch_eval<6, 32>(src, b, ck, stream); break;
+      case 7: launch_eval<7, 32>(src, b, ck, stream); break;
       default: return ARBGPU_ERR_INVALID;
     }
     if (cudaGetLastError() != cudaSuccess) return ARBGPU_ERR_CUDA;
@@ -259,124 +272,17 @@ static arbgpu_status launch_dot_src(arbgpu_ctx *ctx, const Src &src, int64_t ndo
   return ARBGPU_OK;
 }
 
-arbgpu_status launch_batched_dot(arbgpu_ctx *ctx, const arbgpu_balls *res,
-                                 const arbgpu_balls *initial, const uint8_t *sub,
-                                 const arbgpu_balls *x, const int64_t *xoff, const int64_t *xstep,
-                                 const arbgpu_balls *y, const int64_t *yoff, const int64_t *ystep,
-                                 const int64_t *len, const int32_t *prec, int64_t batch,
-                                 int32_t prec_max, int64_t len_max, int complex_mode,
-                                 cudaStream_t stream) {
-  const int parts = complex_mode ? 2 : 1;
-  BatchDotSrc s{};
-  int maxnl = 1;
-  for (int q = 0; q < parts; ++q) {
-    s.x[q] = view_of(x[q]);
-    s.y[q] = view_of(y[q]);
-    s.out[q] = out_of(res[q]);
-    s.init[q] = initial ? view_of(initial[q]) : view_of(x[q]);
-    maxnl = x[q].nlimbs > maxnl ? x[q].nlimbs : maxnl;
-    maxnl = y[q].nlimbs > maxnl ? y[q].nlimbs : maxnl;
-    if (initial) maxnl = initial[q].nlimbs > maxnl ? initial[q].nlimbs : maxnl;
+// Setup launch, then one evaluation launch per size class up to cmax, with `group` lanes per dot.
+template <class Src>
+static arbgpu_status launch_dot_src(arbgpu_ctx *ctx, const Src &src, int64_t ndots, int cmax,
+                                    int group, cudaStream_t stream) {
+  if (ndots <= 0) return ARBGPU_OK;
+  switch (group) {
+    case 4: return launch_dot_group<4>(ctx, src, ndots, cmax, stream);
+    case 8: return launch_dot_group<8>(ctx, src, ndots, cmax, stream);
+    case 16: return launch_dot_group<16>(ctx, src, ndots, cmax, stream);
+    default: return launch_dot_group<32>(ctx, src, ndots, cmax, stream);
   }
-  if (!complex_mode) {
-    s.x[1] = s.x[0];
-    s.y[1] = s.y[0];
-    s.out[1] = s.out[0];
-    s.init[1] = s.init[0];
-  }
-  s.xoff = xoff;
-  s.xstep = xstep;
-  s.yoff = yoff;
-  s.ystep = ystep;
-  s.len = len;
-  s.precs = prec;
-  s.subs = sub;
-  s.batch = batch;
-  s.cplx = complex_mode ? 1 : 0;
-  s.has_init = initial != nullptr;
-  s.prec_max = prec_max;
-  const int64_t terms_max = (complex_mode ? 2 * len_max : len_max);
-  s.len_max = terms_max;
-  s.ndots_host = s.cplx ? 2 * batch : batch;
-  const int cmax = dot_class_for_problem(prec_max, terms_max + 1, maxnl);
-  if (cmax < 0) return ARBGPU_ERR_INVALID;
-  return launch_dot_src(ctx, s, s.cplx ? 2 * batch : batch, cmax, stream);
-}
-
-arbgpu_status launch_matmul_dot(arbgpu_ctx *ctx, const arbgpu_balls *C, const arbgpu_balls *A,
-                                const arbgpu_balls *B, int64_t M, int64_t K, int64_t N,
-                                int64_t lda, int64_t ldb, int64_t ldc, int32_t prec,
-                                int complex_mode, cudaStream_t stream) {
-  const int parts = complex_mode ? 2 : 1;
-  MatDotSrc s{};
-  int maxnl = 1;
-  for (int q = 0; q < parts; ++q) {
-    s.A[q] = view_of(A[q]);
-    s.B[q] = view_of(B[q]);
-    s.C[q] = out_of(C[q]);
-    maxnl = A[q].nlimbs > maxnl ? A[q].nlimbs : maxnl;
-    maxnl = B[q].nlimbs > maxnl ? B[q].nlimbs : maxnl;
-  }
-  if (!complex_mode) {
-    s.A[1] = s.A[0];
-    s.B[1] = s.B[0];
-    s.C[1] = s.C[0];
-  }
-  s.M = M;
-  s.K = K;
-  s.N = N;
-  s.lda = lda;
-  s.ldb = ldb;
-  s.ldc = ldc;
-  s.prec_v = prec;
-  s.cplx = complex_mode ? 1 : 0;
-  s.prec_max = prec;
-  s.len_max = complex_mode ? 2 * K : K;
-  const int cmax = dot_class_for_problem(prec, s.len_max, maxnl);
-  if (cmax < 0) return ARBGPU_ERR_INVALID;
-  return launch_dot_src(ctx, s, (complex_mode ? 2 : 1) * M * N, cmax, stream);
-}
-
-arbgpu_status launch_basecase_dot(arbgpu_ctx *ctx, const arbgpu_balls &C, const arbgpu_balls *A,
-                                  const arbgpu_balls *B, bool cplx, const arbgpu_balls &initial,
-                                  const int32_t *bk, int64_t nbk, int64_t M, int64_t N,
-                                  int64_t lda, int64_t ldb, int64_t ldc, int32_t prec,
-                                  cudaStream_t stream) {
-  BasecaseSrc s{};
-  const int parts = cplx ? 2 : 1;
-  int maxnl = initial.nlimbs;
-  for (int q = 0; q < 2; ++q) {
-    const int src = q < parts ? q : 0;
-    s.A[q] = view_of(A[src]);
-    s.B[q] = view_of(B[src]);
-    maxnl = A[src].nlimbs > maxnl ? A[src].nlimbs : maxnl;
-    maxnl = B[src].nlimbs > maxnl ? B[src].nlimbs : maxnl;
-  }
-  s.init = view_of(initial);
-  s.C = out_of(C);
-  s.bk = bk;
-  s.nbk = nbk;
-  s.M = M;
-  s.N = N;
-  s.lda = lda;
-  s.ldb = ldb;
-  s.ldc = ldc;
-  s.prec_v = prec;
-  s.prec_max = prec;
-  s.len_max = nbk;
-  const int cmax = dot_class_for_problem(prec, nbk + 1, maxnl);
-  if (cmax < 0) return ARBGPU_ERR_INVALID;
-  return launch_dot_src(ctx, s, M * N, cmax, stream);
-}
-
-arbgpu_status launch_grouped_dot(arbgpu_ctx *ctx, const GroupItem *dev_items,
-                                 const int64_t *dev_ends, int32_t count, int64_t total_dots,
-                                 int prec_max, int64_t k_max, int max_nlimbs,
-                                 cudaStream_t stream) {
-  GroupedDotSrc s{dev_items, dev_ends, count, total_dots, prec_max, 2 * k_max};
-  const int cmax = dot_class_for_problem(prec_max, 2 * k_max + 1, max_nlimbs);
-  if (cmax < 0) return ARBGPU_ERR_INVALID;
-  return launch_dot_src(ctx, s, total_dots, cmax, stream);
 }
 
 }  // namespace arbgpu
