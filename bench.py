@@ -157,6 +157,9 @@ def roofline_of(name, k, peaks, sm_mhz):
     return {"kernel": name, "ms_avg": avg_s * 1e3}
 
 
+DOT_KERNELS = ("dot_setup", "dot_eval", "dot_fused")
+
+
 def dot_work(terms_by_n, unique_bytes=None):
     """Algorithmic work of a dot-path call: terms_by_n maps limbs read per factor (n) to the number
     of terms.  mults = 4 n^2 32-bit multiplies per term (n^2 64x64->128-bit limb products);
@@ -170,10 +173,11 @@ def dot_work(terms_by_n, unique_bytes=None):
 
 
 def dot_roofline(kernels, work, calls, peaks, sm_mhz):
-    """Roofline of the dot path over the timed region: one setup launch and one launch per size
-    class each call.  The bound is whichever of HBM bytes or integer multiplies takes longer at
+    """Roofline of the dot path over the timed region: one fused launch, or one setup launch and
+    one launch per size class, each call.  The bound is whichever of HBM bytes or integer multiplies takes longer at
     peak; `achieved` divides the work of one call by the device time of one call."""
-    t_eval = kernels.get("dot_eval", {}).get("ms_total", 0.0) * 1e-3 / calls
+    t_eval = (kernels.get("dot_eval", {}).get("ms_total", 0.0) +
+              kernels.get("dot_fused", {}).get("ms_total", 0.0)) * 1e-3 / calls
     t_set = kernels.get("dot_setup", {}).get("ms_total", 0.0) * 1e-3 / calls
     t_all = t_eval + t_set
     if t_all <= 0:
@@ -182,7 +186,8 @@ def dot_roofline(kernels, work, calls, peaks, sm_mhz):
     hbm_peak = peaks.get("hbm_gbs", 6800.0)
     t_hbm = work["bytes"] / (hbm_peak * 1e9)
     t_alu = work["mults"] / (alu_peak * 1e12)
-    base = {"kernel": "dot_setup + dot_eval", "ms_per_call": t_all * 1e3,
+    names = [k for k in ("dot_setup", "dot_eval", "dot_fused") if k in kernels]
+    base = {"kernel": " + ".join(names), "ms_per_call": t_all * 1e3,
             "eval_ms_per_call": t_eval * 1e3, "terms_per_call": work["terms"],
             "traffic": None}
     if t_hbm >= t_alu:
@@ -405,10 +410,10 @@ def run_workload(args):
     roofline = None
     if kernels:
         dom = max(kernels.items(), key=lambda kv: kv[1]["ms_total"])
-        if dom[0] in ("dot_setup", "dot_eval") and work is not None:
+        if dom[0] in DOT_KERNELS and work is not None:
             roofline = dot_roofline(kernels, work, args.steps, peaks, sm_mhz)
             roofline["share_of_step"] = round(sum(
-                kernels.get(k, {}).get("share", 0) or 0 for k in ("dot_setup", "dot_eval")), 4)
+                kernels.get(k, {}).get("share", 0) or 0 for k in DOT_KERNELS), 4)
         else:
             roofline = roofline_of(dom[0], dom[1], peaks, sm_mhz)
             roofline["share_of_step"] = dom[1]["share"]
@@ -565,13 +570,13 @@ def main():
     tensor = None
     if kernels:
         dom = max(kernels.items(), key=lambda kv: kv[1]["ms_total"])
-        if dom[0] in ("dot_setup", "dot_eval"):
+        if dom[0] in DOT_KERNELS:
             n = (prec + 63) // 64
             ent = (case.M * case.K + case.K * case.N + case.M * case.N) * (8 * n + 24)
             roofline = dot_roofline(kernels, dot_work({n: macs}, unique_bytes=ent), args.steps,
                                     peaks, sm_mhz)
             roofline["share_of_step"] = round(sum(
-                kernels.get(k, {}).get("share", 0) or 0 for k in ("dot_setup", "dot_eval")), 4)
+                kernels.get(k, {}).get("share", 0) or 0 for k in DOT_KERNELS), 4)
         else:
             roofline = roofline_of(dom[0], dom[1], peaks, sm_mhz)
             roofline["share_of_step"] = dom[1]["share"]

@@ -32,7 +32,7 @@ arbgpu_status launch_basecase_dot(arbgpu_ctx *ctx, const arbgpu_balls &C, const 
   s.len_max = nbk;
   const int cmax = dot_class_for_problem(prec, nbk + 1, maxnl);
   if (cmax < 0) return ARBGPU_ERR_INVALID;
-  return launch_dot_src(ctx, s, M * N, cmax, dot_group_matrix(), stream);
+  return launch_dot_fused(ctx, s, M * N, cmax, dot_group_matrix(), stream);
 }
 
 }  // namespace arbgpu

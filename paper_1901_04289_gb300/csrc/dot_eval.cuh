@@ -642,9 +642,11 @@ __device__ void dot_eval_class(const Src &src, const typename Src::Cursor &cur,
 
 // Setup pass of dot d (Section III-C): finishes the dot (special values, limits, [0 +- 0]) or
 // parks its setup in the output entry.  CMAX bounds the classes the launch will evaluate.
+// Returns true with the setup in `su` and the dot's class in `cls` when the dot still needs its
+// evaluation; otherwise the dot has been written out.
 template <int G, class Src>
-__device__ void dot_setup(const Src &src, int64_t d, int cmax, int gl, unsigned gm, int *status) {
-  const typename Src::Cursor cur = src.cursor(d);
+__device__ bool dot_setup_core(const Src &src, const typename Src::Cursor &cur, int cmax, int gl,
+                               unsigned gm, int *status, DotSetup &su, int &cls) {
   const int prec = src.prec(cur);
   const int64_t nt = src.nterms(cur);
   const bool has_init = src.has_initial();
@@ -654,7 +656,7 @@ __device__ void dot_setup(const Src &src, int64_t d, int cmax, int gl, unsigned 
       (int64_t)out.nlimbs * 64 < prec) {
     if (gl == 0) set_status(status, ARBGPU_ERR_LIMIT);
     write_special<G>(out, oi, gl);
-    return;
+    return false;
   }
   bool special = false;
   int64_t nnz = 0;
@@ -697,18 +699,17 @@ __device__ void dot_setup(const Src &src, int64_t d, int cmax, int gl, unsigned 
   if (group_any(special, gm)) {
     if (gl == 0) set_status(status, ARBGPU_ERR_UNSUPPORTED_VALUE);
     write_special<G>(out, oi, gl);
-    return;
+    return false;
   }
   nnz = group_sum_i64<G>(nnz, gm);
   e_max = group_max_i64<G>(e_max, gm);
   e_rad = group_max_i64<G>(e_rad, gm);
   nsig_max = (int)group_max_i64<G>(nsig_max, gm);
-  DotSetup su;
   su.has_mid = e_max != INT64_MIN;
   su.has_rad = e_rad != INT64_MIN;
   if (!su.has_mid && !su.has_rad) {  // [0 +- 0]
     write_zero<G>(out, oi, gl);
-    return;
+    return false;
   }
   const int extend = bc64(nnz) + 1;
   su.n_s = dot_ns(prec, ntot, nnz);
@@ -720,9 +721,22 @@ __device__ void dot_setup(const Src &src, int64_t d, int cmax, int gl, unsigned 
   if (c < 0 || c > cmax) {
     if (gl == 0) set_status(status, ARBGPU_ERR_LIMIT);
     write_special<G>(out, oi, gl);
-    return;
+    return false;
   }
+  cls = c;
+  return true;
+}
+
+// Setup of dot d, parked in its output entry for the evaluation launch of its class.
+template <int G, class Src>
+__device__ void dot_setup(const Src &src, int64_t d, int cmax, int gl, unsigned gm, int *status) {
+  const typename Src::Cursor cur = src.cursor(d);
+  DotSetup su;
+  int c = 0;
+  if (!dot_setup_core<G>(src, cur, cmax, gl, gm, status, su, c)) return;
   if (gl == 0) {
+    const BallsOut &out = src.out_view(cur);
+    const int64_t oi = src.out_index(cur);
     out.exp[oi] = su.e_s;
     out.rad_exp[oi] = su.e_rad;
     out.flags[oi] = pack_setup(c, su);
@@ -793,6 +807,31 @@ __global__ void __launch_bounds__(256, DotClassBlocks<C>::B)
       }
       __syncwarp();
     }
+  }
+}
+
+// Setup and evaluation in one launch, every dot in class C (the largest class of the problem):
+// for sources whose dots share one precision, so that all of them need (nearly) the same class.
+template <int C, int G, class Src>
+__global__ void __launch_bounds__(256, DotClassBlocks<C>::B)
+    dot_fused_kernel(const __grid_constant__ Src src, int *status) {
+  constexpr int DPW = 32 / G;
+  const int lane = threadIdx.x & 31;
+  const int gl = lane & (G - 1);
+  const unsigned gm = group_mask<G>(lane);
+  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const int64_t nd = src.ndots();
+  for (int64_t d0 = warp * DPW; d0 < nd; d0 += nwarps * DPW) {
+    const int64_t d = d0 + lane / G;
+    if (d < nd) {
+      const typename Src::Cursor cur = src.cursor(d);
+      DotSetup su;
+      int c = 0;
+      if (dot_setup_core<G>(src, cur, C, gl, gm, status, su, c))
+        dot_eval_class<C, G>(src, cur, su, src.prec(cur), gl, gm);
+    }
+    __syncwarp();
   }
 }
 

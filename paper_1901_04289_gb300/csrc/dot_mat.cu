@@ -34,7 +34,7 @@ arbgpu_status launch_matmul_dot(arbgpu_ctx *ctx, const arbgpu_balls *C, const ar
   s.len_max = complex_mode ? 2 * K : K;
   const int cmax = dot_class_for_problem(prec, s.len_max, maxnl);
   if (cmax < 0) return ARBGPU_ERR_INVALID;
-  return launch_dot_src(ctx, s, (complex_mode ? 2 : 1) * M * N, cmax, dot_group_matrix(), stream);
+  return launch_dot_fused(ctx, s, (complex_mode ? 2 : 1) * M * N, cmax, dot_group_matrix(), stream);
 }
 
 }  // namespace arbgpu

@@ -285,4 +285,45 @@ static arbgpu_status launch_dot_src(arbgpu_ctx *ctx, const Src &src, int64_t ndo
   }
 }
 
+template <int C, int G, class Src>
+static void launch_fused(const Src &src, unsigned blocks, int *status, cudaStream_t stream) {
+  dot_fused_kernel<C, G, Src><<<blocks, 256, 0, stream>>>(src, status);
+}
+
+// One launch: setup and evaluation of every dot in class cmax, `group` lanes per dot.  For sources
+// whose dots share one precision (a matrix product), where the class hardly varies.
+template <class Src>
+static arbgpu_status launch_dot_fused(arbgpu_ctx *ctx, const Src &src, int64_t ndots, int cmax,
+                                      int group, cudaStream_t stream) {
+  if (ndots <= 0) return ARBGPU_OK;
+  const int G = cmax >= 5 ? 32 : group;
+  const int64_t per_block = 8 * (32 / G);
+  int64_t blocks = (ndots + per_block - 1) / per_block;
+  const int64_t cap = (int64_t)ctx->sm_count * 16;
+  if (blocks > cap) blocks = cap;
+  const unsigned b = (unsigned)blocks;
+  int *st = ctx->status;
+  LaunchScope scope(ctx, stream, "dot_fused", src.units());
+#define ARB_FUSED(C)                                             \
+  switch (G) {                                                   \
+    case 4: launch_fused<C, 4>(src, b, st, stream); break;       \
+    case 8: launch_fused<C, 8>(src, b, st, stream); break;       \
+    case 16: launch_fused<C, 16>(src, b, st, stream); break;     \
+    default: launch_fused<C, 32>(src, b, st, stream); break;     \
+  }
+  switch (cmax) {
+    case 0: ARB_FUSED(0); break;
+    case 1: ARB_FUSED(1); break;
+    case 2: ARB_FUSED(2); break;
+    case 3: ARB_FUSED(3); break;
+    case 4: ARB_FUSED(4); break;
+    case 5: launch_fused<5, 32>(src, b, st, stream); break;
+    case 6: launch_fused<6, 32>(src, b, st, stream); break;
+    case 7: launch_fused<7, 32>(src, b, st, stream); break;
+    default: return ARBGPU_ERR_INVALID;
+  }
+#undef ARB_FUSED
+  return cudaGetLastError() == cudaSuccess ? ARBGPU_OK : ARBGPU_ERR_CUDA;
+}
+
 }  // namespace arbgpu

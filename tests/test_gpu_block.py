@@ -157,7 +157,7 @@ def test_several_blocks_with_basecase(arb):
     h, blocks = alg2.plan(A, B, M, K, N, p)
     assert any(b[2] for b in blocks) and any(not b[2] for b in blocks)
     out, names = run_mm(arb, A, B, M, K, N, p, arb.ALG_BLOCK, trace=True)
-    assert "accumulate" in names and "dot_setup" in names and "plan" in names
+    assert "accumulate" in names and "dot_fused" in names and "plan" in names
     check_bounds(out, A, B, M, K, N, p, [(i, j) for i in range(M) for j in range(N)])
 
 
@@ -168,7 +168,7 @@ def test_several_blocks_without_basecase(arb):
     h, blocks = alg2.plan(A, B, M, K, N, p)
     assert len(blocks) >= 3 and not any(b[2] for b in blocks)
     out, names = run_mm(arb, A, B, M, K, N, p, arb.ALG_BLOCK, trace=True)
-    assert "acc_round" in names and "dot_setup" not in names
+    assert "acc_round" in names and "dot_fused" not in names
     assert names.count("accumulate") == len(blocks)
     rng = np.random.default_rng(2)
     check_bounds(out, A, B, M, K, N, p, [(int(a), int(b)) for a, b in
