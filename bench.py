@@ -417,6 +417,30 @@ def run_workload(args):
         else:
             roofline = roofline_of(dom[0], dom[1], peaks, sm_mhz)
             roofline["share_of_step"] = dom[1]["share"]
+    graph = None
+    if wl == "n32dots":
+        # latency of the call replayed from a CUDA graph (no host work between calls)
+        g = torch.cuda.CUDAGraph()
+        side = torch.cuda.Stream()
+        side.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(side):
+            step()
+        torch.cuda.current_stream().wait_stream(side)
+        with torch.cuda.graph(g):
+            step()
+        g.replay()
+        torch.cuda.synchronize()
+        reps = 200
+        ga, gb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ga.record()
+        for _ in range(reps):
+            g.replay()
+        gb.record()
+        torch.cuda.synchronize()
+        gus = ga.elapsed_time(gb) * 1e3 / reps
+        graph = {"us_per_call": gus, "GMAC_s": macs / (gus * 1e-6) / 1e9, "calls": reps,
+                 "l2": "not flushed between replays (the inputs stay in L2)"}
+        ctx.check()
     r, sample, _dt = cpu_fn(args.cpu_seconds)
     line = {"metric": "ball multiply-adds per second (complex MACs for complex)",
             "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
@@ -427,6 +451,9 @@ def run_workload(args):
             "cpu_baseline": {"value": r / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
                              "sample": sample},
             "io_bytes": {"in": inbytes, "out": outbytes}, "clocks": clocks}
+    if graph:
+        line["us_per_call"] = ms / args.steps * 1e3
+        line["graph_replay"] = graph
     print(json.dumps(line), flush=True)
 
 

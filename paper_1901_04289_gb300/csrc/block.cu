@@ -18,6 +18,7 @@
 #include <vector>
 
 #include "internal.h"
+#include "round_regs.cuh"
 #include "tc_gemm.cuh"
 
 namespace arbgpu {
@@ -325,15 +326,16 @@ __constant__ uint16_t c_pow16[CRT_MAX_MODULI * CRT_MAX_CHUNKS];
 
 // Device copies of the tables of one modulus count (in the workspace).
 struct CrtTables {
-  const uint32_t *W32;  // [NM][NW32P]
-  const uint64_t *M;
-  const uint64_t *halfM;
+  const uint32_t *Q32;   // [NM][NW32P]: M / m_t in 32-bit limbs
+  const uint32_t *M32;   // [NW32P]: M
+  const uint32_t *y;     // [NM]: (M / m_t)^-1 mod m_t
+  const float *rinv;     // [NM]: 1 / m_t
   int NM, NMW, NW32P;
 };
 
 // One exact integer product.  kind 0: digit + carry form of T itself.  kind 1 (multimodular): for
-// every modulus t, digits [t][3][Mp][Np] and carries [t][Mp][Np] of P_t = sum_k r_ik s_kj over
-// the residues, from which T follows by the Chinese remainder theorem.
+// every modulus t, z_t = (P_t mod m_t) y_t mod m_t ([t][Mp][Np] uint16 in `digits`) of the exact
+// residue product P_t = sum_k r_ik s_kj, from which T follows by the Chinese remainder theorem.
 struct IntProduct {
   const uint8_t *digits;
   const int32_t *carries;
@@ -353,99 +355,51 @@ __device__ __forceinline__ uint32_t barrett_mod(uint64_t x, uint32_t m, uint64_t
   return (uint32_t)r;
 }
 
-// T_ij from its residues: sum_t r_t W_t reduced mod M and centred into (-M/2, M/2).  The sum is
-// formed in 32-bit limbs, sixteen at a time in 64-bit register accumulators (each < NM 2^48).
+// z_t = (P_t mod m_t) y_t mod m_t of entry o, written by the residue-product GEMM (uint16 planes
+// [NM][Mp][Np] in place of digits).
+__device__ __forceinline__ uint32_t crt_z(const IntProduct &p, int t, int64_t pl, int64_t o) {
+  return __ldg((const uint16_t *)p.digits + (int64_t)t * pl + o);
+}
+
+// T_ij from its residues (Chinese remainder theorem): T = sum_t z_t Q_t - q M with
+// q = round(sum_t z_t / m_t), a two's-complement integer of nw = NMW + 1 limbs.  The sum is formed
+// in 32-bit limbs, sixteen at a time in 64-bit register accumulators (each < NM 2^48).
 __device__ int crt_assemble(const IntProduct &p, int64_t i, int64_t j, int64_t Mp, int64_t Np,
                             uint64_t *T) {
   const CrtTables &c = p.crt;
   const int nw = c.NMW + 1;
   const int64_t pl = Mp * Np, o = i * Np + j;
-  uint32_t rr[CRT_MAX_MODULI];
+  uint16_t zz[CRT_MAX_MODULI];
+  float qs = 0.f;
   for (int t = 0; t < c.NM; ++t) {
-    const uint8_t *dg = p.digits + (int64_t)t * 3 * pl + o;
-    int64_t P = (int64_t)dg[0] | ((int64_t)dg[pl] << 8) | ((int64_t)dg[2 * pl] << 16);
-    P += (int64_t)p.carries[(int64_t)t * pl + o] * (int64_t)(1 << 24);
-    const uint32_t m = c_mods[t];
-    rr[t] = P >= 0 ? barrett_mod((uint64_t)P, m, c_inv[t])
-                   : (m - barrett_mod((uint64_t)(-P), m, c_inv[t])) % m;
+    const uint32_t z = crt_z(p, t, pl, o);
+    zz[t] = (uint16_t)z;
+    qs = fmaf((float)z, __ldg(c.rinv + t), qs);
   }
-  uint64_t carry = 0;
-  for (int l0 = 0; l0 < c.NW32P; l0 += 16) {
+  const int64_t q = (int64_t)rintf(qs);
+  int64_t carry = 0;
+  for (int l0 = 0; l0 < 2 * nw; l0 += 16) {
     uint64_t acc[16];
 #pragma unroll
-    for (int q = 0; q < 16; ++q) acc[q] = 0;
+    for (int u = 0; u < 16; ++u) acc[u] = 0;
     for (int t = 0; t < c.NM; ++t) {
-      const uint32_t r = rr[t];
-      const uint4 *w4 = (const uint4 *)(c.W32 + (int64_t)t * c.NW32P + l0);
+      const uint64_t z = zz[t];
+      const uint32_t *row = c.Q32 + (int64_t)t * c.NW32P;
 #pragma unroll
-      for (int q4 = 0; q4 < 4; ++q4) {
-        const uint4 w = __ldg(w4 + q4);
-        acc[4 * q4 + 0] += (uint64_t)r * w.x;
-        acc[4 * q4 + 1] += (uint64_t)r * w.y;
-        acc[4 * q4 + 2] += (uint64_t)r * w.z;
-        acc[4 * q4 + 3] += (uint64_t)r * w.w;
-      }
+      for (int u = 0; u < 16; ++u)
+        if (l0 + u < c.NW32P) acc[u] += z * __ldg(row + l0 + u);
     }
 #pragma unroll
-    for (int q = 0; q < 16; q += 2) {
-      const uint64_t v0 = acc[q] + carry;
-      const uint64_t lo = (uint32_t)v0;
-      const uint64_t v1 = acc[q + 1] + (v0 >> 32);
-      const int k = (l0 + q) >> 1;
-      if (k < nw) T[k] = lo | ((uint64_t)(uint32_t)v1 << 32);
+    for (int u = 0; u < 16; u += 2) {
+      const int l = l0 + u;
+      const int64_t m0 = l < c.NW32P ? __ldg(c.M32 + l) : 0;
+      const int64_t m1 = l + 1 < c.NW32P ? __ldg(c.M32 + l + 1) : 0;
+      const int64_t v0 = (int64_t)acc[u] - q * m0 + carry;
+      carry = v0 >> 32;
+      const int64_t v1 = (int64_t)acc[u + 1] - q * m1 + carry;
       carry = v1 >> 32;
-    }
-  }
-  // q ~ floor(T / M) (< NM 2^16) from the leading limbs; then correct
-  const int n = c.NMW;
-  const double sc = 18446744073709551616.0;  // 2^64
-  const double tt = ((double)T[n] * sc + (double)T[n - 1]) * sc + (double)T[n - 2];
-  const double mm = (double)c.M[n - 1] * sc + (double)c.M[n - 2];
-  double qd = floor(tt / mm) - 2.0;
-  uint64_t q = qd > 0 ? (uint64_t)qd : 0;
-  if (q) {
-    u128 cy = 0;
-    uint64_t borrow = 0;
-    for (int k = 0; k <= n; ++k) {
-      cy += (u128)(k < n ? c.M[k] : 0) * q;
-      const uint64_t sub = (uint64_t)cy;
-      cy >>= 64;
-      const u128 d = (u128)T[k] - sub - borrow;
-      T[k] = (uint64_t)d;
-      borrow = (uint64_t)(d >> 64) & 1;
-    }
-  }
-  for (int it = 0; it < 8; ++it) {  // while T >= M: T -= M
-    bool ge = T[n] != 0;
-    if (!ge) {
-      ge = true;
-      for (int k = n - 1; k >= 0; --k)
-        if (T[k] != c.M[k]) {
-          ge = T[k] > c.M[k];
-          break;
-        }
-    }
-    if (!ge) break;
-    uint64_t borrow = 0;
-    for (int k = 0; k <= n; ++k) {
-      const u128 d = (u128)T[k] - (k < n ? c.M[k] : 0) - borrow;
-      T[k] = (uint64_t)d;
-      borrow = (uint64_t)(d >> 64) & 1;
-    }
-  }
-  // centre: T > (M - 1) / 2  ->  T - M (two's complement)
-  bool gt = false;
-  for (int k = n - 1; k >= 0; --k)
-    if (T[k] != c.halfM[k]) {
-      gt = T[k] > c.halfM[k];
-      break;
-    }
-  if (gt) {
-    uint64_t borrow = 0;
-    for (int k = 0; k <= n; ++k) {
-      const u128 d = (u128)T[k] - (k < n ? c.M[k] : 0) - borrow;
-      T[k] = (uint64_t)d;
-      borrow = (uint64_t)(d >> 64) & 1;
+      const int k = l >> 1;
+      if (k < nw) T[k] = (uint64_t)(uint32_t)v0 | ((uint64_t)(uint32_t)v1 << 32);
     }
   }
   return nw;
@@ -746,6 +700,194 @@ __global__ void block_round_kernel(const RoundArgs a) {
   round_store(T, nw, sigma, 0, rad, a.prec, a.C, i * a.ldc + j);
 }
 
+// ------------------------------------------------------------------------- register epilogue
+//
+// The same epilogue for products of at most NW limbs, with every limb array in registers (compile-
+// time sizes, runtime positions) and, for the multimodular engine, the Chinese-remainder weights
+// W_t and M in shared memory.
+
+// T (two's complement over NW limbs) from its digits and group carries.
+template <int NW>
+__device__ __forceinline__ void digit_assemble_regs(const IntProduct &p, int64_t i, int64_t j,
+                                                    int64_t Mp, int64_t Np, uint64_t (&T)[NW]) {
+  const uint8_t *dp = p.digits + i * Np + j;
+  const int64_t pl = Mp * Np;
+#pragma unroll
+  for (int k = 0; k < NW; ++k) {
+    uint64_t w = 0;
+#pragma unroll
+    for (int b = 0; b < 8; ++b)
+      if (8 * k + b < p.ND) w |= (uint64_t)__ldg(dp + (int64_t)(8 * k + b) * pl) << (8 * b);
+    T[k] = w;
+  }
+  for (int g = 0; g < p.groups; ++g) {
+    const int64_t c = __ldg(p.carries + ((int64_t)g * Mp + i) * Np + j);
+    if (c == 0) continue;
+    const int pos = 8 * p.ends.e[g];
+    const int li = pos >> 6, bi = pos & 63;
+    const uint64_t lo = (uint64_t)c << bi;
+    const uint64_t hi = bi ? (uint64_t)(c >> (64 - bi)) : (uint64_t)(c < 0 ? -1 : 0);
+    const uint64_t ext = c < 0 ? ~(uint64_t)0 : 0;
+    u128 sum = 0;
+#pragma unroll
+    for (int k = 0; k < NW; ++k) {
+      const uint64_t add = k < li ? 0 : (k == li ? lo : (k == li + 1 ? hi : ext));
+      sum += (u128)T[k] + add;
+      T[k] = (uint64_t)sum;
+      sum >>= 64;
+    }
+  }
+}
+
+// T from its residues (the multimodular engine) as a two's-complement integer over NW limbs:
+// T = sum_t z_t Q_t - q M.  sQ: Q32 rows of 2 NW limbs (zero padded), sM: M in 2 NW limbs, sr:
+// 1 / m_t (shared memory).
+template <int NW>
+__device__ __forceinline__ void crt_assemble_regs(const IntProduct &p, int64_t i, int64_t j,
+                                                  int64_t Mp, int64_t Np, const uint32_t *sQ,
+                                                  const uint32_t *sM, const float *sr,
+                                                  uint64_t (&T)[NW]) {
+  constexpr int L32 = 2 * NW;
+  const int64_t pl = Mp * Np, o = i * Np + j;
+  uint64_t acc[L32];
+#pragma unroll
+  for (int l = 0; l < L32; ++l) acc[l] = 0;
+  float qs = 0.f;
+  for (int t = 0; t < p.crt.NM; ++t) {
+    const uint32_t z = crt_z(p, t, pl, o);
+    qs = fmaf((float)z, sr[t], qs);
+    const uint4 *w4 = (const uint4 *)(sQ + t * L32);
+#pragma unroll
+    for (int u = 0; u < L32 / 4; ++u) {
+      const uint4 w = w4[u];
+      acc[4 * u + 0] += (uint64_t)z * w.x;
+      acc[4 * u + 1] += (uint64_t)z * w.y;
+      acc[4 * u + 2] += (uint64_t)z * w.z;
+      acc[4 * u + 3] += (uint64_t)z * w.w;
+    }
+  }
+  const int64_t q = (int64_t)rintf(qs);
+  int64_t carry = 0;
+#pragma unroll
+  for (int k = 0; k < NW; ++k) {
+    const int64_t v0 = (int64_t)acc[2 * k] - q * (int64_t)sM[2 * k] + carry;
+    carry = v0 >> 32;
+    const int64_t v1 = (int64_t)acc[2 * k + 1] - q * (int64_t)sM[2 * k + 1] + carry;
+    carry = v1 >> 32;
+    T[k] = (uint64_t)(uint32_t)v0 | ((uint64_t)(uint32_t)v1 << 32);
+  }
+}
+
+// Round T (two's complement over NW limbs) times 2^sigma to p bits and store it into entry oi of
+// C with radius >= |rounded - T 2^sigma| + extra 2^sigma + rad.
+template <int NW>
+__device__ __forceinline__ void round_store_regs(const uint64_t (&T)[NW], int64_t sigma,
+                                                 uint64_t extra, Mag rad, int prec,
+                                                 const BallsOut &C, int64_t oi) {
+  const bool neg = (T[NW - 1] >> 63) != 0;
+  uint64_t a[NW];
+  {
+    const uint64_t flip = neg ? ~(uint64_t)0 : 0;
+    u128 cc = neg ? 1 : 0;
+#pragma unroll
+    for (int k = 0; k < NW; ++k) {
+      cc += (u128)(T[k] ^ flip);
+      a[k] = (uint64_t)cc;
+      cc >>= 64;
+    }
+  }
+  int L = limbs_bitlen<NW>(a);
+  const bool zero = L == 0;
+  uint64_t ta[NW + 1];
+  Mag r1{0u, 0};
+  if (!zero)
+    round_abs_regs<NW>(a, L, prec, extra, sigma, ta, r1);
+  else
+    r1 = mag_from_u64(extra, sigma);
+  store_rounded<NW + 1, 1>(C, oi, 0, zero, neg, ta, sigma + L, mag_add_up(r1, rad));
+}
+
+// Radius bound of one block product from its two radius products (values < 2^64).
+__device__ __forceinline__ Mag product_mag_regs(const IntProduct &p, int64_t i, int64_t j,
+                                                int64_t Mp, int64_t Np, int64_t base) {
+  if (p.ND == 0) return Mag{0u, 0};
+  uint64_t acc[2];
+  digit_assemble_regs<2>(p, i, j, Mp, Np, acc);  // nonnegative and < 2^64
+  return mag_from_u64(acc[0], base);
+}
+
+__device__ __forceinline__ Mag block_radius_regs(const IntProduct &rp1, const IntProduct &rp2,
+                                                 const int64_t *rtop, const int64_t *rrad,
+                                                 const int64_t *crad, const int64_t *cplus,
+                                                 int64_t i, int64_t j, int64_t Mp, int64_t Np) {
+  Mag r{0u, 0};
+  if (rp1.ND && rtop[i] != INT64_MIN && crad[j] != INT64_MIN)
+    r = mag_add_up(r, product_mag_regs(rp1, i, j, Mp, Np, rtop[i] + crad[j] - 2 * BL_W));
+  if (rp2.ND && rrad[i] != INT64_MIN && cplus[j] != INT64_MIN)
+    r = mag_add_up(r, product_mag_regs(rp2, i, j, Mp, Np, rrad[i] + cplus[j] - 2 * BL_W));
+  return r;
+}
+
+// Shared-memory bytes of the register epilogue's tables for NW limbs.
+static size_t crt_smem_bytes(const IntProduct &p, int NW) {
+  if (p.kind != 1) return 0;
+  return ((size_t)p.crt.NM + 1) * 2 * NW * 4 + (size_t)p.crt.NM * 4;
+}
+
+template <int NW>
+__global__ void __launch_bounds__(128) block_round_regs_kernel(const RoundArgs a) {
+  constexpr int L32 = 2 * NW;
+  extern __shared__ uint4 smem_u4[];
+  uint32_t *sQ = (uint32_t *)smem_u4;
+  uint32_t *sM = nullptr;
+  float *sr = nullptr;
+  if (a.mid.kind == 1) {
+    const CrtTables &c = a.mid.crt;
+    sM = sQ + c.NM * L32;
+    sr = (float *)(sM + L32);
+    for (int k = threadIdx.x; k < (c.NM + 1) * L32; k += blockDim.x) {
+      const int t = k / L32, l = k - t * L32;
+      const uint32_t *src = t < c.NM ? c.Q32 + (int64_t)t * c.NW32P : c.M32;
+      sQ[k] = l < c.NW32P ? __ldg(src + l) : 0u;
+    }
+    for (int k = threadIdx.x; k < c.NM; k += blockDim.x) sr[k] = __ldg(c.rinv + k);
+    __syncthreads();
+  }
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= a.M * a.N) return;
+  const int64_t i = idx / a.N, j = idx - i * a.N;
+  uint64_t T[NW];
+  if (a.mid.kind == 1)
+    crt_assemble_regs<NW>(a.mid, i, j, a.Mp, a.Np, sQ, sM, sr, T);
+  else
+    digit_assemble_regs<NW>(a.mid, i, j, a.Mp, a.Np, T);
+  const bool rowz = a.rtop[i] == INT64_MIN, colz = a.ctop[j] == INT64_MIN;
+  const int64_t sigma = (rowz ? 0 : a.rbot[i]) + (colz ? 0 : a.cbot[j]);  // T * 2^sigma
+  const Mag rad =
+      block_radius_regs(a.rp1, a.rp2, a.rtop, a.rrad, a.crad, a.cplus, i, j, a.Mp, a.Np);
+  round_store_regs<NW>(T, sigma, 0, rad, a.prec, a.C, i * a.ldc + j);
+}
+
+// Limbs of the assembled product of `p` (two's complement, including the sign).
+static int product_limbs(const IntProduct &p) {
+  return p.kind == 1 ? p.crt.NMW + 1 : (8 * p.ND + 32 + 63) / 64 + 1;
+}
+
+// The rounding epilogue of one block: the register kernel of the smallest size that holds the
+// product, else the general one.
+static void launch_block_round(const RoundArgs &ra, cudaStream_t s) {
+  const int nw = product_limbs(ra.mid);
+  const unsigned blocks = (unsigned)((ra.M * ra.N + 127) / 128);
+  if (crt_smem_bytes(ra.mid, 8) <= 48 * 1024 && ra.prec < 64 * 8 && nw <= 8)
+    block_round_regs_kernel<8><<<blocks, 128, crt_smem_bytes(ra.mid, 8), s>>>(ra);
+  else if (crt_smem_bytes(ra.mid, 12) <= 48 * 1024 && ra.prec < 64 * 12 && nw <= 12)
+    block_round_regs_kernel<12><<<blocks, 128, crt_smem_bytes(ra.mid, 12), s>>>(ra);
+  else if (crt_smem_bytes(ra.mid, 16) <= 48 * 1024 && ra.prec < 64 * 16 && nw <= 16)
+    block_round_regs_kernel<16><<<blocks, 128, crt_smem_bytes(ra.mid, 16), s>>>(ra);
+  else
+    block_round_kernel<<<blocks, 128, 0, s>>>(ra);
+}
+
 // ------------------------------------------------------------------------- several blocks
 
 // Per-entry top / bottom exponents (INT64_MIN / INT64_MAX for zeros) for the planner.
@@ -1014,7 +1156,7 @@ struct BlockWs {
   // per output part: accumulator, initial balls, basecase index list
   size_t acc[2], err[2], rman[2], rexp[2], ilimbs[2], iexp[2], iflags[2], irman[2], irexp[2], bk[2];
   // multimodular engine: residue planes, residue products, tables
-  size_t resA, resB, cdig, ccar, cmods, cinv, cpow, cW, cM, chalf;
+  size_t resA, resB, cdig, ccar, cztab, czinv, cpow, cQ, cM, cy, crinv;
   size_t total;
   int Smax, NDmax, Gmax, Gr, maxb, nacc, NMmax, NMWmax;
   int64_t Kp, Mp, Np;
@@ -1099,12 +1241,13 @@ static BlockWs block_ws(arbgpu_ctx *ctx, int64_t M, int64_t K, int64_t N, int pr
   w.resB = take((size_t)2 * w.NMmax * N * w.Kp * 2);
   w.cdig = take((size_t)3 * w.NMmax * w.Mp * w.Np);
   w.ccar = take((size_t)4 * w.NMmax * w.Mp * w.Np);
-  w.cmods = take(4 * (size_t)w.NMmax);
-  w.cinv = take(8 * (size_t)w.NMmax);
+  w.cztab = take(16 * (size_t)w.NMmax);
+  w.czinv = take(8 * (size_t)w.NMmax);
   w.cpow = take(4 * (size_t)w.NMmax * CRT_MAX_CHUNKS);
-  w.cW = take(4 * (size_t)w.NMmax * ((2 * w.NMWmax + 2 + 15) / 16 * 16));
-  w.cM = take(8 * (size_t)w.NMWmax);
-  w.chalf = take(8 * (size_t)w.NMWmax);
+  w.cQ = take(4 * (size_t)w.NMmax * ((2 * w.NMWmax + 15) / 16 * 16));
+  w.cM = take(4 * (size_t)((2 * w.NMWmax + 15) / 16 * 16));
+  w.cy = take(4 * (size_t)w.NMmax);
+  w.crinv = take(4 * (size_t)w.NMmax);
   w.total = off;
   return w;
 }
@@ -1195,13 +1338,20 @@ static arbgpu_status run_block(arbgpu_ctx *ctx, const BlockWs &w, uint8_t *ws, c
   if (plan) {
     // ---- multimodular: residues, NM batched residue products, CRT in the consumer
     if (ensure_crt_constants(ctx->device) != ARBGPU_OK) return ARBGPU_ERR_CUDA;
-    CrtTables ct{(const uint32_t *)(ws + w.cW), (const uint64_t *)(ws + w.cM),
-                 (const uint64_t *)(ws + w.chalf), plan->NM, plan->NMW, plan->NW32P};
-    if (cudaMemcpyAsync(ws + w.cW, plan->W32.data(), 4 * plan->W32.size(),
+    CrtTables ct{(const uint32_t *)(ws + w.cQ), (const uint32_t *)(ws + w.cM),
+                 (const uint32_t *)(ws + w.cy), (const float *)(ws + w.crinv), plan->NM,
+                 plan->NMW, plan->NW32P};
+    if (cudaMemcpyAsync(ws + w.cQ, plan->Q32.data(), 4 * plan->Q32.size(),
                         cudaMemcpyHostToDevice, s) != cudaSuccess ||
-        cudaMemcpyAsync(ws + w.cM, plan->M.data(), 8 * plan->M.size(), cudaMemcpyHostToDevice,
+        cudaMemcpyAsync(ws + w.cM, plan->M32.data(), 4 * plan->M32.size(), cudaMemcpyHostToDevice,
                         s) != cudaSuccess ||
-        cudaMemcpyAsync(ws + w.chalf, plan->halfM.data(), 8 * plan->halfM.size(),
+        cudaMemcpyAsync(ws + w.cy, plan->y.data(), 4 * plan->y.size(), cudaMemcpyHostToDevice,
+                        s) != cudaSuccess ||
+        cudaMemcpyAsync(ws + w.crinv, plan->rinv.data(), 4 * plan->rinv.size(),
+                        cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        cudaMemcpyAsync(ws + w.cztab, plan->ztab.data(), 4 * plan->ztab.size(),
+                        cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        cudaMemcpyAsync(ws + w.czinv, plan->inv.data(), 8 * plan->inv.size(),
                         cudaMemcpyHostToDevice, s) != cudaSuccess)
       return ARBGPU_ERR_CUDA;
     __nv_bfloat16 *resA = (__nv_bfloat16 *)(ws + w.resA), *resB = (__nv_bfloat16 *)(ws + w.resB);
@@ -1220,9 +1370,12 @@ static arbgpu_status run_block(arbgpu_ctx *ctx, const BlockWs &w, uint8_t *ws, c
     if (cudaGetLastError() != cudaSuccess) return ARBGPU_ERR_CUDA;
     DigitGemmArgs g{resA, resB, (int)M, (int)N, Kp, 2, 2, 1, ws + w.cdig,
                     (int32_t *)(ws + w.ccar), "crt_gemm", NM};
+    g.zout = (uint16_t *)(ws + w.cdig);
+    g.ztab = (const uint32_t *)(ws + w.cztab);
+    g.zinv = (const uint64_t *)(ws + w.czinv);
     arbgpu_status stg = launch_digit_gemm(ctx, g, s);
     if (stg != ARBGPU_OK) return stg;
-    *mid = IntProduct{ws + w.cdig, (int32_t *)(ws + w.ccar), 3, 1, {}, 1, ct};
+    *mid = IntProduct{ws + w.cdig, nullptr, 3, 1, {}, 1, ct};
     mid->ends.e[0] = 3;
   } else {
     const int ND = SA + SB - 1;
@@ -1459,9 +1612,9 @@ arbgpu_status block_matmul(arbgpu_ctx *ctx, const arbgpu_balls *C, const arbgpu_
       {
         // work units: 32-bit multiply-adds of the CRT sums (multimodular), else entries
       const int64_t units =
-          ra.mid.kind == 1 ? M * N * ra.mid.crt.NM * (int64_t)ra.mid.crt.NW32P : M * N;
+          ra.mid.kind == 1 ? M * N * ra.mid.crt.NM * (int64_t)(2 * ra.mid.crt.NMW) : M * N;
       LaunchScope sc(ctx, s, "block_round", units);
-        block_round_kernel<<<(unsigned)((M * N + 127) / 128), 128, 0, s>>>(ra);
+        launch_block_round(ra, s);
       }
       *used_block = true;
       return cudaGetLastError() == cudaSuccess ? ARBGPU_OK : ARBGPU_ERR_CUDA;

@@ -1,7 +1,10 @@
 // Host side of the multimodular integer engine: the moduli (primes just below 2^16), their Barrett
-// reciprocals, the tables 2^(16c) mod m_t, and the Chinese-remainder weights
-// W_t = (M / m_t) * ((M / m_t)^-1 mod m_t), M = prod m_t, all computed once per modulus count and
-// cached.  (The paper's integer products use FLINT's multimodular algorithm, Section IV.)
+// reciprocals, the tables 2^(16c) mod m_t, and the Chinese-remainder data of M = prod m_t: the
+// cofactors Q_t = M / m_t, y_t = Q_t^-1 mod m_t and 1 / m_t, all computed once per modulus count and
+// cached.  An integer T with |T| < M / 8 follows from its residues r_t as
+//   T = sum_t z_t Q_t - q M,   z_t = r_t y_t mod m_t,   q = round(sum_t z_t / m_t),
+// since sum_t z_t Q_t = T (mod M) and sum_t z_t / m_t = q + T / M with |T / M| < 1/8, so a float
+// sum fixes q.  (The paper's integer products use FLINT's multimodular algorithm, Section IV.)
 #include <cmath>
 #include <map>
 #include <memory>
@@ -75,18 +78,20 @@ std::unique_ptr<CrtPlan> build_plan(int NM) {
   if (P->NMW < 2) P->NMW = 2;
   M.resize(P->NMW, 0);
   P->M = M;
-  // (M - 1) / 2 (M is odd)
-  P->halfM = M;
-  P->halfM[0] -= 1;
-  for (int k = 0; k < P->NMW; ++k) {
-    const uint64_t hi = k + 1 < P->NMW ? P->halfM[k + 1] : 0;
-    P->halfM[k] = (P->halfM[k] >> 1) | (hi << 63);
-  }
   P->inv.resize(NM);
-  P->W.assign((size_t)NM * P->NMW, 0);
+  P->y.resize(NM);
+  P->rinv.resize(NM);
+  P->NW32P = (2 * P->NMW + 15) / 16 * 16;
+  P->Q32.assign((size_t)NM * P->NW32P, 0);
+  P->M32.assign((size_t)P->NW32P, 0);
+  for (int k = 0; k < P->NMW; ++k) {
+    P->M32[2 * k] = (uint32_t)P->M[k];
+    P->M32[2 * k + 1] = (uint32_t)(P->M[k] >> 32);
+  }
   for (int t = 0; t < NM; ++t) {
     const uint32_t m = P->mods[t];
     P->inv[t] = ~(uint64_t)0 / m;
+    P->rinv[t] = (float)(1.0 / (double)m);
     std::vector<uint64_t> Q{1};
     uint64_t qmod = 1;
     for (int s = 0; s < NM; ++s)
@@ -94,17 +99,18 @@ std::unique_ptr<CrtPlan> build_plan(int NM) {
         mul_small(Q, P->mods[s]);
         qmod = qmod * (P->mods[s] % m) % m;
       }
-    mul_small(Q, inv_mod((uint32_t)qmod, m));
-    for (int k = 0; k < P->NMW && k < (int)Q.size(); ++k) P->W[(size_t)t * P->NMW + k] = Q[k];
-  }
-  P->NW32P = (2 * P->NMW + 2 + 15) / 16 * 16;
-  P->W32.assign((size_t)NM * P->NW32P, 0);
-  for (int t = 0; t < NM; ++t)
-    for (int k = 0; k < P->NMW; ++k) {
-      const uint64_t v = P->W[(size_t)t * P->NMW + k];
-      P->W32[(size_t)t * P->NW32P + 2 * k] = (uint32_t)v;
-      P->W32[(size_t)t * P->NW32P + 2 * k + 1] = (uint32_t)(v >> 32);
+    P->y[t] = inv_mod((uint32_t)qmod, m);
+    for (int k = 0; k < P->NMW && k < (int)Q.size(); ++k) {
+      P->Q32[(size_t)t * P->NW32P + 2 * k] = (uint32_t)Q[k];
+      P->Q32[(size_t)t * P->NW32P + 2 * k + 1] = (uint32_t)(Q[k] >> 32);
     }
+  }
+  P->ztab.assign((size_t)4 * NM, 0);
+  for (int t = 0; t < NM; ++t) {
+    P->ztab[4 * t] = P->mods[t];
+    P->ztab[4 * t + 1] = (uint32_t)((((uint64_t)1) << 32) / P->mods[t]);
+    P->ztab[4 * t + 2] = P->y[t];
+  }
   P->NCHP = CRT_MAX_CHUNKS;
   P->pow16.resize((size_t)NM * P->NCHP);
   for (int t = 0; t < NM; ++t) {
@@ -119,13 +125,13 @@ std::unique_ptr<CrtPlan> build_plan(int NM) {
 
 }  // namespace
 
-// Number of moduli whose product exceeds 2^bits (so signed integers of `bits` bits, sign
-// included, are recovered uniquely from their residues).
+// Number of moduli whose product M exceeds 2^(bits + 3): signed integers T of `bits` bits, sign
+// included, then satisfy |T| < M / 8, as the reconstruction requires.
 int crt_moduli_for_bits(int bits) {
   const auto &pr = primes_desc();
   double acc = 0;
   int n = 0;
-  while (n < (int)pr.size() && acc < bits + 1.0) acc += std::log2((double)pr[n++]);
+  while (n < (int)pr.size() && acc < bits + 3.0) acc += std::log2((double)pr[n++]);
   return n < 5 ? 5 : n;
 }
 

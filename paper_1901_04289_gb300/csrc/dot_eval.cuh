@@ -30,6 +30,7 @@
 #pragma once
 
 #include "common.cuh"
+#include "round_regs.cuh"
 
 namespace arbgpu {
 
@@ -296,56 +297,12 @@ __device__ __forceinline__ void acc_term(LaneAcc<NS> &acc, const uint64_t (&xa)[
 
 // ---------------------------------------------------------------- finalise (registers only)
 
-// Smallest 30-bit mag >= v * 2^base for a fixed-size limb array (the same value as
-// mag_from_limbs, without dynamically indexed arrays).
-template <int N>
-__device__ __forceinline__ Mag mag_up_regs(const uint64_t (&v)[N], int64_t base) {
-  int top = -1;
-#pragma unroll
-  for (int k = 0; k < N; ++k)
-    if (v[k]) top = k;
-  if (top < 0) return Mag{0u, 0};
-  uint64_t hi = 0, lo = 0;
-  bool rest = false;
-#pragma unroll
-  for (int k = 0; k < N; ++k) {
-    if (k == top) hi = v[k];
-    if (k == top - 1) lo = v[k];
-    if (k < top - 1) rest |= v[k] != 0;
-  }
-  const int lb = bitlen64(hi);
-  const int64_t L = (int64_t)top * 64 + lb;
-  if (L <= 64) return mag_from_u64(hi, base);
-  const uint64_t w = (lb == 64) ? hi : ((hi << (64 - lb)) | (lo >> lb));
-  const bool sticky = rest || ((lb == 64) ? (lo != 0) : ((lo << (64 - lb)) != 0));
-  uint64_t b = w >> 34;
-  if ((w & ((((uint64_t)1) << 34) - 1)) || sticky) b += 1;
-  int64_t e = base + L;
-  if (b == ((uint64_t)1 << P_RAD)) {
-    b >>= 1;
-    e += 1;
-  }
-  return Mag{(uint32_t)b, e};
-}
-
-// v <<= 64 q for 0 <= q < N (a barrel shifter over limbs: log2 N rounds of selects).
-template <int N>
-__device__ __forceinline__ void limbs_shift_up(uint64_t (&v)[N], int q) {
-#pragma unroll
-  for (int b = 1; b < N; b <<= 1) {
-    const bool on = (q & b) != 0;
-#pragma unroll
-    for (int j = N - 1; j >= 0; --j) v[j] = on ? (j >= b ? v[j - b] : 0) : v[j];
-  }
-}
-
 // Round the reduced accumulator to p bits and write output entry `oi` (Algorithm 1, step 4).
 // Every lane of the group holds the reduced sums and computes the same values; the output limbs are
 // written by the group's lanes in parallel, the scalar fields by its first lane.
 template <int NS, int G>
 __device__ void dot_finalise(const LaneAcc<NS> &acc, const DotSetup &su, int prec,
                              const BallsOut &out, int64_t oi, int gl) {
-  constexpr int NT = NS + 1;  // the top-aligned frame
   uint64_t a[NS];
   const bool neg = (acc.s[NS - 1] >> 63) != 0;
   {
@@ -358,120 +315,17 @@ __device__ void dot_finalise(const LaneAcc<NS> &acc, const DotSetup &su, int pre
       c >>= 64;
     }
   }
-  int L = 0;  // bit length of |sum|
-#pragma unroll
-  for (int k = 0; k < NS; ++k)
-    if (a[k]) L = 64 * k + bitlen64(a[k]);
+  int L = limbs_bitlen<NS>(a);
   const int64_t ulp_e = su.e_s - 64LL * su.n_s;
   const bool zero = (L == 0) || !su.has_mid;
-  uint64_t ta[NT];
+  uint64_t ta[NS + 1];
   Mag r1{0u, 0};
-  int64_t oexp = 0;
-  if (!zero) {
-    // ta = |sum| * 2^s0, top bit at 64 NT - 1 (s0 >= 65 since |sum| < 2^(64 NS - 1))
-    const int s0 = 64 * NT - L;
-    const int bs = s0 & 63;
-    ta[0] = a[0] << bs;
-#pragma unroll
-    for (int j = 1; j < NS; ++j) ta[j] = shl_funnel(a[j], a[j - 1], bs);
-    ta[NS] = shl_funnel(0, a[NS - 1], bs);
-    limbs_shift_up<NT>(ta, s0 >> 6);
-    // keep the top p bits: cut at bit c of ta (bits below c are the rounding remainder)
-    const int c = 64 * NT - prec;
-    const int cl = c >> 6, cb = c & 63;
-    const int rl = (c - 1) >> 6, rb = (c - 1) & 63;
-    uint64_t rem[NT];
-    uint64_t rword = 0, lword = 0;
-    bool sticky = false;
-#pragma unroll
-    for (int j = 0; j < NT; ++j) {
-      const uint64_t low = j < cl ? ~(uint64_t)0 : (j == cl ? ((((uint64_t)1) << cb) - 1) : 0);
-      rem[j] = ta[j] & low;
-      ta[j] &= ~low;
-      if (j == rl) rword = rem[j];
-      if (j == cl) lword = ta[j];
-      const uint64_t below_r = j < rl ? ~(uint64_t)0 : (j == rl ? ((((uint64_t)1) << rb) - 1) : 0);
-      sticky |= (rem[j] & below_r) != 0;
-    }
-    const bool rbit = (rword >> rb) & 1;
-    const bool lsb = (lword >> cb) & 1;
-    const bool up = rbit && (sticky || lsb);
-    // eps = |rounded - sum| in units of ta: 2^c - rem when rounding up, else rem
-    uint64_t E[NT + 1];
-    if (up) {
-      u128 cc = 0;
-      uint64_t borrow = 0;
-#pragma unroll
-      for (int j = 0; j < NT; ++j) {
-        const uint64_t unit = j == cl ? (((uint64_t)1) << cb) : 0;
-        cc += (u128)ta[j] + unit;
-        ta[j] = (uint64_t)cc;
-        cc >>= 64;
-        const u128 dlt = (u128)unit - rem[j] - borrow;
-        E[j] = (uint64_t)dlt;
-        borrow = (uint64_t)(dlt >> 64) & 1;
-      }
-      if ((uint64_t)cc) {  // rounded up to 2^(64 NT): one bit longer
-#pragma unroll
-        for (int j = 0; j < NT; ++j) ta[j] = 0;
-        ta[NT - 1] = ((uint64_t)1) << 63;
-        L += 1;
-      }
-    } else {
-#pragma unroll
-      for (int j = 0; j < NT; ++j) E[j] = rem[j];
-    }
-    E[NT] = 0;
-    // E += err * 2^s0 (err counts accumulator ulps)
-    {
-      const int q = s0 >> 6;
-      const uint64_t lo = acc.err << bs;
-      const uint64_t hi = bs ? (acc.err >> (64 - bs)) : 0;
-      u128 cc = 0;
-#pragma unroll
-      for (int j = 0; j < NT + 1; ++j) {
-        const uint64_t add = (j == q) ? lo : ((j == q + 1) ? hi : 0);
-        cc += (u128)E[j] + add;
-        E[j] = (uint64_t)cc;
-        cc >>= 64;
-      }
-    }
-    r1 = mag_up_regs<NT + 1>(E, ulp_e - s0);
-    oexp = ulp_e + L;
-  } else if (su.has_mid) {
+  if (!zero)
+    round_abs_regs<NS>(a, L, prec, acc.err, ulp_e, ta, r1);
+  else if (su.has_mid)
     r1 = mag_from_u64(acc.err, ulp_e);
-  }
   const Mag r2 = su.has_rad ? mag_from_u64(acc.srad, su.e_rad - P_RAD) : Mag{0u, 0};
-  const Mag r = mag_add_up(r1, r2);
-  const int nl = out.nlimbs;
-  // output limb nl-1-m is ta[NT-1-m] (m < NT), zero below
-  for (int m = gl; m < nl; m += G) {
-    uint64_t v = 0;
-    if (!zero) {
-#pragma unroll
-      for (int j = 0; j < NT; ++j)
-        if (m == NT - 1 - j) v = ta[j];
-    }
-    out.limbs[(int64_t)(nl - 1 - m) * out.stride + oi] = v;
-  }
-  if (gl == 0) {
-    uint32_t fl;
-    if (zero) {
-      out.exp[oi] = 0;
-      fl = ARBGPU_FLAG_ZERO;
-    } else {
-      // significant limbs: from the top limb down to the lowest nonzero one
-      int jmin = NT - 1;
-#pragma unroll
-      for (int j = NT - 1; j >= 0; --j)
-        if (ta[j] && NT - 1 - j < nl) jmin = j;
-      out.exp[oi] = oexp;
-      fl = (neg ? ARBGPU_FLAG_SIGN : 0u) | ((uint32_t)(NT - jmin) << ARBGPU_NSIG_SHIFT);
-    }
-    out.flags[oi] = fl;
-    out.rad_man[oi] = r.man;
-    out.rad_exp[oi] = r.man ? r.exp : 0;
-  }
+  store_rounded<NS + 1, G>(out, oi, gl, zero, neg, ta, ulp_e + L, mag_add_up(r1, r2));
 }
 
 template <int G>

@@ -72,6 +72,12 @@ struct DigitGemmArgs {
   int32_t *carries;
   const char *name;
   int batch = 1;  // independent products sharing the plane layout (item b: planes b*SA.., b*SB..)
+  // multimodular mode (SA = SB = 2, one group): item b writes z_b = (P_b mod m_b) y_b mod m_b as
+  // uint16 [batch][Mp][Np] instead of digits and carries; ztab [batch][4] = m, floor(2^32 / m),
+  // y, 0 and zinv [batch] = floor((2^64 - 1) / m)
+  uint16_t *zout = nullptr;
+  const uint32_t *ztab = nullptr;
+  const uint64_t *zinv = nullptr;
 };
 arbgpu_status launch_digit_gemm(arbgpu_ctx *ctx, const DigitGemmArgs &a, cudaStream_t stream);
 int digit_gemm_groups(arbgpu_ctx *ctx, int M, int N, int ND);
@@ -122,13 +128,16 @@ arbgpu_status launch_grouped_dot(arbgpu_ctx *ctx, const GroupItem *dev_items,
 constexpr int CRT_MAX_CHUNKS = 100;  // 16-bit chunks of a scaled integer (1600 bits)
 constexpr int CRT_MAX_MODULI = 256;
 struct CrtPlan {
-  int NM, NMW, NCHP, NW32P;       // moduli, limbs of M, columns of pow16, columns of W32
+  int NM, NMW, NCHP, NW32P;       // moduli, limbs of M, columns of pow16, columns of Q32
   std::vector<uint32_t> mods;     // m_t
   std::vector<uint64_t> inv;      // floor((2^64 - 1) / m_t)
   std::vector<uint32_t> pow16;    // [NM][NCHP]: 2^(16c) mod m_t
-  std::vector<uint64_t> W;        // [NM][NMW]: (M / m_t) * ((M / m_t)^-1 mod m_t)
-  std::vector<uint32_t> W32;      // [NM][NW32P]: W in 32-bit limbs, zero padded
-  std::vector<uint64_t> M, halfM; // M and (M - 1) / 2
+  std::vector<uint32_t> Q32;      // [NM][NW32P]: M / m_t in 32-bit limbs, zero padded
+  std::vector<uint32_t> M32;      // [NW32P]: M in 32-bit limbs
+  std::vector<uint32_t> y;        // [NM]: (M / m_t)^-1 mod m_t
+  std::vector<float> rinv;        // [NM]: 1 / m_t rounded to float
+  std::vector<uint32_t> ztab;     // [NM][4]: m_t, floor(2^32 / m_t), y_t, 0
+  std::vector<uint64_t> M;        // M
 };
 int crt_moduli_for_bits(int bits);
 const CrtPlan *crt_plan(int NM);

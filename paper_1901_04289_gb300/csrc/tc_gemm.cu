@@ -162,6 +162,8 @@ __global__ void __launch_bounds__(TG_THREADS, 1)
     const int64_t gcol = n0 + half * 64;
     uint32_t chain = 0;
     bool ok = true;
+    const bool zmode = P.zout != nullptr;  // d0 = 0, d1 = 3 in this mode
+    uint32_t zp[3][16];                     // its three digit bytes per column, packed
     for (int d = d0; d < d1 && ok; ++d) {
       const int jlo = max(0, d - (P.SB - 1)), jhi = min(d, P.SA - 1);
       const int nchains_d = ((jhi - jlo + 1) * nkb + TG_CHAIN_KB - 1) / TG_CHAIN_KB;
@@ -203,14 +205,56 @@ __global__ void __launch_bounds__(TG_THREADS, 1)
       }
 #pragma unroll
       for (int c = 0; c < 64; ++c) R[c] >>= 8;
+      if (zmode) {
+#pragma unroll
+        for (int c = 0; c < 16; ++c) {
+          if (d == 0) zp[0][c] = packed[c];
+          if (d == 1) zp[1][c] = packed[c];
+          if (d == 2) zp[2][c] = packed[c];
+        }
+        continue;
+      }
       uint4 *dst = (uint4 *)(out_digits + ((int64_t)d * P.Mp + gm) * P.Np + gcol);
 #pragma unroll
       for (int c = 0; c < 4; ++c)
         dst[c] = make_uint4(packed[4 * c], packed[4 * c + 1], packed[4 * c + 2], packed[4 * c + 3]);
     }
-    int4 *cdst = (int4 *)(out_carries + ((int64_t)group * P.Mp + gm) * P.Np + gcol);
+    if (zmode) {
+      if (ok) {
+        // P = bytes + R 2^24 exactly; |P| <= Kp (m / 2)^2 < 2^50, so P + m 2^35 is in (0, 2^52)
+        const uint32_t m = __ldg(P.ztab + 4 * bidx), i32 = __ldg(P.ztab + 4 * bidx + 1);
+        const uint32_t y = __ldg(P.ztab + 4 * bidx + 2);
+        const uint64_t i64 = __ldg(P.zinv + bidx);
+        uint32_t zz[32];
 #pragma unroll
-    for (int c = 0; c < 16; ++c) cdst[c] = make_int4(R[4 * c], R[4 * c + 1], R[4 * c + 2], R[4 * c + 3]);
+        for (int c = 0; c < 64; ++c) {
+          const int sh = 8 * (c & 3);
+          const int64_t pv = (int64_t)((zp[0][c >> 2] >> sh) & 255u) |
+                             ((int64_t)((zp[1][c >> 2] >> sh) & 255u) << 8) |
+                             ((int64_t)((zp[2][c >> 2] >> sh) & 255u) << 16) |
+                             ((int64_t)R[c] * (int64_t)(1 << 24));
+          const uint64_t x = (uint64_t)(pv + ((int64_t)m << 35));
+          uint64_t r = x - __umul64hi(x, i64) * m;
+          while (r >= m) r -= m;
+          const uint32_t ry = (uint32_t)r * y;
+          uint32_t z = ry - __umulhi(ry, i32) * m;
+          if (z >= m) z -= m;
+          if (c & 1)
+            zz[c >> 1] |= z << 16;
+          else
+            zz[c >> 1] = z;
+        }
+        uint4 *zdst = (uint4 *)(P.zout + ((int64_t)bidx * P.Mp + gm) * P.Np + gcol);
+#pragma unroll
+        for (int c = 0; c < 8; ++c)
+          zdst[c] = make_uint4(zz[4 * c], zz[4 * c + 1], zz[4 * c + 2], zz[4 * c + 3]);
+      }
+    } else {
+      int4 *cdst = (int4 *)(out_carries + ((int64_t)group * P.Mp + gm) * P.Np + gcol);
+#pragma unroll
+      for (int c = 0; c < 16; ++c)
+        cdst[c] = make_int4(R[4 * c], R[4 * c + 1], R[4 * c + 2], R[4 * c + 3]);
+    }
   }
 
   tc_fence_before();
@@ -312,6 +356,11 @@ arbgpu_status launch_digit_gemm(arbgpu_ctx *ctx, const DigitGemmArgs &a, cudaStr
   P.carries = a.carries;
   P.batch = a.batch > 0 ? a.batch : 1;
   P.status = ctx->status;
+  P.zout = a.zout;
+  P.ztab = a.ztab;
+  P.zinv = a.zinv;
+  if (a.zout && (a.SA != 2 || a.SB != 2 || a.groups != 1 || !a.ztab || !a.zinv))
+    return ARBGPU_ERR_INVALID;
   const int G = a.groups;
   if (G < 1 || G > TG_MAXG || G > P.ND) return ARBGPU_ERR_INVALID;
   P.groups = G;

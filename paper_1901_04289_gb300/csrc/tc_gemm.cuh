@@ -55,6 +55,11 @@ struct DigitGemmParams {
   int batch;                // independent products: item b uses planes [b*SA, (b+1)*SA) of A,
                             // [b*SB, (b+1)*SB) of B, and its own digits / carries
   int *status;
+  // Multimodular mode (2 x 2 digits, one group): instead of digits and carries, item b writes
+  // z_b = (P_b mod m_b) y_b mod m_b of its exact product P_b to zout[b][Mp][Np].
+  uint16_t *zout;
+  const uint32_t *ztab;     // [batch][4]: m_b, floor(2^32 / m_b), y_b, unused
+  const uint64_t *zinv;     // [batch]: floor((2^64 - 1) / m_b)
 };
 
 // ------------------------------------------------------------------------------ PTX wrappers
