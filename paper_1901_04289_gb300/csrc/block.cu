@@ -319,10 +319,9 @@ struct Ends {
 };
 
 // Per-modulus constants (the first CRT_MAX_MODULI primes below 2^16), loaded once per device:
-// m_t, floor((2^64 - 1) / m_t) and 2^(16c) mod m_t.
+// m_t and floor((2^64 - 1) / m_t).
 __constant__ uint32_t c_mods[CRT_MAX_MODULI];
 __constant__ uint64_t c_inv[CRT_MAX_MODULI];
-__constant__ uint16_t c_pow16[CRT_MAX_MODULI * CRT_MAX_CHUNKS];
 
 // Device copies of the tables of one modulus count (in the workspace).
 struct CrtTables {
@@ -435,110 +434,95 @@ __device__ __forceinline__ int assemble(const IntProduct &p, int64_t i, int64_t 
 
 // Residues of the scaled integers for the multimodular engine: X = (-1)^neg L 2^sh (as in the
 // digit split), r_t = X mod m_t in balanced form, split into two balanced bytes r_t = 256 h + l,
-// written to planes [2t] (l) and [2t + 1] (h) of [2 NM][rows][Kp].  NCH (a bound on the number of
-// 16-bit chunks of |X|) is a template argument so that the chunks stay in registers; each thread
-// takes RE consecutive entries of one row, sharing the loads of the table 2^(16c) mod m_t.
+// written to planes [2t] (l) and [2t + 1] (h) of [2 NM][rows][Kp].  |X| is cut into NCH 32-bit
+// chunks (a template bound, so they stay in registers); r_t = sum_c chunk_c (2^(32c) mod m_t)
+// reduced once (the sum is below NCH 2^48).
 
-__device__ __forceinline__ void residue_chunks(const BallsView &X, int64_t e, int64_t sh,
-                                               uint32_t *ch, int nch) {
+// Bits [32c, 32c + 32) of L 2^sh for c = 0..NCH-1 (zero outside L).
+template <int NCH>
+__device__ __forceinline__ void residue_chunks32(const BallsView &X, int64_t e, int64_t sh,
+                                                 uint32_t (&ch)[NCH]) {
   const int nl = X.nlimbs;
-  for (int c = 0; c < nch; ++c) {
-    const int64_t pos = 16LL * c - sh;
+#pragma unroll
+  for (int c = 0; c < NCH; ++c) {
+    const int64_t pos = 32LL * c - sh;  // bit of L at bit 32c of X
     uint32_t v = 0;
-    if (pos > -16 && pos < 64LL * nl) {
+    if (pos > -32 && pos < 64LL * nl) {
       if (pos >= 0) {
         const int li = (int)(pos >> 6), bi = (int)(pos & 63);
         uint64_t w = __ldg(X.limbs + (int64_t)li * X.stride + e) >> bi;
-        if (bi > 48 && li + 1 < nl) w |= __ldg(X.limbs + (int64_t)(li + 1) * X.stride + e) << (64 - bi);
-        v = (uint32_t)(w & 0xFFFFu);
+        if (bi > 32 && li + 1 < nl) w |= __ldg(X.limbs + (int64_t)(li + 1) * X.stride + e) << (64 - bi);
+        v = (uint32_t)w;
       } else {
-        v = (uint32_t)((__ldg(X.limbs + e) << (-pos)) & 0xFFFFu);
+        v = (uint32_t)(__ldg(X.limbs + e) << (-pos));
       }
     }
     ch[c] = v;
   }
 }
 
-template <int NCH, int RE>
-__global__ void residue_split_kernel(const BallsView X, bool is_b, int64_t rows, int64_t k0,
-                                     int64_t K, int64_t Kp, int64_t ld, const int64_t *bot, int NM,
-                                     __nv_bfloat16 *out) {
-  constexpr int RES_E = RE;
-  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;  // group of RES_E entries
-  const int64_t kq = Kp / RES_E;                                        // Kp is a multiple of 64
-  if (idx >= rows * kq) return;
-  const int64_t r = idx / kq, kb = (idx - (idx / kq) * kq) * RES_E;
+template <int NCH>
+__global__ void __launch_bounds__(128) residue_split_kernel(
+    const BallsView X, bool is_b, int64_t rows, int64_t k0, int64_t K, int64_t Kp, int64_t ld,
+    const int64_t *bot, int NM, const uint32_t *pw32, int pw_stride, __nv_bfloat16 *out) {
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= rows * Kp) return;
+  const int64_t r = idx / Kp, k = idx - r * Kp;
   const int64_t plane = rows * Kp;
-  __nv_bfloat16 *o = out + r * Kp + kb;
-  uint32_t ch[RES_E][NCH];
-  bool live[RES_E], neg[RES_E];
-  bool any = false;
+  __nv_bfloat16 *o = out + r * Kp + k;
+  uint32_t ch[NCH];
+  bool live = false, neg = false;
 #pragma unroll
-  for (int u = 0; u < RES_E; ++u) {
-    const int64_t k = kb + u;
-    live[u] = false;
-    neg[u] = false;
-#pragma unroll
-    for (int c = 0; c < NCH; ++c) ch[u][c] = 0;
-    if (k < K) {
-      const int64_t e = is_b ? ((k0 + k) * ld + r) : (r * ld + k0 + k);
-      const uint32_t fl = __ldg(X.flags + e);
-      if (!(fl & (ARBGPU_FLAG_ZERO | SPECIAL_MASK))) {
-        live[u] = true;
-        neg[u] = (fl & ARBGPU_FLAG_SIGN) != 0;
-        const int64_t sh = __ldg(X.exp + e) - 64LL * X.nlimbs - bot[r];
-        residue_chunks(X, e, sh, ch[u], NCH);
-        any = true;
-      }
+  for (int c = 0; c < NCH; ++c) ch[c] = 0;
+  if (k < K) {
+    const int64_t e = is_b ? ((k0 + k) * ld + r) : (r * ld + k0 + k);
+    const uint32_t fl = __ldg(X.flags + e);
+    if (!(fl & (ARBGPU_FLAG_ZERO | SPECIAL_MASK))) {
+      live = true;
+      neg = (fl & ARBGPU_FLAG_SIGN) != 0;
+      const int64_t sh = __ldg(X.exp + e) - 64LL * X.nlimbs - bot[r];
+      residue_chunks32<NCH>(X, e, sh, ch);
     }
   }
   const __nv_bfloat16 z = __int2bfloat16_rn(0);
-  if (!any) {
-    for (int t = 0; t < 2 * NM; ++t)
-#pragma unroll
-      for (int u = 0; u < RES_E; ++u) o[(int64_t)t * plane + u] = z;
+  if (!__any_sync(__activemask(), live)) {
+    for (int t = 0; t < 2 * NM; ++t) o[(int64_t)t * plane] = z;
     return;
   }
   for (int t = 0; t < NM; ++t) {
-    const uint16_t *pw = c_pow16 + t * CRT_MAX_CHUNKS;
-    uint64_t acc[RES_E];
+    const uint32_t *pw = pw32 + (int64_t)t * pw_stride;  // the same row for every thread
+    uint64_t acc = 0;
 #pragma unroll
-    for (int u = 0; u < RES_E; ++u) acc[u] = 0;
-#pragma unroll
-    for (int c = 0; c < NCH; ++c) {
-      const uint32_t w = pw[c];
-#pragma unroll
-      for (int u = 0; u < RES_E; ++u) acc[u] += (uint64_t)ch[u][c] * w;
-    }
+    for (int c = 0; c < NCH; ++c) acc += (uint64_t)ch[c] * __ldg(pw + c);
     const uint32_t m = c_mods[t];
-    const uint64_t iv = c_inv[t];
-#pragma unroll
-    for (int u = 0; u < RES_E; ++u) {
-      int32_t res = (int32_t)barrett_mod(acc[u], m, iv);
-      if (res > (int32_t)(m >> 1)) res -= (int32_t)m;
-      if (neg[u]) res = -res;
-      if (!live[u]) res = 0;
-      const int32_t lo = ((res + 128) & 255) - 128;
-      const int32_t hi = (res - lo) >> 8;
-      o[(int64_t)(2 * t) * plane + u] = __int2bfloat16_rn(lo);
-      o[(int64_t)(2 * t + 1) * plane + u] = __int2bfloat16_rn(hi);
-    }
+    int32_t res = (int32_t)barrett_mod(acc, m, c_inv[t]);
+    if (res > (int32_t)(m >> 1)) res -= (int32_t)m;
+    if (neg) res = -res;
+    if (!live) res = 0;
+    const int32_t lo = ((res + 128) & 255) - 128;
+    const int32_t hi = (res - lo) >> 8;
+    o[(int64_t)(2 * t) * plane] = __int2bfloat16_rn(lo);
+    o[(int64_t)(2 * t + 1) * plane] = __int2bfloat16_rn(hi);
   }
 }
 
+// nch: 32-bit chunks of the largest |X| of the operand.
 static void launch_residues(int nch, int64_t n, cudaStream_t s, const BallsView &X, bool is_b,
                             int64_t rows, int64_t k0, int64_t K, int64_t Kp, int64_t ld,
-                            const int64_t *bot, int NM, __nv_bfloat16 *out) {
-#define ARB_RES(NCH_, RE_)                                                                  \
-  residue_split_kernel<NCH_, RE_><<<(unsigned)((n / RE_ + 127) / 128), 128, 0, s>>>(         \
-      X, is_b, rows, k0, K, Kp, ld, bot, NM, out)
-  if (nch <= 12) ARB_RES(12, 2);
-  else if (nch <= 20) ARB_RES(20, 1);
-  else if (nch <= 28) ARB_RES(28, 1);
-  else if (nch <= 40) ARB_RES(40, 1);
-  else if (nch <= 56) ARB_RES(56, 1);
-  else if (nch <= 72) ARB_RES(72, 1);
-  else ARB_RES(CRT_MAX_CHUNKS, 1);
+                            const int64_t *bot, int NM, const uint32_t *pw32, int pw_stride,
+                            __nv_bfloat16 *out) {
+#define ARB_RES(NCH_)                                                                         \
+  residue_split_kernel<NCH_><<<(unsigned)((n + 127) / 128), 128, 0, s>>>(                     \
+      X, is_b, rows, k0, K, Kp, ld, bot, NM, pw32, pw_stride, out)
+  if (nch <= 4) ARB_RES(4);
+  else if (nch <= 6) ARB_RES(6);
+  else if (nch <= 8) ARB_RES(8);
+  else if (nch <= 11) ARB_RES(11);
+  else if (nch <= 14) ARB_RES(14);
+  else if (nch <= 18) ARB_RES(18);
+  else if (nch <= 24) ARB_RES(24);
+  else if (nch <= 34) ARB_RES(34);
+  else ARB_RES(CRT_MAX_CHUNKS32);
 #undef ARB_RES
 }
 
@@ -550,11 +534,8 @@ static arbgpu_status ensure_crt_constants(int device) {
   if (done[device & 255]) return ARBGPU_OK;
   const CrtPlan *full = crt_plan(CRT_MAX_MODULI);
   if (!full) return ARBGPU_ERR_CUDA;
-  std::vector<uint16_t> pw((size_t)CRT_MAX_MODULI * CRT_MAX_CHUNKS);
-  for (size_t q = 0; q < pw.size(); ++q) pw[q] = (uint16_t)full->pow16[q];
   if (cudaMemcpyToSymbol(c_mods, full->mods.data(), 4 * CRT_MAX_MODULI) != cudaSuccess ||
-      cudaMemcpyToSymbol(c_inv, full->inv.data(), 8 * CRT_MAX_MODULI) != cudaSuccess ||
-      cudaMemcpyToSymbol(c_pow16, pw.data(), 2 * pw.size()) != cudaSuccess)
+      cudaMemcpyToSymbol(c_inv, full->inv.data(), 8 * CRT_MAX_MODULI) != cudaSuccess)
     return ARBGPU_ERR_CUDA;
   done[device & 255] = true;
   return ARBGPU_OK;
@@ -1243,7 +1224,7 @@ static BlockWs block_ws(arbgpu_ctx *ctx, int64_t M, int64_t K, int64_t N, int pr
   w.ccar = take((size_t)4 * w.NMmax * w.Mp * w.Np);
   w.cztab = take(16 * (size_t)w.NMmax);
   w.czinv = take(8 * (size_t)w.NMmax);
-  w.cpow = take(4 * (size_t)w.NMmax * CRT_MAX_CHUNKS);
+  w.cpow = take(4 * (size_t)w.NMmax * CRT_MAX_CHUNKS32);
   w.cQ = take(4 * (size_t)w.NMmax * ((2 * w.NMWmax + 15) / 16 * 16));
   w.cM = take(4 * (size_t)((2 * w.NMWmax + 15) / 16 * 16));
   w.cy = take(4 * (size_t)w.NMmax);
@@ -1288,7 +1269,7 @@ static bool choose_crt(int SA, int SB, int NM, int64_t M, int64_t N, int64_t Kp,
   const double t_mma = 2.6e-15, t_crt = 7e-13, t_res = 2.2e-13, t_dig = 4e-12;
   const double MN = (double)M * (double)N;
   const double nw32 = 2.0 * ((16.0 * NM + 63) / 64 + 1);
-  const double nch = (double)((hA > hB ? hA : hB) + 2) / 16 + 1;
+  const double nch = (double)((hA > hB ? hA : hB) + 2) / 32 + 1;
   const double digits = t_mma * SA * SB * (double)Kp * MN + t_dig * (SA + SB) * MN;
   const double crt = t_mma * 4.0 * NM * (double)Kp * MN + t_crt * NM * nw32 * MN +
                      t_res * NM * nch * (double)Kp * (double)(M + N);
@@ -1352,20 +1333,22 @@ static arbgpu_status run_block(arbgpu_ctx *ctx, const BlockWs &w, uint8_t *ws, c
         cudaMemcpyAsync(ws + w.cztab, plan->ztab.data(), 4 * plan->ztab.size(),
                         cudaMemcpyHostToDevice, s) != cudaSuccess ||
         cudaMemcpyAsync(ws + w.czinv, plan->inv.data(), 8 * plan->inv.size(),
+                        cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        cudaMemcpyAsync(ws + w.cpow, plan->pow32.data(), 4 * plan->pow32.size(),
                         cudaMemcpyHostToDevice, s) != cudaSuccess)
       return ARBGPU_ERR_CUDA;
     __nv_bfloat16 *resA = (__nv_bfloat16 *)(ws + w.resA), *resB = (__nv_bfloat16 *)(ws + w.resB);
     {
       const int64_t n = M * Kp;
-      LaunchScope sc(ctx, s, "residues_a", n * NM * ((hA + 2 + 15) / 16 + 1));
-      launch_residues((int)((hA + 2 + 15) / 16) + 1, n, s, Av, false,
-                      M, k0, Kb, Kp, lda, ln.rbot, NM, resA);
+      LaunchScope sc(ctx, s, "residues_a", n * NM * ((hA + 2 + 31) / 32 + 1));
+      launch_residues((int)((hA + 2 + 31) / 32) + 1, n, s, Av, false, M, k0, Kb, Kp, lda,
+                      ln.rbot, NM, (const uint32_t *)(ws + w.cpow), plan->NCHP, resA);
     }
     {
       const int64_t n = N * Kp;
-      LaunchScope sc(ctx, s, "residues_b", n * NM * ((hB + 2 + 15) / 16 + 1));
-      launch_residues((int)((hB + 2 + 15) / 16) + 1, n, s, Bv, true,
-                      N, k0, Kb, Kp, ldb, ln.cbot, NM, resB);
+      LaunchScope sc(ctx, s, "residues_b", n * NM * ((hB + 2 + 31) / 32 + 1));
+      launch_residues((int)((hB + 2 + 31) / 32) + 1, n, s, Bv, true, N, k0, Kb, Kp, ldb,
+                      ln.cbot, NM, (const uint32_t *)(ws + w.cpow), plan->NCHP, resB);
     }
     if (cudaGetLastError() != cudaSuccess) return ARBGPU_ERR_CUDA;
     DigitGemmArgs g{resA, resB, (int)M, (int)N, Kp, 2, 2, 1, ws + w.cdig,

@@ -1,5 +1,5 @@
 // Host side of the multimodular integer engine: the moduli (primes just below 2^16), their Barrett
-// reciprocals, the tables 2^(16c) mod m_t, and the Chinese-remainder data of M = prod m_t: the
+// reciprocals, the tables 2^(32c) mod m_t, and the Chinese-remainder data of M = prod m_t: the
 // cofactors Q_t = M / m_t, y_t = Q_t^-1 mod m_t and 1 / m_t, all computed once per modulus count and
 // cached.  An integer T with |T| < M / 8 follows from its residues r_t as
 //   T = sum_t z_t Q_t - q M,   z_t = r_t y_t mod m_t,   q = round(sum_t z_t / m_t),
@@ -111,13 +111,13 @@ std::unique_ptr<CrtPlan> build_plan(int NM) {
     P->ztab[4 * t + 1] = (uint32_t)((((uint64_t)1) << 32) / P->mods[t]);
     P->ztab[4 * t + 2] = P->y[t];
   }
-  P->NCHP = CRT_MAX_CHUNKS;
-  P->pow16.resize((size_t)NM * P->NCHP);
+  P->NCHP = CRT_MAX_CHUNKS32;
+  P->pow32.resize((size_t)NM * P->NCHP);
   for (int t = 0; t < NM; ++t) {
     uint64_t v = 1;
     for (int c = 0; c < P->NCHP; ++c) {
-      P->pow16[(size_t)t * P->NCHP + c] = (uint32_t)v;
-      v = (v << 16) % P->mods[t];
+      P->pow32[(size_t)t * P->NCHP + c] = (uint32_t)v;
+      v = (v << 32) % P->mods[t];
     }
   }
   return P;

@@ -125,13 +125,13 @@ arbgpu_status launch_grouped_dot(arbgpu_ctx *ctx, const GroupItem *dev_items,
                                  int prec_max, int64_t k_max, int max_nlimbs, cudaStream_t stream);
 
 // Multimodular engine (crt.cu): moduli = the NM largest primes below 2^16.
-constexpr int CRT_MAX_CHUNKS = 100;  // 16-bit chunks of a scaled integer (1600 bits)
+constexpr int CRT_MAX_CHUNKS32 = 50;  // 32-bit chunks of a scaled integer (1600 bits)
 constexpr int CRT_MAX_MODULI = 256;
 struct CrtPlan {
-  int NM, NMW, NCHP, NW32P;       // moduli, limbs of M, columns of pow16, columns of Q32
+  int NM, NMW, NCHP, NW32P;       // moduli, limbs of M, columns of pow32, columns of Q32
   std::vector<uint32_t> mods;     // m_t
   std::vector<uint64_t> inv;      // floor((2^64 - 1) / m_t)
-  std::vector<uint32_t> pow16;    // [NM][NCHP]: 2^(16c) mod m_t
+  std::vector<uint32_t> pow32;    // [NM][NCHP]: 2^(32c) mod m_t
   std::vector<uint32_t> Q32;      // [NM][NW32P]: M / m_t in 32-bit limbs, zero padded
   std::vector<uint32_t> M32;      // [NW32P]: M in 32-bit limbs
   std::vector<uint32_t> y;        // [NM]: (M / m_t)^-1 mod m_t
