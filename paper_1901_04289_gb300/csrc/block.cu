@@ -91,14 +91,44 @@ __device__ __forceinline__ bool scan_range(const int32_t *blocks, int64_t K, int
   return blocks[3 * b + 2] == 0;
 }
 
-// One warp per row of A (lanes over k): row top / bottom / radius top over the scan range.
+// The scans run in three launches: the line statistics start at their identities, chunks of the
+// inner dimension fold their entries in with atomics (many warps per line), and a last pass derives
+// the per-line quantities that need the finished values (heights, |B| + R_B exponents).
+
+// rtop/rrad = INT64_MIN, rbot = INT64_MAX for `nr` rows (and the same for `nc` columns).
+__global__ void scan_init_kernel(int64_t *rtop, int64_t *rbot, int64_t *rrad, int64_t nr,
+                                 int64_t *ctop, int64_t *cbot, int64_t *crad, int64_t nc) {
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx < nr) {
+    rtop[idx] = INT64_MIN;
+    rbot[idx] = INT64_MAX;
+    rrad[idx] = INT64_MIN;
+  } else if (idx < nr + nc) {
+    const int64_t j = idx - nr;
+    ctop[j] = INT64_MIN;
+    cbot[j] = INT64_MAX;
+    crad[j] = INT64_MIN;
+  }
+}
+
+// Chunk blockIdx.z of the scan range, of `chunk` indices.
+__device__ __forceinline__ bool scan_chunk(const int32_t *blocks, int64_t K, int64_t chunk,
+                                           int64_t &k0, int64_t &k1) {
+  int64_t b0, b1;
+  if (!scan_range(blocks, K, b0, b1)) return false;
+  k0 = b0 + (int64_t)blockIdx.z * chunk;
+  k1 = k0 + chunk < b1 ? k0 + chunk : b1;
+  return k0 < k1;
+}
+
+// One warp per (row of A, chunk of k): row top / bottom / radius top folded into the row's values.
 __global__ void scan_rows_kernel(const BallsView A, int64_t M, int64_t K, int64_t lda,
-                                 const int32_t *blocks, int64_t *rtop, int64_t *rbot,
-                                 int64_t *rrad, BlockStats *st) {
+                                 const int32_t *blocks, int64_t chunk, int64_t *rtop,
+                                 int64_t *rbot, int64_t *rrad, BlockStats *st) {
   const int lane = threadIdx.x & 31;
   const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   int64_t k0, k1;
-  if (i >= M || !scan_range(blocks, K, k0, k1)) return;
+  if (i >= M || !scan_chunk(blocks, K, chunk, k0, k1)) return;
   const int64_t ob = (int64_t)blockIdx.y * M;
   st += blockIdx.y;
   int64_t top = INT64_MIN, bot = INT64_MAX, rad = INT64_MIN, pm = 0;
@@ -126,24 +156,26 @@ __global__ void scan_rows_kernel(const BallsView A, int64_t M, int64_t K, int64_
   special = __any_sync(0xffffffffu, special);
   anyrad = __any_sync(0xffffffffu, anyrad);
   if (lane == 0) {
-    rtop[ob + i] = top;
-    rbot[ob + i] = bot;
-    rrad[ob + i] = rad;
-    if (top != INT64_MIN) atomic_max_i64(&st->hA, top - bot);
-    atomic_max_i64(&st->pA, pm);
+    if (top != INT64_MIN) {
+      atomic_max_i64(rtop + ob + i, top);
+      atomic_min_i64(rbot + ob + i, bot);
+    }
+    if (rad != INT64_MIN) atomic_max_i64(rrad + ob + i, rad);
+    if (pm) atomic_max_i64(&st->pA, pm);
     if (special) atomicOr(&st->special, 1);
     if (anyrad) atomicOr(&st->radA, 1);
   }
 }
 
-// Columns of B: block (32 columns) x (32 k-slices); reads coalesced along the row.
+// Columns of B: block (32 columns) x (8 k-slices) over chunk blockIdx.z of k; reads coalesced
+// along the row, folded into the columns' values.
 __global__ void scan_cols_kernel(const BallsView B, int64_t K, int64_t N, int64_t ldb,
-                                 const int32_t *blocks, int64_t *ctop, int64_t *cbot,
-                                 int64_t *crad, int64_t *cplus, BlockStats *st) {
-  __shared__ int64_t s_top[32][33], s_bot[32][33], s_rad[32][33], s_pm[32][33];
-  __shared__ int s_flags[32][33];
+                                 const int32_t *blocks, int64_t chunk, int64_t *ctop,
+                                 int64_t *cbot, int64_t *crad, BlockStats *st) {
+  __shared__ int64_t s_top[8][33], s_bot[8][33], s_rad[8][33], s_pm[8][33];
+  __shared__ int s_flags[8][33];
   int64_t k0, k1;
-  if (!scan_range(blocks, K, k0, k1)) return;  // uniform over the CTA
+  if (!scan_chunk(blocks, K, chunk, k0, k1)) return;  // uniform over the CTA
   const int64_t ob = (int64_t)blockIdx.y * N;
   st += blockIdx.y;
   const int tx = threadIdx.x, ty = threadIdx.y;
@@ -151,7 +183,7 @@ __global__ void scan_cols_kernel(const BallsView B, int64_t K, int64_t N, int64_
   int64_t top = INT64_MIN, bot = INT64_MAX, rad = INT64_MIN, pm = 0;
   int flags = 0;
   if (j < N) {
-    for (int64_t k = k0 + ty; k < k1; k += 32) {
+    for (int64_t k = k0 + ty; k < k1; k += 8) {
       EntryScan e = scan_entry(B, k * ldb + j);
       if (e.special) flags |= 1;
       if (e.nz) {
@@ -172,24 +204,93 @@ __global__ void scan_cols_kernel(const BallsView B, int64_t K, int64_t N, int64_
   s_flags[ty][tx] = flags;
   __syncthreads();
   if (ty == 0 && j < N) {
-    for (int y = 1; y < 32; ++y) {
+    for (int y = 1; y < 8; ++y) {
       top = max((long long)top, (long long)s_top[y][tx]);
       bot = min((long long)bot, (long long)s_bot[y][tx]);
       rad = max((long long)rad, (long long)s_rad[y][tx]);
       pm = max((long long)pm, (long long)s_pm[y][tx]);
       flags |= s_flags[y][tx];
     }
-    ctop[ob + j] = top;
-    cbot[ob + j] = bot;
-    crad[ob + j] = rad;
-    // |b| + r_b < 2^(max(top, rexp) + 1)
-    const int64_t mx = top > rad ? top : rad;
-    cplus[ob + j] = mx == INT64_MIN ? INT64_MIN : mx + 1;
-    if (top != INT64_MIN) atomic_max_i64(&st->hB, top - bot);
-    atomic_max_i64(&st->pB, pm);
+    if (top != INT64_MIN) {
+      atomic_max_i64(ctop + ob + j, top);
+      atomic_min_i64(cbot + ob + j, bot);
+    }
+    if (rad != INT64_MIN) atomic_max_i64(crad + ob + j, rad);
+    if (pm) atomic_max_i64(&st->pB, pm);
     if (flags & 1) atomicOr(&st->special, 1);
     if (flags & 2) atomicOr(&st->radB, 1);
   }
+}
+
+// Row / column heights into the statistics, and cplus = exponent bound of |b| + r_b per column
+// (|b| + r_b < 2^(max(top, rexp) + 1)).  Rows [0, M) then columns [0, N) of each of the
+// gridDim.y scan ranges.
+__global__ void scan_finish_kernel(const int64_t *rtop, const int64_t *rbot, int64_t M,
+                                   const int64_t *ctop, const int64_t *cbot, const int64_t *crad,
+                                   int64_t *cplus, int64_t N, BlockStats *st_rows,
+                                   BlockStats *st_cols) {
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int b = blockIdx.y;
+  if (idx < M) {
+    const int64_t o = (int64_t)b * M + idx;
+    if (rtop[o] != INT64_MIN) atomic_max_i64(&st_rows[b].hA, rtop[o] - rbot[o]);
+  } else if (idx < M + N) {
+    const int64_t o = (int64_t)b * N + (idx - M);
+    const int64_t top = ctop[o], rad = crad[o];
+    if (top != INT64_MIN) atomic_max_i64(&st_cols[b].hB, top - cbot[o]);
+    if (cplus) {
+      const int64_t mx = top > rad ? top : rad;
+      cplus[o] = mx == INT64_MIN ? INT64_MIN : mx + 1;
+    }
+  }
+}
+
+// Inner-dimension chunk of the scans so that about `lines_target` warps or CTAs cover a range of
+// `len` indices for `lines` lines.
+static int64_t scan_chunk_len(int64_t len, int64_t lines, int64_t target, int64_t minchunk) {
+  int64_t z = target / (lines > 0 ? lines : 1);
+  if (z < 1) z = 1;
+  int64_t chunk = (len + z - 1) / z;
+  if (chunk < minchunk) chunk = minchunk;
+  return chunk;
+}
+
+// Scans of the rows of X (M x K) and the columns of Y (K x N) over the whole inner range
+// (blocks = null, nb = 1) or over each of the nb ranges of a plan: the line statistics and the
+// per-range BlockStats (rows into st_rows, columns into st_cols; both must hold their identities).
+static arbgpu_status run_scans(arbgpu_ctx *ctx, cudaStream_t s, const BallsView &Xv, int64_t M,
+                               int64_t K, int64_t ldx, const BallsView &Yv, int64_t N,
+                               int64_t ldy, const int32_t *blocks, int nb, int64_t kmax,
+                               int64_t *rtop, int64_t *rbot, int64_t *rrad, int64_t *ctop,
+                               int64_t *cbot, int64_t *crad, int64_t *cplus,
+                               BlockStats *st_rows, BlockStats *st_cols) {
+  {
+    const int64_t n = (M + N) * nb;
+    LaunchScope sc(ctx, s, "scan_init", n);
+    scan_init_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(rtop, rbot, rrad, M * nb, ctop,
+                                                                 cbot, crad, N * nb);
+  }
+  const int64_t rchunk = scan_chunk_len(kmax, M * nb, 8192, 64);
+  const int64_t cchunk = scan_chunk_len(kmax, (N + 31) / 32 * nb, 1024, 32);
+  {
+    LaunchScope sc(ctx, s, "scan_rows", M * K);
+    scan_rows_kernel<<<dim3((unsigned)((M * 32 + 255) / 256), (unsigned)nb,
+                            (unsigned)((kmax + rchunk - 1) / rchunk)),
+                       256, 0, s>>>(Xv, M, K, ldx, blocks, rchunk, rtop, rbot, rrad, st_rows);
+  }
+  {
+    LaunchScope sc(ctx, s, "scan_cols", K * N);
+    scan_cols_kernel<<<dim3((unsigned)((N + 31) / 32), (unsigned)nb,
+                            (unsigned)((kmax + cchunk - 1) / cchunk)),
+                       dim3(32, 8), 0, s>>>(Yv, K, N, ldy, blocks, cchunk, ctop, cbot, crad,
+                                            st_cols);
+  }
+  {
+    LaunchScope sc(ctx, s, "scan_finish", (M + N) * nb);
+    scan_finish_kernel<<<dim3((unsigned)((M + N + 255) / 256), (unsigned)nb), 256, 0, s>>>(
+        rtop, rbot, M, ctop, cbot, crad, cplus, N, st_rows, st_cols);
+  }
+  return cudaGetLastError() == cudaSuccess ? ARBGPU_OK : ARBGPU_ERR_CUDA;
 }
 
 // Balanced base-256 digits of X = (-1)^neg * L * 2^sh, L the midpoint's limb integer (nl limbs,
@@ -1461,16 +1562,12 @@ static arbgpu_status accumulate_product(arbgpu_ctx *ctx, const BlockWs &w, uint8
                 (int64_t *)(ws + w.bctop), (int64_t *)(ws + w.bcbot), (int64_t *)(ws + w.bcrad),
                 (int64_t *)(ws + w.bcplus)};
     {
-      LaunchScope sc(ctx, s, "scan_rows", M * K);
-      scan_rows_kernel<<<dim3((unsigned)((M * 32 + 255) / 256), (unsigned)hnb), 256, 0, s>>>(
-          Xv, M, K, ldx, blocks, (int64_t *)per.rtop, (int64_t *)per.rbot, (int64_t *)per.rrad,
-          bst);
-    }
-    {
-      LaunchScope sc(ctx, s, "scan_cols", K * N);
-      scan_cols_kernel<<<dim3((unsigned)((N + 31) / 32), (unsigned)hnb), dim3(32, 32), 0, s>>>(
-          Yv, K, N, ldy, blocks, (int64_t *)per.ctop, (int64_t *)per.cbot, (int64_t *)per.crad,
-          (int64_t *)per.cplus, bst);
+      // chunks sized for the whole range (a block's chunks beyond its end return at once)
+      const arbgpu_status sst = run_scans(
+          ctx, s, Xv, M, K, ldx, Yv, N, ldy, blocks, hnb, K, (int64_t *)per.rtop,
+          (int64_t *)per.rbot, (int64_t *)per.rrad, (int64_t *)per.ctop, (int64_t *)per.cbot,
+          (int64_t *)per.crad, (int64_t *)per.cplus, bst, bst);
+      if (sst != ARBGPU_OK) return sst;
     }
     if (cudaMemcpyAsync(hbs.data(), bst, sizeof(BlockStats) * hnb, cudaMemcpyDeviceToHost, s) !=
             cudaSuccess ||
@@ -1543,18 +1640,12 @@ arbgpu_status block_matmul(arbgpu_ctx *ctx, const arbgpu_balls *C, const arbgpu_
     colsL[q] = Lines{nullptr, nullptr, nullptr, (int64_t *)(ws + w.pctop[q]),
                      (int64_t *)(ws + w.pcbot[q]), (int64_t *)(ws + w.pcrad[q]),
                      (int64_t *)(ws + w.pcplus[q])};
-    {
-      LaunchScope sc(ctx, s, "scan_rows", M * K);
-      scan_rows_kernel<<<(unsigned)((M * 32 + 255) / 256), 256, 0, s>>>(
-          Av[q], M, K, lda, nullptr, (int64_t *)rowsL[q].rtop, (int64_t *)rowsL[q].rbot,
-          (int64_t *)rowsL[q].rrad, pst + q);
-    }
-    {
-      LaunchScope sc(ctx, s, "scan_cols", K * N);
-      scan_cols_kernel<<<(unsigned)((N + 31) / 32), dim3(32, 32), 0, s>>>(
-          Bv[q], K, N, ldb, nullptr, (int64_t *)colsL[q].ctop, (int64_t *)colsL[q].cbot,
-          (int64_t *)colsL[q].crad, (int64_t *)colsL[q].cplus, pst + 2 + q);
-    }
+    const arbgpu_status sst = run_scans(
+        ctx, s, Av[q], M, K, lda, Bv[q], N, ldb, nullptr, 1, K, (int64_t *)rowsL[q].rtop,
+        (int64_t *)rowsL[q].rbot, (int64_t *)rowsL[q].rrad, (int64_t *)colsL[q].ctop,
+        (int64_t *)colsL[q].cbot, (int64_t *)colsL[q].crad, (int64_t *)colsL[q].cplus, pst + q,
+        pst + 2 + q);
+    if (sst != ARBGPU_OK) return sst;
   }
   BlockStats hst[4];
   if (cudaMemcpyAsync(hst, pst, sizeof(hst), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
