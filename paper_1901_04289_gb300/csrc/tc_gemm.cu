@@ -33,10 +33,10 @@ __global__ void __launch_bounds__(TG_THREADS, 1)
   const int ntiles = P.tiles_m * P.tiles_n;
   const int tile = blockIdx.x % ntiles;
   const int group = (blockIdx.x / ntiles) % P.groups;
-  const int bidx = blockIdx.x / (ntiles * P.groups);  // batch item
-  const int zA = bidx * P.SA, zB = bidx * P.SB;       // its first digit plane
-  uint8_t *const out_digits = P.digits + (int64_t)bidx * P.ND * P.Mp * P.Np;
-  int32_t *const out_carries = P.carries + (int64_t)bidx * P.groups * P.Mp * P.Np;
+  // batch items [b_first, b_last) run one after the other in this CTA, their pipelines back to back
+  const int bchunk = blockIdx.x / (ntiles * P.groups);
+  const int b_first = bchunk * P.ipc;
+  const int b_last = min(P.batch, b_first + P.ipc);
   const int mt = tile / P.tiles_n, nt = tile % P.tiles_n;
   const int m0 = mt * TG_BM, n0 = nt * TG_BN;
   const int d0 = P.dstart[group], d1 = P.dstart[group + 1];
@@ -77,7 +77,9 @@ __global__ void __launch_bounds__(TG_THREADS, 1)
       tma_prefetch_desc(&tmB);
       uint32_t item = 0;
       bool ok = true;
+      for (int bi = b_first; bi < b_last && ok; ++bi)
       for (int d = d0; d < d1 && ok; ++d) {
+        const int zA = bi * P.SA, zB = bi * P.SB;  // the item's first digit planes
         const int jlo = max(0, d - (P.SB - 1)), jhi = min(d, P.SA - 1);
         for (int j = jlo; j <= jhi && ok; ++j) {
           const int l = d - j;
@@ -108,6 +110,7 @@ __global__ void __launch_bounds__(TG_THREADS, 1)
       const uint32_t idesc = idesc_bf16_f32(TG_BM, TG_BN);
       uint32_t item = 0, chain = 0;
       bool ok = true;
+      for (int bi = b_first; bi < b_last && ok; ++bi)
       for (int d = d0; d < d1 && ok; ++d) {
         const int jlo = max(0, d - (P.SB - 1)), jhi = min(d, P.SA - 1);
         int kbc = 0;
@@ -155,14 +158,17 @@ __global__ void __launch_bounds__(TG_THREADS, 1)
     const int half = (warp - 2) >> 2;   // which 64 of the tile's 128 columns
     const int row = 32 * q + lane;
     const uint32_t lane_addr = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(half * 64);
-    int32_t R[64];
-#pragma unroll
-    for (int c = 0; c < 64; ++c) R[c] = 0;
     const int64_t gm = m0 + row;
     const int64_t gcol = n0 + half * 64;
     uint32_t chain = 0;
     bool ok = true;
     const bool zmode = P.zout != nullptr;  // d0 = 0, d1 = 3 in this mode
+    for (int bi = b_first; bi < b_last && ok; ++bi) {
+    uint8_t *const out_digits = P.digits + (int64_t)bi * P.ND * P.Mp * P.Np;
+    int32_t *const out_carries = P.carries + (int64_t)bi * P.groups * P.Mp * P.Np;
+    int32_t R[64];
+#pragma unroll
+    for (int c = 0; c < 64; ++c) R[c] = 0;
     uint32_t zp[3][16];                     // its three digit bytes per column, packed
     for (int d = d0; d < d1 && ok; ++d) {
       const int jlo = max(0, d - (P.SB - 1)), jhi = min(d, P.SA - 1);
@@ -222,9 +228,9 @@ __global__ void __launch_bounds__(TG_THREADS, 1)
     if (zmode) {
       if (ok) {
         // P = bytes + R 2^24 exactly; |P| <= Kp (m / 2)^2 < 2^50, so P + m 2^35 is in (0, 2^52)
-        const uint32_t m = __ldg(P.ztab + 4 * bidx), i32 = __ldg(P.ztab + 4 * bidx + 1);
-        const uint32_t y = __ldg(P.ztab + 4 * bidx + 2);
-        const uint64_t i64 = __ldg(P.zinv + bidx);
+        const uint32_t m = __ldg(P.ztab + 4 * bi), i32 = __ldg(P.ztab + 4 * bi + 1);
+        const uint32_t y = __ldg(P.ztab + 4 * bi + 2);
+        const uint64_t i64 = __ldg(P.zinv + bi);
         uint32_t zz[32];
 #pragma unroll
         for (int c = 0; c < 64; ++c) {
@@ -244,17 +250,18 @@ __global__ void __launch_bounds__(TG_THREADS, 1)
           else
             zz[c >> 1] = z;
         }
-        uint4 *zdst = (uint4 *)(P.zout + ((int64_t)bidx * P.Mp + gm) * P.Np + gcol);
+        uint4 *zdst = (uint4 *)(P.zout + ((int64_t)bi * P.Mp + gm) * P.Np + gcol);
 #pragma unroll
         for (int c = 0; c < 8; ++c)
           zdst[c] = make_uint4(zz[4 * c], zz[4 * c + 1], zz[4 * c + 2], zz[4 * c + 3]);
       }
-    } else {
+    } else if (ok) {
       int4 *cdst = (int4 *)(out_carries + ((int64_t)group * P.Mp + gm) * P.Np + gcol);
 #pragma unroll
       for (int c = 0; c < 16; ++c)
         cdst[c] = make_int4(R[4 * c], R[4 * c + 1], R[4 * c + 2], R[4 * c + 3]);
     }
+    }  // batch items
   }
 
   tc_fence_before();
@@ -383,7 +390,22 @@ arbgpu_status launch_digit_gemm(arbgpu_ctx *ctx, const DigitGemmArgs &a, cudaStr
       return ARBGPU_ERR_CUDA;
     attr_set[dev] = true;
   }
-  const int64_t grid = (int64_t)P.tiles_m * P.tiles_n * G * P.batch;
+  // batch items per CTA: the fewest waves x items over the SMs (items of a CTA run back to back)
+  {
+    const int64_t per = (int64_t)P.tiles_m * P.tiles_n * G;
+    int best = 1;
+    int64_t best_cost = INT64_MAX;
+    for (int ipc = 1; ipc <= P.batch; ++ipc) {
+      const int64_t ctas = per * ((P.batch + ipc - 1) / ipc);
+      const int64_t cost = (ctas + ctx->sm_count - 1) / ctx->sm_count * ipc;
+      if (cost < best_cost) {
+        best_cost = cost;
+        best = ipc;
+      }
+    }
+    P.ipc = best;
+  }
+  const int64_t grid = (int64_t)P.tiles_m * P.tiles_n * G * ((P.batch + P.ipc - 1) / P.ipc);
   if (grid > 0x7fffffff) return ARBGPU_ERR_LIMIT;
   LaunchScope scope(ctx, stream, a.name ? a.name : "digit_gemm",
                     (int64_t)(a.SA) * a.SB * (int64_t)a.M * a.N * a.Kp * P.batch);

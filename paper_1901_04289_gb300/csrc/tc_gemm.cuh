@@ -54,6 +54,7 @@ struct DigitGemmParams {
   int64_t Mp, Np;           // padded leading sizes (multiples of the tile)
   int batch;                // independent products: item b uses planes [b*SA, (b+1)*SA) of A,
                             // [b*SB, (b+1)*SB) of B, and its own digits / carries
+  int ipc;                  // batch items per CTA (consecutive, run back to back)
   int *status;
   // Multimodular mode (2 x 2 digits, one group): instead of digits and carries, item b writes
   // z_b = (P_b mod m_b) y_b mod m_b of its exact product P_b to zout[b][Mp][Np].
