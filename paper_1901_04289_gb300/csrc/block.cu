@@ -566,6 +566,14 @@ template <int NCH>
 __global__ void __launch_bounds__(128) residue_split_kernel(
     const BallsView X, bool is_b, int64_t rows, int64_t k0, int64_t K, int64_t Kp, int64_t ld,
     const int64_t *bot, int NM, const uint32_t *pw32, int pw_stride, __nv_bfloat16 *out) {
+  constexpr int NC4 = (NCH + 3) / 4 * 4;  // table row in shared memory, padded for 16-byte loads
+  extern __shared__ uint4 s_pw4[];
+  uint32_t *s_pw = (uint32_t *)s_pw4;
+  for (int q = threadIdx.x; q < NM * NC4; q += blockDim.x) {
+    const int t = q / NC4, c = q - t * NC4;
+    s_pw[q] = c < NCH ? __ldg(pw32 + (int64_t)t * pw_stride + c) : 0u;
+  }
+  __syncthreads();
   const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= rows * Kp) return;
   const int64_t r = idx / Kp, k = idx - r * Kp;
@@ -591,10 +599,16 @@ __global__ void __launch_bounds__(128) residue_split_kernel(
     return;
   }
   for (int t = 0; t < NM; ++t) {
-    const uint32_t *pw = pw32 + (int64_t)t * pw_stride;  // the same row for every thread
+    const uint4 *pw = (const uint4 *)(s_pw + t * NC4);  // the same row for every thread
     uint64_t acc = 0;
 #pragma unroll
-    for (int c = 0; c < NCH; ++c) acc += (uint64_t)ch[c] * __ldg(pw + c);
+    for (int c4 = 0; c4 < NC4 / 4; ++c4) {
+      const uint4 w = pw[c4];
+      if (4 * c4 + 0 < NCH) acc += (uint64_t)ch[4 * c4 + 0] * w.x;
+      if (4 * c4 + 1 < NCH) acc += (uint64_t)ch[4 * c4 + 1] * w.y;
+      if (4 * c4 + 2 < NCH) acc += (uint64_t)ch[4 * c4 + 2] * w.z;
+      if (4 * c4 + 3 < NCH) acc += (uint64_t)ch[4 * c4 + 3] * w.w;
+    }
     const uint32_t m = c_mods[t];
     int32_t res = (int32_t)barrett_mod(acc, m, c_inv[t]);
     if (res > (int32_t)(m >> 1)) res -= (int32_t)m;
@@ -613,7 +627,8 @@ static void launch_residues(int nch, int64_t n, cudaStream_t s, const BallsView 
                             const int64_t *bot, int NM, const uint32_t *pw32, int pw_stride,
                             __nv_bfloat16 *out) {
 #define ARB_RES(NCH_)                                                                         \
-  residue_split_kernel<NCH_><<<(unsigned)((n + 127) / 128), 128, 0, s>>>(                     \
+  residue_split_kernel<NCH_><<<(unsigned)((n + 127) / 128), 128,                              \
+                               (size_t)NM * ((NCH_ + 3) / 4 * 4) * 4, s>>>(                   \
       X, is_b, rows, k0, K, Kp, ld, bot, NM, pw32, pw_stride, out)
   if (nch <= 4) ARB_RES(4);
   else if (nch <= 6) ARB_RES(6);
@@ -835,17 +850,27 @@ __device__ __forceinline__ void crt_assemble_regs(const IntProduct &p, int64_t i
 #pragma unroll
   for (int l = 0; l < L32; ++l) acc[l] = 0;
   float qs = 0.f;
-  for (int t = 0; t < p.crt.NM; ++t) {
-    const uint32_t z = crt_z(p, t, pl, o);
-    qs = fmaf((float)z, sr[t], qs);
-    const uint4 *w4 = (const uint4 *)(sQ + t * L32);
+  const int NM = p.crt.NM;
+  for (int t0 = 0; t0 < NM; t0 += 8) {
+    // the residues of eight moduli are requested together
+    uint32_t zb[8];
 #pragma unroll
-    for (int u = 0; u < L32 / 4; ++u) {
-      const uint4 w = w4[u];
-      acc[4 * u + 0] += (uint64_t)z * w.x;
-      acc[4 * u + 1] += (uint64_t)z * w.y;
-      acc[4 * u + 2] += (uint64_t)z * w.z;
-      acc[4 * u + 3] += (uint64_t)z * w.w;
+    for (int u = 0; u < 8; ++u) zb[u] = t0 + u < NM ? crt_z(p, t0 + u, pl, o) : 0u;
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      if (t0 + u >= NM) break;
+      const int t = t0 + u;
+      const uint32_t z = zb[u];
+      qs = fmaf((float)z, sr[t], qs);
+      const uint4 *w4 = (const uint4 *)(sQ + t * L32);
+#pragma unroll
+      for (int q4 = 0; q4 < L32 / 4; ++q4) {
+        const uint4 w = w4[q4];
+        acc[4 * q4 + 0] += (uint64_t)z * w.x;
+        acc[4 * q4 + 1] += (uint64_t)z * w.y;
+        acc[4 * q4 + 2] += (uint64_t)z * w.z;
+        acc[4 * q4 + 3] += (uint64_t)z * w.w;
+      }
     }
   }
   const int64_t q = (int64_t)rintf(qs);
@@ -1390,7 +1415,9 @@ static arbgpu_status run_block(arbgpu_ctx *ctx, const BlockWs &w, uint8_t *ws, c
   const int NM = crt_moduli_for_bits((int)((hA > 0 ? hA : 0) + (hB > 0 ? hB : 0) +
                                            bit_length(Kb) + 2));
   const CrtPlan *plan = nullptr;
-  if (choose_crt(SA, SB, NM, M, N, Kp, hA, hB) && NM <= w.NMmax) {
+  const int nch32 = (int)(((hA > hB ? hA : hB) + 2 + 31) / 32) + 1;
+  const size_t res_smem = (size_t)NM * ((nch32 + 3) / 4 * 4) * 4;  // residue kernel's table
+  if (choose_crt(SA, SB, NM, M, N, Kp, hA, hB) && NM <= w.NMmax && res_smem <= 48 * 1024) {
     plan = crt_plan(NM);
     if (plan && plan->NMW + 1 > RD_MAXW) plan = nullptr;
   }
