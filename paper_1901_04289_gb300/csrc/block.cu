@@ -420,9 +420,10 @@ struct Ends {
 };
 
 // Per-modulus constants (the first CRT_MAX_MODULI primes below 2^16), loaded once per device:
-// m_t and floor((2^64 - 1) / m_t).
+// m_t, floor((2^64 - 1) / m_t) and floor(2^32 / m_t).
 __constant__ uint32_t c_mods[CRT_MAX_MODULI];
 __constant__ uint64_t c_inv[CRT_MAX_MODULI];
+__constant__ uint32_t c_inv32[CRT_MAX_MODULI];  // floor(2^32 / m_t)
 
 // Device copies of the tables of one modulus count (in the workspace).
 struct CrtTables {
@@ -434,8 +435,8 @@ struct CrtTables {
 };
 
 // One exact integer product.  kind 0: digit + carry form of T itself.  kind 1 (multimodular): for
-// every modulus t, z_t = (P_t mod m_t) y_t mod m_t ([t][Mp][Np] uint16 in `digits`) of the exact
-// residue product P_t = sum_k r_ik s_kj, from which T follows by the Chinese remainder theorem.
+// every modulus t, z_t = P_t mod m_t ([t][Mp][Np] uint16 in `digits`) of the exact residue product
+// P_t = sum_k r_ik (s_kj y_t mod m_t), from which T follows by the Chinese remainder theorem.
 struct IntProduct {
   const uint8_t *digits;
   const int32_t *carries;
@@ -455,8 +456,8 @@ __device__ __forceinline__ uint32_t barrett_mod(uint64_t x, uint32_t m, uint64_t
   return (uint32_t)r;
 }
 
-// z_t = (P_t mod m_t) y_t mod m_t of entry o, written by the residue-product GEMM (uint16 planes
-// [NM][Mp][Np] in place of digits).
+// z_t = P_t y_t mod m_t of entry o, written by the residue-product GEMM (uint16 planes [NM][Mp][Np]
+// in place of digits; the right-hand residues carry the factor y_t).
 __device__ __forceinline__ uint32_t crt_z(const IntProduct &p, int t, int64_t pl, int64_t o) {
   return __ldg((const uint16_t *)p.digits + (int64_t)t * pl + o);
 }
@@ -565,7 +566,8 @@ __device__ __forceinline__ void residue_chunks32(const BallsView &X, int64_t e, 
 template <int NCH>
 __global__ void __launch_bounds__(128) residue_split_kernel(
     const BallsView X, bool is_b, int64_t rows, int64_t k0, int64_t K, int64_t Kp, int64_t ld,
-    const int64_t *bot, int NM, const uint32_t *pw32, int pw_stride, __nv_bfloat16 *out) {
+    const int64_t *bot, int NM, const uint32_t *pw32, int pw_stride, const uint32_t *ymul,
+    __nv_bfloat16 *out) {
   constexpr int NC4 = (NCH + 3) / 4 * 4;  // table row in shared memory, padded for 16-byte loads
   extern __shared__ uint4 s_pw4[];
   uint32_t *s_pw = (uint32_t *)s_pw4;
@@ -611,6 +613,12 @@ __global__ void __launch_bounds__(128) residue_split_kernel(
     }
     const uint32_t m = c_mods[t];
     int32_t res = (int32_t)barrett_mod(acc, m, c_inv[t]);
+    if (ymul) {  // res y < 2^32: one 32-bit Barrett step and one correction
+      const uint32_t x = (uint32_t)res * __ldg(ymul + t);
+      uint32_t r2 = x - __umulhi(x, c_inv32[t]) * m;
+      if (r2 >= m) r2 -= m;
+      res = (int32_t)r2;
+    }
     if (res > (int32_t)(m >> 1)) res -= (int32_t)m;
     if (neg) res = -res;
     if (!live) res = 0;
@@ -625,11 +633,11 @@ __global__ void __launch_bounds__(128) residue_split_kernel(
 static void launch_residues(int nch, int64_t n, cudaStream_t s, const BallsView &X, bool is_b,
                             int64_t rows, int64_t k0, int64_t K, int64_t Kp, int64_t ld,
                             const int64_t *bot, int NM, const uint32_t *pw32, int pw_stride,
-                            __nv_bfloat16 *out) {
+                            const uint32_t *ymul, __nv_bfloat16 *out) {
 #define ARB_RES(NCH_)                                                                         \
   residue_split_kernel<NCH_><<<(unsigned)((n + 127) / 128), 128,                              \
                                (size_t)NM * ((NCH_ + 3) / 4 * 4) * 4, s>>>(                   \
-      X, is_b, rows, k0, K, Kp, ld, bot, NM, pw32, pw_stride, out)
+      X, is_b, rows, k0, K, Kp, ld, bot, NM, pw32, pw_stride, ymul, out)
   if (nch <= 4) ARB_RES(4);
   else if (nch <= 6) ARB_RES(6);
   else if (nch <= 8) ARB_RES(8);
@@ -650,8 +658,12 @@ static arbgpu_status ensure_crt_constants(int device) {
   if (done[device & 255]) return ARBGPU_OK;
   const CrtPlan *full = crt_plan(CRT_MAX_MODULI);
   if (!full) return ARBGPU_ERR_CUDA;
+  std::vector<uint32_t> inv32(CRT_MAX_MODULI);
+  for (int t = 0; t < CRT_MAX_MODULI; ++t)
+    inv32[t] = (uint32_t)((((uint64_t)1) << 32) / full->mods[t]);
   if (cudaMemcpyToSymbol(c_mods, full->mods.data(), 4 * CRT_MAX_MODULI) != cudaSuccess ||
-      cudaMemcpyToSymbol(c_inv, full->inv.data(), 8 * CRT_MAX_MODULI) != cudaSuccess)
+      cudaMemcpyToSymbol(c_inv, full->inv.data(), 8 * CRT_MAX_MODULI) != cudaSuccess ||
+      cudaMemcpyToSymbol(c_inv32, inv32.data(), 4 * CRT_MAX_MODULI) != cudaSuccess)
     return ARBGPU_ERR_CUDA;
   done[device & 255] = true;
   return ARBGPU_OK;
@@ -1470,13 +1482,16 @@ static arbgpu_status run_block(arbgpu_ctx *ctx, const BlockWs &w, uint8_t *ws, c
       const int64_t n = M * Kp;
       LaunchScope sc(ctx, s, "residues_a", n * NM * ((hA + 2 + 31) / 32 + 1));
       launch_residues((int)((hA + 2 + 31) / 32) + 1, n, s, Av, false, M, k0, Kb, Kp, lda,
-                      ln.rbot, NM, (const uint32_t *)(ws + w.cpow), plan->NCHP, resA);
+                      ln.rbot, NM, (const uint32_t *)(ws + w.cpow), plan->NCHP, nullptr, resA);
     }
     {
       const int64_t n = N * Kp;
       LaunchScope sc(ctx, s, "residues_b", n * NM * ((hB + 2 + 31) / 32 + 1));
+      // the right-hand residues carry the factor y_t = (M / m_t)^-1 mod m_t of the
+      // reconstruction, so the residue products are already z_t = P_t y_t mod m_t
       launch_residues((int)((hB + 2 + 31) / 32) + 1, n, s, Bv, true, N, k0, Kb, Kp, ldb,
-                      ln.cbot, NM, (const uint32_t *)(ws + w.cpow), plan->NCHP, resB);
+                      ln.cbot, NM, (const uint32_t *)(ws + w.cpow), plan->NCHP,
+                      (const uint32_t *)(ws + w.cy), resB);
     }
     if (cudaGetLastError() != cudaSuccess) return ARBGPU_ERR_CUDA;
     DigitGemmArgs g{resA, resB, (int)M, (int)N, Kp, 2, 2, 1, ws + w.cdig,

@@ -108,8 +108,6 @@ std::unique_ptr<CrtPlan> build_plan(int NM) {
   P->ztab.assign((size_t)4 * NM, 0);
   for (int t = 0; t < NM; ++t) {
     P->ztab[4 * t] = P->mods[t];
-    P->ztab[4 * t + 1] = (uint32_t)((((uint64_t)1) << 32) / P->mods[t]);
-    P->ztab[4 * t + 2] = P->y[t];
   }
   P->NCHP = CRT_MAX_CHUNKS32;
   P->pow32.resize((size_t)NM * P->NCHP);

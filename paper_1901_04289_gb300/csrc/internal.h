@@ -72,9 +72,9 @@ struct DigitGemmArgs {
   int32_t *carries;
   const char *name;
   int batch = 1;  // independent products sharing the plane layout (item b: planes b*SA.., b*SB..)
-  // multimodular mode (SA = SB = 2, one group): item b writes z_b = (P_b mod m_b) y_b mod m_b as
-  // uint16 [batch][Mp][Np] instead of digits and carries; ztab [batch][4] = m, floor(2^32 / m),
-  // y, 0 and zinv [batch] = floor((2^64 - 1) / m)
+  // multimodular mode (SA = SB = 2, one group): item b writes P_b mod m_b as uint16 [batch][Mp][Np]
+  // instead of digits and carries; ztab [batch][4] = m, 0, 0, 0 and zinv [batch] =
+  // floor((2^64 - 1) / m)
   uint16_t *zout = nullptr;
   const uint32_t *ztab = nullptr;
   const uint64_t *zinv = nullptr;
@@ -136,7 +136,7 @@ struct CrtPlan {
   std::vector<uint32_t> M32;      // [NW32P]: M in 32-bit limbs
   std::vector<uint32_t> y;        // [NM]: (M / m_t)^-1 mod m_t
   std::vector<float> rinv;        // [NM]: 1 / m_t rounded to float
-  std::vector<uint32_t> ztab;     // [NM][4]: m_t, floor(2^32 / m_t), y_t, 0
+  std::vector<uint32_t> ztab;     // [NM][4]: m_t, 0, 0, 0
   std::vector<uint64_t> M;        // M
 };
 int crt_moduli_for_bits(int bits);

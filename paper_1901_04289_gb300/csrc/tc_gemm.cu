@@ -228,8 +228,7 @@ __global__ void __launch_bounds__(TG_THREADS, 1)
     if (zmode) {
       if (ok) {
         // P = bytes + R 2^24 exactly; |P| <= Kp (m / 2)^2 < 2^50, so P + m 2^35 is in (0, 2^52)
-        const uint32_t m = __ldg(P.ztab + 4 * bi), i32 = __ldg(P.ztab + 4 * bi + 1);
-        const uint32_t y = __ldg(P.ztab + 4 * bi + 2);
+        const uint32_t m = __ldg(P.ztab + 4 * bi);
         const uint64_t i64 = __ldg(P.zinv + bi);
         uint32_t zz[32];
 #pragma unroll
@@ -242,9 +241,7 @@ __global__ void __launch_bounds__(TG_THREADS, 1)
           const uint64_t x = (uint64_t)(pv + ((int64_t)m << 35));
           uint64_t r = x - __umul64hi(x, i64) * m;
           while (r >= m) r -= m;
-          const uint32_t ry = (uint32_t)r * y;
-          uint32_t z = ry - __umulhi(ry, i32) * m;
-          if (z >= m) z -= m;
+          const uint32_t z = (uint32_t)r;
           if (c & 1)
             zz[c >> 1] |= z << 16;
           else
@@ -270,6 +267,207 @@ __global__ void __launch_bounds__(TG_THREADS, 1)
   if (warp == 1) {
     __syncwarp();
     tmem_dealloc(tmem, TG_TMEM_COLS);
+  }
+}
+
+// ------------------------------------------------------------------------ multimodular kernel
+//
+// The residue products of the multimodular engine (2 x 2 balanced digits per modulus, K <= 1024):
+// every k-block stage holds A0, A1 (the two digit planes of the left residues) and B0 | B1 stacked
+// into one 256-row operand, and two MMAs of 128 x 256 x 16 per k-step write the four products
+// A0 B0 | A0 B1 | A1 B0 | A1 B1 into the four 128-column quarters of TMEM (one chain over the whole
+// K: |sum| <= K 2^14 <= 2^24 stays exact in FP32).  Sixteen drain warps (4 lane quadrants x 4
+// column quarters) form P = D0 + 2^8 D1 + 2^16 D2 exactly and write P mod m per entry, as the
+// general kernel's multimodular mode does.
+
+constexpr int CG_STAGES = 3;
+constexpr int CG_STAGE_BYTES = 4 * TG_TILE_BYTES;  // A0, A1, B0, B1
+constexpr size_t CG_SMEM_BYTES = 1024 + (size_t)CG_STAGES * CG_STAGE_BYTES + 256;
+constexpr int CG_TMEM_COLS = 512;
+constexpr int CG_MAX_KP = 1024;
+constexpr int CG_EPI_WARPS = 16;  // 4 lane quadrants x 4 column quarters
+constexpr int CG_THREADS = 32 * (2 + CG_EPI_WARPS);
+
+struct CgShared {
+  uint64_t full[CG_STAGES];
+  uint64_t empty[CG_STAGES];
+  uint64_t accf, acce, done;
+  uint32_t tmem_base;
+  int abort;
+};
+
+__global__ void __launch_bounds__(CG_THREADS, 1)
+    crt_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                    const __grid_constant__ DigitGemmParams P) {
+  extern __shared__ __align__(1024) uint8_t smem_raw[];
+  uint8_t *stages = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  CgShared *sh = (CgShared *)(stages + (size_t)CG_STAGES * CG_STAGE_BYTES);
+  const int warp = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31;
+  const int ntiles = P.tiles_m * P.tiles_n;
+  const int tile = blockIdx.x % ntiles;
+  const int bchunk = blockIdx.x / ntiles;
+  const int b_first = bchunk * P.ipc;
+  const int b_last = min(P.batch, b_first + P.ipc);
+  const int mt = tile / P.tiles_n, nt = tile % P.tiles_n;
+  const int m0 = mt * TG_BM, n0 = nt * TG_BN;
+  const int nkb = P.Kp / TG_BK;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < CG_STAGES; ++s) {
+      mbar_init(&sh->full[s], 1);
+      mbar_init(&sh->empty[s], 1);
+    }
+    mbar_init(&sh->accf, 1);
+    mbar_init(&sh->acce, CG_EPI_WARPS);
+    mbar_init(&sh->done, 1);
+    sh->abort = 0;
+    fence_mbar_init();
+  }
+  if (warp == 1) {
+    tmem_alloc(&sh->tmem_base, CG_TMEM_COLS);
+    tmem_relinquish();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = sh->tmem_base;
+  volatile int *abort = &sh->abort;
+  auto give_up = [&]() {
+    *abort = 1;
+    set_status(P.status, ARBGPU_ERR_TIMEOUT);
+  };
+
+  if (warp == 0) {
+    // ------------------------------------------------------------ TMA producer
+    if (lane == 0) {
+      tma_prefetch_desc(&tmA);
+      tma_prefetch_desc(&tmB);
+      uint32_t it = 0;
+      bool ok = true;
+      for (int bi = b_first; bi < b_last && ok; ++bi) {
+        for (int kb = 0; kb < nkb; ++kb, ++it) {
+          const int s = it % CG_STAGES;
+          if (!mbar_wait(&sh->empty[s], ((it / CG_STAGES) & 1) ^ 1, abort)) {
+            give_up();
+            ok = false;
+            break;
+          }
+          uint8_t *st = stages + (size_t)s * CG_STAGE_BYTES;
+          mbar_arrive_expect_tx(&sh->full[s], CG_STAGE_BYTES);
+          tma_load_3d(st, &tmA, &sh->full[s], kb * TG_BK, m0, 2 * bi);
+          tma_load_3d(st + TG_TILE_BYTES, &tmA, &sh->full[s], kb * TG_BK, m0, 2 * bi + 1);
+          tma_load_3d(st + 2 * TG_TILE_BYTES, &tmB, &sh->full[s], kb * TG_BK, n0, 2 * bi);
+          tma_load_3d(st + 3 * TG_TILE_BYTES, &tmB, &sh->full[s], kb * TG_BK, n0, 2 * bi + 1);
+        }
+      }
+      // before leaving, let every load this thread issued land (bounded)
+      const uint32_t first = it > (uint32_t)CG_STAGES ? it - CG_STAGES : 0;
+      for (uint32_t q = first; q < it; ++q)
+        mbar_wait(&sh->full[q % CG_STAGES], (q / CG_STAGES) & 1, abort);
+    }
+  } else if (warp == 1) {
+    // ------------------------------------------------------------ MMA issuer
+    if (lane == 0) {
+      const uint32_t idesc = idesc_bf16_f32(TG_BM, 2 * TG_BN);
+      uint32_t it = 0;
+      bool ok = true;
+      for (int bi = b_first, ii = 0; bi < b_last && ok; ++bi, ++ii) {
+        // the drain must have read the previous item's accumulators
+        if (!mbar_wait(&sh->acce, (ii & 1) ^ 1, abort)) {
+          give_up();
+          break;
+        }
+        tc_fence_after();
+        for (int kb = 0; kb < nkb; ++kb, ++it) {
+          const int s = it % CG_STAGES;
+          if (!mbar_wait(&sh->full[s], (it / CG_STAGES) & 1, abort)) {
+            give_up();
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          uint8_t *st = stages + (size_t)s * CG_STAGE_BYTES;
+          const uint64_t a0 = sw128_desc(smem_u32(st));
+          const uint64_t a1 = sw128_desc(smem_u32(st + TG_TILE_BYTES));
+          const uint64_t b = sw128_desc(smem_u32(st + 2 * TG_TILE_BYTES));
+#pragma unroll
+          for (int kk = 0; kk < TG_BK / 16; ++kk) {
+            const uint32_t acc = (kb > 0 || kk > 0) ? 1u : 0u;
+            umma_bf16(tmem, a0 + 2 * kk, b + 2 * kk, idesc, acc);              // A0 B0 | A0 B1
+            umma_bf16(tmem + 2 * TG_BN, a1 + 2 * kk, b + 2 * kk, idesc, acc);  // A1 B0 | A1 B1
+          }
+          umma_commit(&sh->empty[s]);
+        }
+        if (ok) umma_commit(&sh->accf);
+      }
+      umma_commit(&sh->done);
+      mbar_wait(&sh->done, 0, abort);
+    }
+  } else {
+    // ------------------------------------------------------------ drain: P mod m per entry
+    const int q = warp & 3;                   // TMEM lane quadrant this warp may access
+    const int col0 = 32 * ((warp - 2) >> 2);  // its 32 of the tile's 128 columns
+    const int row = 32 * q + lane;
+    const uint32_t lane_addr = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)col0;
+    const int64_t gm = m0 + row;
+    const int64_t gcol = n0 + col0;
+    for (int bi = b_first, ii = 0; bi < b_last; ++bi, ++ii) {
+      const bool got = __all_sync(0xffffffffu, mbar_wait(&sh->accf, ii & 1, abort));
+      if (!got) {
+        if (lane == 0) give_up();
+        break;
+      }
+      tc_fence_after();
+      // P = D0 + 2^8 (D1a + D1b) + 2^16 D2 from the quarters A0 B0 | A0 B1 | A1 B0 | A1 B1
+      int64_t Pc[32];
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        uint32_t v0[16], v1[16], v2[16], v3[16];
+        tmem_ld16(lane_addr + 16 * h, v0);
+        tmem_ld16(lane_addr + TG_BN + 16 * h, v1);
+        tmem_ld16(lane_addr + 2 * TG_BN + 16 * h, v2);
+        tmem_ld16(lane_addr + 3 * TG_BN + 16 * h, v3);
+        tmem_wait_ld();
+#pragma unroll
+        for (int c = 0; c < 16; ++c) {
+          const int64_t d1 = (int64_t)__float2int_rn(__uint_as_float(v1[c])) +
+                             __float2int_rn(__uint_as_float(v2[c]));
+          Pc[16 * h + c] = (int64_t)__float2int_rn(__uint_as_float(v0[c])) + d1 * 256 +
+                           (int64_t)__float2int_rn(__uint_as_float(v3[c])) * 65536;
+        }
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&sh->acce);
+      // |P| <= Kp (m / 2)^2 < 2^50, so P + m 2^35 is in (0, 2^52)
+      const uint32_t m = __ldg(P.ztab + 4 * bi);
+      const uint64_t i64 = __ldg(P.zinv + bi);
+      uint4 *zdst = (uint4 *)(P.zout + ((int64_t)bi * P.Mp + gm) * P.Np + gcol);
+#pragma unroll
+      for (int c8 = 0; c8 < 4; ++c8) {
+        uint32_t zz[4];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const uint64_t x = (uint64_t)(Pc[8 * c8 + u] + ((int64_t)m << 35));
+          uint64_t r = x - __umul64hi(x, i64) * m;
+          if (r >= m) r -= m;
+          if (u & 1)
+            zz[u >> 1] |= (uint32_t)r << 16;
+          else
+            zz[u >> 1] = (uint32_t)r;
+        }
+        zdst[c8] = make_uint4(zz[0], zz[1], zz[2], zz[3]);
+      }
+    }
+  }
+
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 1) {
+    __syncwarp();
+    tmem_dealloc(tmem, CG_TMEM_COLS);
   }
 }
 
@@ -406,6 +604,20 @@ arbgpu_status launch_digit_gemm(arbgpu_ctx *ctx, const DigitGemmArgs &a, cudaStr
     P.ipc = best;
   }
   const int64_t grid = (int64_t)P.tiles_m * P.tiles_n * G * ((P.batch + P.ipc - 1) / P.ipc);
+  if (a.zout && a.Kp <= CG_MAX_KP) {
+    static bool cg_attr[256] = {};
+    if (!cg_attr[dev]) {
+      if (cudaFuncSetAttribute(crt_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)CG_SMEM_BYTES) != cudaSuccess)
+        return ARBGPU_ERR_CUDA;
+      cg_attr[dev] = true;
+    }
+    if (grid > 0x7fffffff) return ARBGPU_ERR_LIMIT;
+    LaunchScope scope(ctx, stream, a.name ? a.name : "crt_gemm",
+                      (int64_t)(a.SA) * a.SB * (int64_t)a.M * a.N * a.Kp * P.batch);
+    crt_gemm_kernel<<<(unsigned)grid, CG_THREADS, CG_SMEM_BYTES, stream>>>(tmA, tmB, P);
+    return cudaGetLastError() == cudaSuccess ? ARBGPU_OK : ARBGPU_ERR_CUDA;
+  }
   if (grid > 0x7fffffff) return ARBGPU_ERR_LIMIT;
   LaunchScope scope(ctx, stream, a.name ? a.name : "digit_gemm",
                     (int64_t)(a.SA) * a.SB * (int64_t)a.M * a.N * a.Kp * P.batch);

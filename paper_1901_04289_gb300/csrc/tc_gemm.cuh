@@ -57,9 +57,9 @@ struct DigitGemmParams {
   int ipc;                  // batch items per CTA (consecutive, run back to back)
   int *status;
   // Multimodular mode (2 x 2 digits, one group): instead of digits and carries, item b writes
-  // z_b = (P_b mod m_b) y_b mod m_b of its exact product P_b to zout[b][Mp][Np].
+  // P_b mod m_b of its exact product P_b to zout[b][Mp][Np] (uint16).
   uint16_t *zout;
-  const uint32_t *ztab;     // [batch][4]: m_b, floor(2^32 / m_b), y_b, unused
+  const uint32_t *ztab;     // [batch][4]: m_b, unused
   const uint64_t *zinv;     // [batch]: floor((2^64 - 1) / m_b)
 };
 
@@ -179,6 +179,15 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
         "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),
         "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),
         "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+}
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, "
+      "%12, %13, %14, %15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15])
       : "r"(taddr));
 }
 __device__ __forceinline__ void tmem_wait_ld() {
