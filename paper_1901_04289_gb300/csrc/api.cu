@@ -155,6 +155,7 @@ arbgpu_status arbgpu_destroy(arbgpu_ctx *ctx) {
     cudaEventDestroy(r.stop);
   }
   for (auto e : ctx->event_pool) cudaEventDestroy(e);
+  for (auto &t : ctx->crt_tables) cudaFree(t.second);
   cudaFree(ctx->status);
   delete ctx;
   return ARBGPU_OK;

@@ -1268,14 +1268,14 @@ struct BlockWs {
   // whole-range scans of the operand parts: rows of A_re / A_im, columns of B_re / B_im
   size_t pstats, prtop[2], prbot[2], prrad[2], pctop[2], pcbot[2], pcrad[2], pcplus[2];
   // operands and products of one block
-  size_t dA, dB, rA1, rA2, rB1, rB2, mdig, mcar, r1dig, r1car, r2dig, r2car;
+  size_t dA, dB, rA1, rB1, mdig, mcar, r1dig, r1car, r2dig, r2car;
   // several blocks: planner input, plan, per-block line statistics
   size_t tA, bA, tB, bB, blocks, nblocks, bstats;
   size_t brtop, brbot, brrad, bctop, bcbot, bcrad, bcplus;
   // per output part: accumulator, initial balls, basecase index list
   size_t acc[2], err[2], rman[2], rexp[2], ilimbs[2], iexp[2], iflags[2], irman[2], irexp[2], bk[2];
   // multimodular engine: residue planes, residue products, tables
-  size_t resA, resB, cdig, ccar, cztab, czinv, cpow, cQ, cM, cy, crinv;
+  size_t resA, resB, cdig, ccar;
   size_t total;
   int Smax, NDmax, Gmax, Gr, maxb, nacc, NMmax, NMWmax;
   int64_t Kp, Mp, Np;
@@ -1320,16 +1320,15 @@ static BlockWs block_ws(arbgpu_ctx *ctx, int64_t M, int64_t K, int64_t N, int pr
   }
   w.dA = take((size_t)w.Smax * M * w.Kp * 2);
   w.dB = take((size_t)w.Smax * N * w.Kp * 2);
-  w.rA1 = take((size_t)BL_SR * M * w.Kp * 2);
-  w.rA2 = take((size_t)BL_SR * M * w.Kp * 2);
-  w.rB1 = take((size_t)BL_SR * N * w.Kp * 2);
-  w.rB2 = take((size_t)BL_SR * N * w.Kp * 2);
+  // the two radius products' operands and results are adjacent, so both run as one batch
+  w.rA1 = take((size_t)2 * BL_SR * M * w.Kp * 2);  // both radius operands of A
+  w.rB1 = take((size_t)2 * BL_SR * N * w.Kp * 2);
   w.mdig = take((size_t)w.NDmax * w.Mp * w.Np);
   w.mcar = take((size_t)w.Gmax * w.Mp * w.Np * 4);
-  w.r1dig = take((size_t)(2 * BL_SR - 1) * w.Mp * w.Np);
-  w.r1car = take((size_t)w.Gr * w.Mp * w.Np * 4);
-  w.r2dig = take((size_t)(2 * BL_SR - 1) * w.Mp * w.Np);
-  w.r2car = take((size_t)w.Gr * w.Mp * w.Np * 4);
+  w.r1dig = take((size_t)2 * (2 * BL_SR - 1) * w.Mp * w.Np);
+  w.r2dig = w.r1dig + (size_t)(2 * BL_SR - 1) * w.Mp * w.Np;
+  w.r1car = take((size_t)2 * w.Gr * w.Mp * w.Np * 4);
+  w.r2car = w.r1car + (size_t)w.Gr * w.Mp * w.Np * 4;
   w.tA = take(8 * (size_t)M * K);
   w.bA = take(8 * (size_t)M * K);
   w.tB = take(8 * (size_t)K * N);
@@ -1359,14 +1358,7 @@ static BlockWs block_ws(arbgpu_ctx *ctx, int64_t M, int64_t K, int64_t N, int pr
   w.resA = take((size_t)2 * w.NMmax * M * w.Kp * 2);
   w.resB = take((size_t)2 * w.NMmax * N * w.Kp * 2);
   w.cdig = take((size_t)3 * w.NMmax * w.Mp * w.Np);
-  w.ccar = take((size_t)4 * w.NMmax * w.Mp * w.Np);
-  w.cztab = take(16 * (size_t)w.NMmax);
-  w.czinv = take(8 * (size_t)w.NMmax);
-  w.cpow = take(4 * (size_t)w.NMmax * CRT_MAX_CHUNKS32);
-  w.cQ = take(4 * (size_t)w.NMmax * ((2 * w.NMWmax + 15) / 16 * 16));
-  w.cM = take(4 * (size_t)((2 * w.NMWmax + 15) / 16 * 16));
-  w.cy = take(4 * (size_t)w.NMmax);
-  w.crinv = take(4 * (size_t)w.NMmax);
+  w.ccar = take(256);  // the multimodular GEMM writes no carries
   w.total = off;
   return w;
 }
@@ -1436,8 +1428,9 @@ static arbgpu_status run_block(arbgpu_ctx *ctx, const BlockWs &w, uint8_t *ws, c
   if (!plan && (SA > w.Smax || SB > w.Smax || !digit_gemm_fits(SA, SB, Kp)))
     return ARBGPU_ERR_LIMIT;
   __nv_bfloat16 *dA = (__nv_bfloat16 *)(ws + w.dA), *dB = (__nv_bfloat16 *)(ws + w.dB);
-  __nv_bfloat16 *rA1 = (__nv_bfloat16 *)(ws + w.rA1), *rA2 = (__nv_bfloat16 *)(ws + w.rA2);
-  __nv_bfloat16 *rB1 = (__nv_bfloat16 *)(ws + w.rB1), *rB2 = (__nv_bfloat16 *)(ws + w.rB2);
+  // the second radius product's planes follow the first's at this block's Kp (one batched GEMM)
+  __nv_bfloat16 *rA1 = (__nv_bfloat16 *)(ws + w.rA1), *rA2 = rA1 + (size_t)BL_SR * M * Kp;
+  __nv_bfloat16 *rB1 = (__nv_bfloat16 *)(ws + w.rB1), *rB2 = rB1 + (size_t)BL_SR * N * Kp;
   // radius operands (and the digit planes when the digit engine runs)
   if (!plan || radA || radB) {
     const int64_t n = M * Kp;
@@ -1459,30 +1452,15 @@ static arbgpu_status run_block(arbgpu_ctx *ctx, const BlockWs &w, uint8_t *ws, c
   if (plan) {
     // ---- multimodular: residues, NM batched residue products, CRT in the consumer
     if (ensure_crt_constants(ctx->device) != ARBGPU_OK) return ARBGPU_ERR_CUDA;
-    CrtTables ct{(const uint32_t *)(ws + w.cQ), (const uint32_t *)(ws + w.cM),
-                 (const uint32_t *)(ws + w.cy), (const float *)(ws + w.crinv), plan->NM,
-                 plan->NMW, plan->NW32P};
-    if (cudaMemcpyAsync(ws + w.cQ, plan->Q32.data(), 4 * plan->Q32.size(),
-                        cudaMemcpyHostToDevice, s) != cudaSuccess ||
-        cudaMemcpyAsync(ws + w.cM, plan->M32.data(), 4 * plan->M32.size(), cudaMemcpyHostToDevice,
-                        s) != cudaSuccess ||
-        cudaMemcpyAsync(ws + w.cy, plan->y.data(), 4 * plan->y.size(), cudaMemcpyHostToDevice,
-                        s) != cudaSuccess ||
-        cudaMemcpyAsync(ws + w.crinv, plan->rinv.data(), 4 * plan->rinv.size(),
-                        cudaMemcpyHostToDevice, s) != cudaSuccess ||
-        cudaMemcpyAsync(ws + w.cztab, plan->ztab.data(), 4 * plan->ztab.size(),
-                        cudaMemcpyHostToDevice, s) != cudaSuccess ||
-        cudaMemcpyAsync(ws + w.czinv, plan->inv.data(), 8 * plan->inv.size(),
-                        cudaMemcpyHostToDevice, s) != cudaSuccess ||
-        cudaMemcpyAsync(ws + w.cpow, plan->pow32.data(), 4 * plan->pow32.size(),
-                        cudaMemcpyHostToDevice, s) != cudaSuccess)
-      return ARBGPU_ERR_CUDA;
+    CrtDevTables dt{};
+    if (crt_device_tables(ctx, plan, &dt) != ARBGPU_OK) return ARBGPU_ERR_CUDA;
+    CrtTables ct{dt.Q32, dt.M32, dt.y, dt.rinv, plan->NM, plan->NMW, plan->NW32P};
     __nv_bfloat16 *resA = (__nv_bfloat16 *)(ws + w.resA), *resB = (__nv_bfloat16 *)(ws + w.resB);
     {
       const int64_t n = M * Kp;
       LaunchScope sc(ctx, s, "residues_a", n * NM * ((hA + 2 + 31) / 32 + 1));
       launch_residues((int)((hA + 2 + 31) / 32) + 1, n, s, Av, false, M, k0, Kb, Kp, lda,
-                      ln.rbot, NM, (const uint32_t *)(ws + w.cpow), plan->NCHP, nullptr, resA);
+                      ln.rbot, NM, dt.pow32, plan->NCHP, nullptr, resA);
     }
     {
       const int64_t n = N * Kp;
@@ -1490,15 +1468,14 @@ static arbgpu_status run_block(arbgpu_ctx *ctx, const BlockWs &w, uint8_t *ws, c
       // the right-hand residues carry the factor y_t = (M / m_t)^-1 mod m_t of the
       // reconstruction, so the residue products are already z_t = P_t y_t mod m_t
       launch_residues((int)((hB + 2 + 31) / 32) + 1, n, s, Bv, true, N, k0, Kb, Kp, ldb,
-                      ln.cbot, NM, (const uint32_t *)(ws + w.cpow), plan->NCHP,
-                      (const uint32_t *)(ws + w.cy), resB);
+                      ln.cbot, NM, dt.pow32, plan->NCHP, dt.y, resB);
     }
     if (cudaGetLastError() != cudaSuccess) return ARBGPU_ERR_CUDA;
     DigitGemmArgs g{resA, resB, (int)M, (int)N, Kp, 2, 2, 1, ws + w.cdig,
                     (int32_t *)(ws + w.ccar), "crt_gemm", NM};
     g.zout = (uint16_t *)(ws + w.cdig);
-    g.ztab = (const uint32_t *)(ws + w.cztab);
-    g.zinv = (const uint64_t *)(ws + w.czinv);
+    g.ztab = dt.ztab;
+    g.zinv = dt.inv;
     arbgpu_status stg = launch_digit_gemm(ctx, g, s);
     if (stg != ARBGPU_OK) return stg;
     *mid = IntProduct{ws + w.cdig, nullptr, 3, 1, {}, 1, ct};
@@ -1517,21 +1494,23 @@ static arbgpu_status run_block(arbgpu_ctx *ctx, const BlockWs &w, uint8_t *ws, c
   const int NDr = 2 * BL_SR - 1;
   *rp1 = IntProduct{};
   *rp2 = IntProduct{};
-  if (radB) {
-    DigitGemmArgs g{rA1, rB1, (int)M, (int)N, Kp, BL_SR, BL_SR, w.Gr, ws + w.r1dig,
-                    (int32_t *)(ws + w.r1car), "digit_gemm_rad"};
+  if (radA || radB) {
+    // P1 = U(|A|) V(R_B) and P2 = U(R_A) V(|B| + R_B): one launch when both are needed
+    const bool both = radA && radB;
+    DigitGemmArgs g{radB ? rA1 : rA2, radB ? rB1 : rB2, (int)M, (int)N, Kp, BL_SR, BL_SR, w.Gr,
+                    ws + (radB ? w.r1dig : w.r2dig),
+                    (int32_t *)(ws + (radB ? w.r1car : w.r2car)), "digit_gemm_rad",
+                    both ? 2 : 1};
     arbgpu_status stg = launch_digit_gemm(ctx, g, s);
     if (stg != ARBGPU_OK) return stg;
-    *rp1 = IntProduct{ws + w.r1dig, (int32_t *)(ws + w.r1car), NDr, w.Gr, {}, 0, {}};
-    digit_gemm_group_ends(BL_SR, BL_SR, w.Gr, rp1->ends.e);
-  }
-  if (radA) {
-    DigitGemmArgs g{rA2, rB2, (int)M, (int)N, Kp, BL_SR, BL_SR, w.Gr, ws + w.r2dig,
-                    (int32_t *)(ws + w.r2car), "digit_gemm_rad"};
-    arbgpu_status stg = launch_digit_gemm(ctx, g, s);
-    if (stg != ARBGPU_OK) return stg;
-    *rp2 = IntProduct{ws + w.r2dig, (int32_t *)(ws + w.r2car), NDr, w.Gr, {}, 0, {}};
-    digit_gemm_group_ends(BL_SR, BL_SR, w.Gr, rp2->ends.e);
+    if (radB) {
+      *rp1 = IntProduct{ws + w.r1dig, (int32_t *)(ws + w.r1car), NDr, w.Gr, {}, 0, {}};
+      digit_gemm_group_ends(BL_SR, BL_SR, w.Gr, rp1->ends.e);
+    }
+    if (radA) {
+      *rp2 = IntProduct{ws + w.r2dig, (int32_t *)(ws + w.r2car), NDr, w.Gr, {}, 0, {}};
+      digit_gemm_group_ends(BL_SR, BL_SR, w.Gr, rp2->ends.e);
+    }
   }
   return ARBGPU_OK;
 }

@@ -6,6 +6,7 @@
 // since sum_t z_t Q_t = T (mod M) and sum_t z_t / m_t = q + T / M with |T / M| < 1/8, so a float
 // sum fixes q.  (The paper's integer products use FLINT's multimodular algorithm, Section IV.)
 #include <cmath>
+#include <cstring>
 #include <map>
 #include <memory>
 #include <mutex>
@@ -131,6 +132,42 @@ int crt_moduli_for_bits(int bits) {
   int n = 0;
   while (n < (int)pr.size() && acc < bits + 3.0) acc += std::log2((double)pr[n++]);
   return n < 5 ? 5 : n;
+}
+
+arbgpu_status crt_device_tables(arbgpu_ctx *ctx, const CrtPlan *P, CrtDevTables *out) {
+  auto al = [](size_t v) { return (v + 255) / 256 * 256; };
+  const size_t oQ = 0, oM = oQ + al(4 * P->Q32.size()), oy = oM + al(4 * P->M32.size());
+  const size_t oz = oy + al(4 * P->y.size()), op = oz + al(4 * P->ztab.size());
+  const size_t orv = op + al(4 * P->pow32.size()), oi = orv + al(4 * P->rinv.size());
+  const size_t total = oi + al(8 * P->inv.size());
+  auto it = ctx->crt_tables.find(P->NM);
+  uint8_t *base = nullptr;
+  if (it != ctx->crt_tables.end()) {
+    base = (uint8_t *)it->second;
+  } else {
+    if (cudaMalloc(&base, total) != cudaSuccess) return ARBGPU_ERR_CUDA;
+    std::vector<uint8_t> h(total, 0);
+    memcpy(h.data() + oQ, P->Q32.data(), 4 * P->Q32.size());
+    memcpy(h.data() + oM, P->M32.data(), 4 * P->M32.size());
+    memcpy(h.data() + oy, P->y.data(), 4 * P->y.size());
+    memcpy(h.data() + oz, P->ztab.data(), 4 * P->ztab.size());
+    memcpy(h.data() + op, P->pow32.data(), 4 * P->pow32.size());
+    memcpy(h.data() + orv, P->rinv.data(), 4 * P->rinv.size());
+    memcpy(h.data() + oi, P->inv.data(), 8 * P->inv.size());
+    if (cudaMemcpy(base, h.data(), total, cudaMemcpyHostToDevice) != cudaSuccess) {
+      cudaFree(base);
+      return ARBGPU_ERR_CUDA;
+    }
+    ctx->crt_tables[P->NM] = base;
+  }
+  out->Q32 = (const uint32_t *)(base + oQ);
+  out->M32 = (const uint32_t *)(base + oM);
+  out->y = (const uint32_t *)(base + oy);
+  out->ztab = (const uint32_t *)(base + oz);
+  out->pow32 = (const uint32_t *)(base + op);
+  out->rinv = (const float *)(base + orv);
+  out->inv = (const uint64_t *)(base + oi);
+  return ARBGPU_OK;
 }
 
 const CrtPlan *crt_plan(int NM) {

@@ -4,6 +4,7 @@
 #include <cstddef>
 #include <cstdint>
 #include <cuda_runtime.h>
+#include <map>
 #include <vector>
 
 #include "arbgpu.h"
@@ -18,6 +19,7 @@ struct arbgpu_trace_rec {
 
 struct arbgpu_ctx {
   int device;
+  std::map<int, void *> crt_tables;  // multimodular tables on the device, per modulus count
   int sm_count;
   int *status;       // device int: first recorded error code
   int64_t launches;  // kernels launched through this context
@@ -141,6 +143,13 @@ struct CrtPlan {
 };
 int crt_moduli_for_bits(int bits);
 const CrtPlan *crt_plan(int NM);
+// Device copies of a plan's tables, uploaded once per context and modulus count.
+struct CrtDevTables {
+  const uint32_t *Q32, *M32, *y, *ztab, *pow32;
+  const float *rinv;
+  const uint64_t *inv;
+};
+arbgpu_status crt_device_tables(arbgpu_ctx *ctx, const CrtPlan *plan, CrtDevTables *out);
 
 // Dot-kernel size class for a precision, a maximal term count and operand limb counts (-1: none).
 int dot_class_for_problem(int prec, int64_t max_terms, int max_nlimbs);
