@@ -563,7 +563,7 @@ __device__ __forceinline__ void residue_chunks32(const BallsView &X, int64_t e, 
   }
 }
 
-template <int NCH>
+template <int NCH, int RE>
 __global__ void __launch_bounds__(128) residue_split_kernel(
     const BallsView X, bool is_b, int64_t rows, int64_t k0, int64_t K, int64_t Kp, int64_t ld,
     const int64_t *bot, int NM, const uint32_t *pw32, int pw_stride, const uint32_t *ymul,
@@ -576,56 +576,79 @@ __global__ void __launch_bounds__(128) residue_split_kernel(
     s_pw[q] = c < NCH ? __ldg(pw32 + (int64_t)t * pw_stride + c) : 0u;
   }
   __syncthreads();
+  // thread idx takes entries k = k_lo + u * (Kp / RE), u < RE, of one row: each of the RE
+  // sub-ranges is walked by consecutive threads, so loads and stores stay coalesced
+  const int64_t kq = Kp / RE;
   const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= rows * Kp) return;
-  const int64_t r = idx / Kp, k = idx - r * Kp;
+  if (idx >= rows * kq) return;
+  const int64_t r = idx / kq, k_lo = idx - r * kq;
   const int64_t plane = rows * Kp;
-  __nv_bfloat16 *o = out + r * Kp + k;
-  uint32_t ch[NCH];
-  bool live = false, neg = false;
+  __nv_bfloat16 *o = out + r * Kp + k_lo;
+  uint32_t ch[RE][NCH];
+  bool live[RE], neg[RE];
+  bool any = false;
 #pragma unroll
-  for (int c = 0; c < NCH; ++c) ch[c] = 0;
-  if (k < K) {
-    const int64_t e = is_b ? ((k0 + k) * ld + r) : (r * ld + k0 + k);
-    const uint32_t fl = __ldg(X.flags + e);
-    if (!(fl & (ARBGPU_FLAG_ZERO | SPECIAL_MASK))) {
-      live = true;
-      neg = (fl & ARBGPU_FLAG_SIGN) != 0;
-      const int64_t sh = __ldg(X.exp + e) - 64LL * X.nlimbs - bot[r];
-      residue_chunks32<NCH>(X, e, sh, ch);
+  for (int u = 0; u < RE; ++u) {
+    const int64_t k = k_lo + u * kq;
+    live[u] = neg[u] = false;
+#pragma unroll
+    for (int c = 0; c < NCH; ++c) ch[u][c] = 0;
+    if (k < K) {
+      const int64_t e = is_b ? ((k0 + k) * ld + r) : (r * ld + k0 + k);
+      const uint32_t fl = __ldg(X.flags + e);
+      if (!(fl & (ARBGPU_FLAG_ZERO | SPECIAL_MASK))) {
+        live[u] = true;
+        neg[u] = (fl & ARBGPU_FLAG_SIGN) != 0;
+        const int64_t sh = __ldg(X.exp + e) - 64LL * X.nlimbs - bot[r];
+        residue_chunks32<NCH>(X, e, sh, ch[u]);
+      }
     }
+    any |= live[u];
   }
   const __nv_bfloat16 z = __int2bfloat16_rn(0);
-  if (!__any_sync(__activemask(), live)) {
-    for (int t = 0; t < 2 * NM; ++t) o[(int64_t)t * plane] = z;
+  if (!__any_sync(__activemask(), any)) {
+    for (int t = 0; t < 2 * NM; ++t)
+#pragma unroll
+      for (int u = 0; u < RE; ++u) o[(int64_t)t * plane + u * kq] = z;
     return;
   }
   for (int t = 0; t < NM; ++t) {
     const uint4 *pw = (const uint4 *)(s_pw + t * NC4);  // the same row for every thread
-    uint64_t acc = 0;
+    uint64_t acc[RE];
+#pragma unroll
+    for (int u = 0; u < RE; ++u) acc[u] = 0;
 #pragma unroll
     for (int c4 = 0; c4 < NC4 / 4; ++c4) {
       const uint4 w = pw[c4];
-      if (4 * c4 + 0 < NCH) acc += (uint64_t)ch[4 * c4 + 0] * w.x;
-      if (4 * c4 + 1 < NCH) acc += (uint64_t)ch[4 * c4 + 1] * w.y;
-      if (4 * c4 + 2 < NCH) acc += (uint64_t)ch[4 * c4 + 2] * w.z;
-      if (4 * c4 + 3 < NCH) acc += (uint64_t)ch[4 * c4 + 3] * w.w;
+#pragma unroll
+      for (int u = 0; u < RE; ++u) {
+        if (4 * c4 + 0 < NCH) acc[u] += (uint64_t)ch[u][4 * c4 + 0] * w.x;
+        if (4 * c4 + 1 < NCH) acc[u] += (uint64_t)ch[u][4 * c4 + 1] * w.y;
+        if (4 * c4 + 2 < NCH) acc[u] += (uint64_t)ch[u][4 * c4 + 2] * w.z;
+        if (4 * c4 + 3 < NCH) acc[u] += (uint64_t)ch[u][4 * c4 + 3] * w.w;
+      }
     }
     const uint32_t m = c_mods[t];
-    int32_t res = (int32_t)barrett_mod(acc, m, c_inv[t]);
-    if (ymul) {  // res y < 2^32: one 32-bit Barrett step and one correction
-      const uint32_t x = (uint32_t)res * __ldg(ymul + t);
-      uint32_t r2 = x - __umulhi(x, c_inv32[t]) * m;
-      if (r2 >= m) r2 -= m;
-      res = (int32_t)r2;
+    const uint64_t iv = c_inv[t];
+    const uint32_t yt = ymul ? __ldg(ymul + t) : 1u;
+    const uint32_t i32 = c_inv32[t];
+#pragma unroll
+    for (int u = 0; u < RE; ++u) {
+      int32_t res = (int32_t)barrett_mod(acc[u], m, iv);
+      if (ymul) {  // res y < 2^32: one 32-bit Barrett step and one correction
+        const uint32_t x = (uint32_t)res * yt;
+        uint32_t r2 = x - __umulhi(x, i32) * m;
+        if (r2 >= m) r2 -= m;
+        res = (int32_t)r2;
+      }
+      if (res > (int32_t)(m >> 1)) res -= (int32_t)m;
+      if (neg[u]) res = -res;
+      if (!live[u]) res = 0;
+      const int32_t lo = ((res + 128) & 255) - 128;
+      const int32_t hi = (res - lo) >> 8;
+      o[(int64_t)(2 * t) * plane + u * kq] = __int2bfloat16_rn(lo);
+      o[(int64_t)(2 * t + 1) * plane + u * kq] = __int2bfloat16_rn(hi);
     }
-    if (res > (int32_t)(m >> 1)) res -= (int32_t)m;
-    if (neg) res = -res;
-    if (!live) res = 0;
-    const int32_t lo = ((res + 128) & 255) - 128;
-    const int32_t hi = (res - lo) >> 8;
-    o[(int64_t)(2 * t) * plane] = __int2bfloat16_rn(lo);
-    o[(int64_t)(2 * t + 1) * plane] = __int2bfloat16_rn(hi);
   }
 }
 
@@ -634,19 +657,19 @@ static void launch_residues(int nch, int64_t n, cudaStream_t s, const BallsView 
                             int64_t rows, int64_t k0, int64_t K, int64_t Kp, int64_t ld,
                             const int64_t *bot, int NM, const uint32_t *pw32, int pw_stride,
                             const uint32_t *ymul, __nv_bfloat16 *out) {
-#define ARB_RES(NCH_)                                                                         \
-  residue_split_kernel<NCH_><<<(unsigned)((n + 127) / 128), 128,                              \
-                               (size_t)NM * ((NCH_ + 3) / 4 * 4) * 4, s>>>(                   \
+#define ARB_RES(NCH_, RE_)                                                                    \
+  residue_split_kernel<NCH_, RE_><<<(unsigned)((n / RE_ + 127) / 128), 128,                   \
+                                    (size_t)NM * ((NCH_ + 3) / 4 * 4) * 4, s>>>(              \
       X, is_b, rows, k0, K, Kp, ld, bot, NM, pw32, pw_stride, ymul, out)
-  if (nch <= 4) ARB_RES(4);
-  else if (nch <= 6) ARB_RES(6);
-  else if (nch <= 8) ARB_RES(8);
-  else if (nch <= 11) ARB_RES(11);
-  else if (nch <= 14) ARB_RES(14);
-  else if (nch <= 18) ARB_RES(18);
-  else if (nch <= 24) ARB_RES(24);
-  else if (nch <= 34) ARB_RES(34);
-  else ARB_RES(CRT_MAX_CHUNKS32);
+  if (nch <= 4) ARB_RES(4, 2);
+  else if (nch <= 6) ARB_RES(6, 2);
+  else if (nch <= 8) ARB_RES(8, 2);
+  else if (nch <= 11) ARB_RES(11, 2);
+  else if (nch <= 14) ARB_RES(14, 2);
+  else if (nch <= 18) ARB_RES(18, 1);
+  else if (nch <= 24) ARB_RES(24, 1);
+  else if (nch <= 34) ARB_RES(34, 1);
+  else ARB_RES(CRT_MAX_CHUNKS32, 1);
 #undef ARB_RES
 }
 
