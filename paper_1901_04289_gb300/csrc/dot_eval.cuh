@@ -516,7 +516,7 @@ __device__ bool dot_setup_core(const Src &src, const typename Src::Cursor &cur, 
   int64_t nnz = 0;
   int64_t e_max = INT64_MIN, e_rad = INT64_MIN;
   int nsig_max = 0;
-  constexpr int U = 4;  // terms per lane per step, loads issued together
+  constexpr int U = 2;  // terms per lane per step, loads issued together
   const int64_t ntot = nt + (has_init ? 1 : 0);
   for (int64_t t0 = gl; t0 < ntot; t0 += G * U) {
     Opnd x[U], y[U];
@@ -598,7 +598,7 @@ __device__ void dot_setup(const Src &src, int64_t d, int cmax, int gl, unsigned 
 }
 
 template <int G, class Src>
-__global__ void __launch_bounds__(256) dot_setup_kernel(const __grid_constant__ Src src, int cmax,
+__global__ void __launch_bounds__(256, 4) dot_setup_kernel(const __grid_constant__ Src src, int cmax,
                                                         int *status) {
   constexpr int DPW = 32 / G;  // dots per warp step
   const int lane = threadIdx.x & 31;
@@ -619,7 +619,7 @@ constexpr int DOT_CHUNK = 32;
 // Resident 256-thread blocks per SM the register budget of each class is sized for.
 template <int C>
 struct DotClassBlocks {
-  static constexpr int B = C <= 4 ? 2 : 1;
+  static constexpr int B = C <= 2 ? 3 : (C <= 4 ? 2 : 1);
 };
 
 // Evaluation of every pending dot of class C: a warp reads the parked flags of `chunk` dots and
