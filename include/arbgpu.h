@@ -95,10 +95,10 @@ int arbgpu_version(void);
  *   on its stream (a few microseconds of overhead per launch).
  * arbgpu_trace_read: waits for the recorded launches, writes up to `max_entries` records (kernel
  *   name -- a static string --, device time in ms, and the algorithmic work units the launch
- *   processed -- dot_kernel: dots (arbgpu_dot) or M*N*K ball multiply-adds (arbgpu_mat_mul);
- *   digit_gemm* / crt_gemm: digit multiply-adds on the tensor cores; residues_*: 16x16-bit
- *   multiply-adds; block_round: 32-bit multiply-adds of the CRT sums (multimodular) or entries;
- *   others: entries) and clears the record list. */
+ *   processed -- dot_fused / dot_setup / dot_eval (the last class launch of a call): dots
+ *   (arbgpu_dot) or terms (matrix products); digit_gemm* / crt_gemm: digit multiply-adds on the
+ *   tensor cores; residues_*: 32x16-bit multiply-adds; block_round: 32-bit multiply-adds of the
+ *   CRT sums (multimodular) or entries; others: entries) and clears the record list. */
 typedef struct {
   const char *name;
   float ms;

@@ -97,8 +97,8 @@ arbgpu_status block_matmul(arbgpu_ctx *ctx, const arbgpu_balls *C, const arbgpu_
                            int64_t ldb, int64_t ldc, int prec, bool cplx, void *workspace,
                            size_t ws_bytes, cudaStream_t s, bool *used_block);
 
-// Dot products that finish the basecase blocks of Algorithm 2 (dot.cu): entry (i, j) of C is
-// initial[i*N + j] + sum over the tagged indices e = bk[t] (k = e >> 2, combo = e & 3) of
+// Dot products that finish the basecase blocks of Algorithm 2 (dot_basecase.cu): entry (i, j) of C
+// is initial[i*N + j] + sum over the tagged indices e = bk[t] (k = e >> 2, combo = e & 3) of
 // +- X[i*lda + k] * Y[k*ldb + j] with (X, Y, sign) = (A0, B0, +), (A1, B1, -), (A0, B1, +),
 // (A1, B0, +) for combo 0..3 (A1, B1: imaginary parts, used when cplx).
 arbgpu_status launch_basecase_dot(arbgpu_ctx *ctx, const arbgpu_balls &C, const arbgpu_balls *A,
@@ -114,8 +114,8 @@ arbgpu_status int_mat_mul_run(arbgpu_ctx *ctx, uint64_t *T, int32_t t_limbs, con
                               cudaStream_t s);
 size_t int_mat_mul_workspace(arbgpu_ctx *ctx, int xl, int yl, int64_t M, int64_t K, int64_t N);
 
-// Grouped classical products (dot.cu): one launch over the items of a device work list; `ends`
-// holds the running totals of virtual dots (item q owns dots [ends[q-1], ends[q])).
+// Grouped classical products (dot_grouped.cu): one launch sequence over the items of a device work
+// list; `ends` holds the running totals of virtual dots (item q owns dots [ends[q-1], ends[q])).
 struct GroupItem {
   BallsView A[2], B[2];
   BallsOut C[2];
