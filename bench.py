@@ -205,6 +205,21 @@ def dot_roofline(kernels, work, calls, peaks, sm_mhz):
     return base
 
 
+# --------------------------------------------------------------------------- replicas
+
+def replica_throughput(ms, units, world, device="cpu"):
+    """Whole-job rate of `world` independent replicas that each processed `units` work units in
+    `ms` milliseconds: the slowest rank's time (max over ranks through torch.distributed when
+    world > 1) sets the job time.  Returns (ms_max, units per second / 1e9 over all ranks)."""
+    import torch
+    import torch.distributed as dist
+    tot = torch.tensor([ms], dtype=torch.float64, device=device)
+    if world > 1:
+        dist.all_reduce(tot, op=dist.ReduceOp.MAX)
+    ms_max = float(tot.item())
+    return ms_max, world * units / (ms_max * 1e-3) / 1e9
+
+
 # --------------------------------------------------------------------------- oracle arm
 
 def oracle_sample(case, prec, entries, seconds):
@@ -580,12 +595,7 @@ def main():
     sampler.start()
     ms, launches, recs, _, _ = timed(case, prec, alg, args.steps, args.warmup, trace=True)
     clocks = sampler.stop()
-    # max over ranks
-    tot = torch.tensor([ms], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(tot, op=dist.ReduceOp.MAX)
-    ms_max = float(tot.item())
-    value = world * macs * args.steps / (ms_max * 1e-3) / 1e9
+    ms_max, value = replica_throughput(ms, macs * args.steps, world, dev)
     e2e_ms, _, _, h2d, d2h = timed(case, prec, alg, args.steps, 2, e2e=True)
     e2e_value = macs * args.steps / (e2e_ms * 1e-3) / 1e9
 
