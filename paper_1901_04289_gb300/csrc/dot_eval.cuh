@@ -198,12 +198,13 @@ __device__ __forceinline__ int64_t term_rad_exp_max(const Opnd &x, const Opnd &y
   return cur;
 }
 
-// srad += upper bound of (a/2^30)(b/2^30) 2^e in units of 2^(e_rad - 30) (Section III-E).
-__device__ __forceinline__ void srad_add(uint64_t &srad, uint64_t a, uint64_t b, int64_t e,
+// srad += upper bound of (a/2^30)(b/2^30) 2^e in units of 2^(e_rad - 30) (Section III-E); a, b
+// are at most 2^31 and 2^30, so the product is one 32 x 32 -> 64-bit multiply.
+__device__ __forceinline__ void srad_add(uint64_t &srad, uint32_t a, uint32_t b, int64_t e,
                                          int64_t e_rad) {
   int64_t d = e_rad - e;
   if (d < P_RAD)
-    srad += ((a * b) >> (P_RAD + (int)d)) + 1;
+    srad += (((uint64_t)a * b) >> (P_RAD + (int)d)) + 1;
   else
     srad += 1;
 }
@@ -211,8 +212,10 @@ __device__ __forceinline__ void srad_add(uint64_t &srad, uint64_t a, uint64_t b,
 __device__ __forceinline__ void term_radius(uint64_t &srad, const Opnd &x, uint64_t xtop,
                                             const Opnd &y, uint64_t ytop, int64_t e_rad) {
   bool xz = opnd_zero(x), yz = opnd_zero(y);
-  if (!xz && y.rman) srad_add(srad, (xtop >> (64 - P_RAD)) + 1, y.rman, x.e + y.rexp, e_rad);
-  if (!yz && x.rman) srad_add(srad, (ytop >> (64 - P_RAD)) + 1, x.rman, y.e + x.rexp, e_rad);
+  if (!xz && y.rman)
+    srad_add(srad, (uint32_t)(xtop >> (64 - P_RAD)) + 1, y.rman, x.e + y.rexp, e_rad);
+  if (!yz && x.rman)
+    srad_add(srad, (uint32_t)(ytop >> (64 - P_RAD)) + 1, x.rman, y.e + x.rexp, e_rad);
   if (x.rman && y.rman) srad_add(srad, x.rman, y.rman, x.rexp + y.rexp, e_rad);
 }
 
@@ -228,23 +231,63 @@ __device__ __forceinline__ void load_leading(const BallsView &v, int64_t i, int 
   }
 }
 
-// p = a * b (schoolbook, exact).
+// (c0, c1, c2) += a * b for 32-bit a, b: the 64-bit product into a three-word column accumulator
+// (carries stay inside the one asm statement).
+__device__ __forceinline__ void mac3(uint32_t &c0, uint32_t &c1, uint32_t &c2, uint32_t a,
+                                     uint32_t b) {
+  asm("mad.lo.cc.u32 %0, %3, %4, %0;\n\t"
+      "madc.hi.cc.u32 %1, %3, %4, %1;\n\t"
+      "addc.u32 %2, %2, 0;"
+      : "+r"(c0), "+r"(c1), "+r"(c2)
+      : "r"(a), "r"(b));
+}
+
+// p = a * b exactly (NX 64-bit limbs each): product scanning over 32-bit words, one column of the
+// 2NX x 2NX partial products at a time (row products of 64-bit limbs for long operands).
 template <int NX>
 __device__ __forceinline__ void mul_limbs(const uint64_t (&a)[NX], const uint64_t (&b)[NX],
                                           uint64_t (&p)[2 * NX]) {
+  if constexpr (NX > 6) {  // long operands: 64-bit row products keep fewer words live
 #pragma unroll
-  for (int k = 0; k < 2 * NX; ++k) p[k] = 0;
+    for (int k = 0; k < 2 * NX; ++k) p[k] = 0;
+#pragma unroll
+    for (int i = 0; i < NX; ++i) {
+      uint64_t carry = 0;
+#pragma unroll
+      for (int j = 0; j < NX; ++j) {
+        const u128 t = (u128)a[i] * b[j] + p[i + j] + carry;
+        p[i + j] = (uint64_t)t;
+        carry = (uint64_t)(t >> 64);
+      }
+      p[i + NX] = carry;
+    }
+    return;
+  }
+  constexpr int n = 2 * NX;
+  uint32_t A[n], B[n], R[2 * n];
 #pragma unroll
   for (int i = 0; i < NX; ++i) {
-    uint64_t carry = 0;
-#pragma unroll
-    for (int j = 0; j < NX; ++j) {
-      u128 t = (u128)a[i] * b[j] + p[i + j] + carry;
-      p[i + j] = (uint64_t)t;
-      carry = (uint64_t)(t >> 64);
-    }
-    p[i + NX] = carry;
+    A[2 * i] = (uint32_t)a[i];
+    A[2 * i + 1] = (uint32_t)(a[i] >> 32);
+    B[2 * i] = (uint32_t)b[i];
+    B[2 * i + 1] = (uint32_t)(b[i] >> 32);
   }
+  uint32_t c0 = 0, c1 = 0, c2 = 0;
+#pragma unroll
+  for (int k = 0; k < 2 * n - 1; ++k) {
+#pragma unroll
+    for (int i = 0; i < n; ++i) {
+      const int j = k - i;
+      if (j >= 0 && j < n) mac3(c0, c1, c2, A[i], B[j]);
+    }
+    R[k] = c0;
+    c0 = c1;
+    c1 = c2;
+    c2 = 0;
+  }
+  R[2 * n - 1] = c0;
+#pragma unroll
+  for (int k = 0; k < 2 * NX; ++k) p[k] = (uint64_t)R[2 * k] | ((uint64_t)R[2 * k + 1] << 32);
 }
 
 // Per-lane accumulation state.
