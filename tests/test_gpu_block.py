@@ -328,3 +328,17 @@ def test_multimodular_p1024(arb):
         (out,), names = _run_engine(arb, engine, A, B, M, K, N, p)
         assert kernel in names
         check_entries(out, A, B, M, K, N, p, sample, 16)
+
+
+def test_multimodular_long_inner_dimension(arb):
+    """K > 1024: the residue products run in the general GEMM's multimodular mode (chains of at
+    most 256 products, carries between them); midpoints are still the exactly rounded values."""
+    rng = np.random.default_rng(43)
+    M, K, N, p = 40, 1100, 36, 128
+    A = random_balls(rng, M * K, 2, 128, -10, 10, rad_bits=120, rad_zero_frac=0.5)
+    B = random_balls(rng, K * N, 2, 128, -10, 10, rad_bits=120, rad_zero_frac=0.5)
+    (out,), names = _run_engine(arb, "crt", A, B, M, K, N, p)
+    assert "crt_gemm" in names
+    rng2 = np.random.default_rng(4)
+    check_entries(out, A, B, M, K, N, p, [(int(a), int(b)) for a, b in
+                                         zip(rng2.integers(0, M, 30), rng2.integers(0, N, 30))], 2)
