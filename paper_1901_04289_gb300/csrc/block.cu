@@ -567,7 +567,8 @@ template <int NCH, int RE>
 __global__ void __launch_bounds__(128) residue_split_kernel(
     const BallsView X, bool is_b, int64_t rows, int64_t k0, int64_t K, int64_t Kp, int64_t ld,
     const int64_t *bot, int NM, const uint32_t *pw32, int pw_stride, const uint32_t *ymul,
-    __nv_bfloat16 *out) {
+    __nv_bfloat16 *out, SplitOut ro, const int64_t *top, const int64_t *radtop,
+    const int64_t *plustop) {
   constexpr int NC4 = (NCH + 3) / 4 * 4;  // table row in shared memory, padded for 16-byte loads
   extern __shared__ uint4 s_pw4[];
   uint32_t *s_pw = (uint32_t *)s_pw4;
@@ -593,14 +594,32 @@ __global__ void __launch_bounds__(128) residue_split_kernel(
     live[u] = neg[u] = false;
 #pragma unroll
     for (int c = 0; c < NCH; ++c) ch[u][c] = 0;
+    Mag absm{0u, 0}, rad{0u, 0};
     if (k < K) {
       const int64_t e = is_b ? ((k0 + k) * ld + r) : (r * ld + k0 + k);
       const uint32_t fl = __ldg(X.flags + e);
+      const int64_t ex = __ldg(X.exp + e);
       if (!(fl & (ARBGPU_FLAG_ZERO | SPECIAL_MASK))) {
         live[u] = true;
         neg[u] = (fl & ARBGPU_FLAG_SIGN) != 0;
-        const int64_t sh = __ldg(X.exp + e) - 64LL * X.nlimbs - bot[r];
+        const int64_t sh = ex - 64LL * X.nlimbs - bot[r];
         residue_chunks32<NCH>(X, e, sh, ch[u]);
+        if (ro.r1 || ro.r2) absm = mid_upper(X, e, ex);
+      }
+      if (ro.r1 || ro.r2) rad = Mag{__ldg(X.rad_man + e), __ldg(X.rad_exp + e)};
+    }
+    // the radius operands of this entry (zero in the padding), as the split kernel writes them
+    if (ro.r1 || ro.r2) {
+      const int64_t off = r * Kp + k;
+      if (!is_b) {
+        if (ro.r1) put_small_digits(window_up(absm.man, absm.exp, top[r]), ro.r1 + off, plane);
+        if (ro.r2) put_small_digits(window_up(rad.man, rad.exp, radtop[r]), ro.r2 + off, plane);
+      } else {
+        if (ro.r1) put_small_digits(window_up(rad.man, rad.exp, radtop[r]), ro.r1 + off, plane);
+        if (ro.r2) {
+          const Mag plus = mag_add_up(absm, rad);
+          put_small_digits(window_up(plus.man, plus.exp, plustop[r]), ro.r2 + off, plane);
+        }
       }
     }
     any |= live[u];
@@ -656,11 +675,13 @@ __global__ void __launch_bounds__(128) residue_split_kernel(
 static void launch_residues(int nch, int64_t n, cudaStream_t s, const BallsView &X, bool is_b,
                             int64_t rows, int64_t k0, int64_t K, int64_t Kp, int64_t ld,
                             const int64_t *bot, int NM, const uint32_t *pw32, int pw_stride,
-                            const uint32_t *ymul, __nv_bfloat16 *out) {
+                            const uint32_t *ymul, __nv_bfloat16 *out, const SplitOut &ro,
+                            const int64_t *top, const int64_t *radtop, const int64_t *plustop) {
 #define ARB_RES(NCH_, RE_)                                                                    \
   residue_split_kernel<NCH_, RE_><<<(unsigned)((n / RE_ + 127) / 128), 128,                   \
                                     (size_t)NM * ((NCH_ + 3) / 4 * 4) * 4, s>>>(              \
-      X, is_b, rows, k0, K, Kp, ld, bot, NM, pw32, pw_stride, ymul, out)
+      X, is_b, rows, k0, K, Kp, ld, bot, NM, pw32, pw_stride, ymul, out, ro, top, radtop,     \
+      plustop)
   if (nch <= 4) ARB_RES(4, 2);
   else if (nch <= 6) ARB_RES(6, 2);
   else if (nch <= 8) ARB_RES(8, 2);
@@ -1455,7 +1476,9 @@ static arbgpu_status run_block(arbgpu_ctx *ctx, const BlockWs &w, uint8_t *ws, c
   __nv_bfloat16 *rA1 = (__nv_bfloat16 *)(ws + w.rA1), *rA2 = rA1 + (size_t)BL_SR * M * Kp;
   __nv_bfloat16 *rB1 = (__nv_bfloat16 *)(ws + w.rB1), *rB2 = rB1 + (size_t)BL_SR * N * Kp;
   // radius operands (and the digit planes when the digit engine runs)
-  if (!plan || radA || radB) {
+  // the digit engine's planes and radius operands (the multimodular residue kernels write the
+  // radius operands themselves)
+  if (!plan) {
     const int64_t n = M * Kp;
     SplitOut o{dA, radB ? rA1 : nullptr, radA ? rA2 : nullptr};
     LaunchScope sc(ctx, s, "split_a", n);
@@ -1463,7 +1486,7 @@ static arbgpu_status run_block(arbgpu_ctx *ctx, const BlockWs &w, uint8_t *ws, c
                                                              plan ? 0 : SA, ln.rbot, ln.rtop,
                                                              ln.rrad, nullptr, o);
   }
-  if (!plan || radA || radB) {
+  if (!plan) {
     const int64_t n = N * Kp;
     SplitOut o{dB, radB ? rB1 : nullptr, radA ? rB2 : nullptr};
     LaunchScope sc(ctx, s, "split_b", n);
@@ -1482,16 +1505,20 @@ static arbgpu_status run_block(arbgpu_ctx *ctx, const BlockWs &w, uint8_t *ws, c
     {
       const int64_t n = M * Kp;
       LaunchScope sc(ctx, s, "residues_a", n * NM * ((hA + 2 + 31) / 32 + 1));
+      const SplitOut ro{nullptr, radB ? rA1 : nullptr, radA ? rA2 : nullptr};
       launch_residues((int)((hA + 2 + 31) / 32) + 1, n, s, Av, false, M, k0, Kb, Kp, lda,
-                      ln.rbot, NM, dt.pow32, plan->NCHP, nullptr, resA);
+                      ln.rbot, NM, dt.pow32, plan->NCHP, nullptr, resA, ro, ln.rtop, ln.rrad,
+                      nullptr);
     }
     {
       const int64_t n = N * Kp;
       LaunchScope sc(ctx, s, "residues_b", n * NM * ((hB + 2 + 31) / 32 + 1));
       // the right-hand residues carry the factor y_t = (M / m_t)^-1 mod m_t of the
       // reconstruction, so the residue products are already z_t = P_t y_t mod m_t
+      const SplitOut ro{nullptr, radB ? rB1 : nullptr, radA ? rB2 : nullptr};
       launch_residues((int)((hB + 2 + 31) / 32) + 1, n, s, Bv, true, N, k0, Kb, Kp, ldb,
-                      ln.cbot, NM, dt.pow32, plan->NCHP, dt.y, resB);
+                      ln.cbot, NM, dt.pow32, plan->NCHP, dt.y, resB, ro, ln.ctop, ln.crad,
+                      ln.cplus);
     }
     if (cudaGetLastError() != cudaSuccess) return ARBGPU_ERR_CUDA;
     DigitGemmArgs g{resA, resB, (int)M, (int)N, Kp, 2, 2, 1, ws + w.cdig,
