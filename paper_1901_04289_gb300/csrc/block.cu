@@ -255,6 +255,102 @@ static int64_t scan_chunk_len(int64_t len, int64_t lines, int64_t target, int64_
   return chunk;
 }
 
+// Whole-range scans, one CTA per line group and no atomics on the line values: a row of A per
+// 256-thread CTA, eight columns of B per 1024-thread CTA (8 columns x 128 k-slices, coalesced
+// along the row).  Each CTA finishes its lines (heights, |B| + R_B exponents) itself.
+
+struct LineAcc {
+  int64_t top, bot, rad, pm;
+  int flags;  // 1: special value, 2: nonzero radius
+};
+
+__device__ __forceinline__ void line_fold(LineAcc &a, const EntryScan &e) {
+  if (e.special) a.flags |= 1;
+  if (e.nz) {
+    a.top = max((long long)a.top, (long long)e.top);
+    a.bot = min((long long)a.bot, (long long)e.bot);
+    a.pm = max((long long)a.pm, (long long)(e.top - e.bot));
+  }
+  if (e.rad) {
+    a.flags |= 2;
+    a.rad = max((long long)a.rad, (long long)e.rexp);
+  }
+}
+
+__device__ __forceinline__ void line_merge(LineAcc &a, const LineAcc &b) {
+  a.top = max((long long)a.top, (long long)b.top);
+  a.bot = min((long long)a.bot, (long long)b.bot);
+  a.rad = max((long long)a.rad, (long long)b.rad);
+  a.pm = max((long long)a.pm, (long long)b.pm);
+  a.flags |= b.flags;
+}
+
+__device__ __forceinline__ LineAcc line_shfl_xor(const LineAcc &a, int o) {
+  LineAcc b;
+  b.top = __shfl_xor_sync(0xffffffffu, a.top, o);
+  b.bot = __shfl_xor_sync(0xffffffffu, a.bot, o);
+  b.rad = __shfl_xor_sync(0xffffffffu, a.rad, o);
+  b.pm = __shfl_xor_sync(0xffffffffu, a.pm, o);
+  b.flags = __shfl_xor_sync(0xffffffffu, a.flags, o);
+  return b;
+}
+
+__global__ void __launch_bounds__(256) scan_rows_full_kernel(const BallsView A, int64_t K,
+                                                             int64_t lda, int64_t *rtop,
+                                                             int64_t *rbot, int64_t *rrad,
+                                                             BlockStats *st) {
+  __shared__ LineAcc s_acc[8];
+  const int64_t i = blockIdx.x;
+  LineAcc a{INT64_MIN, INT64_MAX, INT64_MIN, 0, 0};
+  for (int64_t k = threadIdx.x; k < K; k += blockDim.x) line_fold(a, scan_entry(A, i * lda + k));
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) line_merge(a, line_shfl_xor(a, o));
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (lane == 0) s_acc[warp] = a;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) line_merge(a, s_acc[w]);
+    rtop[i] = a.top;
+    rbot[i] = a.bot;
+    rrad[i] = a.rad;
+    if (a.top != INT64_MIN) atomic_max_i64(&st->hA, a.top - a.bot);
+    if (a.pm) atomic_max_i64(&st->pA, a.pm);
+    if (a.flags & 1) atomicOr(&st->special, 1);
+    if (a.flags & 2) atomicOr(&st->radA, 1);
+  }
+}
+
+__global__ void __launch_bounds__(1024) scan_cols_full_kernel(const BallsView B, int64_t K,
+                                                              int64_t N, int64_t ldb,
+                                                              int64_t *ctop, int64_t *cbot,
+                                                              int64_t *crad, int64_t *cplus,
+                                                              BlockStats *st) {
+  __shared__ LineAcc s_acc[32][8];
+  const int tx = threadIdx.x & 7, ty = threadIdx.x >> 3;  // column of the group, k-slice
+  const int64_t j = (int64_t)blockIdx.x * 8 + tx;
+  LineAcc a{INT64_MIN, INT64_MAX, INT64_MIN, 0, 0};
+  if (j < N)
+    for (int64_t k = ty; k < K; k += 128) line_fold(a, scan_entry(B, k * ldb + j));
+  // lanes 8 apart hold the same column
+  line_merge(a, line_shfl_xor(a, 8));
+  line_merge(a, line_shfl_xor(a, 16));
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (lane < 8) s_acc[warp][lane] = a;
+  __syncthreads();
+  if (threadIdx.x < 8 && j < N) {
+    for (int w = 1; w < 32; ++w) line_merge(a, s_acc[w][tx]);
+    ctop[j] = a.top;
+    cbot[j] = a.bot;
+    crad[j] = a.rad;
+    const int64_t mx = a.top > a.rad ? a.top : a.rad;  // |b| + r_b < 2^(max(top, rexp) + 1)
+    cplus[j] = mx == INT64_MIN ? INT64_MIN : mx + 1;
+    if (a.top != INT64_MIN) atomic_max_i64(&st->hB, a.top - a.bot);
+    if (a.pm) atomic_max_i64(&st->pB, a.pm);
+    if (a.flags & 1) atomicOr(&st->special, 1);
+    if (a.flags & 2) atomicOr(&st->radB, 1);
+  }
+}
+
 // Scans of the rows of X (M x K) and the columns of Y (K x N) over the whole inner range
 // (blocks = null, nb = 1) or over each of the nb ranges of a plan: the line statistics and the
 // per-range BlockStats (rows into st_rows, columns into st_cols; both must hold their identities).
@@ -1711,12 +1807,19 @@ arbgpu_status block_matmul(arbgpu_ctx *ctx, const arbgpu_balls *C, const arbgpu_
     colsL[q] = Lines{nullptr, nullptr, nullptr, (int64_t *)(ws + w.pctop[q]),
                      (int64_t *)(ws + w.pcbot[q]), (int64_t *)(ws + w.pcrad[q]),
                      (int64_t *)(ws + w.pcplus[q])};
-    const arbgpu_status sst = run_scans(
-        ctx, s, Av[q], M, K, lda, Bv[q], N, ldb, nullptr, 1, K, (int64_t *)rowsL[q].rtop,
-        (int64_t *)rowsL[q].rbot, (int64_t *)rowsL[q].rrad, (int64_t *)colsL[q].ctop,
-        (int64_t *)colsL[q].cbot, (int64_t *)colsL[q].crad, (int64_t *)colsL[q].cplus, pst + q,
-        pst + 2 + q);
-    if (sst != ARBGPU_OK) return sst;
+    {
+      LaunchScope sc(ctx, s, "scan_rows", M * K);
+      scan_rows_full_kernel<<<(unsigned)M, 256, 0, s>>>(
+          Av[q], K, lda, (int64_t *)rowsL[q].rtop, (int64_t *)rowsL[q].rbot,
+          (int64_t *)rowsL[q].rrad, pst + q);
+    }
+    {
+      LaunchScope sc(ctx, s, "scan_cols", K * N);
+      scan_cols_full_kernel<<<(unsigned)((N + 7) / 8), 1024, 0, s>>>(
+          Bv[q], K, N, ldb, (int64_t *)colsL[q].ctop, (int64_t *)colsL[q].cbot,
+          (int64_t *)colsL[q].crad, (int64_t *)colsL[q].cplus, pst + 2 + q);
+    }
+    if (cudaGetLastError() != cudaSuccess) return ARBGPU_ERR_CUDA;
   }
   BlockStats hst[4];
   if (cudaMemcpyAsync(hst, pst, sizeof(hst), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
