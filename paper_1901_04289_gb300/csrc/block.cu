@@ -57,6 +57,7 @@ __device__ __forceinline__ EntryScan scan_entry(const BallsView &v, int64_t idx)
   const int64_t e = __ldg(v.exp + idx);
   const uint32_t rm = __ldg(v.rad_man + idx);
   const int64_t re = __ldg(v.rad_exp + idx);
+  const uint64_t limb0 = __ldg(v.limbs + idx);  // the lowest limb when all limbs are significant
   s.special = (fl & SPECIAL_MASK) != 0;
   s.nz = !(fl & ARBGPU_FLAG_ZERO) && !s.special;
   s.rad = rm != 0 && !s.special;
@@ -68,7 +69,8 @@ __device__ __forceinline__ EntryScan scan_entry(const BallsView &v, int64_t idx)
     int ns = (int)nsig_of(fl);
     if (ns < 1) ns = 1;
     if (ns > v.nlimbs) ns = v.nlimbs;
-    const uint64_t low = __ldg(v.limbs + (int64_t)(v.nlimbs - ns) * v.stride + idx);
+    const uint64_t low =
+        ns == v.nlimbs ? limb0 : __ldg(v.limbs + (int64_t)(v.nlimbs - ns) * v.stride + idx);
     s.bot = e - 64LL * ns + (low ? __ffsll((long long)low) - 1 : 0);
   }
   if (s.rad && (re >= EXP_LIMIT || re <= -EXP_LIMIT)) s.special = true;
