@@ -10,7 +10,7 @@ arbgpu_status launch_basecase_dot(arbgpu_ctx *ctx, const arbgpu_balls &C, const 
                                   cudaStream_t stream) {
   BasecaseSrc s{};
   const int parts = cplx ? 2 : 1;
-  int maxnl = initial.nlimbs;
+  int maxnl = 1;  // the `initial` term has its own limb array: only A and B size the class
   for (int q = 0; q < 2; ++q) {
     const int src = q < parts ? q : 0;
     s.A[q] = view_of(A[src]);

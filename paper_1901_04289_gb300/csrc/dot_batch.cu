@@ -27,7 +27,6 @@ arbgpu_status launch_batched_dot(arbgpu_ctx *ctx, const arbgpu_balls *res,
     s.init[q] = initial ? view_of(initial[q]) : view_of(x[q]);
     maxnl = x[q].nlimbs > maxnl ? x[q].nlimbs : maxnl;
     maxnl = y[q].nlimbs > maxnl ? y[q].nlimbs : maxnl;
-    if (initial) maxnl = initial[q].nlimbs > maxnl ? initial[q].nlimbs : maxnl;
   }
   if (!complex_mode) {
     s.x[1] = s.x[0];

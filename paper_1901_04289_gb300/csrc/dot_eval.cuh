@@ -298,14 +298,12 @@ struct LaneAcc {
   uint64_t srad;
 };
 
-// Add one midpoint term (both factors nonzero, shift < 64 n_s) to the lane accumulator.
-template <int NX, int NS>
-__device__ __forceinline__ void acc_term(LaneAcc<NS> &acc, const uint64_t (&xa)[NX],
-                                         const uint64_t (&ya)[NX], int F, bool negative) {
-  constexpr int NT = 2 * NX;
-  uint64_t p[NT];
-  mul_limbs<NX>(xa, ya, p);
-  // bit j of p lands at bit j + F of a frame whose limbs [NT, NT + n_s) are the accumulator
+// Add the product p (NT limbs, the product of two top-aligned NT/2-limb factors) of a term to the
+// lane accumulator: bit j of p lands at bit j + F of a frame whose limbs [NT, NT + n_s) are the
+// accumulator; bits below it add one ulp to err.
+template <int NT, int NS>
+__device__ __forceinline__ void acc_add_product(LaneAcc<NS> &acc, const uint64_t (&p)[NT], int F,
+                                                bool negative) {
   const int L0 = F >> 6, b0 = F & 63;
   uint64_t u[NT + 1];
   u[0] = p[0] << b0;
@@ -336,6 +334,31 @@ __device__ __forceinline__ void acc_term(LaneAcc<NS> &acc, const uint64_t (&xa)[
     acc.s[k] = (uint64_t)c;
     c >>= 64;
   }
+}
+
+// Add one midpoint term (both factors nonzero, shift < 64 n_s) to the lane accumulator.
+template <int NX, int NS>
+__device__ __forceinline__ void acc_term(LaneAcc<NS> &acc, const uint64_t (&xa)[NX],
+                                         const uint64_t (&ya)[NX], int F, bool negative) {
+  uint64_t p[2 * NX];
+  mul_limbs<NX>(xa, ya, p);
+  acc_add_product<2 * NX, NS>(acc, p, F, negative);
+}
+
+// The `initial` term x [1 +- 0]: with the one top-aligned in NXI limbs (2^63 in its top limb), the
+// product is x times 2^(63 + 64 (NXI - 1)), a shift, so it needs no limb products.
+template <int NXI, int NS>
+__device__ __forceinline__ void acc_term_one(LaneAcc<NS> &acc, const uint64_t (&xa)[NXI], int F,
+                                             bool negative) {
+  uint64_t p[2 * NXI];
+#pragma unroll
+  for (int k = 0; k < 2 * NXI; ++k) {
+    const int jl = k - NXI + 1, jh = k - NXI;  // limbs of x shifted into limb k
+    const uint64_t lo = (jl >= 0 && jl < NXI) ? (xa[jl] << 63) : 0;
+    const uint64_t hi = (jh >= 0 && jh < NXI) ? (xa[jh] >> 1) : 0;
+    p[k] = lo | hi;
+  }
+  acc_add_product<2 * NXI, NS>(acc, p, F, negative);
 }
 
 // ---------------------------------------------------------------- finalise (registers only)
@@ -443,10 +466,10 @@ __device__ void dot_eval_class(const Src &src, const typename Src::Cursor &cur,
   acc.err = 0;
   acc.srad = 0;
   const int64_t nt = src.nterms(cur);
-  const int64_t ntot = nt + (src.has_initial() ? 1 : 0);
   const int64_t width = 64LL * su.n_s;
   const bool rad = su.has_rad;
-  for (int64_t t0 = gl; t0 < ntot; t0 += G * U) {
+  // the regular terms (NX limbs per factor); the `initial` term follows below
+  for (int64_t t0 = gl; t0 < nt; t0 += G * U) {
     Opnd x[U], y[U];
     const BallsView *xv[U];
     const BallsView *yv[U];
@@ -457,7 +480,7 @@ __device__ void dot_eval_class(const Src &src, const typename Src::Cursor &cur,
 #pragma unroll
     for (int u = 0; u < U; ++u) {
       const int64_t t = t0 + G * u;
-      valid[u] = t < ntot;
+      valid[u] = t < nt;
       xv[u] = nullptr;
       yv[u] = nullptr;
       xi[u] = yi[u] = 0;
@@ -465,7 +488,7 @@ __device__ void dot_eval_class(const Src &src, const typename Src::Cursor &cur,
       x[u] = y[u] = Opnd{ARBGPU_FLAG_ZERO, 0, 0u, 0};
 #pragma unroll
       for (int j = 0; j < NX; ++j) xa[u][j] = ya[u][j] = 0;
-      if (t < nt) {
+      if (valid[u]) {
         const TermLoc tl = src.term(cur, t);
         xv[u] = &src.xview(cur, tl.xa);
         yv[u] = &src.yview(cur, tl.ya);
@@ -476,13 +499,6 @@ __device__ void dot_eval_class(const Src &src, const typename Src::Cursor &cur,
         y[u] = rad ? load_opnd(*yv[u], yi[u]) : load_opnd_mid(*yv[u], yi[u]);
         load_top<NX>(*xv[u], xi[u], xa[u]);
         load_top<NX>(*yv[u], yi[u], ya[u]);
-      } else if (valid[u]) {
-        xv[u] = &src.initial_view(cur);
-        xi[u] = src.initial_index(cur);
-        x[u] = rad ? load_opnd(*xv[u], xi[u]) : load_opnd_mid(*xv[u], xi[u]);
-        y[u] = one_opnd();
-        load_top<NX>(*xv[u], xi[u], xa[u]);
-        ya[u][NX - 1] = (uint64_t)1 << 63;
       }
     }
     // which terms reach the accumulator, and how many limbs of each factor they use
@@ -501,7 +517,7 @@ __device__ void dot_eval_class(const Src &src, const typename Src::Cursor &cur,
           F[u] = (int)(width - shift);
           const int n2 = (F[u] + 63) / 64 + 1;
           const int nx = min((int)nsig_of(x[u].flags), xv[u]->nlimbs);
-          const int ny = yv[u] ? min((int)nsig_of(y[u].flags), yv[u]->nlimbs) : 1;
+          const int ny = min((int)nsig_of(y[u].flags), yv[u]->nlimbs);
           if (nx > n2 || ny > n2) acc.err += 1;
           keep_leading<NX>(xa[u], min(nx, n2));
           keep_leading<NX>(ya[u], min(ny, n2));
@@ -518,6 +534,38 @@ __device__ void dot_eval_class(const Src &src, const typename Src::Cursor &cur,
       }
       if (rad && valid[u] && (x[u].rman || y[u].rman))
         term_radius(acc.srad, x[u], xa[u][NX - 1], y[u], ya[u][NX - 1], su.e_rad);
+    }
+  }
+  // the `initial` term x [1 +- 0], in the group's first lane, its limbs in NS + 1 >= n_s + 1
+  // registers (at most n_s + 1 limbs of a term reach the accumulator)
+  if (src.has_initial() && gl == 0) {
+    constexpr int NXI = NS + 1;
+    const BallsView &iv = src.initial_view(cur);
+    const int64_t ii = src.initial_index(cur);
+    const Opnd x = rad ? load_opnd(iv, ii) : load_opnd_mid(iv, ii);
+    const Opnd y = one_opnd();
+    uint64_t xa[NXI];
+#pragma unroll
+    for (int j = 0; j < NXI; ++j) xa[j] = 0;
+    if (!opnd_zero(x)) {
+      const int64_t shift = su.e_s - (x.e + y.e);
+      if (shift >= width) {
+        acc.err += 1;
+      } else {
+        const int F = (int)(width - shift);
+        const int n2 = (F + 63) / 64 + 1;
+        const int nx = min((int)nsig_of(x.flags), iv.nlimbs);
+        if (nx > n2) acc.err += 1;
+        load_top<NXI>(iv, ii, xa);
+        keep_leading<NXI>(xa, min(nx, n2));
+        acc_term_one<NXI, NS>(acc, xa, F, (x.flags & ARBGPU_FLAG_SIGN) != 0);
+      }
+    }
+    if (rad && x.rman) {
+      uint64_t xtop = xa[NXI - 1];
+      if (!opnd_zero(x) && xtop == 0)
+        xtop = __ldg(iv.limbs + (int64_t)(iv.nlimbs - 1) * iv.stride + ii);
+      term_radius(acc.srad, x, xtop, y, (uint64_t)1 << 63, su.e_rad);
     }
   }
   // butterfly reduction over the group: every lane ends with the full sums
@@ -563,11 +611,12 @@ __device__ bool dot_setup_core(const Src &src, const typename Src::Cursor &cur, 
   const int64_t ntot = nt + (has_init ? 1 : 0);
   for (int64_t t0 = gl; t0 < ntot; t0 += G * U) {
     Opnd x[U], y[U];
-    bool valid[U];
+    bool valid[U], regular[U];
 #pragma unroll
     for (int u = 0; u < U; ++u) {
       const int64_t t = t0 + G * u;
       valid[u] = t < ntot;
+      regular[u] = t < nt;
       x[u] = y[u] = Opnd{ARBGPU_FLAG_ZERO, 0, 0u, 0};
       if (t < nt) {
         const TermLoc tl = src.term(cur, t);
@@ -588,7 +637,9 @@ __device__ bool dot_setup_core(const Src &src, const typename Src::Cursor &cur, 
       if (!opnd_zero(x[u]) && !opnd_zero(y[u])) {
         ++nnz;
         e_max = imax64(e_max, x[u].e + y[u].e);
-        nsig_max = max(nsig_max, (int)max(nsig_of(x[u].flags), nsig_of(y[u].flags)));
+        // the `initial` term has its own limb array, so only the regular terms size the class
+        if (regular[u])
+          nsig_max = max(nsig_max, (int)max(nsig_of(x[u].flags), nsig_of(y[u].flags)));
       }
       e_rad = term_rad_exp_max(x[u], y[u], e_rad);
     }
