@@ -304,14 +304,15 @@ arbgpu_status arbgpu_mat_mul_batched_workspace_size(arbgpu_ctx *ctx,
                                                     int32_t count, size_t *bytes) {
   if (!ctx || !bytes || count < 0 || (count > 0 && !descs)) return ARBGPU_ERR_INVALID;
   size_t grouped = al256(sizeof(GroupItem) * (size_t)count) + al256(8 * (size_t)count);
-  size_t blk = 0;
+  size_t blk = 0, scans = al256(sizeof(BlockStats) * 4 * (size_t)count);
   for (int32_t q = 0; q < count; ++q) {
     const arbgpu_matmul_desc &d = descs[q];
     if (!item_uses_block(d)) continue;
     const size_t b = block_workspace_size(ctx, d.M, d.K, d.N, d.prec, d.complex_mode != 0);
     blk = b > blk ? b : blk;
+    scans += al256(block_scan_bytes(d.M, d.N, d.complex_mode != 0));
   }
-  *bytes = grouped + blk;
+  *bytes = grouped + scans + blk;
   return ARBGPU_OK;
 }
 
@@ -385,16 +386,49 @@ arbgpu_status arbgpu_mat_mul_batched(arbgpu_ctx *ctx, const arbgpu_matmul_desc *
     st = launch_grouped_dot(ctx, ditems, dends, (int32_t)items.size(), total, pmax, kmax, nlmax, s);
     if (st != ARBGPU_OK) return st;
   }
-  // 2. the block items, one after the other, sharing the rest of the workspace
-  for (int32_t q : block_items) {
-    const arbgpu_matmul_desc &d = descs[q];
-    bool used = false;
-    st = block_matmul(ctx, d.C, d.A, d.B, d.M, d.K, d.N, d.lda, d.ldb, d.ldc, d.prec,
-                      d.complex_mode != 0, ws + blk_off, ws_bytes - blk_off, s, &used);
-    if (!used && st == ARBGPU_ERR_LIMIT)
-      st = launch_matmul_dot(ctx, d.C, d.A, d.B, d.M, d.K, d.N, d.lda, d.ldb, d.ldc, d.prec,
-                             d.complex_mode, s);
-    if (st != ARBGPU_OK) return st;
+  // 2. the block items: every item's scans, one read-back of all their statistics, then the
+  //    products one after the other, sharing the rest of the workspace
+  if (!block_items.empty()) {
+    const size_t nb = block_items.size();
+    BlockStats *dstats = (BlockStats *)(ws + blk_off);
+    size_t off = blk_off + al256(sizeof(BlockStats) * 4 * (size_t)count);
+    std::vector<size_t> region(nb);
+    for (size_t i = 0; i < nb; ++i) {
+      const arbgpu_matmul_desc &d = descs[block_items[i]];
+      region[i] = off;
+      off += al256(block_scan_bytes(d.M, d.N, d.complex_mode != 0));
+    }
+    const size_t prod_off = off;
+    if (cudaMemsetAsync(dstats, 0, sizeof(BlockStats) * 4 * nb, s) != cudaSuccess)
+      return ARBGPU_ERR_CUDA;
+    std::vector<char> scanned(nb, 0);
+    for (size_t i = 0; i < nb; ++i) {
+      const arbgpu_matmul_desc &d = descs[block_items[i]];
+      st = block_scan_launch(ctx, d.A, d.B, d.M, d.K, d.N, d.lda, d.ldb, d.complex_mode != 0,
+                             ws + region[i], dstats + 4 * i, s);
+      if (st == ARBGPU_OK)
+        scanned[i] = 1;
+      else if (st != ARBGPU_ERR_LIMIT)
+        return st;
+    }
+    std::vector<BlockStats> hstats(4 * nb);
+    if (cudaMemcpyAsync(hstats.data(), dstats, sizeof(BlockStats) * 4 * nb,
+                        cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+      return ARBGPU_ERR_CUDA;
+    for (size_t i = 0; i < nb; ++i) {
+      const arbgpu_matmul_desc &d = descs[block_items[i]];
+      bool used = false;
+      st = ARBGPU_ERR_LIMIT;
+      if (scanned[i])
+        st = block_finish(ctx, d.C, d.A, d.B, d.M, d.K, d.N, d.lda, d.ldb, d.ldc, d.prec,
+                          d.complex_mode != 0, ws + region[i], hstats.data() + 4 * i,
+                          ws + prod_off, ws_bytes - prod_off, s, &used);
+      if (!used && st == ARBGPU_ERR_LIMIT)
+        st = launch_matmul_dot(ctx, d.C, d.A, d.B, d.M, d.K, d.N, d.lda, d.ldb, d.ldc, d.prec,
+                               d.complex_mode, s);
+      if (st != ARBGPU_OK) return st;
+    }
   }
   return ARBGPU_OK;
 }

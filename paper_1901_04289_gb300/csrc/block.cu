@@ -28,13 +28,6 @@ constexpr int BL_SR = 2;          // digits per radius operand (2^13 fits two ba
 constexpr int BL_MAX_NL = 32;     // input limbs the block path accepts
 constexpr int BL_BASECASE = 30;   // Algorithm 2: blocks shorter than this go to dot products
 
-struct BlockStats {
-  int64_t pA, pB;         // largest significant-bit count of an entry
-  int64_t hA, hB;         // largest row / column height (top - bottom)
-  int32_t special;        // NaN / infinity / out-of-range exponent seen
-  int32_t radA, radB;     // a nonzero radius seen
-  int32_t pad;
-};
 
 __device__ __forceinline__ void atomic_max_i64(int64_t *p, int64_t v) {
   atomicMax((long long *)p, (long long)v);
@@ -1408,7 +1401,7 @@ __global__ void acc_to_ball_kernel(const AccView v, BallsOut I, int64_t M, int64
 
 struct BlockWs {
   // whole-range scans of the operand parts: rows of A_re / A_im, columns of B_re / B_im
-  size_t pstats, prtop[2], prbot[2], prrad[2], pctop[2], pcbot[2], pcrad[2], pcplus[2];
+  size_t scan;  // the whole-range scans' region (block_scan_bytes)
   // operands and products of one block
   size_t dA, dB, rA1, rB1, mdig, mcar, r1dig, r1car, r2dig, r2car;
   // several blocks: planner input, plan, per-block line statistics
@@ -1450,16 +1443,7 @@ static BlockWs block_ws(arbgpu_ctx *ctx, int64_t M, int64_t K, int64_t N, int pr
   };
   const size_t MN = (size_t)M * N;
   const int parts = cplx ? 2 : 1;
-  w.pstats = take(sizeof(BlockStats) * 4);
-  for (int q = 0; q < parts; ++q) {
-    w.prtop[q] = take(8 * M);
-    w.prbot[q] = take(8 * M);
-    w.prrad[q] = take(8 * M);
-    w.pctop[q] = take(8 * N);
-    w.pcbot[q] = take(8 * N);
-    w.pcrad[q] = take(8 * N);
-    w.pcplus[q] = take(8 * N);
-  }
+  w.scan = take(block_scan_bytes(M, N, cplx));
   w.dA = take((size_t)w.Smax * M * w.Kp * 2);
   w.dB = take((size_t)w.Smax * N * w.Kp * 2);
   // the two radius products' operands and results are adjacent, so both run as one batch
@@ -1780,53 +1764,98 @@ static arbgpu_status accumulate_product(arbgpu_ctx *ctx, const BlockWs &w, uint8
 // Ball matrix product by Algorithm 2 (real, or complex by four real products, Section IV-C).
 // Returns ARBGPU_ERR_LIMIT when the inputs hold special values or exceed the path's limits (the
 // caller then uses the classical algorithm).
-arbgpu_status block_matmul(arbgpu_ctx *ctx, const arbgpu_balls *C, const arbgpu_balls *A,
+// The whole-range scans of a product: line arrays of each part and the four BlockStats (rows of
+// A0, A1, columns of B0, B1), at pointers the caller lays out (`scan_region_at`).
+struct ScanRegion {
+  int64_t *rtop[2], *rbot[2], *rrad[2];
+  int64_t *ctop[2], *cbot[2], *crad[2], *cplus[2];
+  BlockStats *pst;  // [4]
+};
+
+size_t block_scan_bytes(int64_t M, int64_t N, bool cplx) {
+  const int parts = cplx ? 2 : 1;
+  auto al = [](size_t v) { return (v + 255) / 256 * 256; };
+  return al(sizeof(BlockStats) * 4) + parts * (3 * al(8 * (size_t)M) + 4 * al(8 * (size_t)N));
+}
+
+static ScanRegion scan_region_at(uint8_t *base, int64_t M, int64_t N, bool cplx) {
+  auto al = [](size_t v) { return (v + 255) / 256 * 256; };
+  ScanRegion r{};
+  size_t off = 0;
+  auto take = [&](size_t n) {
+    uint8_t *p = base + off;
+    off += al(n);
+    return p;
+  };
+  r.pst = (BlockStats *)take(sizeof(BlockStats) * 4);
+  for (int q = 0; q < (cplx ? 2 : 1); ++q) {
+    r.rtop[q] = (int64_t *)take(8 * (size_t)M);
+    r.rbot[q] = (int64_t *)take(8 * (size_t)M);
+    r.rrad[q] = (int64_t *)take(8 * (size_t)M);
+    r.ctop[q] = (int64_t *)take(8 * (size_t)N);
+    r.cbot[q] = (int64_t *)take(8 * (size_t)N);
+    r.crad[q] = (int64_t *)take(8 * (size_t)N);
+    r.cplus[q] = (int64_t *)take(8 * (size_t)N);
+  }
+  return r;
+}
+
+// Whether the block path takes the product at all (otherwise: ARBGPU_ERR_LIMIT, dot products).
+static bool block_accepts(const arbgpu_balls *A, const arbgpu_balls *B, int64_t K, bool cplx) {
+  for (int q = 0; q < (cplx ? 2 : 1); ++q)
+    if (A[q].nlimbs > BL_MAX_NL || B[q].nlimbs > BL_MAX_NL) return false;
+  return K >= BL_BASECASE;
+}
+
+// Phase 1: the whole-range scans (two launches per part); the stats start at zero (a height
+// of 0 and no flags is the identity of every field).
+arbgpu_status block_scan_launch(arbgpu_ctx *ctx, const arbgpu_balls *A, const arbgpu_balls *B,
+                                int64_t M, int64_t K, int64_t N, int64_t lda, int64_t ldb,
+                                bool cplx, void *region, BlockStats *stats, cudaStream_t s) {
+  if (!block_accepts(A, B, K, cplx)) return ARBGPU_ERR_LIMIT;
+  ScanRegion sr = scan_region_at((uint8_t *)region, M, N, cplx);
+  if (stats)
+    sr.pst = stats;  // zeroed by the caller
+  else if (cudaMemsetAsync(sr.pst, 0, sizeof(BlockStats) * 4, s) != cudaSuccess)
+    return ARBGPU_ERR_CUDA;
+  for (int q = 0; q < (cplx ? 2 : 1); ++q) {
+    {
+      LaunchScope sc(ctx, s, "scan_rows", M * K);
+      scan_rows_full_kernel<<<(unsigned)M, 256, 0, s>>>(view_of(A[q]), K, lda, sr.rtop[q],
+                                                        sr.rbot[q], sr.rrad[q], sr.pst + q);
+    }
+    {
+      LaunchScope sc(ctx, s, "scan_cols", K * N);
+      scan_cols_full_kernel<<<(unsigned)((N + 7) / 8), 1024, 0, s>>>(
+          view_of(B[q]), K, N, ldb, sr.ctop[q], sr.cbot[q], sr.crad[q], sr.cplus[q],
+          sr.pst + 2 + q);
+    }
+    if (cudaGetLastError() != cudaSuccess) return ARBGPU_ERR_CUDA;
+  }
+  return ARBGPU_OK;
+}
+
+// Phase 2: the products and the rounding, from the scan results (`region`, and their host copy
+// `hst`, read after the scans finished) and the block workspace.
+arbgpu_status block_finish(arbgpu_ctx *ctx, const arbgpu_balls *C, const arbgpu_balls *A,
                            const arbgpu_balls *B, int64_t M, int64_t K, int64_t N, int64_t lda,
-                           int64_t ldb, int64_t ldc, int prec, bool cplx, void *workspace,
-                           size_t ws_bytes, cudaStream_t s, bool *used_block) {
+                           int64_t ldb, int64_t ldc, int prec, bool cplx, void *region,
+                           const BlockStats *hst, void *workspace, size_t ws_bytes,
+                           cudaStream_t s, bool *used_block) {
   *used_block = false;
   const int parts = cplx ? 2 : 1;
-  for (int q = 0; q < parts; ++q)
-    if (A[q].nlimbs > BL_MAX_NL || B[q].nlimbs > BL_MAX_NL) return ARBGPU_ERR_LIMIT;
-  if (K < BL_BASECASE) return ARBGPU_ERR_LIMIT;
   BlockWs w = block_ws(ctx, M, K, N, prec, cplx);
   if (!workspace || ws_bytes < w.total) return ARBGPU_ERR_WORKSPACE;
   uint8_t *ws = (uint8_t *)workspace;
-  // whole-range scans: rows of each A part (stats 0, 1), columns of each B part (stats 2, 3)
-  BlockStats *pst = (BlockStats *)(ws + w.pstats);
-  BlockStats init{};
-  init.hA = init.hB = INT64_MIN;
-  BlockStats inits[4] = {init, init, init, init};
-  if (cudaMemcpyAsync(pst, inits, sizeof(inits), cudaMemcpyHostToDevice, s) != cudaSuccess)
-    return ARBGPU_ERR_CUDA;
+  const ScanRegion sr = scan_region_at((uint8_t *)region, M, N, cplx);
   BallsView Av[2], Bv[2];
   Lines rowsL[2], colsL[2];
   for (int q = 0; q < parts; ++q) {
     Av[q] = view_of(A[q]);
     Bv[q] = view_of(B[q]);
-    rowsL[q] = Lines{(int64_t *)(ws + w.prtop[q]), (int64_t *)(ws + w.prbot[q]),
-                     (int64_t *)(ws + w.prrad[q]), nullptr, nullptr, nullptr, nullptr};
-    colsL[q] = Lines{nullptr, nullptr, nullptr, (int64_t *)(ws + w.pctop[q]),
-                     (int64_t *)(ws + w.pcbot[q]), (int64_t *)(ws + w.pcrad[q]),
-                     (int64_t *)(ws + w.pcplus[q])};
-    {
-      LaunchScope sc(ctx, s, "scan_rows", M * K);
-      scan_rows_full_kernel<<<(unsigned)M, 256, 0, s>>>(
-          Av[q], K, lda, (int64_t *)rowsL[q].rtop, (int64_t *)rowsL[q].rbot,
-          (int64_t *)rowsL[q].rrad, pst + q);
-    }
-    {
-      LaunchScope sc(ctx, s, "scan_cols", K * N);
-      scan_cols_full_kernel<<<(unsigned)((N + 7) / 8), 1024, 0, s>>>(
-          Bv[q], K, N, ldb, (int64_t *)colsL[q].ctop, (int64_t *)colsL[q].cbot,
-          (int64_t *)colsL[q].crad, (int64_t *)colsL[q].cplus, pst + 2 + q);
-    }
-    if (cudaGetLastError() != cudaSuccess) return ARBGPU_ERR_CUDA;
+    rowsL[q] = Lines{sr.rtop[q], sr.rbot[q], sr.rrad[q], nullptr, nullptr, nullptr, nullptr};
+    colsL[q] = Lines{nullptr, nullptr, nullptr, sr.ctop[q], sr.cbot[q], sr.crad[q], sr.cplus[q]};
   }
-  BlockStats hst[4];
-  if (cudaMemcpyAsync(hst, pst, sizeof(hst), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
-      cudaStreamSynchronize(s) != cudaSuccess)
-    return ARBGPU_ERR_CUDA;
   for (int q = 0; q < parts; ++q)
     if (hst[q].special || hst[2 + q].special) return ARBGPU_ERR_LIMIT;
   auto lines_of = [&](int xa, int yb) {
@@ -1944,6 +1973,30 @@ arbgpu_status block_matmul(arbgpu_ctx *ctx, const arbgpu_balls *C, const arbgpu_
   // the host-side index lists must outlive their copies
   if (cudaStreamSynchronize(s) != cudaSuccess) return ARBGPU_ERR_CUDA;
   return cudaGetLastError() == cudaSuccess ? ARBGPU_OK : ARBGPU_ERR_CUDA;
+}
+
+// Ball matrix product by Algorithm 2 (real, or complex by four real products, Section IV-C):
+// scans, one read-back of their statistics, then the products.  Returns ARBGPU_ERR_LIMIT when the
+// inputs hold special values or exceed the path's limits (the caller then uses the classical
+// algorithm).
+arbgpu_status block_matmul(arbgpu_ctx *ctx, const arbgpu_balls *C, const arbgpu_balls *A,
+                           const arbgpu_balls *B, int64_t M, int64_t K, int64_t N, int64_t lda,
+                           int64_t ldb, int64_t ldc, int prec, bool cplx, void *workspace,
+                           size_t ws_bytes, cudaStream_t s, bool *used_block) {
+  *used_block = false;
+  if (!block_accepts(A, B, K, cplx)) return ARBGPU_ERR_LIMIT;
+  BlockWs w = block_ws(ctx, M, K, N, prec, cplx);
+  if (!workspace || ws_bytes < w.total) return ARBGPU_ERR_WORKSPACE;
+  void *region = (uint8_t *)workspace + w.scan;
+  arbgpu_status st = block_scan_launch(ctx, A, B, M, K, N, lda, ldb, cplx, region, nullptr, s);
+  if (st != ARBGPU_OK) return st;
+  BlockStats hst[4];
+  if (cudaMemcpyAsync(hst, scan_region_at((uint8_t *)region, M, N, cplx).pst, sizeof(hst),
+                      cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess)
+    return ARBGPU_ERR_CUDA;
+  return block_finish(ctx, C, A, B, M, K, N, lda, ldb, ldc, prec, cplx, region, hst, workspace,
+                      ws_bytes, s, used_block);
 }
 
 }  // namespace arbgpu

@@ -87,6 +87,30 @@ bool digit_gemm_fits(int SA, int SB, int64_t Kp);
 // The diagonal ranges the launcher uses: ends[g] = first diagonal after group g (g < groups).
 void digit_gemm_group_ends(int SA, int SB, int groups, int *ends);
 
+// Statistics of the scans of one real product's operands (zero-initialised: every field's identity).
+struct BlockStats {
+  int64_t pA, pB;         // largest significant-bit count of an entry
+  int64_t hA, hB;         // largest row / column height (top - bottom)
+  int32_t special;        // NaN / infinity / out-of-range exponent seen
+  int32_t radA, radB;     // a nonzero radius seen
+  int32_t pad;
+};
+
+// The block product in two phases, for callers that run many products: block_scan_launch (scans
+// into a region of block_scan_bytes, no synchronisation; the four BlockStats -- rows of A0, A1,
+// columns of B0, B1 -- go to `stats`, zeroed by the caller, or to the region when null), then,
+// once those statistics are on the host, block_finish.  Either returns ARBGPU_ERR_LIMIT for a
+// product the block path does not take (then: dot products).
+size_t block_scan_bytes(int64_t M, int64_t N, bool cplx);
+arbgpu_status block_scan_launch(arbgpu_ctx *ctx, const arbgpu_balls *A, const arbgpu_balls *B,
+                                int64_t M, int64_t K, int64_t N, int64_t lda, int64_t ldb,
+                                bool cplx, void *region, BlockStats *stats, cudaStream_t s);
+arbgpu_status block_finish(arbgpu_ctx *ctx, const arbgpu_balls *C, const arbgpu_balls *A,
+                           const arbgpu_balls *B, int64_t M, int64_t K, int64_t N, int64_t lda,
+                           int64_t ldb, int64_t ldc, int prec, bool cplx, void *region,
+                           const BlockStats *hst, void *workspace, size_t ws_bytes,
+                           cudaStream_t s, bool *used_block);
+
 // Block algorithm (block.cu): real or complex (C, A, B point to one or two arbgpu_balls).  Returns
 // ARBGPU_ERR_LIMIT (and *used_block = false) when the inputs hold special values or exceed the
 // path's limits.
