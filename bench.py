@@ -134,11 +134,20 @@ def kernel_summary(recs, step_ms_total):
                 "units": v[2]} for k, v in per.items()}
 
 
-def roofline_of(name, k, peaks, sm_mhz):
-    """Roofline entry of one kernel from its trace totals (ms_total, launches, units)."""
+def roofline_of(name, k, peaks, sm_mhz, limb_n=None):
+    """Roofline entry of one kernel from its trace totals (ms_total, launches, units).  For the
+    fused dot kernel (units = terms) `limb_n` gives the limbs per factor: 4 n^2 32-bit multiplies
+    per term."""
     avg_s = k["ms_total"] / k["launches"] * 1e-3
     units = k["units"] / k["launches"]
     alu_peak = SMS * IMAD_PER_CLK_PER_SM * sm_mhz * 1e6 / 1e12
+    if name == "dot_fused" and limb_n:
+        achieved = 4 * limb_n * limb_n * units / avg_s / 1e12
+        return {"bound": "alu", "kernel": name, "achieved": achieved, "peak": alu_peak,
+                "unit": "T int32-mul/s", "frac": achieved / alu_peak, "traffic": None,
+                "work": f"{units:.4g} terms per launch x {4 * limb_n * limb_n} 32-bit multiplies",
+                "peak_source": f"derived: {SMS} SMs x {IMAD_PER_CLK_PER_SM} IMAD/clk x "
+                               f"{sm_mhz:.0f} MHz"}
     if name in ("crt_gemm", "digit_gemm", "digit_gemm_mid", "digit_gemm_rad"):
         achieved = 2.0 * units / avg_s / 1e12
         peak = peaks.get("bf16_tflops", 1900.0)
@@ -440,7 +449,7 @@ def run_workload(args):
             roofline["share_of_step"] = round(sum(
                 kernels.get(k, {}).get("share", 0) or 0 for k in DOT_KERNELS), 4)
         else:
-            roofline = roofline_of(dom[0], dom[1], peaks, sm_mhz)
+            roofline = roofline_of(dom[0], dom[1], peaks, sm_mhz, limb_n=(prec + 63) // 64)
             roofline["share_of_step"] = dom[1]["share"]
     graph = None
     if wl == "n32dots":
