@@ -1089,7 +1089,7 @@ static size_t crt_smem_bytes(const IntProduct &p, int NW) {
 }
 
 template <int NW>
-__global__ void __launch_bounds__(128) block_round_regs_kernel(const RoundArgs a) {
+__global__ void __launch_bounds__(128, 6) block_round_regs_kernel(const RoundArgs a) {
   constexpr int L32 = 2 * NW;
   extern __shared__ uint4 smem_u4[];
   uint32_t *sQ = (uint32_t *)smem_u4;
