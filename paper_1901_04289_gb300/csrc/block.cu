@@ -511,10 +511,11 @@ struct Ends {
 };
 
 // Per-modulus constants (the first CRT_MAX_MODULI primes below 2^16), loaded once per device:
-// m_t, floor((2^64 - 1) / m_t) and floor(2^32 / m_t).
+// m_t, floor((2^64 - 1) / m_t), floor(2^32 / m_t) and 2^32 mod m_t.
 __constant__ uint32_t c_mods[CRT_MAX_MODULI];
 __constant__ uint64_t c_inv[CRT_MAX_MODULI];
 __constant__ uint32_t c_inv32[CRT_MAX_MODULI];  // floor(2^32 / m_t)
+__constant__ uint32_t c_pow32m[CRT_MAX_MODULI];  // 2^32 mod m_t
 
 // Device copies of the tables of one modulus count (in the workspace).
 struct CrtTables {
@@ -739,12 +740,23 @@ __global__ void __launch_bounds__(128) residue_split_kernel(
       }
     }
     const uint32_t m = c_mods[t];
-    const uint64_t iv = c_inv[t];
     const uint32_t yt = ymul ? __ldg(ymul + t) : 1u;
     const uint32_t i32 = c_inv32[t];
+    const uint32_t c32 = c_pow32m[t];  // 2^32 mod m
 #pragma unroll
     for (int u = 0; u < RE; ++u) {
-      int32_t res = (int32_t)barrett_mod(acc[u], m, iv);
+      // acc = ah 2^32 + al (ah < 2^20): ((ah mod m) c32 + al) mod m in 32-bit Barrett steps
+      const uint32_t ah = (uint32_t)(acc[u] >> 32), al = (uint32_t)acc[u];
+      uint32_t r1 = ah - __umulhi(ah, i32) * m;
+      if (r1 >= m) r1 -= m;
+      const uint32_t x1 = r1 * c32;  // < 2^32
+      uint32_t r2 = x1 - __umulhi(x1, i32) * m;
+      if (r2 >= m) r2 -= m;
+      uint32_t r3 = al - __umulhi(al, i32) * m;
+      if (r3 >= m) r3 -= m;
+      uint32_t rs = r2 + r3;
+      if (rs >= m) rs -= m;
+      int32_t res = (int32_t)rs;
       if (ymul) {  // res y < 2^32: one 32-bit Barrett step and one correction
         const uint32_t x = (uint32_t)res * yt;
         uint32_t r2 = x - __umulhi(x, i32) * m;
@@ -793,12 +805,15 @@ static arbgpu_status ensure_crt_constants(int device) {
   if (done[device & 255]) return ARBGPU_OK;
   const CrtPlan *full = crt_plan(CRT_MAX_MODULI);
   if (!full) return ARBGPU_ERR_CUDA;
-  std::vector<uint32_t> inv32(CRT_MAX_MODULI);
-  for (int t = 0; t < CRT_MAX_MODULI; ++t)
+  std::vector<uint32_t> inv32(CRT_MAX_MODULI), p32(CRT_MAX_MODULI);
+  for (int t = 0; t < CRT_MAX_MODULI; ++t) {
     inv32[t] = (uint32_t)((((uint64_t)1) << 32) / full->mods[t]);
+    p32[t] = (uint32_t)((((uint64_t)1) << 32) % full->mods[t]);
+  }
   if (cudaMemcpyToSymbol(c_mods, full->mods.data(), 4 * CRT_MAX_MODULI) != cudaSuccess ||
       cudaMemcpyToSymbol(c_inv, full->inv.data(), 8 * CRT_MAX_MODULI) != cudaSuccess ||
-      cudaMemcpyToSymbol(c_inv32, inv32.data(), 4 * CRT_MAX_MODULI) != cudaSuccess)
+      cudaMemcpyToSymbol(c_inv32, inv32.data(), 4 * CRT_MAX_MODULI) != cudaSuccess ||
+      cudaMemcpyToSymbol(c_pow32m, p32.data(), 4 * CRT_MAX_MODULI) != cudaSuccess)
     return ARBGPU_ERR_CUDA;
   done[device & 255] = true;
   return ARBGPU_OK;
