@@ -304,13 +304,9 @@ __global__ void __launch_bounds__(CG_THREADS, 1)
   CgShared *sh = (CgShared *)(stages + (size_t)CG_STAGES * CG_STAGE_BYTES);
   const int warp = threadIdx.x >> 5;
   const int lane = threadIdx.x & 31;
+  // persistent: work item w = (modulus w / ntiles, output tile w % ntiles), a grid stride apart
   const int ntiles = P.tiles_m * P.tiles_n;
-  const int tile = blockIdx.x % ntiles;
-  const int bchunk = blockIdx.x / ntiles;
-  const int b_first = bchunk * P.ipc;
-  const int b_last = min(P.batch, b_first + P.ipc);
-  const int mt = tile / P.tiles_n, nt = tile % P.tiles_n;
-  const int m0 = mt * TG_BM, n0 = nt * TG_BN;
+  const int nitems = ntiles * P.batch;
   const int nkb = P.Kp / TG_BK;
 
   if (threadIdx.x == 0) {
@@ -345,7 +341,9 @@ __global__ void __launch_bounds__(CG_THREADS, 1)
       tma_prefetch_desc(&tmB);
       uint32_t it = 0;
       bool ok = true;
-      for (int bi = b_first; bi < b_last && ok; ++bi) {
+      for (int w = blockIdx.x; w < nitems && ok; w += gridDim.x) {
+        const int bi = w / ntiles, tile = w - bi * ntiles;
+        const int m0 = (tile / P.tiles_n) * TG_BM, n0 = (tile % P.tiles_n) * TG_BN;
         for (int kb = 0; kb < nkb; ++kb, ++it) {
           const int s = it % CG_STAGES;
           if (!mbar_wait(&sh->empty[s], ((it / CG_STAGES) & 1) ^ 1, abort)) {
@@ -372,7 +370,7 @@ __global__ void __launch_bounds__(CG_THREADS, 1)
       const uint32_t idesc = idesc_bf16_f32(TG_BM, 2 * TG_BN);
       uint32_t it = 0;
       bool ok = true;
-      for (int bi = b_first, ii = 0; bi < b_last && ok; ++bi, ++ii) {
+      for (int w = blockIdx.x, ii = 0; w < nitems && ok; w += gridDim.x, ++ii) {
         // the drain must have read the previous item's accumulators
         if (!mbar_wait(&sh->acce, (ii & 1) ^ 1, abort)) {
           give_up();
@@ -410,9 +408,10 @@ __global__ void __launch_bounds__(CG_THREADS, 1)
     const int col0 = 32 * ((warp - 2) >> 2);  // its 32 of the tile's 128 columns
     const int row = 32 * q + lane;
     const uint32_t lane_addr = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)col0;
-    const int64_t gm = m0 + row;
-    const int64_t gcol = n0 + col0;
-    for (int bi = b_first, ii = 0; bi < b_last; ++bi, ++ii) {
+    for (int w = blockIdx.x, ii = 0; w < nitems; w += gridDim.x, ++ii) {
+      const int bi = w / ntiles, tile = w - bi * ntiles;
+      const int64_t gm = (tile / P.tiles_n) * TG_BM + row;
+      const int64_t gcol = (tile % P.tiles_n) * TG_BN + col0;
       const bool got = __all_sync(0xffffffffu, mbar_wait(&sh->accf, ii & 1, abort));
       if (!got) {
         if (lane == 0) give_up();
@@ -615,7 +614,9 @@ arbgpu_status launch_digit_gemm(arbgpu_ctx *ctx, const DigitGemmArgs &a, cudaStr
     if (grid > 0x7fffffff) return ARBGPU_ERR_LIMIT;
     LaunchScope scope(ctx, stream, a.name ? a.name : "crt_gemm",
                       (int64_t)(a.SA) * a.SB * (int64_t)a.M * a.N * a.Kp * P.batch);
-    crt_gemm_kernel<<<(unsigned)grid, CG_THREADS, CG_SMEM_BYTES, stream>>>(tmA, tmB, P);
+    const int64_t items = (int64_t)P.tiles_m * P.tiles_n * P.batch;
+    const int64_t cgrid = items < ctx->sm_count ? items : ctx->sm_count;
+    crt_gemm_kernel<<<(unsigned)cgrid, CG_THREADS, CG_SMEM_BYTES, stream>>>(tmA, tmB, P);
     return cudaGetLastError() == cudaSuccess ? ARBGPU_OK : ARBGPU_ERR_CUDA;
   }
   if (grid > 0x7fffffff) return ARBGPU_ERR_LIMIT;
