@@ -529,6 +529,7 @@ struct CrtTables {
 // One exact integer product.  kind 0: digit + carry form of T itself.  kind 1 (multimodular): for
 // every modulus t, z_t = P_t mod m_t ([t][Mp][Np] uint16 in `digits`) of the exact residue product
 // P_t = sum_k r_ik (s_kj y_t mod m_t), from which T follows by the Chinese remainder theorem.
+// kind 2: T itself as int64 [Mp][Np] in `digits` (a radius product, 0 <= T < 2^63).
 struct IntProduct {
   const uint8_t *digits;
   const int32_t *carries;
@@ -832,6 +833,7 @@ struct RoundArgs {
 __device__ __forceinline__ Mag product_mag(const IntProduct &p, int64_t i, int64_t j, int64_t Mp,
                                            int64_t Np, int64_t base) {
   if (p.ND == 0) return Mag{0u, 0};
+  if (p.kind == 2) return mag_from_u64((uint64_t)__ldg((const int64_t *)p.digits + i * Np + j), base);
   uint64_t acc[4];
   assemble(p, i, j, Mp, Np, acc);  // nonnegative and < 2^64 (13+13+log2 K + 2 bits)
   return mag_from_u64(acc[0], base);
@@ -1080,6 +1082,7 @@ __device__ __forceinline__ void round_store_regs(const uint64_t (&T)[NW], int64_
 __device__ __forceinline__ Mag product_mag_regs(const IntProduct &p, int64_t i, int64_t j,
                                                 int64_t Mp, int64_t Np, int64_t base) {
   if (p.ND == 0) return Mag{0u, 0};
+  if (p.kind == 2) return mag_from_u64((uint64_t)__ldg((const int64_t *)p.digits + i * Np + j), base);
   uint64_t acc[2];
   digit_assemble_regs<2>(p, i, j, Mp, Np, acc);  // nonnegative and < 2^64
   return mag_from_u64(acc[0], base);
@@ -1425,7 +1428,7 @@ struct BlockWs {
   // per output part: accumulator, initial balls, basecase index list
   size_t acc[2], err[2], rman[2], rexp[2], ilimbs[2], iexp[2], iflags[2], irman[2], irexp[2], bk[2];
   // multimodular engine: residue planes, residue products, tables
-  size_t resA, resB, cdig, ccar;
+  size_t resA, resB, cdig, ccar, craw;
   size_t total;
   int Smax, NDmax, Gmax, Gr, maxb, nacc, NMmax, NMWmax;
   int64_t Kp, Mp, Np;
@@ -1496,9 +1499,11 @@ static BlockWs block_ws(arbgpu_ctx *ctx, int64_t M, int64_t K, int64_t N, int pr
     w.irexp[q] = take(8 * MN);
     w.bk[q] = take(4 * 2 * (size_t)K);
   }
-  w.resA = take((size_t)2 * w.NMmax * M * w.Kp * 2);
-  w.resB = take((size_t)2 * w.NMmax * N * w.Kp * 2);
+  // residue planes, then the two radius products' operand planes (batch items NM and NM + 1)
+  w.resA = take((size_t)2 * (w.NMmax + 2) * M * w.Kp * 2);
+  w.resB = take((size_t)2 * (w.NMmax + 2) * N * w.Kp * 2);
   w.cdig = take((size_t)3 * w.NMmax * w.Mp * w.Np);
+  w.craw = take((size_t)2 * 8 * w.Mp * w.Np);  // the two radius products as int64
   w.ccar = take(256);  // the multimodular GEMM writes no carries
   w.total = off;
   return w;
@@ -1599,10 +1604,16 @@ static arbgpu_status run_block(arbgpu_ctx *ctx, const BlockWs &w, uint8_t *ws, c
     if (crt_device_tables(ctx, plan, &dt) != ARBGPU_OK) return ARBGPU_ERR_CUDA;
     CrtTables ct{dt.Q32, dt.M32, dt.y, dt.rinv, plan->NM, plan->NMW, plan->NW32P};
     __nv_bfloat16 *resA = (__nv_bfloat16 *)(ws + w.resA), *resB = (__nv_bfloat16 *)(ws + w.resB);
+    // with radii, the two radius products ride in the same GEMM as items NM and NM + 1: their
+    // operand planes follow the residue planes, and their exact values come out as int64
+    const bool fold = (radA || radB) && crt_gemm_one_chain(Kp);
+    __nv_bfloat16 *fA1 = resA + (size_t)2 * NM * M * Kp, *fA2 = fA1 + (size_t)2 * M * Kp;
+    __nv_bfloat16 *fB1 = resB + (size_t)2 * NM * N * Kp, *fB2 = fB1 + (size_t)2 * N * Kp;
     {
       const int64_t n = M * Kp;
       LaunchScope sc(ctx, s, "residues_a", n * NM * ((hA + 2 + 31) / 32 + 1));
-      const SplitOut ro{nullptr, radB ? rA1 : nullptr, radA ? rA2 : nullptr};
+      const SplitOut ro = fold ? SplitOut{nullptr, fA1, fA2}
+                               : SplitOut{nullptr, radB ? rA1 : nullptr, radA ? rA2 : nullptr};
       launch_residues((int)((hA + 2 + 31) / 32) + 1, n, s, Av, false, M, k0, Kb, Kp, lda,
                       ln.rbot, NM, dt.pow32, plan->NCHP, nullptr, resA, ro, ln.rtop, ln.rrad,
                       nullptr);
@@ -1612,21 +1623,32 @@ static arbgpu_status run_block(arbgpu_ctx *ctx, const BlockWs &w, uint8_t *ws, c
       LaunchScope sc(ctx, s, "residues_b", n * NM * ((hB + 2 + 31) / 32 + 1));
       // the right-hand residues carry the factor y_t = (M / m_t)^-1 mod m_t of the
       // reconstruction, so the residue products are already z_t = P_t y_t mod m_t
-      const SplitOut ro{nullptr, radB ? rB1 : nullptr, radA ? rB2 : nullptr};
+      const SplitOut ro = fold ? SplitOut{nullptr, fB1, fB2}
+                               : SplitOut{nullptr, radB ? rB1 : nullptr, radA ? rB2 : nullptr};
       launch_residues((int)((hB + 2 + 31) / 32) + 1, n, s, Bv, true, N, k0, Kb, Kp, ldb,
                       ln.cbot, NM, dt.pow32, plan->NCHP, dt.y, resB, ro, ln.ctop, ln.crad,
                       ln.cplus);
     }
     if (cudaGetLastError() != cudaSuccess) return ARBGPU_ERR_CUDA;
     DigitGemmArgs g{resA, resB, (int)M, (int)N, Kp, 2, 2, 1, ws + w.cdig,
-                    (int32_t *)(ws + w.ccar), "crt_gemm", NM};
+                    (int32_t *)(ws + w.ccar), "crt_gemm", NM + (fold ? 2 : 0)};
     g.zout = (uint16_t *)(ws + w.cdig);
     g.ztab = dt.ztab;
     g.zinv = dt.inv;
+    if (fold) {
+      g.nz = NM;
+      g.zraw = (int64_t *)(ws + w.craw);
+    }
     arbgpu_status stg = launch_digit_gemm(ctx, g, s);
     if (stg != ARBGPU_OK) return stg;
     *mid = IntProduct{ws + w.cdig, nullptr, 3, 1, {}, 1, ct};
     mid->ends.e[0] = 3;
+    if (fold) {
+      *rp1 = radB ? IntProduct{ws + w.craw, nullptr, 1, 1, {}, 2, {}} : IntProduct{};
+      *rp2 = radA ? IntProduct{ws + w.craw + (size_t)8 * w.Mp * w.Np, nullptr, 1, 1, {}, 2, {}}
+                  : IntProduct{};
+      return ARBGPU_OK;
+    }
   } else {
     const int ND = SA + SB - 1;
     const int G = digit_gemm_groups(ctx, (int)M, (int)N, ND);

@@ -80,7 +80,14 @@ struct DigitGemmArgs {
   uint16_t *zout = nullptr;
   const uint32_t *ztab = nullptr;
   const uint64_t *zinv = nullptr;
+  // in that mode, items from `nz` on (when zraw is set) write their exact P as int64 [Mp][Np]
+  // to zraw instead (nonnegative products, for instance the radius bounds)
+  int nz = 0;
+  int64_t *zraw = nullptr;
 };
+// Whether multimodular-mode products of this inner dimension run in the one-chain kernel (the one
+// that also takes raw items).
+bool crt_gemm_one_chain(int64_t Kp);
 arbgpu_status launch_digit_gemm(arbgpu_ctx *ctx, const DigitGemmArgs &a, cudaStream_t stream);
 int digit_gemm_groups(arbgpu_ctx *ctx, int M, int N, int ND);
 bool digit_gemm_fits(int SA, int SB, int64_t Kp);

@@ -439,6 +439,13 @@ __global__ void __launch_bounds__(CG_THREADS, 1)
       tc_fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive(&sh->acce);
+      if (bi >= P.nz) {  // a raw item: P itself
+        longlong2 *rdst =
+            (longlong2 *)(P.zraw + ((int64_t)(bi - P.nz) * P.Mp + gm) * P.Np + gcol);
+#pragma unroll
+        for (int c = 0; c < 16; ++c) rdst[c] = make_longlong2(Pc[2 * c], Pc[2 * c + 1]);
+        continue;
+      }
       // |P| <= Kp (m / 2)^2 < 2^50, so P + m 2^35 is in (0, 2^52)
       const uint32_t m = __ldg(P.ztab + 4 * bi);
       const uint64_t i64 = __ldg(P.zinv + bi);
@@ -541,6 +548,8 @@ void digit_gemm_group_ends(int SA, int SB, int groups, int *ends) {
   ends[groups - 1] = ND;
 }
 
+bool crt_gemm_one_chain(int64_t Kp) { return Kp <= CG_MAX_KP; }
+
 arbgpu_status launch_digit_gemm(arbgpu_ctx *ctx, const DigitGemmArgs &a, cudaStream_t stream) {
   if (a.M <= 0 || a.N <= 0 || a.Kp <= 0 || (a.Kp % TG_BK) != 0 || a.SA < 1 || a.SB < 1)
     return ARBGPU_ERR_INVALID;
@@ -563,6 +572,9 @@ arbgpu_status launch_digit_gemm(arbgpu_ctx *ctx, const DigitGemmArgs &a, cudaStr
   P.zout = a.zout;
   P.ztab = a.ztab;
   P.zinv = a.zinv;
+  P.zraw = a.zraw;
+  P.nz = a.zraw ? a.nz : P.batch;
+  if (a.zraw && (a.Kp > CG_MAX_KP || a.nz < 0 || a.nz > P.batch)) return ARBGPU_ERR_INVALID;
   if (a.zout && (a.SA != 2 || a.SB != 2 || a.groups != 1 || !a.ztab || !a.zinv))
     return ARBGPU_ERR_INVALID;
   const int G = a.groups;

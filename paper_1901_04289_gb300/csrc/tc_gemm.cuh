@@ -59,6 +59,8 @@ struct DigitGemmParams {
   // Multimodular mode (2 x 2 digits, one group): instead of digits and carries, item b writes
   // P_b mod m_b of its exact product P_b to zout[b][Mp][Np] (uint16).
   uint16_t *zout;
+  int nz;                   // items [0, nz) are reduced; items [nz, batch) write P itself to zraw
+  int64_t *zraw;            // [batch - nz][Mp][Np]
   const uint32_t *ztab;     // [batch][4]: m_b, unused
   const uint64_t *zinv;     // [batch]: floor((2^64 - 1) / m_b)
 };
