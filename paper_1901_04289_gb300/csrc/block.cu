@@ -12,6 +12,7 @@
 //   gemm   T = (E A)(B F) exactly on the tensor cores; P1 = U(|A|) V(R_B), P2 = U(R_A) V(|B|+R_B).
 //   round  C_ij = RNE_p(T_ij 2^(-e_i - f_j)) (one rounding of the exact entry) and
 //          R_ij >= eps_round + P1 2^(...) + P2 2^(...), rounded up to a 30-bit radius.
+#include <algorithm>
 #include <cstdlib>
 #include <cstring>
 #include <mutex>
@@ -796,6 +797,468 @@ static void launch_residues(int nch, int64_t n, cudaStream_t s, const BallsView 
   else if (nch <= 34) ARB_RES(34, 1);
   else ARB_RES(CRT_MAX_CHUNKS32, 1);
 #undef ARB_RES
+}
+
+// ---- Residues on the tensor cores.  With the signed base-256 digits x_d = ±(byte d of |X|)
+// (d < 4 NCH, the sign of X on every digit),
+//
+//     X mod m_t = (sum_d x_d w_{t,d}) mod m_t,   w_{t,d} = 2^(8d) mod m_t (times y_t for B),
+//
+// is a product of a digit matrix [entries][digits] and a weight table [digits][(t, byte)]: the
+// balanced weight w (|w| < m_t / 2) is written as 256 h + l with l, h in [-128, 128], column 2t
+// holding l and 2t + 1 holding h.  Every product is at most 255 * 128 in magnitude and at most 128
+// of them are summed, so each FP32 sum S is an integer with |S| < 2^22: exact.  The drain reduces
+// x = S_l + 256 S_h (|x| < 2^31) in FP32 without rounding error: q = rint(x / m) from a rounded x
+// is off by at most one for |x / m| < 2^16, r = (256 S_h - q m) + S_l is exact (every partial
+// result is an integer below 2^24), and one more rint(r / m) step balances r.
+constexpr int RT_ROWS = 128;            // entries per tile: the MMA's M
+constexpr int RT_TILE = RT_ROWS * 128;  // bytes of one 64-digit slab of a tile (SW128, K-major)
+constexpr int RT_MAX_WG = 4;            // warpgroups per CTA, each with its own tile in flight
+constexpr float RT_MAGIC = 12582912.0f; // 1.5 * 2^23: adding it rounds |v| < 2^22 to an integer
+// Dynamic shared memory of at least this much keeps one CTA per SM, so the CTA's 512 TMEM columns
+// are always free when it starts.
+constexpr size_t RT_SMEM_MIN = 120 * 1024;
+constexpr size_t RT_SMEM_MAX = 227 * 1024;
+
+struct RtShared {
+  uint64_t bar[RT_MAX_WG];
+  uint32_t tmem_base;
+  int never;                          // an abort flag nothing sets
+  int fail[RT_MAX_WG];
+  uint32_t info[RT_MAX_WG][RT_ROWS];  // radius operands u1 | u2 << 14 of each tile row
+};
+
+__device__ __forceinline__ void named_bar(int id, int n) {
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory");
+}
+__device__ __forceinline__ void fence_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void tma_store_3d(const CUtensorMap *tm, const void *src, int c0, int c1,
+                                             int c2) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.global.shared::cta.bulk_group [%0, {%2, %3, %4}], [%1];" ::"l"(
+          (uint64_t)tm),
+      "r"(smem_u32(src)), "r"(c0), "r"(c1), "r"(c2)
+      : "memory");
+  asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+}
+__device__ __forceinline__ void tma_store_wait_read() {
+  asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+}
+__device__ __forceinline__ void tma_store_wait_all() {
+  asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+}
+
+__device__ __forceinline__ void cp_async(void *dst, const void *src, int bytes) {
+  if (bytes == 8)
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_u32(dst)), "l"(src)
+                 : "memory");
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_u32(dst)), "l"(src)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+  asm volatile("cp.async.commit_group;" ::: "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.wait_group 0;" ::: "memory");
+}
+
+// Top limbs of an entry the residue step can need: |X| = L 2^sh < 2^(32 NCH) and L's top bit is
+// bit 64 nl - 1, so the nonzero bits of L that reach X lie in its top ceil(NCH / 2) + 1 limbs.
+template <int NCH>
+constexpr int rt_top_limbs() {
+  return (NCH + 1) / 2 + 1;
+}
+// Per producer thread, the raw fields of its next entry, staged by cp.async one tile ahead:
+// words [0] exp, [1] bot, [2] flags | rad_man << 32, [3] rad_exp, [4] and [5] the two radius
+// windows, [6 ...] the top limbs (word 6 + i = limb nl - NLW + i).  Word-major: [word][128].
+constexpr int RT_SLOT_FIXED = 6;
+
+// The float sg * b for byte b of `w` (exact): sg (2^23 + b) + sgb with sgb = -sg 2^23.
+__device__ __forceinline__ float signed_byte(uint32_t w, int b, float sg, float sgb) {
+  return __fmaf_rn(__uint_as_float(__byte_perm(w, 0x4B000000u, 0x7540u | (uint32_t)b)), sg, sgb);
+}
+__device__ __forceinline__ uint32_t bf16x2_bits(float lo, float hi) {
+  const __nv_bfloat162 p = __floats2bfloat162_rn(lo, hi);
+  return *(const uint32_t *)&p;
+}
+
+struct RtArgs {
+  BallsView X;
+  bool is_b;
+  int64_t rows, k0, K, Kp, ld;
+  const int64_t *bot;  // scan: per-row lowest exponent
+  int NM, NPAD, WG, wg_cols, NPL;  // NPL: staged planes per tile (2 NM, plus 4 radius planes)
+  uint32_t tcols;
+  const uint16_t *wtab;  // [NPAD][128] BF16 weight table of this operand
+  const float *rinv;     // [NM] 1 / m_t
+  SplitOut ro;           // radius operands written directly (when not part of the staged planes)
+  const int64_t *top, *radtop, *plustop;
+  int *status;
+};
+
+// Tile = JT operand rows x KT inner positions.  The producer thread reads the entry (pj, pk)
+// (consecutive threads take consecutive elements of X in memory) and fills tile row pj * KT + pk;
+// the drain thread t reads TMEM lane t, i.e. the entry (t / KT, t % KT), and stages its residues
+// at [plane][t], which is the layout of the TMA store's box {KT, JT, planes}.
+template <int NCH, bool IS_B>
+__global__ void __launch_bounds__(RT_ROWS *RT_MAX_WG, 1)
+    residue_tc_kernel(const __grid_constant__ CUtensorMap tmo, const __grid_constant__ RtArgs a) {
+  constexpr int KD = (4 * NCH + 63) / 64;  // 64-digit slabs
+  constexpr int NLW = rt_top_limbs<NCH>();
+  constexpr int SW = RT_SLOT_FIXED + NLW;
+  constexpr int JT = IS_B ? 4 : 2;  // operand rows per tile
+  constexpr int KT = RT_ROWS / JT;  // inner positions per tile (a divisor of Kp)
+  extern __shared__ __align__(1024) uint8_t smem_raw[];
+  uint8_t *sW = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  uint8_t *sA = sW + (size_t)KD * a.NPAD * 128;
+  uint16_t *sO = (uint16_t *)(sA + (size_t)a.WG * KD * RT_TILE);
+  uint64_t *sSlot = (uint64_t *)(sO + (size_t)a.WG * a.NPL * RT_ROWS);
+  float2 *sMod = (float2 *)(sSlot + (size_t)a.WG * SW * RT_ROWS);
+  RtShared *sh = (RtShared *)(sMod + ((a.NM + 1) & ~1));
+  const int g = threadIdx.x >> 7, t = threadIdx.x & 127;
+  const int lane = t & 31, wq = t >> 5;
+
+  if (threadIdx.x == 0) {
+    for (int q = 0; q < a.WG; ++q) {
+      mbar_init(&sh->bar[q], 1);
+      sh->fail[q] = 0;
+    }
+    sh->never = 0;
+    fence_mbar_init();
+  }
+  if (threadIdx.x < 32) {
+    tmem_alloc(&sh->tmem_base, a.tcols);
+    tmem_relinquish();
+  }
+  if (threadIdx.x == 32) tma_prefetch_desc(&tmo);
+  // the weight table into K-major slabs of 64 columns with the 128-byte swizzle
+  for (int q = threadIdx.x; q < a.NPAD * 8 * KD; q += blockDim.x) {
+    const int n = q / (8 * KD), c = q - n * 8 * KD;
+    const uint4 v = __ldg((const uint4 *)(a.wtab + (size_t)n * 128) + c);
+    *(uint4 *)(sW + (size_t)(c >> 3) * a.NPAD * 128 + (size_t)n * 128 +
+               (((c & 7) ^ (n & 7)) << 4)) = v;
+  }
+  for (int q = threadIdx.x; q < a.NM; q += blockDim.x)
+    sMod[q] = make_float2((float)c_mods[q], __ldg(a.rinv + q));
+  fence_async_smem();
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+
+  const int ntk = (int)(a.Kp / KT);
+  const int nT = (int)((a.rows + JT - 1) / JT) * ntk;  // the host keeps this below 2^30
+  const int tstride = (int)gridDim.x * a.WG;
+  const int dtr = tstride / ntk, dtk = tstride - dtr * ntk;
+  uint8_t *myA = sA + (size_t)g * KD * RT_TILE;
+  uint16_t *myO = sO + (size_t)g * a.NPL * RT_ROWS;
+  const uint32_t tm_mma = sh->tmem_base + (uint32_t)(g * a.wg_cols);
+  const uint32_t tm_lane = tm_mma + ((uint32_t)(32 * wq) << 16);
+  const uint32_t idesc = idesc_bf16_f32(RT_ROWS, a.NPAD);
+  // producer's entry (pj, pk): for B, the four threads of a 32-byte sector of a row of B take
+  // consecutive columns j, and the eight threads of a quarter warp fill tile rows with distinct
+  // (row mod 8), so their swizzled 16-byte stores hit distinct banks
+  const int pj = IS_B ? ((t >> 3) & 3) : (t >> 6);
+  const int pk = IS_B ? ((t & 7) + 8 * (t >> 5)) : (t & 63);
+  const int prow = pj * KT + pk;
+  const int dj = t / KT, dk = t % KT;  // drain entry; dj is the same across a warp
+  const bool rad_box = a.NPL > 2 * a.NM;
+  const int64_t plane = a.rows * a.Kp;
+  const bool want_rad = a.ro.r1 || a.ro.r2 || rad_box;
+  const bool w1 = rad_box || a.ro.r1, w2 = rad_box || a.ro.r2;
+  const int nl = a.X.nlimbs;
+  const int lbase = nl - NLW;  // limb index of the slot's first limb (lower limbs are not read)
+  uint64_t *slot = sSlot + ((size_t)g * RT_ROWS + t) * SW;
+  // issue the copies of the producer's entry of tile (tr, tk) (nothing when outside X)
+  auto prefetch = [&](int tr, int tk) {
+    const int64_t r = (int64_t)tr * JT + pj, k = (int64_t)tk * KT + pk;
+    if (r < a.rows && k < a.K) {
+      const BallsView &X = a.X;
+      const int64_t e = IS_B ? ((a.k0 + k) * a.ld + r) : (r * a.ld + a.k0 + k);
+      cp_async(slot, X.exp + e, 8);
+      cp_async(slot + 1, a.bot + r, 8);
+      cp_async(slot + 2, X.flags + e, 4);
+      if (want_rad) {
+        cp_async((uint32_t *)(slot + 2) + 1, X.rad_man + e, 4);
+        cp_async(slot + 3, X.rad_exp + e, 8);
+        if (w1) cp_async(slot + 4, (IS_B ? a.radtop : a.top) + r, 8);
+        if (w2) cp_async(slot + 5, (IS_B ? a.plustop : a.radtop) + r, 8);
+      }
+#pragma unroll
+      for (int i = 0; i < NLW; ++i)
+        if (lbase + i >= 0)
+          cp_async(slot + RT_SLOT_FIXED + i, X.limbs + (int64_t)(lbase + i) * X.stride + e, 8);
+    }
+    cp_async_commit();
+  };
+  const uint32_t *Wd = (const uint32_t *)(slot + RT_SLOT_FIXED);  // 32-bit words of the limbs
+  const int jlo = lbase < 0 ? -2 * lbase : 0;                     // first word that exists
+  int tile = (int)blockIdx.x * a.WG + g;
+  int tr = tile / ntk, tk = tile - tr * ntk;
+  if (tile < nT) prefetch(tr, tk);
+  uint32_t phase = 0;
+  for (; tile < nT; tile += tstride) {
+    if (sh->fail[g]) break;  // set only between this warpgroup's two barriers of a tile
+    int ntr = tr + dtr, ntk2 = tk + dtk;  // the next tile of this warpgroup
+    if (ntk2 >= ntk) {
+      ntk2 -= ntk;
+      ++ntr;
+    }
+    {
+      // ---- produce: signed digits of one entry into tile row prow, radius operands into info
+      const int64_t r = (int64_t)tr * JT + pj, k = (int64_t)tk * KT + pk;
+      uint32_t ch[NCH];
+#pragma unroll
+      for (int c = 0; c < NCH; ++c) ch[c] = 0;
+      uint32_t info = 0;
+      float sg = 1.0f;
+      cp_async_wait_all();
+      if (r < a.rows && k < a.K) {
+        const int64_t ex = (int64_t)slot[0];
+        const uint64_t w2f = slot[2];
+        const uint32_t fl = (uint32_t)w2f;
+        Mag absm{0u, 0};
+        if (!(fl & (ARBGPU_FLAG_ZERO | SPECIAL_MASK))) {
+          if (fl & ARBGPU_FLAG_SIGN) sg = -1.0f;
+          // chunk c = bits [32c - sh, 32c - sh + 32) of L: a funnel shift of the slot's words
+          // q0 + c and q0 + c + 1 by b, with 32 q0 + b = -sh - 64 lbase
+          const int64_t p0 = -(ex - 64LL * nl - (int64_t)slot[1]) - 64LL * lbase;
+          if (p0 > -32LL * (NCH + 1) && p0 < 64LL * NLW) {
+            const int q0 = (int)(p0 >> 5), b = (int)(p0 & 31);
+            uint32_t wv[NCH + 1];
+#pragma unroll
+            for (int c = 0; c <= NCH; ++c) {
+              const int j = q0 + c;
+              wv[c] = ((unsigned)(j - jlo) < (unsigned)(2 * NLW - jlo)) ? Wd[j] : 0u;
+            }
+#pragma unroll
+            for (int c = 0; c < NCH; ++c) ch[c] = __funnelshift_r(wv[c], wv[c + 1], b);
+          }
+          if (want_rad) {
+            const uint64_t top = slot[RT_SLOT_FIXED + NLW - 1];  // limb nl - 1
+            uint64_t bm = (top >> 34) + 1;  // 30-bit upper bound of |m| (Section III-E)
+            int64_t ee = ex;
+            if (bm == ((uint64_t)1 << 30)) {
+              bm >>= 1;
+              ee += 1;
+            }
+            absm = Mag{(uint32_t)bm, ee};
+          }
+        }
+        if (want_rad) {
+          const Mag rad{(uint32_t)(w2f >> 32), (int64_t)slot[3]};
+          uint32_t u1 = 0, u2 = 0;
+          const int64_t f1 = (int64_t)slot[4], f2 = (int64_t)slot[5];
+          if (!IS_B) {
+            if (w1) u1 = window_up(absm.man, absm.exp, f1);
+            if (w2) u2 = window_up(rad.man, rad.exp, f2);
+          } else {
+            if (w1) u1 = window_up(rad.man, rad.exp, f1);
+            if (w2) {
+              const Mag plus = mag_add_up(absm, rad);
+              u2 = window_up(plus.man, plus.exp, f2);
+            }
+          }
+          info = u1 | (u2 << 14);
+        }
+      }
+      // every slot value is in registers now: stage the next tile's entry
+      if (tile + tstride < nT) prefetch(ntr, ntk2);
+      sh->info[g][prow] = info;
+      const float sgb = -8388608.0f * sg;
+      uint8_t *row = myA + (size_t)prow * 128;
+#pragma unroll
+      for (int s = 0; s < KD; ++s) {
+#pragma unroll
+        for (int c16 = 0; c16 < 8; ++c16) {
+          const int c = 16 * s + 2 * c16;  // first of the two 32-bit chunks of these 16 bytes
+          uint32_t wv[4] = {0u, 0u, 0u, 0u};
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            if (c + h < NCH) {
+              const uint32_t x = ch[c + h];
+              wv[2 * h] = bf16x2_bits(signed_byte(x, 0, sg, sgb), signed_byte(x, 1, sg, sgb));
+              wv[2 * h + 1] =
+                  bf16x2_bits(signed_byte(x, 2, sg, sgb), signed_byte(x, 3, sg, sgb));
+            }
+          }
+          *(uint4 *)(row + (size_t)s * RT_TILE + ((c16 ^ (prow & 7)) << 4)) =
+              make_uint4(wv[0], wv[1], wv[2], wv[3]);
+        }
+      }
+    }
+    fence_async_smem();
+    if (t == 0) tma_store_wait_read();  // the previous tile's staged residues have been read
+    named_bar(1 + g, RT_ROWS);
+    if (t == 0) {
+      tc_fence_after();
+#pragma unroll
+      for (int s = 0; s < KD; ++s) {
+        const uint64_t ad = sw128_desc(smem_u32(myA + (size_t)s * RT_TILE));
+        const uint64_t bd = sw128_desc(smem_u32(sW + (size_t)s * a.NPAD * 128));
+#pragma unroll
+        for (int kk = 0; kk < 4; ++kk)
+          umma_bf16(tm_mma, ad + 2 * kk, bd + 2 * kk, idesc, (s > 0 || kk > 0) ? 1u : 0u);
+      }
+      umma_commit(&sh->bar[g]);
+    }
+    // ---- drain: x = S_l + 256 S_h of each modulus, reduced and balanced, split into two bytes
+    const bool got = __all_sync(0xffffffffu, mbar_wait(&sh->bar[g], phase, &sh->never));
+    phase ^= 1;
+    if (!got) {
+      if (lane == 0) {
+        sh->fail[g] = 1;
+        set_status(a.status, ARBGPU_ERR_TIMEOUT);
+      }
+    } else {
+      tc_fence_after();
+      uint16_t *so = myO + t;
+      for (int c0 = 0; c0 < 2 * a.NM; c0 += 16) {
+        uint32_t v[16];
+        tmem_ld16(tm_lane + (uint32_t)c0, v);
+        tmem_wait_ld();
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const int tt = (c0 >> 1) + u;
+          if (tt < a.NM) {
+            const float2 mi = sMod[tt];  // m_t, 1 / m_t
+            const float sl = __uint_as_float(v[2 * u]), sh_ = __uint_as_float(v[2 * u + 1]);
+            const float xf = __fmaf_rn(sh_, 256.0f, sl);
+            const float q = __fadd_rn(__fmaf_rn(xf, mi.y, RT_MAGIC), -RT_MAGIC);
+            float rr = __fadd_rn(__fmaf_rn(-q, mi.x, sh_ * 256.0f), sl);
+            const float q2 = __fadd_rn(__fmaf_rn(rr, mi.y, RT_MAGIC), -RT_MAGIC);
+            rr = __fmaf_rn(-q2, mi.x, rr);  // balanced: |rr| <= (m - 1) / 2
+            // rr = 256 h + l with l in [-128, 127]: h = rint(rr / 256 + 1 / 512)
+            const float hi =
+                __fadd_rn(__fadd_rn(__fmaf_rn(rr, 0.00390625f, 0.001953125f), RT_MAGIC),
+                          -RT_MAGIC);
+            const float lo = __fmaf_rn(hi, -256.0f, rr);
+            const uint32_t bits = bf16x2_bits(lo, hi);
+            so[(2 * tt) * RT_ROWS] = (uint16_t)bits;
+            so[(2 * tt + 1) * RT_ROWS] = (uint16_t)(bits >> 16);
+          }
+        }
+      }
+      tc_fence_before();
+      if (rad_box) {
+        const uint32_t info = sh->info[g][t];
+#pragma unroll
+        for (int w = 0; w < 2; ++w) {
+          const uint32_t u = (info >> (14 * w)) & 0x3FFFu;  // u <= 2^13: two balanced digits
+          const float d0 = (float)(((int)(u & 255u) ^ 128) - 128);
+          const float d1 = (float)(((int)u - (int)d0) >> 8);
+          const uint32_t bits = bf16x2_bits(d0, d1);
+          so[(2 * a.NM + 2 * w) * RT_ROWS] = (uint16_t)bits;
+          so[(2 * a.NM + 2 * w + 1) * RT_ROWS] = (uint16_t)(bits >> 16);
+        }
+      } else {
+        const int64_t r = (int64_t)tr * JT + dj, k = (int64_t)tk * KT + dk;
+        if (r < a.rows && (a.ro.r1 || a.ro.r2)) {
+          const uint32_t info = sh->info[g][t];
+          const int64_t off = r * a.Kp + k;
+          if (a.ro.r1) put_small_digits(info & 0x3FFFu, a.ro.r1 + off, plane);
+          if (a.ro.r2) put_small_digits((info >> 14) & 0x3FFFu, a.ro.r2 + off, plane);
+        }
+      }
+    }
+    fence_async_smem();
+    named_bar(1 + g, RT_ROWS);
+    if (t == 0 && !sh->fail[g]) tma_store_3d(&tmo, myO, tk * KT, tr * JT, 0);
+    tr = ntr;
+    tk = ntk2;
+  }
+  if (t == 0) tma_store_wait_all();
+  cp_async_wait_all();
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (threadIdx.x < 32) tmem_dealloc(sh->tmem_base, a.tcols);
+}
+
+struct RtLayout {
+  int KD, NPAD, WG, wg_cols, NPL, SW;
+  size_t smem;
+};
+
+static size_t residue_tc_smem_for(int KD, int NPAD, int WG, int NPL, int NM, int SW) {
+  return 1024 + (size_t)KD * NPAD * 128 + (size_t)WG * KD * RT_TILE + (size_t)WG * NPL * RT_ROWS * 2 +
+         (size_t)WG * SW * RT_ROWS * 8 + (size_t)((NM + 1) & ~1) * 8 + sizeof(RtShared);
+}
+
+// The kernel's shape for an operand of `nch` 32-bit chunks and NM moduli; false when it does not
+// fit (the CUDA-core residue kernel then runs).
+static bool residue_tc_layout(int nch, int NM, bool rad_box, int64_t entries, RtLayout *L) {
+  if (nch > 32 || NM > 128 || entries > ((int64_t)1 << 36)) return false;
+  L->KD = (4 * nch + 63) / 64;
+  L->NPAD = (2 * NM + 15) / 16 * 16;
+  L->wg_cols = L->NPAD <= 128 ? 128 : 256;
+  L->NPL = 2 * NM + (rad_box ? 4 : 0);
+  const int ncls = nch <= 4 ? 4 : nch <= 8 ? 8 : nch <= 11 ? 11 : nch <= 16 ? 16 : nch <= 24 ? 24 : 32;
+  L->SW = RT_SLOT_FIXED + (ncls + 1) / 2 + 1;
+  if (L->NPL > 256) return false;
+  for (int wg = 512 / L->wg_cols < RT_MAX_WG ? 512 / L->wg_cols : RT_MAX_WG; wg >= 1; --wg) {
+    const size_t s = residue_tc_smem_for(L->KD, L->NPAD, wg, L->NPL, NM, L->SW);
+    if (s <= RT_SMEM_MAX) {
+      L->WG = wg;
+      L->smem = s < RT_SMEM_MIN ? RT_SMEM_MIN : s;
+      return true;
+    }
+  }
+  return false;
+}
+
+static arbgpu_status launch_residues_tc(arbgpu_ctx *ctx, const RtLayout &L, int nch,
+                                        cudaStream_t s, RtArgs a, __nv_bfloat16 *out) {
+  const int JT = a.is_b ? 4 : 2;  // Kp is a multiple of 64, so KT = 32 or 64 divides it
+  a.NPAD = L.NPAD;
+  a.WG = L.WG;
+  a.wg_cols = L.wg_cols;
+  a.NPL = L.NPL;
+  a.tcols = (uint32_t)(L.WG * L.wg_cols);
+  a.status = ctx->status;
+  const int KT = RT_ROWS / JT;
+  const int64_t nT = ((a.rows + JT - 1) / JT) * (a.Kp / KT);
+  int64_t grid = (nT + L.WG - 1) / L.WG;
+  if (grid > ctx->sm_count) grid = ctx->sm_count;
+  if (grid < 1) return ARBGPU_OK;
+  CUtensorMap tm;
+  if (!make_residue_store_map(&tm, out, a.Kp, a.rows, L.NPL, KT, JT, L.NPL))
+    return ARBGPU_ERR_CUDA;
+  const int dev = ctx->device & 255;
+#define ARB_RTC(NCH_)                                                                      \
+  do {                                                                                     \
+    if (a.is_b) {                                                                          \
+      static bool attr_done[256] = {};                                                     \
+      if (!attr_done[dev]) {                                                               \
+        if (cudaFuncSetAttribute(residue_tc_kernel<NCH_, true>,                            \
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize,              \
+                                 (int)RT_SMEM_MAX) != cudaSuccess)                         \
+          return ARBGPU_ERR_CUDA;                                                          \
+        attr_done[dev] = true;                                                             \
+      }                                                                                    \
+      residue_tc_kernel<NCH_, true><<<(unsigned)grid, RT_ROWS * L.WG, L.smem, s>>>(tm, a); \
+    } else {                                                                               \
+      static bool attr_done[256] = {};                                                     \
+      if (!attr_done[dev]) {                                                               \
+        if (cudaFuncSetAttribute(residue_tc_kernel<NCH_, false>,                           \
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize,              \
+                                 (int)RT_SMEM_MAX) != cudaSuccess)                         \
+          return ARBGPU_ERR_CUDA;                                                          \
+        attr_done[dev] = true;                                                             \
+      }                                                                                    \
+      residue_tc_kernel<NCH_, false><<<(unsigned)grid, RT_ROWS * L.WG, L.smem, s>>>(tm, a); \
+    }                                                                                      \
+  } while (0)
+  if (nch <= 4) ARB_RTC(4);
+  else if (nch <= 8) ARB_RTC(8);
+  else if (nch <= 11) ARB_RTC(11);
+  else if (nch <= 16) ARB_RTC(16);
+  else if (nch <= 24) ARB_RTC(24);
+  else ARB_RTC(32);
+#undef ARB_RTC
+  return cudaGetLastError() == cudaSuccess ? ARBGPU_OK : ARBGPU_ERR_CUDA;
 }
 
 // Load the per-modulus constants into this device's constant memory (once per device).
@@ -1614,9 +2077,20 @@ static arbgpu_status run_block(arbgpu_ctx *ctx, const BlockWs &w, uint8_t *ws, c
       LaunchScope sc(ctx, s, "residues_a", n * NM * ((hA + 2 + 31) / 32 + 1));
       const SplitOut ro = fold ? SplitOut{nullptr, fA1, fA2}
                                : SplitOut{nullptr, radB ? rA1 : nullptr, radA ? rA2 : nullptr};
-      launch_residues((int)((hA + 2 + 31) / 32) + 1, n, s, Av, false, M, k0, Kb, Kp, lda,
-                      ln.rbot, NM, dt.pow32, plan->NCHP, nullptr, resA, ro, ln.rtop, ln.rrad,
-                      nullptr);
+      const int nch = (int)((hA + 2 + 31) / 32) + 1;
+      RtLayout L;
+      if (residue_tc_layout(nch, NM, fold, n, &L)) {
+        RtArgs ra{};
+        ra.X = Av, ra.is_b = false, ra.rows = M, ra.k0 = k0, ra.K = Kb, ra.Kp = Kp, ra.ld = lda;
+        ra.bot = ln.rbot, ra.NM = NM, ra.wtab = dt.wtab, ra.rinv = dt.rinv;
+        ra.ro = fold ? SplitOut{} : ro;
+        ra.top = ln.rtop, ra.radtop = ln.rrad, ra.plustop = nullptr;
+        const arbgpu_status st = launch_residues_tc(ctx, L, nch, s, ra, resA);
+        if (st != ARBGPU_OK) return st;
+      } else {
+        launch_residues(nch, n, s, Av, false, M, k0, Kb, Kp, lda, ln.rbot, NM, dt.pow32,
+                        plan->NCHP, nullptr, resA, ro, ln.rtop, ln.rrad, nullptr);
+      }
     }
     {
       const int64_t n = N * Kp;
@@ -1625,9 +2099,21 @@ static arbgpu_status run_block(arbgpu_ctx *ctx, const BlockWs &w, uint8_t *ws, c
       // reconstruction, so the residue products are already z_t = P_t y_t mod m_t
       const SplitOut ro = fold ? SplitOut{nullptr, fB1, fB2}
                                : SplitOut{nullptr, radB ? rB1 : nullptr, radA ? rB2 : nullptr};
-      launch_residues((int)((hB + 2 + 31) / 32) + 1, n, s, Bv, true, N, k0, Kb, Kp, ldb,
-                      ln.cbot, NM, dt.pow32, plan->NCHP, dt.y, resB, ro, ln.ctop, ln.crad,
-                      ln.cplus);
+      const int nch = (int)((hB + 2 + 31) / 32) + 1;
+      RtLayout L;
+      if (residue_tc_layout(nch, NM, fold, n, &L)) {
+        RtArgs ra{};
+        ra.X = Bv, ra.is_b = true, ra.rows = N, ra.k0 = k0, ra.K = Kb, ra.Kp = Kp, ra.ld = ldb;
+        ra.bot = ln.cbot, ra.NM = NM, ra.wtab = dt.wtab + (size_t)plan->NPAD * 128,
+        ra.rinv = dt.rinv;
+        ra.ro = fold ? SplitOut{} : ro;
+        ra.top = ln.ctop, ra.radtop = ln.crad, ra.plustop = ln.cplus;
+        const arbgpu_status st = launch_residues_tc(ctx, L, nch, s, ra, resB);
+        if (st != ARBGPU_OK) return st;
+      } else {
+        launch_residues(nch, n, s, Bv, true, N, k0, Kb, Kp, ldb, ln.cbot, NM, dt.pow32,
+                        plan->NCHP, dt.y, resB, ro, ln.ctop, ln.crad, ln.cplus);
+      }
     }
     if (cudaGetLastError() != cudaSuccess) return ARBGPU_ERR_CUDA;
     DigitGemmArgs g{resA, resB, (int)M, (int)N, Kp, 2, 2, 1, ws + w.cdig,

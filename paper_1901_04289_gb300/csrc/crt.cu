@@ -119,6 +119,29 @@ std::unique_ptr<CrtPlan> build_plan(int NM) {
       v = (v << 32) % P->mods[t];
     }
   }
+  // digit weights of the tensor-core residue step (one table per operand side)
+  P->NPAD = (2 * NM + 15) / 16 * 16;
+  P->wtab.assign((size_t)2 * P->NPAD * 128, 0);
+  auto bf16_bits = [](int v) {  // |v| <= 256: exact in BF16, the top half of the float
+    const float f = (float)v;
+    uint32_t u;
+    memcpy(&u, &f, 4);
+    return (uint16_t)(u >> 16);
+  };
+  for (int side = 0; side < 2; ++side)
+    for (int t = 0; t < NM; ++t) {
+      const uint64_t m = P->mods[t];
+      uint64_t v = 1;  // 2^(8d) mod m
+      for (int d = 0; d < 128; ++d) {
+        int64_t w = (int64_t)(side ? v * P->y[t] % m : v);
+        if (w > (int64_t)(m >> 1)) w -= (int64_t)m;
+        const int64_t l = ((w + 128) & 255) - 128, hb = (w - l) >> 8;
+        uint16_t *row = P->wtab.data() + ((size_t)side * P->NPAD + 2 * t) * 128;
+        row[d] = bf16_bits((int)l);
+        row[128 + d] = bf16_bits((int)hb);
+        v = (v << 8) % m;
+      }
+    }
   return P;
 }
 
@@ -139,7 +162,8 @@ arbgpu_status crt_device_tables(arbgpu_ctx *ctx, const CrtPlan *P, CrtDevTables 
   const size_t oQ = 0, oM = oQ + al(4 * P->Q32.size()), oy = oM + al(4 * P->M32.size());
   const size_t oz = oy + al(4 * P->y.size()), op = oz + al(4 * P->ztab.size());
   const size_t orv = op + al(4 * P->pow32.size()), oi = orv + al(4 * P->rinv.size());
-  const size_t total = oi + al(8 * P->inv.size());
+  const size_t ow = oi + al(8 * P->inv.size());
+  const size_t total = ow + al(2 * P->wtab.size());
   auto it = ctx->crt_tables.find(P->NM);
   uint8_t *base = nullptr;
   if (it != ctx->crt_tables.end()) {
@@ -154,6 +178,7 @@ arbgpu_status crt_device_tables(arbgpu_ctx *ctx, const CrtPlan *P, CrtDevTables 
     memcpy(h.data() + op, P->pow32.data(), 4 * P->pow32.size());
     memcpy(h.data() + orv, P->rinv.data(), 4 * P->rinv.size());
     memcpy(h.data() + oi, P->inv.data(), 8 * P->inv.size());
+    memcpy(h.data() + ow, P->wtab.data(), 2 * P->wtab.size());
     if (cudaMemcpy(base, h.data(), total, cudaMemcpyHostToDevice) != cudaSuccess) {
       cudaFree(base);
       return ARBGPU_ERR_CUDA;
@@ -167,6 +192,7 @@ arbgpu_status crt_device_tables(arbgpu_ctx *ctx, const CrtPlan *P, CrtDevTables 
   out->pow32 = (const uint32_t *)(base + op);
   out->rinv = (const float *)(base + orv);
   out->inv = (const uint64_t *)(base + oi);
+  out->wtab = (const uint16_t *)(base + ow);
   return ARBGPU_OK;
 }
 

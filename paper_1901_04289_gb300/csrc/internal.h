@@ -171,6 +171,10 @@ struct CrtPlan {
   std::vector<float> rinv;        // [NM]: 1 / m_t rounded to float
   std::vector<uint32_t> ztab;     // [NM][4]: m_t, 0, 0, 0
   std::vector<uint64_t> M;        // M
+  int NPAD;                       // 2 NM rounded up to a multiple of 16
+  // [2][NPAD][128] BF16 bits: row 2t + b of operand side o holds byte b (balanced, 256 h + l) of
+  // the balanced w = 2^(8d) mod m_t (side 0) or 2^(8d) y_t mod m_t (side 1) in column d
+  std::vector<uint16_t> wtab;
 };
 int crt_moduli_for_bits(int bits);
 const CrtPlan *crt_plan(int NM);
@@ -178,6 +182,7 @@ const CrtPlan *crt_plan(int NM);
 struct CrtDevTables {
   const uint32_t *Q32, *M32, *y, *ztab, *pow32;
   const float *rinv;
+  const uint16_t *wtab;
   const uint64_t *inv;
 };
 arbgpu_status crt_device_tables(arbgpu_ctx *ctx, const CrtPlan *plan, CrtDevTables *out);

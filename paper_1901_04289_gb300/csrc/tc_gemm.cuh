@@ -65,6 +65,11 @@ struct DigitGemmParams {
   const uint64_t *zinv;     // [batch]: floor((2^64 - 1) / m_b)
 };
 
+// Tensor map for TMA stores into BF16 planes [planes][rows][Kp] (no swizzle), box
+// box_k x box_rows x box_planes (box_k * 2 bytes a multiple of 16, every box side <= 256).
+bool make_residue_store_map(CUtensorMap *tm, void *base, int64_t Kp, int64_t rows, int64_t planes,
+                            int box_k, int box_rows, int box_planes);
+
 // ------------------------------------------------------------------------------ PTX wrappers
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {

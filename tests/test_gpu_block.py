@@ -291,7 +291,7 @@ def _run_engine(arb, engine, A, B, M, K, N, prec, cplx=False):
     return outs, names
 
 
-@pytest.mark.parametrize("kind", ["single", "several", "complex"])
+@pytest.mark.parametrize("kind", ["single", "several", "complex", "p512"])
 def test_digit_and_multimodular_engines_agree_bit_for_bit(arb, kind):
     """The exact block integers T are the same whichever engine forms them (digit products or
     residues + Chinese remainder theorem), so every output field must agree."""
@@ -300,6 +300,10 @@ def test_digit_and_multimodular_engines_agree_bit_for_bit(arb, kind):
         M, K, N, p = 130, 192, 120, 256
         A = random_balls(rng, M * K, 4, 256, -20, 20, rad_bits=250, rad_zero_frac=0.3)
         B = random_balls(rng, K * N, 4, 256, -20, 20, rad_bits=250, rad_zero_frac=0.3)
+    elif kind == "p512":  # about 100 moduli, 28 32-bit chunks per scaled integer
+        M, K, N, p = 67, 100, 45, 512
+        A = random_balls(rng, M * K, 8, 512, -20, 20, rad_bits=500, rad_zero_frac=0.3)
+        B = random_balls(rng, K * N, 8, 512, -20, 20, rad_bits=500, rad_zero_frac=0.3)
     elif kind == "several":
         M, K, N, p = 40, 180, 36, 128
         A, B = band_case(5, M, K, N, 60, 120, nl=2, rad=120)
