@@ -811,9 +811,18 @@ static void launch_residues(int nch, int64_t n, cudaStream_t s, const BallsView 
 // x = S_l + 256 S_h (|x| < 2^31) in FP32 without rounding error: q = rint(x / m) from a rounded x
 // is off by at most one for |x / m| < 2^16, r = (256 S_h - q m) + S_l is exact (every partial
 // result is an integer below 2^24), and one more rint(r / m) step balances r.
+//
+// Roles of a CTA (one per SM, persistent over tiles of 128 entries): two producer warpgroups
+// (alternate tiles) write each entry's digits into a ring of shared-memory tiles, one warp issues the MMAs into a ring of
+// TMEM accumulators, and ND drain warpgroups take the tiles in turn, reduce them, stage the
+// residue planes in shared memory and write them with a TMA store.  Every wait on an mbarrier
+// gives up after ~2 s, sets ARBGPU_ERR_TIMEOUT and leaves the loop.
 constexpr int RT_ROWS = 128;            // entries per tile: the MMA's M
 constexpr int RT_TILE = RT_ROWS * 128;  // bytes of one 64-digit slab of a tile (SW128, K-major)
-constexpr int RT_MAX_WG = 4;            // warpgroups per CTA, each with its own tile in flight
+constexpr int RT_MAX_ND = 3;            // drain warpgroups
+constexpr int RT_MAX_NS = 4;            // digit tiles in flight
+constexpr int RT_NP = 2;      // producer warpgroups (tiles i = p mod RT_NP go to producer p)
+constexpr int RT_MAX_THREADS = 32 * (4 * RT_MAX_ND + 4 * RT_NP + 1);
 constexpr float RT_MAGIC = 12582912.0f; // 1.5 * 2^23: adding it rounds |v| < 2^22 to an integer
 // Dynamic shared memory of at least this much keeps one CTA per SM, so the CTA's 512 TMEM columns
 // are always free when it starts.
@@ -821,15 +830,26 @@ constexpr size_t RT_SMEM_MIN = 120 * 1024;
 constexpr size_t RT_SMEM_MAX = 227 * 1024;
 
 struct RtShared {
-  uint64_t bar[RT_MAX_WG];
+  uint64_t a_full[RT_MAX_NS], a_empty[RT_MAX_NS];        // digit tiles
+  uint64_t t_full[RT_MAX_ND + 1], t_empty[RT_MAX_ND + 1];  // TMEM accumulators
   uint32_t tmem_base;
-  int never;                          // an abort flag nothing sets
-  int fail[RT_MAX_WG];
-  uint32_t info[RT_MAX_WG][RT_ROWS];  // radius operands u1 | u2 << 14 of each tile row
+  int never;  // an abort flag nothing sets
+  uint32_t info[RT_MAX_NS][RT_ROWS];  // radius operands u1 | u2 << 14 of each tile row
 };
 
 __device__ __forceinline__ void named_bar(int id, int n) {
   asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory");
+}
+// A barrier of n threads that also returns whether any of them passed `p` true.
+__device__ __forceinline__ bool named_bar_or(int id, int n, bool p) {
+  uint32_t r;
+  asm volatile(
+      "{\n .reg .pred q, o;\n setp.ne.u32 q, %1, 0;\n bar.red.or.pred o, %2, %3, q;\n"
+      " selp.u32 %0, 1, 0, o;\n}\n"
+      : "=r"(r)
+      : "r"((uint32_t)p), "r"(id), "r"(n)
+      : "memory");
+  return r != 0;
 }
 __device__ __forceinline__ void fence_async_smem() {
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -864,6 +884,10 @@ __device__ __forceinline__ void cp_async_commit() {
 __device__ __forceinline__ void cp_async_wait_all() {
   asm volatile("cp.async.wait_group 0;" ::: "memory");
 }
+template <int N>
+__device__ __forceinline__ void cp_async_wait_pending() {  // at most N groups still in flight
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
 
 // Top limbs of an entry the residue step can need: |X| = L 2^sh < 2^(32 NCH) and L's top bit is
 // bit 64 nl - 1, so the nonzero bits of L that reach X lie in its top ceil(NCH / 2) + 1 limbs.
@@ -871,10 +895,11 @@ template <int NCH>
 constexpr int rt_top_limbs() {
   return (NCH + 1) / 2 + 1;
 }
-// Per producer thread, the raw fields of its next entry, staged by cp.async one tile ahead:
-// words [0] exp, [1] bot, [2] flags | rad_man << 32, [3] rad_exp, [4] and [5] the two radius
-// windows, [6 ...] the top limbs (word 6 + i = limb nl - NLW + i).  Word-major: [word][128].
+// Per producer thread, the raw fields of its entries of its next RT_PD tiles, staged by cp.async: words [0] exp, [1] bot, [2] flags | rad_man << 32, [3] rad_exp, [4] and [5]
+// the two radius windows, [6 ...] the top limbs (word 6 + i = limb nl - NLW + i).  Layout
+// [RT_NP][RT_PD][128][SW].
 constexpr int RT_SLOT_FIXED = 6;
+constexpr int RT_PD = 2;  // tiles staged ahead by each producer thread
 
 // The float sg * b for byte b of `w` (exact): sg (2^23 + b) + sgb with sgb = -sg 2^23.
 __device__ __forceinline__ float signed_byte(uint32_t w, int b, float sg, float sgb) {
@@ -890,7 +915,7 @@ struct RtArgs {
   bool is_b;
   int64_t rows, k0, K, Kp, ld;
   const int64_t *bot;  // scan: per-row lowest exponent
-  int NM, NPAD, WG, wg_cols, NPL;  // NPL: staged planes per tile (2 NM, plus 4 radius planes)
+  int NM, NPAD, NS, ND, wg_cols, NPL;  // NPL: staged planes per tile (2 NM, plus 4 radius planes)
   uint32_t tcols;
   const uint16_t *wtab;  // [NPAD][128] BF16 weight table of this operand
   const float *rinv;     // [NM] 1 / m_t
@@ -899,12 +924,12 @@ struct RtArgs {
   int *status;
 };
 
-// Tile = JT operand rows x KT inner positions.  The producer thread reads the entry (pj, pk)
-// (consecutive threads take consecutive elements of X in memory) and fills tile row pj * KT + pk;
-// the drain thread t reads TMEM lane t, i.e. the entry (t / KT, t % KT), and stages its residues
-// at [plane][t], which is the layout of the TMA store's box {KT, JT, planes}.
+// Tile = JT operand rows x KT inner positions.  The producer thread pt reads the entry (pj, pk)
+// and fills tile row pj * KT + pk; the drain thread t reads TMEM lane t, i.e. the entry
+// (t / KT, t % KT), and stages its residues at [plane][t], which is the layout of the TMA
+// store's box {KT, JT, planes}.
 template <int NCH, bool IS_B>
-__global__ void __launch_bounds__(RT_ROWS *RT_MAX_WG, 1)
+__global__ void __launch_bounds__(RT_MAX_THREADS, 1)
     residue_tc_kernel(const __grid_constant__ CUtensorMap tmo, const __grid_constant__ RtArgs a) {
   constexpr int KD = (4 * NCH + 63) / 64;  // 64-digit slabs
   constexpr int NLW = rt_top_limbs<NCH>();
@@ -912,24 +937,29 @@ __global__ void __launch_bounds__(RT_ROWS *RT_MAX_WG, 1)
   constexpr int JT = IS_B ? 4 : 2;  // operand rows per tile
   constexpr int KT = RT_ROWS / JT;  // inner positions per tile (a divisor of Kp)
   extern __shared__ __align__(1024) uint8_t smem_raw[];
+  const int NS = a.NS, ND = a.ND, NB = a.ND + 1;
   uint8_t *sW = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   uint8_t *sA = sW + (size_t)KD * a.NPAD * 128;
-  uint16_t *sO = (uint16_t *)(sA + (size_t)a.WG * KD * RT_TILE);
-  uint64_t *sSlot = (uint64_t *)(sO + (size_t)a.WG * a.NPL * RT_ROWS);
-  float2 *sMod = (float2 *)(sSlot + (size_t)a.WG * SW * RT_ROWS);
-  RtShared *sh = (RtShared *)(sMod + ((a.NM + 1) & ~1));
-  const int g = threadIdx.x >> 7, t = threadIdx.x & 127;
-  const int lane = t & 31, wq = t >> 5;
+  uint16_t *sO = (uint16_t *)(sA + (size_t)NS * KD * RT_TILE);
+  uint64_t *sSlot = (uint64_t *)(sO + (size_t)ND * a.NPL * RT_ROWS);
+  float2 *sMod = (float2 *)(sSlot + (size_t)RT_NP * RT_PD * SW * RT_ROWS);
+  RtShared *sh = (RtShared *)(sMod + a.NPAD / 2);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int mma_warp = 4 * ND + 4 * RT_NP;
 
   if (threadIdx.x == 0) {
-    for (int q = 0; q < a.WG; ++q) {
-      mbar_init(&sh->bar[q], 1);
-      sh->fail[q] = 0;
+    for (int q = 0; q < NS; ++q) {
+      mbar_init(&sh->a_full[q], RT_ROWS);
+      mbar_init(&sh->a_empty[q], RT_ROWS);
+    }
+    for (int q = 0; q < NB; ++q) {
+      mbar_init(&sh->t_full[q], 1);
+      mbar_init(&sh->t_empty[q], RT_ROWS);
     }
     sh->never = 0;
     fence_mbar_init();
   }
-  if (threadIdx.x < 32) {
+  if (warp == mma_warp) {
     tmem_alloc(&sh->tmem_base, a.tcols);
     tmem_relinquish();
   }
@@ -941,8 +971,8 @@ __global__ void __launch_bounds__(RT_ROWS *RT_MAX_WG, 1)
     *(uint4 *)(sW + (size_t)(c >> 3) * a.NPAD * 128 + (size_t)n * 128 +
                (((c & 7) ^ (n & 7)) << 4)) = v;
   }
-  for (int q = threadIdx.x; q < a.NM; q += blockDim.x)
-    sMod[q] = make_float2((float)c_mods[q], __ldg(a.rinv + q));
+  for (int q = threadIdx.x; q < a.NPAD / 2; q += blockDim.x)
+    sMod[q] = q < a.NM ? make_float2((float)c_mods[q], __ldg(a.rinv + q)) : make_float2(1.0f, 1.0f);
   fence_async_smem();
   tc_fence_before();
   __syncthreads();
@@ -950,71 +980,66 @@ __global__ void __launch_bounds__(RT_ROWS *RT_MAX_WG, 1)
 
   const int ntk = (int)(a.Kp / KT);
   const int nT = (int)((a.rows + JT - 1) / JT) * ntk;  // the host keeps this below 2^30
-  const int tstride = (int)gridDim.x * a.WG;
-  const int dtr = tstride / ntk, dtk = tstride - dtr * ntk;
-  uint8_t *myA = sA + (size_t)g * KD * RT_TILE;
-  uint16_t *myO = sO + (size_t)g * a.NPL * RT_ROWS;
-  const uint32_t tm_mma = sh->tmem_base + (uint32_t)(g * a.wg_cols);
-  const uint32_t tm_lane = tm_mma + ((uint32_t)(32 * wq) << 16);
-  const uint32_t idesc = idesc_bf16_f32(RT_ROWS, a.NPAD);
-  // producer's entry (pj, pk): for B, the four threads of a 32-byte sector of a row of B take
-  // consecutive columns j, and the eight threads of a quarter warp fill tile rows with distinct
-  // (row mod 8), so their swizzled 16-byte stores hit distinct banks
-  const int pj = IS_B ? ((t >> 3) & 3) : (t >> 6);
-  const int pk = IS_B ? ((t & 7) + 8 * (t >> 5)) : (t & 63);
-  const int prow = pj * KT + pk;
-  const int dj = t / KT, dk = t % KT;  // drain entry; dj is the same across a warp
+  // this CTA's tiles: blockIdx.x + i gridDim.x, i = 0, 1, ...
+  const int ntiles = nT > (int)blockIdx.x ? (nT - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
   const bool rad_box = a.NPL > 2 * a.NM;
-  const int64_t plane = a.rows * a.Kp;
-  const bool want_rad = a.ro.r1 || a.ro.r2 || rad_box;
-  const bool w1 = rad_box || a.ro.r1, w2 = rad_box || a.ro.r2;
-  const int nl = a.X.nlimbs;
-  const int lbase = nl - NLW;  // limb index of the slot's first limb (lower limbs are not read)
-  uint64_t *slot = sSlot + ((size_t)g * RT_ROWS + t) * SW;
-  // issue the copies of the producer's entry of tile (tr, tk) (nothing when outside X)
-  auto prefetch = [&](int tr, int tk) {
-    const int64_t r = (int64_t)tr * JT + pj, k = (int64_t)tk * KT + pk;
-    if (r < a.rows && k < a.K) {
-      const BallsView &X = a.X;
-      const int64_t e = IS_B ? ((a.k0 + k) * a.ld + r) : (r * a.ld + a.k0 + k);
-      cp_async(slot, X.exp + e, 8);
-      cp_async(slot + 1, a.bot + r, 8);
-      cp_async(slot + 2, X.flags + e, 4);
-      if (want_rad) {
-        cp_async((uint32_t *)(slot + 2) + 1, X.rad_man + e, 4);
-        cp_async(slot + 3, X.rad_exp + e, 8);
-        if (w1) cp_async(slot + 4, (IS_B ? a.radtop : a.top) + r, 8);
-        if (w2) cp_async(slot + 5, (IS_B ? a.plustop : a.radtop) + r, 8);
-      }
+
+  if (warp >= 4 * ND && warp < mma_warp) {
+    // ------------------------------------------------ producer: digits of 128 entries per tile
+    const int p = (warp - 4 * ND) >> 2, pt = threadIdx.x - 128 * (ND + p);
+    uint64_t *pslots = sSlot + (size_t)p * RT_PD * RT_ROWS * SW;
+    // entry (pj, pk): for B, the four threads of a 32-byte sector of a row of B take consecutive
+    // columns j, and the eight threads of a quarter warp fill tile rows with distinct (row mod 8),
+    // so their swizzled 16-byte stores hit distinct banks
+    const int pj = IS_B ? ((pt >> 3) & 3) : (pt >> 6);
+    const int pk = IS_B ? ((pt & 7) + 8 * (pt >> 5)) : (pt & 63);
+    const int prow = pj * KT + pk;
+    const bool want_rad = a.ro.r1 || a.ro.r2 || rad_box;
+    const bool w1 = rad_box || a.ro.r1, w2 = rad_box || a.ro.r2;
+    const int nl = a.X.nlimbs;
+    const int lbase = nl - NLW;  // limb index of the slot's first limb (lower ones are not read)
+    // copies of the entry of this producer's j-th tile (the CTA's tile i = p + j RT_NP) into
+    // slot j mod RT_PD (none outside X); one commit group per call, empty past the last tile
+    auto prefetch = [&](int j) {
+      uint64_t *slot = pslots + ((size_t)(j % RT_PD) * RT_ROWS + pt) * SW;
+      const int i = p + j * RT_NP;
+      const int tile = (int)blockIdx.x + i * (int)gridDim.x;
+      const int tr = tile / ntk, tk = tile - tr * ntk;
+      const int64_t r = (int64_t)tr * JT + pj, k = (int64_t)tk * KT + pk;
+      if (i < ntiles && r < a.rows && k < a.K) {
+        const BallsView &X = a.X;
+        const int64_t e = IS_B ? ((a.k0 + k) * a.ld + r) : (r * a.ld + a.k0 + k);
+        cp_async(slot, X.exp + e, 8);
+        cp_async(slot + 1, a.bot + r, 8);
+        cp_async(slot + 2, X.flags + e, 4);
+        if (want_rad) {
+          cp_async((uint32_t *)(slot + 2) + 1, X.rad_man + e, 4);
+          cp_async(slot + 3, X.rad_exp + e, 8);
+          if (w1) cp_async(slot + 4, (IS_B ? a.radtop : a.top) + r, 8);
+          if (w2) cp_async(slot + 5, (IS_B ? a.plustop : a.radtop) + r, 8);
+        }
 #pragma unroll
-      for (int i = 0; i < NLW; ++i)
-        if (lbase + i >= 0)
-          cp_async(slot + RT_SLOT_FIXED + i, X.limbs + (int64_t)(lbase + i) * X.stride + e, 8);
-    }
-    cp_async_commit();
-  };
-  const uint32_t *Wd = (const uint32_t *)(slot + RT_SLOT_FIXED);  // 32-bit words of the limbs
-  const int jlo = lbase < 0 ? -2 * lbase : 0;                     // first word that exists
-  int tile = (int)blockIdx.x * a.WG + g;
-  int tr = tile / ntk, tk = tile - tr * ntk;
-  if (tile < nT) prefetch(tr, tk);
-  uint32_t phase = 0;
-  for (; tile < nT; tile += tstride) {
-    if (sh->fail[g]) break;  // set only between this warpgroup's two barriers of a tile
-    int ntr = tr + dtr, ntk2 = tk + dtk;  // the next tile of this warpgroup
-    if (ntk2 >= ntk) {
-      ntk2 -= ntk;
-      ++ntr;
-    }
-    {
-      // ---- produce: signed digits of one entry into tile row prow, radius operands into info
+        for (int i = 0; i < NLW; ++i)
+          if (lbase + i >= 0)
+            cp_async(slot + RT_SLOT_FIXED + i, X.limbs + (int64_t)(lbase + i) * X.stride + e, 8);
+      }
+      cp_async_commit();
+    };
+    const int jlo = lbase < 0 ? -2 * lbase : 0;  // first 32-bit limb word that exists
+    for (int j = 0; j < RT_PD; ++j) prefetch(j);
+    for (int j = 0, i = p; i < ntiles; ++j, i += RT_NP) {
+      const uint64_t *slot = pslots + ((size_t)(j % RT_PD) * RT_ROWS + pt) * SW;
+      const uint32_t *Wd = (const uint32_t *)(slot + RT_SLOT_FIXED);  // 32-bit words of the limbs
+      const int tile = (int)blockIdx.x + i * (int)gridDim.x;
+      const int tr = tile / ntk, tk = tile - tr * ntk;
+      const int s = i % NS;
       const int64_t r = (int64_t)tr * JT + pj, k = (int64_t)tk * KT + pk;
       uint32_t ch[NCH];
 #pragma unroll
       for (int c = 0; c < NCH; ++c) ch[c] = 0;
       uint32_t info = 0;
       float sg = 1.0f;
-      cp_async_wait_all();
+      cp_async_wait_pending<RT_PD - 1>();  // the groups of the later RT_PD - 1 tiles may fly
       if (r < a.rows && k < a.K) {
         const int64_t ex = (int64_t)slot[0];
         const uint64_t w2f = slot[2];
@@ -1064,16 +1089,21 @@ __global__ void __launch_bounds__(RT_ROWS *RT_MAX_WG, 1)
           info = u1 | (u2 << 14);
         }
       }
-      // every slot value is in registers now: stage the next tile's entry
-      if (tile + tstride < nT) prefetch(ntr, ntk2);
-      sh->info[g][prow] = info;
+      // every slot value is in registers now: stage tile j + RT_PD into the same slot
+      prefetch(j + RT_PD);
+      // the digit tile s is free once the drain of the tile that used it has read its info
+      if (!mbar_wait(&sh->a_empty[s], ((i / NS) & 1) ^ 1, &sh->never)) {
+        set_status(a.status, ARBGPU_ERR_TIMEOUT);
+        break;
+      }
+      sh->info[s][prow] = info;
       const float sgb = -8388608.0f * sg;
-      uint8_t *row = myA + (size_t)prow * 128;
+      uint8_t *row = sA + (size_t)s * KD * RT_TILE + (size_t)prow * 128;
 #pragma unroll
-      for (int s = 0; s < KD; ++s) {
+      for (int sl = 0; sl < KD; ++sl) {
 #pragma unroll
         for (int c16 = 0; c16 < 8; ++c16) {
-          const int c = 16 * s + 2 * c16;  // first of the two 32-bit chunks of these 16 bytes
+          const int c = 16 * sl + 2 * c16;  // first of the two 32-bit chunks of these 16 bytes
           uint32_t wv[4] = {0u, 0u, 0u, 0u};
 #pragma unroll
           for (int h = 0; h < 2; ++h) {
@@ -1084,66 +1114,96 @@ __global__ void __launch_bounds__(RT_ROWS *RT_MAX_WG, 1)
                   bf16x2_bits(signed_byte(x, 2, sg, sgb), signed_byte(x, 3, sg, sgb));
             }
           }
-          *(uint4 *)(row + (size_t)s * RT_TILE + ((c16 ^ (prow & 7)) << 4)) =
+          *(uint4 *)(row + (size_t)sl * RT_TILE + ((c16 ^ (prow & 7)) << 4)) =
               make_uint4(wv[0], wv[1], wv[2], wv[3]);
         }
       }
+      fence_async_smem();
+      mbar_arrive(&sh->a_full[s]);
     }
-    fence_async_smem();
-    if (t == 0) tma_store_wait_read();  // the previous tile's staged residues have been read
-    named_bar(1 + g, RT_ROWS);
-    if (t == 0) {
-      tc_fence_after();
+    cp_async_wait_all();
+  } else if (warp == mma_warp) {
+    // ------------------------------------------------ MMA issuer
+    if (lane == 0) {
+      const uint32_t idesc = idesc_bf16_f32(RT_ROWS, a.NPAD);
+      for (int i = 0; i < ntiles; ++i) {
+        const int s = i % NS, b = i % NB;
+        if (!mbar_wait(&sh->a_full[s], (i / NS) & 1, &sh->never) ||
+            !mbar_wait(&sh->t_empty[b], ((i / NB) & 1) ^ 1, &sh->never)) {
+          set_status(a.status, ARBGPU_ERR_TIMEOUT);
+          break;
+        }
+        tc_fence_after();
+        const uint32_t tm = sh->tmem_base + (uint32_t)(b * a.wg_cols);
 #pragma unroll
-      for (int s = 0; s < KD; ++s) {
-        const uint64_t ad = sw128_desc(smem_u32(myA + (size_t)s * RT_TILE));
-        const uint64_t bd = sw128_desc(smem_u32(sW + (size_t)s * a.NPAD * 128));
+        for (int sl = 0; sl < KD; ++sl) {
+          const uint64_t ad = sw128_desc(smem_u32(sA + ((size_t)s * KD + sl) * RT_TILE));
+          const uint64_t bd = sw128_desc(smem_u32(sW + (size_t)sl * a.NPAD * 128));
 #pragma unroll
-        for (int kk = 0; kk < 4; ++kk)
-          umma_bf16(tm_mma, ad + 2 * kk, bd + 2 * kk, idesc, (s > 0 || kk > 0) ? 1u : 0u);
+          for (int kk = 0; kk < 4; ++kk)
+            umma_bf16(tm, ad + 2 * kk, bd + 2 * kk, idesc, (sl > 0 || kk > 0) ? 1u : 0u);
+        }
+        umma_commit(&sh->t_full[b]);
       }
-      umma_commit(&sh->bar[g]);
     }
-    // ---- drain: x = S_l + 256 S_h of each modulus, reduced and balanced, split into two bytes
-    const bool got = __all_sync(0xffffffffu, mbar_wait(&sh->bar[g], phase, &sh->never));
-    phase ^= 1;
-    if (!got) {
-      if (lane == 0) {
-        sh->fail[g] = 1;
-        set_status(a.status, ARBGPU_ERR_TIMEOUT);
+  } else {
+    // ------------------------------------------------ drain warpgroup d: tiles i = d (mod ND)
+    const int d = warp >> 2, t = threadIdx.x & 127, wq = warp & 3;
+    const int dj = t / KT, dk = t % KT;  // the entry of TMEM lane t; dj is the same across a warp
+    const int64_t plane = a.rows * a.Kp;
+    uint16_t *so = sO + (size_t)d * a.NPL * RT_ROWS + t;  // plane p of this row at so[p * 128]
+    for (int i = d; i < ntiles; i += ND) {
+      const int tile = (int)blockIdx.x + i * (int)gridDim.x;
+      const int tr = tile / ntk, tk = tile - tr * ntk;
+      const int s = i % NS, b = i % NB;
+      // (the wait on a_full, complete by then, orders the producer's info writes before the
+      // reads below)
+      const bool got = mbar_wait(&sh->t_full[b], (i / NB) & 1, &sh->never) &&
+                       mbar_wait(&sh->a_full[s], (i / NS) & 1, &sh->never);
+      if (t == 0) tma_store_wait_read();  // this warpgroup's previous store has read its staging
+      if (named_bar_or(1 + d, RT_ROWS, !got)) {
+        if (t == 0) set_status(a.status, ARBGPU_ERR_TIMEOUT);
+        break;
       }
-    } else {
       tc_fence_after();
-      uint16_t *so = myO + t;
+      const uint32_t info = sh->info[s][t];
+      mbar_arrive(&sh->a_empty[s]);
+      const uint32_t tm_lane =
+          sh->tmem_base + (uint32_t)(b * a.wg_cols) + ((uint32_t)(32 * wq) << 16);
       for (int c0 = 0; c0 < 2 * a.NM; c0 += 16) {
         uint32_t v[16];
         tmem_ld16(tm_lane + (uint32_t)c0, v);
         tmem_wait_ld();
+        // eight moduli at once (sMod is padded to a multiple of eight), then the stores of the
+        // real ones
+        uint32_t bits[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const float2 mi = sMod[(c0 >> 1) + u];  // m_t, 1 / m_t
+          const float sl = __uint_as_float(v[2 * u]), sh_ = __uint_as_float(v[2 * u + 1]);
+          const float xf = __fmaf_rn(sh_, 256.0f, sl);
+          const float q = __fadd_rn(__fmaf_rn(xf, mi.y, RT_MAGIC), -RT_MAGIC);
+          float rr = __fadd_rn(__fmaf_rn(-q, mi.x, sh_ * 256.0f), sl);
+          const float q2 = __fadd_rn(__fmaf_rn(rr, mi.y, RT_MAGIC), -RT_MAGIC);
+          rr = __fmaf_rn(-q2, mi.x, rr);  // balanced: |rr| <= (m - 1) / 2
+          // rr = 256 h + l with l in [-128, 127]: h = rint(rr / 256 + 1 / 512)
+          const float hi = __fadd_rn(
+              __fadd_rn(__fmaf_rn(rr, 0.00390625f, 0.001953125f), RT_MAGIC), -RT_MAGIC);
+          const float lo = __fmaf_rn(hi, -256.0f, rr);
+          bits[u] = bf16x2_bits(lo, hi);
+        }
 #pragma unroll
         for (int u = 0; u < 8; ++u) {
           const int tt = (c0 >> 1) + u;
           if (tt < a.NM) {
-            const float2 mi = sMod[tt];  // m_t, 1 / m_t
-            const float sl = __uint_as_float(v[2 * u]), sh_ = __uint_as_float(v[2 * u + 1]);
-            const float xf = __fmaf_rn(sh_, 256.0f, sl);
-            const float q = __fadd_rn(__fmaf_rn(xf, mi.y, RT_MAGIC), -RT_MAGIC);
-            float rr = __fadd_rn(__fmaf_rn(-q, mi.x, sh_ * 256.0f), sl);
-            const float q2 = __fadd_rn(__fmaf_rn(rr, mi.y, RT_MAGIC), -RT_MAGIC);
-            rr = __fmaf_rn(-q2, mi.x, rr);  // balanced: |rr| <= (m - 1) / 2
-            // rr = 256 h + l with l in [-128, 127]: h = rint(rr / 256 + 1 / 512)
-            const float hi =
-                __fadd_rn(__fadd_rn(__fmaf_rn(rr, 0.00390625f, 0.001953125f), RT_MAGIC),
-                          -RT_MAGIC);
-            const float lo = __fmaf_rn(hi, -256.0f, rr);
-            const uint32_t bits = bf16x2_bits(lo, hi);
-            so[(2 * tt) * RT_ROWS] = (uint16_t)bits;
-            so[(2 * tt + 1) * RT_ROWS] = (uint16_t)(bits >> 16);
+            so[(2 * tt) * RT_ROWS] = (uint16_t)bits[u];
+            so[(2 * tt + 1) * RT_ROWS] = (uint16_t)(bits[u] >> 16);
           }
         }
       }
       tc_fence_before();
+      mbar_arrive(&sh->t_empty[b]);
       if (rad_box) {
-        const uint32_t info = sh->info[g][t];
 #pragma unroll
         for (int w = 0; w < 2; ++w) {
           const uint32_t u = (info >> (14 * w)) & 0x3FFFu;  // u <= 2^13: two balanced digits
@@ -1156,35 +1216,32 @@ __global__ void __launch_bounds__(RT_ROWS *RT_MAX_WG, 1)
       } else {
         const int64_t r = (int64_t)tr * JT + dj, k = (int64_t)tk * KT + dk;
         if (r < a.rows && (a.ro.r1 || a.ro.r2)) {
-          const uint32_t info = sh->info[g][t];
           const int64_t off = r * a.Kp + k;
           if (a.ro.r1) put_small_digits(info & 0x3FFFu, a.ro.r1 + off, plane);
           if (a.ro.r2) put_small_digits((info >> 14) & 0x3FFFu, a.ro.r2 + off, plane);
         }
       }
+      fence_async_smem();
+      named_bar(1 + d, RT_ROWS);
+      if (t == 0) tma_store_3d(&tmo, sO + (size_t)d * a.NPL * RT_ROWS, tk * KT, tr * JT, 0);
     }
-    fence_async_smem();
-    named_bar(1 + g, RT_ROWS);
-    if (t == 0 && !sh->fail[g]) tma_store_3d(&tmo, myO, tk * KT, tr * JT, 0);
-    tr = ntr;
-    tk = ntk2;
+    if (t == 0) tma_store_wait_all();
   }
-  if (t == 0) tma_store_wait_all();
-  cp_async_wait_all();
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
-  if (threadIdx.x < 32) tmem_dealloc(sh->tmem_base, a.tcols);
+  if (warp == mma_warp) tmem_dealloc(sh->tmem_base, a.tcols);
 }
 
 struct RtLayout {
-  int KD, NPAD, WG, wg_cols, NPL, SW;
+  int KD, NPAD, NS, ND, wg_cols, NPL, SW;
   size_t smem;
 };
 
-static size_t residue_tc_smem_for(int KD, int NPAD, int WG, int NPL, int NM, int SW) {
-  return 1024 + (size_t)KD * NPAD * 128 + (size_t)WG * KD * RT_TILE + (size_t)WG * NPL * RT_ROWS * 2 +
-         (size_t)WG * SW * RT_ROWS * 8 + (size_t)((NM + 1) & ~1) * 8 + sizeof(RtShared);
+static size_t residue_tc_smem_for(int KD, int NPAD, int NS, int ND, int NPL, int NM, int SW) {
+  return 1024 + (size_t)KD * NPAD * 128 + (size_t)NS * KD * RT_TILE +
+         (size_t)ND * NPL * RT_ROWS * 2 + (size_t)RT_NP * RT_PD * SW * RT_ROWS * 8 +
+         (size_t)NPAD / 2 * 8 + sizeof(RtShared);
 }
 
 // The kernel's shape for an operand of `nch` 32-bit chunks and NM moduli; false when it does not
@@ -1198,14 +1255,17 @@ static bool residue_tc_layout(int nch, int NM, bool rad_box, int64_t entries, Rt
   const int ncls = nch <= 4 ? 4 : nch <= 8 ? 8 : nch <= 11 ? 11 : nch <= 16 ? 16 : nch <= 24 ? 24 : 32;
   L->SW = RT_SLOT_FIXED + (ncls + 1) / 2 + 1;
   if (L->NPL > 256) return false;
-  for (int wg = 512 / L->wg_cols < RT_MAX_WG ? 512 / L->wg_cols : RT_MAX_WG; wg >= 1; --wg) {
-    const size_t s = residue_tc_smem_for(L->KD, L->NPAD, wg, L->NPL, NM, L->SW);
-    if (s <= RT_SMEM_MAX) {
-      L->WG = wg;
-      L->smem = s < RT_SMEM_MIN ? RT_SMEM_MIN : s;
-      return true;
+  const int nd_max = 512 / L->wg_cols - 1 < RT_MAX_ND ? 512 / L->wg_cols - 1 : RT_MAX_ND;
+  for (int nd = nd_max; nd >= 1; --nd)
+    for (int ns = RT_MAX_NS; ns >= 2; --ns) {
+      const size_t s = residue_tc_smem_for(L->KD, L->NPAD, ns, nd, L->NPL, NM, L->SW);
+      if (s <= RT_SMEM_MAX) {
+        L->ND = nd;
+        L->NS = ns;
+        L->smem = s < RT_SMEM_MIN ? RT_SMEM_MIN : s;
+        return true;
+      }
     }
-  }
   return false;
 }
 
@@ -1213,20 +1273,23 @@ static arbgpu_status launch_residues_tc(arbgpu_ctx *ctx, const RtLayout &L, int 
                                         cudaStream_t s, RtArgs a, __nv_bfloat16 *out) {
   const int JT = a.is_b ? 4 : 2;  // Kp is a multiple of 64, so KT = 32 or 64 divides it
   a.NPAD = L.NPAD;
-  a.WG = L.WG;
+  a.NS = L.NS;
+  a.ND = L.ND;
   a.wg_cols = L.wg_cols;
   a.NPL = L.NPL;
-  a.tcols = (uint32_t)(L.WG * L.wg_cols);
+  a.tcols = 32;  // a power of two covering the ND + 1 accumulators
+  while (a.tcols < (uint32_t)((L.ND + 1) * L.wg_cols)) a.tcols *= 2;
   a.status = ctx->status;
   const int KT = RT_ROWS / JT;
   const int64_t nT = ((a.rows + JT - 1) / JT) * (a.Kp / KT);
-  int64_t grid = (nT + L.WG - 1) / L.WG;
+  int64_t grid = nT;
   if (grid > ctx->sm_count) grid = ctx->sm_count;
   if (grid < 1) return ARBGPU_OK;
   CUtensorMap tm;
   if (!make_residue_store_map(&tm, out, a.Kp, a.rows, L.NPL, KT, JT, L.NPL))
     return ARBGPU_ERR_CUDA;
   const int dev = ctx->device & 255;
+  const unsigned threads = 32u * (unsigned)(4 * L.ND + 4 * RT_NP + 1);
 #define ARB_RTC(NCH_)                                                                      \
   do {                                                                                     \
     if (a.is_b) {                                                                          \
@@ -1238,7 +1301,7 @@ static arbgpu_status launch_residues_tc(arbgpu_ctx *ctx, const RtLayout &L, int 
           return ARBGPU_ERR_CUDA;                                                          \
         attr_done[dev] = true;                                                             \
       }                                                                                    \
-      residue_tc_kernel<NCH_, true><<<(unsigned)grid, RT_ROWS * L.WG, L.smem, s>>>(tm, a); \
+      residue_tc_kernel<NCH_, true><<<(unsigned)grid, threads, L.smem, s>>>(tm, a);        \
     } else {                                                                               \
       static bool attr_done[256] = {};                                                     \
       if (!attr_done[dev]) {                                                               \
@@ -1248,7 +1311,7 @@ static arbgpu_status launch_residues_tc(arbgpu_ctx *ctx, const RtLayout &L, int 
           return ARBGPU_ERR_CUDA;                                                          \
         attr_done[dev] = true;                                                             \
       }                                                                                    \
-      residue_tc_kernel<NCH_, false><<<(unsigned)grid, RT_ROWS * L.WG, L.smem, s>>>(tm, a); \
+      residue_tc_kernel<NCH_, false><<<(unsigned)grid, threads, L.smem, s>>>(tm, a);       \
     }                                                                                      \
   } while (0)
   if (nch <= 4) ARB_RTC(4);
