@@ -1000,12 +1000,24 @@ __global__ void __launch_bounds__(RT_MAX_THREADS, 1)
     const int lbase = nl - NLW;  // limb index of the slot's first limb (lower ones are not read)
     // copies of the entry of this producer's j-th tile (the CTA's tile i = p + j RT_NP) into
     // slot j mod RT_PD (none outside X); one commit group per call, empty past the last tile
-    auto prefetch = [&](int j) {
+    // this producer's tiles advance by RT_NP gridDim.x: (tile row, tile column) step by (dtr, dtk)
+    const int jstep = RT_NP * (int)gridDim.x, dtr = jstep / ntk, dtk = jstep - dtr * ntk;
+    auto advance = [&](int &tr, int &tk) {
+      tr += dtr;
+      tk += dtk;
+      if (tk >= ntk) {
+        tk -= ntk;
+        ++tr;
+      }
+    };
+    const int tile0 = (int)blockIdx.x + p * (int)gridDim.x;
+    int ftr = tile0 / ntk, ftk = tile0 - ftr * ntk, fj = 0;  // the next tile to stage
+    auto prefetch = [&]() {
+      const int j = fj++;
       uint64_t *slot = pslots + ((size_t)(j % RT_PD) * RT_ROWS + pt) * SW;
       const int i = p + j * RT_NP;
-      const int tile = (int)blockIdx.x + i * (int)gridDim.x;
-      const int tr = tile / ntk, tk = tile - tr * ntk;
-      const int64_t r = (int64_t)tr * JT + pj, k = (int64_t)tk * KT + pk;
+      const int64_t r = (int64_t)ftr * JT + pj, k = (int64_t)ftk * KT + pk;
+      advance(ftr, ftk);
       if (i < ntiles && r < a.rows && k < a.K) {
         const BallsView &X = a.X;
         const int64_t e = IS_B ? ((a.k0 + k) * a.ld + r) : (r * a.ld + a.k0 + k);
@@ -1026,12 +1038,11 @@ __global__ void __launch_bounds__(RT_MAX_THREADS, 1)
       cp_async_commit();
     };
     const int jlo = lbase < 0 ? -2 * lbase : 0;  // first 32-bit limb word that exists
-    for (int j = 0; j < RT_PD; ++j) prefetch(j);
-    for (int j = 0, i = p; i < ntiles; ++j, i += RT_NP) {
+    for (int j = 0; j < RT_PD; ++j) prefetch();
+    int tr = tile0 / ntk, tk = tile0 - tr * ntk;
+    for (int j = 0, i = p; i < ntiles; ++j, i += RT_NP, advance(tr, tk)) {
       const uint64_t *slot = pslots + ((size_t)(j % RT_PD) * RT_ROWS + pt) * SW;
       const uint32_t *Wd = (const uint32_t *)(slot + RT_SLOT_FIXED);  // 32-bit words of the limbs
-      const int tile = (int)blockIdx.x + i * (int)gridDim.x;
-      const int tr = tile / ntk, tk = tile - tr * ntk;
       const int s = i % NS;
       const int64_t r = (int64_t)tr * JT + pj, k = (int64_t)tk * KT + pk;
       uint32_t ch[NCH];
@@ -1090,9 +1101,9 @@ __global__ void __launch_bounds__(RT_MAX_THREADS, 1)
         }
       }
       // every slot value is in registers now: stage tile j + RT_PD into the same slot
-      prefetch(j + RT_PD);
+      prefetch();
       // the digit tile s is free once the drain of the tile that used it has read its info
-      if (!mbar_wait(&sh->a_empty[s], ((i / NS) & 1) ^ 1, &sh->never)) {
+      if (!mbar_wait_sleep(&sh->a_empty[s], ((i / NS) & 1) ^ 1)) {
         set_status(a.status, ARBGPU_ERR_TIMEOUT);
         break;
       }
@@ -1128,8 +1139,8 @@ __global__ void __launch_bounds__(RT_MAX_THREADS, 1)
       const uint32_t idesc = idesc_bf16_f32(RT_ROWS, a.NPAD);
       for (int i = 0; i < ntiles; ++i) {
         const int s = i % NS, b = i % NB;
-        if (!mbar_wait(&sh->a_full[s], (i / NS) & 1, &sh->never) ||
-            !mbar_wait(&sh->t_empty[b], ((i / NB) & 1) ^ 1, &sh->never)) {
+        if (!mbar_wait_sleep(&sh->a_full[s], (i / NS) & 1) ||
+            !mbar_wait_sleep(&sh->t_empty[b], ((i / NB) & 1) ^ 1)) {
           set_status(a.status, ARBGPU_ERR_TIMEOUT);
           break;
         }
@@ -1158,8 +1169,8 @@ __global__ void __launch_bounds__(RT_MAX_THREADS, 1)
       const int s = i % NS, b = i % NB;
       // (the wait on a_full, complete by then, orders the producer's info writes before the
       // reads below)
-      const bool got = mbar_wait(&sh->t_full[b], (i / NB) & 1, &sh->never) &&
-                       mbar_wait(&sh->a_full[s], (i / NS) & 1, &sh->never);
+      const bool got = mbar_wait_sleep(&sh->t_full[b], (i / NB) & 1) &&
+                       mbar_wait_sleep(&sh->a_full[s], (i / NS) & 1);
       if (t == 0) tma_store_wait_read();  // this warpgroup's previous store has read its staging
       if (named_bar_or(1 + d, RT_ROWS, !got)) {
         if (t == 0) set_status(a.status, ARBGPU_ERR_TIMEOUT);
