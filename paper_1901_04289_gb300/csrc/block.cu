@@ -977,6 +977,7 @@ __global__ void __launch_bounds__(RT_MAX_THREADS, 1)
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
+  pdl_wait();  // the operands and scan results come from earlier kernels
 
   const int ntk = (int)(a.Kp / KT);
   const int nT = (int)((a.rows + JT - 1) / JT) * ntk;  // the host keeps this below 2^30
@@ -1238,6 +1239,7 @@ __global__ void __launch_bounds__(RT_MAX_THREADS, 1)
     }
     if (t == 0) tma_store_wait_all();
   }
+  pdl_trigger();
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
@@ -1312,7 +1314,8 @@ static arbgpu_status launch_residues_tc(arbgpu_ctx *ctx, const RtLayout &L, int 
           return ARBGPU_ERR_CUDA;                                                          \
         attr_done[dev] = true;                                                             \
       }                                                                                    \
-      residue_tc_kernel<NCH_, true><<<(unsigned)grid, threads, L.smem, s>>>(tm, a);        \
+      launch_pdl(residue_tc_kernel<NCH_, true>, dim3((unsigned)grid), dim3(threads), L.smem, s, \
+                 tm, a);                                                                   \
     } else {                                                                               \
       static bool attr_done[256] = {};                                                     \
       if (!attr_done[dev]) {                                                               \
@@ -1322,7 +1325,8 @@ static arbgpu_status launch_residues_tc(arbgpu_ctx *ctx, const RtLayout &L, int 
           return ARBGPU_ERR_CUDA;                                                          \
         attr_done[dev] = true;                                                             \
       }                                                                                    \
-      residue_tc_kernel<NCH_, false><<<(unsigned)grid, threads, L.smem, s>>>(tm, a);       \
+      launch_pdl(residue_tc_kernel<NCH_, false>, dim3((unsigned)grid), dim3(threads), L.smem,   \
+                 s, tm, a);                                                                \
     }                                                                                      \
   } while (0)
   if (nch <= 4) ARB_RTC(4);
@@ -1662,6 +1666,7 @@ __global__ void __launch_bounds__(128, 6) block_round_regs_kernel(const RoundArg
     for (int k = threadIdx.x; k < c.NM; k += blockDim.x) sr[k] = __ldg(c.rinv + k);
     __syncthreads();
   }
+  pdl_wait();  // the block products come from the GEMM kernel before this one
   const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= a.M * a.N) return;
   const int64_t i = idx / a.N, j = idx - i * a.N;
@@ -1688,11 +1693,14 @@ static void launch_block_round(const RoundArgs &ra, cudaStream_t s) {
   const int nw = product_limbs(ra.mid);
   const unsigned blocks = (unsigned)((ra.M * ra.N + 127) / 128);
   if (crt_smem_bytes(ra.mid, 8) <= 48 * 1024 && ra.prec < 64 * 8 && nw <= 8)
-    block_round_regs_kernel<8><<<blocks, 128, crt_smem_bytes(ra.mid, 8), s>>>(ra);
+    launch_pdl(block_round_regs_kernel<8>, dim3(blocks), dim3(128), crt_smem_bytes(ra.mid, 8), s,
+               ra);
   else if (crt_smem_bytes(ra.mid, 12) <= 48 * 1024 && ra.prec < 64 * 12 && nw <= 12)
-    block_round_regs_kernel<12><<<blocks, 128, crt_smem_bytes(ra.mid, 12), s>>>(ra);
+    launch_pdl(block_round_regs_kernel<12>, dim3(blocks), dim3(128), crt_smem_bytes(ra.mid, 12),
+               s, ra);
   else if (crt_smem_bytes(ra.mid, 16) <= 48 * 1024 && ra.prec < 64 * 16 && nw <= 16)
-    block_round_regs_kernel<16><<<blocks, 128, crt_smem_bytes(ra.mid, 16), s>>>(ra);
+    launch_pdl(block_round_regs_kernel<16>, dim3(blocks), dim3(128), crt_smem_bytes(ra.mid, 16),
+               s, ra);
   else
     block_round_kernel<<<blocks, 128, 0, s>>>(ra);
 }

@@ -46,6 +46,31 @@ inline BallsOut out_of(const arbgpu_balls &b) {
 
 __device__ __forceinline__ uint32_t nsig_of(uint32_t flags) { return (flags >> ARBGPU_NSIG_SHIFT) & 0xFFu; }
 
+// Programmatic dependent launch: a kernel launched with launch_pdl may start while the previous
+// kernel of its stream finishes; pdl_wait() returns once that kernel has completed and its writes
+// are visible, so it comes before the first access to anything an earlier kernel writes.
+// pdl_trigger() lets the next such kernel start launching.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                              cudaStream_t stream, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = stream;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
 // Device status word: the first error code wins (atomicCAS from 0).
 __device__ __forceinline__ void set_status(int *status, int code) {
   if (status) atomicCAS(status, 0, code);

@@ -327,6 +327,7 @@ __global__ void __launch_bounds__(CG_THREADS, 1)
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
+  pdl_wait();  // the residue planes come from the kernels before this one
   const uint32_t tmem = sh->tmem_base;
   volatile int *abort = &sh->abort;
   auto give_up = [&]() {
@@ -468,6 +469,7 @@ __global__ void __launch_bounds__(CG_THREADS, 1)
     }
   }
 
+  pdl_trigger();
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
@@ -642,7 +644,8 @@ arbgpu_status launch_digit_gemm(arbgpu_ctx *ctx, const DigitGemmArgs &a, cudaStr
                       (int64_t)(a.SA) * a.SB * (int64_t)a.M * a.N * a.Kp * P.batch);
     const int64_t items = (int64_t)P.tiles_m * P.tiles_n * P.batch;
     const int64_t cgrid = items < ctx->sm_count ? items : ctx->sm_count;
-    crt_gemm_kernel<<<(unsigned)cgrid, CG_THREADS, CG_SMEM_BYTES, stream>>>(tmA, tmB, P);
+    launch_pdl(crt_gemm_kernel, dim3((unsigned)cgrid), dim3(CG_THREADS), CG_SMEM_BYTES, stream,
+               tmA, tmB, P);
     return cudaGetLastError() == cudaSuccess ? ARBGPU_OK : ARBGPU_ERR_CUDA;
   }
   if (grid > 0x7fffffff) return ARBGPU_ERR_LIMIT;
