@@ -525,6 +525,9 @@ struct CrtTables {
   const uint32_t *y;     // [NM]: (M / m_t)^-1 mod m_t
   const float *rinv;     // [NM]: 1 / m_t
   int NM, NMW, NW32P;
+  const uint16_t *wtab;  // reconstruction on the tensor cores: [NQP][128] BF16 weights
+  const float *mbytes;   // [NQ] balanced bytes of M
+  int NQ, NQP;
 };
 
 // One exact integer product.  kind 0: digit + carry form of T itself.  kind 1 (multimodular): for
@@ -1687,9 +1690,304 @@ static int product_limbs(const IntProduct &p) {
   return p.kind == 1 ? p.crt.NMW + 1 : (8 * p.ND + 32 + 63) / 64 + 1;
 }
 
+// ---- The reconstruction on the tensor cores.  For one entry, with z_t = l_t + 256 h_t (bytes),
+//
+//     sum_t z_t Q_t = sum_n 256^n S_n,   S_n = sum_t (l_t q_{t,n} + h_t q_{t,n-1}),
+//
+// with q_{t,n} the balanced bytes of Q_t = M / m_t: a product of the byte matrix
+// [entries][(t, byte)] and the table [(t, byte)][n].  |S_n| < 2^22 (at most 128 products of
+// magnitude <= 255 * 128), so the FP32 sums are exact.  One more column weighs the bytes with
+// 1/m_t and 256/m_t rounded to BF16: its sum is sum_t z_t / m_t with error below NM 2^-9 <= 1/8,
+// and since sum_t z_t / m_t = q + T / M with |T / M| < 1/8, its rint is the q of
+// T = sum_t z_t Q_t - q M.  The drain forms T = sum_n 256^n (S_n - q M_n), M_n the balanced bytes
+// of M, with carries between 32-bit words, then rounds it as block_round does.
+//
+// Roles (one CTA per SM, persistent over tiles of 128 consecutive entries of a row of C): one
+// producer warpgroup loads the tile's residues z with TMA and writes the byte rows, one warp
+// issues the MMAs, ND drain warpgroups take the tiles in turn.  Waits give up after ~2 s.
+constexpr int CR_MAX_ND = 3;
+constexpr int CR_NS = 3;  // byte tiles in flight
+constexpr int CR_NZ = 3;  // residue tiles in flight
+constexpr int CR_THREADS = 32 * (4 * CR_MAX_ND + 5);
+
+struct CrShared {
+  uint64_t z_full[CR_NZ];
+  uint64_t a_full[CR_NS], a_empty[CR_NS];
+  uint64_t t_full[CR_MAX_ND + 1], t_empty[CR_MAX_ND + 1];
+  uint32_t tmem_base;
+};
+
+struct CrArgs {
+  RoundArgs ra;
+  int NM, NQ, NQP, ND, wg_cols;
+  uint32_t tcols;
+  const uint16_t *wtab;  // [NQP][128] BF16
+  const float *mbytes;   // [NQ]
+  int *status;
+};
+
+static size_t crt_tc_smem(int NM, int NQ, int NQP) {
+  return 1024 + (size_t)2 * NQP * 128 + (size_t)CR_NS * 2 * RT_TILE + (size_t)CR_NZ * NM * 256 +
+         (size_t)((NQ + 15) & ~15) * 4 + sizeof(CrShared);
+}
+
+template <int NW>
+__global__ void __launch_bounds__(CR_THREADS, 1)
+    crt_round_tc_kernel(const __grid_constant__ CUtensorMap tmz, const __grid_constant__ CrArgs a) {
+  extern __shared__ __align__(1024) uint8_t smem_raw[];
+  const RoundArgs &ra = a.ra;
+  const int ND = a.ND, NB = a.ND + 1, NM = a.NM;
+  uint8_t *sW = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);  // 2 slabs [NQP][64]
+  uint8_t *sA = sW + (size_t)2 * a.NQP * 128;                                   // CR_NS x 2 slabs
+  uint16_t *sZ = (uint16_t *)(sA + (size_t)CR_NS * 2 * RT_TILE);               // CR_NZ x [NM][128]
+  float *sMb = (float *)(sZ + (size_t)CR_NZ * NM * 128);
+  CrShared *sh = (CrShared *)(sMb + ((a.NQ + 15) & ~15));
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int mma_warp = 4 * ND + 4;
+
+  if (threadIdx.x == 0) {
+    for (int q = 0; q < CR_NZ; ++q) mbar_init(&sh->z_full[q], 1);
+    for (int q = 0; q < CR_NS; ++q) {
+      mbar_init(&sh->a_full[q], RT_ROWS);
+      mbar_init(&sh->a_empty[q], 1);
+    }
+    for (int q = 0; q < NB; ++q) {
+      mbar_init(&sh->t_full[q], 1);
+      mbar_init(&sh->t_empty[q], RT_ROWS);
+    }
+    fence_mbar_init();
+  }
+  if (warp == mma_warp) {
+    tmem_alloc(&sh->tmem_base, a.tcols);
+    tmem_relinquish();
+  }
+  if (threadIdx.x == 32) tma_prefetch_desc(&tmz);
+  for (int q = threadIdx.x; q < a.NQP * 16; q += blockDim.x) {  // weights, 128-byte swizzle
+    const int n = q >> 4, c = q & 15;
+    const uint4 v = __ldg((const uint4 *)(a.wtab + (size_t)n * 128) + c);
+    *(uint4 *)(sW + (size_t)(c >> 3) * a.NQP * 128 + (size_t)n * 128 + (((c & 7) ^ (n & 7)) << 4)) =
+        v;
+  }
+  for (int q = threadIdx.x; q < ((a.NQ + 15) & ~15); q += blockDim.x)  // zero past NQ
+    sMb[q] = q < a.NQ ? __ldg(a.mbytes + q) : 0.0f;
+  fence_async_smem();
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  pdl_wait();  // the residues z come from the GEMM kernel before this one
+
+  const int ntj = (int)((ra.N + RT_ROWS - 1) / RT_ROWS);
+  const int nT = (int)ra.M * ntj;  // the host keeps this below 2^30
+  const int ntiles = nT > (int)blockIdx.x ? (nT - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+
+  if (warp >= 4 * ND && warp < mma_warp) {
+    // ------------------------------------------------ producer: byte rows of the residues
+    const int pt = threadIdx.x - 128 * ND;
+    auto zload = [&](int k) {  // residues of this CTA's k-th tile into stage k mod CR_NZ
+      const int tile = (int)blockIdx.x + k * (int)gridDim.x;
+      const int i = tile / ntj, jb = tile - i * ntj;
+      const int st = k % CR_NZ;
+      mbar_arrive_expect_tx(&sh->z_full[st], (uint32_t)NM * RT_ROWS * 2);
+      tma_load_3d(sZ + (size_t)st * NM * RT_ROWS, &tmz, &sh->z_full[st], jb * RT_ROWS, i, 0);
+    };
+    if (pt == 0)
+      for (int k = 0; k < CR_NZ && k < ntiles; ++k) zload(k);
+    const int nch = (2 * NM + 7) / 8;  // 16-byte chunks of a byte row that hold residues
+    for (int k = 0; k < ntiles; ++k) {
+      const int zs = k % CR_NZ, s = k % CR_NS;
+      const bool ok = mbar_wait_sleep(&sh->z_full[zs], (k / CR_NZ) & 1) &&
+                      mbar_wait_sleep(&sh->a_empty[s], ((k / CR_NS) & 1) ^ 1);
+      // (also: every thread has read the residues of tile k - 1, so its stage can be refilled)
+      if (named_bar_or(1 + ND, RT_ROWS, !ok)) {
+        if (pt == 0) set_status(a.status, ARBGPU_ERR_TIMEOUT);
+        break;
+      }
+      if (pt == 0 && k >= 1 && k - 1 + CR_NZ < ntiles) zload(k - 1 + CR_NZ);
+      const uint16_t *zr = sZ + (size_t)zs * NM * RT_ROWS + pt;
+      uint8_t *row = sA + (size_t)s * 2 * RT_TILE + (size_t)pt * 128;
+#pragma unroll 4
+      for (int c = 0; c < 16; ++c) {  // chunk c: moduli 4c .. 4c + 3 (low byte, high byte)
+        uint32_t wv[4] = {0u, 0u, 0u, 0u};
+        if (c < nch) {
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const int t = 4 * c + u;
+            if (t < NM) {
+              const uint32_t z = zr[t * RT_ROWS];
+              const float lo = __uint_as_float(__byte_perm(z, 0x4B000000u, 0x7540u)) - 8388608.0f;
+              const float hi = __uint_as_float(__byte_perm(z, 0x4B000000u, 0x7541u)) - 8388608.0f;
+              wv[u] = bf16x2_bits(lo, hi);
+            }
+          }
+        }
+        *(uint4 *)(row + (size_t)(c >> 3) * RT_TILE + (((c & 7) ^ (pt & 7)) << 4)) =
+            make_uint4(wv[0], wv[1], wv[2], wv[3]);
+      }
+      fence_async_smem();
+      mbar_arrive(&sh->a_full[s]);
+    }
+  } else if (warp == mma_warp) {
+    // ------------------------------------------------ MMA issuer
+    if (lane == 0) {
+      const uint32_t idesc = idesc_bf16_f32(RT_ROWS, a.NQP);
+      const int nks = (2 * NM + 15) / 16;  // K steps of 16 that hold residue bytes
+      for (int k = 0; k < ntiles; ++k) {
+        const int s = k % CR_NS, b = k % NB;
+        if (!mbar_wait_sleep(&sh->a_full[s], (k / CR_NS) & 1) ||
+            !mbar_wait_sleep(&sh->t_empty[b], ((k / NB) & 1) ^ 1)) {
+          set_status(a.status, ARBGPU_ERR_TIMEOUT);
+          break;
+        }
+        tc_fence_after();
+        const uint32_t tm = sh->tmem_base + (uint32_t)(b * a.wg_cols);
+        for (int ks = 0; ks < nks; ++ks) {
+          const int sl = ks >> 2, sub = ks & 3;
+          const uint64_t ad = sw128_desc(smem_u32(sA + ((size_t)s * 2 + sl) * RT_TILE));
+          const uint64_t bd = sw128_desc(smem_u32(sW + (size_t)sl * a.NQP * 128));
+          umma_bf16(tm, ad + 2 * sub, bd + 2 * sub, idesc, ks > 0 ? 1u : 0u);
+        }
+        umma_commit(&sh->t_full[b]);
+        umma_commit(&sh->a_empty[s]);
+      }
+    }
+  } else {
+    // ------------------------------------------------ drain warpgroup d: tiles k = d (mod ND)
+    const int d = warp >> 2, t = threadIdx.x & 127, wq = warp & 3;
+    for (int k = d; k < ntiles; k += ND) {
+      const int tile = (int)blockIdx.x + k * (int)gridDim.x;
+      const int64_t i = tile / ntj, j = (int64_t)(tile - (int)i * ntj) * RT_ROWS + t;
+      const int b = k % NB;
+      if (!__all_sync(0xffffffffu, mbar_wait_sleep(&sh->t_full[b], (k / NB) & 1))) {
+        if (lane == 0) set_status(a.status, ARBGPU_ERR_TIMEOUT);
+        break;
+      }
+      tc_fence_after();
+      const uint32_t tm =
+          sh->tmem_base + (uint32_t)(b * a.wg_cols) + ((uint32_t)(32 * wq) << 16);
+      float qf;
+      {
+        uint32_t v[16];
+        tmem_ld16(tm + (uint32_t)(a.NQ & ~15), v);
+        tmem_wait_ld();
+        float sq = 0.0f;
+#pragma unroll
+        for (int c = 0; c < 16; ++c)
+          if (c == (a.NQ & 15)) sq = __uint_as_float(v[c]);
+        qf = __fadd_rn(__fadd_rn(sq, RT_MAGIC), -RT_MAGIC);  // q = rint(sum_t z_t / m_t)
+      }
+      // T = sum_n 256^n (S_n - q M_n), four columns per 32-bit word: each biased column
+      // S_n - q M_n + 1.5 2^23 has the bit pattern 0x4B400000 + (S_n - q M_n)
+      uint64_t T[NW];
+      int64_t carry = 0;
+#pragma unroll
+      for (int g = 0; g < NW / 2; ++g) {  // columns 16g .. 16g + 15 = limbs 2g, 2g + 1
+        if (16 * g < a.NQ) {
+          uint32_t v[16];
+          tmem_ld16(tm + (uint32_t)(16 * g), v);
+          tmem_wait_ld();
+          uint32_t wd[4];
+#pragma unroll
+          for (int w = 0; w < 4; ++w) {
+            const float4 mb = *(const float4 *)(sMb + 16 * g + 4 * w);  // zero past NQ
+            const float mbv[4] = {mb.x, mb.y, mb.z, mb.w};
+            int64_t acc = carry - (int64_t)0x4B400000 * 0x01010101LL;
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+              const int n = 16 * g + 4 * w + c;
+              const float col = n < a.NQ ? __uint_as_float(v[4 * w + c]) : 0.0f;
+              const uint32_t bits =
+                  __float_as_uint(__fadd_rn(__fmaf_rn(-qf, mbv[c], col), RT_MAGIC));
+              acc += (int64_t)bits << (8 * c);
+            }
+            wd[w] = (uint32_t)acc;
+            carry = acc >> 32;
+          }
+          T[2 * g] = (uint64_t)wd[0] | ((uint64_t)wd[1] << 32);
+          T[2 * g + 1] = (uint64_t)wd[2] | ((uint64_t)wd[3] << 32);
+        } else {
+          const uint64_t ext = carry < 0 ? ~(uint64_t)0 : 0;  // the sign of T
+          T[2 * g] = ext;
+          T[2 * g + 1] = ext;
+        }
+      }
+      tc_fence_before();
+      mbar_arrive(&sh->t_empty[b]);
+      if (j < ra.N) {
+        const bool rowz = ra.rtop[i] == INT64_MIN, colz = ra.ctop[j] == INT64_MIN;
+        const int64_t sigma = (rowz ? 0 : ra.rbot[i]) + (colz ? 0 : ra.cbot[j]);
+        const Mag rad = block_radius_regs(ra.rp1, ra.rp2, ra.rtop, ra.rrad, ra.crad, ra.cplus, i,
+                                          j, ra.Mp, ra.Np);
+        round_store_regs<NW>(T, sigma, 0, rad, ra.prec, ra.C, i * ra.ldc + j);
+      }
+    }
+  }
+  pdl_trigger();
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == mma_warp) tmem_dealloc(sh->tmem_base, a.tcols);
+}
+
+// The reconstruction and rounding on the tensor cores, when the product is multimodular with
+// NM <= 64 and fits one of the register sizes; false otherwise (block_round then runs).
+static bool launch_crt_round_tc(arbgpu_ctx *ctx, const RoundArgs &ra, cudaStream_t s,
+                                arbgpu_status *st) {
+  const CrtTables &c = ra.mid.crt;
+  if (ra.mid.kind != 1 || c.NM > 64 || !c.wtab || c.NQP > 256 || c.NQP < 16) return false;
+  const int nw = product_limbs(ra.mid);
+  int NW = 0;
+  if (ra.prec < 64 * 8 && nw <= 8 && c.NQ <= 64) NW = 8;
+  else if (ra.prec < 64 * 12 && nw <= 12 && c.NQ <= 96) NW = 12;
+  else if (ra.prec < 64 * 16 && nw <= 16 && c.NQ <= 128) NW = 16;
+  if (!NW) return false;
+  const int64_t ntj = (ra.N + RT_ROWS - 1) / RT_ROWS, nT = ra.M * ntj;
+  if (nT > ((int64_t)1 << 30)) return false;
+  CrArgs a{};
+  a.ra = ra;
+  a.NM = c.NM;
+  a.NQ = c.NQ;
+  a.NQP = c.NQP;
+  a.wg_cols = c.NQP <= 128 ? 128 : 256;
+  a.ND = c.NQP <= 128 ? 3 : 1;
+  a.tcols = 512;
+  a.wtab = c.wtab;
+  a.mbytes = c.mbytes;
+  a.status = ctx->status;
+  size_t smem = crt_tc_smem(c.NM, c.NQ, c.NQP);
+  if (smem > RT_SMEM_MAX) return false;
+  if (smem < RT_SMEM_MIN) smem = RT_SMEM_MIN;
+  CUtensorMap tm;
+  if (!make_z_load_map(&tm, ra.mid.digits, ra.Np, ra.Mp, c.NM, c.NM)) return false;
+  int64_t grid = nT < ctx->sm_count ? nT : ctx->sm_count;
+  const unsigned threads = 32u * (unsigned)(4 * a.ND + 5);
+  const int dev = ctx->device & 255;
+#define ARB_CRT(NW_)                                                                          \
+  do {                                                                                        \
+    static bool attr_done[256] = {};                                                          \
+    if (!attr_done[dev]) {                                                                    \
+      if (cudaFuncSetAttribute(crt_round_tc_kernel<NW_>,                                      \
+                               cudaFuncAttributeMaxDynamicSharedMemorySize,                   \
+                               (int)RT_SMEM_MAX) != cudaSuccess) {                            \
+        *st = ARBGPU_ERR_CUDA;                                                                \
+        return true;                                                                          \
+      }                                                                                       \
+      attr_done[dev] = true;                                                                  \
+    }                                                                                         \
+    launch_pdl(crt_round_tc_kernel<NW_>, dim3((unsigned)grid), dim3(threads), smem, s, tm, a); \
+  } while (0)
+  if (NW == 8) ARB_CRT(8);
+  else if (NW == 12) ARB_CRT(12);
+  else ARB_CRT(16);
+#undef ARB_CRT
+  *st = cudaGetLastError() == cudaSuccess ? ARBGPU_OK : ARBGPU_ERR_CUDA;
+  return true;
+}
+
 // The rounding epilogue of one block: the register kernel of the smallest size that holds the
 // product, else the general one.
-static void launch_block_round(const RoundArgs &ra, cudaStream_t s) {
+static void launch_block_round(arbgpu_ctx *ctx, const RoundArgs &ra, cudaStream_t s) {
+  arbgpu_status tc_st;
+  if (launch_crt_round_tc(ctx, ra, s, &tc_st)) return;  // (launch errors surface at the caller)
   const int nw = product_limbs(ra.mid);
   const unsigned blocks = (unsigned)((ra.M * ra.N + 127) / 128);
   if (crt_smem_bytes(ra.mid, 8) <= 48 * 1024 && ra.prec < 64 * 8 && nw <= 8)
@@ -2147,7 +2445,9 @@ static arbgpu_status run_block(arbgpu_ctx *ctx, const BlockWs &w, uint8_t *ws, c
     if (ensure_crt_constants(ctx->device) != ARBGPU_OK) return ARBGPU_ERR_CUDA;
     CrtDevTables dt{};
     if (crt_device_tables(ctx, plan, &dt) != ARBGPU_OK) return ARBGPU_ERR_CUDA;
-    CrtTables ct{dt.Q32, dt.M32, dt.y, dt.rinv, plan->NM, plan->NMW, plan->NW32P};
+    CrtTables ct{dt.Q32,         dt.M32,     dt.y,      dt.rinv,  plan->NM, plan->NMW,
+                 plan->NW32P,    dt.crt_wtab, dt.mbytes, plan->NQ, plan->NQP};
+    if (plan->NM > 64) ct.wtab = nullptr;  // (the table is built for NM <= 64 only)
     __nv_bfloat16 *resA = (__nv_bfloat16 *)(ws + w.resA), *resB = (__nv_bfloat16 *)(ws + w.resB);
     // with radii, the two radius products ride in the same GEMM as items NM and NM + 1: their
     // operand planes follow the residue planes, and their exact values come out as int64
@@ -2498,7 +2798,7 @@ arbgpu_status block_finish(arbgpu_ctx *ctx, const arbgpu_balls *C, const arbgpu_
       const int64_t units =
           ra.mid.kind == 1 ? M * N * ra.mid.crt.NM * (int64_t)(2 * ra.mid.crt.NMW) : M * N;
       LaunchScope sc(ctx, s, "block_round", units);
-        launch_block_round(ra, s);
+        launch_block_round(ctx, ra, s);
       }
       *used_block = true;
       return cudaGetLastError() == cudaSuccess ? ARBGPU_OK : ARBGPU_ERR_CUDA;

@@ -142,6 +142,54 @@ std::unique_ptr<CrtPlan> build_plan(int NM) {
         v = (v << 8) % m;
       }
     }
+  // reconstruction weights (used when NM <= 64)
+  {
+    auto balanced_bytes = [](const std::vector<uint64_t> &x, int nb) {
+      std::vector<int> d(nb, 0);
+      int carry = 0;
+      for (int n = 0; n < nb; ++n) {
+        const int k = n / 8;
+        int v = (k < (int)x.size() ? (int)((x[k] >> (8 * (n % 8))) & 255) : 0) + carry;
+        carry = 0;
+        if (v >= 128) {
+          v -= 256;
+          carry = 1;
+        }
+        d[n] = v;
+      }
+      return d;
+    };
+    const int NB = (bit_length(P->M) + 7) / 8 + 1;  // balanced bytes of M (and of each Q_t)
+    P->NQ = NB + 1;                                 // the high byte of z shifts Q_t by one
+    P->NQP = (P->NQ + 1 + 15) / 16 * 16;
+    P->crt_wtab.assign((size_t)P->NQP * 128, 0);
+    P->mbytes.assign(P->NQ, 0.f);
+    auto bf16_of = [](float f) {  // round to nearest even (exact for the small integers)
+      uint32_t u;
+      memcpy(&u, &f, 4);
+      u += 0x7FFFu + ((u >> 16) & 1u);
+      return (uint16_t)(u >> 16);
+    };
+    if (NM <= 64) {
+      for (int t = 0; t < NM; ++t) {
+        std::vector<uint64_t> Q(P->NMW, 0);
+        for (int k = 0; k < P->NMW; ++k)
+          Q[k] = (uint64_t)P->Q32[(size_t)t * P->NW32P + 2 * k] |
+                 ((uint64_t)P->Q32[(size_t)t * P->NW32P + 2 * k + 1] << 32);
+        const std::vector<int> qb = balanced_bytes(Q, NB);
+        for (int n = 0; n < P->NQ; ++n) {
+          const int lo = n < NB ? qb[n] : 0, hi = (n >= 1 && n - 1 < NB) ? qb[n - 1] : 0;
+          P->crt_wtab[(size_t)n * 128 + 2 * t] = bf16_of((float)lo);
+          P->crt_wtab[(size_t)n * 128 + 2 * t + 1] = bf16_of((float)hi);
+        }
+        P->crt_wtab[(size_t)P->NQ * 128 + 2 * t] = bf16_of((float)(1.0 / (double)P->mods[t]));
+        P->crt_wtab[(size_t)P->NQ * 128 + 2 * t + 1] =
+            bf16_of((float)(256.0 / (double)P->mods[t]));
+      }
+      const std::vector<int> mb = balanced_bytes(P->M, NB);
+      for (int n = 0; n < NB; ++n) P->mbytes[n] = (float)mb[n];
+    }
+  }
   return P;
 }
 
@@ -163,7 +211,9 @@ arbgpu_status crt_device_tables(arbgpu_ctx *ctx, const CrtPlan *P, CrtDevTables 
   const size_t oz = oy + al(4 * P->y.size()), op = oz + al(4 * P->ztab.size());
   const size_t orv = op + al(4 * P->pow32.size()), oi = orv + al(4 * P->rinv.size());
   const size_t ow = oi + al(8 * P->inv.size());
-  const size_t total = ow + al(2 * P->wtab.size());
+  const size_t ocw = ow + al(2 * P->wtab.size());
+  const size_t omb = ocw + al(2 * P->crt_wtab.size());
+  const size_t total = omb + al(4 * P->mbytes.size());
   auto it = ctx->crt_tables.find(P->NM);
   uint8_t *base = nullptr;
   if (it != ctx->crt_tables.end()) {
@@ -179,6 +229,8 @@ arbgpu_status crt_device_tables(arbgpu_ctx *ctx, const CrtPlan *P, CrtDevTables 
     memcpy(h.data() + orv, P->rinv.data(), 4 * P->rinv.size());
     memcpy(h.data() + oi, P->inv.data(), 8 * P->inv.size());
     memcpy(h.data() + ow, P->wtab.data(), 2 * P->wtab.size());
+    memcpy(h.data() + ocw, P->crt_wtab.data(), 2 * P->crt_wtab.size());
+    memcpy(h.data() + omb, P->mbytes.data(), 4 * P->mbytes.size());
     if (cudaMemcpy(base, h.data(), total, cudaMemcpyHostToDevice) != cudaSuccess) {
       cudaFree(base);
       return ARBGPU_ERR_CUDA;
@@ -193,6 +245,8 @@ arbgpu_status crt_device_tables(arbgpu_ctx *ctx, const CrtPlan *P, CrtDevTables 
   out->rinv = (const float *)(base + orv);
   out->inv = (const uint64_t *)(base + oi);
   out->wtab = (const uint16_t *)(base + ow);
+  out->crt_wtab = (const uint16_t *)(base + ocw);
+  out->mbytes = (const float *)(base + omb);
   return ARBGPU_OK;
 }
 

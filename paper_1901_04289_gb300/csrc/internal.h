@@ -175,6 +175,13 @@ struct CrtPlan {
   // [2][NPAD][128] BF16 bits: row 2t + b of operand side o holds byte b (balanced, 256 h + l) of
   // the balanced w = 2^(8d) mod m_t (side 0) or 2^(8d) y_t mod m_t (side 1) in column d
   std::vector<uint16_t> wtab;
+  // Reconstruction on the tensor cores (NM <= 64): the output has NQ byte columns (balanced
+  // bytes of sum_t z_t Q_t, a q column follows); crt_wtab [NQP][128] BF16 bits, row n < NQ holding
+  // byte n of Q_t in column 2t and byte n - 1 in column 2t + 1 (z_t = l + 256 h, bytes l, h), row
+  // NQ holding 1 / m_t and 256 / m_t (rounded to BF16); mbytes [NQ]: the balanced bytes of M.
+  int NQ, NQP;
+  std::vector<uint16_t> crt_wtab;
+  std::vector<float> mbytes;
 };
 int crt_moduli_for_bits(int bits);
 const CrtPlan *crt_plan(int NM);
@@ -183,6 +190,8 @@ struct CrtDevTables {
   const uint32_t *Q32, *M32, *y, *ztab, *pow32;
   const float *rinv;
   const uint16_t *wtab;
+  const uint16_t *crt_wtab;
+  const float *mbytes;
   const uint64_t *inv;
 };
 arbgpu_status crt_device_tables(arbgpu_ctx *ctx, const CrtPlan *plan, CrtDevTables *out);

@@ -528,6 +528,20 @@ bool make_residue_store_map(CUtensorMap *tm, void *base, int64_t Kp, int64_t row
   return r == CUDA_SUCCESS;
 }
 
+bool make_z_load_map(CUtensorMap *tm, const void *base, int64_t Np, int64_t Mp, int64_t planes,
+                     int box_planes) {
+  PFN_tmapEncodeTiled enc = encode_fn();
+  if (!enc) return false;
+  cuuint64_t dims[3] = {(cuuint64_t)Np, (cuuint64_t)Mp, (cuuint64_t)planes};
+  cuuint64_t strides[2] = {(cuuint64_t)(Np * 2), (cuuint64_t)(Np * 2 * Mp)};
+  cuuint32_t box[3] = {128u, 1u, (cuuint32_t)box_planes};
+  cuuint32_t estr[3] = {1, 1, 1};
+  CUresult r = enc(tm, CU_TENSOR_MAP_DATA_TYPE_UINT16, 3, const_cast<void *>(base), dims, strides,
+                   box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
 int digit_gemm_groups(arbgpu_ctx *ctx, int M, int N, int ND) {
   const int tiles = ((M + TG_BM - 1) / TG_BM) * ((N + TG_BN - 1) / TG_BN);
   int g = ctx->sm_count / tiles;  // one wave of CTAs (one CTA per SM)

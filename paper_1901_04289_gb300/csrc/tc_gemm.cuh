@@ -70,6 +70,11 @@ struct DigitGemmParams {
 bool make_residue_store_map(CUtensorMap *tm, void *base, int64_t Kp, int64_t rows, int64_t planes,
                             int box_k, int box_rows, int box_planes);
 
+// Tensor map for TMA loads of 16-bit residue planes [planes][Mp][Np]: box 128 x 1 x box_planes
+// (128 consecutive columns of one row, every plane).
+bool make_z_load_map(CUtensorMap *tm, const void *base, int64_t Np, int64_t Mp, int64_t planes,
+                     int box_planes);
+
 // ------------------------------------------------------------------------------ PTX wrappers
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
