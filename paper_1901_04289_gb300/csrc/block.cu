@@ -1622,6 +1622,66 @@ __device__ __forceinline__ void round_store_regs(const uint64_t (&T)[NW], int64_
   store_rounded<NW + 1, 1>(C, oi, 0, zero, neg, ta, sigma + L, mag_add_up(r1, rad));
 }
 
+// round_store_regs for a long T and a short precision: only the top NWIN limbs of |T| (64 NWIN >=
+// prec + 66 bits) take part in the rounding.  The bits below that window enter as a sticky bit
+// OR-ed into the window's lowest bit, which keeps round-to-nearest exact (the round bit and the
+// sticky condition are unchanged), and as one more unit of the window's last place in the error
+// bound, which keeps the radius an upper bound of |rounded - T 2^sigma|.
+template <int NW, int NWIN>
+__device__ __forceinline__ void round_store_window(const uint64_t (&T)[NW], int64_t sigma, Mag rad,
+                                                   int prec, const BallsOut &C, int64_t oi) {
+  const bool neg = (T[NW - 1] >> 63) != 0;
+  uint64_t a[NW];
+  {
+    const uint64_t flip = neg ? ~(uint64_t)0 : 0;
+    u128 cc = neg ? 1 : 0;
+#pragma unroll
+    for (int k = 0; k < NW; ++k) {
+      cc += (u128)(T[k] ^ flip);
+      a[k] = (uint64_t)cc;
+      cc >>= 64;
+    }
+  }
+  const int L = limbs_bitlen<NW>(a);
+  uint64_t ta[NWIN + 1];
+  Mag r1{0u, 0};
+  if (L == 0) {
+#pragma unroll
+    for (int k = 0; k <= NWIN; ++k) ta[k] = 0;
+    store_rounded<NWIN + 1, 1>(C, oi, 0, true, neg, ta, sigma, rad);
+    return;
+  }
+  uint64_t w[NWIN];
+  int sh = L - 64 * NWIN;  // the window is a >> sh (sh <= 0: all of a)
+  bool sticky = false;
+  if (sh <= 0) {
+    sh = 0;
+#pragma unroll
+    for (int k = 0; k < NWIN; ++k) w[k] = k < NW ? a[k] : 0;
+  } else {
+    const int q = sh >> 6, r = sh & 63;
+    const uint64_t lowmask = (((uint64_t)1) << r) - 1;
+#pragma unroll
+    for (int k = 0; k < NW; ++k) sticky |= (k < q ? a[k] : (k == q ? (a[k] & lowmask) : 0)) != 0;
+    // a >>= 64 q (a barrel shifter over limbs), then the bit shift r into the window
+#pragma unroll
+    for (int bb = 1; bb < NW; bb <<= 1) {
+      const bool on = (q & bb) != 0;
+#pragma unroll
+      for (int j = 0; j < NW; ++j) a[j] = on ? (j + bb < NW ? a[j + bb] : 0) : a[j];
+    }
+#pragma unroll
+    for (int k = 0; k < NWIN; ++k) {
+      const uint64_t hi = k + 1 < NW ? a[k + 1] : 0;
+      w[k] = r ? ((a[k] >> r) | (hi << (64 - r))) : a[k];
+    }
+    w[0] |= sticky ? 1u : 0u;
+  }
+  int LW = L - sh;
+  round_abs_regs<NWIN>(w, LW, prec, sticky ? 1u : 0u, sigma + sh, ta, r1);
+  store_rounded<NWIN + 1, 1>(C, oi, 0, false, neg, ta, sigma + sh + LW, mag_add_up(r1, rad));
+}
+
 // Radius bound of one block product from its two radius products (values < 2^64).
 __device__ __forceinline__ Mag product_mag_regs(const IntProduct &p, int64_t i, int64_t j,
                                                 int64_t Mp, int64_t Np, int64_t base) {
@@ -1731,7 +1791,7 @@ static size_t crt_tc_smem(int NM, int NQ, int NQP) {
          (size_t)((NQ + 15) & ~15) * 4 + sizeof(CrShared);
 }
 
-template <int NW>
+template <int NW, int NWIN>
 __global__ void __launch_bounds__(CR_THREADS, 1)
     crt_round_tc_kernel(const __grid_constant__ CUtensorMap tmz, const __grid_constant__ CrArgs a) {
   extern __shared__ __align__(1024) uint8_t smem_raw[];
@@ -1917,7 +1977,11 @@ __global__ void __launch_bounds__(CR_THREADS, 1)
         const int64_t sigma = (rowz ? 0 : ra.rbot[i]) + (colz ? 0 : ra.cbot[j]);
         const Mag rad = block_radius_regs(ra.rp1, ra.rp2, ra.rtop, ra.rrad, ra.crad, ra.cplus, i,
                                           j, ra.Mp, ra.Np);
-        round_store_regs<NW>(T, sigma, 0, rad, ra.prec, ra.C, i * ra.ldc + j);
+        if (NWIN > 0)
+          round_store_window<NW, (NWIN > 0 ? NWIN : 1)>(T, sigma, rad, ra.prec, ra.C,
+                                                        i * ra.ldc + j);
+        else
+          round_store_regs<NW>(T, sigma, 0, rad, ra.prec, ra.C, i * ra.ldc + j);
       }
     }
   }
@@ -1961,11 +2025,11 @@ static bool launch_crt_round_tc(arbgpu_ctx *ctx, const RoundArgs &ra, cudaStream
   int64_t grid = nT < ctx->sm_count ? nT : ctx->sm_count;
   const unsigned threads = 32u * (unsigned)(4 * a.ND + 5);
   const int dev = ctx->device & 255;
-#define ARB_CRT(NW_)                                                                          \
+#define ARB_CRT(NW_, NWIN_)                                                                   \
   do {                                                                                        \
     static bool attr_done[256] = {};                                                          \
     if (!attr_done[dev]) {                                                                    \
-      if (cudaFuncSetAttribute(crt_round_tc_kernel<NW_>,                                      \
+      if (cudaFuncSetAttribute(crt_round_tc_kernel<NW_, NWIN_>,                               \
                                cudaFuncAttributeMaxDynamicSharedMemorySize,                   \
                                (int)RT_SMEM_MAX) != cudaSuccess) {                            \
         *st = ARBGPU_ERR_CUDA;                                                                \
@@ -1973,11 +2037,21 @@ static bool launch_crt_round_tc(arbgpu_ctx *ctx, const RoundArgs &ra, cudaStream
       }                                                                                       \
       attr_done[dev] = true;                                                                  \
     }                                                                                         \
-    launch_pdl(crt_round_tc_kernel<NW_>, dim3((unsigned)grid), dim3(threads), smem, s, tm, a); \
+    launch_pdl(crt_round_tc_kernel<NW_, NWIN_>, dim3((unsigned)grid), dim3(threads), smem, s, \
+               tm, a);                                                                        \
   } while (0)
-  if (NW == 8) ARB_CRT(8);
-  else if (NW == 12) ARB_CRT(12);
-  else ARB_CRT(16);
+  // a 6-limb rounding window when it holds prec + 66 bits and T is longer
+  const bool win6 = ra.prec + 66 <= 64 * 6;
+  if (NW == 8) {
+    if (win6) ARB_CRT(8, 6);
+    else ARB_CRT(8, 0);
+  } else if (NW == 12) {
+    if (win6) ARB_CRT(12, 6);
+    else ARB_CRT(12, 0);
+  } else {
+    if (win6) ARB_CRT(16, 6);
+    else ARB_CRT(16, 0);
+  }
 #undef ARB_CRT
   *st = cudaGetLastError() == cudaSuccess ? ARBGPU_OK : ARBGPU_ERR_CUDA;
   return true;
