@@ -272,26 +272,31 @@ __global__ void __launch_bounds__(TG_THREADS, 1)
 
 // ------------------------------------------------------------------------ multimodular kernel
 //
-// The residue products of the multimodular engine (2 x 2 balanced digits per modulus, K <= 1024):
-// every k-block stage holds A0, A1 (the two digit planes of the left residues) and B0 | B1 stacked
-// into one 256-row operand, and two MMAs of 128 x 256 x 16 per k-step write the four products
-// A0 B0 | A0 B1 | A1 B0 | A1 B1 into the four 128-column quarters of TMEM (one chain over the whole
-// K: |sum| <= K 2^14 <= 2^24 stays exact in FP32).  Sixteen drain warps (4 lane quadrants x 4
-// column quarters) form P = D0 + 2^8 D1 + 2^16 D2 exactly and write P mod m per entry, as the
-// general kernel's multimodular mode does.
+// The residue products of the multimodular engine (2 x 2 balanced digits per modulus, K <= 1024).
+// A work item is one modulus and one 128 x 64 output tile.  Every k-block stage holds A0, A1 (the
+// two digit planes of the left residues, 128 rows) and B0 | B1 (64 rows each) stacked into one
+// 128-row operand, and two MMAs of 128 x 128 x 16 per k-step write A0 B0 | A0 B1 | A1 B0 | A1 B1
+// into four 64-column quarters of one of two 256-column TMEM accumulators, so the drain of an
+// item overlaps the MMAs of the next (one chain over the whole K: |sum| <= K 2^14 <= 2^24 stays
+// exact in FP32).  Sixteen drain warps (4 lane quadrants x 4 groups of 16 columns) form
+// P = D0 + 2^8 D1 + 2^16 D2 exactly and write P mod m per entry, as the general kernel's
+// multimodular mode does; items of the raw kind write P itself.
 
-constexpr int CG_STAGES = 3;
-constexpr int CG_STAGE_BYTES = 4 * TG_TILE_BYTES;  // A0, A1, B0, B1
+constexpr int CG_STAGES = 4;
+constexpr int CG_BN = 64;                              // output columns per item
+constexpr int CG_B_TILE = CG_BN * TG_BK * 2;           // 8 KiB: one B digit plane of a k-block
+constexpr int CG_STAGE_BYTES = 2 * TG_TILE_BYTES + 2 * CG_B_TILE;  // A0, A1, B0, B1
 constexpr size_t CG_SMEM_BYTES = 1024 + (size_t)CG_STAGES * CG_STAGE_BYTES + 256;
-constexpr int CG_TMEM_COLS = 512;
+constexpr int CG_ACC_COLS = 4 * CG_BN;                 // one accumulator: four quarters
+constexpr int CG_TMEM_COLS = 2 * CG_ACC_COLS;
 constexpr int CG_MAX_KP = 1024;
-constexpr int CG_EPI_WARPS = 16;  // 4 lane quadrants x 4 column quarters
+constexpr int CG_EPI_WARPS = 16;  // 4 lane quadrants x 4 groups of 16 columns
 constexpr int CG_THREADS = 32 * (2 + CG_EPI_WARPS);
 
 struct CgShared {
   uint64_t full[CG_STAGES];
   uint64_t empty[CG_STAGES];
-  uint64_t accf, acce, done;
+  uint64_t accf[2], acce[2], done;
   uint32_t tmem_base;
   int abort;
 };
@@ -305,7 +310,8 @@ __global__ void __launch_bounds__(CG_THREADS, 1)
   const int warp = threadIdx.x >> 5;
   const int lane = threadIdx.x & 31;
   // persistent: work item w = (modulus w / ntiles, output tile w % ntiles), a grid stride apart
-  const int ntiles = P.tiles_m * P.tiles_n;
+  const int tiles_n = (int)(P.Np / CG_BN);
+  const int ntiles = P.tiles_m * tiles_n;
   const int nitems = ntiles * P.batch;
   const int nkb = P.Kp / TG_BK;
 
@@ -314,8 +320,10 @@ __global__ void __launch_bounds__(CG_THREADS, 1)
       mbar_init(&sh->full[s], 1);
       mbar_init(&sh->empty[s], 1);
     }
-    mbar_init(&sh->accf, 1);
-    mbar_init(&sh->acce, CG_EPI_WARPS);
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&sh->accf[b], 1);
+      mbar_init(&sh->acce[b], CG_EPI_WARPS);
+    }
     mbar_init(&sh->done, 1);
     sh->abort = 0;
     fence_mbar_init();
@@ -344,7 +352,7 @@ __global__ void __launch_bounds__(CG_THREADS, 1)
       bool ok = true;
       for (int w = blockIdx.x; w < nitems && ok; w += gridDim.x) {
         const int bi = w / ntiles, tile = w - bi * ntiles;
-        const int m0 = (tile / P.tiles_n) * TG_BM, n0 = (tile % P.tiles_n) * TG_BN;
+        const int m0 = (tile / tiles_n) * TG_BM, n0 = (tile % tiles_n) * CG_BN;
         for (int kb = 0; kb < nkb; ++kb, ++it) {
           const int s = it % CG_STAGES;
           if (!mbar_wait(&sh->empty[s], ((it / CG_STAGES) & 1) ^ 1, abort)) {
@@ -357,7 +365,8 @@ __global__ void __launch_bounds__(CG_THREADS, 1)
           tma_load_3d(st, &tmA, &sh->full[s], kb * TG_BK, m0, 2 * bi);
           tma_load_3d(st + TG_TILE_BYTES, &tmA, &sh->full[s], kb * TG_BK, m0, 2 * bi + 1);
           tma_load_3d(st + 2 * TG_TILE_BYTES, &tmB, &sh->full[s], kb * TG_BK, n0, 2 * bi);
-          tma_load_3d(st + 3 * TG_TILE_BYTES, &tmB, &sh->full[s], kb * TG_BK, n0, 2 * bi + 1);
+          tma_load_3d(st + 2 * TG_TILE_BYTES + CG_B_TILE, &tmB, &sh->full[s], kb * TG_BK, n0,
+                      2 * bi + 1);
         }
       }
       // before leaving, let every load this thread issued land (bounded)
@@ -368,16 +377,18 @@ __global__ void __launch_bounds__(CG_THREADS, 1)
   } else if (warp == 1) {
     // ------------------------------------------------------------ MMA issuer
     if (lane == 0) {
-      const uint32_t idesc = idesc_bf16_f32(TG_BM, 2 * TG_BN);
+      const uint32_t idesc = idesc_bf16_f32(TG_BM, 2 * CG_BN);
       uint32_t it = 0;
       bool ok = true;
       for (int w = blockIdx.x, ii = 0; w < nitems && ok; w += gridDim.x, ++ii) {
-        // the drain must have read the previous item's accumulators
-        if (!mbar_wait(&sh->acce, (ii & 1) ^ 1, abort)) {
+        const int b = ii & 1;
+        // the drain must have read this accumulator's previous item
+        if (!mbar_wait(&sh->acce[b], ((ii >> 1) & 1) ^ 1, abort)) {
           give_up();
           break;
         }
         tc_fence_after();
+        const uint32_t acc_cols = tmem + (uint32_t)(b * CG_ACC_COLS);
         for (int kb = 0; kb < nkb; ++kb, ++it) {
           const int s = it % CG_STAGES;
           if (!mbar_wait(&sh->full[s], (it / CG_STAGES) & 1, abort)) {
@@ -389,62 +400,63 @@ __global__ void __launch_bounds__(CG_THREADS, 1)
           uint8_t *st = stages + (size_t)s * CG_STAGE_BYTES;
           const uint64_t a0 = sw128_desc(smem_u32(st));
           const uint64_t a1 = sw128_desc(smem_u32(st + TG_TILE_BYTES));
-          const uint64_t b = sw128_desc(smem_u32(st + 2 * TG_TILE_BYTES));
+          const uint64_t bd = sw128_desc(smem_u32(st + 2 * TG_TILE_BYTES));
 #pragma unroll
           for (int kk = 0; kk < TG_BK / 16; ++kk) {
             const uint32_t acc = (kb > 0 || kk > 0) ? 1u : 0u;
-            umma_bf16(tmem, a0 + 2 * kk, b + 2 * kk, idesc, acc);              // A0 B0 | A0 B1
-            umma_bf16(tmem + 2 * TG_BN, a1 + 2 * kk, b + 2 * kk, idesc, acc);  // A1 B0 | A1 B1
+            umma_bf16(acc_cols, a0 + 2 * kk, bd + 2 * kk, idesc, acc);               // A0 B0 | A0 B1
+            umma_bf16(acc_cols + 2 * CG_BN, a1 + 2 * kk, bd + 2 * kk, idesc, acc);   // A1 B0 | A1 B1
           }
           umma_commit(&sh->empty[s]);
         }
-        if (ok) umma_commit(&sh->accf);
+        if (ok) umma_commit(&sh->accf[b]);
       }
       umma_commit(&sh->done);
       mbar_wait(&sh->done, 0, abort);
     }
   } else {
     // ------------------------------------------------------------ drain: P mod m per entry
-    const int q = warp & 3;                   // TMEM lane quadrant this warp may access
-    const int col0 = 32 * ((warp - 2) >> 2);  // its 32 of the tile's 128 columns
+    const int q = warp & 3;                           // TMEM lane quadrant this warp may access
+    const int col0 = 16 * ((warp - 2) >> 2);          // its 16 of the item's 64 columns
     const int row = 32 * q + lane;
     const uint32_t lane_addr = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)col0;
     for (int w = blockIdx.x, ii = 0; w < nitems; w += gridDim.x, ++ii) {
       const int bi = w / ntiles, tile = w - bi * ntiles;
-      const int64_t gm = (tile / P.tiles_n) * TG_BM + row;
-      const int64_t gcol = (tile % P.tiles_n) * TG_BN + col0;
-      const bool got = __all_sync(0xffffffffu, mbar_wait(&sh->accf, ii & 1, abort));
+      const int b = ii & 1;
+      const int64_t gm = (tile / tiles_n) * TG_BM + row;
+      const int64_t gcol = (tile % tiles_n) * CG_BN + col0;
+      const bool got = __all_sync(0xffffffffu, mbar_wait(&sh->accf[b], (ii >> 1) & 1, abort));
       if (!got) {
         if (lane == 0) give_up();
         break;
       }
       tc_fence_after();
       // P = D0 + 2^8 (D1a + D1b) + 2^16 D2 from the quarters A0 B0 | A0 B1 | A1 B0 | A1 B1
-      int64_t Pc[32];
-#pragma unroll
-      for (int h = 0; h < 2; ++h) {
+      const uint32_t base = lane_addr + (uint32_t)(b * CG_ACC_COLS);
+      int64_t Pc[16];
+      {
         uint32_t v0[16], v1[16], v2[16], v3[16];
-        tmem_ld16(lane_addr + 16 * h, v0);
-        tmem_ld16(lane_addr + TG_BN + 16 * h, v1);
-        tmem_ld16(lane_addr + 2 * TG_BN + 16 * h, v2);
-        tmem_ld16(lane_addr + 3 * TG_BN + 16 * h, v3);
+        tmem_ld16(base, v0);
+        tmem_ld16(base + CG_BN, v1);
+        tmem_ld16(base + 2 * CG_BN, v2);
+        tmem_ld16(base + 3 * CG_BN, v3);
         tmem_wait_ld();
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&sh->acce[b]);
 #pragma unroll
         for (int c = 0; c < 16; ++c) {
           const int64_t d1 = (int64_t)__float2int_rn(__uint_as_float(v1[c])) +
                              __float2int_rn(__uint_as_float(v2[c]));
-          Pc[16 * h + c] = (int64_t)__float2int_rn(__uint_as_float(v0[c])) + d1 * 256 +
-                           (int64_t)__float2int_rn(__uint_as_float(v3[c])) * 65536;
+          Pc[c] = (int64_t)__float2int_rn(__uint_as_float(v0[c])) + d1 * 256 +
+                  (int64_t)__float2int_rn(__uint_as_float(v3[c])) * 65536;
         }
       }
-      tc_fence_before();
-      __syncwarp();
-      if (lane == 0) mbar_arrive(&sh->acce);
       if (bi >= P.nz) {  // a raw item: P itself
         longlong2 *rdst =
             (longlong2 *)(P.zraw + ((int64_t)(bi - P.nz) * P.Mp + gm) * P.Np + gcol);
 #pragma unroll
-        for (int c = 0; c < 16; ++c) rdst[c] = make_longlong2(Pc[2 * c], Pc[2 * c + 1]);
+        for (int c = 0; c < 8; ++c) rdst[c] = make_longlong2(Pc[2 * c], Pc[2 * c + 1]);
         continue;
       }
       // |P| <= Kp (m / 2)^2 < 2^50, so P + m 2^35 is in (0, 2^52)
@@ -452,7 +464,7 @@ __global__ void __launch_bounds__(CG_THREADS, 1)
       const uint64_t i64 = __ldg(P.zinv + bi);
       uint4 *zdst = (uint4 *)(P.zout + ((int64_t)bi * P.Mp + gm) * P.Np + gcol);
 #pragma unroll
-      for (int c8 = 0; c8 < 4; ++c8) {
+      for (int c8 = 0; c8 < 2; ++c8) {
         uint32_t zz[4];
 #pragma unroll
         for (int u = 0; u < 8; ++u) {
@@ -499,14 +511,14 @@ static PFN_tmapEncodeTiled encode_fn() {
   return fn;
 }
 
-// 3-D map over digit planes [planes][rows][Kp] of BF16, box = 64 (k) x 128 (rows) x 1 plane.
+// 3-D map over digit planes [planes][rows][Kp] of BF16, box = 64 (k) x box_rows x 1 plane.
 static bool make_plane_map(CUtensorMap *tm, const void *base, int64_t Kp, int64_t rows,
-                           int64_t planes) {
+                           int64_t planes, int box_rows = TG_BM) {
   PFN_tmapEncodeTiled enc = encode_fn();
   if (!enc) return false;
   cuuint64_t dims[3] = {(cuuint64_t)Kp, (cuuint64_t)rows, (cuuint64_t)planes};
   cuuint64_t strides[2] = {(cuuint64_t)(Kp * 2), (cuuint64_t)(Kp * 2 * rows)};
-  cuuint32_t box[3] = {(cuuint32_t)TG_BK, (cuuint32_t)TG_BM, 1};
+  cuuint32_t box[3] = {(cuuint32_t)TG_BK, (cuuint32_t)box_rows, 1};
   cuuint32_t estr[3] = {1, 1, 1};
   CUresult r = enc(tm, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void *>(base), dims, strides,
                    box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
@@ -656,7 +668,9 @@ arbgpu_status launch_digit_gemm(arbgpu_ctx *ctx, const DigitGemmArgs &a, cudaStr
     if (grid > 0x7fffffff) return ARBGPU_ERR_LIMIT;
     LaunchScope scope(ctx, stream, a.name ? a.name : "crt_gemm",
                       (int64_t)(a.SA) * a.SB * (int64_t)a.M * a.N * a.Kp * P.batch);
-    const int64_t items = (int64_t)P.tiles_m * P.tiles_n * P.batch;
+    if (!make_plane_map(&tmB, a.B, a.Kp, a.N, (int64_t)a.SB * P.batch, CG_BN))
+      return ARBGPU_ERR_CUDA;
+    const int64_t items = (int64_t)P.tiles_m * (P.Np / CG_BN) * P.batch;
     const int64_t cgrid = items < ctx->sm_count ? items : ctx->sm_count;
     launch_pdl(crt_gemm_kernel, dim3((unsigned)cgrid), dim3(CG_THREADS), CG_SMEM_BYTES, stream,
                tmA, tmB, P);
