@@ -168,6 +168,12 @@ def roofline_of(name, k, peaks, sm_mhz, limb_n=None):
 
 DOT_KERNELS = ("dot_setup", "dot_eval", "dot_fused")
 
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the headline workload's
+# kernels (N = 512, p = 256), from the ncu capture summarised in
+# profiles/multimodular_n512_p256_full.md; valid only for that workload and those kernels.
+TRAFFIC_N512_P256 = {"crt_gemm": 88.21e6, "block_round": 24.29e6, "residues_a": 14.77e6,
+                     "residues_b": 15.30e6}
+
 
 def dot_work(terms_by_n, unique_bytes=None):
     """Algorithmic work of a dot-path call: terms_by_n maps limbs read per factor (n) to the number
@@ -614,13 +620,13 @@ def main():
         read-back."""
         n = case.N
         nl = (prec + 63) // 64
-        Ad = [arb.Balls.from_raw(case.A[0], device=dev) for _ in range(2)]
-        Bd = [arb.Balls.from_raw(case.B[0], device=dev) for _ in range(2)]
-        Cd = [arb.Balls.empty(case.M * n, nl, device=dev) for _ in range(2)]
-        hA = arb.Balls.from_raw(case.A[0], pin=True)
-        hB = arb.Balls.from_raw(case.B[0], pin=True)
-        hC = [arb.Balls(*(torch.empty_like(t, device="cpu").pin_memory() for t in Cd[0].tensors()))
-              for _ in range(2)]
+        # every ball array is one packed buffer, so each moves in one copy
+        Ad = [arb.Balls.from_raw(case.A[0], device=dev, packed=True) for _ in range(2)]
+        Bd = [arb.Balls.from_raw(case.B[0], device=dev, packed=True) for _ in range(2)]
+        Cd = [arb.Balls.packed(case.M * n, nl, device=dev) for _ in range(2)]
+        hA = arb.Balls.from_raw(case.A[0], pin=True, packed=True)
+        hB = arb.Balls.from_raw(case.B[0], pin=True, packed=True)
+        hC = [arb.Balls.packed(case.M * n, nl, pin=True) for _ in range(2)]
         need = arb.mat_mul_workspace_size(case.M, case.K, n, prec, Ad[0].nlimbs, Bd[0].nlimbs,
                                           False, alg)
         ws = torch.empty(max(need, 1), dtype=torch.uint8, device=dev)
@@ -668,7 +674,8 @@ def main():
         if world > 1:
             dist.barrier()
         ctx.check()
-        return t0.elapsed_time(t1), hA.nbytes() + hB.nbytes(), hC[0].nbytes()
+        return (t0.elapsed_time(t1), hA.buffer.numel() + hB.buffer.numel(),
+                hC[0].buffer.numel())
 
     prec = args.prec
     alg = algs[args.alg]
@@ -708,6 +715,11 @@ def main():
                 tensor = roofline_of(tn, kernels[tn], peaks, sm_mhz)
                 tensor["share_of_step"] = kernels[tn]["share"]
                 break
+        if args.n == N_DEFAULT and prec == 256 and args.alg == "auto":
+            for r in (roofline, tensor):
+                if r and r.get("kernel") in TRAFFIC_N512_P256:
+                    r["traffic"] = TRAFFIC_N512_P256[r["kernel"]]
+                    r["traffic_source"] = "ncu capture, profiles/multimodular_n512_p256_full.md"
 
     compare = {}
     if not args.no_compare and args.n == N_DEFAULT:
@@ -738,8 +750,9 @@ def main():
                            "parallelism": f"replicas x{world}"},
                 "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
                         "d2h_bytes_per_step": d2h,
-                        "how": "every step copies A, B from pinned host memory and reads C back; "
-                               "steps pipelined over 3 streams x 2 buffers, no L2 flush"},
+                        "how": "every step copies A, B from pinned host memory and reads C back "
+                               "(one packed buffer per ball array); steps pipelined over 3 "
+                               "streams x 2 buffers, no L2 flush"},
                 "gpu_launches": launches, "roofline": roofline, "tensor_core": tensor,
                 "kernels": kernels,
                 "cpu_baseline": cpu,

@@ -40,8 +40,40 @@ class Balls:
                      torch.zeros(count, dtype=torch.int64, device=device))
 
     @staticmethod
-    def from_raw(raw, device="cuda", pin=False):
-        """Copy a host ball array (numpy fields: limbs, exp, flags, rad_man, rad_exp)."""
+    def packed(count, nlimbs, device="cuda", pin=False):
+        """Zero balls whose five arrays are 256-byte aligned parts of one buffer (``buffer``), so
+        that the whole array moves between host and device memory in one copy.  ``pin``: pinned
+        host memory instead of ``device``."""
+        sizes = [8 * nlimbs * count, 8 * count, 4 * count, 4 * count, 8 * count]
+        offs, o = [], 0
+        for sz in sizes:
+            offs.append(o)
+            o += (sz + 255) // 256 * 256
+        buf = torch.zeros(max(o, 1), dtype=torch.uint8, device="cpu" if pin else device)
+        if pin:
+            buf = buf.pin_memory()
+
+        def part(i, dt, shape):
+            return buf[offs[i]:offs[i] + sizes[i]].view(dt).view(shape)
+        b = Balls(part(0, torch.int64, (nlimbs, count)), part(1, torch.int64, (count,)),
+                  part(2, torch.int32, (count,)), part(3, torch.int32, (count,)),
+                  part(4, torch.int64, (count,)))
+        b.buffer = buf
+        return b
+
+    @staticmethod
+    def from_raw(raw, device="cuda", pin=False, packed=False):
+        """Copy a host ball array (numpy fields: limbs, exp, flags, rad_man, rad_exp); with
+        ``packed``, into one buffer as ``Balls.packed`` lays it out."""
+        if packed:
+            limbs = np.ascontiguousarray(raw.limbs)
+            b = Balls.packed(int(np.asarray(raw.exp).shape[0]), int(limbs.shape[0]), device, pin)
+            for dst, a, dt in ((b.limbs, limbs, np.int64), (b.exp, raw.exp, np.int64),
+                               (b.flags, raw.flags, np.int32), (b.rad_man, raw.rad_man, np.int32),
+                               (b.rad_exp, raw.rad_exp, np.int64)):
+                dst.copy_(torch.from_numpy(np.ascontiguousarray(a).view(dt)))
+            return b
+
         def t(a, dt):
             x = torch.from_numpy(np.ascontiguousarray(a).view(dt))
             return x.pin_memory() if pin else x.to(device)
@@ -55,6 +87,10 @@ class Balls:
                 self.rad_exp.cpu().numpy())
 
     def copy_from_(self, other, non_blocking=False):
+        mine, theirs = getattr(self, "buffer", None), getattr(other, "buffer", None)
+        if mine is not None and theirs is not None and mine.numel() == theirs.numel():
+            mine.copy_(theirs, non_blocking=non_blocking)  # one copy of the packed buffer
+            return self
         for a, b in ((self.limbs, other.limbs), (self.exp, other.exp), (self.flags, other.flags),
                      (self.rad_man, other.rad_man), (self.rad_exp, other.rad_exp)):
             a.copy_(b, non_blocking=non_blocking)
