@@ -156,6 +156,7 @@ arbgpu_status arbgpu_destroy(arbgpu_ctx *ctx) {
   }
   for (auto e : ctx->event_pool) cudaEventDestroy(e);
   for (auto &t : ctx->crt_tables) cudaFree(t.second);
+  if (ctx->mapped) cudaFreeHost(ctx->mapped);
   cudaFree(ctx->status);
   delete ctx;
   return ARBGPU_OK;
@@ -412,10 +413,8 @@ arbgpu_status arbgpu_mat_mul_batched(arbgpu_ctx *ctx, const arbgpu_matmul_desc *
         return st;
     }
     std::vector<BlockStats> hstats(4 * nb);
-    if (cudaMemcpyAsync(hstats.data(), dstats, sizeof(BlockStats) * 4 * nb,
-                        cudaMemcpyDeviceToHost, s) != cudaSuccess ||
-        cudaStreamSynchronize(s) != cudaSuccess)
-      return ARBGPU_ERR_CUDA;
+    st = read_stats(ctx, dstats, hstats.data(), 4 * nb, s);
+    if (st != ARBGPU_OK) return st;
     for (size_t i = 0; i < nb; ++i) {
       const arbgpu_matmul_desc &d = descs[block_items[i]];
       bool used = false;

@@ -2958,6 +2958,34 @@ arbgpu_status block_finish(arbgpu_ctx *ctx, const arbgpu_balls *C, const arbgpu_
 // scans, one read-back of their statistics, then the products.  Returns ARBGPU_ERR_LIMIT when the
 // inputs hold special values or exceed the path's limits (the caller then uses the classical
 // algorithm).
+__global__ void words_to_mapped_kernel(const uint32_t *src, uint32_t *dst, int words) {
+  for (int q = threadIdx.x; q < words; q += blockDim.x) dst[q] = src[q];
+}
+
+arbgpu_status read_stats(arbgpu_ctx *ctx, const BlockStats *dev, BlockStats *host, size_t n,
+                         cudaStream_t s) {
+  const size_t bytes = n * sizeof(BlockStats);
+  if (bytes > ctx->mapped_bytes) {
+    if (ctx->mapped) cudaFreeHost(ctx->mapped);
+    ctx->mapped = ctx->mapped_dev = nullptr;
+    ctx->mapped_bytes = 0;
+    const size_t want = bytes < 4096 ? 4096 : bytes;
+    if (cudaHostAlloc(&ctx->mapped, want, cudaHostAllocMapped) != cudaSuccess ||
+        cudaHostGetDevicePointer(&ctx->mapped_dev, ctx->mapped, 0) != cudaSuccess)
+      return ARBGPU_ERR_CUDA;
+    ctx->mapped_bytes = want;
+  }
+  {
+    LaunchScope sc(ctx, s, "stats_read", (int64_t)n);
+    words_to_mapped_kernel<<<1, 256, 0, s>>>((const uint32_t *)dev, (uint32_t *)ctx->mapped_dev,
+                                             (int)(bytes / 4));
+  }
+  if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess)
+    return ARBGPU_ERR_CUDA;
+  memcpy(host, ctx->mapped, bytes);
+  return ARBGPU_OK;
+}
+
 arbgpu_status block_matmul(arbgpu_ctx *ctx, const arbgpu_balls *C, const arbgpu_balls *A,
                            const arbgpu_balls *B, int64_t M, int64_t K, int64_t N, int64_t lda,
                            int64_t ldb, int64_t ldc, int prec, bool cplx, void *workspace,
@@ -2970,10 +2998,8 @@ arbgpu_status block_matmul(arbgpu_ctx *ctx, const arbgpu_balls *C, const arbgpu_
   arbgpu_status st = block_scan_launch(ctx, A, B, M, K, N, lda, ldb, cplx, region, nullptr, s);
   if (st != ARBGPU_OK) return st;
   BlockStats hst[4];
-  if (cudaMemcpyAsync(hst, scan_region_at((uint8_t *)region, M, N, cplx).pst, sizeof(hst),
-                      cudaMemcpyDeviceToHost, s) != cudaSuccess ||
-      cudaStreamSynchronize(s) != cudaSuccess)
-    return ARBGPU_ERR_CUDA;
+  st = read_stats(ctx, scan_region_at((uint8_t *)region, M, N, cplx).pst, hst, 4, s);
+  if (st != ARBGPU_OK) return st;
   return block_finish(ctx, C, A, B, M, K, N, lda, ldb, ldc, prec, cplx, region, hst, workspace,
                       ws_bytes, s, used_block);
 }

@@ -26,6 +26,10 @@ struct arbgpu_ctx {
   bool trace;
   std::vector<arbgpu_trace_rec> recs;
   std::vector<cudaEvent_t> event_pool;
+  // mapped pinned host memory (and its device address) for small device-to-host reads
+  void *mapped = nullptr;
+  void *mapped_dev = nullptr;
+  size_t mapped_bytes = 0;
 };
 
 namespace arbgpu {
@@ -102,6 +106,12 @@ struct BlockStats {
   int32_t radA, radB;     // a nonzero radius seen
   int32_t pad;
 };
+
+// Copy n BlockStats from device memory to `host` and wait for them: a kernel stores them into the
+// context's mapped pinned buffer (no copy engine, so the read does not queue behind large copies
+// that other streams have in flight), then the stream is synchronised.
+arbgpu_status read_stats(arbgpu_ctx *ctx, const BlockStats *dev, BlockStats *host, size_t n,
+                         cudaStream_t s);
 
 // The block product in two phases, for callers that run many products: block_scan_launch (scans
 // into a region of block_scan_bytes, no synchronisation; the four BlockStats -- rows of A0, A1,
