@@ -346,3 +346,41 @@ def test_multimodular_long_inner_dimension(arb):
     rng2 = np.random.default_rng(4)
     check_entries(out, A, B, M, K, N, p, [(int(a), int(b)) for a, b in
                                          zip(rng2.integers(0, M, 30), rng2.integers(0, N, 30))], 2)
+
+
+def _balls_of(values, nl):
+    """Raw balls of exact dyadic values (num, exp) with zero radii."""
+    from synth import RawBalls
+    r = RawBalls.zeros(len(values), nl)
+    for q, v in enumerate(values):
+        limbs, e, fl = X.encode_mid(v, nl)
+        for k in range(nl):
+            r.limbs[k, q] = np.uint64(limbs[k])
+        r.exp[q] = e
+        r.flags[q] = fl
+    return r
+
+
+@pytest.mark.parametrize("tail", [1, -1, 0])
+def test_tie_broken_below_the_rounding_window(arb, tail):
+    """Each entry is (2^128 + 1) * 1 + tail * 2^-200 * 2^-200: a tie at p = 128 that only the term
+    2^-400, 529 bits below the top, decides -- below the 6-limb window of |T| that the
+    multimodular epilogue rounds.  The midpoint must be RNE_128 of the exact sum (up, down, or to
+    even without the term) and the ball must contain it."""
+    M, K, N, p = 4, 48, 4, 128
+    nl = 3
+    zero = (0, 0)
+    a = [zero] * (M * K)
+    b = [zero] * (K * N)
+    for i in range(M):
+        a[i * K] = ((1 << 128) + 1, 0)
+        if tail:
+            a[i * K + 1] = (1, -200)
+    for j in range(N):
+        b[j] = (1, 0)
+        if tail:
+            b[N + j] = (tail, -200)
+    A, B = _balls_of(a, nl), _balls_of(b, nl)
+    (out,), names = _run_engine(arb, "crt", A, B, M, K, N, p)
+    assert "crt_gemm" in names
+    check_entries(out, A, B, M, K, N, p, [(i, j) for i in range(M) for j in range(N)], 2)
