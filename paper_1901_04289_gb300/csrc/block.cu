@@ -251,9 +251,7 @@ static int64_t scan_chunk_len(int64_t len, int64_t lines, int64_t target, int64_
   return chunk;
 }
 
-// Whole-range scans, one CTA per line group and no atomics on the line values: a row of A per
-// 256-thread CTA, eight columns of B per 1024-thread CTA (8 columns x 128 k-slices, coalesced
-// along the row).  Each CTA finishes its lines (heights, |B| + R_B exponents) itself.
+// Whole-range scans, one CTA per line group and no atomics on the line values.
 
 struct LineAcc {
   int64_t top, bot, rad, pm;
@@ -291,59 +289,59 @@ __device__ __forceinline__ LineAcc line_shfl_xor(const LineAcc &a, int o) {
   return b;
 }
 
-__global__ void __launch_bounds__(256) scan_rows_full_kernel(const BallsView A, int64_t K,
-                                                             int64_t lda, int64_t *rtop,
-                                                             int64_t *rbot, int64_t *rrad,
-                                                             BlockStats *st) {
-  __shared__ LineAcc s_acc[8];
-  const int64_t i = blockIdx.x;
-  LineAcc a{INT64_MIN, INT64_MAX, INT64_MIN, 0, 0};
-  for (int64_t k = threadIdx.x; k < K; k += blockDim.x) line_fold(a, scan_entry(A, i * lda + k));
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) line_merge(a, line_shfl_xor(a, o));
+// Both whole-range scans in one launch of 1024-thread CTAs: CTAs [0, ceil(M / 4)) take four rows
+// of A (256 threads along each row), the others four columns of B (256 k-slices; a warp reads
+// eight rows of four neighbouring entries, one 32-byte sector each).  Each CTA finishes its lines.
+__global__ void __launch_bounds__(1024) scan_full_kernel(
+    const BallsView A, const BallsView B, int64_t M, int64_t K, int64_t N, int64_t lda,
+    int64_t ldb, int64_t *rtop, int64_t *rbot, int64_t *rrad, BlockStats *st_rows, int64_t *ctop,
+    int64_t *cbot, int64_t *crad, int64_t *cplus, BlockStats *st_cols) {
+  __shared__ LineAcc s_acc[32][4];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  if (lane == 0) s_acc[warp] = a;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) line_merge(a, s_acc[w]);
-    rtop[i] = a.top;
-    rbot[i] = a.bot;
-    rrad[i] = a.rad;
-    if (a.top != INT64_MIN) atomic_max_i64(&st->hA, a.top - a.bot);
-    if (a.pm) atomic_max_i64(&st->pA, a.pm);
-    if (a.flags & 1) atomicOr(&st->special, 1);
-    if (a.flags & 2) atomicOr(&st->radA, 1);
-  }
-}
-
-__global__ void __launch_bounds__(1024) scan_cols_full_kernel(const BallsView B, int64_t K,
-                                                              int64_t N, int64_t ldb,
-                                                              int64_t *ctop, int64_t *cbot,
-                                                              int64_t *crad, int64_t *cplus,
-                                                              BlockStats *st) {
-  __shared__ LineAcc s_acc[32][8];
-  const int tx = threadIdx.x & 7, ty = threadIdx.x >> 3;  // column of the group, k-slice
-  const int64_t j = (int64_t)blockIdx.x * 8 + tx;
+  const int64_t row_ctas = (M + 3) / 4;
   LineAcc a{INT64_MIN, INT64_MAX, INT64_MIN, 0, 0};
+  if ((int64_t)blockIdx.x < row_ctas) {
+    const int r = threadIdx.x >> 8, tk = threadIdx.x & 255;  // row of the group, k-slice
+    const int64_t i = (int64_t)blockIdx.x * 4 + r;
+    if (i < M)
+      for (int64_t k = tk; k < K; k += 256) line_fold(a, scan_entry(A, i * lda + k));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) line_merge(a, line_shfl_xor(a, o));
+    if (lane == 0) s_acc[warp][0] = a;
+    __syncthreads();
+    if (tk == 0 && i < M) {  // warps 8r .. 8r + 7 hold row r
+      for (int w = 1; w < 8; ++w) line_merge(a, s_acc[8 * r + w][0]);
+      rtop[i] = a.top;
+      rbot[i] = a.bot;
+      rrad[i] = a.rad;
+      if (a.top != INT64_MIN) atomic_max_i64(&st_rows->hA, a.top - a.bot);
+      if (a.pm) atomic_max_i64(&st_rows->pA, a.pm);
+      if (a.flags & 1) atomicOr(&st_rows->special, 1);
+      if (a.flags & 2) atomicOr(&st_rows->radA, 1);
+    }
+    return;
+  }
+  const int tx = threadIdx.x & 3, ty = threadIdx.x >> 2;  // column of the group, k-slice
+  const int64_t j = ((int64_t)blockIdx.x - row_ctas) * 4 + tx;
   if (j < N)
-    for (int64_t k = ty; k < K; k += 128) line_fold(a, scan_entry(B, k * ldb + j));
-  // lanes 8 apart hold the same column
+    for (int64_t k = ty; k < K; k += 256) line_fold(a, scan_entry(B, k * ldb + j));
+  // lanes 4 apart hold the same column
+  line_merge(a, line_shfl_xor(a, 4));
   line_merge(a, line_shfl_xor(a, 8));
   line_merge(a, line_shfl_xor(a, 16));
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  if (lane < 8) s_acc[warp][lane] = a;
+  if (lane < 4) s_acc[warp][lane] = a;
   __syncthreads();
-  if (threadIdx.x < 8 && j < N) {
+  if (threadIdx.x < 4 && j < N) {
     for (int w = 1; w < 32; ++w) line_merge(a, s_acc[w][tx]);
     ctop[j] = a.top;
     cbot[j] = a.bot;
     crad[j] = a.rad;
     const int64_t mx = a.top > a.rad ? a.top : a.rad;  // |b| + r_b < 2^(max(top, rexp) + 1)
     cplus[j] = mx == INT64_MIN ? INT64_MIN : mx + 1;
-    if (a.top != INT64_MIN) atomic_max_i64(&st->hB, a.top - a.bot);
-    if (a.pm) atomic_max_i64(&st->pB, a.pm);
-    if (a.flags & 1) atomicOr(&st->special, 1);
-    if (a.flags & 2) atomicOr(&st->radB, 1);
+    if (a.top != INT64_MIN) atomic_max_i64(&st_cols->hB, a.top - a.bot);
+    if (a.pm) atomic_max_i64(&st_cols->pB, a.pm);
+    if (a.flags & 1) atomicOr(&st_cols->special, 1);
+    if (a.flags & 2) atomicOr(&st_cols->radB, 1);
   }
 }
 
@@ -2798,17 +2796,10 @@ arbgpu_status block_scan_launch(arbgpu_ctx *ctx, const arbgpu_balls *A, const ar
   else if (cudaMemsetAsync(sr.pst, 0, sizeof(BlockStats) * 4, s) != cudaSuccess)
     return ARBGPU_ERR_CUDA;
   for (int q = 0; q < (cplx ? 2 : 1); ++q) {
-    {
-      LaunchScope sc(ctx, s, "scan_rows", M * K);
-      scan_rows_full_kernel<<<(unsigned)M, 256, 0, s>>>(view_of(A[q]), K, lda, sr.rtop[q],
-                                                        sr.rbot[q], sr.rrad[q], sr.pst + q);
-    }
-    {
-      LaunchScope sc(ctx, s, "scan_cols", K * N);
-      scan_cols_full_kernel<<<(unsigned)((N + 7) / 8), 1024, 0, s>>>(
-          view_of(B[q]), K, N, ldb, sr.ctop[q], sr.cbot[q], sr.crad[q], sr.cplus[q],
-          sr.pst + 2 + q);
-    }
+    LaunchScope sc(ctx, s, "scans", M * K + K * N);
+    scan_full_kernel<<<(unsigned)((M + 3) / 4 + (N + 3) / 4), 1024, 0, s>>>(
+        view_of(A[q]), view_of(B[q]), M, K, N, lda, ldb, sr.rtop[q], sr.rbot[q], sr.rrad[q],
+        sr.pst + q, sr.ctop[q], sr.cbot[q], sr.crad[q], sr.cplus[q], sr.pst + 2 + q);
     if (cudaGetLastError() != cudaSuccess) return ARBGPU_ERR_CUDA;
   }
   return ARBGPU_OK;
