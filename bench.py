@@ -155,7 +155,7 @@ def roofline_of(name, k, peaks, sm_mhz, limb_n=None):
                 "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
                 "note": "exact BF16 digit products (1 digit MAC = 2 flops) vs the measured "
                         "dense BF16 burst peak (no INT8 tcgen05 on sm_103a)"}
-    if name in ("block_round", "residues_a", "residues_b"):
+    if name in ("block_round", "residues", "residues_a", "residues_b"):
         achieved = units / avg_s / 1e12
         return {"bound": "alu", "kernel": name, "achieved": achieved, "peak": alu_peak,
                 "unit": "T int32-mul/s", "frac": achieved / alu_peak, "traffic": None,
@@ -171,8 +171,7 @@ DOT_KERNELS = ("dot_setup", "dot_eval", "dot_fused")
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the headline workload's
 # kernels (N = 512, p = 256), from the ncu capture summarised in
 # profiles/multimodular_n512_p256_full.md; valid only for that workload and those kernels.
-TRAFFIC_N512_P256 = {"crt_gemm": 88.21e6, "block_round": 24.29e6, "residues_a": 14.77e6,
-                     "residues_b": 15.30e6}
+TRAFFIC_N512_P256 = {"crt_gemm": 88.21e6, "block_round": 24.29e6}
 
 
 def dot_work(terms_by_n, unique_bytes=None):

@@ -911,36 +911,155 @@ __device__ __forceinline__ uint32_t bf16x2_bits(float lo, float hi) {
   return *(const uint32_t *)&p;
 }
 
-struct RtArgs {
+// One operand of the residue step: A (rows of A, tiles of 2 rows x 64 inner positions) or B
+// (columns of B, tiles of 4 columns x 32 inner positions).
+struct RtSide {
   BallsView X;
-  bool is_b;
-  int64_t rows, k0, K, Kp, ld;
-  const int64_t *bot;  // scan: per-row lowest exponent
+  int64_t rows, ld;
+  const int64_t *bot;    // scan: per-line lowest exponent
+  const int64_t *top, *radtop, *plustop;  // the radius windows' exponents (plustop: B only)
+  SplitOut ro;           // radius operands written directly (when not part of the staged planes)
+  const uint16_t *wtab;  // [NPAD][128] BF16 weight table of this operand
+};
+
+struct RtArgs {
+  RtSide side[2];  // 0: A, 1: B
+  int64_t k0, K, Kp;
   int NM, NPAD, NS, ND, wg_cols, NPL;  // NPL: staged planes per tile (2 NM, plus 4 radius planes)
   uint32_t tcols;
-  const uint16_t *wtab;  // [NPAD][128] BF16 weight table of this operand
-  const float *rinv;     // [NM] 1 / m_t
-  SplitOut ro;           // radius operands written directly (when not part of the staged planes)
-  const int64_t *top, *radtop, *plustop;
+  const float *rinv;  // [NM] 1 / m_t
   int *status;
 };
 
-// Tile = JT operand rows x KT inner positions.  The producer thread pt reads the entry (pj, pk)
-// and fills tile row pj * KT + pk; the drain thread t reads TMEM lane t, i.e. the entry
-// (t / KT, t % KT), and stages its residues at [plane][t], which is the layout of the TMA
-// store's box {KT, JT, planes}.
+template <bool IS_B>
+struct RtGeom {
+  static constexpr int JT = IS_B ? 4 : 2;  // operand lines per tile
+  static constexpr int KT = RT_ROWS / JT;  // inner positions per tile (a divisor of Kp)
+  // producer thread pt's entry (pj, pk): for B, the four threads of a 32-byte sector of a row of
+  // B take consecutive columns, and the eight threads of a quarter warp fill tile rows with
+  // distinct (row mod 8), so their swizzled 16-byte stores hit distinct banks
+  __device__ static int pj(int pt) { return IS_B ? ((pt >> 3) & 3) : (pt >> 6); }
+  __device__ static int pk(int pt) { return IS_B ? ((pt & 7) + 8 * (pt >> 5)) : (pt & 63); }
+};
+
+// Stage the raw fields of producer thread pt's entry of tile (tr, tk) of one side into `slot`.
 template <int NCH, bool IS_B>
+__device__ __forceinline__ void rt_prefetch(const RtArgs &a, const RtSide &sd, uint64_t *slot,
+                                            int pt, int tr, int tk, bool want_rad, bool w1,
+                                            bool w2) {
+  using G = RtGeom<IS_B>;
+  constexpr int NLW = rt_top_limbs<NCH>();
+  const int64_t r = (int64_t)tr * G::JT + G::pj(pt), k = (int64_t)tk * G::KT + G::pk(pt);
+  if (r >= sd.rows || k >= a.K) return;
+  const BallsView &X = sd.X;
+  const int lbase = X.nlimbs - NLW;
+  const int64_t e = IS_B ? ((a.k0 + k) * sd.ld + r) : (r * sd.ld + a.k0 + k);
+  cp_async(slot, X.exp + e, 8);
+  cp_async(slot + 1, sd.bot + r, 8);
+  cp_async(slot + 2, X.flags + e, 4);
+  if (want_rad) {
+    cp_async((uint32_t *)(slot + 2) + 1, X.rad_man + e, 4);
+    cp_async(slot + 3, X.rad_exp + e, 8);
+    if (w1) cp_async(slot + 4, (IS_B ? sd.radtop : sd.top) + r, 8);
+    if (w2) cp_async(slot + 5, (IS_B ? sd.plustop : sd.radtop) + r, 8);
+  }
+#pragma unroll
+  for (int i = 0; i < NLW; ++i)
+    if (lbase + i >= 0)
+      cp_async(slot + RT_SLOT_FIXED + i, X.limbs + (int64_t)(lbase + i) * X.stride + e, 8);
+}
+
+// The 32-bit chunks of |X| (scaled), the sign and the radius operands of producer thread pt's
+// entry of tile (tr, tk), from its staged fields.
+template <int NCH, bool IS_B>
+__device__ __forceinline__ void rt_entry(const RtArgs &a, const RtSide &sd, const uint64_t *slot,
+                                         int pt, int tr, int tk, bool want_rad, bool w1, bool w2,
+                                         uint32_t (&ch)[NCH], float &sg, uint32_t &info) {
+  using G = RtGeom<IS_B>;
+  constexpr int NLW = rt_top_limbs<NCH>();
+  const int64_t r = (int64_t)tr * G::JT + G::pj(pt), k = (int64_t)tk * G::KT + G::pk(pt);
+  if (r >= sd.rows || k >= a.K) return;
+  const int nl = sd.X.nlimbs;
+  const int lbase = nl - NLW;  // limb index of the slot's first limb (lower ones are not read)
+  const int jlo = lbase < 0 ? -2 * lbase : 0;  // first 32-bit limb word that exists
+  const uint32_t *Wd = (const uint32_t *)(slot + RT_SLOT_FIXED);
+  const int64_t ex = (int64_t)slot[0];
+  const uint64_t w2f = slot[2];
+  const uint32_t fl = (uint32_t)w2f;
+  Mag absm{0u, 0};
+  if (!(fl & (ARBGPU_FLAG_ZERO | SPECIAL_MASK))) {
+    if (fl & ARBGPU_FLAG_SIGN) sg = -1.0f;
+    // chunk c = bits [32c - sh, 32c - sh + 32) of L: a funnel shift of the slot's words q0 + c
+    // and q0 + c + 1 by b, with 32 q0 + b = -sh - 64 lbase
+    const int64_t p0 = -(ex - 64LL * nl - (int64_t)slot[1]) - 64LL * lbase;
+    if (p0 > -32LL * (NCH + 1) && p0 < 64LL * NLW) {
+      const int q0 = (int)(p0 >> 5), b = (int)(p0 & 31);
+      uint32_t wv[NCH + 1];
+#pragma unroll
+      for (int c = 0; c <= NCH; ++c) {
+        const int j = q0 + c;
+        wv[c] = ((unsigned)(j - jlo) < (unsigned)(2 * NLW - jlo)) ? Wd[j] : 0u;
+      }
+#pragma unroll
+      for (int c = 0; c < NCH; ++c) ch[c] = __funnelshift_r(wv[c], wv[c + 1], b);
+    }
+    if (want_rad) {
+      const uint64_t top = slot[RT_SLOT_FIXED + NLW - 1];  // limb nl - 1
+      uint64_t bm = (top >> 34) + 1;  // 30-bit upper bound of |m| (Section III-E)
+      int64_t ee = ex;
+      if (bm == ((uint64_t)1 << 30)) {
+        bm >>= 1;
+        ee += 1;
+      }
+      absm = Mag{(uint32_t)bm, ee};
+    }
+  }
+  if (want_rad) {
+    const Mag rad{(uint32_t)(w2f >> 32), (int64_t)slot[3]};
+    uint32_t u1 = 0, u2 = 0;
+    const int64_t f1 = (int64_t)slot[4], f2 = (int64_t)slot[5];
+    if (!IS_B) {
+      if (w1) u1 = window_up(absm.man, absm.exp, f1);
+      if (w2) u2 = window_up(rad.man, rad.exp, f2);
+    } else {
+      if (w1) u1 = window_up(rad.man, rad.exp, f1);
+      if (w2) {
+        const Mag plus = mag_add_up(absm, rad);
+        u2 = window_up(plus.man, plus.exp, f2);
+      }
+    }
+    info = u1 | (u2 << 14);
+  }
+}
+
+// Tiles [0, nTA) are those of A, the rest those of B; (side, tile row, tile column) of a tile.
+struct RtTiles {
+  int nTA, ntkA, ntkB;
+  __device__ void locate(int tile, int &side, int &tr, int &tk) const {
+    side = tile >= nTA;
+    const int l = side ? tile - nTA : tile, ntk = side ? ntkB : ntkA;
+    tr = l / ntk;
+    tk = l - tr * ntk;
+  }
+};
+
+// Both operands in one launch (the tiles of A, then those of B).  The producer thread reads the
+// entry (pj, pk) of its side's tile (consecutive threads take consecutive elements of the operand
+// in memory) and fills tile row pj KT + pk; the drain thread t reads TMEM lane t, i.e. the entry
+// (t / KT, t % KT), and stages its residues at [plane][t], the layout of the TMA store's box
+// {KT, JT, planes}.
+template <int NCH>
 __global__ void __launch_bounds__(RT_MAX_THREADS, 1)
-    residue_tc_kernel(const __grid_constant__ CUtensorMap tmo, const __grid_constant__ RtArgs a) {
+    residue_tc_kernel(const __grid_constant__ CUtensorMap tmoA,
+                      const __grid_constant__ CUtensorMap tmoB, const __grid_constant__ RtArgs a) {
   constexpr int KD = (4 * NCH + 63) / 64;  // 64-digit slabs
   constexpr int NLW = rt_top_limbs<NCH>();
   constexpr int SW = RT_SLOT_FIXED + NLW;
-  constexpr int JT = IS_B ? 4 : 2;  // operand rows per tile
-  constexpr int KT = RT_ROWS / JT;  // inner positions per tile (a divisor of Kp)
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   const int NS = a.NS, ND = a.ND, NB = a.ND + 1;
+  const size_t wside = (size_t)KD * a.NPAD * 128;  // one side's weight slabs
   uint8_t *sW = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  uint8_t *sA = sW + (size_t)KD * a.NPAD * 128;
+  uint8_t *sA = sW + 2 * wside;
   uint16_t *sO = (uint16_t *)(sA + (size_t)NS * KD * RT_TILE);
   uint64_t *sSlot = (uint64_t *)(sO + (size_t)ND * a.NPL * RT_ROWS);
   float2 *sMod = (float2 *)(sSlot + (size_t)RT_NP * RT_PD * SW * RT_ROWS);
@@ -964,12 +1083,16 @@ __global__ void __launch_bounds__(RT_MAX_THREADS, 1)
     tmem_alloc(&sh->tmem_base, a.tcols);
     tmem_relinquish();
   }
-  if (threadIdx.x == 32) tma_prefetch_desc(&tmo);
-  // the weight table into K-major slabs of 64 columns with the 128-byte swizzle
-  for (int q = threadIdx.x; q < a.NPAD * 8 * KD; q += blockDim.x) {
-    const int n = q / (8 * KD), c = q - n * 8 * KD;
-    const uint4 v = __ldg((const uint4 *)(a.wtab + (size_t)n * 128) + c);
-    *(uint4 *)(sW + (size_t)(c >> 3) * a.NPAD * 128 + (size_t)n * 128 +
+  if (threadIdx.x == 32) {
+    tma_prefetch_desc(&tmoA);
+    tma_prefetch_desc(&tmoB);
+  }
+  // both weight tables into K-major slabs of 64 columns with the 128-byte swizzle
+  for (int q = threadIdx.x; q < 2 * a.NPAD * 8 * KD; q += blockDim.x) {
+    const int sd = q / (a.NPAD * 8 * KD), qq = q - sd * a.NPAD * 8 * KD;
+    const int n = qq / (8 * KD), c = qq - n * 8 * KD;
+    const uint4 v = __ldg((const uint4 *)(a.side[sd].wtab + (size_t)n * 128) + c);
+    *(uint4 *)(sW + sd * wside + (size_t)(c >> 3) * a.NPAD * 128 + (size_t)n * 128 +
                (((c & 7) ^ (n & 7)) << 4)) = v;
   }
   for (int q = threadIdx.x; q < a.NPAD / 2; q += blockDim.x)
@@ -980,127 +1103,62 @@ __global__ void __launch_bounds__(RT_MAX_THREADS, 1)
   tc_fence_after();
   pdl_wait();  // the operands and scan results come from earlier kernels
 
-  const int ntk = (int)(a.Kp / KT);
-  const int nT = (int)((a.rows + JT - 1) / JT) * ntk;  // the host keeps this below 2^30
+  RtTiles tl;
+  tl.ntkA = (int)(a.Kp / RtGeom<false>::KT);
+  tl.ntkB = (int)(a.Kp / RtGeom<true>::KT);
+  tl.nTA = (int)((a.side[0].rows + 1) / 2) * tl.ntkA;
+  const int nT = tl.nTA + (int)((a.side[1].rows + 3) / 4) * tl.ntkB;  // below 2^30 (host)
   // this CTA's tiles: blockIdx.x + i gridDim.x, i = 0, 1, ...
   const int ntiles = nT > (int)blockIdx.x ? (nT - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
   const bool rad_box = a.NPL > 2 * a.NM;
 
   if (warp >= 4 * ND && warp < mma_warp) {
-    // ------------------------------------------------ producer: digits of 128 entries per tile
+    // ------------------------------------------------ producers: digits of 128 entries per tile
     const int p = (warp - 4 * ND) >> 2, pt = threadIdx.x - 128 * (ND + p);
     uint64_t *pslots = sSlot + (size_t)p * RT_PD * RT_ROWS * SW;
-    // entry (pj, pk): for B, the four threads of a 32-byte sector of a row of B take consecutive
-    // columns j, and the eight threads of a quarter warp fill tile rows with distinct (row mod 8),
-    // so their swizzled 16-byte stores hit distinct banks
-    const int pj = IS_B ? ((pt >> 3) & 3) : (pt >> 6);
-    const int pk = IS_B ? ((pt & 7) + 8 * (pt >> 5)) : (pt & 63);
-    const int prow = pj * KT + pk;
-    const bool want_rad = a.ro.r1 || a.ro.r2 || rad_box;
-    const bool w1 = rad_box || a.ro.r1, w2 = rad_box || a.ro.r2;
-    const int nl = a.X.nlimbs;
-    const int lbase = nl - NLW;  // limb index of the slot's first limb (lower ones are not read)
-    // copies of the entry of this producer's j-th tile (the CTA's tile i = p + j RT_NP) into
-    // slot j mod RT_PD (none outside X); one commit group per call, empty past the last tile
-    // this producer's tiles advance by RT_NP gridDim.x: (tile row, tile column) step by (dtr, dtk)
-    const int jstep = RT_NP * (int)gridDim.x, dtr = jstep / ntk, dtk = jstep - dtr * ntk;
-    auto advance = [&](int &tr, int &tk) {
-      tr += dtr;
-      tk += dtk;
-      if (tk >= ntk) {
-        tk -= ntk;
-        ++tr;
-      }
-    };
-    const int tile0 = (int)blockIdx.x + p * (int)gridDim.x;
-    int ftr = tile0 / ntk, ftk = tile0 - ftr * ntk, fj = 0;  // the next tile to stage
+    bool want[2], w1[2], w2[2];
+#pragma unroll
+    for (int sd = 0; sd < 2; ++sd) {
+      w1[sd] = rad_box || a.side[sd].ro.r1;
+      w2[sd] = rad_box || a.side[sd].ro.r2;
+      want[sd] = w1[sd] || w2[sd];
+    }
+    // staged copies of this producer's j-th tile (the CTA's tile i = p + j RT_NP) into slot
+    // j mod RT_PD; one commit group per call, empty past the last tile
+    int fj = 0;
     auto prefetch = [&]() {
       const int j = fj++;
-      uint64_t *slot = pslots + ((size_t)(j % RT_PD) * RT_ROWS + pt) * SW;
       const int i = p + j * RT_NP;
-      const int64_t r = (int64_t)ftr * JT + pj, k = (int64_t)ftk * KT + pk;
-      advance(ftr, ftk);
-      if (i < ntiles && r < a.rows && k < a.K) {
-        const BallsView &X = a.X;
-        const int64_t e = IS_B ? ((a.k0 + k) * a.ld + r) : (r * a.ld + a.k0 + k);
-        cp_async(slot, X.exp + e, 8);
-        cp_async(slot + 1, a.bot + r, 8);
-        cp_async(slot + 2, X.flags + e, 4);
-        if (want_rad) {
-          cp_async((uint32_t *)(slot + 2) + 1, X.rad_man + e, 4);
-          cp_async(slot + 3, X.rad_exp + e, 8);
-          if (w1) cp_async(slot + 4, (IS_B ? a.radtop : a.top) + r, 8);
-          if (w2) cp_async(slot + 5, (IS_B ? a.plustop : a.radtop) + r, 8);
-        }
-#pragma unroll
-        for (int i = 0; i < NLW; ++i)
-          if (lbase + i >= 0)
-            cp_async(slot + RT_SLOT_FIXED + i, X.limbs + (int64_t)(lbase + i) * X.stride + e, 8);
+      if (i < ntiles) {
+        uint64_t *slot = pslots + ((size_t)(j % RT_PD) * RT_ROWS + pt) * SW;
+        int sd, tr, tk;
+        tl.locate((int)blockIdx.x + i * (int)gridDim.x, sd, tr, tk);
+        if (sd)
+          rt_prefetch<NCH, true>(a, a.side[1], slot, pt, tr, tk, want[1], w1[1], w2[1]);
+        else
+          rt_prefetch<NCH, false>(a, a.side[0], slot, pt, tr, tk, want[0], w1[0], w2[0]);
       }
       cp_async_commit();
     };
-    const int jlo = lbase < 0 ? -2 * lbase : 0;  // first 32-bit limb word that exists
     for (int j = 0; j < RT_PD; ++j) prefetch();
-    int tr = tile0 / ntk, tk = tile0 - tr * ntk;
-    for (int j = 0, i = p; i < ntiles; ++j, i += RT_NP, advance(tr, tk)) {
+    for (int j = 0, i = p; i < ntiles; ++j, i += RT_NP) {
       const uint64_t *slot = pslots + ((size_t)(j % RT_PD) * RT_ROWS + pt) * SW;
-      const uint32_t *Wd = (const uint32_t *)(slot + RT_SLOT_FIXED);  // 32-bit words of the limbs
       const int s = i % NS;
-      const int64_t r = (int64_t)tr * JT + pj, k = (int64_t)tk * KT + pk;
+      int sd, tr, tk;
+      tl.locate((int)blockIdx.x + i * (int)gridDim.x, sd, tr, tk);
       uint32_t ch[NCH];
 #pragma unroll
       for (int c = 0; c < NCH; ++c) ch[c] = 0;
       uint32_t info = 0;
       float sg = 1.0f;
       cp_async_wait_pending<RT_PD - 1>();  // the groups of the later RT_PD - 1 tiles may fly
-      if (r < a.rows && k < a.K) {
-        const int64_t ex = (int64_t)slot[0];
-        const uint64_t w2f = slot[2];
-        const uint32_t fl = (uint32_t)w2f;
-        Mag absm{0u, 0};
-        if (!(fl & (ARBGPU_FLAG_ZERO | SPECIAL_MASK))) {
-          if (fl & ARBGPU_FLAG_SIGN) sg = -1.0f;
-          // chunk c = bits [32c - sh, 32c - sh + 32) of L: a funnel shift of the slot's words
-          // q0 + c and q0 + c + 1 by b, with 32 q0 + b = -sh - 64 lbase
-          const int64_t p0 = -(ex - 64LL * nl - (int64_t)slot[1]) - 64LL * lbase;
-          if (p0 > -32LL * (NCH + 1) && p0 < 64LL * NLW) {
-            const int q0 = (int)(p0 >> 5), b = (int)(p0 & 31);
-            uint32_t wv[NCH + 1];
-#pragma unroll
-            for (int c = 0; c <= NCH; ++c) {
-              const int j = q0 + c;
-              wv[c] = ((unsigned)(j - jlo) < (unsigned)(2 * NLW - jlo)) ? Wd[j] : 0u;
-            }
-#pragma unroll
-            for (int c = 0; c < NCH; ++c) ch[c] = __funnelshift_r(wv[c], wv[c + 1], b);
-          }
-          if (want_rad) {
-            const uint64_t top = slot[RT_SLOT_FIXED + NLW - 1];  // limb nl - 1
-            uint64_t bm = (top >> 34) + 1;  // 30-bit upper bound of |m| (Section III-E)
-            int64_t ee = ex;
-            if (bm == ((uint64_t)1 << 30)) {
-              bm >>= 1;
-              ee += 1;
-            }
-            absm = Mag{(uint32_t)bm, ee};
-          }
-        }
-        if (want_rad) {
-          const Mag rad{(uint32_t)(w2f >> 32), (int64_t)slot[3]};
-          uint32_t u1 = 0, u2 = 0;
-          const int64_t f1 = (int64_t)slot[4], f2 = (int64_t)slot[5];
-          if (!IS_B) {
-            if (w1) u1 = window_up(absm.man, absm.exp, f1);
-            if (w2) u2 = window_up(rad.man, rad.exp, f2);
-          } else {
-            if (w1) u1 = window_up(rad.man, rad.exp, f1);
-            if (w2) {
-              const Mag plus = mag_add_up(absm, rad);
-              u2 = window_up(plus.man, plus.exp, f2);
-            }
-          }
-          info = u1 | (u2 << 14);
-        }
+      int prow;
+      if (sd) {
+        rt_entry<NCH, true>(a, a.side[1], slot, pt, tr, tk, want[1], w1[1], w2[1], ch, sg, info);
+        prow = RtGeom<true>::pj(pt) * RtGeom<true>::KT + RtGeom<true>::pk(pt);
+      } else {
+        rt_entry<NCH, false>(a, a.side[0], slot, pt, tr, tk, want[0], w1[0], w2[0], ch, sg, info);
+        prow = RtGeom<false>::pj(pt) * RtGeom<false>::KT + RtGeom<false>::pk(pt);
       }
       // every slot value is in registers now: stage tile j + RT_PD into the same slot
       prefetch();
@@ -1141,6 +1199,7 @@ __global__ void __launch_bounds__(RT_MAX_THREADS, 1)
       const uint32_t idesc = idesc_bf16_f32(RT_ROWS, a.NPAD);
       for (int i = 0; i < ntiles; ++i) {
         const int s = i % NS, b = i % NB;
+        const int sd = (int)blockIdx.x + i * (int)gridDim.x >= tl.nTA;
         if (!mbar_wait_sleep(&sh->a_full[s], (i / NS) & 1) ||
             !mbar_wait_sleep(&sh->t_empty[b], ((i / NB) & 1) ^ 1)) {
           set_status(a.status, ARBGPU_ERR_TIMEOUT);
@@ -1151,7 +1210,7 @@ __global__ void __launch_bounds__(RT_MAX_THREADS, 1)
 #pragma unroll
         for (int sl = 0; sl < KD; ++sl) {
           const uint64_t ad = sw128_desc(smem_u32(sA + ((size_t)s * KD + sl) * RT_TILE));
-          const uint64_t bd = sw128_desc(smem_u32(sW + (size_t)sl * a.NPAD * 128));
+          const uint64_t bd = sw128_desc(smem_u32(sW + sd * wside + (size_t)sl * a.NPAD * 128));
 #pragma unroll
           for (int kk = 0; kk < 4; ++kk)
             umma_bf16(tm, ad + 2 * kk, bd + 2 * kk, idesc, (sl > 0 || kk > 0) ? 1u : 0u);
@@ -1162,12 +1221,11 @@ __global__ void __launch_bounds__(RT_MAX_THREADS, 1)
   } else {
     // ------------------------------------------------ drain warpgroup d: tiles i = d (mod ND)
     const int d = warp >> 2, t = threadIdx.x & 127, wq = warp & 3;
-    const int dj = t / KT, dk = t % KT;  // the entry of TMEM lane t; dj is the same across a warp
-    const int64_t plane = a.rows * a.Kp;
     uint16_t *so = sO + (size_t)d * a.NPL * RT_ROWS + t;  // plane p of this row at so[p * 128]
     for (int i = d; i < ntiles; i += ND) {
-      const int tile = (int)blockIdx.x + i * (int)gridDim.x;
-      const int tr = tile / ntk, tk = tile - tr * ntk;
+      int sd, tr, tk;
+      tl.locate((int)blockIdx.x + i * (int)gridDim.x, sd, tr, tk);
+      const int JT = sd ? RtGeom<true>::JT : RtGeom<false>::JT, KT = RT_ROWS / JT;
       const int s = i % NS, b = i % NB;
       // (the wait on a_full, complete by then, orders the producer's info writes before the
       // reads below)
@@ -1227,16 +1285,18 @@ __global__ void __launch_bounds__(RT_MAX_THREADS, 1)
           so[(2 * a.NM + 2 * w + 1) * RT_ROWS] = (uint16_t)(bits >> 16);
         }
       } else {
-        const int64_t r = (int64_t)tr * JT + dj, k = (int64_t)tk * KT + dk;
-        if (r < a.rows && (a.ro.r1 || a.ro.r2)) {
-          const int64_t off = r * a.Kp + k;
-          if (a.ro.r1) put_small_digits(info & 0x3FFFu, a.ro.r1 + off, plane);
-          if (a.ro.r2) put_small_digits((info >> 14) & 0x3FFFu, a.ro.r2 + off, plane);
+        const RtSide &side = a.side[sd];
+        const int64_t r = (int64_t)tr * JT + t / KT, k = (int64_t)tk * KT + t % KT;
+        if (r < side.rows && (side.ro.r1 || side.ro.r2)) {
+          const int64_t plane = side.rows * a.Kp, off = r * a.Kp + k;
+          if (side.ro.r1) put_small_digits(info & 0x3FFFu, side.ro.r1 + off, plane);
+          if (side.ro.r2) put_small_digits((info >> 14) & 0x3FFFu, side.ro.r2 + off, plane);
         }
       }
       fence_async_smem();
       named_bar(1 + d, RT_ROWS);
-      if (t == 0) tma_store_3d(&tmo, sO + (size_t)d * a.NPL * RT_ROWS, tk * KT, tr * JT, 0);
+      if (t == 0)
+        tma_store_3d(sd ? &tmoB : &tmoA, sO + (size_t)d * a.NPL * RT_ROWS, tk * KT, tr * JT, 0);
     }
     if (t == 0) tma_store_wait_all();
   }
@@ -1253,13 +1313,13 @@ struct RtLayout {
 };
 
 static size_t residue_tc_smem_for(int KD, int NPAD, int NS, int ND, int NPL, int NM, int SW) {
-  return 1024 + (size_t)KD * NPAD * 128 + (size_t)NS * KD * RT_TILE +
+  return 1024 + (size_t)2 * KD * NPAD * 128 + (size_t)NS * KD * RT_TILE +
          (size_t)ND * NPL * RT_ROWS * 2 + (size_t)RT_NP * RT_PD * SW * RT_ROWS * 8 +
          (size_t)NPAD / 2 * 8 + sizeof(RtShared);
 }
 
-// The kernel's shape for an operand of `nch` 32-bit chunks and NM moduli; false when it does not
-// fit (the CUDA-core residue kernel then runs).
+// The kernel's shape for operands of at most `nch` 32-bit chunks and NM moduli; false when it
+// does not fit (the CUDA-core residue kernel then runs).
 static bool residue_tc_layout(int nch, int NM, bool rad_box, int64_t entries, RtLayout *L) {
   if (nch > 32 || NM > 128 || entries > ((int64_t)1 << 36)) return false;
   L->KD = (4 * nch + 63) / 64;
@@ -1283,9 +1343,10 @@ static bool residue_tc_layout(int nch, int NM, bool rad_box, int64_t entries, Rt
   return false;
 }
 
+// Residues of both operands in one launch; outA / outB: the [NPL][rows][Kp] planes of each side.
 static arbgpu_status launch_residues_tc(arbgpu_ctx *ctx, const RtLayout &L, int nch,
-                                        cudaStream_t s, RtArgs a, __nv_bfloat16 *out) {
-  const int JT = a.is_b ? 4 : 2;  // Kp is a multiple of 64, so KT = 32 or 64 divides it
+                                        cudaStream_t s, RtArgs a, __nv_bfloat16 *outA,
+                                        __nv_bfloat16 *outB) {
   a.NPAD = L.NPAD;
   a.NS = L.NS;
   a.ND = L.ND;
@@ -1294,41 +1355,28 @@ static arbgpu_status launch_residues_tc(arbgpu_ctx *ctx, const RtLayout &L, int 
   a.tcols = 32;  // a power of two covering the ND + 1 accumulators
   while (a.tcols < (uint32_t)((L.ND + 1) * L.wg_cols)) a.tcols *= 2;
   a.status = ctx->status;
-  const int KT = RT_ROWS / JT;
-  const int64_t nT = ((a.rows + JT - 1) / JT) * (a.Kp / KT);
+  const int64_t nT = ((a.side[0].rows + 1) / 2) * (a.Kp / 64) + ((a.side[1].rows + 3) / 4) * (a.Kp / 32);
   int64_t grid = nT;
   if (grid > ctx->sm_count) grid = ctx->sm_count;
   if (grid < 1) return ARBGPU_OK;
-  CUtensorMap tm;
-  if (!make_residue_store_map(&tm, out, a.Kp, a.rows, L.NPL, KT, JT, L.NPL))
+  CUtensorMap tmA, tmB;
+  if (!make_residue_store_map(&tmA, outA, a.Kp, a.side[0].rows, L.NPL, 64, 2, L.NPL) ||
+      !make_residue_store_map(&tmB, outB, a.Kp, a.side[1].rows, L.NPL, 32, 4, L.NPL))
     return ARBGPU_ERR_CUDA;
   const int dev = ctx->device & 255;
   const unsigned threads = 32u * (unsigned)(4 * L.ND + 4 * RT_NP + 1);
 #define ARB_RTC(NCH_)                                                                      \
   do {                                                                                     \
-    if (a.is_b) {                                                                          \
-      static bool attr_done[256] = {};                                                     \
-      if (!attr_done[dev]) {                                                               \
-        if (cudaFuncSetAttribute(residue_tc_kernel<NCH_, true>,                            \
-                                 cudaFuncAttributeMaxDynamicSharedMemorySize,              \
-                                 (int)RT_SMEM_MAX) != cudaSuccess)                         \
-          return ARBGPU_ERR_CUDA;                                                          \
-        attr_done[dev] = true;                                                             \
-      }                                                                                    \
-      launch_pdl(residue_tc_kernel<NCH_, true>, dim3((unsigned)grid), dim3(threads), L.smem, s, \
-                 tm, a);                                                                   \
-    } else {                                                                               \
-      static bool attr_done[256] = {};                                                     \
-      if (!attr_done[dev]) {                                                               \
-        if (cudaFuncSetAttribute(residue_tc_kernel<NCH_, false>,                           \
-                                 cudaFuncAttributeMaxDynamicSharedMemorySize,              \
-                                 (int)RT_SMEM_MAX) != cudaSuccess)                         \
-          return ARBGPU_ERR_CUDA;                                                          \
-        attr_done[dev] = true;                                                             \
-      }                                                                                    \
-      launch_pdl(residue_tc_kernel<NCH_, false>, dim3((unsigned)grid), dim3(threads), L.smem,   \
-                 s, tm, a);                                                                \
+    static bool attr_done[256] = {};                                                       \
+    if (!attr_done[dev]) {                                                                 \
+      if (cudaFuncSetAttribute(residue_tc_kernel<NCH_>,                                    \
+                               cudaFuncAttributeMaxDynamicSharedMemorySize,                \
+                               (int)RT_SMEM_MAX) != cudaSuccess)                           \
+        return ARBGPU_ERR_CUDA;                                                            \
+      attr_done[dev] = true;                                                               \
     }                                                                                      \
+    launch_pdl(residue_tc_kernel<NCH_>, dim3((unsigned)grid), dim3(threads), L.smem, s,    \
+               tmA, tmB, a);                                                               \
   } while (0)
   if (nch <= 4) ARB_RTC(4);
   else if (nch <= 8) ARB_RTC(8);
@@ -2526,47 +2574,35 @@ static arbgpu_status run_block(arbgpu_ctx *ctx, const BlockWs &w, uint8_t *ws, c
     const bool fold = (radA || radB) && crt_gemm_one_chain(Kp);
     __nv_bfloat16 *fA1 = resA + (size_t)2 * NM * M * Kp, *fA2 = fA1 + (size_t)2 * M * Kp;
     __nv_bfloat16 *fB1 = resB + (size_t)2 * NM * N * Kp, *fB2 = fB1 + (size_t)2 * N * Kp;
-    {
-      const int64_t n = M * Kp;
-      LaunchScope sc(ctx, s, "residues_a", n * NM * ((hA + 2 + 31) / 32 + 1));
-      const SplitOut ro = fold ? SplitOut{nullptr, fA1, fA2}
-                               : SplitOut{nullptr, radB ? rA1 : nullptr, radA ? rA2 : nullptr};
-      const int nch = (int)((hA + 2 + 31) / 32) + 1;
-      RtLayout L;
-      if (residue_tc_layout(nch, NM, fold, n, &L)) {
-        RtArgs ra{};
-        ra.X = Av, ra.is_b = false, ra.rows = M, ra.k0 = k0, ra.K = Kb, ra.Kp = Kp, ra.ld = lda;
-        ra.bot = ln.rbot, ra.NM = NM, ra.wtab = dt.wtab, ra.rinv = dt.rinv;
-        ra.ro = fold ? SplitOut{} : ro;
-        ra.top = ln.rtop, ra.radtop = ln.rrad, ra.plustop = nullptr;
-        const arbgpu_status st = launch_residues_tc(ctx, L, nch, s, ra, resA);
-        if (st != ARBGPU_OK) return st;
-      } else {
-        launch_residues(nch, n, s, Av, false, M, k0, Kb, Kp, lda, ln.rbot, NM, dt.pow32,
-                        plan->NCHP, nullptr, resA, ro, ln.rtop, ln.rrad, nullptr);
+    // the right-hand residues carry the factor y_t = (M / m_t)^-1 mod m_t of the reconstruction,
+    // so the residue products are already z_t = P_t y_t mod m_t
+    const SplitOut roA = fold ? SplitOut{nullptr, fA1, fA2}
+                              : SplitOut{nullptr, radB ? rA1 : nullptr, radA ? rA2 : nullptr};
+    const SplitOut roB = fold ? SplitOut{nullptr, fB1, fB2}
+                              : SplitOut{nullptr, radB ? rB1 : nullptr, radA ? rB2 : nullptr};
+    const int nchA = (int)((hA + 2 + 31) / 32) + 1, nchB = (int)((hB + 2 + 31) / 32) + 1;
+    const int nch = nchA > nchB ? nchA : nchB;
+    RtLayout L;
+    if (residue_tc_layout(nch, NM, fold, (M > N ? M : N) * Kp, &L)) {
+      LaunchScope sc(ctx, s, "residues", (M * nchA + N * nchB) * Kp * NM);
+      RtArgs ra{};
+      ra.side[0] = RtSide{Av, M, lda, ln.rbot, ln.rtop, ln.rrad, nullptr,
+                          fold ? SplitOut{} : roA, dt.wtab};
+      ra.side[1] = RtSide{Bv, N, ldb, ln.cbot, ln.ctop, ln.crad, ln.cplus,
+                          fold ? SplitOut{} : roB, dt.wtab + (size_t)plan->NPAD * 128};
+      ra.k0 = k0, ra.K = Kb, ra.Kp = Kp, ra.NM = NM, ra.rinv = dt.rinv;
+      const arbgpu_status st = launch_residues_tc(ctx, L, nch, s, ra, resA, resB);
+      if (st != ARBGPU_OK) return st;
+    } else {
+      {
+        LaunchScope sc(ctx, s, "residues_a", M * Kp * NM * nchA);
+        launch_residues(nchA, M * Kp, s, Av, false, M, k0, Kb, Kp, lda, ln.rbot, NM, dt.pow32,
+                        plan->NCHP, nullptr, resA, roA, ln.rtop, ln.rrad, nullptr);
       }
-    }
-    {
-      const int64_t n = N * Kp;
-      LaunchScope sc(ctx, s, "residues_b", n * NM * ((hB + 2 + 31) / 32 + 1));
-      // the right-hand residues carry the factor y_t = (M / m_t)^-1 mod m_t of the
-      // reconstruction, so the residue products are already z_t = P_t y_t mod m_t
-      const SplitOut ro = fold ? SplitOut{nullptr, fB1, fB2}
-                               : SplitOut{nullptr, radB ? rB1 : nullptr, radA ? rB2 : nullptr};
-      const int nch = (int)((hB + 2 + 31) / 32) + 1;
-      RtLayout L;
-      if (residue_tc_layout(nch, NM, fold, n, &L)) {
-        RtArgs ra{};
-        ra.X = Bv, ra.is_b = true, ra.rows = N, ra.k0 = k0, ra.K = Kb, ra.Kp = Kp, ra.ld = ldb;
-        ra.bot = ln.cbot, ra.NM = NM, ra.wtab = dt.wtab + (size_t)plan->NPAD * 128,
-        ra.rinv = dt.rinv;
-        ra.ro = fold ? SplitOut{} : ro;
-        ra.top = ln.ctop, ra.radtop = ln.crad, ra.plustop = ln.cplus;
-        const arbgpu_status st = launch_residues_tc(ctx, L, nch, s, ra, resB);
-        if (st != ARBGPU_OK) return st;
-      } else {
-        launch_residues(nch, n, s, Bv, true, N, k0, Kb, Kp, ldb, ln.cbot, NM, dt.pow32,
-                        plan->NCHP, dt.y, resB, ro, ln.ctop, ln.crad, ln.cplus);
+      {
+        LaunchScope sc(ctx, s, "residues_b", N * Kp * NM * nchB);
+        launch_residues(nchB, N * Kp, s, Bv, true, N, k0, Kb, Kp, ldb, ln.cbot, NM, dt.pow32,
+                        plan->NCHP, dt.y, resB, roB, ln.ctop, ln.crad, ln.cplus);
       }
     }
     if (cudaGetLastError() != cudaSuccess) return ARBGPU_ERR_CUDA;
