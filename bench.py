@@ -155,7 +155,14 @@ def roofline_of(name, k, peaks, sm_mhz, limb_n=None):
                 "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
                 "note": "exact BF16 digit products (1 digit MAC = 2 flops) vs the measured "
                         "dense BF16 burst peak (no INT8 tcgen05 on sm_103a)"}
-    if name in ("block_round", "residues", "residues_a", "residues_b"):
+    if name == "residues":  # units: algorithmic bytes (operands read, residue planes written)
+        achieved = units / avg_s / 1e9
+        peak = peaks.get("hbm_gbs", 6800.0)
+        return {"bound": "hbm", "kernel": name, "achieved": achieved, "peak": peak,
+                "unit": "GB/s", "frac": achieved / peak, "traffic": None,
+                "work": f"{units:.4g} bytes per launch: every operand entry read once, every "
+                        "residue and radius-operand plane written once"}
+    if name in ("block_round", "residues_a", "residues_b"):
         achieved = units / avg_s / 1e12
         return {"bound": "alu", "kernel": name, "achieved": achieved, "peak": alu_peak,
                 "unit": "T int32-mul/s", "frac": achieved / alu_peak, "traffic": None,

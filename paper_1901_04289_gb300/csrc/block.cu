@@ -2584,7 +2584,11 @@ static arbgpu_status run_block(arbgpu_ctx *ctx, const BlockWs &w, uint8_t *ws, c
     const int nch = nchA > nchB ? nchA : nchB;
     RtLayout L;
     if (residue_tc_layout(nch, NM, fold, (M > N ? M : N) * Kp, &L)) {
-      LaunchScope sc(ctx, s, "residues", (M * nchA + N * nchB) * Kp * NM);
+      // work units: algorithmic bytes (every operand entry read once, every residue and radius
+      // operand plane written once)
+      LaunchScope sc(ctx, s, "residues",
+                     (M * (8 * (int64_t)Av.nlimbs + 24) + N * (8 * (int64_t)Bv.nlimbs + 24)) * Kb +
+                         (int64_t)L.NPL * (M + N) * Kp * 2);
       RtArgs ra{};
       ra.side[0] = RtSide{Av, M, lda, ln.rbot, ln.rtop, ln.rrad, nullptr,
                           fold ? SplitOut{} : roA, dt.wtab};
