@@ -115,7 +115,9 @@ def test_invariants_against_exact(case, seed):
             assert F(m) == F(S) and r == (0, 0)
 
 
-def test_north_star_bound_on_random_signs():
+def test_midpoint_error_bound_on_random_signs():
+    """|m - S| <= 2^-p sum |x y| (the dot's accuracy guarantee, Section III) on 40 random dots
+    with mixed signs."""
     worst = 0.0
     for seed in range(40):
         x, y, _ = _case(seed, 50, 128, 2, 30, None, 0)
