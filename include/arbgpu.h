@@ -144,6 +144,19 @@ arbgpu_status arbgpu_dot(arbgpu_ctx *ctx, const arbgpu_balls *res, const arbgpu_
                          int64_t batch, int32_t prec_max, int64_t len_max, int complex_mode,
                          void *workspace, size_t ws_bytes, void *stream);
 
+/* Midpoint-only dots, the counterpart of arb_approx_dot / acb_approx_dot (Section III: the same
+ * interface without error bounds).  Same arguments and errors as arbgpu_dot.  Each midpoint is the
+ * one arbgpu_dot computes (the same accumulation, one rounding to prec bits); the input radii are
+ * ignored and the output radii are zero: no error bound is claimed.  Special values give
+ * [NaN +- inf] with ARBGPU_ERR_UNSUPPORTED_VALUE, as in arbgpu_dot. */
+arbgpu_status arbgpu_approx_dot(arbgpu_ctx *ctx, const arbgpu_balls *res,
+                                const arbgpu_balls *initial, const uint8_t *sub,
+                                const arbgpu_balls *x, const int64_t *xoff, const int64_t *xstep,
+                                const arbgpu_balls *y, const int64_t *yoff, const int64_t *ystep,
+                                const int64_t *len, const int32_t *prec, int64_t batch,
+                                int32_t prec_max, int64_t len_max, int complex_mode,
+                                void *workspace, size_t ws_bytes, void *stream);
+
 /* Algorithm selection for arbgpu_mat_mul. */
 #define ARBGPU_ALG_AUTO 0
 #define ARBGPU_ALG_DOT 1   /* classical: M*N dot products (Section IV, first paragraph) */

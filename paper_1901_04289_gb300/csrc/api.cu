@@ -173,12 +173,13 @@ arbgpu_status arbgpu_get_status(arbgpu_ctx *ctx, void *stream) {
   return (arbgpu_status)v;
 }
 
-arbgpu_status arbgpu_dot(arbgpu_ctx *ctx, const arbgpu_balls *res, const arbgpu_balls *initial,
-                         const uint8_t *sub, const arbgpu_balls *x, const int64_t *xoff,
-                         const int64_t *xstep, const arbgpu_balls *y, const int64_t *yoff,
-                         const int64_t *ystep, const int64_t *len, const int32_t *prec,
-                         int64_t batch, int32_t prec_max, int64_t len_max, int complex_mode,
-                         void *workspace, size_t ws_bytes, void *stream) {
+static arbgpu_status dot_entry(arbgpu_ctx *ctx, const arbgpu_balls *res,
+                               const arbgpu_balls *initial, const uint8_t *sub,
+                               const arbgpu_balls *x, const int64_t *xoff, const int64_t *xstep,
+                               const arbgpu_balls *y, const int64_t *yoff, const int64_t *ystep,
+                               const int64_t *len, const int32_t *prec, int64_t batch,
+                               int32_t prec_max, int64_t len_max, int complex_mode,
+                               void *workspace, size_t ws_bytes, void *stream, bool approx) {
   (void)workspace;
   (void)ws_bytes;
   if (!ctx || !res || !x || !y || batch < 0) return ARBGPU_ERR_INVALID;
@@ -201,7 +202,28 @@ arbgpu_status arbgpu_dot(arbgpu_ctx *ctx, const arbgpu_balls *res, const arbgpu_
   }
   if (cudaSetDevice(ctx->device) != cudaSuccess) return ARBGPU_ERR_CUDA;
   return launch_batched_dot(ctx, res, initial, sub, x, xoff, xstep, y, yoff, ystep, len, prec,
-                            batch, prec_max, len_max, complex_mode, (cudaStream_t)stream);
+                            batch, prec_max, len_max, complex_mode, (cudaStream_t)stream, approx);
+}
+
+arbgpu_status arbgpu_dot(arbgpu_ctx *ctx, const arbgpu_balls *res, const arbgpu_balls *initial,
+                         const uint8_t *sub, const arbgpu_balls *x, const int64_t *xoff,
+                         const int64_t *xstep, const arbgpu_balls *y, const int64_t *yoff,
+                         const int64_t *ystep, const int64_t *len, const int32_t *prec,
+                         int64_t batch, int32_t prec_max, int64_t len_max, int complex_mode,
+                         void *workspace, size_t ws_bytes, void *stream) {
+  return dot_entry(ctx, res, initial, sub, x, xoff, xstep, y, yoff, ystep, len, prec, batch,
+                   prec_max, len_max, complex_mode, workspace, ws_bytes, stream, false);
+}
+
+arbgpu_status arbgpu_approx_dot(arbgpu_ctx *ctx, const arbgpu_balls *res,
+                                const arbgpu_balls *initial, const uint8_t *sub,
+                                const arbgpu_balls *x, const int64_t *xoff, const int64_t *xstep,
+                                const arbgpu_balls *y, const int64_t *yoff, const int64_t *ystep,
+                                const int64_t *len, const int32_t *prec, int64_t batch,
+                                int32_t prec_max, int64_t len_max, int complex_mode,
+                                void *workspace, size_t ws_bytes, void *stream) {
+  return dot_entry(ctx, res, initial, sub, x, xoff, xstep, y, yoff, ystep, len, prec, batch,
+                   prec_max, len_max, complex_mode, workspace, ws_bytes, stream, true);
 }
 
 // AUTO: the block algorithm from this size on (the paper's default cutoff lies at N = 40..60).

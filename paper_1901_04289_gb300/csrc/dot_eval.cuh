@@ -128,13 +128,15 @@ struct DotSetup {
   int n_s;
   int nx;  // limbs to read per factor (at most)
   bool has_mid, has_rad;
+  bool approx;  // midpoint only: no radius is formed or written
 };
 
 // The setup parked in the output entry's flags word (bit 31 never appears in a finished entry).
 constexpr uint32_t DOT_PENDING = 1u << 31;
 __device__ __forceinline__ uint32_t pack_setup(int cls, const DotSetup &su) {
   return DOT_PENDING | (uint32_t)cls | ((uint32_t)su.n_s << 4) | ((uint32_t)su.nx << 10) |
-         (su.has_mid ? (1u << 16) : 0u) | (su.has_rad ? (1u << 17) : 0u);
+         (su.has_mid ? (1u << 16) : 0u) | (su.has_rad ? (1u << 17) : 0u) |
+         (su.approx ? (1u << 18) : 0u);
 }
 __device__ __forceinline__ int pending_class(uint32_t f) {
   return (f & DOT_PENDING) ? (int)(f & 15u) : -1;
@@ -147,6 +149,7 @@ __device__ __forceinline__ DotSetup unpack_setup(uint32_t f, int64_t e_s, int64_
   su.nx = (int)((f >> 10) & 63u);
   su.has_mid = (f >> 16) & 1u;
   su.has_rad = (f >> 17) & 1u;
+  su.approx = (f >> 18) & 1u;
   return su;
 }
 
@@ -391,7 +394,8 @@ __device__ void dot_finalise(const LaneAcc<NS> &acc, const DotSetup &su, int pre
   else if (su.has_mid)
     r1 = mag_from_u64(acc.err, ulp_e);
   const Mag r2 = su.has_rad ? mag_from_u64(acc.srad, su.e_rad - P_RAD) : Mag{0u, 0};
-  store_rounded<NS + 1, G>(out, oi, gl, zero, neg, ta, ulp_e + L, mag_add_up(r1, r2));
+  store_rounded<NS + 1, G>(out, oi, gl, zero, neg, ta, ulp_e + L,
+                           su.approx ? Mag{0u, 0} : mag_add_up(r1, r2));
 }
 
 template <int G>
@@ -654,7 +658,8 @@ __device__ bool dot_setup_core(const Src &src, const typename Src::Cursor &cur, 
   e_rad = group_max_i64<G>(e_rad, gm);
   nsig_max = (int)group_max_i64<G>(nsig_max, gm);
   su.has_mid = e_max != INT64_MIN;
-  su.has_rad = e_rad != INT64_MIN;
+  su.approx = src.approx;
+  su.has_rad = !su.approx && e_rad != INT64_MIN;  // approx: the radii are ignored
   if (!su.has_mid && !su.has_rad) {  // [0 +- 0]
     write_zero<G>(out, oi, gl);
     return false;

@@ -13,6 +13,7 @@ namespace arbgpu {
 // A complex dot b is two virtual real dots (2b: real part, 2b+1: imaginary part) of length 2N:
 // re = sum a c - b d, im = sum a d + b c (Section III-F).
 struct BatchDotSrc {
+  bool approx;  // midpoints only (radii ignored, zero output radii)
   BallsView x[2], y[2], init[2];
   BallsOut out[2];
   const int64_t *xoff, *xstep, *yoff, *ystep, *len;
@@ -66,6 +67,7 @@ struct BatchDotSrc {
 // Classical product: entry (i, j) is the dot of row i of A and column j of B.  Consecutive warps
 // take consecutive j, so the lanes' reads of B rows are shared through L1.
 struct MatDotSrc {
+  static constexpr bool approx = false;
   BallsView A[2], B[2];
   BallsOut C[2];
   int64_t M, K, N, lda, ldb, ldc;
@@ -113,6 +115,7 @@ struct MatDotSrc {
 // in bk (the basecase blocks of each real product), starting from the accumulated block products
 // as `initial`.
 struct BasecaseSrc {
+  static constexpr bool approx = false;
   BallsView A[2], B[2], init;
   BallsOut C;
   const int32_t *bk;
@@ -158,6 +161,7 @@ struct BasecaseSrc {
 // (binary search over a device work list); inside the item it is entry (i, j) (and, for complex
 // items, its part).
 struct GroupedDotSrc {
+  static constexpr bool approx = false;
   const GroupItem *items;
   const int64_t *ends;
   int32_t count;

@@ -18,7 +18,8 @@ def declared_functions():
 
 def test_header_declares_the_boundary():
     names = declared_functions()
-    for required in ("arbgpu_dot", "arbgpu_mat_mul", "arbgpu_create", "arbgpu_get_status",
+    for required in ("arbgpu_dot", "arbgpu_approx_dot", "arbgpu_mat_mul", "arbgpu_create",
+                     "arbgpu_get_status",
                      "arbgpu_int_mat_mul"):
         assert required in names
 

@@ -20,7 +20,7 @@ def arb():
     return arb
 
 
-def run_batch(arb, batch: DotBatch, nl_out=None, complex_parts=None):
+def run_batch(arb, batch: DotBatch, nl_out=None, complex_parts=None, approx=False):
     import torch
     nl_out = nl_out or (int(batch.prec.max()) + 63) // 64
     n = int(batch.length.shape[0])
@@ -31,7 +31,7 @@ def run_batch(arb, batch: DotBatch, nl_out=None, complex_parts=None):
     t = batch_tensors(batch)
     arb.dot(res, x, y, t["xoff"], t["xstep"], t["yoff"], t["ystep"], t["length"], t["prec"],
             prec_max=int(batch.prec.max()), len_max=int(batch.length.max()), sub=t["sub"],
-            initial=init)
+            initial=init, approx=approx)
     st = arb.default_context().status()
     torch.cuda.synchronize()
     return to_raw(res), st
@@ -101,6 +101,23 @@ def test_batched_dots_bit_exact_vs_alg1(arb, k):
         if mm:
             bad.append((b, mm))
     assert not bad, f"{len(bad)} mismatches, first: {bad[:2]}"
+
+
+@pytest.mark.parametrize("k", [1, 2, 4, 5])
+def test_approx_dots_give_the_ball_midpoints(arb, k):
+    """arbgpu_approx_dot (midpoints only, the approx_dot interface of Section III): every midpoint
+    is the one arbgpu_dot gives (the same accumulation and rounding), bit for bit, whatever the
+    radii; every output radius is zero."""
+    batch = small_batch(**SMALL[k])
+    nl_out = (int(batch.prec.max()) + 63) // 64
+    ball, st = run_batch(arb, batch, nl_out)
+    appr, st2 = run_batch(arb, batch, nl_out, approx=True)
+    assert st == 0 and st2 == 0
+    assert np.array_equal(ball.limbs, appr.limbs)
+    assert np.array_equal(ball.exp, appr.exp)
+    assert np.array_equal(ball.flags, appr.flags)
+    assert not np.any(appr.rad_man) and not np.any(appr.rad_exp)
+    assert np.any(ball.rad_man)  # the ball dots had radii to ignore
 
 
 @pytest.mark.parametrize("k", [1, 2, 4])
