@@ -2505,7 +2505,10 @@ static bool choose_crt(int SA, int SB, int NM, int64_t M, int64_t N, int64_t Kp,
   const char *e = getenv("ARBGPU_ENGINE");
   if (e && !strcmp(e, "digits")) return false;
   if (e && !strcmp(e, "crt")) return true;
-  const double t_mma = 2.6e-15, t_crt = 7e-13, t_res = 2.2e-13, t_dig = 4e-12;
+  // seconds per unit, measured on a GB300 (N = 512, p = 256): the reconstruction runs on the
+  // tensor cores for NM <= 64 and on the CUDA cores above
+  const double t_mma = 2.6e-15, t_crt = NM <= 64 ? 2.1e-13 : 7e-13, t_res = 2.4e-13,
+               t_dig = 4e-12;
   const double MN = (double)M * (double)N;
   const double nw32 = 2.0 * ((16.0 * NM + 63) / 64 + 1);
   const double nch = (double)((hA > hB ? hA : hB) + 2) / 32 + 1;
