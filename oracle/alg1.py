@@ -24,7 +24,8 @@ Steps (Section III-B..E):
 Readings where the paper leaves a choice (each also used by the kernel):
 
 * Rounding to p bits is round-to-nearest, ties to even.
-* The precision reduction of Section III-C step 7 is not applied (p stays as given).
+* The precision reduction of Section III-C step 7 ("optimize p") is applied only when asked
+  (``reduce_prec``); by default p stays as given.
 * ``initial`` is the extra term ``initial * 1`` with the exact ball ``[1 +- 0]`` (Section III-B:
   "extending the dot product to length N + 1"); ``N`` in ``padding`` counts it.
 * The radius is formed as: the integer ``eps_round + err`` (both in accumulator ulps) rounded up to
@@ -89,19 +90,20 @@ def mag_upper_of_mid(x: Entry):
     return (x.top[0] >> (BETA - P_RAD)) + 1, x.e
 
 
-def dot(terms, prec, nlimbs_out, initial=None):
+def dot(terms, prec, nlimbs_out, initial=None, reduce_prec=False):
     """Algorithm 1 on ``terms`` = list of ``(Entry, Entry, negate)``.
 
     Returns a dict with the output layout fields (``limbs``, ``exp``, ``flags``, ``rad_man``,
-    ``rad_exp``), ``status`` (0 or 2 for an unsupported value) and the internal quantities."""
+    ``rad_exp``), ``status`` (0 or 2 for an unsupported value) and the internal quantities.  With
+    ``reduce_prec``, step 7 of Section III-C lowers the working and output precision."""
     try:
-        return _dot(terms, prec, nlimbs_out, initial)
+        return _dot(terms, prec, nlimbs_out, initial, reduce_prec)
     except Special:
         return dict(limbs=[0] * nlimbs_out, exp=0, flags=FLAG_NAN | FLAG_RAD_INF, rad_man=0,
                     rad_exp=0, status=2)
 
 
-def _dot(terms, prec, nlimbs_out, initial):
+def _dot(terms, prec, nlimbs_out, initial, reduce_prec=False):
     if prec < 2:
         raise ValueError("p >= 2")
     allt = list(terms)
@@ -113,16 +115,29 @@ def _dot(terms, prec, nlimbs_out, initial):
     n_nonzero = 0
     e_max = None
     e_rad = None
+    e_min = None  # lowest possible bit of a product, tracked when p > 2 beta (Section III-C)
     for x, y, _neg in allt:
         if not x.zero and not y.zero:
             n_nonzero += 1
             t = x.e + y.e
             e_max = t if e_max is None else max(e_max, t)
+            if prec > 2 * BETA:
+                lo = t - BETA * (x.n + y.n)
+                e_min = lo if e_min is None else min(e_min, lo)
         for ee in _radius_exponents(x, y):
             e_rad = ee if e_rad is None else max(e_rad, ee)
     if e_max is None and e_rad is None:
         return dict(limbs=[0] * nlimbs_out, exp=0, flags=FLAG_ZERO, rad_man=0, rad_exp=0,
                     status=0, n_s=0, e_s=0, err=0, srad=0, e_rad=None)
+    if reduce_prec:  # step 7: a radius above the arithmetic error, or a narrow window of terms
+        if e_max is None:
+            prec = 2
+        else:
+            if e_rad is not None:
+                prec = min(prec, e_max - e_rad + P_RAD)
+            if e_min is not None:
+                prec = min(prec, e_max - e_min + P_RAD)
+            prec = max(prec, 2)
     padding = 4 + bc(N)
     extend = bc(n_nonzero) + 1
     n_s = max(2, -(-(prec + extend + padding) // BETA))
@@ -175,7 +190,7 @@ def _dot(terms, prec, nlimbs_out, initial):
     rman, rexp = mag_add_up(r_mid, r_rad)
     limbs, exp, flags = encode_mid(m, nlimbs_out)
     return dict(limbs=limbs, exp=exp, flags=flags, rad_man=rman, rad_exp=rexp, status=0,
-                n_s=n_s, e_s=e_s, err=err, srad=srad, e_rad=e_rad, sign=sign)
+                n_s=n_s, e_s=e_s, err=err, srad=srad, e_rad=e_rad, sign=sign, prec=prec)
 
 
 def _radius_exponents(x, y):
@@ -227,14 +242,15 @@ SPECIAL_OUTPUT = dict(limbs=None, exp=0, flags=FLAG_NAN | FLAG_RAD_INF, rad_man=
                       status=2)
 
 
-def dot_raw(xraw, xidx, yraw, yidx, prec, nlimbs_out, sub=False, initial=None):
+def dot_raw(xraw, xidx, yraw, yidx, prec, nlimbs_out, sub=False, initial=None,
+            reduce_prec=False):
     """Algorithm 1 on entries of raw ball arrays; ``initial`` is ``(raw, index)`` or None."""
     try:
         terms = real_terms(xraw, xidx, yraw, yidx, sub)
         init = entry(*initial) if initial is not None else None
     except Special:
         return dict(SPECIAL_OUTPUT, limbs=[0] * nlimbs_out)
-    return dot(terms, prec, nlimbs_out, init)
+    return dot(terms, prec, nlimbs_out, init, reduce_prec)
 
 
 def complex_dot_raw(x, xidx, y, yidx, prec, nlimbs_out, sub=False, initial=None):

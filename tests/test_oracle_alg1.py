@@ -222,3 +222,48 @@ def test_planted_mistakes_are_caught(monkeypatch):
     res = alg1.dot(alg1.real_terms(x, range(5), y, range(5)), 64, 1)
     m, r = out_mid_rad(res, 1)
     assert not X.contains(m, r, S, R)
+
+
+# ---- step 7 of Section III-C ("optimize p"), asked for with reduce_prec
+
+@pytest.mark.parametrize("seed", range(8))
+def test_reduced_precision_keeps_a_result_that_fits_its_window(seed):
+    """The paper: when all terms fit in a window smaller than p bits, reducing the precision does
+    not change the result.  One-limb mantissas with exponents within +-6 at p = 256 fit (the exact
+    sum has fewer than 190 bits), so the reduced run must give the same exact ball."""
+    x, y, _ = _case(7000 + seed, 24, 256, 1, 6, None, 0)
+    terms = alg1.real_terms(x, range(24), y, range(24))
+    full = alg1.dot(terms, 256, 4)
+    red = alg1.dot(terms, 256, 4, reduce_prec=True)
+    assert red["prec"] < 256  # the window rule fired
+    assert (red["limbs"], red["exp"], red["flags"]) == (full["limbs"], full["exp"], full["flags"])
+    assert (red["rad_man"], full["rad_man"]) == (0, 0)
+    S, _, _ = X.dot_terms_exact(X.real_dot_terms(x, range(24), y, range(24)))
+    assert F(out_mid_rad(red, 4)[0]) == F(S)
+
+
+@pytest.mark.parametrize("seed", range(8))
+def test_reduced_precision_with_wide_radii_still_contains_the_exact_sum(seed):
+    """Radii near 2^-40 relative: the radius rule lowers p to about 70 bits.  The ball must still
+    contain the exact dot product, and its midpoint has at most the reduced number of bits."""
+    x, y, init = _case(7100 + seed, 30, 256, 4, 20, 40, 0.3, with_init=True)
+    terms = alg1.real_terms(x, range(30), y, range(30))
+    res = alg1.dot(terms, 256, 4, alg1.entry(init, 0), reduce_prec=True)
+    assert res["status"] == 0 and 2 <= res["prec"] < 128
+    S, Sabs, R = X.dot_terms_exact(X.real_dot_terms(x, range(30), y, range(30)), X.ball(init, 0))
+    m, r = out_mid_rad(res, 4)
+    assert X.contains(m, r, S, R)
+    mf = F(m)
+    if mf:
+        num = abs(mf.numerator) // (abs(mf.numerator) & -abs(mf.numerator))  # odd part
+        assert num.bit_length() <= res["prec"]
+
+
+def test_reduced_precision_of_a_zero_midpoint_is_two_bits():
+    """Only radii: e_max is MIN, so p becomes 2 and the result is [0 +- r]."""
+    x = make_balls([0, 0], [Fraction(1, 2**10), 0])
+    y = make_balls([1, 1], [0, Fraction(1, 2**5)])
+    res = alg1.dot(alg1.real_terms(x, range(2), y, range(2)), 128, 2, reduce_prec=True)
+    assert res["prec"] == 2
+    m, r = out_mid_rad(res, 2)
+    assert F(m) == 0 and F(r) > 0
