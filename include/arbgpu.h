@@ -144,6 +144,24 @@ arbgpu_status arbgpu_dot(arbgpu_ctx *ctx, const arbgpu_balls *res, const arbgpu_
                          int64_t batch, int32_t prec_max, int64_t len_max, int complex_mode,
                          void *workspace, size_t ws_bytes, void *stream);
 
+/* Options of arbgpu_dot_ex. */
+#define ARBGPU_DOT_APPROX 1u      /* midpoints only: the input radii are ignored, zero radii out */
+#define ARBGPU_DOT_REDUCE_PREC 2u /* the precision reduction of Section III-C, step 7: per dot,
+                                   * p <- min(p, e_max - e_rad + 30) when a radius is present and,
+                                   * for p > 128, p <- min(p, e_max - e_min + 30) (e_min: the lowest
+                                   * possible bit of a product); then p >= 2, and p = 2 when every
+                                   * midpoint product is zero.  The midpoint is computed and rounded
+                                   * at the reduced precision; the ball still contains the exact
+                                   * result. */
+
+/* arbgpu_dot with options (a bitwise OR of ARBGPU_DOT_*); the other arguments as for arbgpu_dot. */
+arbgpu_status arbgpu_dot_ex(arbgpu_ctx *ctx, const arbgpu_balls *res, const arbgpu_balls *initial,
+                            const uint8_t *sub, const arbgpu_balls *x, const int64_t *xoff,
+                            const int64_t *xstep, const arbgpu_balls *y, const int64_t *yoff,
+                            const int64_t *ystep, const int64_t *len, const int32_t *prec,
+                            int64_t batch, int32_t prec_max, int64_t len_max, int complex_mode,
+                            uint32_t options, void *workspace, size_t ws_bytes, void *stream);
+
 /* Midpoint-only dots, the counterpart of arb_approx_dot / acb_approx_dot (Section III: the same
  * interface without error bounds).  Same arguments and errors as arbgpu_dot.  Each midpoint is the
  * one arbgpu_dot computes (the same accumulation, one rounding to prec bits); the input radii are

@@ -200,25 +200,25 @@ def _ptr(t):
 
 
 def dot(res, x, y, xoff, xstep, yoff, ystep, length, prec, *, prec_max, len_max, sub=None,
-        initial=None, ctx=None, stream=None, approx=False):
-    """Batched ball dots (``arbgpu_dot``; with ``approx``, ``arbgpu_approx_dot``: the same
-    midpoints, zero radii).  ``res``, ``x``, ``y``, ``initial``: a ``Balls`` (real) or a pair
-    ``(re, im)`` (complex).  Index arrays: int64 device tensors; ``prec`` int32; ``sub`` uint8 or
-    None."""
+        initial=None, ctx=None, stream=None, approx=False, reduce_prec=False):
+    """Batched ball dots (``arbgpu_dot_ex``): with ``approx`` the same midpoints and zero radii
+    (``arbgpu_approx_dot``); with ``reduce_prec`` the precision reduction of Section III-C, step 7.
+    ``res``, ``x``, ``y``, ``initial``: a ``Balls`` (real) or a pair ``(re, im)`` (complex).  Index
+    arrays: int64 device tensors; ``prec`` int32; ``sub`` uint8 or None."""
     ctx = ctx or default_context()
     cplx = isinstance(x, (list, tuple))
     r, xs, ys = _pair(res), _pair(x), _pair(y)
     init = _pair(initial) if initial is not None else None
     batch = int(length.shape[0])
-    fn = _lib.lib().arbgpu_approx_dot if approx else _lib.lib().arbgpu_dot
-    rc = fn(
+    options = (1 if approx else 0) | (2 if reduce_prec else 0)
+    rc = _lib.lib().arbgpu_dot_ex(
         ctx.handle, _arr([b.cstruct() for b in r]),
         _arr([b.cstruct() for b in init]) if init else None, _ptr(sub),
         _arr([b.cstruct() for b in xs]), _ptr(xoff), _ptr(xstep), _arr([b.cstruct() for b in ys]),
         _ptr(yoff), _ptr(ystep), _ptr(length), _ptr(prec), batch, int(prec_max), int(len_max),
-        1 if cplx else 0, None, 0, _stream_ptr(stream))
+        1 if cplx else 0, options, None, 0, _stream_ptr(stream))
     if rc != 0:
-        raise ArbgpuError(rc, "arbgpu_approx_dot" if approx else "arbgpu_dot")
+        raise ArbgpuError(rc, "arbgpu_dot_ex")
 
 
 def mat_mul_workspace_size(M, K, N, prec, a_nlimbs, b_nlimbs, complex_mode=False, alg=ALG_AUTO,

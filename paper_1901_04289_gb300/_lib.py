@@ -84,6 +84,8 @@ def lib():
         L.arbgpu_dot.argtypes = [vp, P, P, vp, P, vp, vp, P, vp, vp, vp, vp, i64, i32, i64, C.c_int,
                                  vp, sz, vp]
         L.arbgpu_approx_dot.argtypes = L.arbgpu_dot.argtypes
+        L.arbgpu_dot_ex.argtypes = [vp, P, P, vp, P, vp, vp, P, vp, vp, vp, vp, i64, i32, i64,
+                                    C.c_int, C.c_uint32, vp, sz, vp]
         L.arbgpu_mat_mul.argtypes = [vp, P, P, P, i64, i64, i64, i64, i64, i64, i32, C.c_int,
                                      C.c_int, C.c_uint32, vp, sz, vp]
         L.arbgpu_mat_mul_workspace_size.argtypes = [vp, i64, i64, i64, i32, i32, i32, C.c_int,
@@ -103,7 +105,7 @@ def lib():
         L.arbgpu_trace_read.argtypes = [vp, C.POINTER(CTrace), i32, C.POINTER(C.c_int32)]
         for name in ("arbgpu_launch_count", "arbgpu_trace_enable", "arbgpu_trace_read",
                      "arbgpu_create", "arbgpu_destroy", "arbgpu_get_status", "arbgpu_dot",
-                     "arbgpu_approx_dot",
+                     "arbgpu_approx_dot", "arbgpu_dot_ex",
                      "arbgpu_mat_mul", "arbgpu_mat_mul_workspace_size", "arbgpu_int_mat_mul",
                      "arbgpu_int_mat_mul_workspace_size"):
             getattr(L, name).restype = C.c_int
@@ -122,7 +124,8 @@ def exported_symbols():
     """Names the shared library must export (every function declared in include/arbgpu.h)."""
     return ["arbgpu_create", "arbgpu_destroy", "arbgpu_get_status", "arbgpu_status_string",
             "arbgpu_version", "arbgpu_launch_count", "arbgpu_trace_enable", "arbgpu_trace_read",
-            "arbgpu_dot", "arbgpu_approx_dot", "arbgpu_mat_mul", "arbgpu_mat_mul_workspace_size",
+            "arbgpu_dot", "arbgpu_approx_dot", "arbgpu_dot_ex", "arbgpu_mat_mul",
+            "arbgpu_mat_mul_workspace_size",
             "arbgpu_int_mat_mul", "arbgpu_int_mat_mul_workspace_size",
             "arbgpu_int_mat_mul_noalloc", "arbgpu_mat_mul_batched",
             "arbgpu_mat_mul_batched_workspace_size"]

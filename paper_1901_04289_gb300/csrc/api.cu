@@ -179,10 +179,11 @@ static arbgpu_status dot_entry(arbgpu_ctx *ctx, const arbgpu_balls *res,
                                const arbgpu_balls *y, const int64_t *yoff, const int64_t *ystep,
                                const int64_t *len, const int32_t *prec, int64_t batch,
                                int32_t prec_max, int64_t len_max, int complex_mode,
-                               void *workspace, size_t ws_bytes, void *stream, bool approx) {
+                               void *workspace, size_t ws_bytes, void *stream, uint32_t options) {
   (void)workspace;
   (void)ws_bytes;
   if (!ctx || !res || !x || !y || batch < 0) return ARBGPU_ERR_INVALID;
+  if (options & ~(ARBGPU_DOT_APPROX | ARBGPU_DOT_REDUCE_PREC)) return ARBGPU_ERR_INVALID;
   if (batch == 0) return ARBGPU_OK;
   if (!xoff || !xstep || !yoff || !ystep || !len || !prec) return ARBGPU_ERR_INVALID;
   if (prec_max < 2 || prec_max > 1024 || len_max < 0 || len_max > ((int64_t)1 << 40))
@@ -202,7 +203,9 @@ static arbgpu_status dot_entry(arbgpu_ctx *ctx, const arbgpu_balls *res,
   }
   if (cudaSetDevice(ctx->device) != cudaSuccess) return ARBGPU_ERR_CUDA;
   return launch_batched_dot(ctx, res, initial, sub, x, xoff, xstep, y, yoff, ystep, len, prec,
-                            batch, prec_max, len_max, complex_mode, (cudaStream_t)stream, approx);
+                            batch, prec_max, len_max, complex_mode, (cudaStream_t)stream,
+                            (options & ARBGPU_DOT_APPROX) != 0,
+                            (options & ARBGPU_DOT_REDUCE_PREC) != 0);
 }
 
 arbgpu_status arbgpu_dot(arbgpu_ctx *ctx, const arbgpu_balls *res, const arbgpu_balls *initial,
@@ -212,7 +215,17 @@ arbgpu_status arbgpu_dot(arbgpu_ctx *ctx, const arbgpu_balls *res, const arbgpu_
                          int64_t batch, int32_t prec_max, int64_t len_max, int complex_mode,
                          void *workspace, size_t ws_bytes, void *stream) {
   return dot_entry(ctx, res, initial, sub, x, xoff, xstep, y, yoff, ystep, len, prec, batch,
-                   prec_max, len_max, complex_mode, workspace, ws_bytes, stream, false);
+                   prec_max, len_max, complex_mode, workspace, ws_bytes, stream, 0u);
+}
+
+arbgpu_status arbgpu_dot_ex(arbgpu_ctx *ctx, const arbgpu_balls *res, const arbgpu_balls *initial,
+                            const uint8_t *sub, const arbgpu_balls *x, const int64_t *xoff,
+                            const int64_t *xstep, const arbgpu_balls *y, const int64_t *yoff,
+                            const int64_t *ystep, const int64_t *len, const int32_t *prec,
+                            int64_t batch, int32_t prec_max, int64_t len_max, int complex_mode,
+                            uint32_t options, void *workspace, size_t ws_bytes, void *stream) {
+  return dot_entry(ctx, res, initial, sub, x, xoff, xstep, y, yoff, ystep, len, prec, batch,
+                   prec_max, len_max, complex_mode, workspace, ws_bytes, stream, options);
 }
 
 arbgpu_status arbgpu_approx_dot(arbgpu_ctx *ctx, const arbgpu_balls *res,
@@ -223,7 +236,8 @@ arbgpu_status arbgpu_approx_dot(arbgpu_ctx *ctx, const arbgpu_balls *res,
                                 int32_t prec_max, int64_t len_max, int complex_mode,
                                 void *workspace, size_t ws_bytes, void *stream) {
   return dot_entry(ctx, res, initial, sub, x, xoff, xstep, y, yoff, ystep, len, prec, batch,
-                   prec_max, len_max, complex_mode, workspace, ws_bytes, stream, true);
+                   prec_max, len_max, complex_mode, workspace, ws_bytes, stream,
+                   ARBGPU_DOT_APPROX);
 }
 
 // AUTO: the block algorithm from this size on (the paper's default cutoff lies at N = 40..60).

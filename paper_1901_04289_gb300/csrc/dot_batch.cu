@@ -16,7 +16,7 @@ arbgpu_status launch_batched_dot(arbgpu_ctx *ctx, const arbgpu_balls *res,
                                  const arbgpu_balls *y, const int64_t *yoff, const int64_t *ystep,
                                  const int64_t *len, const int32_t *prec, int64_t batch,
                                  int32_t prec_max, int64_t len_max, int complex_mode,
-                                 cudaStream_t stream, bool approx) {
+                                 cudaStream_t stream, bool approx, bool reduce) {
   const int parts = complex_mode ? 2 : 1;
   BatchDotSrc s{};
   int maxnl = 1;
@@ -45,6 +45,7 @@ arbgpu_status launch_batched_dot(arbgpu_ctx *ctx, const arbgpu_balls *res,
   s.cplx = complex_mode ? 1 : 0;
   s.has_init = initial != nullptr;
   s.approx = approx;
+  s.reduce = reduce;
   s.prec_max = prec_max;
   const int64_t terms_max = (complex_mode ? 2 * len_max : len_max);
   s.len_max = terms_max;

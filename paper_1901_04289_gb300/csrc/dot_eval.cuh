@@ -129,6 +129,7 @@ struct DotSetup {
   int nx;  // limbs to read per factor (at most)
   bool has_mid, has_rad;
   bool approx;  // midpoint only: no radius is formed or written
+  int prec;     // working and output precision (the requested one, or step 7's reduction)
 };
 
 // The setup parked in the output entry's flags word (bit 31 never appears in a finished entry).
@@ -136,7 +137,7 @@ constexpr uint32_t DOT_PENDING = 1u << 31;
 __device__ __forceinline__ uint32_t pack_setup(int cls, const DotSetup &su) {
   return DOT_PENDING | (uint32_t)cls | ((uint32_t)su.n_s << 4) | ((uint32_t)su.nx << 10) |
          (su.has_mid ? (1u << 16) : 0u) | (su.has_rad ? (1u << 17) : 0u) |
-         (su.approx ? (1u << 18) : 0u);
+         (su.approx ? (1u << 18) : 0u) | ((uint32_t)su.prec << 19);
 }
 __device__ __forceinline__ int pending_class(uint32_t f) {
   return (f & DOT_PENDING) ? (int)(f & 15u) : -1;
@@ -150,6 +151,7 @@ __device__ __forceinline__ DotSetup unpack_setup(uint32_t f, int64_t e_s, int64_
   su.has_mid = (f >> 16) & 1u;
   su.has_rad = (f >> 17) & 1u;
   su.approx = (f >> 18) & 1u;
+  su.prec = (int)((f >> 19) & 2047u);
   return su;
 }
 
@@ -610,6 +612,8 @@ __device__ bool dot_setup_core(const Src &src, const typename Src::Cursor &cur, 
   bool special = false;
   int64_t nnz = 0;
   int64_t e_max = INT64_MIN, e_rad = INT64_MIN;
+  int64_t e_min = INT64_MAX;  // lowest possible bit of a product (step 7, when p > 2 beta)
+  const bool track_min = src.reduce && prec > 128;
   int nsig_max = 0;
   constexpr int U = 2;  // terms per lane per step, loads issued together
   const int64_t ntot = nt + (has_init ? 1 : 0);
@@ -641,6 +645,11 @@ __device__ bool dot_setup_core(const Src &src, const typename Src::Cursor &cur, 
       if (!opnd_zero(x[u]) && !opnd_zero(y[u])) {
         ++nnz;
         e_max = imax64(e_max, x[u].e + y[u].e);
+        if (track_min) {
+          const int64_t lo = x[u].e + y[u].e -
+                             64LL * ((int64_t)nsig_of(x[u].flags) + (int64_t)nsig_of(y[u].flags));
+          e_min = lo < e_min ? lo : e_min;
+        }
         // the `initial` term has its own limb array, so only the regular terms size the class
         if (regular[u])
           nsig_max = max(nsig_max, (int)max(nsig_of(x[u].flags), nsig_of(y[u].flags)));
@@ -657,6 +666,7 @@ __device__ bool dot_setup_core(const Src &src, const typename Src::Cursor &cur, 
   e_max = group_max_i64<G>(e_max, gm);
   e_rad = group_max_i64<G>(e_rad, gm);
   nsig_max = (int)group_max_i64<G>(nsig_max, gm);
+  if (track_min) e_min = -group_max_i64<G>(-e_min, gm);
   su.has_mid = e_max != INT64_MIN;
   su.approx = src.approx;
   su.has_rad = !su.approx && e_rad != INT64_MIN;  // approx: the radii are ignored
@@ -664,8 +674,22 @@ __device__ bool dot_setup_core(const Src &src, const typename Src::Cursor &cur, 
     write_zero<G>(out, oi, gl);
     return false;
   }
+  // step 7 of Section III-C, when asked for: a radius above the arithmetic error, or terms that
+  // fit in a narrow window, lower the precision
+  int p = prec;
+  if (src.reduce) {
+    if (!su.has_mid) {
+      p = 2;
+    } else {
+      if (e_rad != INT64_MIN && e_max - e_rad + P_RAD < p) p = (int)(e_max - e_rad + P_RAD);
+      if (track_min && e_min != INT64_MAX && e_max - e_min + P_RAD < p)
+        p = (int)(e_max - e_min + P_RAD);
+      if (p < 2) p = 2;
+    }
+  }
+  su.prec = p;
   const int extend = bc64(nnz) + 1;
-  su.n_s = dot_ns(prec, ntot, nnz);
+  su.n_s = dot_ns(p, ntot, nnz);
   su.e_s = su.has_mid ? e_max + extend : 0;
   su.e_rad = e_rad;
   su.nx = min(nsig_max, su.n_s + 1);
@@ -756,7 +780,7 @@ __global__ void __launch_bounds__(256, DotClassBlocks<C>::B)
         const BallsOut &out = src.out_view(cd);
         const int64_t oi = src.out_index(cd);
         const DotSetup su = unpack_setup(fd, __ldg(out.exp + oi), __ldg(out.rad_exp + oi));
-        dot_eval_class<C, G>(src, cd, su, src.prec(cd), gl, gm);
+        dot_eval_class<C, G>(src, cd, su, su.prec, gl, gm);
       }
       __syncwarp();
     }
@@ -782,7 +806,7 @@ __global__ void __launch_bounds__(256, DotClassBlocks<C>::B)
       DotSetup su;
       int c = 0;
       if (dot_setup_core<G>(src, cur, C, gl, gm, status, su, c))
-        dot_eval_class<C, G>(src, cur, su, src.prec(cur), gl, gm);
+        dot_eval_class<C, G>(src, cur, su, su.prec, gl, gm);
     }
     __syncwarp();
   }

@@ -14,6 +14,7 @@ namespace arbgpu {
 // re = sum a c - b d, im = sum a d + b c (Section III-F).
 struct BatchDotSrc {
   bool approx;  // midpoints only (radii ignored, zero output radii)
+  bool reduce;  // the precision reduction of Section III-C, step 7
   BallsView x[2], y[2], init[2];
   BallsOut out[2];
   const int64_t *xoff, *xstep, *yoff, *ystep, *len;
@@ -68,6 +69,7 @@ struct BatchDotSrc {
 // take consecutive j, so the lanes' reads of B rows are shared through L1.
 struct MatDotSrc {
   static constexpr bool approx = false;
+  static constexpr bool reduce = false;
   BallsView A[2], B[2];
   BallsOut C[2];
   int64_t M, K, N, lda, ldb, ldc;
@@ -116,6 +118,7 @@ struct MatDotSrc {
 // as `initial`.
 struct BasecaseSrc {
   static constexpr bool approx = false;
+  static constexpr bool reduce = false;
   BallsView A[2], B[2], init;
   BallsOut C;
   const int32_t *bk;
@@ -162,6 +165,7 @@ struct BasecaseSrc {
 // items, its part).
 struct GroupedDotSrc {
   static constexpr bool approx = false;
+  static constexpr bool reduce = false;
   const GroupItem *items;
   const int64_t *ends;
   int32_t count;

@@ -54,7 +54,7 @@ arbgpu_status launch_batched_dot(arbgpu_ctx *ctx, const arbgpu_balls *res,
                                  const arbgpu_balls *y, const int64_t *yoff, const int64_t *ystep,
                                  const int64_t *len, const int32_t *prec, int64_t batch,
                                  int32_t prec_max, int64_t len_max, int complex_mode,
-                                 cudaStream_t stream, bool approx = false);
+                                 cudaStream_t stream, bool approx = false, bool reduce = false);
 
 // Kernel (a) over rows x columns: the classical matrix product, one warp per output entry.
 arbgpu_status launch_matmul_dot(arbgpu_ctx *ctx, const arbgpu_balls *C, const arbgpu_balls *A,

@@ -20,7 +20,8 @@ def arb():
     return arb
 
 
-def run_batch(arb, batch: DotBatch, nl_out=None, complex_parts=None, approx=False):
+def run_batch(arb, batch: DotBatch, nl_out=None, complex_parts=None, approx=False,
+              reduce_prec=False):
     import torch
     nl_out = nl_out or (int(batch.prec.max()) + 63) // 64
     n = int(batch.length.shape[0])
@@ -31,18 +32,18 @@ def run_batch(arb, batch: DotBatch, nl_out=None, complex_parts=None, approx=Fals
     t = batch_tensors(batch)
     arb.dot(res, x, y, t["xoff"], t["xstep"], t["yoff"], t["ystep"], t["length"], t["prec"],
             prec_max=int(batch.prec.max()), len_max=int(batch.length.max()), sub=t["sub"],
-            initial=init, approx=approx)
+            initial=init, approx=approx, reduce_prec=reduce_prec)
     st = arb.default_context().status()
     torch.cuda.synchronize()
     return to_raw(res), st
 
 
-def alg1_of(batch: DotBatch, b: int, nl_out: int):
+def alg1_of(batch: DotBatch, b: int, nl_out: int, reduce_prec=False):
     idx_x = [int(batch.xoff[b] + i * batch.xstep[b]) for i in range(int(batch.length[b]))]
     idx_y = [int(batch.yoff[b] + i * batch.ystep[b]) for i in range(int(batch.length[b]))]
     init = (batch.initial, b) if batch.initial is not None else None
     return alg1.dot_raw(batch.x, idx_x, batch.y, idx_y, int(batch.prec[b]), nl_out,
-                        sub=bool(batch.sub[b]), initial=init)
+                        sub=bool(batch.sub[b]), initial=init, reduce_prec=reduce_prec)
 
 
 def small_batch(seed, count, nl, precs, spread, rad_bits, rad_zero, zero_frac=0.0, lmax=70,
@@ -101,6 +102,25 @@ def test_batched_dots_bit_exact_vs_alg1(arb, k):
         if mm:
             bad.append((b, mm))
     assert not bad, f"{len(bad)} mismatches, first: {bad[:2]}"
+
+
+@pytest.mark.parametrize("k", [1, 2, 4, 5])
+def test_reduced_precision_dots_bit_exact_vs_alg1(arb, k):
+    """ARBGPU_DOT_REDUCE_PREC (Section III-C, step 7): every output field equals the Algorithm 1
+    restatement run with the same reduction, and the reduction changes some results."""
+    batch = small_batch(**SMALL[k])
+    nl_out = (int(batch.prec.max()) + 63) // 64
+    out, st = run_batch(arb, batch, nl_out, reduce_prec=True)
+    full, _ = run_batch(arb, batch, nl_out)
+    assert st == 0
+    bad = []
+    for b in range(len(batch.length)):
+        mm = mismatch(out, b, alg1_of(batch, b, nl_out, reduce_prec=True))
+        if mm:
+            bad.append((b, mm))
+    assert not bad, f"{len(bad)} mismatches, first: {bad[:2]}"
+    assert not (np.array_equal(out.limbs, full.limbs) and np.array_equal(out.rad_man,
+                                                                          full.rad_man))
 
 
 @pytest.mark.parametrize("k", [1, 2, 4, 5])
