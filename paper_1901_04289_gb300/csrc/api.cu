@@ -251,14 +251,15 @@ arbgpu_status arbgpu_mat_mul_workspace_size(arbgpu_ctx *ctx, int64_t M, int64_t 
                                             size_t *bytes) {
   (void)a_nlimbs;
   (void)b_nlimbs;
-  (void)flags;
   if (!ctx || !bytes || M < 0 || K < 0 || N < 0 || prec < 2 || prec > 1024)
     return ARBGPU_ERR_INVALID;
+  if (flags & ~ARBGPU_MM_COMPLEX_3M) return ARBGPU_ERR_INVALID;
   *bytes = 0;
   if (alg == ARBGPU_ALG_DOT) return ARBGPU_OK;
   if (alg != ARBGPU_ALG_BLOCK && alg != ARBGPU_ALG_AUTO) return ARBGPU_ERR_INVALID;
   if (alg == ARBGPU_ALG_AUTO && !auto_uses_block(M, K, N)) return ARBGPU_OK;
-  *bytes = block_workspace_size(ctx, M, K, N, prec, complex_mode != 0);
+  *bytes = block_workspace_size(ctx, M, K, N, prec, complex_mode != 0,
+                                (flags & ARBGPU_MM_COMPLEX_3M) != 0);
   return ARBGPU_OK;
 }
 
@@ -266,10 +267,8 @@ arbgpu_status arbgpu_mat_mul(arbgpu_ctx *ctx, const arbgpu_balls *C, const arbgp
                              const arbgpu_balls *B, int64_t M, int64_t K, int64_t N, int64_t lda,
                              int64_t ldb, int64_t ldc, int32_t prec, int complex_mode, int alg,
                              uint32_t flags, void *workspace, size_t ws_bytes, void *stream) {
-  (void)flags;
-  (void)workspace;
-  (void)ws_bytes;
   if (!ctx || !C || !A || !B || M < 0 || K < 0 || N < 0) return ARBGPU_ERR_INVALID;
+  if (flags & ~ARBGPU_MM_COMPLEX_3M) return ARBGPU_ERR_INVALID;
   if (prec < 2 || prec > 1024) return ARBGPU_ERR_INVALID;
   if (M == 0 || N == 0) return ARBGPU_OK;
   if (lda < K || ldb < N || ldc < N) return ARBGPU_ERR_INVALID;
@@ -293,7 +292,8 @@ arbgpu_status arbgpu_mat_mul(arbgpu_ctx *ctx, const arbgpu_balls *C, const arbgp
   if (try_block && K > 0) {
     bool used = false;
     arbgpu_status st = block_matmul(ctx, C, A, B, M, K, N, lda, ldb, ldc, prec, complex_mode != 0,
-                                    workspace, ws_bytes, (cudaStream_t)stream, &used);
+                                    (flags & ARBGPU_MM_COMPLEX_3M) != 0, workspace, ws_bytes,
+                                    (cudaStream_t)stream, &used);
     if (used || st != ARBGPU_ERR_LIMIT) return st;
     // not a single exponent block (or special values): the classical algorithm handles it
   }
@@ -345,7 +345,8 @@ arbgpu_status arbgpu_mat_mul_batched_workspace_size(arbgpu_ctx *ctx,
   for (int32_t q = 0; q < count; ++q) {
     const arbgpu_matmul_desc &d = descs[q];
     if (!item_uses_block(d)) continue;
-    const size_t b = block_workspace_size(ctx, d.M, d.K, d.N, d.prec, d.complex_mode != 0);
+    const size_t b = block_workspace_size(ctx, d.M, d.K, d.N, d.prec, d.complex_mode != 0,
+                                          (d.flags & ARBGPU_MM_COMPLEX_3M) != 0);
     blk = b > blk ? b : blk;
     scans += al256(block_scan_bytes(d.M, d.N, d.complex_mode != 0));
   }
@@ -362,6 +363,7 @@ arbgpu_status arbgpu_mat_mul_batched(arbgpu_ctx *ctx, const arbgpu_matmul_desc *
     const arbgpu_matmul_desc &d = descs[q];
     if (d.alg != ARBGPU_ALG_AUTO && d.alg != ARBGPU_ALG_DOT && d.alg != ARBGPU_ALG_BLOCK)
       return ARBGPU_ERR_INVALID;
+    if (d.flags & ~ARBGPU_MM_COMPLEX_3M) return ARBGPU_ERR_INVALID;
     if (!matmul_args_ok(d.C, d.A, d.B, d.M, d.K, d.N, d.lda, d.ldb, d.ldc, d.prec,
                         d.complex_mode))
       return ARBGPU_ERR_INVALID;
@@ -457,7 +459,8 @@ arbgpu_status arbgpu_mat_mul_batched(arbgpu_ctx *ctx, const arbgpu_matmul_desc *
       st = ARBGPU_ERR_LIMIT;
       if (scanned[i])
         st = block_finish(ctx, d.C, d.A, d.B, d.M, d.K, d.N, d.lda, d.ldb, d.ldc, d.prec,
-                          d.complex_mode != 0, ws + region[i], hstats.data() + 4 * i,
+                          d.complex_mode != 0, (d.flags & ARBGPU_MM_COMPLEX_3M) != 0,
+                          ws + region[i], hstats.data() + 4 * i,
                           ws + prod_off, ws_bytes - prod_off, s, &used);
       if (!used && st == ARBGPU_ERR_LIMIT)
         st = launch_matmul_dot(ctx, d.C, d.A, d.B, d.M, d.K, d.N, d.lda, d.ldb, d.ldc, d.prec,

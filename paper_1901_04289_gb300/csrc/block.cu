@@ -2242,7 +2242,9 @@ struct AccArgs {
   const int64_t *rtop, *rbot, *rrad, *ctop, *cbot, *crad, *cplus;  // this block's lines
   AccView v;
   int64_t M, N, Mp, Np;
-  int negate;  // subtract the product (the -B D part of a complex real part)
+  int negate;    // subtract the product (the -B D part of a complex real part)
+  int skip_mid;  // add only the radius bound (the complex product by eq. 3)
+  int skip_rad;  // add only the product (the complex product by eq. 3)
 };
 
 constexpr int ACC_MAX = 24;
@@ -2256,7 +2258,8 @@ __global__ void accumulate_kernel(const AccArgs a) {
   const int64_t MN = a.M * a.N;
   const AccView &v = a.v;
   int64_t vtop;
-  if (a.rtop[i] != INT64_MIN && a.ctop[j] != INT64_MIN && acc_top(v, i, j, vtop)) {
+  if (!a.skip_mid && a.rtop[i] != INT64_MIN && a.ctop[j] != INT64_MIN &&
+      acc_top(v, i, j, vtop)) {
     uint64_t T[RD_MAXW];
     const int nw = assemble(a.mid, i, j, a.Mp, a.Np, T);
     const bool tneg = (T[nw - 1] >> 63) != 0;
@@ -2297,6 +2300,7 @@ __global__ void accumulate_kernel(const AccArgs a) {
     }
     if (lost) v.err[idx] += 1;
   }
+  if (a.skip_rad) return;
   const Mag r = block_radius(a.rp1, a.rp2, a.rtop, a.rrad, a.crad, a.cplus, i, j, a.Mp, a.Np);
   if (r.man) {
     const Mag cur{v.rman[idx], v.rexp[idx]};
@@ -2378,6 +2382,124 @@ __global__ void acc_to_ball_kernel(const AccView v, BallsOut I, int64_t M, int64
   I.rad_exp[idx] = r.man ? r.exp : 0;
 }
 
+// ------------------------------------------------------------------------- complex product by eq. 3
+
+// The shared scaling of a complex operand's two parts: eq. 3 forms X_re + X_im, so both parts of a
+// row of A (a column of B) take one exponent.  Line tops are the larger, bottoms the smaller of
+// the parts' (an empty line has top INT64_MIN and bottom INT64_MAX); st receives the largest row
+// height (hA) and column height (hB), INT64_MIN when every line is empty.  One CTA.
+__global__ void __launch_bounds__(1024) merge_parts_kernel(
+    const int64_t *rtop0, const int64_t *rbot0, const int64_t *rtop1, const int64_t *rbot1,
+    int64_t M, int64_t *rtop, int64_t *rbot, const int64_t *ctop0, const int64_t *cbot0,
+    const int64_t *ctop1, const int64_t *cbot1, int64_t N, int64_t *ctop, int64_t *cbot,
+    BlockStats *st) {
+  __shared__ long long s_h[2];
+  if (threadIdx.x < 2) s_h[threadIdx.x] = INT64_MIN;
+  __syncthreads();
+  long long hA = INT64_MIN, hB = INT64_MIN;
+  for (int64_t i = threadIdx.x; i < M; i += blockDim.x) {
+    const long long t = max((long long)rtop0[i], (long long)rtop1[i]);
+    const long long b = min((long long)rbot0[i], (long long)rbot1[i]);
+    rtop[i] = t;
+    rbot[i] = b;
+    if (t != INT64_MIN) hA = max(hA, t - b);
+  }
+  for (int64_t j = threadIdx.x; j < N; j += blockDim.x) {
+    const long long t = max((long long)ctop0[j], (long long)ctop1[j]);
+    const long long b = min((long long)cbot0[j], (long long)cbot1[j]);
+    ctop[j] = t;
+    cbot[j] = b;
+    if (t != INT64_MIN) hB = max(hB, t - b);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    hA = max(hA, __shfl_xor_sync(0xffffffffu, hA, o));
+    hB = max(hB, __shfl_xor_sync(0xffffffffu, hB, o));
+  }
+  if ((threadIdx.x & 31) == 0) {
+    atomicMax(&s_h[0], hA);
+    atomicMax(&s_h[1], hB);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    BlockStats m{};
+    m.hA = s_h[0];
+    m.hB = s_h[1];
+    *st = m;
+  }
+}
+
+// Residues of X_re + X_im from those of the parts (the residue of a sum is the sum of the
+// residues): r = r_re + r_im, brought back to the balanced range |r| <= (m_t - 1) / 2 and split
+// again into the balanced bytes r = 256 h + l, l in [-128, 127], that the residue kernels write
+// (planes [2t] = l and [2t + 1] = h of [2 NM][plane]).  Vectors [0, nvA) are those of A (planes
+// of planeA entries), the rest those of B; eight entries per vector (planes are multiples of 8).
+__global__ void residue_sum_kernel(const __nv_bfloat16 *reA, const __nv_bfloat16 *imA,
+                                   __nv_bfloat16 *sumA, int64_t planeA,
+                                   const __nv_bfloat16 *reB, const __nv_bfloat16 *imB,
+                                   __nv_bfloat16 *sumB, int64_t planeB, int NM) {
+  const int64_t nvA = (int64_t)NM * (planeA / 8), nvB = (int64_t)NM * (planeB / 8);
+  int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (v >= nvA + nvB) return;
+  const bool is_b = v >= nvA;
+  if (is_b) v -= nvA;
+  const int64_t plane = is_b ? planeB : planeA, pv = plane / 8;
+  const __nv_bfloat16 *re = is_b ? reB : reA, *im = is_b ? imB : imA;
+  __nv_bfloat16 *sum = is_b ? sumB : sumA;
+  const int t = (int)(v / pv);
+  const int64_t lo = (int64_t)2 * t * plane + (v - (int64_t)t * pv) * 8, hi = lo + plane;
+  const int m = (int)c_mods[t], half = (m - 1) / 2;
+  uint4 q[4] = {*(const uint4 *)(re + lo), *(const uint4 *)(re + hi), *(const uint4 *)(im + lo),
+                *(const uint4 *)(im + hi)};
+  const __nv_bfloat16 *e = (const __nv_bfloat16 *)q;
+  uint4 out[2];
+  __nv_bfloat16 *o = (__nv_bfloat16 *)out;
+#pragma unroll
+  for (int u = 0; u < 8; ++u) {
+    int r = (int)__bfloat162float(e[u]) + 256 * (int)__bfloat162float(e[8 + u]) +
+            (int)__bfloat162float(e[16 + u]) + 256 * (int)__bfloat162float(e[24 + u]);
+    if (r > half)
+      r -= m;
+    else if (r < -half)
+      r += m;
+    const int l = ((r + 128) & 255) - 128;
+    o[u] = __int2bfloat16_rn(l);
+    o[8 + u] = __int2bfloat16_rn((r - l) / 256);
+  }
+  *(uint4 *)(sum + lo) = out[0];
+  *(uint4 *)(sum + hi) = out[1];
+}
+
+// Eq. 3 on the residue products, modulus by modulus (values in [0, m_t)): z_re = z_1 - z_2 and
+// z_im = z_3 - z_1 - z_2 mod m_t, with z_1, z_2, z_3 those of X_re Y_re, X_im Y_im and
+// (X_re + X_im)(Y_re + Y_im) in planes [0, NM), [NM, 2 NM), [2 NM, 3 NM) of `z`.  In place: z_re
+// over z_1, z_im over z_2.  Eight entries per thread (plane is a multiple of 8).
+__global__ void z3m_kernel(uint16_t *z, int NM, int64_t plane) {
+  const int64_t pv = plane / 8;
+  const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (v >= (int64_t)NM * pv) return;
+  const int t = (int)(v / pv);
+  const int64_t o1 = (int64_t)t * plane + (v - (int64_t)t * pv) * 8;
+  const int64_t o2 = o1 + (int64_t)NM * plane, o3 = o2 + (int64_t)NM * plane;
+  const int m = (int)c_mods[t];
+  uint4 q[3] = {*(const uint4 *)(z + o1), *(const uint4 *)(z + o2), *(const uint4 *)(z + o3)};
+  const uint16_t *e = (const uint16_t *)q;
+  uint4 out[2];
+  uint16_t *w = (uint16_t *)out;
+#pragma unroll
+  for (int u = 0; u < 8; ++u) {
+    const int a = e[u], b = e[8 + u], c = e[16 + u];
+    int re = a - b, im = c - a - b;
+    if (re < 0) re += m;
+    if (im < 0) im += m;
+    if (im < 0) im += m;
+    w[u] = (uint16_t)re;
+    w[8 + u] = (uint16_t)im;
+  }
+  *(uint4 *)(z + o1) = out[0];
+  *(uint4 *)(z + o2) = out[1];
+}
+
 // ------------------------------------------------------------------------- workspace and driver
 
 struct BlockWs {
@@ -2392,12 +2514,15 @@ struct BlockWs {
   size_t acc[2], err[2], rman[2], rexp[2], ilimbs[2], iexp[2], iflags[2], irman[2], irexp[2], bk[2];
   // multimodular engine: residue planes, residue products, tables
   size_t resA, resB, cdig, ccar, craw;
+  // complex product by eq. 3: residue planes of the parts and their sum, three residue products
+  size_t r3A, r3B, z3;
   size_t total;
   int Smax, NDmax, Gmax, Gr, maxb, nacc, NMmax, NMWmax;
   int64_t Kp, Mp, Np;
 };
 
-static BlockWs block_ws(arbgpu_ctx *ctx, int64_t M, int64_t K, int64_t N, int prec, bool cplx) {
+static BlockWs block_ws(arbgpu_ctx *ctx, int64_t M, int64_t K, int64_t N, int prec, bool cplx,
+                        bool m3) {
   BlockWs w{};
   const int64_t hmax = (5LL * prec) / 4 + 192;
   w.Smax = (int)((hmax + 2 + 7) / 8);
@@ -2468,14 +2593,19 @@ static BlockWs block_ws(arbgpu_ctx *ctx, int64_t M, int64_t K, int64_t N, int pr
   w.cdig = take((size_t)3 * w.NMmax * w.Mp * w.Np);
   w.craw = take((size_t)2 * 8 * w.Mp * w.Np);  // the two radius products as int64
   w.ccar = take(256);  // the multimodular GEMM writes no carries
+  if (cplx && m3) {
+    w.r3A = take((size_t)3 * 2 * w.NMmax * M * w.Kp * 2);
+    w.r3B = take((size_t)3 * 2 * w.NMmax * N * w.Kp * 2);
+    w.z3 = take((size_t)3 * w.NMmax * w.Mp * w.Np * 2);
+  }
   w.total = off;
   return w;
 }
 
 size_t block_workspace_size(arbgpu_ctx *ctx, int64_t M, int64_t K, int64_t N, int prec,
-                            bool cplx) {
+                            bool cplx, bool m3) {
   if (M <= 0 || N <= 0 || K <= 0) return 0;
-  return block_ws(ctx, M, K, N, prec, cplx).total;
+  return block_ws(ctx, M, K, N, prec, cplx, m3).total;
 }
 
 // Line statistics of one block (pointers into the whole-range or the per-block arrays).
@@ -2516,6 +2646,36 @@ static bool choose_crt(int SA, int SB, int NM, int64_t M, int64_t N, int64_t Kp,
   const double crt = t_mma * 4.0 * NM * (double)Kp * MN + t_crt * NM * nw32 * MN +
                      t_res * NM * nch * (double)Kp * (double)(M + N);
   return crt < digits;
+}
+
+// The radius products of a block on the digit engine, from the operands the split wrote at rA1 /
+// rB1 (the second operands follow at this block's Kp): P1 = U(|A|) V(R_B) when B has radii,
+// P2 = U(R_A) V(|B| + R_B) when A has radii, one launch when both are needed.
+static arbgpu_status radius_gemm(arbgpu_ctx *ctx, const BlockWs &w, uint8_t *ws, int64_t M,
+                                 int64_t N, int64_t Kp, bool radA, bool radB, cudaStream_t s,
+                                 IntProduct *rp1, IntProduct *rp2) {
+  const int NDr = 2 * BL_SR - 1;
+  *rp1 = IntProduct{};
+  *rp2 = IntProduct{};
+  if (!radA && !radB) return ARBGPU_OK;
+  __nv_bfloat16 *rA1 = (__nv_bfloat16 *)(ws + w.rA1), *rA2 = rA1 + (size_t)BL_SR * M * Kp;
+  __nv_bfloat16 *rB1 = (__nv_bfloat16 *)(ws + w.rB1), *rB2 = rB1 + (size_t)BL_SR * N * Kp;
+  const bool both = radA && radB;
+  DigitGemmArgs g{radB ? rA1 : rA2, radB ? rB1 : rB2, (int)M, (int)N, Kp, BL_SR, BL_SR, w.Gr,
+                  ws + (radB ? w.r1dig : w.r2dig),
+                  (int32_t *)(ws + (radB ? w.r1car : w.r2car)), "digit_gemm_rad",
+                  both ? 2 : 1};
+  arbgpu_status stg = launch_digit_gemm(ctx, g, s);
+  if (stg != ARBGPU_OK) return stg;
+  if (radB) {
+    *rp1 = IntProduct{ws + w.r1dig, (int32_t *)(ws + w.r1car), NDr, w.Gr, {}, 0, {}};
+    digit_gemm_group_ends(BL_SR, BL_SR, w.Gr, rp1->ends.e);
+  }
+  if (radA) {
+    *rp2 = IntProduct{ws + w.r2dig, (int32_t *)(ws + w.r2car), NDr, w.Gr, {}, 0, {}};
+    digit_gemm_group_ends(BL_SR, BL_SR, w.Gr, rp2->ends.e);
+  }
+  return ARBGPU_OK;
 }
 
 // Split the block [k0, k0 + Kb) and run its products: T = (E A)(B F), and the radius products
@@ -2643,28 +2803,39 @@ static arbgpu_status run_block(arbgpu_ctx *ctx, const BlockWs &w, uint8_t *ws, c
     *mid = IntProduct{ws + w.mdig, (int32_t *)(ws + w.mcar), ND, G, {}, 0, {}};
     digit_gemm_group_ends(SA, SB, G, mid->ends.e);
   }
-  const int NDr = 2 * BL_SR - 1;
+  return radius_gemm(ctx, w, ws, M, N, Kp, radA, radB, s, rp1, rp2);
+}
+
+// Radius products alone (their operands by the digit split, then radius_gemm): those of the
+// block [k0, k0 + Kb) of X Y under the lines `ln`.
+static arbgpu_status run_radius(arbgpu_ctx *ctx, const BlockWs &w, uint8_t *ws,
+                                const BallsView &Av, const BallsView &Bv, int64_t M, int64_t N,
+                                int64_t lda, int64_t ldb, int64_t k0, int64_t Kb, bool radA,
+                                bool radB, const Lines &ln, cudaStream_t s, IntProduct *rp1,
+                                IntProduct *rp2) {
+  const int64_t Kp = (Kb + TG_BK - 1) / TG_BK * TG_BK;
   *rp1 = IntProduct{};
   *rp2 = IntProduct{};
-  if (radA || radB) {
-    // P1 = U(|A|) V(R_B) and P2 = U(R_A) V(|B| + R_B): one launch when both are needed
-    const bool both = radA && radB;
-    DigitGemmArgs g{radB ? rA1 : rA2, radB ? rB1 : rB2, (int)M, (int)N, Kp, BL_SR, BL_SR, w.Gr,
-                    ws + (radB ? w.r1dig : w.r2dig),
-                    (int32_t *)(ws + (radB ? w.r1car : w.r2car)), "digit_gemm_rad",
-                    both ? 2 : 1};
-    arbgpu_status stg = launch_digit_gemm(ctx, g, s);
-    if (stg != ARBGPU_OK) return stg;
-    if (radB) {
-      *rp1 = IntProduct{ws + w.r1dig, (int32_t *)(ws + w.r1car), NDr, w.Gr, {}, 0, {}};
-      digit_gemm_group_ends(BL_SR, BL_SR, w.Gr, rp1->ends.e);
-    }
-    if (radA) {
-      *rp2 = IntProduct{ws + w.r2dig, (int32_t *)(ws + w.r2car), NDr, w.Gr, {}, 0, {}};
-      digit_gemm_group_ends(BL_SR, BL_SR, w.Gr, rp2->ends.e);
-    }
+  if (!radA && !radB) return ARBGPU_OK;
+  __nv_bfloat16 *rA1 = (__nv_bfloat16 *)(ws + w.rA1), *rA2 = rA1 + (size_t)BL_SR * M * Kp;
+  __nv_bfloat16 *rB1 = (__nv_bfloat16 *)(ws + w.rB1), *rB2 = rB1 + (size_t)BL_SR * N * Kp;
+  {
+    const int64_t n = M * Kp;
+    SplitOut o{nullptr, radB ? rA1 : nullptr, radA ? rA2 : nullptr};
+    LaunchScope sc(ctx, s, "split_a", n);
+    split_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(Av, false, M, k0, Kb, Kp, lda, 0,
+                                                             ln.rbot, ln.rtop, ln.rrad, nullptr, o);
   }
-  return ARBGPU_OK;
+  {
+    const int64_t n = N * Kp;
+    SplitOut o{nullptr, radB ? rB1 : nullptr, radA ? rB2 : nullptr};
+    LaunchScope sc(ctx, s, "split_b", n);
+    split_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(Bv, true, N, k0, Kb, Kp, ldb, 0,
+                                                             ln.cbot, ln.ctop, ln.crad, ln.cplus,
+                                                             o);
+  }
+  if (cudaGetLastError() != cudaSuccess) return ARBGPU_ERR_CUDA;
+  return radius_gemm(ctx, w, ws, M, N, Kp, radA, radB, s, rp1, rp2);
 }
 
 // Statistics of one real product X * Y from the whole-range scans of its parts.
@@ -2781,6 +2952,167 @@ static arbgpu_status accumulate_product(arbgpu_ctx *ctx, const BlockWs &w, uint8
   return cudaGetLastError() == cudaSuccess ? ARBGPU_OK : ARBGPU_ERR_CUDA;
 }
 
+// ---- complex product by eq. 3 (Section IV-C: three real products of the midpoint matrices when
+// the entries are uniformly scaled).  With one exponent per row of A and per column of B shared by
+// both parts (merge_parts_kernel), X_re, X_im, Y_re, Y_im are integer matrices and
+//   P_1 = X_re Y_re,  P_2 = X_im Y_im,  P_3 = (X_re + X_im)(Y_re + Y_im),
+//   Re = P_1 - P_2,  Im = P_3 - P_1 - P_2
+// hold exactly.  The three products run as one batch of residue products; Re and Im are formed
+// modulus by modulus and reconstructed, so |Re|, |Im| < 2 K 2^(hA + hB) sets the modulus count.
+// The radii are the four real radius products of the 4M path.
+struct Plan3M {
+  bool ok;
+  int64_t hA, hB;
+  int NM, nch;
+  const CrtPlan *plan;
+  RtLayout L;
+  int64_t *rtop, *rbot, *ctop, *cbot;  // the shared lines
+};
+
+// Merge the parts' lines and decide: ok when the shared scaling fits one block of height
+// <= h (the bound of Algorithm 2 for the operands' precisions) and the multimodular engine with
+// the tensor-core residue kernel takes the sizes.  One statistics read-back.
+static arbgpu_status plan_3m(arbgpu_ctx *ctx, const BlockWs &w, uint8_t *ws, const Lines *rowsL,
+                             const Lines *colsL, const BlockStats *hst, int64_t M, int64_t K,
+                             int64_t N, int prec, cudaStream_t s, Plan3M *p) {
+  p->ok = false;
+  if (!w.r3A) return ARBGPU_OK;
+  p->rtop = (int64_t *)(ws + w.brtop);
+  p->rbot = (int64_t *)(ws + w.brbot);
+  p->ctop = (int64_t *)(ws + w.bctop);
+  p->cbot = (int64_t *)(ws + w.bcbot);
+  BlockStats *dst = (BlockStats *)(ws + w.bstats);
+  {
+    LaunchScope sc(ctx, s, "merge_parts", M + N);
+    merge_parts_kernel<<<1, 1024, 0, s>>>(rowsL[0].rtop, rowsL[0].rbot, rowsL[1].rtop,
+                                          rowsL[1].rbot, M, p->rtop, p->rbot, colsL[0].ctop,
+                                          colsL[0].cbot, colsL[1].ctop, colsL[1].cbot, N, p->ctop,
+                                          p->cbot, dst);
+    if (cudaGetLastError() != cudaSuccess) return ARBGPU_ERR_CUDA;
+  }
+  BlockStats hm{};
+  const arbgpu_status st = read_stats(ctx, dst, &hm, 1, s);
+  if (st != ARBGPU_OK) return st;
+  if (hm.hA == INT64_MIN || hm.hB == INT64_MIN) return ARBGPU_OK;  // a zero operand
+  BlockStats hs{};
+  hs.pA = hst[0].pA > hst[1].pA ? hst[0].pA : hst[1].pA;
+  hs.pB = hst[2].pB > hst[3].pB ? hst[2].pB : hst[3].pB;
+  const int64_t h = height_bound(prec, hs);
+  if (hm.hA > h || hm.hB > h) return ARBGPU_OK;
+  p->hA = hm.hA;
+  p->hB = hm.hB;
+  p->NM = crt_moduli_for_bits((int)(p->hA + p->hB + bit_length(K) + 3));
+  if (p->NM > w.NMmax) return ARBGPU_OK;
+  p->plan = crt_plan(p->NM);
+  if (!p->plan || p->plan->NMW + 1 > RD_MAXW) return ARBGPU_OK;
+  p->nch = (int)(((p->hA > p->hB ? p->hA : p->hB) + 2 + 31) / 32) + 1;
+  if (!residue_tc_layout(p->nch, p->NM, false, (M > N ? M : N) * w.Kp, &p->L)) return ARBGPU_OK;
+  p->ok = true;
+  return ARBGPU_OK;
+}
+
+// Run the planned eq. 3 product into the accumulators av[0] (Re) and av[1] (Im).
+static arbgpu_status run_3m(arbgpu_ctx *ctx, const BlockWs &w, uint8_t *ws, const Plan3M &p,
+                            const BallsView *Av, const BallsView *Bv, const Lines *rowsL,
+                            const Lines *colsL, const BlockStats *hst, int64_t M, int64_t K,
+                            int64_t N, int64_t lda, int64_t ldb, const AccView *av,
+                            cudaStream_t s) {
+  const int NM = p.NM;
+  const int64_t Kp = w.Kp;
+  if (ensure_crt_constants(ctx->device) != ARBGPU_OK) return ARBGPU_ERR_CUDA;
+  CrtDevTables dt{};
+  if (crt_device_tables(ctx, p.plan, &dt) != ARBGPU_OK) return ARBGPU_ERR_CUDA;
+  // (the accumulator reconstructs on the CUDA cores: no tensor-core weight table)
+  const CrtTables ct{dt.Q32,        dt.M32,  dt.y,      dt.rinv,    NM, p.plan->NMW,
+                     p.plan->NW32P, nullptr, dt.mbytes, p.plan->NQ, p.plan->NQP};
+  // residue planes [re | im | re + im] of each side, 2 NM planes each
+  __nv_bfloat16 *xr = (__nv_bfloat16 *)(ws + w.r3A), *yr = (__nv_bfloat16 *)(ws + w.r3B);
+  const size_t setA = (size_t)2 * NM * M * Kp, setB = (size_t)2 * NM * N * Kp;
+  for (int q = 0; q < 2; ++q) {
+    LaunchScope sc(ctx, s, "residues",
+                   (M * (8 * (int64_t)Av[q].nlimbs + 24) + N * (8 * (int64_t)Bv[q].nlimbs + 24)) *
+                           K +
+                       (int64_t)p.L.NPL * (M + N) * Kp * 2);
+    RtArgs ra{};
+    ra.side[0] = RtSide{Av[q], M,         lda, p.rbot, p.rtop, rowsL[q].rrad, nullptr,
+                        SplitOut{}, dt.wtab};
+    ra.side[1] = RtSide{Bv[q], N, ldb, p.cbot, p.ctop, colsL[q].crad, colsL[q].cplus,
+                        SplitOut{}, dt.wtab + (size_t)p.plan->NPAD * 128};
+    ra.k0 = 0, ra.K = K, ra.Kp = Kp, ra.NM = NM, ra.rinv = dt.rinv;
+    const arbgpu_status st = launch_residues_tc(ctx, p.L, p.nch, s, ra, xr + q * setA,
+                                                yr + q * setB);
+    if (st != ARBGPU_OK) return st;
+  }
+  {
+    const int64_t nv = (int64_t)NM * (M * Kp / 8 + N * Kp / 8);
+    LaunchScope sc(ctx, s, "residue_sum", nv * 8);
+    residue_sum_kernel<<<(unsigned)((nv + 255) / 256), 256, 0, s>>>(
+        xr, xr + setA, xr + 2 * setA, M * Kp, yr, yr + setB, yr + 2 * setB, N * Kp, NM);
+    if (cudaGetLastError() != cudaSuccess) return ARBGPU_ERR_CUDA;
+  }
+  uint16_t *z = (uint16_t *)(ws + w.z3);
+  DigitGemmArgs g{xr, yr, (int)M, (int)N, Kp, 2, 2, 1, ws + w.z3, (int32_t *)(ws + w.ccar),
+                  "crt_gemm", 3 * NM};
+  g.zout = z;
+  g.ztab = dt.ztab;
+  g.zinv = dt.inv;
+  arbgpu_status stg = launch_digit_gemm(ctx, g, s);
+  if (stg != ARBGPU_OK) return stg;
+  const int64_t plane = w.Mp * w.Np;
+  {
+    const int64_t nv = (int64_t)NM * (plane / 8);
+    LaunchScope sc(ctx, s, "z3m", nv * 8);
+    z3m_kernel<<<(unsigned)((nv + 255) / 256), 256, 0, s>>>(z, NM, plane);
+    if (cudaGetLastError() != cudaSuccess) return ARBGPU_ERR_CUDA;
+  }
+  for (int q = 0; q < 2; ++q) {
+    AccArgs aa{};
+    aa.mid = IntProduct{(const uint8_t *)(z + (size_t)q * NM * plane), nullptr, 3, 1, {}, 1, ct};
+    aa.mid.ends.e[0] = 3;
+    aa.rtop = p.rtop;
+    aa.rbot = p.rbot;
+    aa.ctop = p.ctop;
+    aa.cbot = p.cbot;
+    aa.v = av[q];
+    aa.M = M;
+    aa.N = N;
+    aa.Mp = w.Mp;
+    aa.Np = w.Np;
+    aa.skip_rad = 1;
+    LaunchScope sc(ctx, s, "accumulate", M * N);
+    accumulate_kernel<<<(unsigned)((M * N + 127) / 128), 128, 0, s>>>(aa);
+  }
+  // radii: Re from A_re B_re and A_im B_im, Im from A_re B_im and A_im B_re
+  const int pairs[4][3] = {{0, 0, 0}, {0, 1, 1}, {1, 0, 1}, {1, 1, 0}};
+  for (const auto &pr : pairs) {
+    const int part = pr[0], xa = pr[1], yb = pr[2];
+    const bool radA = hst[xa].radA != 0, radB = hst[2 + yb].radB != 0;
+    if (!radA && !radB) continue;
+    const Lines ln{rowsL[xa].rtop, rowsL[xa].rbot, rowsL[xa].rrad, colsL[yb].ctop,
+                   colsL[yb].cbot, colsL[yb].crad, colsL[yb].cplus};
+    AccArgs aa{};
+    const arbgpu_status st = run_radius(ctx, w, ws, Av[xa], Bv[yb], M, N, lda, ldb, 0, K, radA,
+                                        radB, ln, s, &aa.rp1, &aa.rp2);
+    if (st != ARBGPU_OK) return st;
+    aa.rtop = ln.rtop;
+    aa.rbot = ln.rbot;
+    aa.rrad = ln.rrad;
+    aa.ctop = ln.ctop;
+    aa.cbot = ln.cbot;
+    aa.crad = ln.crad;
+    aa.cplus = ln.cplus;
+    aa.v = av[part];
+    aa.M = M;
+    aa.N = N;
+    aa.Mp = w.Mp;
+    aa.Np = w.Np;
+    aa.skip_mid = 1;
+    LaunchScope sc(ctx, s, "accumulate", M * N);
+    accumulate_kernel<<<(unsigned)((M * N + 127) / 128), 128, 0, s>>>(aa);
+  }
+  return cudaGetLastError() == cudaSuccess ? ARBGPU_OK : ARBGPU_ERR_CUDA;
+}
+
 // Ball matrix product by Algorithm 2 (real, or complex by four real products, Section IV-C).
 // Returns ARBGPU_ERR_LIMIT when the inputs hold special values or exceed the path's limits (the
 // caller then uses the classical algorithm).
@@ -2852,12 +3184,12 @@ arbgpu_status block_scan_launch(arbgpu_ctx *ctx, const arbgpu_balls *A, const ar
 // `hst`, read after the scans finished) and the block workspace.
 arbgpu_status block_finish(arbgpu_ctx *ctx, const arbgpu_balls *C, const arbgpu_balls *A,
                            const arbgpu_balls *B, int64_t M, int64_t K, int64_t N, int64_t lda,
-                           int64_t ldb, int64_t ldc, int prec, bool cplx, void *region,
+                           int64_t ldb, int64_t ldc, int prec, bool cplx, bool m3, void *region,
                            const BlockStats *hst, void *workspace, size_t ws_bytes,
                            cudaStream_t s, bool *used_block) {
   *used_block = false;
   const int parts = cplx ? 2 : 1;
-  BlockWs w = block_ws(ctx, M, K, N, prec, cplx);
+  BlockWs w = block_ws(ctx, M, K, N, prec, cplx, m3);
   if (!workspace || ws_bytes < w.total) return ARBGPU_ERR_WORKSPACE;
   uint8_t *ws = (uint8_t *)workspace;
   const ScanRegion sr = scan_region_at((uint8_t *)region, M, N, cplx);
@@ -2913,6 +3245,13 @@ arbgpu_status block_finish(arbgpu_ctx *ctx, const arbgpu_balls *C, const arbgpu_
     }
   }
 
+  // complex by eq. 3 when the shared scaling of the parts fits one block
+  Plan3M p3{};
+  if (cplx && m3) {
+    const arbgpu_status st = plan_3m(ctx, w, ws, rowsL, colsL, hst, M, K, N, prec, s, &p3);
+    if (st != ARBGPU_OK) return st;
+  }
+
   // ---- accumulate every real product into its output part, then finish each part
   // real: C = A B.  complex: Re C = Ar Br - Ai Bi, Im C = Ar Bi + Ai Br (four real products).
   struct Prod {
@@ -2938,13 +3277,23 @@ arbgpu_status block_finish(arbgpu_ctx *ctx, const arbgpu_balls *C, const arbgpu_
         av[q].ftop_c[np] = colsL[prods[t].yb].ctop;
         ++np;
       }
+    if (p3.ok) {  // both parts' products lie under the shared lines
+      av[q].ftop_r[0] = p3.rtop;
+      av[q].ftop_c[0] = p3.ctop;
+      av[q].ftop_r[1] = av[q].ftop_c[1] = nullptr;
+    }
     if (cudaMemsetAsync(av[q].acc, 0, 8 * (size_t)w.nacc * MN, s) != cudaSuccess ||
         cudaMemsetAsync(av[q].err, 0, 4 * MN, s) != cudaSuccess ||
         cudaMemsetAsync(av[q].rman, 0, 4 * MN, s) != cudaSuccess ||
         cudaMemsetAsync(av[q].rexp, 0, 8 * MN, s) != cudaSuccess)
       return ARBGPU_ERR_CUDA;
   }
-  for (int t = 0; t < nprods; ++t) {
+  if (p3.ok) {
+    const arbgpu_status st3 =
+        run_3m(ctx, w, ws, p3, Av, Bv, rowsL, colsL, hst, M, K, N, lda, ldb, av, s);
+    if (st3 != ARBGPU_OK) return st3;
+  }
+  for (int t = 0; t < (p3.ok ? 0 : nprods); ++t) {
     const Prod &pr = prods[t];
     const BlockStats hs = merge_stats(hst[pr.xa], hst[2 + pr.yb]);
     arbgpu_status st1 = accumulate_product(ctx, w, ws, Av[pr.xa], Bv[pr.yb], M, K, N, lda, ldb,
@@ -3022,11 +3371,11 @@ arbgpu_status read_stats(arbgpu_ctx *ctx, const BlockStats *dev, BlockStats *hos
 
 arbgpu_status block_matmul(arbgpu_ctx *ctx, const arbgpu_balls *C, const arbgpu_balls *A,
                            const arbgpu_balls *B, int64_t M, int64_t K, int64_t N, int64_t lda,
-                           int64_t ldb, int64_t ldc, int prec, bool cplx, void *workspace,
-                           size_t ws_bytes, cudaStream_t s, bool *used_block) {
+                           int64_t ldb, int64_t ldc, int prec, bool cplx, bool m3,
+                           void *workspace, size_t ws_bytes, cudaStream_t s, bool *used_block) {
   *used_block = false;
   if (!block_accepts(A, B, K, cplx)) return ARBGPU_ERR_LIMIT;
-  BlockWs w = block_ws(ctx, M, K, N, prec, cplx);
+  BlockWs w = block_ws(ctx, M, K, N, prec, cplx, m3);
   if (!workspace || ws_bytes < w.total) return ARBGPU_ERR_WORKSPACE;
   void *region = (uint8_t *)workspace + w.scan;
   arbgpu_status st = block_scan_launch(ctx, A, B, M, K, N, lda, ldb, cplx, region, nullptr, s);
@@ -3034,8 +3383,8 @@ arbgpu_status block_matmul(arbgpu_ctx *ctx, const arbgpu_balls *C, const arbgpu_
   BlockStats hst[4];
   st = read_stats(ctx, scan_region_at((uint8_t *)region, M, N, cplx).pst, hst, 4, s);
   if (st != ARBGPU_OK) return st;
-  return block_finish(ctx, C, A, B, M, K, N, lda, ldb, ldc, prec, cplx, region, hst, workspace,
-                      ws_bytes, s, used_block);
+  return block_finish(ctx, C, A, B, M, K, N, lda, ldb, ldc, prec, cplx, m3, region, hst,
+                      workspace, ws_bytes, s, used_block);
 }
 
 }  // namespace arbgpu

@@ -124,19 +124,21 @@ arbgpu_status block_scan_launch(arbgpu_ctx *ctx, const arbgpu_balls *A, const ar
                                 bool cplx, void *region, BlockStats *stats, cudaStream_t s);
 arbgpu_status block_finish(arbgpu_ctx *ctx, const arbgpu_balls *C, const arbgpu_balls *A,
                            const arbgpu_balls *B, int64_t M, int64_t K, int64_t N, int64_t lda,
-                           int64_t ldb, int64_t ldc, int prec, bool cplx, void *region,
+                           int64_t ldb, int64_t ldc, int prec, bool cplx, bool m3, void *region,
                            const BlockStats *hst, void *workspace, size_t ws_bytes,
                            cudaStream_t s, bool *used_block);
 
 // Block algorithm (block.cu): real or complex (C, A, B point to one or two arbgpu_balls).  Returns
 // ARBGPU_ERR_LIMIT (and *used_block = false) when the inputs hold special values or exceed the
 // path's limits.
+// m3: complex midpoints by eq. 3 (three real products) where the parts share one scaling in a
+// single block; the workspace then holds the three products' planes.
 size_t block_workspace_size(arbgpu_ctx *ctx, int64_t M, int64_t K, int64_t N, int prec,
-                            bool cplx);
+                            bool cplx, bool m3);
 arbgpu_status block_matmul(arbgpu_ctx *ctx, const arbgpu_balls *C, const arbgpu_balls *A,
                            const arbgpu_balls *B, int64_t M, int64_t K, int64_t N, int64_t lda,
-                           int64_t ldb, int64_t ldc, int prec, bool cplx, void *workspace,
-                           size_t ws_bytes, cudaStream_t s, bool *used_block);
+                           int64_t ldb, int64_t ldc, int prec, bool cplx, bool m3,
+                           void *workspace, size_t ws_bytes, cudaStream_t s, bool *used_block);
 
 // Dot products that finish the basecase blocks of Algorithm 2 (dot_basecase.cu): entry (i, j) of C
 // is initial[i*N + j] + sum over the tagged indices e = bk[t] (k = e >> 2, combo = e & 3) of
@@ -173,13 +175,13 @@ constexpr int CRT_MAX_MODULI = 256;
 struct CrtPlan {
   int NM, NMW, NCHP, NW32P;       // moduli, limbs of M, columns of pow32, columns of Q32
   std::vector<uint32_t> mods;     // m_t
-  std::vector<uint64_t> inv;      // floor((2^64 - 1) / m_t)
+  std::vector<uint64_t> inv;      // [3 NM]: floor((2^64 - 1) / m_(t mod NM))
   std::vector<uint32_t> pow32;    // [NM][NCHP]: 2^(32c) mod m_t
   std::vector<uint32_t> Q32;      // [NM][NW32P]: M / m_t in 32-bit limbs, zero padded
   std::vector<uint32_t> M32;      // [NW32P]: M in 32-bit limbs
   std::vector<uint32_t> y;        // [NM]: (M / m_t)^-1 mod m_t
   std::vector<float> rinv;        // [NM]: 1 / m_t rounded to float
-  std::vector<uint32_t> ztab;     // [NM][4]: m_t, 0, 0, 0
+  std::vector<uint32_t> ztab;     // [3 NM][4]: m_(t mod NM), 0, 0, 0
   std::vector<uint64_t> M;        // M
   int NPAD;                       // 2 NM rounded up to a multiple of 16
   // [2][NPAD][128] BF16 bits: row 2t + b of operand side o holds byte b (balanced, 256 h + l) of

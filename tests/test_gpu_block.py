@@ -215,14 +215,14 @@ def test_identity_times_matrix(arb):
         assert int(out.rad_man[idx]) == 0
 
 
-def run_cmm(arb, A2, B2, M, K, N, prec, alg, trace=False):
+def run_cmm(arb, A2, B2, M, K, N, prec, alg, trace=False, flags=0):
     nl = (prec + 63) // 64
     ctx = arb.default_context()
     C2 = [arb.Balls.empty(M * N, nl), arb.Balls.empty(M * N, nl)]
     if trace:
         ctx.trace(True)
     arb.mat_mul(C2, [arb.Balls.from_raw(a) for a in A2], [arb.Balls.from_raw(b) for b in B2], M, K,
-                N, prec, alg=alg)
+                N, prec, alg=alg, flags=flags)
     st = ctx.status()
     names = [r[0] for r in ctx.trace_read()] if trace else []
     ctx.trace(False)
@@ -257,6 +257,77 @@ def test_complex_block_uniform(arb):
     rng2 = np.random.default_rng(4)
     check_complex(outs, A2, B2, n, n, n, p, [(int(a), int(b)) for a, b in
                                              zip(rng2.integers(0, n, 80), rng2.integers(0, n, 80))])
+
+
+@pytest.mark.parametrize("M,K,N,prec,spread", [(96, 96, 96, 128, 10), (70, 100, 90, 256, 20),
+                                                (33, 200, 130, 64, 3)])
+def test_complex_3m_exact_rounding(arb, M, K, N, prec, spread):
+    """Eq. 3 (Section IV-C): with one scaling per row of A and column of B shared by both parts,
+    Re = P1 - P2 and Im = P3 - P1 - P2 from three exact products.  The integers are exact, so
+    every sampled midpoint is RNE_p of the exact part, the same as the four-product path gives,
+    and every ball contains the exact value."""
+    rng = np.random.default_rng(60 + M)
+    nl = (prec + 63) // 64
+    A2 = [random_balls(rng, M * K, nl, prec, -spread, spread, rad_bits=prec - 8,
+                       rad_zero_frac=0.5) for _ in "ri"]
+    B2 = [random_balls(rng, K * N, nl, prec, -spread, spread, rad_bits=prec - 8,
+                       rad_zero_frac=0.5) for _ in "ri"]
+    o3, n3 = run_cmm(arb, A2, B2, M, K, N, prec, arb.ALG_BLOCK, trace=True,
+                     flags=arb.MM_COMPLEX_3M)
+    assert "z3m" in n3 and "residue_sum" in n3
+    assert n3.count("crt_gemm") == 1 and n3.count("residues") == 2
+    o4, n4 = run_cmm(arb, A2, B2, M, K, N, prec, arb.ALG_BLOCK, trace=True)
+    assert "z3m" not in n4
+    for a, b in zip(o3, o4):
+        for f in ("limbs", "exp", "flags"):
+            assert np.array_equal(getattr(a, f), getattr(b, f)), f
+    rng2 = np.random.default_rng(6)
+    entries = [(int(a), int(b)) for a, b in zip(rng2.integers(0, M, 40), rng2.integers(0, N, 40))]
+    check_complex(o3, A2, B2, M, K, N, prec, entries)
+    for i, j in entries:
+        re, im = X.complex_dot_terms(A2, [i * K + k for k in range(K)], B2,
+                                     [k * N + j for k in range(K)])
+        idx = i * N + j
+        for part, terms in ((0, re), (1, im)):
+            m_ref = X.result_exact(terms, prec, nl)[0]
+            limbs, e, fl = X.encode_mid(m_ref, nl)
+            got = ([int(o3[part].limbs[k, idx]) for k in range(nl)], int(o3[part].exp[idx]),
+                   int(o3[part].flags[idx]))
+            assert got == (limbs, e, fl), (part, i, j)
+
+
+def test_complex_3m_exact_inputs_and_zero_part(arb):
+    """Eq. 3 with exact inputs whose imaginary parts are zero in A: Im C = Ar Bi exactly, zero
+    radii wherever the exact sums fit in p bits (small integers)."""
+    rng = np.random.default_rng(70)
+    M, K, N, p = 64, 64, 64, 128
+    A2 = [random_balls(rng, M * K, 2, 8, 8, 8) for _ in "ri"]
+    B2 = [random_balls(rng, K * N, 2, 8, 8, 8) for _ in "ri"]
+    A2[1].flags[:] = 2
+    A2[1].limbs[:] = 0
+    A2[1].exp[:] = 0
+    o3, n3 = run_cmm(arb, A2, B2, M, K, N, p, arb.ALG_BLOCK, trace=True, flags=arb.MM_COMPLEX_3M)
+    assert "z3m" in n3
+    for idx in range(0, M * N, 37):
+        for part in (0, 1):
+            assert int(o3[part].rad_man[idx]) == 0
+    rng2 = np.random.default_rng(7)
+    check_complex(o3, A2, B2, M, K, N, p,
+                  [(int(a), int(b)) for a, b in zip(rng2.integers(0, M, 30), rng2.integers(0, N, 30))])
+
+
+def test_complex_3m_falls_back_to_4m_for_several_blocks(arb):
+    """When the shared scaling needs several blocks (Laplace exponents along the inner index), the
+    flag leaves the four-product path in place and the result is still rigorous."""
+    from synth.workloads import complex_matmul_laplace
+    case = complex_matmul_laplace(n=128, structured=True)
+    outs, names = run_cmm(arb, case.A, case.B, 128, 128, 128, 128, arb.ALG_BLOCK, trace=True,
+                          flags=arb.MM_COMPLEX_3M)
+    assert "z3m" not in names and "plan" in names
+    rng2 = np.random.default_rng(8)
+    check_complex(outs, case.A, case.B, 128, 128, 128, 128,
+                  [(int(a), int(b)) for a, b in zip(rng2.integers(0, 128, 30),
+                                                    rng2.integers(0, 128, 30))])
 
 
 @pytest.mark.parametrize("structured", [True, False])
