@@ -1418,7 +1418,18 @@ struct RoundArgs {
   BallsOut C;
   int64_t M, N, ldc, Mp, Np;
   int prec;
+  // optional radius bound added to every entry ([M][N], index i N + j; null when absent): the
+  // radius products of the complex product by eq. 3, summed beforehand
+  const uint32_t *xrman;
+  const int64_t *xrexp;
 };
+
+__device__ __forceinline__ Mag with_extra_radius(const RoundArgs &a, int64_t i, int64_t j, Mag r) {
+  if (!a.xrman) return r;
+  const int64_t o = i * a.N + j;
+  const Mag x{__ldg(a.xrman + o), __ldg(a.xrexp + o)};
+  return x.man ? mag_add_up(r, x) : r;
+}
 
 __device__ __forceinline__ Mag product_mag(const IntProduct &p, int64_t i, int64_t j, int64_t Mp,
                                            int64_t Np, int64_t base) {
@@ -1547,7 +1558,8 @@ __global__ void block_round_kernel(const RoundArgs a) {
   const int nw = assemble(a.mid, i, j, a.Mp, a.Np, T);
   const bool rowz = a.rtop[i] == INT64_MIN, colz = a.ctop[j] == INT64_MIN;
   const int64_t sigma = (rowz ? 0 : a.rbot[i]) + (colz ? 0 : a.cbot[j]);  // T * 2^sigma
-  const Mag rad = block_radius(a.rp1, a.rp2, a.rtop, a.rrad, a.crad, a.cplus, i, j, a.Mp, a.Np);
+  const Mag rad = with_extra_radius(
+      a, i, j, block_radius(a.rp1, a.rp2, a.rtop, a.rrad, a.crad, a.cplus, i, j, a.Mp, a.Np));
   round_store(T, nw, sigma, 0, rad, a.prec, a.C, i * a.ldc + j);
 }
 
@@ -1786,8 +1798,8 @@ __global__ void __launch_bounds__(128, 6) block_round_regs_kernel(const RoundArg
     digit_assemble_regs<NW>(a.mid, i, j, a.Mp, a.Np, T);
   const bool rowz = a.rtop[i] == INT64_MIN, colz = a.ctop[j] == INT64_MIN;
   const int64_t sigma = (rowz ? 0 : a.rbot[i]) + (colz ? 0 : a.cbot[j]);  // T * 2^sigma
-  const Mag rad =
-      block_radius_regs(a.rp1, a.rp2, a.rtop, a.rrad, a.crad, a.cplus, i, j, a.Mp, a.Np);
+  const Mag rad = with_extra_radius(
+      a, i, j, block_radius_regs(a.rp1, a.rp2, a.rtop, a.rrad, a.crad, a.cplus, i, j, a.Mp, a.Np));
   round_store_regs<NW>(T, sigma, 0, rad, a.prec, a.C, i * a.ldc + j);
 }
 
@@ -2021,8 +2033,9 @@ __global__ void __launch_bounds__(CR_THREADS, 1)
       if (j < ra.N) {
         const bool rowz = ra.rtop[i] == INT64_MIN, colz = ra.ctop[j] == INT64_MIN;
         const int64_t sigma = (rowz ? 0 : ra.rbot[i]) + (colz ? 0 : ra.cbot[j]);
-        const Mag rad = block_radius_regs(ra.rp1, ra.rp2, ra.rtop, ra.rrad, ra.crad, ra.cplus, i,
-                                          j, ra.Mp, ra.Np);
+        const Mag rad = with_extra_radius(ra, i, j,
+                                          block_radius_regs(ra.rp1, ra.rp2, ra.rtop, ra.rrad,
+                                                            ra.crad, ra.cplus, i, j, ra.Mp, ra.Np));
         if (NWIN > 0)
           round_store_window<NW, (NWIN > 0 ? NWIN : 1)>(T, sigma, rad, ra.prec, ra.C,
                                                         i * ra.ldc + j);
@@ -3011,20 +3024,22 @@ static arbgpu_status plan_3m(arbgpu_ctx *ctx, const BlockWs &w, uint8_t *ws, con
   return ARBGPU_OK;
 }
 
-// Run the planned eq. 3 product into the accumulators av[0] (Re) and av[1] (Im).
+// Run the planned eq. 3 product: the radius bounds of each part summed into av[q].rman / rexp
+// (zeroed by the caller), then Re and Im reconstructed and rounded straight into C[0], C[1].
 static arbgpu_status run_3m(arbgpu_ctx *ctx, const BlockWs &w, uint8_t *ws, const Plan3M &p,
-                            const BallsView *Av, const BallsView *Bv, const Lines *rowsL,
-                            const Lines *colsL, const BlockStats *hst, int64_t M, int64_t K,
-                            int64_t N, int64_t lda, int64_t ldb, const AccView *av,
-                            cudaStream_t s) {
+                            const arbgpu_balls *C, const BallsView *Av, const BallsView *Bv,
+                            const Lines *rowsL, const Lines *colsL, const BlockStats *hst,
+                            int64_t M, int64_t K, int64_t N, int64_t lda, int64_t ldb,
+                            int64_t ldc, int prec, const AccView *av, cudaStream_t s) {
   const int NM = p.NM;
   const int64_t Kp = w.Kp;
   if (ensure_crt_constants(ctx->device) != ARBGPU_OK) return ARBGPU_ERR_CUDA;
   CrtDevTables dt{};
   if (crt_device_tables(ctx, p.plan, &dt) != ARBGPU_OK) return ARBGPU_ERR_CUDA;
-  // (the accumulator reconstructs on the CUDA cores: no tensor-core weight table)
-  const CrtTables ct{dt.Q32,        dt.M32,  dt.y,      dt.rinv,    NM, p.plan->NMW,
-                     p.plan->NW32P, nullptr, dt.mbytes, p.plan->NQ, p.plan->NQP};
+  // (the tensor-core reconstruction's weight table exists for NM <= 64)
+  const CrtTables ct{dt.Q32,        dt.M32,                      dt.y,      dt.rinv,
+                     NM,            p.plan->NMW,                 p.plan->NW32P,
+                     NM <= 64 ? dt.crt_wtab : nullptr, dt.mbytes, p.plan->NQ, p.plan->NQP};
   // residue planes [re | im | re + im] of each side, 2 NM planes each
   __nv_bfloat16 *xr = (__nv_bfloat16 *)(ws + w.r3A), *yr = (__nv_bfloat16 *)(ws + w.r3B);
   const size_t setA = (size_t)2 * NM * M * Kp, setB = (size_t)2 * NM * N * Kp;
@@ -3065,24 +3080,7 @@ static arbgpu_status run_3m(arbgpu_ctx *ctx, const BlockWs &w, uint8_t *ws, cons
     z3m_kernel<<<(unsigned)((nv + 255) / 256), 256, 0, s>>>(z, NM, plane);
     if (cudaGetLastError() != cudaSuccess) return ARBGPU_ERR_CUDA;
   }
-  for (int q = 0; q < 2; ++q) {
-    AccArgs aa{};
-    aa.mid = IntProduct{(const uint8_t *)(z + (size_t)q * NM * plane), nullptr, 3, 1, {}, 1, ct};
-    aa.mid.ends.e[0] = 3;
-    aa.rtop = p.rtop;
-    aa.rbot = p.rbot;
-    aa.ctop = p.ctop;
-    aa.cbot = p.cbot;
-    aa.v = av[q];
-    aa.M = M;
-    aa.N = N;
-    aa.Mp = w.Mp;
-    aa.Np = w.Np;
-    aa.skip_rad = 1;
-    LaunchScope sc(ctx, s, "accumulate", M * N);
-    accumulate_kernel<<<(unsigned)((M * N + 127) / 128), 128, 0, s>>>(aa);
-  }
-  // radii: Re from A_re B_re and A_im B_im, Im from A_re B_im and A_im B_re
+  // radii: Re from A_re B_re and A_im B_im, Im from A_re B_im and A_im B_re, summed per entry
   const int pairs[4][3] = {{0, 0, 0}, {0, 1, 1}, {1, 0, 1}, {1, 1, 0}};
   for (const auto &pr : pairs) {
     const int part = pr[0], xa = pr[1], yb = pr[2];
@@ -3109,6 +3107,31 @@ static arbgpu_status run_3m(arbgpu_ctx *ctx, const BlockWs &w, uint8_t *ws, cons
     aa.skip_mid = 1;
     LaunchScope sc(ctx, s, "accumulate", M * N);
     accumulate_kernel<<<(unsigned)((M * N + 127) / 128), 128, 0, s>>>(aa);
+  }
+  if (cudaGetLastError() != cudaSuccess) return ARBGPU_ERR_CUDA;
+  // Re and Im are exact integers under the shared lines: one rounding each, as for a real block
+  for (int q = 0; q < 2; ++q) {
+    RoundArgs ra{};
+    ra.mid = IntProduct{(const uint8_t *)(z + (size_t)q * NM * plane), nullptr, 3, 1, {}, 1, ct};
+    ra.mid.ends.e[0] = 3;
+    ra.rtop = p.rtop;
+    ra.rbot = p.rbot;
+    ra.rrad = rowsL[q].rrad;
+    ra.ctop = p.ctop;
+    ra.cbot = p.cbot;
+    ra.crad = colsL[q].crad;
+    ra.cplus = colsL[q].cplus;
+    ra.C = out_of(C[q]);
+    ra.M = M;
+    ra.N = N;
+    ra.ldc = ldc;
+    ra.Mp = w.Mp;
+    ra.Np = w.Np;
+    ra.prec = prec;
+    ra.xrman = av[q].rman;
+    ra.xrexp = av[q].rexp;
+    LaunchScope sc(ctx, s, "block_round", M * N * (int64_t)NM * (2 * ct.NMW));
+    launch_block_round(ctx, ra, s);
   }
   return cudaGetLastError() == cudaSuccess ? ARBGPU_OK : ARBGPU_ERR_CUDA;
 }
@@ -3282,16 +3305,19 @@ arbgpu_status block_finish(arbgpu_ctx *ctx, const arbgpu_balls *C, const arbgpu_
       av[q].ftop_c[0] = p3.ctop;
       av[q].ftop_r[1] = av[q].ftop_c[1] = nullptr;
     }
-    if (cudaMemsetAsync(av[q].acc, 0, 8 * (size_t)w.nacc * MN, s) != cudaSuccess ||
-        cudaMemsetAsync(av[q].err, 0, 4 * MN, s) != cudaSuccess ||
+    // (eq. 3 rounds the exact parts directly: only the radius sums are used)
+    if ((!p3.ok && cudaMemsetAsync(av[q].acc, 0, 8 * (size_t)w.nacc * MN, s) != cudaSuccess) ||
+        (!p3.ok && cudaMemsetAsync(av[q].err, 0, 4 * MN, s) != cudaSuccess) ||
         cudaMemsetAsync(av[q].rman, 0, 4 * MN, s) != cudaSuccess ||
         cudaMemsetAsync(av[q].rexp, 0, 8 * MN, s) != cudaSuccess)
       return ARBGPU_ERR_CUDA;
   }
   if (p3.ok) {
-    const arbgpu_status st3 =
-        run_3m(ctx, w, ws, p3, Av, Bv, rowsL, colsL, hst, M, K, N, lda, ldb, av, s);
+    const arbgpu_status st3 = run_3m(ctx, w, ws, p3, C, Av, Bv, rowsL, colsL, hst, M, K, N, lda,
+                                     ldb, ldc, prec, av, s);
     if (st3 != ARBGPU_OK) return st3;
+    *used_block = true;
+    return ARBGPU_OK;
   }
   for (int t = 0; t < (p3.ok ? 0 : nprods); ++t) {
     const Prod &pr = prods[t];
