@@ -198,17 +198,23 @@ arbgpu_status arbgpu_approx_dot(arbgpu_ctx *ctx, const arbgpu_balls *res,
  *   ARBGPU_ALG_BLOCK  Algorithm 2: the inner dimension is cut greedily into blocks in which every
  *                     row of A and column of B scales to integers of height <= h
  *                     (h = 1.25 min(p, max(p_A, p_B)) + 192); each block's scaled integer matrices
- *                     are split into signed 8-bit digits and multiplied exactly on the tensor cores
- *                     (BF16 digits, FP32 accumulation kept below 2^24, so every product is exact);
- *                     blocks shorter than 30 indices are done by dot products.  All contributions
- *                     to an entry are summed exactly and rounded once.  Radii:
+ *                     are multiplied exactly on the tensor cores by one of two engines, chosen by a
+ *                     cost model (the environment variable ARBGPU_ENGINE=digits|crt forces one):
+ *                     signed 8-bit digit products, or residues modulo 16-bit primes and the Chinese
+ *                     remainder theorem (BF16 digits, FP32 accumulation kept below 2^24, so every
+ *                     product is exact); blocks shorter than 30 indices are done by dot products.
+ *                     A single block is rounded once from its exact integer; several blocks are
+ *                     summed in a fixed-point window and the bits below it go to the radius.  Radii:
  *                     |A| R_B + R_A (|B| + R_B) from exact integer products of magnitudes rounded
  *                     up to 8*S_r-bit windows.
  *   ARBGPU_ALG_AUTO   picks by size and precision.
  *
  *   complex_mode  0 real; 1 complex: C, A, B each point to TWO arbgpu_balls (real, imaginary)
+ *   flags         0 or ARBGPU_MM_COMPLEX_3M (complex only; the same flags must be given to
+ *                 arbgpu_mat_mul_workspace_size)
  *   workspace     device memory of at least arbgpu_mat_mul_workspace_size() bytes (BLOCK/AUTO)
- * The block path reads back its plan (a few bytes per block) with one stream synchronisation.
+ * The block path reads back a few bytes of statistics, and its plan when there are several blocks,
+ * each with one stream synchronisation.
  */
 arbgpu_status arbgpu_mat_mul(arbgpu_ctx *ctx, const arbgpu_balls *C, const arbgpu_balls *A,
                              const arbgpu_balls *B, int64_t M, int64_t K, int64_t N, int64_t lda,
