@@ -73,3 +73,39 @@ def test_grouped_batch_mixed(arb):
                     m, r = X.mid(outs[part], idx), X.rad(outs[part], idx)
                     assert X.contains(m, r, S, R)
                     assert X.accuracy_ratio(m, S, Sabs, p) <= 1.0
+
+
+def test_grouped_batch_complex_3m_matches_single_calls(arb):
+    """Complex block items with ARBGPU_MM_COMPLEX_3M in a grouped batch give, field for field, what
+    the single-product call with the same flag gives (eq. 3, Section IV-C), next to a real item."""
+    rng = np.random.default_rng(32)
+    specs = [(64, 128, True), (80, 256, False), (72, 192, True)]
+    items, singles, outs = [], [], []
+    for n, p, cplx in specs:
+        nl = (p + 63) // 64
+        parts = 2 if cplx else 1
+        A = [arb.Balls.from_raw(random_balls(rng, n * n, nl, p, -10, 10, rad_bits=p - 8,
+                                             rad_zero_frac=0.5)) for _ in range(parts)]
+        B = [arb.Balls.from_raw(random_balls(rng, n * n, nl, p, -10, 10, rad_bits=p - 8,
+                                             rad_zero_frac=0.5)) for _ in range(parts)]
+        Cb = [arb.Balls.empty(n * n, nl) for _ in range(parts)]
+        Cs = [arb.Balls.empty(n * n, nl) for _ in range(parts)]
+        pick = (lambda v: v) if cplx else (lambda v: v[0])
+        items.append(dict(C=pick(Cb), A=pick(A), B=pick(B), M=n, K=n, N=n, prec=p,
+                          alg=arb.ALG_BLOCK, flags=arb.MM_COMPLEX_3M))
+        arb.mat_mul(pick(Cs), pick(A), pick(B), n, n, n, p, alg=arb.ALG_BLOCK,
+                    flags=arb.MM_COMPLEX_3M)
+        outs.append(Cb)
+        singles.append(Cs)
+    ctx = arb.default_context()
+    ctx.trace(True)
+    arb.mat_mul_batched(items)
+    assert ctx.status() == 0
+    names = [r[0] for r in ctx.trace_read()]
+    ctx.trace(False)
+    assert names.count("z3m") == 2  # both complex items took eq. 3
+    for Cb, Cs in zip(outs, singles):
+        for a, b in zip(Cb, Cs):
+            ra, rb = to_raw(a), to_raw(b)
+            for f in ("limbs", "exp", "flags", "rad_man", "rad_exp"):
+                assert np.array_equal(getattr(ra, f), getattr(rb, f)), f
