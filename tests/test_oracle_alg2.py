@@ -110,14 +110,22 @@ def test_scaling_is_minimal_and_integral():
             assert Fraction(Ys[k][j]) == ball_values(B, k * N + j)[0] * Fraction(2) ** f[j]
 
 
-def test_greedy_blocks_are_within_height_and_maximal():
+def _greedy_case(drift):
+    """Two rows of A against a narrow B.  Without drift the exponents of A are i.i.d. over a range
+    wider than h, so every block is a basecase block; with drift they climb 6 per inner index, so
+    full blocks of about 34 indices form and each ends before K."""
     rng = np.random.default_rng(3)
     M, K, N, p = 2, 150, 2, 64
-    ea = rng.integers(-200, 200, size=M * K)
+    if drift:
+        ea = np.repeat(6 * np.arange(K)[None, :], M, axis=0).ravel() + rng.integers(-3, 4, M * K)
+    else:
+        ea = rng.integers(-200, 200, size=M * K)
     A = random_balls(rng, M * K, 1, 64, exps=ea)
     B = random_balls(rng, K * N, 1, 64, -3, 3)
-    h, blocks = alg2.plan(A, B, M, K, N, p)
+    return A, B, M, K, N, p
 
+
+def _check_greedy(A, B, M, K, N, h, blocks):
     def height_ok(start, stop):
         for i in range(M):
             tbs = [alg2.top_bottom(A, i * K + k) for k in range(start, stop)]
@@ -129,11 +137,30 @@ def test_greedy_blocks_are_within_height_and_maximal():
                 return False
         return True
 
+    assert blocks[0][0] == 0 and blocks[-1][1] == K
+    assert all(blocks[t][1] == blocks[t + 1][0] for t in range(len(blocks) - 1))
     for start, stop, base in blocks:
         if not base:
+            assert stop - start >= alg2.BASECASE
             assert height_ok(start, stop)
             if stop < K:
-                assert not height_ok(start, stop + 1)
+                assert not height_ok(start, stop + 1)  # maximal
+        else:  # a basecase block: the greedy block from `start` is shorter than 30 indices
+            t = start + 1
+            while t < K and height_ok(start, t + 1):
+                t += 1
+            assert t - start < alg2.BASECASE
+
+
+@pytest.mark.parametrize("drift", [False, True])
+def test_greedy_blocks_are_within_height_and_maximal(drift):
+    A, B, M, K, N, p = _greedy_case(drift)
+    h, blocks = alg2.plan(A, B, M, K, N, p)
+    _check_greedy(A, B, M, K, N, h, blocks)
+    if drift:  # the maximality check above really ran
+        assert any(not base and stop < K for _, stop, base in blocks)
+    else:
+        assert all(base for _, _, base in blocks)
 
 
 def test_int_matmul_vs_numpy():
@@ -148,3 +175,68 @@ def test_uniform_workload_is_one_block():
     case = matmul_uniform(9, 40, 256, -20, 20, rad_bits=250)
     h, blocks = alg2.plan(case.A[0], case.B[0], 40, 40, 40, 256)
     assert h == 512 and blocks == [(0, 40, False)]
+
+
+# ------------------------------------------------------------------ planted mistakes
+
+def _fails(fn, *args):
+    try:
+        fn(*args)
+    except (AssertionError, IndexError, ValueError):
+        return True
+    return False
+
+
+def test_planted_mistakes_are_caught(monkeypatch):
+    """Each plausible slip in the restatement makes at least one pin above fail."""
+    orig_tb, orig_sb, orig_plan = alg2.top_bottom, alg2.scaled_block, alg2.plan
+
+    # (a) the sign of a mantissa dropped: the blocks no longer reproduce the exact product
+    def unsigned(raw, i):
+        r = orig_tb(raw, i)
+        return None if r is None else (r[0], r[1], abs(r[2]), r[3])
+    monkeypatch.setattr(alg2, "top_bottom", unsigned)
+    assert _fails(test_blocks_reproduce_exact_product, "uniform")
+    monkeypatch.setattr(alg2, "top_bottom", orig_tb)
+
+    # (b) the lowest set bit placed one position too high: every value doubles
+    def shifted(raw, i):
+        r = orig_tb(raw, i)
+        return None if r is None else (r[0], r[1] + 1, r[2], r[3] + 1)
+    monkeypatch.setattr(alg2, "top_bottom", shifted)
+    assert _fails(test_blocks_reproduce_exact_product, "badly_scaled")
+    monkeypatch.setattr(alg2, "top_bottom", orig_tb)
+
+    # (c) a scaling one bit larger than needed: still exact, but no longer minimal (Fig. 2)
+    def loose(A, B, M, K, N, start, stop):
+        e, f, Xs, Ys = orig_sb(A, B, M, K, N, start, stop)
+        return [v + 1 for v in e], f, [[2 * x for x in row] for row in Xs], Ys
+    monkeypatch.setattr(alg2, "scaled_block", loose)
+    assert not _fails(test_blocks_reproduce_exact_product, "uniform")
+    assert _fails(test_scaling_is_minimal_and_integral)
+    monkeypatch.setattr(alg2, "scaled_block", orig_sb)
+
+    # (d) a transposed operand in the integer product
+    monkeypatch.setattr(alg2, "int_matmul", lambda X, Y: [[sum(r[k] * Y[j][k] for k in range(len(r)))
+                                                           for j in range(len(Y[0]))] for r in X])
+    assert _fails(test_int_matmul_vs_numpy)
+    monkeypatch.undo()
+
+    # (e) the greedy search stopping one index early (the next block starting there)
+    def early(A, B, M, K, N, prec):
+        h, blocks = orig_plan(A, B, M, K, N, prec)
+        out, shift = [], 0
+        for start, stop, base in blocks:
+            start -= shift
+            if not base and stop < K:
+                out.append((start, stop - 1, base))
+                shift = 1
+            else:
+                out.append((start, stop, base))
+                shift = 0
+        return h, out
+    A, B, M, K, N, p = _greedy_case(True)
+    h, blocks = early(A, B, M, K, N, p)
+    assert _fails(_check_greedy, A, B, M, K, N, h, blocks)
+    h, blocks = orig_plan(A, B, M, K, N, p)
+    assert not _fails(_check_greedy, A, B, M, K, N, h, blocks)
