@@ -187,3 +187,74 @@ def test_ball_values_agree_with_oracle_decode():
     for i in range(50):
         m, r = ball_values(raw, i)
         assert F(X.mid(raw, i)) == m and F(X.rad(raw, i)) == r
+
+
+# ------------------------------------------------------------------ planted mistakes
+
+def _fails(fn, *args):
+    try:
+        fn(*args)
+    except (AssertionError, ValueError):  # a failed pin, or the decoder's own layout check
+        return True
+    return False
+
+
+def test_planted_mistakes_are_caught(monkeypatch):
+    """Each plausible slip in the exact oracle makes at least one pin above fail, and every pin
+    passes again once the slip is undone."""
+    orig = {n: getattr(X, n) for n in ("limb_field", "dot_terms_exact", "complex_dot_terms",
+                                       "rne", "mag_from")}
+
+    # (a) limbs read most significant first
+    def reversed_limbs(raw, i):
+        v = 0
+        for k in range(raw.nlimbs):
+            v = (v << 64) | int(raw.limbs[k, i])
+        return v
+    monkeypatch.setattr(X, "limb_field", reversed_limbs)
+    assert _fails(test_decode_handmade_multilimb)
+    monkeypatch.setattr(X, "limb_field", orig["limb_field"])
+
+    # (b) the last term of a dot dropped
+    monkeypatch.setattr(X, "dot_terms_exact",
+                        lambda terms, initial=None: orig["dot_terms_exact"](terms[:-1], initial))
+    assert _fails(test_exact_dot_vs_fraction_bruteforce, 1)
+    monkeypatch.setattr(X, "dot_terms_exact", orig["dot_terms_exact"])
+
+    # (c) a wrong sign on b d in the real part of a complex product
+    def re_plus_bd(x, xidx, y, yidx, sub=False):
+        re, im = orig["complex_dot_terms"](x, xidx, y, yidx, sub)
+        return [(a, c, bool(sub)) for a, c, _ in re], im
+    monkeypatch.setattr(X, "complex_dot_terms", re_plus_bd)
+    assert _fails(test_complex_terms_closed_form)
+    monkeypatch.setattr(X, "complex_dot_terms", orig["complex_dot_terms"])
+
+    # (d) ties rounded away from zero instead of to even
+    def ties_away(v, p):
+        num, e = v
+        n = abs(num).bit_length()
+        if n <= p:
+            return orig["rne"](v, p)
+        cut = n - p
+        q, rem = divmod(abs(num), 1 << cut)
+        if 2 * rem == (1 << cut):  # an exact tie
+            r = ((q + 1) << cut) * (1 if num > 0 else -1)
+            return (r, e), X.dy_abs(X.dy_add((r, e), X.dy_neg(v)))
+        return orig["rne"](v, p)
+    monkeypatch.setattr(X, "rne", ties_away)
+    assert _fails(test_rne_ties_even_handmade)
+    monkeypatch.setattr(X, "rne", orig["rne"])
+
+    # (e) a radius magnitude rounded down instead of up
+    def mag_down(v):
+        b, f = orig["mag_from"](v)
+        return (b - 1, f) if b > 2**29 else (b, f)
+    monkeypatch.setattr(X, "mag_from", mag_down)
+    assert _fails(test_mag_from_upper_and_tight)
+    monkeypatch.setattr(X, "mag_from", orig["mag_from"])
+
+    for fn, args in ((test_decode_handmade_multilimb, ()),
+                     (test_exact_dot_vs_fraction_bruteforce, (1,)),
+                     (test_complex_terms_closed_form, ()), (test_rne_ties_even_handmade, ()),
+                     (test_mag_from_upper_and_tight, ())):
+        assert not _fails(fn, *args)
