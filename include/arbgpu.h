@@ -181,7 +181,7 @@ arbgpu_status arbgpu_approx_dot(arbgpu_ctx *ctx, const arbgpu_balls *res,
 #define ARBGPU_ALG_BLOCK 2 /* scaled integer blocks (Algorithm 2, Section IV-A) */
 
 /* Flags for arbgpu_mat_mul. */
-/* Complex midpoints by eq. 3 (Section IV-C): when one exponent per row of A and per column of B,
+/* Complex midpoints by eq. 2 (Section IV-C): when one exponent per row of A and per column of B,
  * shared by the real and imaginary parts, scales both parts to integers within one block of
  * Algorithm 2, Re = Ar Br - Ai Bi and Im = (Ar + Ai)(Br + Bi) - Ar Br - Ai Bi are formed exactly
  * from three integer products instead of four; radii come from the four real radius products as

@@ -1419,7 +1419,7 @@ struct RoundArgs {
   int64_t M, N, ldc, Mp, Np;
   int prec;
   // optional radius bound added to every entry ([M][N], index i N + j; null when absent): the
-  // radius products of the complex product by eq. 3, summed beforehand
+  // radius products of the complex product by eq. 2, summed beforehand
   const uint32_t *xrman;
   const int64_t *xrexp;
 };
@@ -2256,8 +2256,8 @@ struct AccArgs {
   AccView v;
   int64_t M, N, Mp, Np;
   int negate;    // subtract the product (the -B D part of a complex real part)
-  int skip_mid;  // add only the radius bound (the complex product by eq. 3)
-  int skip_rad;  // add only the product (the complex product by eq. 3)
+  int skip_mid;  // add only the radius bound (the complex product by eq. 2)
+  int skip_rad;  // add only the product (the complex product by eq. 2)
 };
 
 constexpr int ACC_MAX = 24;
@@ -2395,9 +2395,9 @@ __global__ void acc_to_ball_kernel(const AccView v, BallsOut I, int64_t M, int64
   I.rad_exp[idx] = r.man ? r.exp : 0;
 }
 
-// ------------------------------------------------------------------------- complex product by eq. 3
+// ------------------------------------------------------------------------- complex product by eq. 2
 
-// The shared scaling of a complex operand's two parts: eq. 3 forms X_re + X_im, so both parts of a
+// The shared scaling of a complex operand's two parts: eq. 2 forms X_re + X_im, so both parts of a
 // row of A (a column of B) take one exponent.  Line tops are the larger, bottoms the smaller of
 // the parts' (an empty line has top INT64_MIN and bottom INT64_MAX); st receives the largest row
 // height (hA) and column height (hB), INT64_MIN when every line is empty.  One CTA.
@@ -2483,7 +2483,7 @@ __global__ void residue_sum_kernel(const __nv_bfloat16 *reA, const __nv_bfloat16
   *(uint4 *)(sum + hi) = out[1];
 }
 
-// Eq. 3 on the residue products, modulus by modulus (values in [0, m_t)): z_re = z_1 - z_2 and
+// Eq. 2 on the residue products, modulus by modulus (values in [0, m_t)): z_re = z_1 - z_2 and
 // z_im = z_3 - z_1 - z_2 mod m_t, with z_1, z_2, z_3 those of X_re Y_re, X_im Y_im and
 // (X_re + X_im)(Y_re + Y_im) in planes [0, NM), [NM, 2 NM), [2 NM, 3 NM) of `z`.  In place: z_re
 // over z_1, z_im over z_2.  Eight entries per thread (plane is a multiple of 8).
@@ -2527,7 +2527,7 @@ struct BlockWs {
   size_t acc[2], err[2], rman[2], rexp[2], ilimbs[2], iexp[2], iflags[2], irman[2], irexp[2], bk[2];
   // multimodular engine: residue planes, residue products, tables
   size_t resA, resB, cdig, ccar, craw;
-  // complex product by eq. 3: residue planes of the parts and their sum, three residue products
+  // complex product by eq. 2: residue planes of the parts and their sum, three residue products
   size_t r3A, r3B, z3;
   size_t total;
   int Smax, NDmax, Gmax, Gr, maxb, nacc, NMmax, NMWmax;
@@ -2965,7 +2965,7 @@ static arbgpu_status accumulate_product(arbgpu_ctx *ctx, const BlockWs &w, uint8
   return cudaGetLastError() == cudaSuccess ? ARBGPU_OK : ARBGPU_ERR_CUDA;
 }
 
-// ---- complex product by eq. 3 (Section IV-C: three real products of the midpoint matrices when
+// ---- complex product by eq. 2 (Section IV-C: three real products of the midpoint matrices when
 // the entries are uniformly scaled).  With one exponent per row of A and per column of B shared by
 // both parts (merge_parts_kernel), X_re, X_im, Y_re, Y_im are integer matrices and
 //   P_1 = X_re Y_re,  P_2 = X_im Y_im,  P_3 = (X_re + X_im)(Y_re + Y_im),
@@ -3024,7 +3024,7 @@ static arbgpu_status plan_3m(arbgpu_ctx *ctx, const BlockWs &w, uint8_t *ws, con
   return ARBGPU_OK;
 }
 
-// Run the planned eq. 3 product: the radius bounds of each part summed into av[q].rman / rexp
+// Run the planned eq. 2 product: the radius bounds of each part summed into av[q].rman / rexp
 // (zeroed by the caller), then Re and Im reconstructed and rounded straight into C[0], C[1].
 static arbgpu_status run_3m(arbgpu_ctx *ctx, const BlockWs &w, uint8_t *ws, const Plan3M &p,
                             const arbgpu_balls *C, const BallsView *Av, const BallsView *Bv,
@@ -3268,7 +3268,7 @@ arbgpu_status block_finish(arbgpu_ctx *ctx, const arbgpu_balls *C, const arbgpu_
     }
   }
 
-  // complex by eq. 3 when the shared scaling of the parts fits one block
+  // complex by eq. 2 when the shared scaling of the parts fits one block
   Plan3M p3{};
   if (cplx && m3) {
     const arbgpu_status st = plan_3m(ctx, w, ws, rowsL, colsL, hst, M, K, N, prec, s, &p3);
@@ -3305,7 +3305,7 @@ arbgpu_status block_finish(arbgpu_ctx *ctx, const arbgpu_balls *C, const arbgpu_
       av[q].ftop_c[0] = p3.ctop;
       av[q].ftop_r[1] = av[q].ftop_c[1] = nullptr;
     }
-    // (eq. 3 rounds the exact parts directly: only the radius sums are used)
+    // (eq. 2 rounds the exact parts directly: only the radius sums are used)
     if ((!p3.ok && cudaMemsetAsync(av[q].acc, 0, 8 * (size_t)w.nacc * MN, s) != cudaSuccess) ||
         (!p3.ok && cudaMemsetAsync(av[q].err, 0, 4 * MN, s) != cudaSuccess) ||
         cudaMemsetAsync(av[q].rman, 0, 4 * MN, s) != cudaSuccess ||

@@ -107,7 +107,7 @@ std::unique_ptr<CrtPlan> build_plan(int NM) {
     }
   }
   // GEMM item tables for up to three residue products in one batch (the complex product by
-  // eq. 3 runs its three real products as items t, NM + t and 2 NM + t of modulus t)
+  // eq. 2 runs its three real products as items t, NM + t and 2 NM + t of modulus t)
   P->ztab.assign((size_t)4 * 3 * NM, 0);
   for (int t = 0; t < 3 * NM; ++t) P->ztab[4 * t] = P->mods[t % NM];
   for (int t = NM; t < 3 * NM; ++t) P->inv.push_back(P->inv[t - NM]);

@@ -131,7 +131,7 @@ arbgpu_status block_finish(arbgpu_ctx *ctx, const arbgpu_balls *C, const arbgpu_
 // Block algorithm (block.cu): real or complex (C, A, B point to one or two arbgpu_balls).  Returns
 // ARBGPU_ERR_LIMIT (and *used_block = false) when the inputs hold special values or exceed the
 // path's limits.
-// m3: complex midpoints by eq. 3 (three real products) where the parts share one scaling in a
+// m3: complex midpoints by eq. 2 (three real products) where the parts share one scaling in a
 // single block; the workspace then holds the three products' planes.
 size_t block_workspace_size(arbgpu_ctx *ctx, int64_t M, int64_t K, int64_t N, int prec,
                             bool cplx, bool m3);

@@ -77,7 +77,7 @@ def test_grouped_batch_mixed(arb):
 
 def test_grouped_batch_complex_3m_matches_single_calls(arb):
     """Complex block items with ARBGPU_MM_COMPLEX_3M in a grouped batch give, field for field, what
-    the single-product call with the same flag gives (eq. 3, Section IV-C), next to a real item."""
+    the single-product call with the same flag gives (eq. 2, Section IV-C), next to a real item."""
     rng = np.random.default_rng(32)
     specs = [(64, 128, True), (80, 256, False), (72, 192, True)]
     items, singles, outs = [], [], []
@@ -103,7 +103,7 @@ def test_grouped_batch_complex_3m_matches_single_calls(arb):
     assert ctx.status() == 0
     names = [r[0] for r in ctx.trace_read()]
     ctx.trace(False)
-    assert names.count("z3m") == 2  # both complex items took eq. 3
+    assert names.count("z3m") == 2  # both complex items took eq. 2
     for Cb, Cs in zip(outs, singles):
         for a, b in zip(Cb, Cs):
             ra, rb = to_raw(a), to_raw(b)

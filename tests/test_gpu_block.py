@@ -262,7 +262,7 @@ def test_complex_block_uniform(arb):
 @pytest.mark.parametrize("M,K,N,prec,spread", [(96, 96, 96, 128, 10), (70, 100, 90, 256, 20),
                                                 (33, 200, 130, 64, 3)])
 def test_complex_3m_exact_rounding(arb, M, K, N, prec, spread):
-    """Eq. 3 (Section IV-C): with one scaling per row of A and column of B shared by both parts,
+    """Eq. 2 (Section IV-C): with one scaling per row of A and column of B shared by both parts,
     Re = P1 - P2 and Im = P3 - P1 - P2 from three exact products.  The integers are exact, so
     every sampled midpoint is RNE_p of the exact part, the same as the four-product path gives,
     and every ball contains the exact value."""
@@ -297,7 +297,7 @@ def test_complex_3m_exact_rounding(arb, M, K, N, prec, spread):
 
 
 def test_complex_3m_exact_inputs_and_zero_part(arb):
-    """Eq. 3 with exact inputs whose imaginary parts are zero in A: Im C = Ar Bi exactly, zero
+    """Eq. 2 with exact inputs whose imaginary parts are zero in A: Im C = Ar Bi exactly, zero
     radii wherever the exact sums fit in p bits (small integers)."""
     rng = np.random.default_rng(70)
     M, K, N, p = 64, 64, 64, 128

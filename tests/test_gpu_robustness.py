@@ -3,7 +3,7 @@
 Races would show up as run-to-run differences. The integer paths are deterministic by
 construction: exact integer sums, and reductions in a fixed order. So two calls on the same inputs
 must agree bit for bit in every output field, on each path: one block, several blocks with
-basecase dots, classical dots, and the complex product by eq. 3. Argument errors (a workspace
+basecase dots, classical dots, and the complex product by eq. 2. Argument errors (a workspace
 smaller than the query gave, unknown flag bits) return at once, launch nothing and leave the device
 status word clear."""
 from __future__ import annotations
@@ -80,7 +80,7 @@ def test_short_workspace_is_rejected(arb):
     assert arb.default_context().status() == 0
 
 
-def test_eq3_flag_needs_the_workspace_queried_with_it(arb):
+def test_3m_flag_needs_the_workspace_queried_with_it(arb):
     M = K = N = 64
     p = 128
     A, B = _inputs(arb, 92, M, K, N, p, 2, -10, 10)
