@@ -146,7 +146,7 @@ arbgpu_status arbgpu_dot(arbgpu_ctx *ctx, const arbgpu_balls *res, const arbgpu_
 
 /* Options of arbgpu_dot_ex. */
 #define ARBGPU_DOT_APPROX 1u      /* midpoints only: the input radii are ignored, zero radii out */
-#define ARBGPU_DOT_REDUCE_PREC 2u /* the precision reduction of Section III-C, step 7: per dot,
+#define ARBGPU_DOT_REDUCE_PREC 2u /* the precision reduction ("optimize p") of Section III-C: per dot,
                                    * p <- min(p, e_max - e_rad + 30) when a radius is present and,
                                    * for p > 128, p <- min(p, e_max - e_min + 30) (e_min: the lowest
                                    * possible bit of a product); then p >= 2, and p = 2 when every

@@ -18,13 +18,13 @@ Steps (Section III-B..E):
   subtracted in two's complement; nonzero bits falling below the accumulator add one ulp.
 * Radius (Section III-E): each midpoint becomes the 30-bit upper bound "top 30 bits of the top limb,
   plus one"; each nonzero product adds ``floor(ab / 2^(30 + e_rad - e)) + 1`` (or 1) to ``srad``.
-* Finalisation (Algorithm 1, step 4): negate if the top bit is set, round to ``p`` bits, and bound
+* Finalisation (Algorithm 1's last phase): negate if the top bit is set, round to ``p`` bits, and bound
   ``eps_round + err * 2^(e_s - 64 n_s) + srad * 2^(e_rad - 30)`` by a 30-bit radius.
 
 Readings where the paper leaves a choice (each also used by the kernel):
 
 * Rounding to p bits is round-to-nearest, ties to even.
-* The precision reduction of Section III-C step 7 ("optimize p") is applied only when asked
+* The precision reduction of Section III-C ("optimize p") is applied only when asked
   (``reduce_prec``); by default p stays as given.
 * ``initial`` is the extra term ``initial * 1`` with the exact ball ``[1 +- 0]`` (Section III-B:
   "extending the dot product to length N + 1"); ``N`` in ``padding`` counts it.
@@ -95,7 +95,7 @@ def dot(terms, prec, nlimbs_out, initial=None, reduce_prec=False):
 
     Returns a dict with the output layout fields (``limbs``, ``exp``, ``flags``, ``rad_man``,
     ``rad_exp``), ``status`` (0 or 2 for an unsupported value) and the internal quantities.  With
-    ``reduce_prec``, step 7 of Section III-C lowers the working and output precision."""
+    ``reduce_prec``, the "optimize p" step of Section III-C lowers the working and output precision."""
     try:
         return _dot(terms, prec, nlimbs_out, initial, reduce_prec)
     except Special:
@@ -129,7 +129,7 @@ def _dot(terms, prec, nlimbs_out, initial, reduce_prec=False):
     if e_max is None and e_rad is None:
         return dict(limbs=[0] * nlimbs_out, exp=0, flags=FLAG_ZERO, rad_man=0, rad_exp=0,
                     status=0, n_s=0, e_s=0, err=0, srad=0, e_rad=None)
-    if reduce_prec:  # step 7: a radius above the arithmetic error, or a narrow window of terms
+    if reduce_prec:  # "optimize p": a radius above the arithmetic error, or a narrow window of terms
         if e_max is None:
             prec = 2
         else:

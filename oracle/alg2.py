@@ -3,7 +3,7 @@
 Steps, in the paper's order:
 
 * ``h = 1.25 * min(p, max(p_A, p_B)) + 192`` where ``p_M`` is the least precision that holds every
-  entry of ``M`` exactly (Algorithm 2, step 2).
+  entry of ``M`` exactly (Algorithm 2's height bound).
 * Greedy extraction (Section IV-A): starting at the first unused inner index, append indices while
   every row of ``A_s`` and every column of ``B_s`` still scales to integers of height below ``2^h``.
 * A block of fewer than 30 indices is widened to ``min(30, |S|)`` indices and done with dot products

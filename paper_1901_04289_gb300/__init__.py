@@ -202,7 +202,7 @@ def _ptr(t):
 def dot(res, x, y, xoff, xstep, yoff, ystep, length, prec, *, prec_max, len_max, sub=None,
         initial=None, ctx=None, stream=None, approx=False, reduce_prec=False):
     """Batched ball dots (``arbgpu_dot_ex``): with ``approx`` the same midpoints and zero radii
-    (``arbgpu_approx_dot``); with ``reduce_prec`` the precision reduction of Section III-C, step 7.
+    (``arbgpu_approx_dot``); with ``reduce_prec`` the precision reduction ("optimize p") of Section III-C.
     ``res``, ``x``, ``y``, ``initial``: a ``Balls`` (real) or a pair ``(re, im)`` (complex).  Index
     arrays: int64 device tensors; ``prec`` int32; ``sub`` uint8 or None."""
     ctx = ctx or default_context()

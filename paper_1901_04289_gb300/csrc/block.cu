@@ -3,7 +3,7 @@
 //
 //   scan   per row of A / column of B: largest exponent (top), exponent of the lowest set bit
 //          (bottom), largest radius exponent; global p_A, p_B and the largest heights.
-//   plan   h = 1.25 min(p, max(p_A, p_B)) + 192 (Algorithm 2, step 2); the product is one block when
+//   plan   h = 1.25 min(p, max(p_A, p_B)) + 192 (Algorithm 2's height bound); the product is one block when
 //          every row of A and column of B scales to integers of height <= h (the common case the
 //          paper describes: uniformly scaled inputs need a single block).
 //   split  E A and B F with the minimal-height scalings e_i = -bottom_i, f_j = -bottom_j (Fig. 2),

@@ -18,7 +18,7 @@
 //     reduction                 the lanes' n_s-limb accumulators, err and srad are added with a
 //                               butterfly of warp shuffles; integer addition modulo 2^(64 NS) is
 //                               associative, so the result equals the sequential sum bit for bit.
-//     finalise (Algorithm 1, step 4) negate if negative, round to p bits (nearest, ties to even),
+//     finalise (Algorithm 1's finalisation) negate if negative, round to p bits (nearest, ties to even),
 //                               radius = eps_round + err ulps + srad, rounded up to 30 bits; all
 //                               in registers (fixed-size limb arrays, runtime bit positions).
 //
@@ -129,7 +129,7 @@ struct DotSetup {
   int nx;  // limbs to read per factor (at most)
   bool has_mid, has_rad;
   bool approx;  // midpoint only: no radius is formed or written
-  int prec;     // working and output precision (the requested one, or step 7's reduction)
+  int prec;     // working and output precision (the requested one, or Section III-C's reduction)
 };
 
 // The setup parked in the output entry's flags word (bit 31 never appears in a finished entry).
@@ -368,7 +368,7 @@ __device__ __forceinline__ void acc_term_one(LaneAcc<NS> &acc, const uint64_t (&
 
 // ---------------------------------------------------------------- finalise (registers only)
 
-// Round the reduced accumulator to p bits and write output entry `oi` (Algorithm 1, step 4).
+// Round the reduced accumulator to p bits and write output entry `oi` (Algorithm 1's finalisation).
 // Every lane of the group holds the reduced sums and computes the same values; the output limbs are
 // written by the group's lanes in parallel, the scalar fields by its first lane.
 template <int NS, int G>
@@ -612,7 +612,7 @@ __device__ bool dot_setup_core(const Src &src, const typename Src::Cursor &cur, 
   bool special = false;
   int64_t nnz = 0;
   int64_t e_max = INT64_MIN, e_rad = INT64_MIN;
-  int64_t e_min = INT64_MAX;  // lowest possible bit of a product (step 7, when p > 2 beta)
+  int64_t e_min = INT64_MAX;  // lowest possible bit of a product ("optimize p", when p > 2 beta)
   const bool track_min = src.reduce && prec > 128;
   int nsig_max = 0;
   constexpr int U = 2;  // terms per lane per step, loads issued together
@@ -674,7 +674,7 @@ __device__ bool dot_setup_core(const Src &src, const typename Src::Cursor &cur, 
     write_zero<G>(out, oi, gl);
     return false;
   }
-  // step 7 of Section III-C, when asked for: a radius above the arithmetic error, or terms that
+  // "optimize p" of Section III-C, when asked for: a radius above the arithmetic error, or terms that
   // fit in a narrow window, lower the precision
   int p = prec;
   if (src.reduce) {

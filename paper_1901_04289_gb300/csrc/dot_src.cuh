@@ -14,7 +14,7 @@ namespace arbgpu {
 // re = sum a c - b d, im = sum a d + b c (Section III-F).
 struct BatchDotSrc {
   bool approx;  // midpoints only (radii ignored, zero output radii)
-  bool reduce;  // the precision reduction of Section III-C, step 7
+  bool reduce;  // the precision reduction ("optimize p") of Section III-C
   BallsView x[2], y[2], init[2];
   BallsOut out[2];
   const int64_t *xoff, *xstep, *yoff, *ystep, *len;

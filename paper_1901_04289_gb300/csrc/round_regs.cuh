@@ -1,6 +1,6 @@
 // Rounding of a multi-limb magnitude to p bits in registers (fixed-size limb arrays indexed only
 // by compile-time positions; the bit positions are runtime values), shared by the dot kernel
-// (Algorithm 1, step 4) and the block product's epilogue (Algorithm 2): round to nearest, ties to
+// (Algorithm 1's finalisation) and the block product's epilogue (Algorithm 2): round to nearest, ties to
 // even, the exact rounding error (plus an error count) rounded up to a 30-bit mag, and the store of
 // the rounded ball.
 #pragma once

@@ -106,7 +106,7 @@ def test_batched_dots_bit_exact_vs_alg1(arb, k):
 
 @pytest.mark.parametrize("k", [1, 2, 4, 5])
 def test_reduced_precision_dots_bit_exact_vs_alg1(arb, k):
-    """ARBGPU_DOT_REDUCE_PREC (Section III-C, step 7): every output field equals the Algorithm 1
+    """ARBGPU_DOT_REDUCE_PREC (Section III-C, "optimize p"): every output field equals the Algorithm 1
     restatement run with the same reduction, and the reduction changes some results."""
     batch = small_batch(**SMALL[k])
     nl_out = (int(batch.prec.max()) + 63) // 64

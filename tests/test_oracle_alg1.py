@@ -224,7 +224,7 @@ def test_planted_mistakes_are_caught(monkeypatch):
     assert not X.contains(m, r, S, R)
 
 
-# ---- step 7 of Section III-C ("optimize p"), asked for with reduce_prec
+# ---- the "optimize p" step of Section III-C, asked for with reduce_prec
 
 @pytest.mark.parametrize("seed", range(8))
 def test_reduced_precision_keeps_a_result_that_fits_its_window(seed):
