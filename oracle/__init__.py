@@ -14,5 +14,7 @@ Modules:
 * ``alg1``   -- Algorithm 1 (Section III) restated step by step on Python integers: the fixed-point
   limb accumulator, the ulp error counter and the radius accumulator.
 * ``alg2``   -- Algorithm 2 (Section IV-A): the height bound, the greedy block extraction, the
-  optimal row/column scaling exponents and the exact scaled integer block products.
+  optimal row/column scaling exponents and the exact scaled integer block products; and Section
+  IV-B's suggested inner scaling with a permutation of the inner index (ordered, non-contiguous
+  blocks).
 """

@@ -22,6 +22,10 @@ Readings (each also used by the GPU planner):
 * ``F_s`` scales column ``j`` (the figure's ``f_{i,s}`` index is read as ``f_{j,s}``).
 * All contributions to an entry are summed exactly and rounded once, so a product without basecase
   blocks has the midpoint ``RNE_p(sum_k a_ik b_kj)``.
+
+``plan_ordered`` / ``scaled_block_ordered`` restate Section IV-B's suggested improvement (an inner
+scaling of the columns of A_s against the rows of B_s, combined with a permutation of the inner
+index); its reading is given above ``inner_order``.
 """
 from __future__ import annotations
 
@@ -68,6 +72,12 @@ def plan(A, B, M, K, N, prec):
     h = height_bound(prec, pA, pB)
     tbA = [[top_bottom(A, i * K + k) for k in range(K)] for i in range(M)]
     tbB = [[top_bottom(B, k * N + j) for k in range(K)] for j in range(N)]
+    return h, _greedy(tbA, tbB, M, N, K, h)
+
+
+def _greedy(tbA, tbB, M, N, K, h):
+    """The greedy extraction over positions 0..K-1 of the per-line entry lists ``tbA[i][t]``,
+    ``tbB[j][t]`` (``(top, bottom, ...)`` or None for a zero)."""
     blocks = []
     start = 0
     while start < K:
@@ -111,7 +121,7 @@ def plan(A, B, M, K, N, prec):
         else:
             blocks.append((start, stop, False))
         start = stop
-    return h, blocks
+    return blocks
 
 
 def _force(tbA, tbB, k, M, N):
@@ -142,6 +152,76 @@ def scaled_block(A, B, M, K, N, start, stop):
         f.append(fj)
         cols.append([0 if tb is None else tb[2] << (tb[3] + fj) for tb in col])
     Y = [[cols[j][kk] for j in range(N)] for kk in range(stop - start)]
+    return e, f, X, Y
+
+
+# ---- Section IV-B's suggested improvement: an inner scaling G_s G_s^-1 of the columns of A_s and
+# the rows of B_s, combined with a permutation of the inner index (non-contiguous blocks).
+#
+# Reading (the paper leaves the strategy open; the GPU planner follows the same rule):
+# * a_k = largest top over column k of A, b_k = largest top over row k of B;
+# * an index whose column of A or row of B is entirely zero contributes nothing to A B and is left
+#   out of the midpoint product;
+# * g_k = floor((b_k - a_k) / 2): column k of A is multiplied by 2^g_k and row k of B by 2^-g_k
+#   (exact, and A B is unchanged), which brings both tops to within one of (a_k + b_k) / 2;
+# * the live indices are ordered by a_k + b_k, the magnitude bound of their products (ties by
+#   index), and the greedy extraction of Section IV-A runs over that order.
+
+def inner_order(A, B, M, K, N):
+    """``(order, g)``: the live inner indices in planning order and the inner scaling exponent of
+    every index (0 for the left-out ones)."""
+    g = [0] * K
+    keyed = []
+    for k in range(K):
+        ta = [top_bottom(A, i * K + k) for i in range(M)]
+        tb = [top_bottom(B, k * N + j) for j in range(N)]
+        ta = [t[0] for t in ta if t is not None]
+        tb = [t[0] for t in tb if t is not None]
+        if not ta or not tb:
+            continue
+        a, b = max(ta), max(tb)
+        g[k] = (b - a) // 2
+        keyed.append((a + b, k))
+    keyed.sort()
+    return [k for _, k in keyed], g
+
+
+def plan_ordered(A, B, M, K, N, prec):
+    """``(h, order, g, blocks)``: the greedy blocks over positions of ``order`` (blocks index
+    positions; position t is inner index order[t]), under the inner scaling ``g``."""
+    pA = precision_of(A, M * K)
+    pB = precision_of(B, K * N)
+    h = height_bound(prec, pA, pB)
+    order, g = inner_order(A, B, M, K, N)
+
+    def shifted(tb, d):
+        return None if tb is None else (tb[0] + d, tb[1] + d, tb[2], tb[3] + d)
+    tbA = [[shifted(top_bottom(A, i * K + k), g[k]) for k in order] for i in range(M)]
+    tbB = [[shifted(top_bottom(B, k * N + j), -g[k]) for k in order] for j in range(N)]
+    return h, order, g, _greedy(tbA, tbB, M, N, len(order), h)
+
+
+def scaled_block_ordered(A, B, M, K, N, ks, g):
+    """``(e, f, X, Y)`` of the block of inner indices ``ks`` (any order) under the inner scaling
+    ``g``: ``X = E_s A_s G_s`` (M x |s|) and ``Y = G_s^-1 B_s F_s`` (|s| x N) with minimal-height
+    row and column scalings (Fig. 2), so that ``E_s^-1 X Y F_s^-1 = A_s B_s``."""
+    e, X = [], []
+    for i in range(M):
+        row = [top_bottom(A, i * K + k) for k in ks]
+        sh = [None if tb is None else tb[3] + g[k] for tb, k in zip(row, ks)]
+        lows = [v for v in sh if v is not None]
+        ei = -min(lows) if lows else 0
+        e.append(ei)
+        X.append([0 if tb is None else tb[2] << (v + ei) for tb, v in zip(row, sh)])
+    f, cols = [], []
+    for j in range(N):
+        col = [top_bottom(B, k * N + j) for k in ks]
+        sh = [None if tb is None else tb[3] - g[k] for tb, k in zip(col, ks)]
+        lows = [v for v in sh if v is not None]
+        fj = -min(lows) if lows else 0
+        f.append(fj)
+        cols.append([0 if tb is None else tb[2] << (v + fj) for tb, v in zip(col, sh)])
+    Y = [[cols[j][t] for j in range(N)] for t in range(len(ks))]
     return e, f, X, Y
 
 

@@ -240,3 +240,142 @@ def test_planted_mistakes_are_caught(monkeypatch):
     assert _fails(_check_greedy, A, B, M, K, N, h, blocks)
     h, blocks = orig_plan(A, B, M, K, N, p)
     assert not _fails(_check_greedy, A, B, M, K, N, h, blocks)
+
+
+# ------------------------------------------------------------------ inner scaling + permutation
+# (Section IV-B's suggested improvement, in the reading of ``oracle.alg2.inner_order``)
+
+def recombined_ordered(A, B, M, K, N, prec):
+    h, order, g, blocks = alg2.plan_ordered(A, B, M, K, N, prec)
+    C = [[Fraction(0)] * N for _ in range(M)]
+    for start, stop, base in blocks:
+        ks = order[start:stop]
+        if base:
+            for i in range(M):
+                for j in range(N):
+                    C[i][j] += sum(ball_values(A, i * K + k)[0] * ball_values(B, k * N + j)[0]
+                                   for k in ks)
+        else:
+            e, f, Xs, Ys = alg2.scaled_block_ordered(A, B, M, K, N, ks, g)
+            T = alg2.int_matmul(Xs, Ys)
+            for i in range(M):
+                for j in range(N):
+                    C[i][j] += Fraction(T[i][j]) * Fraction(2) ** (-e[i] - f[j])
+    return order, g, blocks, C
+
+
+def _ordered_case(kind):
+    from synth.workloads import complex_matmul_laplace
+    rng = np.random.default_rng(hash(kind) % 2**32)
+    if kind in ("structured", "literal"):
+        case = complex_matmul_laplace(n=32, structured=(kind == "structured"))
+        return case.A[0], case.B[1], 32, 32, 32, 128
+    if kind == "uniform":
+        M, K, N, p = 5, 36, 4, 128
+        return (random_balls(rng, M * K, 2, 128, -20, 20), random_balls(rng, K * N, 2, 128, -20, 20),
+                M, K, N, p)
+    # zeros: column 3 of A and row 7 of B entirely zero, scattered zero entries elsewhere
+    M, K, N, p = 4, 40, 3, 64
+    A = random_balls(rng, M * K, 1, 64, -5, 5, zero_frac=0.3)
+    B = random_balls(rng, K * N, 1, 64, -5, 5, zero_frac=0.3)
+    for i in range(M):
+        A.flags[i * K + 3] = X.FLAG_ZERO
+        A.limbs[:, i * K + 3] = 0
+    B.flags[7 * N:8 * N] = X.FLAG_ZERO
+    B.limbs[:, 7 * N:8 * N] = 0
+    return A, B, M, K, N, p
+
+
+@pytest.mark.parametrize("kind", ["structured", "literal", "uniform", "zeros"])
+def test_ordered_blocks_reproduce_exact_product(kind):
+    A, B, M, K, N, p = _ordered_case(kind)
+    order, g, blocks, C = recombined_ordered(A, B, M, K, N, p)
+    assert C == exact_product(A, B, M, K, N)
+    # the blocks tile the positions of the order, and the order is a set of distinct indices
+    assert blocks[0][0] == 0 and blocks[-1][1] == len(order)
+    assert all(blocks[t][1] == blocks[t + 1][0] for t in range(len(blocks) - 1))
+    assert len(set(order)) == len(order) and set(order) <= set(range(K))
+    if kind == "zeros":
+        assert 3 not in order and 7 not in order
+
+
+def _tops(A, B, M, K, N, k):
+    ta = [alg2.top_bottom(A, i * K + k) for i in range(M)]
+    tb = [alg2.top_bottom(B, k * N + j) for j in range(N)]
+    return [t[0] for t in ta if t], [t[0] for t in tb if t]
+
+
+def test_inner_order_is_sorted_balanced_and_leaves_out_dead_indices():
+    A, B, M, K, N, p = _ordered_case("zeros")
+    order, g = alg2.inner_order(A, B, M, K, N)
+    live = [k for k in range(K) if all(_tops(A, B, M, K, N, k))]
+    assert sorted(order) == live
+    keys = []
+    for k in order:
+        ta, tb = _tops(A, B, M, K, N, k)
+        a, b = max(ta), max(tb)
+        keys.append(a + b)
+        assert abs((a + g[k]) - (b - g[k])) <= 1  # the scaled tops meet in the middle
+    assert keys == sorted(keys)
+
+
+def test_ordered_greedy_blocks_are_within_height_and_maximal():
+    from synth.workloads import complex_matmul_laplace
+    case = complex_matmul_laplace(n=48, structured=True)
+    A, B, M, K, N, p = case.A[0], case.B[0], 48, 48, 48, 128
+    h, order, g, blocks = alg2.plan_ordered(A, B, M, K, N, p)
+
+    def height_ok(start, stop):
+        ks = order[start:stop]
+        for i in range(M):
+            tbs = [(t[0] + g[k], t[1] + g[k]) for k in ks
+                   for t in [alg2.top_bottom(A, i * K + k)] if t]
+            if tbs and max(t[0] for t in tbs) - min(t[1] for t in tbs) > h:
+                return False
+        for j in range(N):
+            tbs = [(t[0] - g[k], t[1] - g[k]) for k in ks
+                   for t in [alg2.top_bottom(B, k * N + j)] if t]
+            if tbs and max(t[0] for t in tbs) - min(t[1] for t in tbs) > h:
+                return False
+        return True
+
+    for start, stop, base in blocks:
+        if not base:
+            assert height_ok(start, stop)
+            if stop < len(order):
+                assert not height_ok(start, stop + 1)
+
+
+def test_ordering_turns_the_structured_workload_into_full_blocks():
+    """On the structured Laplace(40) workload at N = 128 the contiguous greedy leaves most of the
+    inner dimension to basecase dots; ordered and scaled, nearly all of it forms full blocks."""
+    from synth.workloads import complex_matmul_laplace
+    n = 128
+    case = complex_matmul_laplace(n=n, structured=True)
+    for xa, yb in ((0, 0), (1, 1)):
+        A, B = case.A[xa], case.B[yb]
+        _, blocks = alg2.plan(A, B, n, n, n, 128)
+        _, order, _, blocks2 = alg2.plan_ordered(A, B, n, n, n, 128)
+        base1 = sum(b - a for a, b, base in blocks if base) / n
+        base2 = sum(b - a for a, b, base in blocks2 if base) / len(order)
+        assert base1 >= 0.5 and base2 <= 0.1, (base1, base2)
+
+
+def test_planted_mistakes_in_the_ordered_plan_are_caught(monkeypatch):
+    orig = alg2.inner_order
+
+    # (f) the inner scaling forgotten
+    monkeypatch.setattr(alg2, "inner_order",
+                        lambda A, B, M, K, N: (orig(A, B, M, K, N)[0], [0] * K))
+    assert _fails(test_inner_order_is_sorted_balanced_and_leaves_out_dead_indices)
+    monkeypatch.setattr(alg2, "inner_order", orig)
+
+    # (g) ordered by the tops of A alone instead of the product bound a_k + b_k
+    def by_a(A, B, M, K, N):
+        order, g = orig(A, B, M, K, N)
+        key = {k: max(_tops(A, B, M, K, N, k)[0]) for k in order}
+        return sorted(order, key=lambda k: (key[k], k)), g
+    monkeypatch.setattr(alg2, "inner_order", by_a)
+    assert _fails(test_inner_order_is_sorted_balanced_and_leaves_out_dead_indices)
+    monkeypatch.setattr(alg2, "inner_order", orig)
+    assert not _fails(test_inner_order_is_sorted_balanced_and_leaves_out_dead_indices)
