@@ -160,30 +160,32 @@ def scaled_block(A, B, M, K, N, start, stop):
 #
 # Reading (the paper leaves the strategy open; the GPU planner follows the same rule):
 # * a_k = largest top over column k of A, b_k = largest top over row k of B;
-# * an index whose column of A or row of B is entirely zero contributes nothing to A B and is left
-#   out of the midpoint product;
+# * an index whose column of A or row of B is entirely zero contributes nothing to the midpoint
+#   product A B; it keeps g_k = 0 and comes after the live indices, in index order (its radii may
+#   still count, so it is not dropped);
 # * g_k = floor((b_k - a_k) / 2): column k of A is multiplied by 2^g_k and row k of B by 2^-g_k
 #   (exact, and A B is unchanged), which brings both tops to within one of (a_k + b_k) / 2;
 # * the live indices are ordered by a_k + b_k, the magnitude bound of their products (ties by
 #   index), and the greedy extraction of Section IV-A runs over that order.
 
 def inner_order(A, B, M, K, N):
-    """``(order, g)``: the live inner indices in planning order and the inner scaling exponent of
-    every index (0 for the left-out ones)."""
+    """``(order, g)``: a permutation of the inner indices in planning order (the live ones by
+    a_k + b_k, then the dead ones) and the inner scaling exponent of every index (0 when dead)."""
     g = [0] * K
-    keyed = []
+    keyed, dead = [], []
     for k in range(K):
         ta = [top_bottom(A, i * K + k) for i in range(M)]
         tb = [top_bottom(B, k * N + j) for j in range(N)]
         ta = [t[0] for t in ta if t is not None]
         tb = [t[0] for t in tb if t is not None]
         if not ta or not tb:
+            dead.append(k)
             continue
         a, b = max(ta), max(tb)
         g[k] = (b - a) // 2
         keyed.append((a + b, k))
     keyed.sort()
-    return [k for _, k in keyed], g
+    return [k for _, k in keyed] + dead, g
 
 
 def plan_ordered(A, B, M, K, N, prec):
