@@ -2513,6 +2513,134 @@ __global__ void z3m_kernel(uint16_t *z, int NM, int64_t plane) {
   *(uint4 *)(z + o2) = out[1];
 }
 
+// ------------------------------------------------------------------------- inner ordering
+//
+// Section IV-B suggests an inner scaling G_s G_s^-1 of the columns of A_s against the rows of B_s,
+// combined with permutations.  Reading (the paper leaves the strategy open): a_k and b_k are the
+// largest tops of column k of A and row k of B; g_k = floor((b_k - a_k) / 2) multiplies column k
+// of A by 2^g_k and row k of B by 2^-g_k, which leaves A B unchanged and brings both tops to within
+// one of (a_k + b_k) / 2; the indices are ordered by a_k + b_k (ties by index), and those whose
+// column of A or row of B has only zero midpoints come last with g_k = 0 (their radii may still
+// count).  The greedy extraction of Section IV-A then runs over that order, on copies of the
+// operands permuted and scaled so (`gather_inner_kernel`); the basecase dots read the original
+// operands at the original indices.  Off unless ARBGPU_INNER_ORDER=1.
+
+static bool inner_order_enabled() {
+  const char *e = getenv("ARBGPU_INNER_ORDER");
+  return e && !strcmp(e, "1");
+}
+
+// Bytes of a ball array of `count` entries with `nl` limb planes (256-byte aligned parts).
+static size_t ball_array_bytes(int64_t count, int nl) {
+  auto al = [](size_t v) { return (v + 255) / 256 * 256; };
+  const size_t c = (size_t)(count > 0 ? count : 1);
+  return al(8 * c * nl) + al(8 * c) + al(4 * c) + al(4 * c) + al(8 * c);
+}
+
+static BallsOut ball_array_at(uint8_t *base, int64_t count, int nl) {
+  auto al = [](size_t v) { return (v + 255) / 256 * 256; };
+  const size_t c = (size_t)(count > 0 ? count : 1);
+  BallsOut b{};
+  b.limbs = (uint64_t *)base;
+  b.stride = (int64_t)c;
+  b.nlimbs = nl;
+  size_t o = al(8 * c * nl);
+  b.exp = (int64_t *)(base + o);
+  o += al(8 * c);
+  b.flags = (uint32_t *)(base + o);
+  o += al(4 * c);
+  b.rad_man = (uint32_t *)(base + o);
+  o += al(4 * c);
+  b.rad_exp = (int64_t *)(base + o);
+  return b;
+}
+
+// a[k] = largest top of column k of A (M x K entry tops, row-major), b[k] = largest top of row k
+// of B (K x N); INT64_MIN when every entry is zero.  One CTA per inner index.
+__global__ void __launch_bounds__(256) inner_tops_kernel(const int64_t *tA, const int64_t *tB,
+                                                         int64_t M, int64_t K, int64_t N,
+                                                         int64_t *a, int64_t *b) {
+  __shared__ long long s_m[2];
+  const int64_t k = blockIdx.x;
+  if (threadIdx.x < 2) s_m[threadIdx.x] = INT64_MIN;
+  __syncthreads();
+  long long ma = INT64_MIN, mb = INT64_MIN;
+  for (int64_t i = threadIdx.x; i < M; i += blockDim.x) ma = max(ma, (long long)tA[i * K + k]);
+  for (int64_t j = threadIdx.x; j < N; j += blockDim.x) mb = max(mb, (long long)tB[k * N + j]);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    ma = max(ma, __shfl_xor_sync(0xffffffffu, ma, o));
+    mb = max(mb, __shfl_xor_sync(0xffffffffu, mb, o));
+  }
+  if ((threadIdx.x & 31) == 0) {
+    atomicMax(&s_m[0], ma);
+    atomicMax(&s_m[1], mb);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    a[k] = s_m[0];
+    b[k] = s_m[1];
+  }
+}
+
+// Reordered, scaled copy of an operand: A'[i, t] = A[i, ord[t]] 2^g[ord[t]] (rows x K, row-major
+// with leading dimension K) or, for B, B'[t, j] = B[ord[t], j] 2^-g[ord[t]] (K x cols).  Midpoint
+// and radius exponents move by the same amount, so each ball is scaled exactly.  A moved exponent
+// outside the fast path's range sets *out_of_range (the caller then keeps the original order).
+__global__ void gather_inner_kernel(const BallsView X, int64_t ld, bool is_b, int64_t rows,
+                                    int64_t K, int64_t cols, const int32_t *ord, const int64_t *g,
+                                    BallsOut Y, int *out_of_range) {
+  const int64_t n = is_b ? K * cols : rows * K;
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= n) return;
+  int64_t src, k;
+  if (is_b) {
+    const int64_t t = idx / cols, j = idx - t * cols;
+    k = ord[t];
+    src = k * ld + j;
+  } else {
+    const int64_t i = idx / K, t = idx - i * K;
+    k = ord[t];
+    src = i * ld + k;
+  }
+  const int64_t d = is_b ? -g[k] : g[k];
+  for (int q = 0; q < X.nlimbs; ++q)
+    Y.limbs[(int64_t)q * Y.stride + idx] = __ldg(X.limbs + (int64_t)q * X.stride + src);
+  const uint32_t fl = __ldg(X.flags + src);
+  const uint32_t rm = __ldg(X.rad_man + src);
+  const int64_t e = __ldg(X.exp + src), re = __ldg(X.rad_exp + src);
+  const bool mid = !(fl & (ARBGPU_FLAG_ZERO | SPECIAL_MASK));
+  const int64_t e2 = mid ? e + d : e, re2 = rm ? re + d : re;
+  if ((mid && (e2 >= EXP_LIMIT || e2 <= -EXP_LIMIT)) || (rm && (re2 >= EXP_LIMIT || re2 <= -EXP_LIMIT)))
+    atomicOr(out_of_range, 1);
+  Y.flags[idx] = fl;
+  Y.exp[idx] = e2;
+  Y.rad_man[idx] = rm;
+  Y.rad_exp[idx] = re2;
+}
+
+// The order and scaling of the inner indices from their tops (host side of the reading above).
+static void inner_order_host(const std::vector<int64_t> &a, const std::vector<int64_t> &b,
+                             std::vector<int32_t> &ord, std::vector<int64_t> &g) {
+  const int64_t K = (int64_t)a.size();
+  std::vector<std::pair<int64_t, int32_t>> live;
+  std::vector<int32_t> dead;
+  g.assign((size_t)K, 0);
+  for (int64_t k = 0; k < K; ++k) {
+    if (a[k] == INT64_MIN || b[k] == INT64_MIN) {
+      dead.push_back((int32_t)k);
+      continue;
+    }
+    const int64_t d = b[k] - a[k];
+    g[k] = d >= 0 ? d / 2 : -((-d + 1) / 2);  // floor(d / 2)
+    live.push_back({a[k] + b[k], (int32_t)k});
+  }
+  std::sort(live.begin(), live.end());
+  ord.clear();
+  for (const auto &v : live) ord.push_back(v.second);
+  ord.insert(ord.end(), dead.begin(), dead.end());
+}
+
 // ------------------------------------------------------------------------- workspace and driver
 
 struct BlockWs {
@@ -2529,6 +2657,9 @@ struct BlockWs {
   size_t resA, resB, cdig, ccar, craw;
   // complex product by eq. 2: residue planes of the parts and their sum, three residue products
   size_t r3A, r3B, z3;
+  // inner ordering (Section IV-B): per-index tops, the order and scaling, the reordered operands,
+  // the range flag of the scaled exponents
+  size_t ia, ib, iord, ig, oA, oB, irange;
   size_t total;
   int Smax, NDmax, Gmax, Gr, maxb, nacc, NMmax, NMWmax;
   int64_t Kp, Mp, Np;
@@ -2606,6 +2737,15 @@ static BlockWs block_ws(arbgpu_ctx *ctx, int64_t M, int64_t K, int64_t N, int pr
   w.cdig = take((size_t)3 * w.NMmax * w.Mp * w.Np);
   w.craw = take((size_t)2 * 8 * w.Mp * w.Np);  // the two radius products as int64
   w.ccar = take(256);  // the multimodular GEMM writes no carries
+  if (inner_order_enabled()) {
+    w.ia = take(8 * (size_t)K);
+    w.ib = take(8 * (size_t)K);
+    w.iord = take(4 * (size_t)K);
+    w.ig = take(8 * (size_t)K);
+    w.oA = take(ball_array_bytes(M * K, BL_MAX_NL));
+    w.oB = take(ball_array_bytes(K * N, BL_MAX_NL));
+    w.irange = take(4);
+  }
   if (cplx && m3) {
     w.r3A = take((size_t)3 * 2 * w.NMmax * M * w.Kp * 2);
     w.r3B = take((size_t)3 * 2 * w.NMmax * N * w.Kp * 2);
@@ -2877,7 +3017,8 @@ static arbgpu_status accumulate_product(arbgpu_ctx *ctx, const BlockWs &w, uint8
                                         int64_t K, int64_t N, int64_t ldx, int64_t ldy, int prec,
                                         const Lines &full, const BlockStats &hs, bool negate,
                                         int combo, const AccView &av, cudaStream_t s,
-                                        std::vector<int32_t> &basek) {
+                                        std::vector<int32_t> &basek,
+                                        const std::vector<int32_t> *kmap = nullptr) {
   const int64_t h = height_bound(prec, hs);
   std::vector<int32_t> hb;
   std::vector<BlockStats> hbs;
@@ -2935,7 +3076,8 @@ static arbgpu_status accumulate_product(arbgpu_ctx *ctx, const BlockWs &w, uint8
   for (int b = 0; b < hnb; ++b) {
     const int64_t k0 = hb[3 * b], k1 = hb[3 * b + 1];
     if (hb[3 * b + 2]) {
-      for (int64_t k = k0; k < k1; ++k) basek.push_back((int32_t)((k << 2) | combo));
+      for (int64_t k = k0; k < k1; ++k)  // (inner indices of the caller's operands)
+        basek.push_back((int32_t)(((kmap ? (int64_t)(*kmap)[k] : k) << 2) | combo));
       continue;
     }
     const int64_t oM = planned ? (int64_t)b * M : 0, oN = planned ? (int64_t)b * N : 0;
@@ -3136,6 +3278,71 @@ static arbgpu_status run_3m(arbgpu_ctx *ctx, const BlockWs &w, uint8_t *ws, cons
   return cudaGetLastError() == cudaSuccess ? ARBGPU_OK : ARBGPU_ERR_CUDA;
 }
 
+// accumulate_product over the inner order (see "inner ordering" above): the order and scaling
+// from the per-index tops, reordered and scaled copies of X and Y, then the same greedy blocks,
+// products and basecase dots; basecase indices are reported in X's and Y's own numbering.
+static arbgpu_status accumulate_product_ordered(arbgpu_ctx *ctx, const BlockWs &w, uint8_t *ws,
+                                                const BallsView &Xv, const BallsView &Yv,
+                                                int64_t M, int64_t K, int64_t N, int64_t ldx,
+                                                int64_t ldy, int prec, const Lines &full,
+                                                const BlockStats &hs, bool negate, int combo,
+                                                const AccView &av, cudaStream_t s,
+                                                std::vector<int32_t> &basek) {
+  if (Xv.nlimbs > BL_MAX_NL || Yv.nlimbs > BL_MAX_NL) return ARBGPU_ERR_LIMIT;
+  int64_t *tA = (int64_t *)(ws + w.tA), *bA = (int64_t *)(ws + w.bA);
+  int64_t *tB = (int64_t *)(ws + w.tB), *bB = (int64_t *)(ws + w.bB);
+  int64_t *da = (int64_t *)(ws + w.ia), *db = (int64_t *)(ws + w.ib);
+  {
+    LaunchScope sc(ctx, s, "entry_tb", M * K + K * N);
+    entry_tb_kernel<<<(unsigned)((M * K + 255) / 256), 256, 0, s>>>(Xv, M, K, ldx, tA, bA);
+    entry_tb_kernel<<<(unsigned)((K * N + 255) / 256), 256, 0, s>>>(Yv, K, N, ldy, tB, bB);
+  }
+  {
+    LaunchScope sc(ctx, s, "inner_tops", M * K + K * N);
+    inner_tops_kernel<<<(unsigned)K, 256, 0, s>>>(tA, tB, M, K, N, da, db);
+  }
+  std::vector<int64_t> a((size_t)K), b((size_t)K), g;
+  std::vector<int32_t> ord;
+  if (cudaGetLastError() != cudaSuccess ||
+      cudaMemcpyAsync(a.data(), da, 8 * (size_t)K, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaMemcpyAsync(b.data(), db, 8 * (size_t)K, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess)
+    return ARBGPU_ERR_CUDA;
+  inner_order_host(a, b, ord, g);
+  int32_t *dord = (int32_t *)(ws + w.iord);
+  int64_t *dg = (int64_t *)(ws + w.ig);
+  if (cudaMemcpyAsync(dord, ord.data(), 4 * (size_t)K, cudaMemcpyHostToDevice, s) !=
+          cudaSuccess ||
+      cudaMemcpyAsync(dg, g.data(), 8 * (size_t)K, cudaMemcpyHostToDevice, s) != cudaSuccess)
+    return ARBGPU_ERR_CUDA;
+  const BallsOut oX = ball_array_at(ws + w.oA, M * K, Xv.nlimbs);
+  const BallsOut oY = ball_array_at(ws + w.oB, K * N, Yv.nlimbs);
+  int *drange = (int *)(ws + w.irange);
+  int hrange = 0;
+  if (cudaMemsetAsync(drange, 0, 4, s) != cudaSuccess) return ARBGPU_ERR_CUDA;
+  {
+    LaunchScope sc(ctx, s, "gather_inner", M * K + K * N);
+    gather_inner_kernel<<<(unsigned)((M * K + 255) / 256), 256, 0, s>>>(Xv, ldx, false, M, K, N,
+                                                                        dord, dg, oX, drange);
+    gather_inner_kernel<<<(unsigned)((K * N + 255) / 256), 256, 0, s>>>(Yv, ldy, true, M, K, N,
+                                                                        dord, dg, oY, drange);
+    if (cudaGetLastError() != cudaSuccess ||
+        cudaMemcpyAsync(&hrange, drange, 4, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+      return ARBGPU_ERR_CUDA;
+  }
+  if (hrange)  // a scaled exponent would leave the fast path's range: keep the original order
+    return accumulate_product(ctx, w, ws, Xv, Yv, M, K, N, ldx, ldy, prec, full, hs, negate,
+                              combo, av, s, basek);
+  const BallsView Xo{oX.limbs, oX.stride, oX.nlimbs, oX.exp, oX.flags, oX.rad_man, oX.rad_exp};
+  const BallsView Yo{oY.limbs, oY.stride, oY.nlimbs, oY.exp, oY.flags, oY.rad_man, oY.rad_exp};
+  // (`ord` and `g` stay alive until this returns: accumulate_product synchronises the stream)
+  const arbgpu_status st = accumulate_product(ctx, w, ws, Xo, Yo, M, K, N, K, N, prec, full, hs,
+                                              negate, combo, av, s, basek, &ord);
+  if (cudaStreamSynchronize(s) != cudaSuccess) return ARBGPU_ERR_CUDA;
+  return st;
+}
+
 // Ball matrix product by Algorithm 2 (real, or complex by four real products, Section IV-C).
 // Returns ARBGPU_ERR_LIMIT when the inputs hold special values or exceed the path's limits (the
 // caller then uses the classical algorithm).
@@ -3322,9 +3529,16 @@ arbgpu_status block_finish(arbgpu_ctx *ctx, const arbgpu_balls *C, const arbgpu_
   for (int t = 0; t < (p3.ok ? 0 : nprods); ++t) {
     const Prod &pr = prods[t];
     const BlockStats hs = merge_stats(hst[pr.xa], hst[2 + pr.yb]);
-    arbgpu_status st1 = accumulate_product(ctx, w, ws, Av[pr.xa], Bv[pr.yb], M, K, N, lda, ldb,
-                                           prec, lines_of(pr.xa, pr.yb), hs, pr.neg, pr.combo,
-                                           av[pr.part], s, basek[pr.part]);
+    const int64_t hb = height_bound(prec, hs);
+    // several blocks: over the inner order when it is enabled (its workspace exists)
+    const bool ordered = w.oA && (hs.hA > hb || hs.hB > hb);
+    arbgpu_status st1 =
+        ordered ? accumulate_product_ordered(ctx, w, ws, Av[pr.xa], Bv[pr.yb], M, K, N, lda, ldb,
+                                             prec, lines_of(pr.xa, pr.yb), hs, pr.neg, pr.combo,
+                                             av[pr.part], s, basek[pr.part])
+                : accumulate_product(ctx, w, ws, Av[pr.xa], Bv[pr.yb], M, K, N, lda, ldb, prec,
+                                     lines_of(pr.xa, pr.yb), hs, pr.neg, pr.combo, av[pr.part], s,
+                                     basek[pr.part]);
     if (st1 != ARBGPU_OK) return st1;
   }
   for (int q = 0; q < parts; ++q) {
