@@ -455,3 +455,21 @@ def test_tie_broken_below_the_rounding_window(arb, tail):
     (out,), names = _run_engine(arb, "crt", A, B, M, K, N, p)
     assert "crt_gemm" in names
     check_entries(out, A, B, M, K, N, p, [(i, j) for i in range(M) for j in range(N)], 2)
+
+
+def test_pascal_product_closed_form(arb):
+    """L L^T = C(i+j, i) for the lower-triangular Pascal matrix L_ik = C(i, k) (Vandermonde's
+    identity; Section V multiplies Pascal matrices): exact integers up to C(126, 63) < 2^122, so
+    at p = 128 every entry is exact with zero radius, through one scaled integer block."""
+    from math import comb
+    from tests.ballmake import make_balls
+    n, p = 64, 128
+    A = make_balls([comb(i, k) for i in range(n) for k in range(n)])
+    B = make_balls([comb(j, k) for k in range(n) for j in range(n)])
+    out, names = run_mm(arb, A, B, n, n, n, p, arb.ALG_BLOCK, nl_out=2, trace=True)
+    assert "plan" not in names  # one block
+    for i in range(n):
+        for j in range(n):
+            idx = i * n + j
+            assert X.dy_to_fraction(X.mid(out, idx)) == comb(i + j, i), (i, j)
+            assert int(out.rad_man[idx]) == 0, (i, j)
