@@ -235,7 +235,14 @@ def mat_mul_workspace_size(M, K, N, prec, a_nlimbs, b_nlimbs, complex_mode=False
 
 def mat_mul(C_out, A, B, M, K, N, prec, *, alg=ALG_AUTO, flags=0, lda=None, ldb=None, ldc=None,
             workspace=None, ctx=None, stream=None):
-    """Ball matrix product ``C = A * B`` (``arbgpu_mat_mul``); complex when A is a pair."""
+    """Ball matrix product ``C = A * B`` (``arbgpu_mat_mul``); complex when A is a pair.
+
+    ``A`` is M x K, ``B`` K x N, ``C_out`` M x N, row-major with leading dimensions ``lda``, ``ldb``,
+    ``ldc`` (default K, N, N).  ``alg``: ``ALG_AUTO`` (Algorithm 2 from M, K, N >= 48, dots below),
+    ``ALG_DOT`` (one Algorithm 1 dot per entry) or ``ALG_BLOCK`` (Algorithm 2).  ``flags``: 0 or
+    ``MM_COMPLEX_3M`` (complex midpoints by eq. 2 when the parts share one scaling in a single
+    block).  ``workspace``: a device tensor of at least ``mat_mul_workspace_size`` bytes for the
+    same arguments, else one cached in the context is used."""
     ctx = ctx or default_context()
     cplx = isinstance(A, (list, tuple))
     cs, As, Bs = _pair(C_out), _pair(A), _pair(B)
