@@ -25,7 +25,9 @@ Readings (each also used by the GPU planner):
 
 ``plan_ordered`` / ``scaled_block_ordered`` restate Section IV-B's suggested improvement (an inner
 scaling of the columns of A_s against the rows of B_s, combined with a permutation of the inner
-index); its reading is given above ``inner_order``.
+index); its reading is given above ``inner_order``.  ``plan_complex_shared`` /
+``scaled_block_complex`` / ``eq2_block_products`` restate Section IV-C's complex product by eq. 2
+over blocks planned for both parts together.
 """
 from __future__ import annotations
 
@@ -225,6 +227,76 @@ def scaled_block_ordered(A, B, M, K, N, ks, g):
         cols.append([0 if tb is None else tb[2] << (v + fj) for tb, v in zip(col, sh)])
     Y = [[cols[j][t] for j in range(N)] for t in range(len(ks))]
     return e, f, X, Y
+
+
+# ---- Complex products by eq. 2 with several blocks (Section IV-C's second suggestion: a splitting
+# and scaling strategy that considers the real and imaginary parts together).
+#
+# Reading: the height of a row of A_s (a column of B_s) is taken over both parts, so each entry
+# contributes the larger top and the smaller bottom of its real and imaginary part; the greedy
+# extraction of Section IV-A runs on those merged values, and each full block takes one scaling
+# per row and per column for both parts.  Then X_re + X_im and Y_re + Y_im are integers and, per
+# block, Re = P1 - P2 and Im = P3 - P1 - P2 with P1 = X_re Y_re, P2 = X_im Y_im,
+# P3 = (X_re + X_im)(Y_re + Y_im) (eq. 2), all exact.
+
+def _merged_tb(re, im, idx):
+    a, b = top_bottom(re, idx), top_bottom(im, idx)
+    if a is None and b is None:
+        return None
+    if a is None or b is None:
+        t = a if a is not None else b
+        return t[0], t[1]
+    return max(a[0], b[0]), min(a[1], b[1])
+
+
+def plan_complex_shared(A, B, M, K, N, prec):
+    """``(h, blocks)`` for the complex product of ``A = (A_re, A_im)`` and ``B = (B_re, B_im)``
+    with the merged heights; h from the largest precision over all four parts."""
+    pA = max(precision_of(A[0], M * K), precision_of(A[1], M * K))
+    pB = max(precision_of(B[0], K * N), precision_of(B[1], K * N))
+    h = height_bound(prec, pA, pB)
+    tbA = [[_merged_tb(A[0], A[1], i * K + k) for k in range(K)] for i in range(M)]
+    tbB = [[_merged_tb(B[0], B[1], k * N + j) for k in range(K)] for j in range(N)]
+    return h, _greedy(tbA, tbB, M, N, K, h)
+
+
+def scaled_block_complex(A, B, M, K, N, start, stop):
+    """``(e, f, (X_re, X_im), (Y_re, Y_im))`` of block ``[start, stop)`` under one minimal scaling
+    per row of A and per column of B shared by both parts."""
+    e = []
+    Xs = ([], [])
+    for i in range(M):
+        rows = [[top_bottom(A[q], i * K + k) for k in range(start, stop)] for q in (0, 1)]
+        lows = [tb[3] for row in rows for tb in row if tb is not None]
+        ei = -min(lows) if lows else 0
+        e.append(ei)
+        for q in (0, 1):
+            Xs[q].append([0 if tb is None else tb[2] << (tb[3] + ei) for tb in rows[q]])
+    f = []
+    cols = ([], [])
+    for j in range(N):
+        cs = [[top_bottom(B[q], k * N + j) for k in range(start, stop)] for q in (0, 1)]
+        lows = [tb[3] for col in cs for tb in col if tb is not None]
+        fj = -min(lows) if lows else 0
+        f.append(fj)
+        for q in (0, 1):
+            cols[q].append([0 if tb is None else tb[2] << (tb[3] + fj) for tb in cs[q]])
+    Ys = tuple([[cols[q][j][t] for j in range(N)] for t in range(stop - start)] for q in (0, 1))
+    return e, f, Xs, Ys
+
+
+def eq2_block_products(Xs, Ys):
+    """``(Re, Im)`` of one block from three integer products (eq. 2)."""
+    Xr, Xi = Xs
+    Yr, Yi = Ys
+    P1 = int_matmul(Xr, Yr)
+    P2 = int_matmul(Xi, Yi)
+    Xsum = [[a + b for a, b in zip(ra, rb)] for ra, rb in zip(Xr, Xi)]
+    Ysum = [[a + b for a, b in zip(ra, rb)] for ra, rb in zip(Yr, Yi)]
+    P3 = int_matmul(Xsum, Ysum)
+    Re = [[p1 - p2 for p1, p2 in zip(r1, r2)] for r1, r2 in zip(P1, P2)]
+    Im = [[p3 - p1 - p2 for p3, p1, p2 in zip(r3, r1, r2)] for r3, r1, r2 in zip(P3, P1, P2)]
+    return Re, Im
 
 
 def int_matmul(X, Y):

@@ -383,3 +383,126 @@ def test_planted_mistakes_in_the_ordered_plan_are_caught(monkeypatch):
     assert _fails(test_inner_order_is_sorted_balanced_and_leaves_out_dead_indices)
     monkeypatch.setattr(alg2, "inner_order", orig)
     assert not _fails(test_inner_order_is_sorted_balanced_and_leaves_out_dead_indices)
+
+
+# ------------------------------------------------------------------ complex, eq. 2 over shared blocks
+# (Section IV-C's second suggestion, in the reading of ``oracle.alg2.plan_complex_shared``)
+
+def exact_complex_product(A, B, M, K, N):
+    re = [[Fraction(0)] * N for _ in range(M)]
+    im = [[Fraction(0)] * N for _ in range(M)]
+    for i in range(M):
+        for j in range(N):
+            for k in range(K):
+                ar, ai = ball_values(A[0], i * K + k)[0], ball_values(A[1], i * K + k)[0]
+                br, bi = ball_values(B[0], k * N + j)[0], ball_values(B[1], k * N + j)[0]
+                re[i][j] += ar * br - ai * bi
+                im[i][j] += ar * bi + ai * br
+    return re, im
+
+
+def recombined_complex(A, B, M, K, N, prec, products=alg2.eq2_block_products):
+    h, blocks = alg2.plan_complex_shared(A, B, M, K, N, prec)
+    re = [[Fraction(0)] * N for _ in range(M)]
+    im = [[Fraction(0)] * N for _ in range(M)]
+    for start, stop, base in blocks:
+        if base:
+            sub_re, sub_im = exact_complex_product(
+                [_cols(A[q], M, K, start, stop) for q in (0, 1)],
+                [_rows(B[q], K, N, start, stop) for q in (0, 1)], M, stop - start, N)
+        else:
+            e, f, Xs, Ys = alg2.scaled_block_complex(A, B, M, K, N, start, stop)
+            R, I = products(Xs, Ys)
+            sc = [[Fraction(2) ** (-e[i] - f[j]) for j in range(N)] for i in range(M)]
+            sub_re = [[R[i][j] * sc[i][j] for j in range(N)] for i in range(M)]
+            sub_im = [[I[i][j] * sc[i][j] for j in range(N)] for i in range(M)]
+        for i in range(M):
+            for j in range(N):
+                re[i][j] += sub_re[i][j]
+                im[i][j] += sub_im[i][j]
+    return blocks, re, im
+
+
+def _cols(raw, M, K, start, stop):
+    idx = [i * K + k for i in range(M) for k in range(start, stop)]
+    return _take(raw, idx)
+
+
+def _rows(raw, K, N, start, stop):
+    idx = [k * N + j for k in range(start, stop) for j in range(N)]
+    return _take(raw, idx)
+
+
+def _take(raw, idx):
+    from synth import RawBalls
+    idx = np.asarray(idx)
+    return RawBalls(raw.nlimbs, raw.limbs[:, idx].copy(), raw.exp[idx].copy(),
+                    raw.flags[idx].copy(), raw.rad_man[idx].copy(), raw.rad_exp[idx].copy())
+
+
+def _complex_case(kind):
+    from synth.workloads import complex_matmul_laplace
+    rng = np.random.default_rng(hash(kind) % 2**32)
+    if kind == "structured":
+        case = complex_matmul_laplace(n=32, structured=True)
+        return case.A, case.B, 32, 32, 32, 128
+    if kind == "banded":  # columns 40..79 of both parts of A sit 2^900 higher: two full blocks
+        M, K, N, p = 3, 80, 2, 64
+        ea = rng.integers(-5, 5, size=M * K)
+        for k in range(40, 80):
+            ea[np.arange(M) * K + k] += 900
+        A = [random_balls(rng, M * K, 1, 64, exps=ea) for _ in "ri"]
+        B = [random_balls(rng, K * N, 1, 64, -5, 5) for _ in "ri"]
+        return A, B, M, K, N, p
+    M, K, N, p = 4, 40, 3, 128
+    A = [random_balls(rng, M * K, 2, 128, -20, 20) for _ in "ri"]
+    B = [random_balls(rng, K * N, 2, 128, -20, 20) for _ in "ri"]
+    if kind == "zero_im":
+        A[1].flags[:] = X.FLAG_ZERO
+        A[1].limbs[:] = 0
+    return A, B, M, K, N, p
+
+
+@pytest.mark.parametrize("kind", ["uniform", "structured", "zero_im", "banded"])
+def test_complex_shared_blocks_reproduce_exact_product(kind):
+    A, B, M, K, N, p = _complex_case(kind)
+    blocks, re, im = recombined_complex(A, B, M, K, N, p)
+    ere, eim = exact_complex_product(A, B, M, K, N)
+    assert re == ere and im == eim
+    assert blocks[0][0] == 0 and blocks[-1][1] == K
+    if kind in ("uniform", "zero_im"):
+        assert blocks == [(0, K, False)]
+    if kind == "banded":
+        assert blocks == [(0, 40, False), (40, 80, False)]
+
+
+def test_eq2_equals_the_four_products_on_a_shared_block():
+    A, B, M, K, N, p = _complex_case("uniform")
+    e, f, Xs, Ys = alg2.scaled_block_complex(A, B, M, K, N, 0, K)
+    R, I = alg2.eq2_block_products(Xs, Ys)
+    mm = alg2.int_matmul
+    rr, ii, ri, ir = mm(Xs[0], Ys[0]), mm(Xs[1], Ys[1]), mm(Xs[0], Ys[1]), mm(Xs[1], Ys[0])
+    assert R == [[a - b for a, b in zip(x, y)] for x, y in zip(rr, ii)]
+    assert I == [[a + b for a, b in zip(x, y)] for x, y in zip(ri, ir)]
+
+
+def test_shared_scaling_is_minimal_over_both_parts():
+    A, B, M, K, N, p = _complex_case("uniform")
+    e, f, Xs, Ys = alg2.scaled_block_complex(A, B, M, K, N, 0, K)
+    for i in range(M):
+        assert any(v & 1 for q in (0, 1) for v in Xs[q][i])  # minimal over both parts
+        for q in (0, 1):
+            for k in range(K):
+                assert Fraction(Xs[q][i][k]) == (ball_values(A[q], i * K + k)[0] *
+                                                 Fraction(2) ** e[i])
+    for j in range(N):
+        assert any(Ys[q][k][j] & 1 for q in (0, 1) for k in range(K))
+
+
+def test_planted_sign_slip_in_eq2_is_caught():
+    def wrong(Xs, Ys):  # P3 = (X_re + X_im)(Y_re - Y_im)
+        return alg2.eq2_block_products(Xs, (Ys[0], [[-v for v in r] for r in Ys[1]]))
+    A, B, M, K, N, p = _complex_case("uniform")
+    _, re, im = recombined_complex(A, B, M, K, N, p, products=wrong)
+    ere, eim = exact_complex_product(A, B, M, K, N)
+    assert (re, im) != (ere, eim)
