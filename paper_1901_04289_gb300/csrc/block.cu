@@ -2619,28 +2619,6 @@ __global__ void gather_inner_kernel(const BallsView X, int64_t ld, bool is_b, in
   Y.rad_exp[idx] = re2;
 }
 
-// The order and scaling of the inner indices from their tops (host side of the reading above).
-static void inner_order_host(const std::vector<int64_t> &a, const std::vector<int64_t> &b,
-                             std::vector<int32_t> &ord, std::vector<int64_t> &g) {
-  const int64_t K = (int64_t)a.size();
-  std::vector<std::pair<int64_t, int32_t>> live;
-  std::vector<int32_t> dead;
-  g.assign((size_t)K, 0);
-  for (int64_t k = 0; k < K; ++k) {
-    if (a[k] == INT64_MIN || b[k] == INT64_MIN) {
-      dead.push_back((int32_t)k);
-      continue;
-    }
-    const int64_t d = b[k] - a[k];
-    g[k] = d >= 0 ? d / 2 : -((-d + 1) / 2);  // floor(d / 2)
-    live.push_back({a[k] + b[k], (int32_t)k});
-  }
-  std::sort(live.begin(), live.end());
-  ord.clear();
-  for (const auto &v : live) ord.push_back(v.second);
-  ord.insert(ord.end(), dead.begin(), dead.end());
-}
-
 // ------------------------------------------------------------------------- workspace and driver
 
 struct BlockWs {

@@ -208,6 +208,12 @@ struct CrtDevTables {
 };
 arbgpu_status crt_device_tables(arbgpu_ctx *ctx, const CrtPlan *plan, CrtDevTables *out);
 
+// Inner ordering (inner_order.cu), from a_k / b_k = the largest tops of column k of A / row k of B
+// (INT64_MIN when all zero): `ord` lists the indices with a nonzero midpoint product by a_k + b_k
+// (ties by index), then the others; g_k = floor((b_k - a_k) / 2) for the former, 0 for the latter.
+void inner_order_host(const std::vector<int64_t> &a, const std::vector<int64_t> &b,
+                      std::vector<int32_t> &ord, std::vector<int64_t> &g);
+
 // Dot-kernel size class for a precision, a maximal term count and operand limb counts (-1: none).
 int dot_class_for_problem(int prec, int64_t max_terms, int max_nlimbs);
 
