@@ -1815,9 +1815,10 @@ static int product_limbs(const IntProduct &p) {
 // with q_{t,n} the balanced bytes of Q_t = M / m_t: a product of the byte matrix
 // [entries][(t, byte)] and the table [(t, byte)][n].  |S_n| < 2^22 (at most 128 products of
 // magnitude <= 255 * 128), so the FP32 sums are exact.  One more column weighs the bytes with
-// 1/m_t and 256/m_t rounded to BF16: its sum is sum_t z_t / m_t with error below NM 2^-9 <= 1/8,
-// and since sum_t z_t / m_t = q + T / M with |T / M| < 1/8, its rint is the q of
-// T = sum_t z_t Q_t - q M.  The drain forms T = sum_n 256^n (S_n - q M_n), M_n the balanced bytes
+// 1/m_t and 256/m_t rounded to BF16 (the second is exactly 256 times the first): its sum is
+// sum_t z_t / m_t with error below sum_t m_t |bf16(1/m_t) - 1/m_t| < NM 2^-8 <= 1/4 (0.118 for
+// the 64 largest primes below 2^16), and since sum_t z_t / m_t = q + T / M with |T / M| < 1/8,
+// the total stays below 1/2 and its rint is the q of T = sum_t z_t Q_t - q M.  The drain forms T = sum_n 256^n (S_n - q M_n), M_n the balanced bytes
 // of M, with carries between 32-bit words, then rounds it as block_round does.
 //
 // Roles (one CTA per SM, persistent over tiles of 128 consecutive entries of a row of C): one

@@ -15,6 +15,7 @@ from __future__ import annotations
 import os
 import shutil
 import subprocess
+from fractions import Fraction
 
 import numpy as np
 import pytest
@@ -122,6 +123,16 @@ def test_crt_tables(harness, NM):
             assert abs(q1 - 1 / m) <= 2 ** -8 / m and abs(q256 - 256 / m) <= 2 ** -8 * 256 / m
         mb = [np.array([v], dtype=np.uint32).view(np.float32)[0] for v in t["mbytes"]]
         assert all(-128 <= v <= 127 for v in mb) and balanced_sum([int(v) for v in mb]) == M
+        # the q column: with z_t = l + 256 h < m_t, sum_t z_t w_t differs from sum_t z_t / m_t by
+        # less than sum_t m_t |w_t - 1/m_t|; with |T / M| < 1/8 its rint is q while that stays
+        # below 3/8 (and 256 / m_t's weight is exactly 256 times 1 / m_t's)
+        err = Fraction(0)
+        for k, m in enumerate(mods):
+            w1 = Fraction(bf16_value(cw[NQ * 128 + 2 * k]))
+            w256 = Fraction(bf16_value(cw[NQ * 128 + 2 * k + 1]))
+            assert w256 == 256 * w1
+            err += m * abs(w1 - Fraction(1, m))
+        assert err < Fraction(1, 4)
 
 
 def test_modulus_count_covers_the_bits(harness):
