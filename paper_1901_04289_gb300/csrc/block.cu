@@ -18,6 +18,7 @@
 #include <mutex>
 #include <vector>
 
+#include "inner_order.cuh"
 #include "internal.h"
 #include "round_regs.cuh"
 #include "tc_gemm.cuh"
@@ -2584,40 +2585,15 @@ __global__ void __launch_bounds__(256) inner_tops_kernel(const int64_t *tA, cons
   }
 }
 
-// Reordered, scaled copy of an operand: A'[i, t] = A[i, ord[t]] 2^g[ord[t]] (rows x K, row-major
-// with leading dimension K) or, for B, B'[t, j] = B[ord[t], j] 2^-g[ord[t]] (K x cols).  Midpoint
-// and radius exponents move by the same amount, so each ball is scaled exactly.  A moved exponent
-// outside the fast path's range sets *out_of_range (the caller then keeps the original order).
+// Reordered, scaled copy of an operand (gather_inner_entry, inner_order.cuh), one thread per
+// entry of the copy.
 __global__ void gather_inner_kernel(const BallsView X, int64_t ld, bool is_b, int64_t rows,
                                     int64_t K, int64_t cols, const int32_t *ord, const int64_t *g,
                                     BallsOut Y, int *out_of_range) {
   const int64_t n = is_b ? K * cols : rows * K;
   const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= n) return;
-  int64_t src, k;
-  if (is_b) {
-    const int64_t t = idx / cols, j = idx - t * cols;
-    k = ord[t];
-    src = k * ld + j;
-  } else {
-    const int64_t i = idx / K, t = idx - i * K;
-    k = ord[t];
-    src = i * ld + k;
-  }
-  const int64_t d = is_b ? -g[k] : g[k];
-  for (int q = 0; q < X.nlimbs; ++q)
-    Y.limbs[(int64_t)q * Y.stride + idx] = __ldg(X.limbs + (int64_t)q * X.stride + src);
-  const uint32_t fl = __ldg(X.flags + src);
-  const uint32_t rm = __ldg(X.rad_man + src);
-  const int64_t e = __ldg(X.exp + src), re = __ldg(X.rad_exp + src);
-  const bool mid = !(fl & (ARBGPU_FLAG_ZERO | SPECIAL_MASK));
-  const int64_t e2 = mid ? e + d : e, re2 = rm ? re + d : re;
-  if ((mid && (e2 >= EXP_LIMIT || e2 <= -EXP_LIMIT)) || (rm && (re2 >= EXP_LIMIT || re2 <= -EXP_LIMIT)))
-    atomicOr(out_of_range, 1);
-  Y.flags[idx] = fl;
-  Y.exp[idx] = e2;
-  Y.rad_man[idx] = rm;
-  Y.rad_exp[idx] = re2;
+  if (gather_inner_entry(X, ld, is_b, K, cols, ord, g, Y, idx)) atomicOr(out_of_range, 1);
 }
 
 // ------------------------------------------------------------------------- workspace and driver
