@@ -234,8 +234,8 @@ typedef struct {
   int64_t M, K, N, lda, ldb, ldc;
   int32_t prec;
   int32_t complex_mode;
-  int32_t alg;
-  uint32_t flags;
+  int32_t alg;    /* as for arbgpu_mat_mul */
+  uint32_t flags; /* as for arbgpu_mat_mul: 0 or ARBGPU_MM_COMPLEX_3M */
 } arbgpu_matmul_desc;
 
 arbgpu_status arbgpu_mat_mul_batched(arbgpu_ctx *ctx, const arbgpu_matmul_desc *descs,

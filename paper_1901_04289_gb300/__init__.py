@@ -265,8 +265,9 @@ def mat_mul(C_out, A, B, M, K, N, prec, *, alg=ALG_AUTO, flags=0, lda=None, ldb=
 
 def mat_mul_batched(items, *, workspace=None, ctx=None, stream=None):
     """Grouped batch of ball matrix products (``arbgpu_mat_mul_batched``).  ``items``: list of
-    dicts with keys C, A, B (Balls or (re, im) pairs), M, K, N, prec and optional alg, lda, ldb,
-    ldc.  Small classical items run in one grouped launch, the others by the block algorithm."""
+    dicts with keys C, A, B (Balls or (re, im) pairs), M, K, N, prec and optional alg, flags
+    (``MM_COMPLEX_3M``), lda, ldb, ldc.  Small classical items run in one grouped launch, the
+    others by the block algorithm."""
     ctx = ctx or default_context()
     arr = (_lib.CMatmulDesc * len(items))()
     for q, it in enumerate(items):
