@@ -267,3 +267,58 @@ def test_reduced_precision_of_a_zero_midpoint_is_two_bits():
     assert res["prec"] == 2
     m, r = out_mid_rad(res, 2)
     assert F(m) == 0 and F(r) > 0
+
+
+# ---- complex dots (Section III-F): two real dots of length 2N, ac - bd and ad + bc
+
+def _complex_case(seed, n, prec, nl, spread, rad_bits):
+    rng = np.random.default_rng(seed)
+    mk = lambda: random_balls(rng, n, nl, 64 * nl, -spread, spread, rad_bits=rad_bits,  # noqa
+                              rad_zero_frac=0.5, zero_frac=0.1)
+    return (mk(), mk()), (mk(), mk())
+
+
+@pytest.mark.parametrize("seed", range(4))
+@pytest.mark.parametrize("sub,with_init", [(False, False), (True, True)])
+def test_complex_dot_against_exact(seed, sub, with_init):
+    n, prec, nl = 9, 128, 2
+    x, y = _complex_case(50 + seed, n, prec, nl, 40, 120)
+    init = None
+    if with_init:
+        rng = np.random.default_rng(seed)
+        init = ((random_balls(rng, 1, nl, 128, -5, 5, rad_bits=100),
+                 random_balls(rng, 1, nl, 128, -5, 5, rad_bits=100)), 0)
+    re, im = alg1.complex_dot_raw(x, range(n), y, range(n), prec, nl, sub=sub, initial=init)
+    xre, xim = X.complex_dot_terms(x, range(n), y, range(n), sub=sub)
+    for res, terms, q in ((re, xre, 0), (im, xim, 1)):
+        ib = X.ball(init[0][q], 0) if init else None
+        S, Sabs, R = X.dot_terms_exact(terms, ib)
+        m, r = out_mid_rad(res, nl)
+        assert X.contains(m, r, S, R)
+        assert X.accuracy_ratio(m, S, Sabs, prec) <= 1.0
+
+
+def test_complex_single_term_closed_form():
+    """(3/4 - 5/8 i)(7/2 + 1/16 i) = (21/8 + 5/128) + (3/64 - 35/16) i, exact at p = 64."""
+    x = (make_balls([Fraction(3, 4)]), make_balls([Fraction(-5, 8)]))
+    y = (make_balls([Fraction(7, 2)]), make_balls([Fraction(1, 16)]))
+    re, im = alg1.complex_dot_raw(x, [0], y, [0], 64, 1)
+    assert F(out_mid_rad(re, 1)[0]) == Fraction(21, 8) + Fraction(5, 128)
+    assert F(out_mid_rad(im, 1)[0]) == Fraction(3, 64) - Fraction(35, 16)
+    assert out_mid_rad(re, 1)[1] == (0, 0) and out_mid_rad(im, 1)[1] == (0, 0)
+
+
+def test_planted_complex_sign_slip_is_caught(monkeypatch):
+    """b d added instead of subtracted in the real part: containment fails."""
+    orig = alg1.complex_terms
+
+    def plus_bd(x, xidx, y, yidx, sub=False):
+        re, im = orig(x, xidx, y, yidx, sub)
+        return [(a, c, bool(sub)) for a, c, _ in re], im
+    monkeypatch.setattr(alg1, "complex_terms", plus_bd)
+    x, y = _complex_case(77, 6, 128, 2, 10, None)
+    re, _ = alg1.complex_dot_raw(x, range(6), y, range(6), 128, 2)
+    xre, _ = X.complex_dot_terms(x, range(6), y, range(6))
+    S, Sabs, R = X.dot_terms_exact(xre)
+    m, r = out_mid_rad(re, 2)
+    assert not X.contains(m, r, S, R)
