@@ -16,8 +16,9 @@ Readings (each also used by the GPU planner):
 * "height of a row below 2^h" is ``max_k top(a_ik) - min_k bottom(a_ik) <= h`` over the nonzero
   entries, where ``top`` is the exponent ``e`` with ``2^(e-1) <= |a| < 2^e`` and ``bottom`` the
   exponent of the lowest set bit; the same for the columns of ``B``.
-* The greedy search stops before the first index that breaks the bound, but a block always holds at
-  least one index.
+* The greedy search stops before the first index that breaks the bound.  When the first index
+  alone breaks it (an entry taller than h, which happens when p < p_A), the block is that one
+  index, so a block always holds at least one index and no full block ever exceeds h.
 * ``h`` is rounded down to an integer.
 * ``F_s`` scales column ``j`` (the figure's ``f_{i,s}`` index is read as ``f_{j,s}``).
 * All contributions to an entry are summed exactly and rounded once, so a product without basecase
@@ -108,15 +109,16 @@ def _greedy(tbA, tbB, M, N, K, h):
             return nha, nla, nhb, nlb
 
         st = admit(start)
-        if st is None:  # a single index always forms a block
-            st = _force(tbA, tbB, start, M, N)
-        hi_a, lo_a, hi_b, lo_b = st
-        while stop < K:
-            st = admit(stop)
-            if st is None:
-                break
+        if st is not None:
             hi_a, lo_a, hi_b, lo_b = st
-            stop += 1
+            while stop < K:
+                st = admit(stop)
+                if st is None:
+                    break
+                hi_a, lo_a, hi_b, lo_b = st
+                stop += 1
+        # else: the first index alone breaks the bound (an entry taller than h, e.g. p_A > h);
+        # the block is that index alone, so every block holds at least one index
         if stop - start < BASECASE:
             stop = start + min(BASECASE, K - start)
             blocks.append((start, stop, True))
@@ -124,14 +126,6 @@ def _greedy(tbA, tbB, M, N, K, h):
             blocks.append((start, stop, False))
         start = stop
     return blocks
-
-
-def _force(tbA, tbB, k, M, N):
-    hi_a = [tbA[i][k][0] if tbA[i][k] else None for i in range(M)]
-    lo_a = [tbA[i][k][1] if tbA[i][k] else None for i in range(M)]
-    hi_b = [tbB[j][k][0] if tbB[j][k] else None for j in range(N)]
-    lo_b = [tbB[j][k][1] if tbB[j][k] else None for j in range(N)]
-    return hi_a, lo_a, hi_b, lo_b
 
 
 def scaled_block(A, B, M, K, N, start, stop):

@@ -164,6 +164,109 @@ def test_greedy_blocks_are_within_height_and_maximal(drift):
         assert all(base for _, _, base in blocks)
 
 
+def _brute_plan(A, B, M, K, N, h):
+    """The plan rule written out by brute force: from each start, the longest range [start, t) in
+    which every row of A and column of B (heights recomputed from scratch for every range) has
+    height <= h, but at least one index; a range shorter than 30 is widened to min(30, K - start)
+    and marked as a basecase block."""
+    def line_ok(tbs):
+        tbs = [t for t in tbs if t is not None]
+        return not tbs or max(t[0] for t in tbs) - min(t[1] for t in tbs) <= h
+
+    def ok(start, stop):
+        return (all(line_ok([alg2.top_bottom(A, i * K + k) for k in range(start, stop)])
+                    for i in range(M)) and
+                all(line_ok([alg2.top_bottom(B, k * N + j) for k in range(start, stop)])
+                    for j in range(N)))
+    out, start = [], 0
+    while start < K:
+        t = start
+        while t < K and ok(start, t + 1):
+            t += 1
+        stop = max(t, start + 1)
+        if stop - start < alg2.BASECASE:
+            stop = start + min(alg2.BASECASE, K - start)
+            out.append((start, stop, True))
+        else:
+            out.append((start, stop, False))
+        start = stop
+    return out
+
+
+def _tall_case(kind):
+    """Products at p = 64 with some 1024-bit entries: p_A > p makes h = 1.25*64 + 192 = 272, so a
+    1024-bit entry alone is taller than h and its index can only form a block by itself."""
+    rng = np.random.default_rng(zlib.crc32(kind.encode()))
+    if kind == "all_tall":       # every entry is taller than h
+        M, K, N = 2, 40, 2
+        bits_a = np.full(M * K, 1024)
+    elif kind == "tall_then_zeros":  # row 0 of A: a tall entry at index 0, zeros after it
+        M, K, N = 3, 70, 2
+        bits_a = np.full(M * K, 64)
+        bits_a[0] = 1024
+    else:                        # "tall_in_middle": one tall entry at index 40 of row 1
+        M, K, N = 2, 100, 3
+        bits_a = np.full(M * K, 64)
+        bits_a[K + 40] = 1024
+    A = random_balls(rng, M * K, 16, bits_a, -5, 5)
+    B = random_balls(rng, K * N, 16, 64, -5, 5)
+    if kind == "tall_then_zeros":
+        A.limbs[:, 1:K] = 0
+        A.flags[1:K] = X.FLAG_ZERO
+        A.exp[1:K] = 0
+    return A, B, M, K, N, 64
+
+
+TALL_PLANS = {
+    "all_tall": [(0, 30, True), (30, 40, True)],
+    "tall_then_zeros": [(0, 30, True), (30, 70, False)],
+    "tall_in_middle": [(0, 40, False), (40, 70, True), (70, 100, False)],
+}
+
+
+@pytest.mark.parametrize("kind", sorted(TALL_PLANS))
+def test_entry_taller_than_h_forms_a_block_alone(kind):
+    """Section IV-A's greedy extraction when an entry is taller than h (p < p_A): the index of such
+    an entry is a block by itself (then widened to a basecase block), every block holds at least
+    one index, the plan equals the brute-force rule, and the blocks reproduce the exact product."""
+    A, B, M, K, N, p = _tall_case(kind)
+    h, blocks, C = recombined(A, B, M, K, N, p)
+    assert h == 272
+    assert blocks == TALL_PLANS[kind] == _brute_plan(A, B, M, K, N, h)
+    assert all(stop > start for start, stop, _ in blocks)
+    assert C == exact_product(A, B, M, K, N)
+
+
+def test_extending_a_forced_block_is_caught():
+    """A planted variant of the rule that keeps growing a block whose first index is taller than h
+    (while the next indices leave the tall lines empty) gives a different plan, which the
+    brute-force pin above rejects."""
+    A, B, M, K, N, p = _tall_case("tall_then_zeros")
+    h = 272
+
+    def tall_line_touched(start, k):
+        for i in range(M):
+            tbs = [alg2.top_bottom(A, i * K + t) for t in range(start, k + 1)]
+            if tbs[-1] is not None:
+                live = [t for t in tbs if t is not None]
+                if max(t[0] for t in live) - min(t[1] for t in live) > h:
+                    return True
+        for j in range(N):
+            tbs = [alg2.top_bottom(B, t * N + j) for t in range(start, k + 1)]
+            if tbs[-1] is not None:
+                live = [t for t in tbs if t is not None]
+                if max(t[0] for t in live) - min(t[1] for t in live) > h:
+                    return True
+        return False
+    stop = 1
+    while stop < K and not tall_line_touched(0, stop):
+        stop += 1
+    planted = [(0, stop, stop < alg2.BASECASE)]
+    assert planted == [(0, K, False)]
+    assert planted != _brute_plan(A, B, M, K, N, h)
+    assert alg2.plan(A, B, M, K, N, p)[1] == _brute_plan(A, B, M, K, N, h)
+
+
 def test_int_matmul_vs_numpy():
     rng = np.random.default_rng(4)
     Xm = rng.integers(-2**20, 2**20, size=(5, 7))
