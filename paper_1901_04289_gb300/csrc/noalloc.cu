@@ -49,12 +49,25 @@ extern "C" arbgpu_status arbgpu_int_mat_mul_noalloc(uint64_t *T, int32_t t_limbs
   local.trace = false;
   if (cudaDeviceGetAttribute(&local.sm_count, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
     return ARBGPU_ERR_CUDA;
+  if (t_limbs > 2 * 32 + 4) return ARBGPU_ERR_INVALID;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (M == 0 || N == 0 || K == 0) {
+    // No scratch is needed: an empty product writes nothing, K = 0 writes zeros.
+    if (status && cudaMemsetAsync(status, 0, sizeof(int), s) != cudaSuccess) return ARBGPU_ERR_CUDA;
+    return arbgpu::int_mat_mul_run(&local, T, t_limbs, X, x_limbs, Y, y_limbs, M, K, N, nullptr,
+                                   0, s);
+  }
+  // Every operand and output entry takes at least one byte of scratch, so these products bound
+  // the layout's size before it is computed; all three are below 2^61 and cannot wrap.
+  const uint64_t cap = ARBGPU_NOALLOC_SCRATCH_BYTES;
+  if ((uint64_t)M * (uint64_t)K > cap || (uint64_t)K * (uint64_t)N > cap ||
+      (uint64_t)M * (uint64_t)N > cap)
+    return ARBGPU_ERR_LIMIT;
   const size_t need = arbgpu::int_mat_mul_workspace(&local, x_limbs, y_limbs, M, K, N);
   if (need > ARBGPU_NOALLOC_SCRATCH_BYTES) return ARBGPU_ERR_LIMIT;
   void *scratch = nullptr;
   const arbgpu_status st = scratch_on_device(dev, &scratch);
   if (st != ARBGPU_OK) return st;
-  cudaStream_t s = (cudaStream_t)stream;
   if (status && cudaMemsetAsync(status, 0, sizeof(int), s) != cudaSuccess) return ARBGPU_ERR_CUDA;
   return arbgpu::int_mat_mul_run(&local, T, t_limbs, X, x_limbs, Y, y_limbs, M, K, N, scratch,
                                  ARBGPU_NOALLOC_SCRATCH_BYTES, s);

@@ -555,7 +555,8 @@ bool make_z_load_map(CUtensorMap *tm, const void *base, int64_t Np, int64_t Mp, 
 }
 
 int digit_gemm_groups(arbgpu_ctx *ctx, int M, int N, int ND) {
-  const int tiles = ((M + TG_BM - 1) / TG_BM) * ((N + TG_BN - 1) / TG_BN);
+  int tiles = ((M + TG_BM - 1) / TG_BM) * ((N + TG_BN - 1) / TG_BN);
+  if (tiles < 1) tiles = 1;  // empty products (M or N zero) still get a valid layout
   int g = ctx->sm_count / tiles;  // one wave of CTAs (one CTA per SM)
   if (g < 1) g = 1;
   if (g > ND) g = ND;
