@@ -245,6 +245,26 @@ arbgpu_status arbgpu_mat_mul_batched_workspace_size(arbgpu_ctx *ctx,
                                                     const arbgpu_matmul_desc *descs,
                                                     int32_t count, size_t *bytes);
 
+/*
+ * The block plans (Algorithm 2's greedy extraction, Section IV-A) that the last arbgpu_mat_mul or
+ * arbgpu_mat_mul_batched call on `ctx` used, for inspection and testing (host-only, synchronous;
+ * the plans are known on the host once that call has returned).  One record per real product
+ * that ran the block algorithm, in the order they ran (a complex product by four real products
+ * gives Ar Br, Ai Bi, Ar Bi, Ai Br; batched items in item order):
+ *   kind   0: blocks over the inner index in its own order; 1: over the inner ordering (the
+ *          block positions index the order listed after the triples); 2: the one block of a
+ *          complex product by eq. 2 (ARBGPU_MM_COMPLEX_3M) shared by both parts
+ *   h      the height bound, floor(1.25 min(p, max(p_A, p_B))) + 192
+ *   K      the inner dimension
+ *   nb     the number of blocks, then nb triples (start, stop, basecase): [start, stop) covers
+ *          positions of the inner index; basecase = 1 for a block done by dot products
+ *   kind 1 only: K positions' inner indices (the order), then K inner scaling exponents g_k
+ * `words` receives the first min(n, max_words) words; *n_words is set to n.  A call that took
+ * the classical algorithm leaves no record.
+ */
+arbgpu_status arbgpu_last_plans(arbgpu_ctx *ctx, int64_t *words, int64_t max_words,
+                                int64_t *n_words);
+
 /* Workspace bytes arbgpu_mat_mul needs for these sizes (host-only, synchronous).  `a_nlimbs` and
  * `b_nlimbs` are the input arrays' limb counts. */
 arbgpu_status arbgpu_mat_mul_workspace_size(arbgpu_ctx *ctx, int64_t M, int64_t K, int64_t N,
@@ -277,8 +297,11 @@ arbgpu_status arbgpu_int_mat_mul_workspace_size(arbgpu_ctx *ctx, int32_t x_limbs
  * ARBGPU_NOALLOC_SCRATCH_BYTES inside the library, which every GPU that loads the library keeps
  * until the process exits.
  *   - Runs on the current device and on `stream`.  The first call on each device looks up the
- *     array's device address (cudaGetSymbolAddress with that device current); make that first
- *     call before any stream capture.
+ *     array's device address (cudaGetSymbolAddress with that device current) and keeps it for
+ *     the life of the process; make that first call before any stream capture, and do not use
+ *     this call after cudaDeviceReset (the kept address would then be stale).
+ *   - Empty products (M or N zero) return ARBGPU_OK and write nothing; K = 0 writes zeros; none
+ *     of these touch the scratch array.
  *   - Sizes whose scratch would exceed ARBGPU_NOALLOC_SCRATCH_BYTES are rejected synchronously
  *     with ARBGPU_ERR_LIMIT (arbgpu_int_mat_mul_workspace_size gives the scratch a size needs).
  *   - Every call shares the one array, which keeps the last call's contents: calls whose GPU work

@@ -159,6 +159,33 @@ class Context:
             raise ArbgpuError(rc, "arbgpu_trace_read")
         return [(buf[i].name.decode(), float(buf[i].ms), int(buf[i].units)) for i in range(n.value)]
 
+    def last_plans(self):
+        """The block plans of the last matrix-product call (``arbgpu_last_plans``), one dict per
+        real product: kind, h, K, blocks [(start, stop, basecase)], and for kind 1 the inner
+        order and the scaling exponents."""
+        n = C.c_int64(0)
+        rc = _lib.lib().arbgpu_last_plans(self.handle, None, 0, C.byref(n))
+        if rc != 0:
+            raise ArbgpuError(rc, "arbgpu_last_plans")
+        buf = (C.c_int64 * max(1, n.value))()
+        rc = _lib.lib().arbgpu_last_plans(self.handle, buf, n.value, C.byref(n))
+        if rc != 0:
+            raise ArbgpuError(rc, "arbgpu_last_plans")
+        w = list(buf)[:n.value]
+        out, q = [], 0
+        while q < len(w):
+            kind, h, K, nb = w[q:q + 4]
+            q += 4
+            blocks = [(w[q + 3 * b], w[q + 3 * b + 1], bool(w[q + 3 * b + 2])) for b in range(nb)]
+            q += 3 * nb
+            rec = dict(kind=kind, h=h, K=K, blocks=blocks)
+            if kind == 1:
+                rec["order"] = w[q:q + K]
+                rec["g"] = w[q + K:q + 2 * K]
+                q += 2 * K
+            out.append(rec)
+        return out
+
     def workspace(self, nbytes):
         """A cached device buffer of at least ``nbytes`` bytes."""
         if nbytes == 0:

@@ -287,6 +287,7 @@ arbgpu_status arbgpu_mat_mul(arbgpu_ctx *ctx, const arbgpu_balls *C, const arbgp
   if (cudaSetDevice(ctx->device) != cudaSuccess) return ARBGPU_ERR_CUDA;
   if (alg != ARBGPU_ALG_DOT && alg != ARBGPU_ALG_BLOCK && alg != ARBGPU_ALG_AUTO)
     return ARBGPU_ERR_INVALID;
+  ctx->plan_log.clear();
   const bool try_block =
       alg == ARBGPU_ALG_BLOCK || (alg == ARBGPU_ALG_AUTO && auto_uses_block(M, K, N));
   if (try_block && K > 0) {
@@ -299,6 +300,15 @@ arbgpu_status arbgpu_mat_mul(arbgpu_ctx *ctx, const arbgpu_balls *C, const arbgp
   }
   return launch_matmul_dot(ctx, C, A, B, M, K, N, lda, ldb, ldc, prec, complex_mode,
                            (cudaStream_t)stream);
+}
+
+arbgpu_status arbgpu_last_plans(arbgpu_ctx *ctx, int64_t *words, int64_t max_words,
+                                int64_t *n_words) {
+  if (!ctx || !n_words || max_words < 0 || (max_words > 0 && !words)) return ARBGPU_ERR_INVALID;
+  const int64_t n = (int64_t)ctx->plan_log.size();
+  *n_words = n;
+  for (int64_t q = 0; q < n && q < max_words; ++q) words[q] = ctx->plan_log[(size_t)q];
+  return ARBGPU_OK;
 }
 
 }  // extern "C"
@@ -373,6 +383,7 @@ arbgpu_status arbgpu_mat_mul_batched(arbgpu_ctx *ctx, const arbgpu_matmul_desc *
   if (st != ARBGPU_OK) return st;
   if (ws_bytes < need || (need && !workspace)) return ARBGPU_ERR_WORKSPACE;
   if (cudaSetDevice(ctx->device) != cudaSuccess) return ARBGPU_ERR_CUDA;
+  ctx->plan_log.clear();
   cudaStream_t s = (cudaStream_t)stream;
   uint8_t *ws = (uint8_t *)workspace;
   const size_t items_off = 0, ends_off = al256(sizeof(GroupItem) * (size_t)count);

@@ -2964,6 +2964,19 @@ static int64_t height_bound(int prec, const BlockStats &hs) {
   return (5 * (prec < pmax ? (int64_t)prec : pmax)) / 4 + 192;
 }
 
+// Append one plan record to ctx->plan_log: kind (0 contiguous, 1 over the inner order, 2 one
+// block shared by both parts of a complex product by eq. 2), h, K, the block count, then the
+// [start, stop, basecase] triples.
+static void log_plan(arbgpu_ctx *ctx, int kind, int64_t h, int64_t K,
+                     const std::vector<int32_t> &triples) {
+  std::vector<int64_t> &L = ctx->plan_log;
+  L.push_back(kind);
+  L.push_back(h);
+  L.push_back(K);
+  L.push_back((int64_t)(triples.size() / 3));
+  for (int32_t v : triples) L.push_back(v);
+}
+
 // Add (-1)^negate X Y to the accumulator by Algorithm 2: plan the blocks of this product, run the
 // products of the full blocks and accumulate them; append the basecase indices, tagged with
 // `combo`, to `basek`.
@@ -2984,6 +2997,7 @@ static arbgpu_status accumulate_product(arbgpu_ctx *ctx, const BlockWs &w, uint8
   if (hs.hA <= h && hs.hB <= h) {
     hb = {0, (int32_t)K, 0};
     hbs = {hs};
+    log_plan(ctx, 0, h, K, hb);
   } else {
     int64_t *tA = (int64_t *)(ws + w.tA), *bA = (int64_t *)(ws + w.bA);
     int64_t *tB = (int64_t *)(ws + w.tB), *bB = (int64_t *)(ws + w.bB);
@@ -3026,6 +3040,7 @@ static arbgpu_status accumulate_product(arbgpu_ctx *ctx, const BlockWs &w, uint8
             cudaSuccess ||
         cudaStreamSynchronize(s) != cudaSuccess)
       return ARBGPU_ERR_CUDA;
+    log_plan(ctx, 0, h, K, hb);
   }
   const bool planned = per.rtop != full.rtop;
   for (int b = 0; b < hnb; ++b) {
@@ -3118,6 +3133,7 @@ static arbgpu_status plan_3m(arbgpu_ctx *ctx, const BlockWs &w, uint8_t *ws, con
   p->nch = (int)(((p->hA > p->hB ? p->hA : p->hB) + 2 + 31) / 32) + 1;
   if (!residue_tc_layout(p->nch, p->NM, false, (M > N ? M : N) * w.Kp, &p->L)) return ARBGPU_OK;
   p->ok = true;
+  log_plan(ctx, 2, h, K, {0, (int32_t)K, 0});
   return ARBGPU_OK;
 }
 
@@ -3292,9 +3308,16 @@ static arbgpu_status accumulate_product_ordered(arbgpu_ctx *ctx, const BlockWs &
   const BallsView Xo{oX.limbs, oX.stride, oX.nlimbs, oX.exp, oX.flags, oX.rad_man, oX.rad_exp};
   const BallsView Yo{oY.limbs, oY.stride, oY.nlimbs, oY.exp, oY.flags, oY.rad_man, oY.rad_exp};
   // (`ord` and `g` stay alive until this returns: accumulate_product synchronises the stream)
+  const size_t rec = ctx->plan_log.size();
   const arbgpu_status st = accumulate_product(ctx, w, ws, Xo, Yo, M, K, N, K, N, prec, full, hs,
                                               negate, combo, av, s, basek, &ord);
   if (cudaStreamSynchronize(s) != cudaSuccess) return ARBGPU_ERR_CUDA;
+  if (st == ARBGPU_OK && rec < ctx->plan_log.size()) {
+    // the record covers positions of the order: mark it and append the order and the scaling
+    ctx->plan_log[rec] = 1;
+    for (int64_t k = 0; k < K; ++k) ctx->plan_log.push_back(ord[(size_t)k]);
+    for (int64_t k = 0; k < K; ++k) ctx->plan_log.push_back(g[(size_t)k]);
+  }
   return st;
 }
 
@@ -3398,6 +3421,7 @@ arbgpu_status block_finish(arbgpu_ctx *ctx, const arbgpu_balls *C, const arbgpu_
     const int64_t h = height_bound(prec, hs);
     if (hs.hA <= h && hs.hB <= h) {
       // ---- one block: exact product, one rounding per entry
+      log_plan(ctx, 0, h, K, {0, (int32_t)K, 0});
       const Lines full = lines_of(0, 0);
       RoundArgs ra{};
       arbgpu_status st1 = run_block(ctx, w, ws, Av[0], Bv[0], M, N, lda, ldb, 0, K, hs.hA, hs.hB,

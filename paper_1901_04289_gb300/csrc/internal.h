@@ -30,6 +30,8 @@ struct arbgpu_ctx {
   void *mapped = nullptr;
   void *mapped_dev = nullptr;
   size_t mapped_bytes = 0;
+  // block plans of the last matrix-product call, one record per real product (arbgpu_last_plans)
+  std::vector<int64_t> plan_log;
 };
 
 namespace arbgpu {
