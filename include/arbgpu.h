@@ -204,7 +204,13 @@ arbgpu_status arbgpu_approx_dot(arbgpu_ctx *ctx, const arbgpu_balls *res,
  *                     remainder theorem (BF16 digits, FP32 accumulation kept below 2^24, so every
  *                     product is exact); blocks shorter than 30 indices are done by dot products.
  *                     A single block is rounded once from its exact integer; several blocks are
- *                     summed in a fixed-point window and the bits below it go to the radius.  Radii:
+ *                     summed in a fixed-point window placed under each entry's largest term
+ *                     exponent, max_k top(a_ik) + top(b_kj), and the bits below it go to the
+ *                     radius.  When the inner index in its own order needs several blocks, it is
+ *                     first permuted and scaled (Section IV-B: column k of A times 2^g_k, row k of
+ *                     B times 2^-g_k, indices sorted by their product bound), which often leaves
+ *                     one block; a real product with one such block is rounded once from it.
+ *                     The environment variable ARBGPU_INNER_ORDER=0 keeps the own order.  Radii:
  *                     |A| R_B + R_A (|B| + R_B) from exact integer products of magnitudes rounded
  *                     up to 8*S_r-bit windows.
  *   ARBGPU_ALG_AUTO   picks by size and precision.
@@ -266,7 +272,8 @@ arbgpu_status arbgpu_last_plans(arbgpu_ctx *ctx, int64_t *words, int64_t max_wor
                                 int64_t *n_words);
 
 /* Workspace bytes arbgpu_mat_mul needs for these sizes (host-only, synchronous).  `a_nlimbs` and
- * `b_nlimbs` are the input arrays' limb counts. */
+ * `b_nlimbs` are the input arrays' limb counts (the larger of the two parts when complex, 1..64):
+ * the inner ordering keeps reordered copies of the operands at these widths. */
 arbgpu_status arbgpu_mat_mul_workspace_size(arbgpu_ctx *ctx, int64_t M, int64_t K, int64_t N,
                                             int32_t prec, int32_t a_nlimbs, int32_t b_nlimbs,
                                             int complex_mode, int alg, uint32_t flags,

@@ -277,8 +277,8 @@ def mat_mul(C_out, A, B, M, K, N, prec, *, alg=ALG_AUTO, flags=0, lda=None, ldb=
     ldb = N if ldb is None else ldb
     ldc = N if ldc is None else ldc
     if workspace is None:
-        need = mat_mul_workspace_size(M, K, N, prec, As[0].nlimbs, Bs[0].nlimbs, cplx, alg, flags,
-                                      ctx)
+        need = mat_mul_workspace_size(M, K, N, prec, max(a.nlimbs for a in As),
+                                      max(b.nlimbs for b in Bs), cplx, alg, flags, ctx)
         workspace = ctx.workspace(need)
     wsp = _ptr(workspace)
     wsb = 0 if workspace is None else workspace.numel() * workspace.element_size()

@@ -249,9 +249,8 @@ arbgpu_status arbgpu_mat_mul_workspace_size(arbgpu_ctx *ctx, int64_t M, int64_t 
                                             int32_t prec, int32_t a_nlimbs, int32_t b_nlimbs,
                                             int complex_mode, int alg, uint32_t flags,
                                             size_t *bytes) {
-  (void)a_nlimbs;
-  (void)b_nlimbs;
-  if (!ctx || !bytes || M < 0 || K < 0 || N < 0 || prec < 2 || prec > 1024)
+  if (!ctx || !bytes || M < 0 || K < 0 || N < 0 || prec < 2 || prec > 1024 || a_nlimbs < 1 ||
+      b_nlimbs < 1 || a_nlimbs > 64 || b_nlimbs > 64)
     return ARBGPU_ERR_INVALID;
   if (flags & ~ARBGPU_MM_COMPLEX_3M) return ARBGPU_ERR_INVALID;
   *bytes = 0;
@@ -259,7 +258,7 @@ arbgpu_status arbgpu_mat_mul_workspace_size(arbgpu_ctx *ctx, int64_t M, int64_t 
   if (alg != ARBGPU_ALG_BLOCK && alg != ARBGPU_ALG_AUTO) return ARBGPU_ERR_INVALID;
   if (alg == ARBGPU_ALG_AUTO && !auto_uses_block(M, K, N)) return ARBGPU_OK;
   *bytes = block_workspace_size(ctx, M, K, N, prec, complex_mode != 0,
-                                (flags & ARBGPU_MM_COMPLEX_3M) != 0);
+                                (flags & ARBGPU_MM_COMPLEX_3M) != 0, a_nlimbs, b_nlimbs);
   return ARBGPU_OK;
 }
 
@@ -355,8 +354,13 @@ arbgpu_status arbgpu_mat_mul_batched_workspace_size(arbgpu_ctx *ctx,
   for (int32_t q = 0; q < count; ++q) {
     const arbgpu_matmul_desc &d = descs[q];
     if (!item_uses_block(d)) continue;
+    int nlA = d.A[0].nlimbs, nlB = d.B[0].nlimbs;
+    if (d.complex_mode) {
+      nlA = d.A[1].nlimbs > nlA ? d.A[1].nlimbs : nlA;
+      nlB = d.B[1].nlimbs > nlB ? d.B[1].nlimbs : nlB;
+    }
     const size_t b = block_workspace_size(ctx, d.M, d.K, d.N, d.prec, d.complex_mode != 0,
-                                          (d.flags & ARBGPU_MM_COMPLEX_3M) != 0);
+                                          (d.flags & ARBGPU_MM_COMPLEX_3M) != 0, nlA, nlB);
     blk = b > blk ? b : blk;
     scans += al256(block_scan_bytes(d.M, d.N, d.complex_mode != 0));
   }

@@ -13,6 +13,7 @@
 //   round  C_ij = RNE_p(T_ij 2^(-e_i - f_j)) (one rounding of the exact entry) and
 //          R_ij >= eps_round + P1 2^(...) + P2 2^(...), rounded up to a 30-bit radius.
 #include <algorithm>
+#include <functional>
 #include <cstdlib>
 #include <cstring>
 #include <mutex>
@@ -2151,74 +2152,199 @@ __global__ void entry_tb_kernel(const BallsView X, int64_t rows, int64_t cols, i
   bot[idx] = e.nz ? e.bot : INT64_MAX;
 }
 
-// Greedy extraction of Algorithm 2 (one CTA): from the current start, every line (row of A, column
-// of B) walks the inner index until its height would exceed h; the block ends at the first such
-// index over all lines (a block holds at least one index); blocks shorter than the basecase size
-// are widened to min(30, remaining) and marked for dot products.  Writes [start, stop, basecase]
-// triples and their count.
-__global__ void __launch_bounds__(1024)
-    plan_kernel(const int64_t *tA, const int64_t *bA, const int64_t *tB, const int64_t *bB, int64_t M,
-                int64_t K, int64_t N, int64_t h, int32_t *blocks, int32_t *nblocks, int maxb) {
-  __shared__ int s_end, s_start, s_nb;
-  if (threadIdx.x == 0) {
-    s_start = 0;
-    s_nb = 0;
-  }
-  __syncthreads();
-  const int64_t lines = M + N;
-  while (true) {
-    const int start = s_start;
-    if (start >= K) break;
-    __syncthreads();
-    if (threadIdx.x == 0) s_end = (int)K;
-    __syncthreads();
-    for (int64_t L = threadIdx.x; L < lines; L += blockDim.x) {
-      const int64_t *tp = L < M ? tA + L * K : tB + (L - M);
-      const int64_t *bp = L < M ? bA + L * K : bB + (L - M);
-      const int64_t stride = L < M ? 1 : N;
-      int64_t hi = INT64_MIN, lo = INT64_MAX;
-      bool stop = false;
-      for (int64_t k = start; !stop && k < *(volatile int *)&s_end; k += 8) {
-        int64_t tt[8], bb[8];
-#pragma unroll
-        for (int u = 0; u < 8; ++u) {
-          const bool in = k + u < K;
-          tt[u] = in ? tp[(k + u) * stride] : INT64_MIN;
-          bb[u] = in ? bp[(k + u) * stride] : INT64_MAX;
-        }
-#pragma unroll
-        for (int u = 0; u < 8; ++u) {
-          if (stop || tt[u] == INT64_MIN) continue;
-          hi = max((long long)hi, (long long)tt[u]);
-          lo = min((long long)lo, (long long)bb[u]);
-          if (hi - lo > h) {
-            atomicMin(&s_end, (int)(k + u));
-            stop = true;
-          }
-        }
+// The same per-entry exponents of a K x N operand, written transposed ([N][K]: column j of the
+// operand is row j of the output) through a 32 x 32 shared-memory tile, so that every line the
+// planner walks -- a row of A or a column of B -- is contiguous.
+__global__ void __launch_bounds__(256) entry_tb_t_kernel(const BallsView X, int64_t K, int64_t N,
+                                                         int64_t ld, int64_t *topT,
+                                                         int64_t *botT) {
+  __shared__ int64_t st[32][33], sb[32][33];
+  const int64_t tiles_n = (N + 31) / 32;
+  const int64_t k0 = ((int64_t)blockIdx.x / tiles_n) * 32, j0 = ((int64_t)blockIdx.x % tiles_n) * 32;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  for (int r = ty; r < 32; r += 8) {
+    const int64_t k = k0 + r, j = j0 + tx;
+    int64_t t = INT64_MIN, b = INT64_MAX;
+    if (k < K && j < N) {
+      const EntryScan e = scan_entry(X, k * ld + j);
+      if (e.nz) {
+        t = e.top;
+        b = e.bot;
       }
     }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      int end = s_end;
+    st[r][tx] = t;
+    sb[r][tx] = b;
+  }
+  __syncthreads();
+  for (int r = ty; r < 32; r += 8) {
+    const int64_t j = j0 + r, k = k0 + tx;
+    if (j < N && k < K) {
+      topT[j * K + k] = st[tx][r];
+      botT[j * K + k] = sb[tx][r];
+    }
+  }
+}
+
+// Bounded grid barrier of a cooperative launch (every CTA is resident): the last CTA to arrive
+// resets the count and bumps the generation; the others wait for the bump, giving up after about
+// two seconds (then *failed is set and the caller leaves).  bar[0] = count, bar[1] = generation.
+__device__ __forceinline__ bool grid_barrier(unsigned *bar, int *failed) {
+  __shared__ int s_ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    s_ok = 1;
+    volatile unsigned *gen = bar + 1;
+    const unsigned g = *gen;
+    __threadfence();
+    if (atomicAdd(bar, 1u) == gridDim.x - 1) {
+      atomicExch(bar, 0u);
+      __threadfence();
+      atomicAdd(bar + 1, 1u);
+    } else {
+      const uint64_t t0 = global_ns();
+      while (*gen == g) {
+        if (*(volatile int *)failed || global_ns() - t0 > 2000000000ull) {
+          atomicExch(failed, 1);
+          s_ok = 0;
+          break;
+        }
+        __nanosleep(64);
+      }
+    }
+    __threadfence();
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
+// Greedy extraction of Algorithm 2 as one cooperative launch: from the current start, one warp
+// per line (a row of A in tA/bA [M][K], a column of B in tBT/bBT [N][K]) scans 32 indices at a
+// time with prefix max / min across the lanes and records the first index at which the line's
+// height (max top - min bottom over its nonzero entries) would exceed h; the block ends there
+// (the minimum over the lines; a block holds at least one index).  Blocks shorter than the basecase
+// size are widened to min(30, remaining) and marked for dot products.  CTA 0 writes the
+// [start, stop, basecase] triples and their count; state[0] = start, state[1] = end of the block
+// being found, bar = the barrier words (zeroed by the host), failed = the give-up flag (zeroed).
+__global__ void __launch_bounds__(256) plan_coop_kernel(const int64_t *tA, const int64_t *bA,
+                                                        const int64_t *tBT, const int64_t *bBT,
+                                                        int64_t M, int64_t K, int64_t N, int64_t h,
+                                                        int32_t *blocks, int32_t *nblocks,
+                                                        int maxb, int *state, unsigned *bar,
+                                                        int *failed, int *status) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const int64_t lines = M + N;
+  volatile int *vstate = state;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    state[0] = 0;
+    state[1] = (int)K;
+    *nblocks = 0;
+  }
+  if (!grid_barrier(bar, failed)) goto fail;
+  for (int iter = 0;; ++iter) {
+    const int start = vstate[0];
+    if (start >= K || iter > maxb) break;
+    for (int64_t L = warp; L < lines; L += nwarps) {
+      const int64_t *tp = L < M ? tA + L * K : tBT + (L - M) * K;
+      const int64_t *bp = L < M ? bA + L * K : bBT + (L - M) * K;
+      long long hi = INT64_MIN, lo = INT64_MAX;
+      // the current end, read by lane 0 and broadcast so that the loop stays warp-uniform
+      int lim = __shfl_sync(0xffffffffu, lane == 0 ? vstate[1] : 0, 0);
+      for (int64_t k0 = start; k0 < K && k0 < lim; k0 += 32) {
+        const int64_t k = k0 + lane;
+        long long t = k < K ? tp[k] : INT64_MIN;
+        long long b = k < K ? bp[k] : INT64_MAX;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {  // inclusive prefix max of tops, min of bottoms
+          const long long ut = __shfl_up_sync(0xffffffffu, t, o);
+          const long long ub = __shfl_up_sync(0xffffffffu, b, o);
+          if (lane >= o) {
+            t = max(t, ut);
+            b = min(b, ub);
+          }
+        }
+        t = max(t, hi);
+        b = min(b, lo);
+        const bool bad = t != INT64_MIN && t - b > h;
+        const unsigned m = __ballot_sync(0xffffffffu, bad);
+        if (m) {
+          if (lane == 0) atomicMin(state + 1, (int)(k0 + __ffs(m) - 1));
+          break;
+        }
+        hi = __shfl_sync(0xffffffffu, t, 31);
+        lo = __shfl_sync(0xffffffffu, b, 31);
+        lim = __shfl_sync(0xffffffffu, lane == 0 ? vstate[1] : 0, 0);
+      }
+    }
+    if (!grid_barrier(bar, failed)) goto fail;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+      int end = state[1];
       if (end <= start) end = start + 1;
       int base = 0;
       if (end - start < BL_BASECASE) {
         end = start + (int)min((int64_t)BL_BASECASE, K - start);
         base = 1;
       }
-      const int b = s_nb;
+      const int b = *nblocks;
       if (b < maxb) {
         blocks[3 * b] = start;
         blocks[3 * b + 1] = end;
         blocks[3 * b + 2] = base;
       }
-      s_nb = b + 1;
-      s_start = end;
+      *nblocks = b + 1;
+      state[0] = end;
+      state[1] = (int)K;
     }
-    __syncthreads();
+    if (!grid_barrier(bar, failed)) goto fail;
   }
-  if (threadIdx.x == 0) *nblocks = s_nb;
+  return;
+fail:
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    *nblocks = 0;
+    set_status(status, ARBGPU_ERR_TIMEOUT);
+  }
+}
+
+// CTAs of plan_coop_kernel that fit on the device at once (a cooperative launch needs them all
+// resident), per device.
+static int plan_coop_grid(int device, int64_t lines) {
+  static std::mutex mu;
+  static std::vector<int> per_device;
+  int cap;
+  {
+    std::lock_guard<std::mutex> lock(mu);
+    if ((int)per_device.size() <= device) per_device.resize(device + 1, 0);
+    if (!per_device[device]) {
+      int per_sm = 0, sms = 0;
+      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, plan_coop_kernel, 256, 0) !=
+              cudaSuccess ||
+          cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess)
+        return 0;
+      per_device[device] = per_sm * sms;
+    }
+    cap = per_device[device];
+  }
+  const int64_t want = (lines + 7) / 8;  // eight warps (lines) per CTA
+  return (int)(want < cap ? want : cap);
+}
+
+// a[k] = max over rows r of m[r][k] (INT64_MIN when every row holds INT64_MIN there): the column
+// maxima of a row-major rows x K matrix, 32 columns per CTA, 8 row groups reduced in shared memory.
+__global__ void __launch_bounds__(256) colmax_kernel(const int64_t *m, int64_t rows, int64_t K,
+                                                     int64_t *a) {
+  __shared__ long long s[8][32];
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  const int64_t k = (int64_t)blockIdx.x * 32 + tx;
+  long long v = INT64_MIN;
+  if (k < K)
+    for (int64_t r = ty; r < rows; r += 8) v = max(v, (long long)m[r * K + k]);
+  s[ty][tx] = v;
+  __syncthreads();
+  if (ty == 0 && k < K) {
+    for (int q = 1; q < 8; ++q) v = max(v, s[q][tx]);
+    a[k] = v;
+  }
 }
 
 // Per-entry windowed accumulator over several blocks, Algorithm 1 style: nacc limbs of two's
@@ -2232,10 +2358,18 @@ struct AccView {
   int nacc;
   int bcK;                                  // bit length bound of the number of summed products
   const int64_t *ftop_r[2], *ftop_c[2];     // whole-range row / column tops of the products summed
+  // when set: per entry, max over the summed products and inner indices k of top(a_ik) + top(b_kj)
+  // (INT64_MIN when every product is zero there), the tighter exponent bound (maxplus_top_kernel)
+  const int64_t *etop = nullptr;
+  int64_t ncols = 0;  // N, the row length of etop
 };
 
 // Exponent bound of the accumulated sum at (i, j); false when every product is zero there.
 __device__ __forceinline__ bool acc_top(const AccView &v, int64_t i, int64_t j, int64_t &top) {
+  if (v.etop) {
+    top = v.etop[i * (v.ncols) + j];
+    return top != INT64_MIN;
+  }
   bool live = false;
   top = INT64_MIN;
   for (int q = 0; q < 2; ++q) {
@@ -2263,6 +2397,79 @@ struct AccArgs {
 };
 
 constexpr int ACC_MAX = 24;
+
+// The exponent bound that places the accumulator window (the per-entry counterpart of
+// Algorithm 1's e_max): etop[i][j] = max(etop[i][j], max_k top(x_ik) + top(y_kj)) over the nonzero
+// entries, so |sum_k x_ik y_kj| < K 2^etop.  A max-plus matrix product, computed in int32 relative
+// to each row's top rt_i and each column's top ct_j: d = top - rt_i (or - ct_j) <= 0, clamped
+// below at -2^30 (a clamp only raises the bound, which stays an upper bound; a zero entry takes the
+// clamp value).  64 x 64 outputs per CTA of 256 threads (4 x 4 each), the inner index in chunks
+// of 32 through shared memory.
+constexpr int MP_T = 64, MP_K = 32;
+constexpr int32_t MP_FLOOR = -(1 << 30);
+
+__device__ __forceinline__ int32_t mp_rel(const BallsView &v, int64_t idx, int64_t ref) {
+  const uint32_t fl = __ldg(v.flags + idx);
+  if ((fl & ARBGPU_FLAG_ZERO) || ref == INT64_MIN) return MP_FLOOR;
+  const int64_t d = __ldg(v.exp + idx) - ref;
+  return d < MP_FLOOR ? MP_FLOOR : (int32_t)d;
+}
+
+__global__ void __launch_bounds__(256) maxplus_top_kernel(const BallsView X, int64_t ldx,
+                                                          const BallsView Y, int64_t ldy,
+                                                          const int64_t *rt, const int64_t *ct,
+                                                          int64_t M, int64_t K, int64_t N,
+                                                          int64_t *etop, int first) {
+  __shared__ int32_t sa[MP_K][MP_T + 1];
+  __shared__ int32_t sb[MP_K][MP_T + 1];
+  const int64_t i0 = (int64_t)blockIdx.y * MP_T, j0 = (int64_t)blockIdx.x * MP_T;
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  int32_t acc[4][4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) acc[a][b] = INT32_MIN;
+  for (int64_t k0 = 0; k0 < K; k0 += MP_K) {
+    for (int t = threadIdx.x; t < MP_K * MP_T; t += 256) {
+      // A tile: row r, inner kk (consecutive threads along kk: the row's entries are contiguous)
+      const int kk = t % MP_K, r = t / MP_K;
+      const int64_t i = i0 + r, k = k0 + kk;
+      sa[kk][r] = (i < M && k < K) ? mp_rel(X, i * ldx + k, rt[i]) : MP_FLOOR;
+      // B tile: inner kk, column c (consecutive threads along c)
+      const int c = t % MP_T, kb = t / MP_T;
+      const int64_t j = j0 + c, k2 = k0 + kb;
+      sb[kb][c] = (j < N && k2 < K) ? mp_rel(Y, k2 * ldy + j, ct[j]) : MP_FLOOR;
+    }
+    __syncthreads();
+#pragma unroll 8
+    for (int kk = 0; kk < MP_K; ++kk) {
+      int32_t av[4], bv[4];
+#pragma unroll
+      for (int a = 0; a < 4; ++a) av[a] = sa[kk][ty + 16 * a];
+#pragma unroll
+      for (int b = 0; b < 4; ++b) bv[b] = sb[kk][tx + 16 * b];
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) acc[a][b] = max(acc[a][b], av[a] + bv[b]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int a = 0; a < 4; ++a) {
+    const int64_t i = i0 + ty + 16 * a;
+    if (i >= M) continue;
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      const int64_t j = j0 + tx + 16 * b;
+      if (j >= N) continue;
+      const bool live = rt[i] != INT64_MIN && ct[j] != INT64_MIN;
+      const int64_t e = live ? rt[i] + ct[j] + (int64_t)acc[a][b] : INT64_MIN;
+      int64_t *o = etop + i * N + j;
+      if (first || e > *o) *o = e;
+    }
+  }
+}
 
 // acc += T_s 2^sigma_s (bits below the window truncated toward zero, one ulp each time),
 // rad += this block's radius bound.
@@ -2525,11 +2732,12 @@ __global__ void z3m_kernel(uint16_t *z, int NM, int64_t plane) {
 // column of A or row of B has only zero midpoints come last with g_k = 0 (their radii may still
 // count).  The greedy extraction of Section IV-A then runs over that order, on copies of the
 // operands permuted and scaled so (`gather_inner_kernel`); the basecase dots read the original
-// operands at the original indices.  Off unless ARBGPU_INNER_ORDER=1.
+// operands at the original indices.  On by default for products that need several blocks;
+// ARBGPU_INNER_ORDER=0 turns it off.
 
 static bool inner_order_enabled() {
   const char *e = getenv("ARBGPU_INNER_ORDER");
-  return e && !strcmp(e, "1");
+  return !(e && !strcmp(e, "0"));
 }
 
 // Bytes of a ball array of `count` entries with `nl` limb planes (256-byte aligned parts).
@@ -2557,34 +2765,6 @@ static BallsOut ball_array_at(uint8_t *base, int64_t count, int nl) {
   return b;
 }
 
-// a[k] = largest top of column k of A (M x K entry tops, row-major), b[k] = largest top of row k
-// of B (K x N); INT64_MIN when every entry is zero.  One CTA per inner index.
-__global__ void __launch_bounds__(256) inner_tops_kernel(const int64_t *tA, const int64_t *tB,
-                                                         int64_t M, int64_t K, int64_t N,
-                                                         int64_t *a, int64_t *b) {
-  __shared__ long long s_m[2];
-  const int64_t k = blockIdx.x;
-  if (threadIdx.x < 2) s_m[threadIdx.x] = INT64_MIN;
-  __syncthreads();
-  long long ma = INT64_MIN, mb = INT64_MIN;
-  for (int64_t i = threadIdx.x; i < M; i += blockDim.x) ma = max(ma, (long long)tA[i * K + k]);
-  for (int64_t j = threadIdx.x; j < N; j += blockDim.x) mb = max(mb, (long long)tB[k * N + j]);
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    ma = max(ma, __shfl_xor_sync(0xffffffffu, ma, o));
-    mb = max(mb, __shfl_xor_sync(0xffffffffu, mb, o));
-  }
-  if ((threadIdx.x & 31) == 0) {
-    atomicMax(&s_m[0], ma);
-    atomicMax(&s_m[1], mb);
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    a[k] = s_m[0];
-    b[k] = s_m[1];
-  }
-}
-
 // Reordered, scaled copy of an operand (gather_inner_entry, inner_order.cuh), one thread per
 // entry of the copy.
 __global__ void gather_inner_kernel(const BallsView X, int64_t ld, bool is_b, int64_t rows,
@@ -2608,6 +2788,7 @@ struct BlockWs {
   size_t brtop, brbot, brrad, bctop, bcbot, bcrad, bcplus;
   // per output part: accumulator, initial balls, basecase index list
   size_t acc[2], err[2], rman[2], rexp[2], ilimbs[2], iexp[2], iflags[2], irman[2], irexp[2], bk[2];
+  size_t etop[2];  // per-entry exponent bound of the accumulated products (maxplus_top_kernel)
   // multimodular engine: residue planes, residue products, tables
   size_t resA, resB, cdig, ccar, craw;
   // complex product by eq. 2: residue planes of the parts and their sum, three residue products
@@ -2621,7 +2802,7 @@ struct BlockWs {
 };
 
 static BlockWs block_ws(arbgpu_ctx *ctx, int64_t M, int64_t K, int64_t N, int prec, bool cplx,
-                        bool m3) {
+                        bool m3, int nlA, int nlB) {
   BlockWs w{};
   const int64_t hmax = (5LL * prec) / 4 + 192;
   w.Smax = (int)((hmax + 2 + 7) / 8);
@@ -2665,7 +2846,7 @@ static BlockWs block_ws(arbgpu_ctx *ctx, int64_t M, int64_t K, int64_t N, int pr
   w.tB = take(8 * (size_t)K * N);
   w.bB = take(8 * (size_t)K * N);
   w.blocks = take(12 * (size_t)w.maxb);
-  w.nblocks = take(8);
+  w.nblocks = take(64);  // block count, planner state (2 ints), barrier words (2), give-up flag
   w.bstats = take(sizeof(BlockStats) * (size_t)w.maxb);
   w.brtop = take(8 * (size_t)w.maxb * M);
   w.brbot = take(8 * (size_t)w.maxb * M);
@@ -2685,6 +2866,7 @@ static BlockWs block_ws(arbgpu_ctx *ctx, int64_t M, int64_t K, int64_t N, int pr
     w.irman[q] = take(4 * MN);
     w.irexp[q] = take(8 * MN);
     w.bk[q] = take(4 * 2 * (size_t)K);
+    w.etop[q] = take(8 * MN);
   }
   // residue planes, then the two radius products' operand planes (batch items NM and NM + 1)
   w.resA = take((size_t)2 * (w.NMmax + 2) * M * w.Kp * 2);
@@ -2697,8 +2879,9 @@ static BlockWs block_ws(arbgpu_ctx *ctx, int64_t M, int64_t K, int64_t N, int pr
     w.ib = take(8 * (size_t)K);
     w.iord = take(4 * (size_t)K);
     w.ig = take(8 * (size_t)K);
-    w.oA = take(ball_array_bytes(M * K, BL_MAX_NL));
-    w.oB = take(ball_array_bytes(K * N, BL_MAX_NL));
+    // the reordered copies keep the operands' limb counts
+    w.oA = take(ball_array_bytes(M * K, nlA < 1 || nlA > BL_MAX_NL ? BL_MAX_NL : nlA));
+    w.oB = take(ball_array_bytes(K * N, nlB < 1 || nlB > BL_MAX_NL ? BL_MAX_NL : nlB));
     w.irange = take(4);
   }
   if (cplx && m3) {
@@ -2711,9 +2894,9 @@ static BlockWs block_ws(arbgpu_ctx *ctx, int64_t M, int64_t K, int64_t N, int pr
 }
 
 size_t block_workspace_size(arbgpu_ctx *ctx, int64_t M, int64_t K, int64_t N, int prec,
-                            bool cplx, bool m3) {
+                            bool cplx, bool m3, int nlA, int nlB) {
   if (M <= 0 || N <= 0 || K <= 0) return 0;
-  return block_ws(ctx, M, K, N, prec, cplx, m3).total;
+  return block_ws(ctx, M, K, N, prec, cplx, m3, nlA, nlB).total;
 }
 
 // Line statistics of one block (pointers into the whole-range or the per-block arrays).
@@ -2964,6 +3147,19 @@ static int64_t height_bound(int prec, const BlockStats &hs) {
   return (5 * (prec < pmax ? (int64_t)prec : pmax)) / 4 + 192;
 }
 
+// Per-entry tops and bottoms of X (M x K, rows in tA / bA) and of Y (K x N, columns in the rows of
+// tBT / bBT) for the planner and the inner ordering.
+static arbgpu_status entry_tops(arbgpu_ctx *ctx, const BallsView &Xv, const BallsView &Yv,
+                                int64_t M, int64_t K, int64_t N, int64_t ldx, int64_t ldy,
+                                int64_t *tA, int64_t *bA, int64_t *tBT, int64_t *bBT,
+                                cudaStream_t s) {
+  LaunchScope sc(ctx, s, "entry_tb", M * K + K * N);
+  entry_tb_kernel<<<(unsigned)((M * K + 255) / 256), 256, 0, s>>>(Xv, M, K, ldx, tA, bA);
+  const int64_t tiles = ((K + 31) / 32) * ((N + 31) / 32);
+  entry_tb_t_kernel<<<(unsigned)tiles, 256, 0, s>>>(Yv, K, N, ldy, tBT, bBT);
+  return cudaGetLastError() == cudaSuccess ? ARBGPU_OK : ARBGPU_ERR_CUDA;
+}
+
 // Append one plan record to ctx->plan_log: kind (0 contiguous, 1 over the inner order, 2 one
 // block shared by both parts of a complex product by eq. 2), h, K, the block count, then the
 // [start, stop, basecase] triples.
@@ -2977,6 +3173,12 @@ static void log_plan(arbgpu_ctx *ctx, int kind, int64_t h, int64_t K,
   for (int32_t v : triples) L.push_back(v);
 }
 
+// Output of a real product that may be rounded straight from one exact block.
+struct DirectRound {
+  BallsOut C;
+  int64_t ldc;
+};
+
 // Add (-1)^negate X Y to the accumulator by Algorithm 2: plan the blocks of this product, run the
 // products of the full blocks and accumulate them; append the basecase indices, tagged with
 // `combo`, to `basek`.
@@ -2986,7 +3188,10 @@ static arbgpu_status accumulate_product(arbgpu_ctx *ctx, const BlockWs &w, uint8
                                         const Lines &full, const BlockStats &hs, bool negate,
                                         int combo, const AccView &av, cudaStream_t s,
                                         std::vector<int32_t> &basek,
-                                        const std::vector<int32_t> *kmap = nullptr) {
+                                        const std::vector<int32_t> *kmap = nullptr,
+                                        const DirectRound *direct = nullptr,
+                                        bool *rounded = nullptr,
+                                        const std::function<arbgpu_status()> *prepare = nullptr) {
   const int64_t h = height_bound(prec, hs);
   std::vector<int32_t> hb;
   std::vector<BlockStats> hbs;
@@ -3000,16 +3205,25 @@ static arbgpu_status accumulate_product(arbgpu_ctx *ctx, const BlockWs &w, uint8
     log_plan(ctx, 0, h, K, hb);
   } else {
     int64_t *tA = (int64_t *)(ws + w.tA), *bA = (int64_t *)(ws + w.bA);
-    int64_t *tB = (int64_t *)(ws + w.tB), *bB = (int64_t *)(ws + w.bB);
+    int64_t *tBT = (int64_t *)(ws + w.tB), *bBT = (int64_t *)(ws + w.bB);
     int32_t *blocks = (int32_t *)(ws + w.blocks), *nblocks = (int32_t *)(ws + w.nblocks);
+    const arbgpu_status est = entry_tops(ctx, Xv, Yv, M, K, N, ldx, ldy, tA, bA, tBT, bBT, s);
+    if (est != ARBGPU_OK) return est;
     {
-      LaunchScope sc(ctx, s, "entry_tb", M * K + K * N);
-      entry_tb_kernel<<<(unsigned)((M * K + 255) / 256), 256, 0, s>>>(Xv, M, K, ldx, tA, bA);
-      entry_tb_kernel<<<(unsigned)((K * N + 255) / 256), 256, 0, s>>>(Yv, K, N, ldy, tB, bB);
-    }
-    {
+      int *state = (int *)(nblocks + 2);
+      unsigned *bar = (unsigned *)(nblocks + 4);
+      int *failed = (int *)(nblocks + 6);
+      int64_t hh = h;
+      int maxb = w.maxb;
+      int *status = ctx->status;
+      void *args[] = {&tA, &bA, &tBT, &bBT, &M, &K, &N, &hh, &blocks, &nblocks, &maxb,
+                      &state, &bar, &failed, &status};
+      const int grid = plan_coop_grid(ctx->device, M + N);
+      if (grid < 1 || cudaMemsetAsync(nblocks, 0, 32, s) != cudaSuccess) return ARBGPU_ERR_CUDA;
       LaunchScope sc(ctx, s, "plan", M + N);
-      plan_kernel<<<1, 1024, 0, s>>>(tA, bA, tB, bB, M, K, N, h, blocks, nblocks, w.maxb);
+      if (cudaLaunchCooperativeKernel((const void *)plan_coop_kernel, dim3(grid), dim3(256), args,
+                                      0, s) != cudaSuccess)
+        return ARBGPU_ERR_CUDA;
     }
     int32_t nb = 0;
     if (cudaMemcpyAsync(&nb, nblocks, 4, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
@@ -3043,6 +3257,41 @@ static arbgpu_status accumulate_product(arbgpu_ctx *ctx, const BlockWs &w, uint8
     log_plan(ctx, 0, h, K, hb);
   }
   const bool planned = per.rtop != full.rtop;
+  if (direct && planned && hnb == 1 && hb[2] == 0 && !negate) {
+    // one full block after all (over the inner order): exact product, one rounding per entry
+    const Lines lb{per.rtop, per.rbot, per.rrad, per.ctop, per.cbot, per.crad, per.cplus};
+    RoundArgs ra{};
+    const arbgpu_status st1 = run_block(ctx, w, ws, Xv, Yv, M, N, ldx, ldy, 0, K, hbs[0].hA,
+                                        hbs[0].hB, hbs[0].radA != 0, hbs[0].radB != 0, lb, s,
+                                        &ra.mid, &ra.rp1, &ra.rp2);
+    if (st1 != ARBGPU_OK) return st1;
+    ra.rtop = lb.rtop;
+    ra.rbot = lb.rbot;
+    ra.rrad = lb.rrad;
+    ra.ctop = lb.ctop;
+    ra.cbot = lb.cbot;
+    ra.crad = lb.crad;
+    ra.cplus = lb.cplus;
+    ra.C = direct->C;
+    ra.M = M;
+    ra.N = N;
+    ra.ldc = direct->ldc;
+    ra.Mp = w.Mp;
+    ra.Np = w.Np;
+    ra.prec = prec;
+    {
+      const int64_t units =
+          ra.mid.kind == 1 ? M * N * ra.mid.crt.NM * (int64_t)(2 * ra.mid.crt.NMW) : M * N;
+      LaunchScope sc(ctx, s, "block_round", units);
+      launch_block_round(ctx, ra, s);
+    }
+    *rounded = true;
+    return cudaGetLastError() == cudaSuccess ? ARBGPU_OK : ARBGPU_ERR_CUDA;
+  }
+  if (prepare) {  // the accumulator's set-up, launched before its first use
+    const arbgpu_status pst = (*prepare)();
+    if (pst != ARBGPU_OK) return pst;
+  }
   for (int b = 0; b < hnb; ++b) {
     const int64_t k0 = hb[3 * b], k1 = hb[3 * b + 1];
     if (hb[3 * b + 2]) {
@@ -3258,19 +3507,20 @@ static arbgpu_status accumulate_product_ordered(arbgpu_ctx *ctx, const BlockWs &
                                                 int64_t ldy, int prec, const Lines &full,
                                                 const BlockStats &hs, bool negate, int combo,
                                                 const AccView &av, cudaStream_t s,
-                                                std::vector<int32_t> &basek) {
+                                                std::vector<int32_t> &basek,
+                                                const DirectRound *direct, bool *rounded,
+                                                const std::function<arbgpu_status()> *prepare) {
   if (Xv.nlimbs > BL_MAX_NL || Yv.nlimbs > BL_MAX_NL) return ARBGPU_ERR_LIMIT;
   int64_t *tA = (int64_t *)(ws + w.tA), *bA = (int64_t *)(ws + w.bA);
-  int64_t *tB = (int64_t *)(ws + w.tB), *bB = (int64_t *)(ws + w.bB);
+  int64_t *tBT = (int64_t *)(ws + w.tB), *bBT = (int64_t *)(ws + w.bB);
   int64_t *da = (int64_t *)(ws + w.ia), *db = (int64_t *)(ws + w.ib);
+  const arbgpu_status est = entry_tops(ctx, Xv, Yv, M, K, N, ldx, ldy, tA, bA, tBT, bBT, s);
+  if (est != ARBGPU_OK) return est;
   {
-    LaunchScope sc(ctx, s, "entry_tb", M * K + K * N);
-    entry_tb_kernel<<<(unsigned)((M * K + 255) / 256), 256, 0, s>>>(Xv, M, K, ldx, tA, bA);
-    entry_tb_kernel<<<(unsigned)((K * N + 255) / 256), 256, 0, s>>>(Yv, K, N, ldy, tB, bB);
-  }
-  {
+    // a_k = largest top of column k of X, b_k = largest top of row k of Y
     LaunchScope sc(ctx, s, "inner_tops", M * K + K * N);
-    inner_tops_kernel<<<(unsigned)K, 256, 0, s>>>(tA, tB, M, K, N, da, db);
+    colmax_kernel<<<(unsigned)((K + 31) / 32), 256, 0, s>>>(tA, M, K, da);
+    colmax_kernel<<<(unsigned)((K + 31) / 32), 256, 0, s>>>(tBT, N, K, db);
   }
   std::vector<int64_t> a((size_t)K), b((size_t)K), g;
   std::vector<int32_t> ord;
@@ -3304,13 +3554,14 @@ static arbgpu_status accumulate_product_ordered(arbgpu_ctx *ctx, const BlockWs &
   }
   if (hrange)  // a scaled exponent would leave the fast path's range: keep the original order
     return accumulate_product(ctx, w, ws, Xv, Yv, M, K, N, ldx, ldy, prec, full, hs, negate,
-                              combo, av, s, basek);
+                              combo, av, s, basek, nullptr, nullptr, nullptr, prepare);
   const BallsView Xo{oX.limbs, oX.stride, oX.nlimbs, oX.exp, oX.flags, oX.rad_man, oX.rad_exp};
   const BallsView Yo{oY.limbs, oY.stride, oY.nlimbs, oY.exp, oY.flags, oY.rad_man, oY.rad_exp};
   // (`ord` and `g` stay alive until this returns: accumulate_product synchronises the stream)
   const size_t rec = ctx->plan_log.size();
   const arbgpu_status st = accumulate_product(ctx, w, ws, Xo, Yo, M, K, N, K, N, prec, full, hs,
-                                              negate, combo, av, s, basek, &ord);
+                                              negate, combo, av, s, basek, &ord, direct, rounded,
+                                              prepare);
   if (cudaStreamSynchronize(s) != cudaSuccess) return ARBGPU_ERR_CUDA;
   if (st == ARBGPU_OK && rec < ctx->plan_log.size()) {
     // the record covers positions of the order: mark it and append the order and the scaling
@@ -3360,6 +3611,13 @@ static ScanRegion scan_region_at(uint8_t *base, int64_t M, int64_t N, bool cplx)
   return r;
 }
 
+// The larger limb count of an operand's parts.
+static int operand_limbs(const arbgpu_balls *X, bool cplx) {
+  int nl = X[0].nlimbs;
+  if (cplx && X[1].nlimbs > nl) nl = X[1].nlimbs;
+  return nl;
+}
+
 // Whether the block path takes the product at all (otherwise: ARBGPU_ERR_LIMIT, dot products).
 static bool block_accepts(const arbgpu_balls *A, const arbgpu_balls *B, int64_t K, bool cplx) {
   for (int q = 0; q < (cplx ? 2 : 1); ++q)
@@ -3397,7 +3655,8 @@ arbgpu_status block_finish(arbgpu_ctx *ctx, const arbgpu_balls *C, const arbgpu_
                            cudaStream_t s, bool *used_block) {
   *used_block = false;
   const int parts = cplx ? 2 : 1;
-  BlockWs w = block_ws(ctx, M, K, N, prec, cplx, m3);
+  BlockWs w = block_ws(ctx, M, K, N, prec, cplx, m3, operand_limbs(A, cplx),
+                       operand_limbs(B, cplx));
   if (!workspace || ws_bytes < w.total) return ARBGPU_ERR_WORKSPACE;
   uint8_t *ws = (uint8_t *)workspace;
   const ScanRegion sr = scan_region_at((uint8_t *)region, M, N, cplx);
@@ -3498,6 +3757,32 @@ arbgpu_status block_finish(arbgpu_ctx *ctx, const arbgpu_balls *C, const arbgpu_
         cudaMemsetAsync(av[q].rexp, 0, 8 * MN, s) != cudaSuccess)
       return ARBGPU_ERR_CUDA;
   }
+  // The window of each part's accumulator sits under the exact per-entry exponent bound, computed
+  // once before the part's first accumulation (a real product rounded straight from one exact
+  // block needs none).
+  bool etop_done[2] = {false, false};
+  auto etop_of = [&](int q) -> arbgpu_status {
+    if (etop_done[q]) return ARBGPU_OK;
+    etop_done[q] = true;
+    int64_t *et = (int64_t *)(ws + w.etop[q]);
+    bool first = true;
+    for (int t = 0; t < nprods; ++t) {
+      const Prod &pr = prods[t];
+      if (pr.part != q) continue;
+      LaunchScope sc(ctx, s, "maxplus_top", M * K * N);
+      const dim3 grid((unsigned)((N + MP_T - 1) / MP_T), (unsigned)((M + MP_T - 1) / MP_T));
+      maxplus_top_kernel<<<grid, 256, 0, s>>>(Av[pr.xa], lda, Bv[pr.yb], ldb,
+                                               rowsL[pr.xa].rtop, colsL[pr.yb].ctop, M, K, N, et,
+                                               first ? 1 : 0);
+      first = false;
+    }
+    return cudaGetLastError() == cudaSuccess ? ARBGPU_OK : ARBGPU_ERR_CUDA;
+  };
+  if (!p3.ok)
+    for (int q = 0; q < parts; ++q) {
+      av[q].etop = (int64_t *)(ws + w.etop[q]);
+      av[q].ncols = N;
+    }
   if (p3.ok) {
     const arbgpu_status st3 = run_3m(ctx, w, ws, p3, C, Av, Bv, rowsL, colsL, hst, M, K, N, lda,
                                      ldb, ldc, prec, av, s);
@@ -3505,22 +3790,28 @@ arbgpu_status block_finish(arbgpu_ctx *ctx, const arbgpu_balls *C, const arbgpu_
     *used_block = true;
     return ARBGPU_OK;
   }
+  bool rounded[2] = {false, false};
+  const DirectRound direct{out_of(C[0]), ldc};
   for (int t = 0; t < (p3.ok ? 0 : nprods); ++t) {
     const Prod &pr = prods[t];
     const BlockStats hs = merge_stats(hst[pr.xa], hst[2 + pr.yb]);
     const int64_t hb = height_bound(prec, hs);
-    // several blocks: over the inner order when it is enabled (its workspace exists)
+    const std::function<arbgpu_status()> prep = [&etop_of, q = pr.part]() { return etop_of(q); };
+    // several blocks: over the inner order when it is enabled (its workspace exists); a real
+    // product whose inner order leaves one full block is rounded from it directly
     const bool ordered = w.oA && (hs.hA > hb || hs.hB > hb);
     arbgpu_status st1 =
         ordered ? accumulate_product_ordered(ctx, w, ws, Av[pr.xa], Bv[pr.yb], M, K, N, lda, ldb,
                                              prec, lines_of(pr.xa, pr.yb), hs, pr.neg, pr.combo,
-                                             av[pr.part], s, basek[pr.part])
+                                             av[pr.part], s, basek[pr.part],
+                                             cplx ? nullptr : &direct, &rounded[pr.part], &prep)
                 : accumulate_product(ctx, w, ws, Av[pr.xa], Bv[pr.yb], M, K, N, lda, ldb, prec,
                                      lines_of(pr.xa, pr.yb), hs, pr.neg, pr.combo, av[pr.part], s,
-                                     basek[pr.part]);
+                                     basek[pr.part], nullptr, nullptr, nullptr, &prep);
     if (st1 != ARBGPU_OK) return st1;
   }
   for (int q = 0; q < parts; ++q) {
+    if (rounded[q]) continue;
     if (basek[q].empty()) {
       LaunchScope sc(ctx, s, "acc_round", M * N);
       acc_round_kernel<<<(unsigned)((M * N + 127) / 128), 128, 0, s>>>(av[q], out_of(C[q]), M, N,
@@ -3594,7 +3885,8 @@ arbgpu_status block_matmul(arbgpu_ctx *ctx, const arbgpu_balls *C, const arbgpu_
                            void *workspace, size_t ws_bytes, cudaStream_t s, bool *used_block) {
   *used_block = false;
   if (!block_accepts(A, B, K, cplx)) return ARBGPU_ERR_LIMIT;
-  BlockWs w = block_ws(ctx, M, K, N, prec, cplx, m3);
+  BlockWs w = block_ws(ctx, M, K, N, prec, cplx, m3, operand_limbs(A, cplx),
+                       operand_limbs(B, cplx));
   if (!workspace || ws_bytes < w.total) return ARBGPU_ERR_WORKSPACE;
   void *region = (uint8_t *)workspace + w.scan;
   arbgpu_status st = block_scan_launch(ctx, A, B, M, K, N, lda, ldb, cplx, region, nullptr, s);

@@ -127,6 +127,20 @@ def check_bounds(out, A, B, M, K, N, prec, entries):
     return worst
 
 
+@pytest.fixture
+def contiguous():
+    """The inner index in its own order (the inner ordering of Section IV-B off), so that the
+    blocks are the contiguous ones of ``alg2.plan``."""
+    import os
+    old = os.environ.get("ARBGPU_INNER_ORDER")
+    os.environ["ARBGPU_INNER_ORDER"] = "0"
+    yield
+    if old is None:
+        del os.environ["ARBGPU_INNER_ORDER"]
+    else:
+        os.environ["ARBGPU_INNER_ORDER"] = old
+
+
 def jump_case(seed, M, K, N, jumps, p, nl=1, rad=None):
     """Columns listed in `jumps` of A are 2^900 larger than the rest: Algorithm 2 cuts there."""
     rng = np.random.default_rng(seed)
@@ -149,7 +163,7 @@ def band_case(seed, M, K, N, lo, hi, nl=1, rad=None):
     return A, B
 
 
-def test_several_blocks_with_basecase(arb):
+def test_several_blocks_with_basecase(arb, contiguous):
     """Column 35 of A jumps by 2^900: blocks [0, 35), a one-column block widened to a 30-column
     basecase, then the rest; the block part is accumulated and the basecase done by dots."""
     M, K, N, p = 24, 100, 20, 64
@@ -161,7 +175,7 @@ def test_several_blocks_with_basecase(arb):
     check_bounds(out, A, B, M, K, N, p, [(i, j) for i in range(M) for j in range(N)])
 
 
-def test_several_blocks_without_basecase(arb):
+def test_several_blocks_without_basecase(arb, contiguous):
     """Columns 60..119 of A sit 2^900 higher: three full blocks, no basecase."""
     M, K, N, p = 40, 180, 36, 128
     A, B = band_case(5, M, K, N, 60, 120, nl=2, rad=120)
@@ -175,7 +189,7 @@ def test_several_blocks_without_basecase(arb):
                                          zip(rng.integers(0, M, 200), rng.integers(0, N, 200))])
 
 
-def test_structured_laplace_blocks(arb):
+def test_structured_laplace_blocks(arb, contiguous):
     """Exponents c_k + U[-4, 4] with c_k ~ Laplace(40) along the inner index (the structured complex
     workload's real part at a small size): many blocks of the plan, exact accumulation, bounds."""
     rng = np.random.default_rng(7)

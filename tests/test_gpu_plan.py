@@ -2,8 +2,9 @@
 element by element: every [start, stop, basecase] triple and the height bound h that the GPU used
 (read back through ``arbgpu_last_plans``) must equal ``oracle.alg2.plan`` on the same inputs, and
 the results must contain the exact product within the accuracy bound.  With the inner ordering of
-Section IV-B on, the order, the inner scaling exponents and the blocks must equal
-``oracle.alg2.plan_ordered``."""
+Section IV-B on (the default), the order, the inner scaling exponents and the blocks must equal
+``oracle.alg2.plan_ordered``; a real product left with one full block over that order is rounded
+once from its exact integer product, so its midpoints are RNE_p of the exact sum."""
 from __future__ import annotations
 
 import os
@@ -70,9 +71,20 @@ def _sample(M, N, count, seed):
     return [(int(a), int(b)) for a, b in zip(rng.integers(0, M, count), rng.integers(0, N, count))]
 
 
+@pytest.fixture
+def contiguous():
+    old = os.environ.get("ARBGPU_INNER_ORDER")
+    os.environ["ARBGPU_INNER_ORDER"] = "0"
+    yield
+    if old is None:
+        del os.environ["ARBGPU_INNER_ORDER"]
+    else:
+        os.environ["ARBGPU_INNER_ORDER"] = old
+
+
 @pytest.mark.parametrize("kind", sorted(TALL_PLANS) + ["jump", "band", "drift", "iid",
                                                        "structured", "single"])
-def test_device_plan_equals_oracle_plan(arb, kind):
+def test_device_plan_equals_oracle_plan(arb, contiguous, kind):
     A, B, M, K, N, p = _case(kind)
     h, blocks = alg2.plan(A, B, M, K, N, p)
     out, _ = run_mm(arb, A, B, M, K, N, p, arb.ALG_BLOCK)
@@ -85,7 +97,7 @@ def test_device_plan_equals_oracle_plan(arb, kind):
         check_entries(out, A, B, M, K, N, p, _sample(M, N, 60, 4), (p + 63) // 64)
 
 
-def test_device_plans_of_a_complex_product(arb):
+def test_device_plans_of_a_complex_product(arb, contiguous):
     """The four real products of a complex product (Ar Br, Ai Bi, Ar Bi, Ai Br), each planned on
     its own (the structured complex Laplace workload at N = 128)."""
     case = complex_matmul_laplace(n=128, structured=True)
@@ -154,9 +166,25 @@ def test_inner_ordered_plan_equals_oracle(arb, ordered, kind):
     assert "gather_inner" in names
     assert arb.default_context().last_plans() == [want]
     check_bounds(out, A, B, M, K, N, p, _sample(M, N, 150, 7))
+    if blocks == [(0, K, False)]:
+        # one full block over the inner order: rounded once from the exact product
+        assert "block_round" in names and "accumulate" not in names
+        check_entries(out, A, B, M, K, N, p, _sample(M, N, 80, 8), (p + 63) // 64)
     if kind == "structured":  # ordering leaves almost nothing to the basecase
         base = sum(stop - start for start, stop, b in blocks if b)
         assert base <= K // 10
+
+
+def test_inner_ordering_is_the_default(arb):
+    """Without the environment variable the inner ordering runs for products that need several
+    blocks (the structured real product: one full block over the order, exactly rounded)."""
+    assert os.environ.get("ARBGPU_INNER_ORDER") is None
+    A, B, M, K, N, p = _case("structured")
+    want = _expected_ordered(A, B, M, K, N, p)
+    out, names = run_mm(arb, A, B, M, K, N, p, arb.ALG_BLOCK, trace=True)
+    assert arb.default_context().last_plans() == [want]
+    assert want["blocks"] == [(0, K, False)]
+    check_entries(out, A, B, M, K, N, p, _sample(M, N, 80, 9), (p + 63) // 64)
 
 
 def test_inner_ordered_complex_product(arb, ordered):
