@@ -28,7 +28,8 @@ Readings (each also used by the GPU planner):
 scaling of the columns of A_s against the rows of B_s, combined with a permutation of the inner
 index); its reading is given above ``inner_order``.  ``plan_complex_shared`` /
 ``scaled_block_complex`` / ``eq2_block_products`` restate Section IV-C's complex product by eq. 2
-over blocks planned for both parts together.
+over blocks planned for both parts together; ``plan_complex_ordered`` /
+``scaled_block_complex_ordered`` combine that with the inner ordering.
 """
 from __future__ import annotations
 
@@ -276,6 +277,74 @@ def scaled_block_complex(A, B, M, K, N, start, stop):
         for q in (0, 1):
             cols[q].append([0 if tb is None else tb[2] << (tb[3] + fj) for tb in cs[q]])
     Ys = tuple([[cols[q][j][t] for j in range(N)] for t in range(stop - start)] for q in (0, 1))
+    return e, f, Xs, Ys
+
+
+# The two suggestions together: eq. 2 over blocks planned for both parts at once, over an inner
+# order and scaling shared by the parts.  Reading: a_k is the largest top over column k of both
+# parts of A, b_k over row k of both parts of B; g_k, the dead indices and the order follow
+# ``inner_order``; the greedy extraction runs on the merged tops and bottoms of ``plan_complex_shared``
+# shifted by g_k (column k of both parts of A) and -g_k (row k of both parts of B).
+
+def inner_order_complex(A, B, M, K, N):
+    """``(order, g)`` of ``inner_order`` with the tops merged over the real and imaginary parts."""
+    g = [0] * K
+    keyed, dead = [], []
+    for k in range(K):
+        ta = [t[0] for q in (0, 1) for t in (top_bottom(A[q], i * K + k) for i in range(M))
+              if t is not None]
+        tb = [t[0] for q in (0, 1) for t in (top_bottom(B[q], k * N + j) for j in range(N))
+              if t is not None]
+        if not ta or not tb:
+            dead.append(k)
+            continue
+        a, b = max(ta), max(tb)
+        g[k] = (b - a) // 2
+        keyed.append((a + b, k))
+    keyed.sort()
+    return [k for _, k in keyed] + dead, g
+
+
+def plan_complex_ordered(A, B, M, K, N, prec):
+    """``(h, order, g, blocks)``: the merged-part greedy blocks over positions of the shared order
+    under the shared inner scaling (h as in ``plan_complex_shared``)."""
+    pA = max(precision_of(A[0], M * K), precision_of(A[1], M * K))
+    pB = max(precision_of(B[0], K * N), precision_of(B[1], K * N))
+    h = height_bound(prec, pA, pB)
+    order, g = inner_order_complex(A, B, M, K, N)
+
+    def shifted(tb, d):
+        return None if tb is None else (tb[0] + d, tb[1] + d)
+    tbA = [[shifted(_merged_tb(A[0], A[1], i * K + k), g[k]) for k in order] for i in range(M)]
+    tbB = [[shifted(_merged_tb(B[0], B[1], k * N + j), -g[k]) for k in order] for j in range(N)]
+    return h, order, g, _greedy(tbA, tbB, M, N, len(order), h)
+
+
+def scaled_block_complex_ordered(A, B, M, K, N, ks, g):
+    """``(e, f, (X_re, X_im), (Y_re, Y_im))`` of the block of inner indices ``ks`` under the inner
+    scaling ``g``: ``X_q = E_s A_q,s G_s`` and ``Y_q = G_s^-1 B_q,s F_s`` with one minimal scaling
+    per row of A and per column of B shared by both parts."""
+    e = []
+    Xs = ([], [])
+    for i in range(M):
+        rows = [[top_bottom(A[q], i * K + k) for k in ks] for q in (0, 1)]
+        sh = [[None if tb is None else tb[3] + g[k] for tb, k in zip(rows[q], ks)] for q in (0, 1)]
+        lows = [v for q in (0, 1) for v in sh[q] if v is not None]
+        ei = -min(lows) if lows else 0
+        e.append(ei)
+        for q in (0, 1):
+            Xs[q].append([0 if tb is None else tb[2] << (v + ei) for tb, v in zip(rows[q], sh[q])])
+    f = []
+    cols = ([], [])
+    for j in range(N):
+        cs = [[top_bottom(B[q], k * N + j) for k in ks] for q in (0, 1)]
+        sh = [[None if tb is None else tb[3] - g[k] for tb, k in zip(cs[q], ks)] for q in (0, 1)]
+        lows = [v for q in (0, 1) for v in sh[q] if v is not None]
+        fj = -min(lows) if lows else 0
+        f.append(fj)
+        for q in (0, 1):
+            cols[q].append([0 if tb is None else tb[2] << (v + fj) for tb, v in zip(cs[q], sh[q])])
+    Ys = tuple([[cols[q][j][t] for j in range(N)] for t in range(len(ks))] for q in (0, 1))
     return e, f, Xs, Ys
 
 

@@ -610,3 +610,105 @@ def test_planted_sign_slip_in_eq2_is_caught():
     _, re, im = recombined_complex(A, B, M, K, N, p, products=wrong)
     ere, eim = exact_complex_product(A, B, M, K, N)
     assert (re, im) != (ere, eim)
+
+
+# ------------------------------------------------------------------ complex, eq. 2 over shared blocks
+# of the inner ordering (both suggestions of Sections IV-B and IV-C together)
+
+def recombined_complex_ordered(A, B, M, K, N, prec, products=alg2.eq2_block_products):
+    h, order, g, blocks = alg2.plan_complex_ordered(A, B, M, K, N, prec)
+    re = [[Fraction(0)] * N for _ in range(M)]
+    im = [[Fraction(0)] * N for _ in range(M)]
+    for start, stop, base in blocks:
+        ks = order[start:stop]
+        if base:
+            sub_re, sub_im = exact_complex_product(
+                [_take(A[q], [i * K + k for i in range(M) for k in ks]) for q in (0, 1)],
+                [_take(B[q], [k * N + j for k in ks for j in range(N)]) for q in (0, 1)],
+                M, len(ks), N)
+        else:
+            e, f, Xs, Ys = alg2.scaled_block_complex_ordered(A, B, M, K, N, ks, g)
+            R, I = products(Xs, Ys)
+            sc = [[Fraction(2) ** (-e[i] - f[j]) for j in range(N)] for i in range(M)]
+            sub_re = [[R[i][j] * sc[i][j] for j in range(N)] for i in range(M)]
+            sub_im = [[I[i][j] * sc[i][j] for j in range(N)] for i in range(M)]
+        for i in range(M):
+            for j in range(N):
+                re[i][j] += sub_re[i][j]
+                im[i][j] += sub_im[i][j]
+    return h, order, g, blocks, re, im
+
+
+@pytest.mark.parametrize("kind", ["uniform", "structured", "zero_im", "banded"])
+def test_complex_ordered_blocks_reproduce_exact_product(kind):
+    A, B, M, K, N, p = _complex_case(kind)
+    h, order, g, blocks, re, im = recombined_complex_ordered(A, B, M, K, N, p)
+    ere, eim = exact_complex_product(A, B, M, K, N)
+    assert re == ere and im == eim
+    assert sorted(order) == list(range(K))
+    assert blocks[0][0] == 0 and blocks[-1][1] == K
+    if kind == "banded":  # products 2^895 apart cannot share a block, whatever the scaling
+        assert blocks == [(0, 40, False), (40, 80, False)]
+        assert sorted(order[:40]) == list(range(40))
+
+
+def test_complex_ordering_merges_the_parts_tops():
+    """a_k and b_k are the largest tops over both parts: the order and g agree with a direct
+    computation from the merged columns and rows."""
+    A, B, M, K, N, p = _complex_case("structured")
+    order, g = alg2.inner_order_complex(A, B, M, K, N)
+    keys = []
+    for k in range(K):
+        a = max(int(A[q].exp[i * K + k]) for q in (0, 1) for i in range(M)
+                if not int(A[q].flags[i * K + k]) & X.FLAG_ZERO)
+        b = max(int(B[q].exp[k * N + j]) for q in (0, 1) for j in range(N)
+                if not int(B[q].flags[k * N + j]) & X.FLAG_ZERO)
+        assert g[k] == math.floor((b - a) / 2)
+        keys.append((a + b, k))
+    assert order == [k for _, k in sorted(keys)]
+
+
+def test_complex_ordering_leaves_full_blocks_on_a_structured_product():
+    """The structured Laplace recipe at N = 128: the contiguous shared plan is all basecase, the
+    shared plan over the merged order puts most indices in full blocks."""
+    from synth.workloads import complex_matmul_laplace
+    case = complex_matmul_laplace(n=128, structured=True)
+    _, shared = alg2.plan_complex_shared(case.A, case.B, 128, 128, 128, 128)
+    _, _, _, ordered = alg2.plan_complex_ordered(case.A, case.B, 128, 128, 128, 128)
+    assert all(b for _, _, b in shared)
+    assert sum(stop - start for start, stop, b in ordered if not b) >= 3 * 128 // 4
+
+
+def test_complex_ordered_scaling_is_minimal_and_exact():
+    A, B, M, K, N, p = _complex_case("structured")
+    h, order, g, blocks = alg2.plan_complex_ordered(A, B, M, K, N, p)
+    e, f, Xs, Ys = alg2.scaled_block_complex_ordered(A, B, M, K, N, order, g)
+    for i in range(M):
+        assert any(v & 1 for q in (0, 1) for v in Xs[q][i])
+        for q in (0, 1):
+            for t, k in enumerate(order):
+                assert Fraction(Xs[q][i][t]) == (ball_values(A[q], i * K + k)[0] *
+                                                 Fraction(2) ** (e[i] + g[k]))
+    for j in range(N):
+        assert any(Ys[q][t][j] & 1 for q in (0, 1) for t in range(K))
+        for q in (0, 1):
+            for t, k in enumerate(order):
+                assert Fraction(Ys[q][t][j]) == (ball_values(B[q], k * N + j)[0] *
+                                                 Fraction(2) ** (f[j] - g[k]))
+
+
+def test_planted_mistakes_in_the_complex_ordering_are_caught(monkeypatch):
+    # (a) the inner scaling applied to B with the wrong sign: the blocks no longer reproduce A B
+    orig = alg2.scaled_block_complex_ordered
+
+    def wrong_sign(A, B, M, K, N, ks, g):
+        return orig(A, B, M, K, N, ks, [-v for v in g])
+    A, B, M, K, N, p = _complex_case("structured")
+    h, order, g, blocks = alg2.plan_complex_ordered(A, B, M, K, N, p)
+    e, f, Xs, Ys = wrong_sign(A, B, M, K, N, order, g)
+    bad = any(Fraction(Ys[0][t][j]) != ball_values(B[0], k * N + j)[0] * Fraction(2) ** (f[j] - g[k])
+              for t, k in enumerate(order) for j in range(N))
+    assert bad
+    # (b) tops taken from the real part only: the order differs from the merged one
+    only_re = alg2.inner_order(A[0], B[0], M, K, N)
+    assert only_re != alg2.inner_order_complex(A, B, M, K, N)
