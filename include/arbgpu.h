@@ -75,9 +75,18 @@ typedef struct arbgpu_ctx arbgpu_ctx;
 
 /* Library context for one device: holds the device status word.  Create before use, on the host
  * thread that will use it; one context per host thread.  `device` is a CUDA device ordinal.
- * Allocates a few bytes of device memory once (here, not on the compute paths). */
+ * Allocates a few bytes of device memory and a small mapped pinned host buffer once (here, not on
+ * the compute paths). */
 arbgpu_status arbgpu_create(arbgpu_ctx **ctx, int device);
 arbgpu_status arbgpu_destroy(arbgpu_ctx *ctx);
+
+/* Set-up of the block algorithm's constant tables (host-only, synchronous): uploads, into device
+ * memory owned by `ctx`, every table of the multimodular engine (the moduli, weights and cofactors
+ * of Section IV-A's integer product) that a matrix product at precision <= max_prec with an inner
+ * dimension <= max_inner can use.  Without it, the first product that needs a table uploads it
+ * (one cudaMalloc per modulus count, kept until arbgpu_destroy); after it, such products allocate
+ * nothing.  Call it before capturing matrix products in a CUDA graph.  max_prec in [2, 1024]. */
+arbgpu_status arbgpu_reserve(arbgpu_ctx *ctx, int32_t max_prec, int64_t max_inner);
 
 /* Synchronises `stream`, returns the first device-side error recorded since the previous call
  * (ARBGPU_OK if none) and clears it. */

@@ -159,6 +159,12 @@ class Context:
             raise ArbgpuError(rc, "arbgpu_trace_read")
         return [(buf[i].name.decode(), float(buf[i].ms), int(buf[i].units)) for i in range(n.value)]
 
+    def reserve(self, max_prec, max_inner):
+        """Upload every table the block path can need up to these sizes (``arbgpu_reserve``)."""
+        rc = _lib.lib().arbgpu_reserve(self.handle, int(max_prec), int(max_inner))
+        if rc != 0:
+            raise ArbgpuError(rc, "arbgpu_reserve")
+
     def last_plans(self):
         """The block plans of the last matrix-product call (``arbgpu_last_plans``), one dict per
         real product: kind, h, K, blocks [(start, stop, basecase)], and for kind 1 the inner

@@ -101,11 +101,12 @@ def lib():
                                                             C.POINTER(C.c_size_t)]
         L.arbgpu_mat_mul_batched_workspace_size.restype = C.c_int
         L.arbgpu_last_plans.argtypes = [vp, vp, i64, C.POINTER(C.c_int64)]
+        L.arbgpu_reserve.argtypes = [vp, i32, i64]
         L.arbgpu_launch_count.argtypes = [vp, C.POINTER(C.c_int64)]
         L.arbgpu_trace_enable.argtypes = [vp, C.c_int]
         L.arbgpu_trace_read.argtypes = [vp, C.POINTER(CTrace), i32, C.POINTER(C.c_int32)]
         for name in ("arbgpu_launch_count", "arbgpu_trace_enable", "arbgpu_trace_read",
-                     "arbgpu_last_plans",
+                     "arbgpu_last_plans", "arbgpu_reserve",
                      "arbgpu_create", "arbgpu_destroy", "arbgpu_get_status", "arbgpu_dot",
                      "arbgpu_approx_dot", "arbgpu_dot_ex",
                      "arbgpu_mat_mul", "arbgpu_mat_mul_workspace_size", "arbgpu_int_mat_mul",
@@ -130,4 +131,4 @@ def exported_symbols():
             "arbgpu_mat_mul_workspace_size",
             "arbgpu_int_mat_mul", "arbgpu_int_mat_mul_workspace_size",
             "arbgpu_int_mat_mul_noalloc", "arbgpu_mat_mul_batched",
-            "arbgpu_mat_mul_batched_workspace_size", "arbgpu_last_plans"]
+            "arbgpu_mat_mul_batched_workspace_size", "arbgpu_last_plans", "arbgpu_reserve"]

@@ -136,16 +136,34 @@ arbgpu_status arbgpu_create(arbgpu_ctx **ctx, int device) {
   c->launches = 0;
   c->trace = false;
   cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, device);
+  // the status word and the mapped pinned buffer of the block path's statistics read-back (room
+  // for the statistics of 256 block products; a larger batch grows it once)
   if (cudaMalloc(&c->status, sizeof(int)) != cudaSuccess ||
-      cudaMemset(c->status, 0, sizeof(int)) != cudaSuccess) {
+      cudaMemset(c->status, 0, sizeof(int)) != cudaSuccess ||
+      cudaHostAlloc(&c->mapped, 4 * 256 * sizeof(BlockStats), cudaHostAllocMapped) !=
+          cudaSuccess ||
+      cudaHostGetDevicePointer(&c->mapped_dev, c->mapped, 0) != cudaSuccess) {
+    if (c->status) cudaFree(c->status);
+    if (c->mapped) cudaFreeHost(c->mapped);
     delete c;
     cudaSetDevice(prev);
     return ARBGPU_ERR_CUDA;
   }
+  c->mapped_bytes = 4 * 256 * sizeof(BlockStats);
   cudaDeviceSynchronize();
   cudaSetDevice(prev);
   *ctx = c;
   return ARBGPU_OK;
+}
+
+arbgpu_status arbgpu_reserve(arbgpu_ctx *ctx, int32_t max_prec, int64_t max_inner) {
+  if (!ctx || max_prec < 2 || max_prec > 1024 || max_inner < 1) return ARBGPU_ERR_INVALID;
+  int prev = 0;
+  cudaGetDevice(&prev);
+  if (cudaSetDevice(ctx->device) != cudaSuccess) return ARBGPU_ERR_CUDA;
+  const arbgpu_status st = block_reserve(ctx, max_prec, max_inner);
+  cudaSetDevice(prev);
+  return st;
 }
 
 arbgpu_status arbgpu_destroy(arbgpu_ctx *ctx) {

@@ -1412,6 +1412,98 @@ static arbgpu_status ensure_crt_constants(int device) {
   return ARBGPU_OK;
 }
 
+// Per-entry windowed accumulator over several blocks, Algorithm 1 style: nacc limbs of two's
+// complement at 2^base with base = top_i + top_j + bc(K) + 2 - 64 nacc (so the sum of all blocks
+// fits), a count of ulps lost below the window, and a 30-bit radius.
+struct AccView {
+  uint64_t *acc;  // [nacc][M*N]
+  uint32_t *err;  // [M*N]
+  uint32_t *rman;
+  int64_t *rexp;
+  int nacc;
+  int bcK;                                  // bit length bound of the number of summed products
+  const int64_t *ftop_r[2], *ftop_c[2];     // whole-range row / column tops of the products summed
+  // when set: per entry, max over the summed products and inner indices k of top(a_ik) + top(b_kj)
+  // (INT64_MIN when every product is zero there), the tighter exponent bound (maxplus_top_kernel)
+  const int64_t *etop = nullptr;
+  int64_t ncols = 0;  // N, the row length of etop
+};
+
+// Exponent bound of the accumulated sum at (i, j); false when every product is zero there.
+__device__ __forceinline__ bool acc_top(const AccView &v, int64_t i, int64_t j, int64_t &top) {
+  if (v.etop) {
+    top = v.etop[i * (v.ncols) + j];
+    return top != INT64_MIN;
+  }
+  bool live = false;
+  top = INT64_MIN;
+  for (int q = 0; q < 2; ++q) {
+    if (!v.ftop_r[q]) continue;
+    const int64_t a = v.ftop_r[q][i], b = v.ftop_c[q][j];
+    if (a == INT64_MIN || b == INT64_MIN) continue;
+    live = true;
+    top = a + b > top ? a + b : top;
+  }
+  return live;
+}
+
+__device__ __forceinline__ int64_t acc_base_of(const AccView &v, int64_t top) {
+  return top + v.bcK + 2 - 64LL * v.nacc;
+}
+
+// Adds (-1)^negate T 2^sigma (T: nw two's-complement limbs, destroyed) into the window of entry
+// idx: the bits of |T| below the window are dropped (truncated toward zero) and counted as one
+// lost ulp.  top: the entry's exponent bound (acc_top).
+__device__ __forceinline__ void acc_add_T(const AccView &v, int64_t idx, int64_t MN, uint64_t *T,
+                                          int nw, int64_t sigma, int64_t top, bool negate) {
+  const bool tneg = (T[nw - 1] >> 63) != 0;
+  const bool neg = tneg != negate;
+  if (tneg) {
+    u128 c = 1;
+    for (int k = 0; k < nw; ++k) {
+      c += (u128)(~T[k]);
+      T[k] = (uint64_t)c;
+      c >>= 64;
+    }
+  }
+  const int64_t sh = sigma - acc_base_of(v, top);  // T's bit 0 at bit sh of the window
+  uint64_t W[24];
+  bool lost = false;
+  for (int q = 0; q < v.nacc; ++q) {
+    // bits [64q - sh, 64q - sh + 64) of |T|
+    const int64_t lo = 64LL * q - sh;
+    const int64_t li = lo >= 0 ? (lo >> 6) : -((-lo + 63) >> 6);
+    const int bi = (int)(lo - li * 64);
+    const uint64_t w0 = (li >= 0 && li < nw) ? T[li] : 0;
+    const uint64_t w1 = (li + 1 >= 0 && li + 1 < nw) ? T[li + 1] : 0;
+    W[q] = bi ? ((w0 >> bi) | (w1 << (64 - bi))) : w0;
+  }
+  if (sh < 0) {  // bits of |T| below the window
+    const int64_t cut = -sh;
+    for (int64_t w = 0; w < (cut >> 6) && w < nw && !lost; ++w) lost = T[w] != 0;
+    if (!lost && (cut & 63) && (cut >> 6) < nw)
+      lost = (T[cut >> 6] & ((((uint64_t)1) << (cut & 63)) - 1)) != 0;
+  }
+  const uint64_t flip = neg ? ~(uint64_t)0 : 0;
+  u128 c = neg ? 1 : 0;
+  for (int q = 0; q < v.nacc; ++q) {
+    const int64_t o = (int64_t)q * MN + idx;
+    c += (u128)v.acc[o] + (W[q] ^ flip);
+    v.acc[o] = (uint64_t)c;
+    c >>= 64;
+  }
+  if (lost) v.err[idx] += 1;
+}
+
+// rad(idx) += r, rounded up.
+__device__ __forceinline__ void acc_add_radius(const AccView &v, int64_t idx, Mag r) {
+  if (!r.man) return;
+  const Mag cur{v.rman[idx], v.rexp[idx]};
+  const Mag nr = mag_add_up(cur, r);
+  v.rman[idx] = nr.man;
+  v.rexp[idx] = nr.exp;
+}
+
 struct RoundArgs {
   IntProduct mid;
   IntProduct rp1, rp2;  // radius products (ND = 0 when absent)
@@ -1424,6 +1516,10 @@ struct RoundArgs {
   // radius products of the complex product by eq. 2, summed beforehand
   const uint32_t *xrman;
   const int64_t *xrexp;
+  // accumulate mode (crt_round_tc_kernel<.., .., true>): (-1)^negate T 2^sigma goes into this
+  // window accumulator and the block's radius bound into its radius, instead of a rounding into C
+  AccView acc;
+  int negate;
 };
 
 __device__ __forceinline__ Mag with_extra_radius(const RoundArgs &a, int64_t i, int64_t j, Mag r) {
@@ -1852,7 +1948,7 @@ static size_t crt_tc_smem(int NM, int NQ, int NQP) {
          (size_t)((NQ + 15) & ~15) * 4 + sizeof(CrShared);
 }
 
-template <int NW, int NWIN>
+template <int NW, int NWIN, bool ACC>
 __global__ void __launch_bounds__(CR_THREADS, 1)
     crt_round_tc_kernel(const __grid_constant__ CUtensorMap tmz, const __grid_constant__ CrArgs a) {
   extern __shared__ __align__(1024) uint8_t smem_raw[];
@@ -2033,7 +2129,18 @@ __global__ void __launch_bounds__(CR_THREADS, 1)
       }
       tc_fence_before();
       mbar_arrive(&sh->t_empty[b]);
-      if (j < ra.N) {
+      if (ACC && j < ra.N) {
+        // accumulate mode: add (-1)^negate T 2^sigma into the entry's window, the radius bound
+        // into its radius
+        const int64_t idx = i * ra.N + j;
+        int64_t vtop;
+        if (ra.rtop[i] != INT64_MIN && ra.ctop[j] != INT64_MIN && acc_top(ra.acc, i, j, vtop))
+          acc_add_T(ra.acc, idx, ra.M * ra.N, T, NW, ra.rbot[i] + ra.cbot[j], vtop,
+                    ra.negate != 0);
+        acc_add_radius(ra.acc, idx,
+                       block_radius_regs(ra.rp1, ra.rp2, ra.rtop, ra.rrad, ra.crad, ra.cplus, i,
+                                         j, ra.Mp, ra.Np));
+      } else if (j < ra.N) {
         const bool rowz = ra.rtop[i] == INT64_MIN, colz = ra.ctop[j] == INT64_MIN;
         const int64_t sigma = (rowz ? 0 : ra.rbot[i]) + (colz ? 0 : ra.cbot[j]);
         const Mag rad = with_extra_radius(ra, i, j,
@@ -2057,7 +2164,7 @@ __global__ void __launch_bounds__(CR_THREADS, 1)
 // The reconstruction and rounding on the tensor cores, when the product is multimodular with
 // NM <= 64 and fits one of the register sizes; false otherwise (block_round then runs).
 static bool launch_crt_round_tc(arbgpu_ctx *ctx, const RoundArgs &ra, cudaStream_t s,
-                                arbgpu_status *st) {
+                                arbgpu_status *st, bool acc = false) {
   const CrtTables &c = ra.mid.crt;
   if (ra.mid.kind != 1 || c.NM > 64 || !c.wtab || c.NQP > 256 || c.NQP < 16) return false;
   const int nw = product_limbs(ra.mid);
@@ -2087,11 +2194,11 @@ static bool launch_crt_round_tc(arbgpu_ctx *ctx, const RoundArgs &ra, cudaStream
   int64_t grid = nT < ctx->sm_count ? nT : ctx->sm_count;
   const unsigned threads = 32u * (unsigned)(4 * a.ND + 5);
   const int dev = ctx->device & 255;
-#define ARB_CRT(NW_, NWIN_)                                                                   \
+#define ARB_CRT(NW_, NWIN_, ACC_)                                                             \
   do {                                                                                        \
     static bool attr_done[256] = {};                                                          \
     if (!attr_done[dev]) {                                                                    \
-      if (cudaFuncSetAttribute(crt_round_tc_kernel<NW_, NWIN_>,                               \
+      if (cudaFuncSetAttribute(crt_round_tc_kernel<NW_, NWIN_, ACC_>,                         \
                                cudaFuncAttributeMaxDynamicSharedMemorySize,                   \
                                (int)RT_SMEM_MAX) != cudaSuccess) {                            \
         *st = ARBGPU_ERR_CUDA;                                                                \
@@ -2099,20 +2206,25 @@ static bool launch_crt_round_tc(arbgpu_ctx *ctx, const RoundArgs &ra, cudaStream
       }                                                                                       \
       attr_done[dev] = true;                                                                  \
     }                                                                                         \
-    launch_pdl(crt_round_tc_kernel<NW_, NWIN_>, dim3((unsigned)grid), dim3(threads), smem, s, \
+    launch_pdl(crt_round_tc_kernel<NW_, NWIN_, ACC_>, dim3((unsigned)grid), dim3(threads),    \
+               smem, s,                                                                       \
                tm, a);                                                                        \
   } while (0)
   // a 6-limb rounding window when it holds prec + 66 bits and T is longer
   const bool win6 = ra.prec + 66 <= 64 * 6;
-  if (NW == 8) {
-    if (win6) ARB_CRT(8, 6);
-    else ARB_CRT(8, 0);
+  if (acc) {
+    if (NW == 8) ARB_CRT(8, 0, true);
+    else if (NW == 12) ARB_CRT(12, 0, true);
+    else ARB_CRT(16, 0, true);
+  } else if (NW == 8) {
+    if (win6) ARB_CRT(8, 6, false);
+    else ARB_CRT(8, 0, false);
   } else if (NW == 12) {
-    if (win6) ARB_CRT(12, 6);
-    else ARB_CRT(12, 0);
+    if (win6) ARB_CRT(12, 6, false);
+    else ARB_CRT(12, 0, false);
   } else {
-    if (win6) ARB_CRT(16, 6);
-    else ARB_CRT(16, 0);
+    if (win6) ARB_CRT(16, 6, false);
+    else ARB_CRT(16, 0, false);
   }
 #undef ARB_CRT
   *st = cudaGetLastError() == cudaSuccess ? ARBGPU_OK : ARBGPU_ERR_CUDA;
@@ -2347,45 +2459,6 @@ __global__ void __launch_bounds__(256) colmax_kernel(const int64_t *m, int64_t r
   }
 }
 
-// Per-entry windowed accumulator over several blocks, Algorithm 1 style: nacc limbs of two's
-// complement at 2^base with base = top_i + top_j + bc(K) + 2 - 64 nacc (so the sum of all blocks
-// fits), a count of ulps lost below the window, and a 30-bit radius.
-struct AccView {
-  uint64_t *acc;  // [nacc][M*N]
-  uint32_t *err;  // [M*N]
-  uint32_t *rman;
-  int64_t *rexp;
-  int nacc;
-  int bcK;                                  // bit length bound of the number of summed products
-  const int64_t *ftop_r[2], *ftop_c[2];     // whole-range row / column tops of the products summed
-  // when set: per entry, max over the summed products and inner indices k of top(a_ik) + top(b_kj)
-  // (INT64_MIN when every product is zero there), the tighter exponent bound (maxplus_top_kernel)
-  const int64_t *etop = nullptr;
-  int64_t ncols = 0;  // N, the row length of etop
-};
-
-// Exponent bound of the accumulated sum at (i, j); false when every product is zero there.
-__device__ __forceinline__ bool acc_top(const AccView &v, int64_t i, int64_t j, int64_t &top) {
-  if (v.etop) {
-    top = v.etop[i * (v.ncols) + j];
-    return top != INT64_MIN;
-  }
-  bool live = false;
-  top = INT64_MIN;
-  for (int q = 0; q < 2; ++q) {
-    if (!v.ftop_r[q]) continue;
-    const int64_t a = v.ftop_r[q][i], b = v.ftop_c[q][j];
-    if (a == INT64_MIN || b == INT64_MIN) continue;
-    live = true;
-    top = a + b > top ? a + b : top;
-  }
-  return live;
-}
-
-__device__ __forceinline__ int64_t acc_base_of(const AccView &v, int64_t top) {
-  return top + v.bcK + 2 - 64LL * v.nacc;
-}
-
 struct AccArgs {
   IntProduct mid, rp1, rp2;
   const int64_t *rtop, *rbot, *rrad, *ctop, *cbot, *crad, *cplus;  // this block's lines
@@ -2403,65 +2476,87 @@ constexpr int ACC_MAX = 24;
 // entries, so |sum_k x_ik y_kj| < K 2^etop.  A max-plus matrix product, computed in int32 relative
 // to each row's top rt_i and each column's top ct_j: d = top - rt_i (or - ct_j) <= 0, clamped
 // below at -2^30 (a clamp only raises the bound, which stays an upper bound; a zero entry takes the
-// clamp value).  64 x 64 outputs per CTA of 256 threads (4 x 4 each), the inner index in chunks
-// of 32 through shared memory.
-constexpr int MP_T = 64, MP_K = 32;
+// clamp value).  rel_tops_kernel writes the relative tops once per operand; maxplus_top_kernel
+// computes 128 x 128 outputs per CTA of 256 threads (8 x 8 each), the inner index in chunks of 32
+// through shared memory, the next chunk's loads in flight while the current one is consumed.
+constexpr int MP_T = 128, MP_K = 32, MP_PAD = 4;
 constexpr int32_t MP_FLOOR = -(1 << 30);
 
-__device__ __forceinline__ int32_t mp_rel(const BallsView &v, int64_t idx, int64_t ref) {
-  const uint32_t fl = __ldg(v.flags + idx);
-  if ((fl & ARBGPU_FLAG_ZERO) || ref == INT64_MIN) return MP_FLOOR;
-  const int64_t d = __ldg(v.exp + idx) - ref;
-  return d < MP_FLOOR ? MP_FLOOR : (int32_t)d;
+// rel[r * cols + c] = top(X[r * ld + c]) - ref, ref = rt[r] (by_row) or rt[c], clamped; zeros and
+// empty lines give the floor.
+__global__ void rel_tops_kernel(const BallsView X, int64_t ld, int64_t rows, int64_t cols,
+                                const int64_t *rt, bool by_row, int32_t *rel) {
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= rows * cols) return;
+  const int64_t r = idx / cols, c = idx - (idx / cols) * cols;
+  const int64_t e = r * ld + c;
+  const int64_t ref = by_row ? rt[r] : rt[c];
+  const uint32_t fl = __ldg(X.flags + e);
+  int32_t v = MP_FLOOR;
+  if (!(fl & ARBGPU_FLAG_ZERO) && ref != INT64_MIN) {
+    const int64_t d = __ldg(X.exp + e) - ref;
+    v = d < MP_FLOOR ? MP_FLOOR : (int32_t)d;
+  }
+  rel[idx] = v;
 }
 
-__global__ void __launch_bounds__(256) maxplus_top_kernel(const BallsView X, int64_t ldx,
-                                                          const BallsView Y, int64_t ldy,
+__global__ void __launch_bounds__(256) maxplus_top_kernel(const int32_t *dX, const int32_t *dY,
                                                           const int64_t *rt, const int64_t *ct,
                                                           int64_t M, int64_t K, int64_t N,
                                                           int64_t *etop, int first) {
-  __shared__ int32_t sa[MP_K][MP_T + 1];
-  __shared__ int32_t sb[MP_K][MP_T + 1];
+  __shared__ __align__(16) int32_t sa[MP_K][MP_T + MP_PAD];
+  __shared__ __align__(16) int32_t sb[MP_K][MP_T + MP_PAD];
   const int64_t i0 = (int64_t)blockIdx.y * MP_T, j0 = (int64_t)blockIdx.x * MP_T;
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-  int32_t acc[4][4];
+  int32_t acc[8][8];
 #pragma unroll
-  for (int a = 0; a < 4; ++a)
+  for (int a = 0; a < 8; ++a)
 #pragma unroll
-    for (int b = 0; b < 4; ++b) acc[a][b] = INT32_MIN;
-  for (int64_t k0 = 0; k0 < K; k0 += MP_K) {
-    for (int t = threadIdx.x; t < MP_K * MP_T; t += 256) {
-      // A tile: row r, inner kk (consecutive threads along kk: the row's entries are contiguous)
+    for (int b = 0; b < 8; ++b) acc[a][b] = INT32_MIN;
+  // this thread's 16 loads of each tile: A rows r = t / 32 (kk = t % 32), B rows kb = t / 128
+  int32_t ra[16], rb[16];
+  auto load = [&](int64_t k0) {
+#pragma unroll
+    for (int u = 0; u < 16; ++u) {
+      const int t = threadIdx.x + 256 * u;
       const int kk = t % MP_K, r = t / MP_K;
       const int64_t i = i0 + r, k = k0 + kk;
-      sa[kk][r] = (i < M && k < K) ? mp_rel(X, i * ldx + k, rt[i]) : MP_FLOOR;
-      // B tile: inner kk, column c (consecutive threads along c)
+      ra[u] = (i < M && k < K) ? __ldg(dX + i * K + k) : MP_FLOOR;
       const int c = t % MP_T, kb = t / MP_T;
       const int64_t j = j0 + c, k2 = k0 + kb;
-      sb[kb][c] = (j < N && k2 < K) ? mp_rel(Y, k2 * ldy + j, ct[j]) : MP_FLOOR;
+      rb[u] = (j < N && k2 < K) ? __ldg(dY + k2 * N + j) : MP_FLOOR;
+    }
+  };
+  load(0);
+  for (int64_t k0 = 0; k0 < K; k0 += MP_K) {
+#pragma unroll
+    for (int u = 0; u < 16; ++u) {
+      const int t = threadIdx.x + 256 * u;
+      sa[t % MP_K][t / MP_K] = ra[u];
+      sb[t / MP_T][t % MP_T] = rb[u];
     }
     __syncthreads();
-#pragma unroll 8
+    if (k0 + MP_K < K) load(k0 + MP_K);
+#pragma unroll 4
     for (int kk = 0; kk < MP_K; ++kk) {
-      int32_t av[4], bv[4];
+      const int4 a0 = *(const int4 *)&sa[kk][8 * ty], a1 = *(const int4 *)&sa[kk][8 * ty + 4];
+      const int4 b0 = *(const int4 *)&sb[kk][8 * tx], b1 = *(const int4 *)&sb[kk][8 * tx + 4];
+      const int32_t av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+      const int32_t bv[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
 #pragma unroll
-      for (int a = 0; a < 4; ++a) av[a] = sa[kk][ty + 16 * a];
+      for (int a = 0; a < 8; ++a)
 #pragma unroll
-      for (int b = 0; b < 4; ++b) bv[b] = sb[kk][tx + 16 * b];
-#pragma unroll
-      for (int a = 0; a < 4; ++a)
-#pragma unroll
-        for (int b = 0; b < 4; ++b) acc[a][b] = max(acc[a][b], av[a] + bv[b]);
+        for (int b = 0; b < 8; ++b) acc[a][b] = max(acc[a][b], av[a] + bv[b]);
     }
     __syncthreads();
   }
 #pragma unroll
-  for (int a = 0; a < 4; ++a) {
-    const int64_t i = i0 + ty + 16 * a;
+  for (int a = 0; a < 8; ++a) {
+    const int64_t i = i0 + 8 * ty + a;
     if (i >= M) continue;
 #pragma unroll
-    for (int b = 0; b < 4; ++b) {
-      const int64_t j = j0 + tx + 16 * b;
+    for (int b = 0; b < 8; ++b) {
+      const int64_t j = j0 + 8 * tx + b;
       if (j >= N) continue;
       const bool live = rt[i] != INT64_MIN && ct[j] != INT64_MIN;
       const int64_t e = live ? rt[i] + ct[j] + (int64_t)acc[a][b] : INT64_MIN;
@@ -2484,52 +2579,11 @@ __global__ void accumulate_kernel(const AccArgs a) {
       acc_top(v, i, j, vtop)) {
     uint64_t T[RD_MAXW];
     const int nw = assemble(a.mid, i, j, a.Mp, a.Np, T);
-    const bool tneg = (T[nw - 1] >> 63) != 0;
-    const bool neg = tneg != (a.negate != 0);
-    if (tneg) {
-      u128 c = 1;
-      for (int k = 0; k < nw; ++k) {
-        c += (u128)(~T[k]);
-        T[k] = (uint64_t)c;
-        c >>= 64;
-      }
-    }
-    const int64_t sh = a.rbot[i] + a.cbot[j] - acc_base_of(v, vtop);  // T's bit 0 at bit sh
-    uint64_t W[ACC_MAX];
-    bool lost = false;
-    for (int q = 0; q < v.nacc; ++q) {
-      // bits [64q - sh, 64q - sh + 64) of |T|
-      const int64_t lo = 64LL * q - sh;
-      const int64_t li = lo >= 0 ? (lo >> 6) : -((-lo + 63) >> 6);
-      const int bi = (int)(lo - li * 64);
-      const uint64_t w0 = (li >= 0 && li < nw) ? T[li] : 0;
-      const uint64_t w1 = (li + 1 >= 0 && li + 1 < nw) ? T[li + 1] : 0;
-      W[q] = bi ? ((w0 >> bi) | (w1 << (64 - bi))) : w0;
-    }
-    if (sh < 0) {  // bits of |T| below the window
-      const int64_t cut = -sh;
-      for (int64_t w = 0; w < (cut >> 6) && w < nw && !lost; ++w) lost = T[w] != 0;
-      if (!lost && (cut & 63) && (cut >> 6) < nw)
-        lost = (T[cut >> 6] & ((((uint64_t)1) << (cut & 63)) - 1)) != 0;
-    }
-    const uint64_t flip = neg ? ~(uint64_t)0 : 0;
-    u128 c = neg ? 1 : 0;
-    for (int q = 0; q < v.nacc; ++q) {
-      const int64_t o = (int64_t)q * MN + idx;
-      c += (u128)v.acc[o] + (W[q] ^ flip);
-      v.acc[o] = (uint64_t)c;
-      c >>= 64;
-    }
-    if (lost) v.err[idx] += 1;
+    acc_add_T(v, idx, MN, T, nw, a.rbot[i] + a.cbot[j], vtop, a.negate != 0);
   }
   if (a.skip_rad) return;
-  const Mag r = block_radius(a.rp1, a.rp2, a.rtop, a.rrad, a.crad, a.cplus, i, j, a.Mp, a.Np);
-  if (r.man) {
-    const Mag cur{v.rman[idx], v.rexp[idx]};
-    const Mag nr = mag_add_up(cur, r);
-    v.rman[idx] = nr.man;
-    v.rexp[idx] = nr.exp;
-  }
+  acc_add_radius(v, idx,
+                 block_radius(a.rp1, a.rp2, a.rtop, a.rrad, a.crad, a.cplus, i, j, a.Mp, a.Np));
 }
 
 // Final rounding of the accumulator (no basecase blocks).
@@ -2789,6 +2843,7 @@ struct BlockWs {
   // per output part: accumulator, initial balls, basecase index list
   size_t acc[2], err[2], rman[2], rexp[2], ilimbs[2], iexp[2], iflags[2], irman[2], irexp[2], bk[2];
   size_t etop[2];  // per-entry exponent bound of the accumulated products (maxplus_top_kernel)
+  size_t relA[2], relB[2];  // tops of A's and B's parts relative to their lines (int32)
   // multimodular engine: residue planes, residue products, tables
   size_t resA, resB, cdig, ccar, craw;
   // complex product by eq. 2: residue planes of the parts and their sum, three residue products
@@ -2867,6 +2922,8 @@ static BlockWs block_ws(arbgpu_ctx *ctx, int64_t M, int64_t K, int64_t N, int pr
     w.irexp[q] = take(8 * MN);
     w.bk[q] = take(4 * 2 * (size_t)K);
     w.etop[q] = take(8 * MN);
+    w.relA[q] = take(4 * (size_t)M * K);
+    w.relB[q] = take(4 * (size_t)K * N);
   }
   // residue planes, then the two radius products' operand planes (batch items NM and NM + 1)
   w.resA = take((size_t)2 * (w.NMmax + 2) * M * w.Kp * 2);
@@ -2891,6 +2948,24 @@ static BlockWs block_ws(arbgpu_ctx *ctx, int64_t M, int64_t K, int64_t N, int pr
   }
   w.total = off;
   return w;
+}
+
+// Every multimodular table a product at precision <= max_prec with an inner dimension <=
+// max_inner can use, on the device now (so that later calls allocate nothing).
+arbgpu_status block_reserve(arbgpu_ctx *ctx, int max_prec, int64_t max_inner) {
+  if (ensure_crt_constants(ctx->device) != ARBGPU_OK) return ARBGPU_ERR_CUDA;
+  const int64_t hmax = (5LL * max_prec) / 4 + 192;
+  int bk = 0;
+  for (int64_t v = max_inner; v > 0; v >>= 1) ++bk;
+  int top = crt_moduli_for_bits((int)(2 * (hmax + 1) + bk + 2));
+  if (top > CRT_MAX_MODULI) top = CRT_MAX_MODULI;
+  for (int nm = 1; nm <= top; ++nm) {
+    const CrtPlan *plan = crt_plan(nm);
+    if (!plan) continue;
+    CrtDevTables dt{};
+    if (crt_device_tables(ctx, plan, &dt) != ARBGPU_OK) return ARBGPU_ERR_CUDA;
+  }
+  return ARBGPU_OK;
 }
 
 size_t block_workspace_size(arbgpu_ctx *ctx, int64_t M, int64_t K, int64_t N, int prec,
@@ -3321,6 +3396,32 @@ static arbgpu_status accumulate_product(arbgpu_ctx *ctx, const BlockWs &w, uint8
     aa.Np = w.Np;
     aa.negate = negate ? 1 : 0;
     LaunchScope sc(ctx, s, "accumulate", M * N);
+    if (aa.mid.kind == 1) {
+      // multimodular: the reconstruction on the tensor cores, adding into the window
+      RoundArgs ra{};
+      ra.mid = aa.mid;
+      ra.rp1 = aa.rp1;
+      ra.rp2 = aa.rp2;
+      ra.rtop = aa.rtop;
+      ra.rbot = aa.rbot;
+      ra.rrad = aa.rrad;
+      ra.ctop = aa.ctop;
+      ra.cbot = aa.cbot;
+      ra.crad = aa.crad;
+      ra.cplus = aa.cplus;
+      ra.M = M;
+      ra.N = N;
+      ra.Mp = w.Mp;
+      ra.Np = w.Np;
+      ra.prec = prec;
+      ra.acc = av;
+      ra.negate = aa.negate;
+      arbgpu_status tst = ARBGPU_OK;
+      if (launch_crt_round_tc(ctx, ra, s, &tst, true)) {
+        if (tst != ARBGPU_OK) return tst;
+        continue;
+      }
+    }
     accumulate_kernel<<<(unsigned)((M * N + 127) / 128), 128, 0, s>>>(aa);
   }
   return cudaGetLastError() == cudaSuccess ? ARBGPU_OK : ARBGPU_ERR_CUDA;
@@ -3761,6 +3862,7 @@ arbgpu_status block_finish(arbgpu_ctx *ctx, const arbgpu_balls *C, const arbgpu_
   // once before the part's first accumulation (a real product rounded straight from one exact
   // block needs none).
   bool etop_done[2] = {false, false};
+  bool rel_done[4] = {false, false, false, false};  // relative tops of A0, A1, B0, B1
   auto etop_of = [&](int q) -> arbgpu_status {
     if (etop_done[q]) return ARBGPU_OK;
     etop_done[q] = true;
@@ -3769,11 +3871,24 @@ arbgpu_status block_finish(arbgpu_ctx *ctx, const arbgpu_balls *C, const arbgpu_
     for (int t = 0; t < nprods; ++t) {
       const Prod &pr = prods[t];
       if (pr.part != q) continue;
+      // the operands' tops relative to their lines (each operand part once per call)
+      int32_t *dX = (int32_t *)(ws + w.relA[pr.xa]), *dY = (int32_t *)(ws + w.relB[pr.yb]);
+      if (!rel_done[pr.xa]) {
+        LaunchScope sc(ctx, s, "rel_tops", M * K);
+        rel_tops_kernel<<<(unsigned)((M * K + 255) / 256), 256, 0, s>>>(
+            Av[pr.xa], lda, M, K, rowsL[pr.xa].rtop, true, dX);
+        rel_done[pr.xa] = true;
+      }
+      if (!rel_done[2 + pr.yb]) {
+        LaunchScope sc(ctx, s, "rel_tops", K * N);
+        rel_tops_kernel<<<(unsigned)((K * N + 255) / 256), 256, 0, s>>>(
+            Bv[pr.yb], ldb, K, N, colsL[pr.yb].ctop, false, dY);
+        rel_done[2 + pr.yb] = true;
+      }
       LaunchScope sc(ctx, s, "maxplus_top", M * K * N);
       const dim3 grid((unsigned)((N + MP_T - 1) / MP_T), (unsigned)((M + MP_T - 1) / MP_T));
-      maxplus_top_kernel<<<grid, 256, 0, s>>>(Av[pr.xa], lda, Bv[pr.yb], ldb,
-                                               rowsL[pr.xa].rtop, colsL[pr.yb].ctop, M, K, N, et,
-                                               first ? 1 : 0);
+      maxplus_top_kernel<<<grid, 256, 0, s>>>(dX, dY, rowsL[pr.xa].rtop, colsL[pr.yb].ctop, M, K,
+                                               N, et, first ? 1 : 0);
       first = false;
     }
     return cudaGetLastError() == cudaSuccess ? ARBGPU_OK : ARBGPU_ERR_CUDA;

@@ -137,6 +137,8 @@ arbgpu_status block_finish(arbgpu_ctx *ctx, const arbgpu_balls *C, const arbgpu_
 // single block; the workspace then holds the three products' planes.
 size_t block_workspace_size(arbgpu_ctx *ctx, int64_t M, int64_t K, int64_t N, int prec,
                             bool cplx, bool m3, int nlA, int nlB);
+// Uploads every multimodular table for products up to these sizes (arbgpu_reserve).
+arbgpu_status block_reserve(arbgpu_ctx *ctx, int max_prec, int64_t max_inner);
 arbgpu_status block_matmul(arbgpu_ctx *ctx, const arbgpu_balls *C, const arbgpu_balls *A,
                            const arbgpu_balls *B, int64_t M, int64_t K, int64_t N, int64_t lda,
                            int64_t ldb, int64_t ldc, int prec, bool cplx, bool m3,

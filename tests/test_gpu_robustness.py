@@ -109,3 +109,27 @@ def test_unknown_flag_bits_are_rejected(arb):
         arb.mat_mul(C, A[0], B[0], M, K, N, p, alg=arb.ALG_BLOCK, flags=2, workspace=ws)
     assert e.value.code == 1
     assert arb.default_context().status() == 0
+
+
+def test_reserve_uploads_tables_and_products_still_match(arb):
+    """arbgpu_reserve on a fresh context, then the same product there and on the default context:
+    bit-identical outputs.  Bad arguments are rejected synchronously."""
+    from paper_1901_04289_gb300 import _lib
+    ctx = arb.Context()
+    try:
+        ctx.reserve(256, 512)
+        with pytest.raises(_lib.ArbgpuError):
+            ctx.reserve(1, 512)
+        with pytest.raises(_lib.ArbgpuError):
+            ctx.reserve(256, 0)
+        A, B = _inputs(arb, 91, 96, 120, 80, 256, 1, -20, 20)
+        outs = []
+        for c in (ctx, arb.default_context()):
+            C = arb.Balls.empty(96 * 80, 4)
+            arb.mat_mul(C, A[0], B[0], 96, 120, 80, 256, alg=arb.ALG_BLOCK, ctx=c)
+            assert c.status() == 0
+            outs.append(to_raw(C))
+        for f in FIELDS:
+            assert np.array_equal(getattr(outs[0], f), getattr(outs[1], f)), f
+    finally:
+        ctx.close()
