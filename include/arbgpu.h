@@ -107,11 +107,13 @@ int arbgpu_version(void);
  *   processed -- dot_fused / dot_setup / dot_eval (the last class launch of a call): dots
  *   (arbgpu_dot) or terms (matrix products); digit_gemm* / crt_gemm: digit multiply-adds on the
  *   tensor cores; residues_*: 32x16-bit multiply-adds; block_round: 32-bit multiply-adds of the
- *   CRT sums (multimodular) or entries; others: entries) and clears the record list. */
+ *   CRT sums (multimodular) or entries; others: entries), the launch's start in ms after the
+ *   first recorded launch's start, and clears the record list. */
 typedef struct {
   const char *name;
   float ms;
   int64_t units;
+  float start_ms;
 } arbgpu_trace_entry;
 
 arbgpu_status arbgpu_launch_count(arbgpu_ctx *ctx, int64_t *count);

@@ -150,13 +150,17 @@ class Context:
     def trace(self, enable=True):
         _lib.lib().arbgpu_trace_enable(self.handle, 1 if enable else 0)
 
-    def trace_read(self, max_entries=4096):
-        """[(kernel name, device ms, work units)] of the launches traced since the last read."""
+    def trace_read(self, max_entries=4096, with_start=False):
+        """[(kernel name, device ms, work units)] of the launches traced since the last read
+        (with ``with_start``, a fourth field: the start in ms after the first traced launch)."""
         buf = (_lib.CTrace * max_entries)()
         n = C.c_int32(0)
         rc = _lib.lib().arbgpu_trace_read(self.handle, buf, max_entries, C.byref(n))
         if rc != 0:
             raise ArbgpuError(rc, "arbgpu_trace_read")
+        if with_start:
+            return [(buf[i].name.decode(), float(buf[i].ms), int(buf[i].units),
+                     float(buf[i].start_ms)) for i in range(n.value)]
         return [(buf[i].name.decode(), float(buf[i].ms), int(buf[i].units)) for i in range(n.value)]
 
     def reserve(self, max_prec, max_inner):

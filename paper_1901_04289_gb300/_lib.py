@@ -53,7 +53,8 @@ class CMatmulDesc(C.Structure):
 
 
 class CTrace(C.Structure):
-    _fields_ = [("name", C.c_char_p), ("ms", C.c_float), ("units", C.c_int64)]
+    _fields_ = [("name", C.c_char_p), ("ms", C.c_float), ("units", C.c_int64),
+                ("start_ms", C.c_float)]
 
 
 class ArbgpuError(RuntimeError):

@@ -88,14 +88,17 @@ arbgpu_status arbgpu_trace_read(arbgpu_ctx *ctx, arbgpu_trace_entry *out, int32_
                                 int32_t *n_entries) {
   if (!ctx || !n_entries || (max_entries > 0 && !out)) return ARBGPU_ERR_INVALID;
   int32_t n = 0;
+  const cudaEvent_t t0 = ctx->recs.empty() ? nullptr : ctx->recs.front().start;
   for (auto &r : ctx->recs) {
     if (cudaEventSynchronize(r.stop) != cudaSuccess) return ARBGPU_ERR_CUDA;
     if (n < max_entries) {
-      float ms = 0.f;
+      float ms = 0.f, at = 0.f;
       cudaEventElapsedTime(&ms, r.start, r.stop);
+      cudaEventElapsedTime(&at, t0, r.start);
       out[n].name = r.name;
       out[n].ms = ms;
       out[n].units = r.units;
+      out[n].start_ms = at;
       ++n;
     }
     ctx->event_pool.push_back(r.start);
@@ -142,14 +145,18 @@ arbgpu_status arbgpu_create(arbgpu_ctx **ctx, int device) {
       cudaMemset(c->status, 0, sizeof(int)) != cudaSuccess ||
       cudaHostAlloc(&c->mapped, 4 * 256 * sizeof(BlockStats), cudaHostAllocMapped) !=
           cudaSuccess ||
-      cudaHostGetDevicePointer(&c->mapped_dev, c->mapped, 0) != cudaSuccess) {
+      cudaHostGetDevicePointer(&c->mapped_dev, c->mapped, 0) != cudaSuccess ||
+      cudaHostAlloc(&c->pub, 256, cudaHostAllocMapped) != cudaSuccess ||
+      cudaHostGetDevicePointer(&c->pub_dev, c->pub, 0) != cudaSuccess) {
     if (c->status) cudaFree(c->status);
     if (c->mapped) cudaFreeHost(c->mapped);
+    if (c->pub) cudaFreeHost(c->pub);
     delete c;
     cudaSetDevice(prev);
     return ARBGPU_ERR_CUDA;
   }
   c->mapped_bytes = 4 * 256 * sizeof(BlockStats);
+  memset(c->pub, 0, 256);
   cudaDeviceSynchronize();
   cudaSetDevice(prev);
   *ctx = c;
@@ -175,6 +182,7 @@ arbgpu_status arbgpu_destroy(arbgpu_ctx *ctx) {
   for (auto e : ctx->event_pool) cudaEventDestroy(e);
   for (auto &t : ctx->crt_tables) cudaFree(t.second);
   if (ctx->mapped) cudaFreeHost(ctx->mapped);
+  if (ctx->pub) cudaFreeHost(ctx->pub);
   cudaFree(ctx->status);
   delete ctx;
   return ARBGPU_OK;

@@ -13,6 +13,9 @@
 //   round  C_ij = RNE_p(T_ij 2^(-e_i - f_j)) (one rounding of the exact entry) and
 //          R_ij >= eps_round + P1 2^(...) + P2 2^(...), rounded up to a 30-bit radius.
 #include <algorithm>
+#include <thread>
+#include <chrono>
+#include <atomic>
 #include <functional>
 #include <cstdlib>
 #include <cstring>
@@ -294,10 +297,44 @@ __device__ __forceinline__ LineAcc line_shfl_xor(const LineAcc &a, int o) {
 // Both whole-range scans in one launch of 1024-thread CTAs: CTAs [0, ceil(M / 4)) take four rows
 // of A (256 threads along each row), the others four columns of B (256 k-slices; a warp reads
 // eight rows of four neighbouring entries, one 32-byte sector each).  Each CTA finishes its lines.
+// Publication of the statistics to the host: the last CTA of the launch to finish copies `n`
+// BlockStats from `src` into mapped pinned host memory `dst` (as 32-bit words), then writes `seq`
+// into the word after them (system-scope fences between), so that the host can poll for `seq`
+// instead of synchronising the stream.  `done` counts the finished CTAs (zeroed beforehand).
+struct StatsPublish {
+  const BlockStats *src;
+  int n;
+  uint32_t *dst;
+  unsigned *done;
+  uint32_t seq;
+};
+
+__device__ __forceinline__ void publish_stats(const StatsPublish &pub, bool wrote) {
+  __shared__ bool s_last;
+  if (wrote) __threadfence();  // this thread's statistics updates are visible device-wide
+  __syncthreads();             // every line of this CTA is finished
+  if (threadIdx.x == 0) {
+    __threadfence();
+    s_last = atomicAdd(pub.done, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  const int words = pub.n * (int)(sizeof(BlockStats) / 4);
+  const volatile uint32_t *src = (const volatile uint32_t *)pub.src;
+  for (int q = threadIdx.x; q < words; q += blockDim.x) pub.dst[q] = src[q];
+  __threadfence_system();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    *(volatile uint32_t *)(pub.dst + words) = pub.seq;
+    __threadfence_system();
+  }
+}
+
 __global__ void __launch_bounds__(1024) scan_full_kernel(
     const BallsView A, const BallsView B, int64_t M, int64_t K, int64_t N, int64_t lda,
     int64_t ldb, int64_t *rtop, int64_t *rbot, int64_t *rrad, BlockStats *st_rows, int64_t *ctop,
-    int64_t *cbot, int64_t *crad, int64_t *cplus, BlockStats *st_cols) {
+    int64_t *cbot, int64_t *crad, int64_t *cplus, BlockStats *st_cols, const StatsPublish pub) {
   __shared__ LineAcc s_acc[32][4];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t row_ctas = (M + 3) / 4;
@@ -321,6 +358,7 @@ __global__ void __launch_bounds__(1024) scan_full_kernel(
       if (a.flags & 1) atomicOr(&st_rows->special, 1);
       if (a.flags & 2) atomicOr(&st_rows->radA, 1);
     }
+    if (pub.dst) publish_stats(pub, tk == 0);
     return;
   }
   const int tx = threadIdx.x & 3, ty = threadIdx.x >> 2;  // column of the group, k-slice
@@ -345,6 +383,7 @@ __global__ void __launch_bounds__(1024) scan_full_kernel(
     if (a.flags & 1) atomicOr(&st_cols->special, 1);
     if (a.flags & 2) atomicOr(&st_cols->radB, 1);
   }
+  if (pub.dst) publish_stats(pub, threadIdx.x < 4);
 }
 
 // Scans of the rows of X (M x K) and the columns of Y (K x N) over the whole inner range
@@ -3684,6 +3723,9 @@ struct ScanRegion {
   BlockStats *pst;  // [4]
 };
 
+static_assert(sizeof(BlockStats) * 4 + 2 * sizeof(unsigned) <= 256,
+              "the stats and the finished-CTA counters share the scan region's first 256 bytes");
+
 size_t block_scan_bytes(int64_t M, int64_t N, bool cplx) {
   const int parts = cplx ? 2 : 1;
   auto al = [](size_t v) { return (v + 255) / 256 * 256; };
@@ -3733,17 +3775,53 @@ arbgpu_status block_scan_launch(arbgpu_ctx *ctx, const arbgpu_balls *A, const ar
                                 bool cplx, void *region, BlockStats *stats, cudaStream_t s) {
   if (!block_accepts(A, B, K, cplx)) return ARBGPU_ERR_LIMIT;
   ScanRegion sr = scan_region_at((uint8_t *)region, M, N, cplx);
+  // without a caller's stats array: the four BlockStats and the finished-CTA counters (in the
+  // region's first 256 bytes) start at zero, and the last launch publishes the statistics to the
+  // context's mapped words under a new sequence number (block_wait_stats)
+  unsigned *done = (unsigned *)(sr.pst + 4);
   if (stats)
     sr.pst = stats;  // zeroed by the caller
-  else if (cudaMemsetAsync(sr.pst, 0, sizeof(BlockStats) * 4, s) != cudaSuccess)
+  else if (cudaMemsetAsync(sr.pst, 0, 256, s) != cudaSuccess)
     return ARBGPU_ERR_CUDA;
-  for (int q = 0; q < (cplx ? 2 : 1); ++q) {
+  const int parts = cplx ? 2 : 1;
+  for (int q = 0; q < parts; ++q) {
+    StatsPublish pub{};
+    if (!stats && q == parts - 1) {
+      pub = StatsPublish{sr.pst, 4, (uint32_t *)ctx->pub_dev, done + q, ++ctx->pub_seq};
+      if (pub.seq == 0) pub.seq = ++ctx->pub_seq;  // (0 is the words' initial value)
+    }
     LaunchScope sc(ctx, s, "scans", M * K + K * N);
     scan_full_kernel<<<(unsigned)((M + 3) / 4 + (N + 3) / 4), 1024, 0, s>>>(
         view_of(A[q]), view_of(B[q]), M, K, N, lda, ldb, sr.rtop[q], sr.rbot[q], sr.rrad[q],
-        sr.pst + q, sr.ctop[q], sr.cbot[q], sr.crad[q], sr.cplus[q], sr.pst + 2 + q);
+        sr.pst + q, sr.ctop[q], sr.cbot[q], sr.crad[q], sr.cplus[q], sr.pst + 2 + q, pub);
     if (cudaGetLastError() != cudaSuccess) return ARBGPU_ERR_CUDA;
   }
+  return ARBGPU_OK;
+}
+
+// Waits for the statistics that the last block_scan_launch without a stats array publishes
+// (sequence number ctx->pub_seq) and copies the four BlockStats to `host`: a poll of the mapped
+// sequence word, which answers as soon as the scan's last CTA has written it, where a stream
+// synchronisation would also wait for the host to be woken.  Gives up after about 20 s, and
+// reports a stream that has failed, or has finished without publishing.
+arbgpu_status block_wait_stats(arbgpu_ctx *ctx, BlockStats *host, cudaStream_t s) {
+  const volatile uint32_t *words = (const volatile uint32_t *)ctx->pub;
+  const int nw = 4 * (int)(sizeof(BlockStats) / 4);
+  const auto t0 = std::chrono::steady_clock::now();
+  for (int64_t it = 0;; ++it) {
+    if (words[nw] == ctx->pub_seq) break;
+    if ((it & 1023) == 1023) {
+      const cudaError_t q = cudaStreamQuery(s);
+      if (q != cudaSuccess && q != cudaErrorNotReady) return ARBGPU_ERR_CUDA;
+      if (q == cudaSuccess && words[nw] != ctx->pub_seq) return ARBGPU_ERR_CUDA;
+      const double el =
+          std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+      if (el > 20.0) return ARBGPU_ERR_TIMEOUT;
+      if (el > 1e-3) std::this_thread::yield();
+    }
+  }
+  std::atomic_thread_fence(std::memory_order_acquire);
+  memcpy(host, (const void *)ctx->pub, sizeof(BlockStats) * 4);
   return ARBGPU_OK;
 }
 
@@ -4007,7 +4085,7 @@ arbgpu_status block_matmul(arbgpu_ctx *ctx, const arbgpu_balls *C, const arbgpu_
   arbgpu_status st = block_scan_launch(ctx, A, B, M, K, N, lda, ldb, cplx, region, nullptr, s);
   if (st != ARBGPU_OK) return st;
   BlockStats hst[4];
-  st = read_stats(ctx, scan_region_at((uint8_t *)region, M, N, cplx).pst, hst, 4, s);
+  st = block_wait_stats(ctx, hst, s);
   if (st != ARBGPU_OK) return st;
   return block_finish(ctx, C, A, B, M, K, N, lda, ldb, ldc, prec, cplx, m3, region, hst,
                       workspace, ws_bytes, s, used_block);

@@ -32,6 +32,11 @@ struct arbgpu_ctx {
   size_t mapped_bytes = 0;
   // block plans of the last matrix-product call, one record per real product (arbgpu_last_plans)
   std::vector<int64_t> plan_log;
+  // mapped pinned words that the scan kernel publishes a single product's statistics to (four
+  // BlockStats and a sequence word), and the last sequence number used
+  void *pub = nullptr;
+  void *pub_dev = nullptr;
+  uint32_t pub_seq = 0;
 };
 
 namespace arbgpu {
