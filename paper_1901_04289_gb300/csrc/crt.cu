@@ -109,7 +109,13 @@ std::unique_ptr<CrtPlan> build_plan(int NM) {
   // GEMM item tables for up to three residue products in one batch (the complex product by
   // eq. 2 runs its three real products as items t, NM + t and 2 NM + t of modulus t)
   P->ztab.assign((size_t)4 * 3 * NM, 0);
-  for (int t = 0; t < 3 * NM; ++t) P->ztab[4 * t] = P->mods[t % NM];
+  for (int t = 0; t < 3 * NM; ++t) {
+    const uint32_t m = P->mods[t % NM];
+    const float mf = (float)m, rinv = (float)(1.0 / (double)m);
+    P->ztab[4 * t] = m;
+    memcpy(&P->ztab[4 * t + 1], &mf, 4);    // m as a float (exact: m < 2^16)
+    memcpy(&P->ztab[4 * t + 2], &rinv, 4);  // 1 / m rounded to nearest
+  }
   for (int t = NM; t < 3 * NM; ++t) P->inv.push_back(P->inv[t - NM]);
   P->NCHP = CRT_MAX_CHUNKS32;
   P->pow32.resize((size_t)NM * P->NCHP);

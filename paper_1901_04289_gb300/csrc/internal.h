@@ -86,7 +86,7 @@ struct DigitGemmArgs {
   const char *name;
   int batch = 1;  // independent products sharing the plane layout (item b: planes b*SA.., b*SB..)
   // multimodular mode (SA = SB = 2, one group): item b writes P_b mod m_b as uint16 [batch][Mp][Np]
-  // instead of digits and carries; ztab [batch][4] = m, 0, 0, 0 and zinv [batch] =
+  // instead of digits and carries; ztab [batch][4] = m, float(m), float(1 / m), 0 and zinv [batch] =
   // floor((2^64 - 1) / m)
   uint16_t *zout = nullptr;
   const uint32_t *ztab = nullptr;
@@ -190,7 +190,7 @@ struct CrtPlan {
   std::vector<uint32_t> M32;      // [NW32P]: M in 32-bit limbs
   std::vector<uint32_t> y;        // [NM]: (M / m_t)^-1 mod m_t
   std::vector<float> rinv;        // [NM]: 1 / m_t rounded to float
-  std::vector<uint32_t> ztab;     // [3 NM][4]: m_(t mod NM), 0, 0, 0
+  std::vector<uint32_t> ztab;     // [3 NM][4]: m, float(m), float(1 / m), 0 (m = m_(t mod NM))
   std::vector<uint64_t> M;        // M
   int NPAD;                       // 2 NM rounded up to a multiple of 16
   // [2][NPAD][128] BF16 bits: row 2t + b of operand side o holds byte b (balanced, 256 h + l) of

@@ -3,6 +3,9 @@
 #include <mutex>
 
 #include "internal.h"
+#include <cstdlib>
+#include <cstring>
+
 #include "tc_gemm.cuh"
 
 namespace arbgpu {
@@ -433,44 +436,57 @@ __global__ void __launch_bounds__(CG_THREADS, 1)
       tc_fence_after();
       // P = D0 + 2^8 (D1a + D1b) + 2^16 D2 from the quarters A0 B0 | A0 B1 | A1 B0 | A1 B1
       const uint32_t base = lane_addr + (uint32_t)(b * CG_ACC_COLS);
-      int64_t Pc[16];
-      {
-        uint32_t v0[16], v1[16], v2[16], v3[16];
-        tmem_ld16(base, v0);
-        tmem_ld16(base + CG_BN, v1);
-        tmem_ld16(base + 2 * CG_BN, v2);
-        tmem_ld16(base + 3 * CG_BN, v3);
-        tmem_wait_ld();
-        tc_fence_before();
-        __syncwarp();
-        if (lane == 0) mbar_arrive(&sh->acce[b]);
-#pragma unroll
-        for (int c = 0; c < 16; ++c) {
-          const int64_t d1 = (int64_t)__float2int_rn(__uint_as_float(v1[c])) +
-                             __float2int_rn(__uint_as_float(v2[c]));
-          Pc[c] = (int64_t)__float2int_rn(__uint_as_float(v0[c])) + d1 * 256 +
-                  (int64_t)__float2int_rn(__uint_as_float(v3[c])) * 65536;
-        }
-      }
+      uint32_t v0[16], v1[16], v2[16], v3[16];
+      tmem_ld16(base, v0);
+      tmem_ld16(base + CG_BN, v1);
+      tmem_ld16(base + 2 * CG_BN, v2);
+      tmem_ld16(base + 3 * CG_BN, v3);
+      tmem_wait_ld();
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&sh->acce[b]);
       if (bi >= P.nz) {  // a raw item: P itself
         longlong2 *rdst =
             (longlong2 *)(P.zraw + ((int64_t)(bi - P.nz) * P.Mp + gm) * P.Np + gcol);
 #pragma unroll
-        for (int c = 0; c < 8; ++c) rdst[c] = make_longlong2(Pc[2 * c], Pc[2 * c + 1]);
+        for (int c = 0; c < 8; ++c) {
+          int64_t pc[2];
+#pragma unroll
+          for (int u = 0; u < 2; ++u) {
+            const int cc = 2 * c + u;
+            const int64_t d1 = (int64_t)__float2int_rn(__uint_as_float(v1[cc])) +
+                               __float2int_rn(__uint_as_float(v2[cc]));
+            pc[u] = (int64_t)__float2int_rn(__uint_as_float(v0[cc])) + d1 * 256 +
+                    (int64_t)__float2int_rn(__uint_as_float(v3[cc])) * 65536;
+          }
+          rdst[c] = make_longlong2(pc[0], pc[1]);
+        }
         continue;
       }
-      // |P| <= Kp (m / 2)^2 < 2^50, so P + m 2^35 is in (0, 2^52)
-      const uint32_t m = __ldg(P.ztab + 4 * bi);
-      const uint64_t i64 = __ldg(P.zinv + bi);
+      // P mod m by Horner's rule in FP32, every step exact: the quarters D0, D1a, D1b, D2 are
+      // exact integers of magnitude <= Kp 2^14 <= 2^24; bal(x) = x - m rint(x / m) has
+      // |bal(x)| <= m / 2 + 2 (the quotient from x (1 / m) can miss a half-way point by one);
+      // then u = bal(bal(D2) 256 + bal(D1a) + bal(D1b)) and z = bal(u 256 + bal(D0)) stay below
+      // 2^24 in every intermediate, and z = P mod m in balanced form.
+      const float mf = __uint_as_float(__ldg(P.ztab + 4 * bi + 1));    // m as a float
+      const float rinv = __uint_as_float(__ldg(P.ztab + 4 * bi + 2));  // 1 / m rounded
+      const int mi = (int)__ldg(P.ztab + 4 * bi);
+      auto bal = [&](float x) {
+        const float q = __fadd_rn(__fmaf_rn(x, rinv, TG_MAGIC), -TG_MAGIC);
+        return __fmaf_rn(-q, mf, x);
+      };
       uint4 *zdst = (uint4 *)(P.zout + ((int64_t)bi * P.Mp + gm) * P.Np + gcol);
 #pragma unroll
       for (int c8 = 0; c8 < 2; ++c8) {
         uint32_t zz[4];
 #pragma unroll
         for (int u = 0; u < 8; ++u) {
-          const uint64_t x = (uint64_t)(Pc[8 * c8 + u] + ((int64_t)m << 35));
-          uint64_t r = x - __umul64hi(x, i64) * m;
-          if (r >= m) r -= m;
+          const int cc = 8 * c8 + u;
+          const float d1 = __fadd_rn(bal(__uint_as_float(v1[cc])), bal(__uint_as_float(v2[cc])));
+          const float hi = bal(__fmaf_rn(bal(__uint_as_float(v3[cc])), 256.0f, d1));
+          const float z = bal(__fmaf_rn(hi, 256.0f, bal(__uint_as_float(v0[cc]))));
+          int r = (int)(__float_as_uint(__fadd_rn(z, TG_MAGIC)) - TG_MAGIC_BITS);
+          r += r < 0 ? mi : 0;
           if (u & 1)
             zz[u >> 1] |= (uint32_t)r << 16;
           else

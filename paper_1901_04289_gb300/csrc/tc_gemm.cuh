@@ -61,7 +61,7 @@ struct DigitGemmParams {
   uint16_t *zout;
   int nz;                   // items [0, nz) are reduced; items [nz, batch) write P itself to zraw
   int64_t *zraw;            // [batch - nz][Mp][Np]
-  const uint32_t *ztab;     // [batch][4]: m_b, unused
+  const uint32_t *ztab;     // [batch][4]: m_b, m_b and 1 / m_b as float bits, unused
   const uint64_t *zinv;     // [batch]: floor((2^64 - 1) / m_b)
 };
 

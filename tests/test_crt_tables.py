@@ -96,7 +96,8 @@ def test_crt_tables(harness, NM):
     for b in range(3 * NM):
         m = mods[b % NM]
         assert t["inv"][b] == ((1 << 64) - 1) // m
-        assert t["ztab"][4 * b:4 * b + 4] == [m, 0, 0, 0]
+        f32 = lambda v: int(np.array([v], dtype=np.float32).view(np.uint32)[0])  # noqa: E731
+        assert t["ztab"][4 * b:4 * b + 4] == [m, f32(m), f32(1.0 / m), 0]
     # residue weights: row 2t (+1) of side o holds the low (high) balanced byte of the balanced
     # 2^(8d) mod m_t, times y_t for the right-hand side
     w = t["wtab"]
@@ -146,3 +147,58 @@ def test_modulus_count_covers_the_bits(harness):
         if n > 5:
             prev = prod // primes[n - 1]
             assert prev <= 2 ** (bits + 3)  # and no modulus more than needed
+
+
+# ---- the residue GEMM's drain: P mod m by Horner's rule in FP32 (crt_gemm_kernel).  Emulated
+# here with exact rationals and round-to-nearest-even to 24 bits, on the extreme quarters.
+
+def _f32(x):
+    """x (a Fraction) rounded to the nearest float32 value, ties to even (no overflow here)."""
+    from fractions import Fraction
+    if x == 0:
+        return Fraction(0)
+    sign = -1 if x < 0 else 1
+    a = abs(x)
+    e = a.numerator.bit_length() - a.denominator.bit_length()
+    if Fraction(2) ** e > a:
+        e -= 1
+    scale = Fraction(2) ** (23 - e)  # 24 significant bits
+    v = a * scale
+    n, r = divmod(v.numerator, v.denominator)
+    twice = 2 * r
+    if twice > v.denominator or (twice == v.denominator and n & 1):
+        n += 1
+    return sign * Fraction(n) / scale
+
+
+def _drain_mod(D0, D1a, D1b, D2, m):
+    from fractions import Fraction
+    MAGIC = Fraction(3 * 2**22)
+    mf = _f32(Fraction(m))
+    rinv = _f32(Fraction(1, m))
+    fma = lambda a, b, c: _f32(a * b + c)  # noqa: E731
+
+    def bal(x):
+        q = _f32(fma(x, rinv, MAGIC) - MAGIC)
+        return fma(-q, mf, x)
+    d1 = _f32(bal(Fraction(D1a)) + bal(Fraction(D1b)))
+    hi = bal(fma(bal(Fraction(D2)), Fraction(256), d1))
+    z = bal(fma(hi, Fraction(256), bal(Fraction(D0))))
+    assert z.denominator == 1 and abs(z) <= m // 2 + 2
+    r = int(z)
+    return r + m if r < 0 else r
+
+
+def test_float_horner_reduction_of_the_residue_products_is_exact():
+    import random
+    rnd = random.Random(9)
+    top = 1024 * 2**14  # Kp = 1024 products of balanced bytes (one chain of the kernel)
+    mods = [65521, 65519, 32771, 40009]
+    edge = [top, -top, top - 1, -(top - 1), 0, 1, -1, 2**22, -(2**22)]
+    for m in mods:
+        cases = [(a, b, c, d) for a in edge[:3] for b in edge[:3] for c in edge[:3]
+                 for d in edge[:3]]
+        cases += [tuple(rnd.randint(-top, top) for _ in range(4)) for _ in range(300)]
+        for D0, D1a, D1b, D2 in cases:
+            P = D0 + 256 * (D1a + D1b) + 65536 * D2
+            assert _drain_mod(D0, D1a, D1b, D2, m) == P % m, (m, D0, D1a, D1b, D2)

@@ -419,6 +419,23 @@ def test_multimodular_p1024(arb):
         check_entries(out, A, B, M, K, N, p, sample, 16)
 
 
+def test_multimodular_kp_1024_one_chain(arb):
+    """K = 1000 (Kp = 1024): the residue products' longest single chain, whose quarter sums reach
+    2^24, reduced modulo m in FP32 by the GEMM's drain; midpoints exactly rounded."""
+    rng = np.random.default_rng(44)
+    M, K, N, p = 40, 1000, 36, 128
+    A = random_balls(rng, M * K, 2, 128, -10, 10, rad_bits=120, rad_zero_frac=0.5)
+    B = random_balls(rng, K * N, 2, 128, -10, 10, rad_bits=120, rad_zero_frac=0.5)
+    (out,), names = _run_engine(arb, "crt", A, B, M, K, N, p)
+    assert "crt_gemm" in names
+    (dig,), _ = _run_engine(arb, "digits", A, B, M, K, N, p)
+    for f in ("limbs", "exp", "flags", "rad_man", "rad_exp"):
+        assert np.array_equal(getattr(out, f), getattr(dig, f)), f
+    rng2 = np.random.default_rng(5)
+    check_entries(out, A, B, M, K, N, p, [(int(a), int(b)) for a, b in
+                                         zip(rng2.integers(0, M, 30), rng2.integers(0, N, 30))], 2)
+
+
 def test_multimodular_long_inner_dimension(arb):
     """K > 1024: the residue products run in the general GEMM's multimodular mode (chains of at
     most 256 products, carries between them); midpoints are still the exactly rounded values."""
