@@ -21,6 +21,7 @@ Usage: python bench.py [--gpus N --steps K --warmup W] [--impl ours|reference]
 from __future__ import annotations
 
 import argparse
+import ctypes
 import json
 import os
 import statistics
@@ -428,6 +429,41 @@ def run_workload(args):
                 done += 1
             dt = time.perf_counter() - t0
             return done * n / dt, f"{done} complex entries x {n} terms in {dt:.1f} s", dt
+    elif wl == "series":
+        # power series exponentials (Section V's dot-product recurrence), many series at once
+        from synth import random_balls
+        length, batch, prec = 200, 1024, 128
+        rng = np.random.default_rng(SEED_BASE + 6)
+        raw = random_balls(rng, length * batch, 2, 128, -3, 1, rad_bits=120, rad_zero_frac=0.5)
+        a = arb.Balls.from_raw(raw)
+        res = arb.Balls.empty(length * batch, 2)
+        n = ctypes.c_size_t(0)
+        arb._lib.lib().arbgpu_series_exp_workspace_size(ctx.handle, length, batch, prec,
+                                                        ctypes.byref(n))
+        ws = torch.empty(max(int(n.value), 1), dtype=torch.uint8, device="cuda")
+
+        def step():
+            arb.series_exp(res, a, length, batch, prec, workspace=ws, ctx=ctx)
+        macs = batch * (length * (length - 1) // 2 + 2 * length)
+        work = dot_work({3: macs})  # the working balls carry ceil(p / 64) + 1 limbs
+        name = (f"power series exp, {batch} series x {length} coefficients, p={prec}: 128-bit "
+                f"mantissas, exponents U[-3,1], radii 2^-120 relative (half zero)")
+        inbytes, outbytes = a.nbytes(), res.nbytes()
+
+        def cpu_fn(limit):
+            from fractions import Fraction
+            from oracle import series as OS
+            done = terms = 0
+            t0 = time.perf_counter()
+            while time.perf_counter() - t0 < limit and done < batch:
+                s_ = done
+                av = [X.dy_to_fraction(X.mid(raw, k * batch + s_)) for k in range(length)]
+                rv = [X.dy_to_fraction(X.rad(raw, k * batch + s_)) for k in range(length)]
+                OS.exp_series_radius(av, rv, length)
+                done += 1
+                terms += length * (length - 1) // 2 + 2 * length
+            dt = time.perf_counter() - t0
+            return terms / dt, f"{done} series x {length} coefficients in {dt:.1f} s", dt
     else:  # grouped
         cases = grouped_matmuls()
         items = []
@@ -575,7 +611,7 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--workload", default="n512",
                     choices=["n512", "n32dots", "dots", "complex2048", "complex2048_literal",
-                             "grouped"],
+                             "series", "grouped"],
                     help="n512 (default): the headline; the others are the remaining synthetic "
                          "workloads, one JSON line each")
     args = ap.parse_args()

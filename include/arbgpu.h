@@ -291,6 +291,25 @@ arbgpu_status arbgpu_mat_mul_workspace_size(arbgpu_ctx *ctx, int64_t M, int64_t 
                                             size_t *bytes);
 
 /*
+ * Power series exponential, the consumer of the dot product that Section V describes: for each of
+ * `batch` series a_1 x + a_2 x^2 + ... (a_0 is ignored), the coefficients b_0 .. b_{len-1} of its
+ * exponential by the recurrence b_0 = 1, b_k = (sum_{j=1}^k (j a_j) b_{k-j}) / k, each step one
+ * batched call of the Algorithm 1 dot kernel over all series (j a_j and the division by k are dots
+ * of length one against exact integer balls and balls containing 1/k).
+ *   a, res   ball arrays of len * batch entries: coefficient k of series s at index k batch + s
+ *            (res->nlimbs >= ceil(prec / 64)); res must not alias a
+ *   prec     working and output precision in bits, 2..1024
+ *   workspace  device memory of at least arbgpu_series_exp_workspace_size() bytes
+ * Every output ball contains the exact coefficient of the exponential of every series whose
+ * coefficients lie in the input balls.  2 (len - 1) + 1 batched dot launches on `stream`.
+ */
+arbgpu_status arbgpu_series_exp(arbgpu_ctx *ctx, const arbgpu_balls *res, const arbgpu_balls *a,
+                                int64_t len, int64_t batch, int32_t prec, void *workspace,
+                                size_t ws_bytes, void *stream);
+arbgpu_status arbgpu_series_exp_workspace_size(arbgpu_ctx *ctx, int64_t len, int64_t batch,
+                                               int32_t prec, size_t *bytes);
+
+/*
  * Exact integer matrix product T = X * Y over Z, reduced modulo 2^(64 t_limbs): the engine behind
  * the block path (it replaces the paper's FLINT fmpz_mat_mul, Section IV).  Signed integers in
  * two's complement limb planes: X[k * (M*K) + i*K + kk] is limb k (little-endian) of X[i][kk],

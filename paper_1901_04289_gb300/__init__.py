@@ -354,3 +354,22 @@ def int_mat_mul(T, t_limbs, X, x_limbs, Y, y_limbs, M, K, N, *, workspace=None, 
                                        y_limbs, M, K, N, _ptr(workspace), wsb, _stream_ptr(stream))
     if rc != 0:
         raise ArbgpuError(rc, "arbgpu_int_mat_mul")
+
+
+def series_exp(res, a, length, batch, prec, *, workspace=None, ctx=None, stream=None):
+    """Power series exponential of ``batch`` series (``arbgpu_series_exp``): coefficient k of
+    series s at index k * batch + s of ``a`` and ``res``."""
+    ctx = ctx or default_context()
+    if workspace is None:
+        n = C.c_size_t(0)
+        rc = _lib.lib().arbgpu_series_exp_workspace_size(ctx.handle, length, batch, prec,
+                                                         C.byref(n))
+        if rc != 0:
+            raise ArbgpuError(rc, "arbgpu_series_exp_workspace_size")
+        workspace = ctx.workspace(int(n.value))
+    wsb = 0 if workspace is None else workspace.numel() * workspace.element_size()
+    r, x = res.cstruct(), a.cstruct()
+    rc = _lib.lib().arbgpu_series_exp(ctx.handle, C.byref(r), C.byref(x), length, batch, prec,
+                                      _ptr(workspace), wsb, _stream_ptr(stream))
+    if rc != 0:
+        raise ArbgpuError(rc, "arbgpu_series_exp")

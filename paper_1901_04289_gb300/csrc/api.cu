@@ -8,7 +8,7 @@
 
 using namespace arbgpu;
 
-namespace {
+namespace arbgpu {
 
 bool balls_ok(const arbgpu_balls &b) {
   if (b.count < 0 || b.nlimbs < 1 || b.nlimbs > 64) return false;
@@ -38,7 +38,7 @@ bool balls_alias(const arbgpu_balls &out, const arbgpu_balls &in) {
   return false;
 }
 
-}  // namespace
+}  // namespace arbgpu
 
 namespace arbgpu {
 

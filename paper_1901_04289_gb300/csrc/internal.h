@@ -54,6 +54,10 @@ struct LaunchScope {
 
 namespace arbgpu {
 
+// Argument checks of the C ABI (api.cu): a well-formed ball array; whether two arrays share memory.
+bool balls_ok(const arbgpu_balls &b);
+bool balls_alias(const arbgpu_balls &out, const arbgpu_balls &in);
+
 // Kernel (a): batched dots (real or complex).
 arbgpu_status launch_batched_dot(arbgpu_ctx *ctx, const arbgpu_balls *res,
                                  const arbgpu_balls *initial, const uint8_t *sub,
