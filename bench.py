@@ -142,7 +142,7 @@ def roofline_of(name, k, peaks, sm_mhz, limb_n=None):
     avg_s = k["ms_total"] / k["launches"] * 1e-3
     units = k["units"] / k["launches"]
     alu_peak = SMS * IMAD_PER_CLK_PER_SM * sm_mhz * 1e6 / 1e12
-    if name == "dot_fused" and limb_n:
+    if name in ("dot_fused", "dot_tile") and limb_n:
         achieved = 4 * limb_n * limb_n * units / avg_s / 1e12
         return {"bound": "alu", "kernel": name, "achieved": achieved, "peak": alu_peak,
                 "unit": "T int32-mul/s", "frac": achieved / alu_peak, "traffic": None,
@@ -174,7 +174,7 @@ def roofline_of(name, k, peaks, sm_mhz, limb_n=None):
     return {"kernel": name, "ms_avg": avg_s * 1e3}
 
 
-DOT_KERNELS = ("dot_setup", "dot_eval", "dot_fused")
+DOT_KERNELS = ("dot_setup", "dot_eval", "dot_fused", "dot_tile")
 
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the headline workload's
 # kernels (N = 512, p = 256), from the ncu capture summarised in
@@ -200,7 +200,8 @@ def dot_roofline(kernels, work, calls, peaks, sm_mhz):
     one launch per size class, each call.  The bound is whichever of HBM bytes or integer multiplies takes longer at
     peak; `achieved` divides the work of one call by the device time of one call."""
     t_eval = (kernels.get("dot_eval", {}).get("ms_total", 0.0) +
-              kernels.get("dot_fused", {}).get("ms_total", 0.0)) * 1e-3 / calls
+              kernels.get("dot_fused", {}).get("ms_total", 0.0) +
+              kernels.get("dot_tile", {}).get("ms_total", 0.0)) * 1e-3 / calls
     t_set = kernels.get("dot_setup", {}).get("ms_total", 0.0) * 1e-3 / calls
     t_all = t_eval + t_set
     if t_all <= 0:
@@ -209,7 +210,7 @@ def dot_roofline(kernels, work, calls, peaks, sm_mhz):
     hbm_peak = peaks.get("hbm_gbs", 6800.0)
     t_hbm = work["bytes"] / (hbm_peak * 1e9)
     t_alu = work["mults"] / (alu_peak * 1e12)
-    names = [k for k in ("dot_setup", "dot_eval", "dot_fused") if k in kernels]
+    names = [k for k in ("dot_setup", "dot_eval", "dot_fused", "dot_tile") if k in kernels]
     base = {"kernel": " + ".join(names), "ms_per_call": t_all * 1e3,
             "eval_ms_per_call": t_eval * 1e3, "terms_per_call": work["terms"],
             "traffic": None}

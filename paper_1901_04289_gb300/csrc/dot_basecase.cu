@@ -1,5 +1,6 @@
 // Kernel (a) for the basecase blocks of Algorithm 2.
 #include "dot_src.cuh"
+#include "dot_tile.cuh"
 
 namespace arbgpu {
 
@@ -32,6 +33,27 @@ arbgpu_status launch_basecase_dot(arbgpu_ctx *ctx, const arbgpu_balls &C, const 
   s.len_max = nbk;
   const int cmax = dot_class_for_problem(prec, nbk + 1, maxnl);
   if (cmax < 0) return ARBGPU_ERR_INVALID;
+  {
+    TileSrc t{};
+    t.A[0] = s.A[0];
+    t.A[1] = s.A[1];
+    t.B[0] = s.B[0];
+    t.B[1] = s.B[1];
+    t.C[0] = t.C[1] = s.C;
+    t.init = s.init;
+    t.M = M;
+    t.N = N;
+    t.lda = lda;
+    t.ldb = ldb;
+    t.ldc = ldc;
+    t.nterms = nbk;
+    t.mode = 2;
+    t.bk = bk;
+    t.prec = prec;
+    t.has_init = 1;
+    arbgpu_status st = ARBGPU_OK;
+    if (launch_dot_tile(ctx, t, 1, cmax, stream, &st, M * N * nbk)) return st;
+  }
   return launch_dot_fused(ctx, s, M * N, cmax, dot_group_matrix(), stream);
 }
 

@@ -1,5 +1,6 @@
 // Kernel (a) over rows x columns: the classical matrix product.
 #include "dot_src.cuh"
+#include "dot_tile.cuh"
 
 namespace arbgpu {
 
@@ -34,6 +35,27 @@ arbgpu_status launch_matmul_dot(arbgpu_ctx *ctx, const arbgpu_balls *C, const ar
   s.len_max = complex_mode ? 2 * K : K;
   const int cmax = dot_class_for_problem(prec, s.len_max, maxnl);
   if (cmax < 0) return ARBGPU_ERR_INVALID;
+  {
+    TileSrc t{};
+    for (int q = 0; q < 2; ++q) {
+      t.A[q] = s.A[q];
+      t.B[q] = s.B[q];
+      t.C[q] = s.C[q];
+    }
+    t.init = s.A[0];
+    t.M = M;
+    t.N = N;
+    t.lda = lda;
+    t.ldb = ldb;
+    t.ldc = ldc;
+    t.nterms = s.len_max;
+    t.mode = complex_mode ? 1 : 0;
+    t.prec = prec;
+    t.has_init = 0;
+    arbgpu_status st = ARBGPU_OK;
+    const int parts = complex_mode ? 2 : 1;
+    if (launch_dot_tile(ctx, t, parts, cmax, stream, &st, parts * M * N * s.len_max)) return st;
+  }
   return launch_dot_fused(ctx, s, (complex_mode ? 2 : 1) * M * N, cmax, dot_group_matrix(), stream);
 }
 

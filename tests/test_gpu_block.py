@@ -171,7 +171,7 @@ def test_several_blocks_with_basecase(arb, contiguous):
     h, blocks = alg2.plan(A, B, M, K, N, p)
     assert any(b[2] for b in blocks) and any(not b[2] for b in blocks)
     out, names = run_mm(arb, A, B, M, K, N, p, arb.ALG_BLOCK, trace=True)
-    assert "accumulate" in names and "dot_fused" in names and "plan" in names
+    assert "accumulate" in names and "dot_tile" in names and "plan" in names
     check_bounds(out, A, B, M, K, N, p, [(i, j) for i in range(M) for j in range(N)])
 
 
@@ -182,7 +182,7 @@ def test_several_blocks_without_basecase(arb, contiguous):
     h, blocks = alg2.plan(A, B, M, K, N, p)
     assert len(blocks) >= 3 and not any(b[2] for b in blocks)
     out, names = run_mm(arb, A, B, M, K, N, p, arb.ALG_BLOCK, trace=True)
-    assert "acc_round" in names and "dot_fused" not in names
+    assert "acc_round" in names and "dot_tile" not in names and "dot_fused" not in names
     assert names.count("accumulate") == len(blocks)
     rng = np.random.default_rng(2)
     check_bounds(out, A, B, M, K, N, p, [(int(a), int(b)) for a, b in
@@ -504,3 +504,38 @@ def test_pascal_product_closed_form(arb):
             idx = i * n + j
             assert X.dy_to_fraction(X.mid(out, idx)) == comb(i + j, i), (i, j)
             assert int(out.rad_man[idx]) == 0, (i, j)
+
+
+@pytest.mark.parametrize("cplx", [False, True])
+def test_basecase_dots_tiled_equal_lane_groups(arb, cplx):
+    """The basecase blocks of Algorithm 2 through the tiled dot kernel equal, in every output
+    field, the group-of-lanes kernel (ARBGPU_DOT_TILE=0): the tagged index lists, the complex
+    combinations and the accumulated blocks as `initial` term."""
+    import os
+    from synth.workloads import complex_matmul_laplace
+    if cplx:  # tiles of 32 x 32 entries: enough of them to fill the SMs
+        case = complex_matmul_laplace(n=448, structured=False)
+        A, B, M, K, N, p = case.A, case.B, 448, 448, 448, 128
+    else:
+        A, B = jump_case(4, 640, 100, 320, [35], 64, rad=60)
+        M, K, N, p = 640, 100, 320, 64
+    outs = []
+    for tile in ("1", "0"):
+        old = os.environ.get("ARBGPU_DOT_TILE")
+        os.environ["ARBGPU_DOT_TILE"] = tile
+        try:
+            if cplx:
+                o, names = run_cmm(arb, A, B, M, K, N, p, arb.ALG_BLOCK, trace=True)
+            else:
+                o1, names = run_mm(arb, A, B, M, K, N, p, arb.ALG_BLOCK, trace=True)
+                o = [o1]
+            assert ("dot_tile" in names) == (tile == "1")
+            outs.append(o)
+        finally:
+            if old is None:
+                del os.environ["ARBGPU_DOT_TILE"]
+            else:
+                os.environ["ARBGPU_DOT_TILE"] = old
+    for a, b in zip(outs[0], outs[1]):
+        for f in ("limbs", "exp", "flags", "rad_man", "rad_exp"):
+            assert np.array_equal(getattr(a, f), getattr(b, f)), f

@@ -294,3 +294,50 @@ def test_matmul_by_dots_p256_sampled(arb):
         i, j = divmod(int(e), 96)
         ref = alg1.matmul_entry(case.A[0], case.B[0], 96, 96, i, j, 256, 4)
         assert mismatch(out, int(e), ref) is None
+
+
+@pytest.mark.parametrize("M,K,N,prec,cplx", [(330, 70, 450, 128, False), (170, 129, 400, 256, False),
+                                             (90, 40, 700, 512, False), (200, 33, 360, 1024, False),
+                                             (310, 50, 330, 64, True), (400, 17, 80, 192, True)])
+def test_tiled_matrix_dots_equal_the_lane_group_kernel(arb, M, K, N, prec, cplx):
+    """The classical product through the shared-memory tiled dot kernel equals, in every output
+    field, the group-of-lanes kernel (ARBGPU_DOT_TILE=0) and the Algorithm 1 restatement."""
+    import os
+
+    from tests.gpu_util import to_raw
+    rng = np.random.default_rng(M * 1000 + K)
+    nl = (prec + 63) // 64
+    parts = 2 if cplx else 1
+    A = [random_balls(rng, M * K, nl, prec, -12, 12, rad_bits=prec - 6, rad_zero_frac=0.4,
+                      zero_frac=0.1) for _ in range(parts)]
+    B = [random_balls(rng, K * N, nl, prec, -12, 12, rad_bits=prec - 6, rad_zero_frac=0.4,
+                      zero_frac=0.1) for _ in range(parts)]
+    outs = []
+    for tile in ("1", "0"):
+        old = os.environ.get("ARBGPU_DOT_TILE")
+        os.environ["ARBGPU_DOT_TILE"] = tile
+        try:
+            C = [arb.Balls.empty(M * N, nl) for _ in range(parts)]
+            ctx = arb.default_context()
+            ctx.trace(True)
+            arb.mat_mul(C if cplx else C[0], [arb.Balls.from_raw(a) for a in A] if cplx
+                        else arb.Balls.from_raw(A[0]), [arb.Balls.from_raw(b) for b in B] if cplx
+                        else arb.Balls.from_raw(B[0]), M, K, N, prec, alg=arb.ALG_DOT)
+            assert ctx.status() == 0
+            names = [r[0] for r in ctx.trace_read()]
+            ctx.trace(False)
+            assert ("dot_tile" in names) == (tile == "1")
+            outs.append([to_raw(c) for c in C])
+        finally:
+            if old is None:
+                del os.environ["ARBGPU_DOT_TILE"]
+            else:
+                os.environ["ARBGPU_DOT_TILE"] = old
+    for a, b in zip(outs[0], outs[1]):
+        for f in ("limbs", "exp", "flags", "rad_man", "rad_exp"):
+            assert np.array_equal(getattr(a, f), getattr(b, f)), f
+    if not cplx:
+        for e in range(0, M * N, 997):
+            i, j = divmod(e, N)
+            ref = alg1.matmul_entry(A[0], B[0], K, N, i, j, prec, nl)
+            assert mismatch(outs[0][0], e, ref) is None, (i, j)
