@@ -375,3 +375,73 @@ def int_matmul_entry(X, Y, i, j):
 
 def height(v: int) -> int:
     return abs(v).bit_length()
+
+
+# ---- Section IV-B's last paragraph: Algorithm 2 uses every input bit, where Algorithm 1 omits
+# negligible limbs.  Reading (the paper leaves it to future work; the GPU path follows the same
+# rule): with E_ij = max_k top(a_ik) + top(b_kj) (the largest product exponent of entry (i, j),
+# Algorithm 1's e_max of that dot), every bit of row i of A below 2^tau_i and of column j of B
+# below 2^sigma_j is dropped (truncation toward zero), where
+#     tau_i = min_j (E_ij - top_j(B)) - p - G,   sigma_j = min_i (E_ij - top_i(A)) - p - G,
+#     G = bc(K) + 8,
+# the minima over the entries with a nonzero product.  Then |a_ik - a'_ik| < 2^tau_i and the
+# error of every product sum is below K (2^(tau_i + top_j) + 2^(top_i + sigma_j) + ...) <=
+# 3 K 2^(E_ij - p - G) < 2^-p 2^(E_ij - 2) 3/64 <= (3/64) 2^-p sum_k |a_ik b_kj|; each truncated
+# line's nonzero entries carry 2^tau (2^sigma) more radius, so the ball stays rigorous.  A line
+# without any nonzero product is left as it is.
+
+def bc(v: int) -> int:
+    return int(v).bit_length()
+
+
+def omission_thresholds(A, B, M, K, N, prec):
+    """``(tau, sigma)``: the truncation exponents of the rows of A and the columns of B (None for a
+    line left as it is)."""
+    G = bc(K) + 8
+    ta = [[top_bottom(A, i * K + k) for k in range(K)] for i in range(M)]
+    tb = [[top_bottom(B, k * N + j) for j in range(N)] for k in range(K)]
+    rtop = [max((t[0] for t in row if t is not None), default=None) for row in ta]
+    ctop = [max((tb[k][j][0] for k in range(K) if tb[k][j] is not None), default=None)
+            for j in range(N)]
+    E = [[None] * N for _ in range(M)]
+    for i in range(M):
+        for j in range(N):
+            for k in range(K):
+                a, b = ta[i][k], tb[k][j]
+                if a is not None and b is not None:
+                    v = a[0] + b[0]
+                    E[i][j] = v if E[i][j] is None else max(E[i][j], v)
+    tau = []
+    for i in range(M):
+        d = [E[i][j] - ctop[j] for j in range(N) if E[i][j] is not None]
+        tau.append(min(d) - prec - G if d else None)
+    sigma = []
+    for j in range(N):
+        d = [E[i][j] - rtop[i] for i in range(M) if E[i][j] is not None]
+        sigma.append(min(d) - prec - G if d else None)
+    return tau, sigma
+
+
+def truncate_value(tb, t):
+    """The value ``mant 2^shift`` of ``tb = top_bottom(...)`` with every bit below 2^t dropped
+    (toward zero), as ``(integer, exponent)``; ``t`` None keeps it."""
+    if tb is None:
+        return 0, 0
+    mant, shift = tb[2], tb[3]
+    if t is None or shift >= t:
+        return mant, shift
+    q = abs(mant) >> (t - shift)
+    return (q if mant > 0 else -q), t
+
+
+def omitted_product(A, B, M, K, N, tau, sigma):
+    """The exact product of the truncated operands, entry by entry, as Fractions."""
+    from fractions import Fraction
+    a = [[truncate_value(top_bottom(A, i * K + k), tau[i]) for k in range(K)] for i in range(M)]
+    b = [[truncate_value(top_bottom(B, k * N + j), sigma[j]) for j in range(N)]
+         for k in range(K)]
+
+    def val(v):
+        return Fraction(v[0]) * Fraction(2) ** v[1]
+    return [[sum(val(a[i][k]) * val(b[k][j]) for k in range(K)) for j in range(N)]
+            for i in range(M)]

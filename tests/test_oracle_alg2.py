@@ -712,3 +712,91 @@ def test_planted_mistakes_in_the_complex_ordering_are_caught(monkeypatch):
     # (b) tops taken from the real part only: the order differs from the merged one
     only_re = alg2.inner_order(A[0], B[0], M, K, N)
     assert only_re != alg2.inner_order_complex(A, B, M, K, N)
+
+
+# ------------------------------------------------------------------ negligible-limb omission
+# (Section IV-B's last paragraph, in the reading of ``oracle.alg2.omission_thresholds``)
+
+def _wide_case(seed, M, K, N, p, bits, spread):
+    rng = np.random.default_rng(seed)
+    nl = (bits + 63) // 64
+    A = random_balls(rng, M * K, nl, bits, -spread, spread)
+    B = random_balls(rng, K * N, nl, bits, -spread, spread)
+    return A, B
+
+
+@pytest.mark.parametrize("seed,M,K,N,p,bits,spread", [(1, 4, 12, 3, 64, 1024, 5),
+                                                     (2, 5, 9, 4, 128, 200, 60),
+                                                     (3, 3, 7, 6, 64, 64, 200)])
+def test_omission_keeps_the_accuracy_bound(seed, M, K, N, p, bits, spread):
+    """The truncated operands' exact product differs from the exact product by at most
+    (3/64) 2^-p sum_k |a_ik b_kj| on every entry (the bound the reading derives), every dropped
+    part of an entry is below 2^tau (2^sigma), and something is dropped at all."""
+    from fractions import Fraction
+    A, B = _wide_case(seed, M, K, N, p, bits, spread)
+    tau, sigma = alg2.omission_thresholds(A, B, M, K, N, p)
+    T = alg2.omitted_product(A, B, M, K, N, tau, sigma)
+    S = exact_product(A, B, M, K, N)
+    dropped = False
+    for i in range(M):
+        for k in range(K):
+            tb = alg2.top_bottom(A, i * K + k)
+            v, e = alg2.truncate_value(tb, tau[i])
+            if tb is not None:
+                exact = Fraction(tb[2]) * Fraction(2) ** tb[3]
+                d = abs(exact - Fraction(v) * Fraction(2) ** e)
+                assert d < Fraction(2) ** tau[i]
+                dropped = dropped or d > 0
+    for i in range(M):
+        for j in range(N):
+            sabs = sum(abs(ball_values(A, i * K + k)[0] * ball_values(B, k * N + j)[0])
+                       for k in range(K))
+            assert abs(T[i][j] - S[i][j]) <= Fraction(3, 64) * sabs / Fraction(2) ** p, (i, j)
+    assert dropped
+
+
+def test_omission_thresholds_by_brute_force():
+    """tau_i and sigma_j against a direct evaluation of their definition (all pairs (i, j) and
+    every k), on a case with zero entries and an empty row."""
+    rng = np.random.default_rng(8)
+    M, K, N, p = 4, 6, 5, 64
+    A = random_balls(rng, M * K, 2, 128, -40, 40, zero_frac=0.3)
+    B = random_balls(rng, K * N, 2, 128, -40, 40, zero_frac=0.3)
+    A.flags[0:K] = X.FLAG_ZERO  # row 0 of A entirely zero: no product, no truncation
+    A.limbs[:, 0:K] = 0
+    tau, sigma = alg2.omission_thresholds(A, B, M, K, N, p)
+    G = alg2.bc(K) + 8
+    val = lambda raw, i: None if int(raw.flags[i]) & X.FLAG_ZERO else int(raw.exp[i])  # noqa
+    for i in range(M):
+        cand = []
+        for j in range(N):
+            prods = [val(A, i * K + k) + val(B, k * N + j) for k in range(K)
+                     if val(A, i * K + k) is not None and val(B, k * N + j) is not None]
+            cols = [val(B, k * N + j) for k in range(K) if val(B, k * N + j) is not None]
+            if prods:
+                cand.append(max(prods) - max(cols))
+        assert tau[i] == (min(cand) - p - G if cand else None)
+    assert tau[0] is None
+    for j in range(N):
+        cand = []
+        for i in range(M):
+            prods = [val(A, i * K + k) + val(B, k * N + j) for k in range(K)
+                     if val(A, i * K + k) is not None and val(B, k * N + j) is not None]
+            rows = [val(A, i * K + k) for k in range(K) if val(A, i * K + k) is not None]
+            if prods:
+                cand.append(max(prods) - max(rows))
+        assert sigma[j] == (min(cand) - p - G if cand else None)
+
+
+def test_planted_omission_slip_is_caught(monkeypatch):
+    """Thresholds 150 bits higher than the reading's (as if E_ij were replaced by a bound 150
+    bits too large) drop bits that matter: the accuracy pin fails."""
+    orig = alg2.omission_thresholds
+
+    def coarse(A, B, M, K, N, prec):
+        tau, sigma = orig(A, B, M, K, N, prec)
+        return ([None if t is None else t + 150 for t in tau],
+                [None if t is None else t + 150 for t in sigma])
+    monkeypatch.setattr(alg2, "omission_thresholds", coarse)
+    with pytest.raises(AssertionError):
+        test_omission_keeps_the_accuracy_bound(2, 5, 9, 4, 128, 200, 60)
