@@ -221,7 +221,15 @@ arbgpu_status arbgpu_approx_dot(arbgpu_ctx *ctx, const arbgpu_balls *res,
  *                     first permuted and scaled (Section IV-B: column k of A times 2^g_k, row k of
  *                     B times 2^-g_k, indices sorted by their product bound), which often leaves
  *                     one block; a real product with one such block is rounded once from it.
- *                     The environment variable ARBGPU_INNER_ORDER=0 keeps the own order.  Radii:
+ *                     The environment variable ARBGPU_INNER_ORDER=0 keeps the own order.
+ *                     Before that, a product that needs several blocks and holds lines much
+ *                     taller than p needs has its negligible limbs omitted (Section IV-B, last
+ *                     paragraph): with E_ij = max_k top(a_ik) + top(b_kj), the bits of row i of A
+ *                     below min_j (E_ij - top_j(B)) - p - bc(K) - 8 (and likewise for the
+ *                     columns of B) are dropped and added to those entries' radii; the midpoint
+ *                     error stays below (3/64) 2^-p sum_k |a_ik b_kj| and the ball stays
+ *                     rigorous.  When the truncated operands fit one block, that block is used.
+ *                     ARBGPU_OMIT=0 keeps every bit.  Radii:
  *                     |A| R_B + R_A (|B| + R_B) from exact integer products of magnitudes rounded
  *                     up to 8*S_r-bit windows.
  *   ARBGPU_ALG_AUTO   picks by size and precision.
@@ -270,7 +278,8 @@ arbgpu_status arbgpu_mat_mul_batched_workspace_size(arbgpu_ctx *ctx,
  * gives Ar Br, Ai Bi, Ar Bi, Ai Br; batched items in item order):
  *   kind   0: blocks over the inner index in its own order; 1: over the inner ordering (the
  *          block positions index the order listed after the triples); 2: the one block of a
- *          complex product by eq. 2 (ARBGPU_MM_COMPLEX_3M) shared by both parts
+ *          complex product by eq. 2 (ARBGPU_MM_COMPLEX_3M) shared by both parts; 3: one block
+ *          of the operands with their negligible limbs omitted (see arbgpu_mat_mul)
  *   h      the height bound, floor(1.25 min(p, max(p_A, p_B))) + 192
  *   K      the inner dimension
  *   nb     the number of blocks, then nb triples (start, stop, basecase): [start, stop) covers

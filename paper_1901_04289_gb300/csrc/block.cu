@@ -937,10 +937,11 @@ template <int NCH>
 constexpr int rt_top_limbs() {
   return (NCH + 1) / 2 + 1;
 }
-// Per producer thread, the raw fields of its entries of its next RT_PD tiles, staged by cp.async: words [0] exp, [1] bot, [2] flags | rad_man << 32, [3] rad_exp, [4] and [5]
-// the two radius windows, [6 ...] the top limbs (word 6 + i = limb nl - NLW + i).  Layout
-// [RT_NP][RT_PD][128][SW].
-constexpr int RT_SLOT_FIXED = 6;
+// Per producer thread, the raw fields of its entries of its next RT_PD tiles, staged by cp.async:
+// words [0] exp, [1] bot, [2] flags | rad_man << 32, [3] rad_exp, [4] and [5] the two radius
+// windows, [6] the line's omission exponent, [7 ...] the top limbs (word 7 + i = limb
+// nl - NLW + i).  Layout [RT_NP][RT_PD][128][SW].
+constexpr int RT_SLOT_FIXED = 7;
 constexpr int RT_PD = 2;  // tiles staged ahead by each producer thread
 
 // The float sg * b for byte b of `w` (exact): sg (2^23 + b) + sgb with sgb = -sg 2^23.
@@ -961,6 +962,9 @@ struct RtSide {
   const int64_t *top, *radtop, *plustop;  // the radius windows' exponents (plustop: B only)
   SplitOut ro;           // radius operands written directly (when not part of the staged planes)
   const uint16_t *wtab;  // [NPAD][128] BF16 weight table of this operand
+  // negligible-limb omission: per line, the exponent tau below which the line's bits were
+  // dropped (INT64_MIN: none); every nonzero entry of such a line carries 2^tau more radius
+  const int64_t *trunc = nullptr;
 };
 
 struct RtArgs {
@@ -1003,6 +1007,7 @@ __device__ __forceinline__ void rt_prefetch(const RtArgs &a, const RtSide &sd, u
     cp_async(slot + 3, X.rad_exp + e, 8);
     if (w1) cp_async(slot + 4, (IS_B ? sd.radtop : sd.top) + r, 8);
     if (w2) cp_async(slot + 5, (IS_B ? sd.plustop : sd.radtop) + r, 8);
+    if (sd.trunc) cp_async(slot + 6, sd.trunc + r, 8);
   }
 #pragma unroll
   for (int i = 0; i < NLW; ++i)
@@ -1056,7 +1061,11 @@ __device__ __forceinline__ void rt_entry(const RtArgs &a, const RtSide &sd, cons
     }
   }
   if (want_rad) {
-    const Mag rad{(uint32_t)(w2f >> 32), (int64_t)slot[3]};
+    Mag rad{(uint32_t)(w2f >> 32), (int64_t)slot[3]};
+    if (sd.trunc && !(fl & (ARBGPU_FLAG_ZERO | SPECIAL_MASK))) {
+      const int64_t t = (int64_t)slot[6];  // bits below 2^t were dropped from this line
+      if (t != INT64_MIN) rad = mag_add_up(rad, Mag{1u << 29, t + 1});
+    }
     uint32_t u1 = 0, u2 = 0;
     const int64_t f1 = (int64_t)slot[4], f2 = (int64_t)slot[5];
     if (!IS_B) {
@@ -2883,6 +2892,8 @@ struct BlockWs {
   size_t acc[2], err[2], rman[2], rexp[2], ilimbs[2], iexp[2], iflags[2], irman[2], irexp[2], bk[2];
   size_t etop[2];  // per-entry exponent bound of the accumulated products (maxplus_top_kernel)
   size_t relA[2], relB[2];  // tops of A's and B's parts relative to their lines (int32)
+  // negligible-limb omission: one product's E, its truncated lines and their statistics
+  size_t eprod, om_rbot, om_rrad, om_rtrunc, om_cbot, om_crad, om_cplus, om_ctrunc, om_stats;
   // multimodular engine: residue planes, residue products, tables
   size_t resA, resB, cdig, ccar, craw;
   // complex product by eq. 2: residue planes of the parts and their sum, three residue products
@@ -2964,6 +2975,15 @@ static BlockWs block_ws(arbgpu_ctx *ctx, int64_t M, int64_t K, int64_t N, int pr
     w.relA[q] = take(4 * (size_t)M * K);
     w.relB[q] = take(4 * (size_t)K * N);
   }
+  w.eprod = take(8 * MN);
+  w.om_rbot = take(8 * (size_t)M);
+  w.om_rrad = take(8 * (size_t)M);
+  w.om_rtrunc = take(8 * (size_t)M);
+  w.om_cbot = take(8 * (size_t)N);
+  w.om_crad = take(8 * (size_t)N);
+  w.om_cplus = take(8 * (size_t)N);
+  w.om_ctrunc = take(8 * (size_t)N);
+  w.om_stats = take(sizeof(BlockStats));
   // residue planes, then the two radius products' operand planes (batch items NM and NM + 1)
   w.resA = take((size_t)2 * (w.NMmax + 2) * M * w.Kp * 2);
   w.resB = take((size_t)2 * (w.NMmax + 2) * N * w.Kp * 2);
@@ -3016,6 +3036,8 @@ size_t block_workspace_size(arbgpu_ctx *ctx, int64_t M, int64_t K, int64_t N, in
 // Line statistics of one block (pointers into the whole-range or the per-block arrays).
 struct Lines {
   const int64_t *rtop, *rbot, *rrad, *ctop, *cbot, *crad, *cplus;
+  // negligible-limb omission (omit_product): the per-line exponents below which bits were dropped
+  const int64_t *rtrunc = nullptr, *ctrunc = nullptr;
 };
 
 static int digits_for_height(int64_t h) { return h < 0 ? 1 : (int)((h + 2 + 7) / 8); }
@@ -3098,10 +3120,14 @@ static arbgpu_status run_block(arbgpu_ctx *ctx, const BlockWs &w, uint8_t *ws, c
   const CrtPlan *plan = nullptr;
   const int nch32 = (int)(((hA > hB ? hA : hB) + 2 + 31) / 32) + 1;
   const size_t res_smem = (size_t)NM * ((nch32 + 3) / 4 * 4) * 4;  // residue kernel's table
-  if (choose_crt(SA, SB, NM, M, N, Kp, hA, hB) && NM <= w.NMmax && res_smem <= 48 * 1024) {
+  const bool omitted = ln.rtrunc || ln.ctrunc;  // only the tensor-core residue kernel adds the
+                                                 // omission's radius
+  if ((omitted || choose_crt(SA, SB, NM, M, N, Kp, hA, hB)) && NM <= w.NMmax &&
+      res_smem <= 48 * 1024) {
     plan = crt_plan(NM);
     if (plan && plan->NMW + 1 > RD_MAXW) plan = nullptr;
   }
+  if (omitted && !plan) return ARBGPU_ERR_LIMIT;
   if (!plan && (SA > w.Smax || SB > w.Smax || !digit_gemm_fits(SA, SB, Kp)))
     return ARBGPU_ERR_LIMIT;
   __nv_bfloat16 *dA = (__nv_bfloat16 *)(ws + w.dA), *dB = (__nv_bfloat16 *)(ws + w.dB);
@@ -3159,13 +3185,15 @@ static arbgpu_status run_block(arbgpu_ctx *ctx, const BlockWs &w, uint8_t *ws, c
                          (int64_t)L.NPL * (M + N) * Kp * 2);
       RtArgs ra{};
       ra.side[0] = RtSide{Av, M, lda, ln.rbot, ln.rtop, ln.rrad, nullptr,
-                          fold ? SplitOut{} : roA, dt.wtab};
+                          fold ? SplitOut{} : roA, dt.wtab, ln.rtrunc};
       ra.side[1] = RtSide{Bv, N, ldb, ln.cbot, ln.ctop, ln.crad, ln.cplus,
-                          fold ? SplitOut{} : roB, dt.wtab + (size_t)plan->NPAD * 128};
+                          fold ? SplitOut{} : roB, dt.wtab + (size_t)plan->NPAD * 128,
+                          ln.ctrunc};
       ra.k0 = k0, ra.K = Kb, ra.Kp = Kp, ra.NM = NM, ra.rinv = dt.rinv;
       const arbgpu_status st = launch_residues_tc(ctx, L, nch, s, ra, resA, resB);
       if (st != ARBGPU_OK) return st;
     } else {
+      if (omitted) return ARBGPU_ERR_LIMIT;
       {
         LaunchScope sc(ctx, s, "residues_a", M * Kp * NM * nchA);
         launch_residues(nchA, M * Kp, s, Av, false, M, k0, Kb, Kp, lda, ln.rbot, NM, dt.pow32,
@@ -3287,6 +3315,160 @@ static void log_plan(arbgpu_ctx *ctx, int kind, int64_t h, int64_t K,
   for (int32_t v : triples) L.push_back(v);
 }
 
+// ---- negligible-limb omission (Section IV-B's last paragraph: Algorithm 2 uses every input bit,
+// where Algorithm 1 omits negligible limbs).  Reading: with E_ij = max_k top(x_ik) + top(y_kj)
+// (maxplus_top_kernel), the bits of row i of X below tau_i = min_j (E_ij - ctop_j) - p - G and of
+// column j of Y below sigma_j = min_i (E_ij - rtop_i) - p - G, G = bc(K) + 8 (minima over the
+// entries with a nonzero product), are dropped toward zero: the scaled integers then start at
+// max(bottom, tau).  The product changes by less than 3 K 2^(E_ij - p - G) <= (3/64) 2^-p
+// sum_k |x_ik y_kj|, and every nonzero entry of a truncated line carries 2^tau (2^sigma) more
+// radius (the tensor-core residue kernel adds it), so the ball stays rigorous.  A line without a
+// nonzero product is left as it is.
+
+// Rows: one warp per row of X.  Writes the truncated row lines and tau (INT64_MIN: none) and
+// folds the row heights and radius flags into st.
+__global__ void __launch_bounds__(256) omission_rows_kernel(
+    const int64_t *E, int64_t M, int64_t N, const int64_t *rtop, const int64_t *rbot,
+    const int64_t *rrad, const int64_t *ctop, int64_t off, int64_t *obot, int64_t *orad,
+    int64_t *otrunc, BlockStats *st) {
+  const int lane = threadIdx.x & 31;
+  const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (i >= M) return;
+  long long m = INT64_MAX;
+  for (int64_t j = lane; j < N; j += 32) {
+    const int64_t e = E[i * N + j];
+    if (e != INT64_MIN) m = min(m, (long long)(e - ctop[j]));
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m = min(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if (lane != 0) return;
+  int64_t bot = rbot[i], rr = rrad[i], t = INT64_MIN;
+  if (m != INT64_MAX && rtop[i] != INT64_MIN && bot < m - off) {
+    t = m - off;
+    bot = t;
+    rr = rr > t + 1 ? rr : t + 1;
+  }
+  obot[i] = bot;
+  orad[i] = rr;
+  otrunc[i] = t;
+  if (rtop[i] != INT64_MIN) atomic_max_i64(&st->hA, rtop[i] - bot);
+  if (rr != INT64_MIN) atomicOr(&st->radA, 1);
+}
+
+// Columns: 32 columns x 8 row slices per CTA, the slices' minima combined in shared memory.
+__global__ void __launch_bounds__(256) omission_cols_kernel(
+    const int64_t *E, int64_t M, int64_t N, const int64_t *rtop, const int64_t *ctop,
+    const int64_t *cbot, const int64_t *crad, int64_t off, int64_t *obot, int64_t *orad,
+    int64_t *oplus, int64_t *otrunc, BlockStats *st) {
+  __shared__ long long s_m[8][32];
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  const int64_t j = (int64_t)blockIdx.x * 32 + tx;
+  long long m = INT64_MAX;
+  if (j < N)
+    for (int64_t i = ty; i < M; i += 8) {
+      const int64_t e = E[i * N + j];
+      if (e != INT64_MIN) m = min(m, (long long)(e - rtop[i]));
+    }
+  s_m[ty][tx] = m;
+  __syncthreads();
+  if (ty != 0 || j >= N) return;
+  for (int q = 1; q < 8; ++q) m = min(m, s_m[q][tx]);
+  int64_t bot = cbot[j], rr = crad[j], t = INT64_MIN;
+  if (m != INT64_MAX && ctop[j] != INT64_MIN && bot < m - off) {
+    t = m - off;
+    bot = t;
+    rr = rr > t + 1 ? rr : t + 1;
+  }
+  obot[j] = bot;
+  orad[j] = rr;
+  otrunc[j] = t;
+  const int64_t mx = ctop[j] > rr ? ctop[j] : rr;  // |y| + r_y < 2^(max(top, rexp) + 1)
+  oplus[j] = mx == INT64_MIN ? INT64_MIN : mx + 1;
+  if (ctop[j] != INT64_MIN) atomic_max_i64(&st->hB, ctop[j] - bot);
+  if (rr != INT64_MIN) atomicOr(&st->radB, 1);
+}
+
+static bool omission_enabled() {
+  const char *e = getenv("ARBGPU_OMIT");
+  return !(e && !strcmp(e, "0"));
+}
+
+// Whether the omission is worth trying for a product with these statistics: it needs several
+// blocks as it is, and some line is more than 32 bits taller than p + G needs.  (For a product
+// that already fits one block the saved moduli did not repay the extra passes and the statistics
+// read-back: the grouped workload of 256 products ran 77 -> 94 ms with it.)
+static bool omission_wanted(int prec, int64_t K, const BlockStats &hs, bool one_block) {
+  if (!omission_enabled() || one_block) return false;
+  int bk = 0;
+  for (int64_t v = K; v > 0; v >>= 1) ++bk;
+  const int64_t lim = (int64_t)prec + bk + 8 + 32;
+  return hs.hA > lim || hs.hB > lim;
+}
+
+struct Omitted {
+  bool ok;
+  Lines lines;
+  BlockStats hs;
+};
+
+// The omission for X Y under the whole-range lines `full` (dX, dY: the operands' tops relative to
+// those lines, rel_tops_kernel): E, the thresholds, the truncated lines in the workspace and
+// their statistics (one read-back).  ok when the truncated operands fit one
+// block of height <= h (h of the untruncated operands' precisions) and the tensor-core residue
+// kernel takes them; otherwise nothing is used.
+static arbgpu_status omit_product(arbgpu_ctx *ctx, const BlockWs &w, uint8_t *ws,
+                                  const int32_t *dX, const int32_t *dY, int64_t M, int64_t K,
+                                  int64_t N, int prec, const Lines &full, const BlockStats &hs,
+                                  cudaStream_t s, Omitted *out) {
+  out->ok = false;
+  int bk = 0;
+  for (int64_t v = K; v > 0; v >>= 1) ++bk;
+  const int64_t off = (int64_t)prec + bk + 8;
+  int64_t *E = (int64_t *)(ws + w.eprod);
+  {
+    LaunchScope sc(ctx, s, "maxplus_top", M * K * N);
+    const dim3 grid((unsigned)((N + MP_T - 1) / MP_T), (unsigned)((M + MP_T - 1) / MP_T));
+    maxplus_top_kernel<<<grid, 256, 0, s>>>(dX, dY, full.rtop, full.ctop, M, K, N, E, 1);
+  }
+  int64_t *rb = (int64_t *)(ws + w.om_rbot), *rr = (int64_t *)(ws + w.om_rrad);
+  int64_t *rt = (int64_t *)(ws + w.om_rtrunc);
+  int64_t *cb = (int64_t *)(ws + w.om_cbot), *cr = (int64_t *)(ws + w.om_crad);
+  int64_t *cp = (int64_t *)(ws + w.om_cplus), *ct = (int64_t *)(ws + w.om_ctrunc);
+  BlockStats *st = (BlockStats *)(ws + w.om_stats);
+  if (cudaMemsetAsync(st, 0, sizeof(BlockStats), s) != cudaSuccess) return ARBGPU_ERR_CUDA;
+  {
+    LaunchScope sc(ctx, s, "omission", M * N);
+    omission_rows_kernel<<<(unsigned)((M + 7) / 8), 256, 0, s>>>(
+        E, M, N, full.rtop, full.rbot, full.rrad, full.ctop, off, rb, rr, rt, st);
+    omission_cols_kernel<<<(unsigned)((N + 31) / 32), 256, 0, s>>>(
+        E, M, N, full.rtop, full.ctop, full.cbot, full.crad, off, cb, cr, cp, ct, st);
+    if (cudaGetLastError() != cudaSuccess) return ARBGPU_ERR_CUDA;
+  }
+  BlockStats os{};
+  const arbgpu_status rs = read_stats(ctx, st, &os, 1, s);
+  if (rs != ARBGPU_OK) return rs;
+  os.pA = hs.pA;
+  os.pB = hs.pB;
+  os.special = hs.special;
+  const int64_t h = height_bound(prec, hs);
+  if (os.hA > h || os.hB > h) return ARBGPU_OK;
+  // the tensor-core residue kernel must take the truncated operands (it adds their radius)
+  const int NM = crt_moduli_for_bits((int)((os.hA > 0 ? os.hA : 0) + (os.hB > 0 ? os.hB : 0) +
+                                           bk + 2));
+  const int nch = (int)(((os.hA > os.hB ? os.hA : os.hB) + 2 + 31) / 32) + 1;
+  if (NM > w.NMmax || NM > 128 || nch > 32) return ARBGPU_OK;
+  {
+    RtLayout L;  // (with the radius planes: the larger of the two shapes)
+    if (!residue_tc_layout(nch, NM, true, (M > N ? M : N) * w.Kp, &L)) return ARBGPU_OK;
+    const CrtPlan *plan = crt_plan(NM);
+    if (!plan || plan->NMW + 1 > RD_MAXW) return ARBGPU_OK;
+  }
+  out->lines = Lines{full.rtop, rb, rr, full.ctop, cb, cr, cp, rt, ct};
+  out->hs = os;
+  out->ok = true;
+  return ARBGPU_OK;
+}
+
 // Output of a real product that may be rounded straight from one exact block.
 struct DirectRound {
   BallsOut C;
@@ -3305,7 +3487,8 @@ static arbgpu_status accumulate_product(arbgpu_ctx *ctx, const BlockWs &w, uint8
                                         const std::vector<int32_t> *kmap = nullptr,
                                         const DirectRound *direct = nullptr,
                                         bool *rounded = nullptr,
-                                        const std::function<arbgpu_status()> *prepare = nullptr) {
+                                        const std::function<arbgpu_status()> *prepare = nullptr,
+                                        int plan_kind = 0) {
   const int64_t h = height_bound(prec, hs);
   std::vector<int32_t> hb;
   std::vector<BlockStats> hbs;
@@ -3316,7 +3499,7 @@ static arbgpu_status accumulate_product(arbgpu_ctx *ctx, const BlockWs &w, uint8
   if (hs.hA <= h && hs.hB <= h) {
     hb = {0, (int32_t)K, 0};
     hbs = {hs};
-    log_plan(ctx, 0, h, K, hb);
+    log_plan(ctx, plan_kind, h, K, hb);
   } else {
     int64_t *tA = (int64_t *)(ws + w.tA), *bA = (int64_t *)(ws + w.bA);
     int64_t *tBT = (int64_t *)(ws + w.tB), *bBT = (int64_t *)(ws + w.bB);
@@ -3414,8 +3597,11 @@ static arbgpu_status accumulate_product(arbgpu_ctx *ctx, const BlockWs &w, uint8
       continue;
     }
     const int64_t oM = planned ? (int64_t)b * M : 0, oN = planned ? (int64_t)b * N : 0;
-    const Lines lb{per.rtop + oM, per.rbot + oM, per.rrad + oM, per.ctop + oN,
-                   per.cbot + oN, per.crad + oN, per.cplus + oN};
+    // (the omission's per-line exponents belong to the whole-range lines: one block only)
+    const Lines lb{per.rtop + oM,  per.rbot + oM,  per.rrad + oM,
+                   per.ctop + oN,  per.cbot + oN,  per.crad + oN,
+                   per.cplus + oN, planned ? nullptr : per.rtrunc,
+                   planned ? nullptr : per.ctrunc};
     AccArgs aa{};
     arbgpu_status st1 = run_block(ctx, w, ws, Xv, Yv, M, N, ldx, ldy, k0, k1 - k0, hbs[b].hA,
                                   hbs[b].hB, hbs[b].radA != 0, hbs[b].radB != 0, lb, s, &aa.mid,
@@ -3854,10 +4040,70 @@ arbgpu_status block_finish(arbgpu_ctx *ctx, const arbgpu_balls *C, const arbgpu_
                  colsL[yb].cbot, colsL[yb].crad, colsL[yb].cplus};
   };
 
+  // the operands' tops relative to their lines (rel_tops_kernel), once per operand part per call:
+  // the max-plus bound of the accumulator's window and the negligible-limb omission use them
+  bool rel_done[4] = {false, false, false, false};  // A0, A1, B0, B1
+  auto ensure_rel = [&](int xa, int yb) -> arbgpu_status {
+    if (!rel_done[xa]) {
+      LaunchScope sc(ctx, s, "rel_tops", M * K);
+      rel_tops_kernel<<<(unsigned)((M * K + 255) / 256), 256, 0, s>>>(
+          Av[xa], lda, M, K, rowsL[xa].rtop, true, (int32_t *)(ws + w.relA[xa]));
+      rel_done[xa] = true;
+    }
+    if (!rel_done[2 + yb]) {
+      LaunchScope sc(ctx, s, "rel_tops", K * N);
+      rel_tops_kernel<<<(unsigned)((K * N + 255) / 256), 256, 0, s>>>(
+          Bv[yb], ldb, K, N, colsL[yb].ctop, false, (int32_t *)(ws + w.relB[yb]));
+      rel_done[2 + yb] = true;
+    }
+    return cudaGetLastError() == cudaSuccess ? ARBGPU_OK : ARBGPU_ERR_CUDA;
+  };
+
   if (!cplx) {
     const BlockStats hs = merge_stats(hst[0], hst[2]);
     const int64_t h = height_bound(prec, hs);
-    if (hs.hA <= h && hs.hB <= h) {
+    const bool one = hs.hA <= h && hs.hB <= h;
+    if (omission_wanted(prec, K, hs, one)) {
+      // ---- negligible limbs omitted: one block of the truncated operands, rounded once
+      arbgpu_status so = ensure_rel(0, 0);
+      if (so != ARBGPU_OK) return so;
+      Omitted om{};
+      so = omit_product(ctx, w, ws, (const int32_t *)(ws + w.relA[0]),
+                        (const int32_t *)(ws + w.relB[0]), M, K, N, prec, lines_of(0, 0), hs, s,
+                        &om);
+      if (so != ARBGPU_OK) return so;
+      if (om.ok) {
+        RoundArgs ra{};
+        so = run_block(ctx, w, ws, Av[0], Bv[0], M, N, lda, ldb, 0, K, om.hs.hA, om.hs.hB,
+                       om.hs.radA != 0, om.hs.radB != 0, om.lines, s, &ra.mid, &ra.rp1, &ra.rp2);
+        if (so != ARBGPU_OK) return so;
+        log_plan(ctx, 3, h, K, {0, (int32_t)K, 0});
+        const Lines &ln = om.lines;
+        ra.rtop = ln.rtop;
+        ra.rbot = ln.rbot;
+        ra.rrad = ln.rrad;
+        ra.ctop = ln.ctop;
+        ra.cbot = ln.cbot;
+        ra.crad = ln.crad;
+        ra.cplus = ln.cplus;
+        ra.C = out_of(C[0]);
+        ra.M = M;
+        ra.N = N;
+        ra.ldc = ldc;
+        ra.Mp = w.Mp;
+        ra.Np = w.Np;
+        ra.prec = prec;
+        {
+          const int64_t units =
+              ra.mid.kind == 1 ? M * N * ra.mid.crt.NM * (int64_t)(2 * ra.mid.crt.NMW) : M * N;
+          LaunchScope sc(ctx, s, "block_round", units);
+          launch_block_round(ctx, ra, s);
+        }
+        *used_block = true;
+        return cudaGetLastError() == cudaSuccess ? ARBGPU_OK : ARBGPU_ERR_CUDA;
+      }
+    }
+    if (one) {
       // ---- one block: exact product, one rounding per entry
       log_plan(ctx, 0, h, K, {0, (int32_t)K, 0});
       const Lines full = lines_of(0, 0);
@@ -3940,7 +4186,6 @@ arbgpu_status block_finish(arbgpu_ctx *ctx, const arbgpu_balls *C, const arbgpu_
   // once before the part's first accumulation (a real product rounded straight from one exact
   // block needs none).
   bool etop_done[2] = {false, false};
-  bool rel_done[4] = {false, false, false, false};  // relative tops of A0, A1, B0, B1
   auto etop_of = [&](int q) -> arbgpu_status {
     if (etop_done[q]) return ARBGPU_OK;
     etop_done[q] = true;
@@ -3949,20 +4194,10 @@ arbgpu_status block_finish(arbgpu_ctx *ctx, const arbgpu_balls *C, const arbgpu_
     for (int t = 0; t < nprods; ++t) {
       const Prod &pr = prods[t];
       if (pr.part != q) continue;
-      // the operands' tops relative to their lines (each operand part once per call)
-      int32_t *dX = (int32_t *)(ws + w.relA[pr.xa]), *dY = (int32_t *)(ws + w.relB[pr.yb]);
-      if (!rel_done[pr.xa]) {
-        LaunchScope sc(ctx, s, "rel_tops", M * K);
-        rel_tops_kernel<<<(unsigned)((M * K + 255) / 256), 256, 0, s>>>(
-            Av[pr.xa], lda, M, K, rowsL[pr.xa].rtop, true, dX);
-        rel_done[pr.xa] = true;
-      }
-      if (!rel_done[2 + pr.yb]) {
-        LaunchScope sc(ctx, s, "rel_tops", K * N);
-        rel_tops_kernel<<<(unsigned)((K * N + 255) / 256), 256, 0, s>>>(
-            Bv[pr.yb], ldb, K, N, colsL[pr.yb].ctop, false, dY);
-        rel_done[2 + pr.yb] = true;
-      }
+      const arbgpu_status rs = ensure_rel(pr.xa, pr.yb);
+      if (rs != ARBGPU_OK) return rs;
+      const int32_t *dX = (const int32_t *)(ws + w.relA[pr.xa]);
+      const int32_t *dY = (const int32_t *)(ws + w.relB[pr.yb]);
       LaunchScope sc(ctx, s, "maxplus_top", M * K * N);
       const dim3 grid((unsigned)((N + MP_T - 1) / MP_T), (unsigned)((M + MP_T - 1) / MP_T));
       maxplus_top_kernel<<<grid, 256, 0, s>>>(dX, dY, rowsL[pr.xa].rtop, colsL[pr.yb].ctop, M, K,
@@ -3990,6 +4225,24 @@ arbgpu_status block_finish(arbgpu_ctx *ctx, const arbgpu_balls *C, const arbgpu_
     const BlockStats hs = merge_stats(hst[pr.xa], hst[2 + pr.yb]);
     const int64_t hb = height_bound(prec, hs);
     const std::function<arbgpu_status()> prep = [&etop_of, q = pr.part]() { return etop_of(q); };
+    if (cplx && omission_wanted(prec, K, hs, hs.hA <= hb && hs.hB <= hb)) {
+      // negligible limbs omitted: when the truncated operands fit one block, that block is
+      // accumulated (a real product tried this before reaching the loop)
+      arbgpu_status so = ensure_rel(pr.xa, pr.yb);
+      if (so != ARBGPU_OK) return so;
+      Omitted om{};
+      so = omit_product(ctx, w, ws, (const int32_t *)(ws + w.relA[pr.xa]),
+                        (const int32_t *)(ws + w.relB[pr.yb]), M, K, N, prec,
+                        lines_of(pr.xa, pr.yb), hs, s, &om);
+      if (so != ARBGPU_OK) return so;
+      if (om.ok) {
+        so = accumulate_product(ctx, w, ws, Av[pr.xa], Bv[pr.yb], M, K, N, lda, ldb, prec,
+                                om.lines, om.hs, pr.neg, pr.combo, av[pr.part], s,
+                                basek[pr.part], nullptr, nullptr, nullptr, &prep, 3);
+        if (so != ARBGPU_OK) return so;
+        continue;
+      }
+    }
     // several blocks: over the inner order when it is enabled (its workspace exists); a real
     // product whose inner order leaves one full block is rounded from it directly
     const bool ordered = w.oA && (hs.hA > hb || hs.hB > hb);

@@ -35,3 +35,28 @@ def batch_tensors(batch, device="cuda"):
                 yoff=t(batch.yoff, torch.int64), ystep=t(batch.ystep, torch.int64),
                 length=t(batch.length, torch.int64), prec=t(batch.prec, torch.int32),
                 sub=t(batch.sub, torch.uint8))
+
+
+class env:
+    """Set environment variables for the duration of a ``with`` block (or a fixture), then
+    restore them: the library reads its ARBGPU_* switches on every call."""
+
+    def __init__(self, **values):
+        self.values = values
+        self.old = {}
+
+    def __enter__(self):
+        import os
+        for k, v in self.values.items():
+            self.old[k] = os.environ.get(k)
+            os.environ[k] = v
+        return self
+
+    def __exit__(self, *exc):
+        import os
+        for k, v in self.old.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
+        return False

@@ -10,7 +10,7 @@ from oracle import alg1, alg2
 from oracle import exact as X
 from synth import SEED_BASE, random_balls
 from synth.workloads import block_matmul_n512, matmul_uniform
-from tests.gpu_util import to_raw
+from tests.gpu_util import env, to_raw
 
 pytestmark = pytest.mark.gpu
 
@@ -129,16 +129,11 @@ def check_bounds(out, A, B, M, K, N, prec, entries):
 
 @pytest.fixture
 def contiguous():
-    """The inner index in its own order (the inner ordering of Section IV-B off), so that the
-    blocks are the contiguous ones of ``alg2.plan``."""
-    import os
-    old = os.environ.get("ARBGPU_INNER_ORDER")
-    os.environ["ARBGPU_INNER_ORDER"] = "0"
-    yield
-    if old is None:
-        del os.environ["ARBGPU_INNER_ORDER"]
-    else:
-        os.environ["ARBGPU_INNER_ORDER"] = old
+    """The inner index in its own order (the inner ordering of Section IV-B off) and every input
+    bit kept (no negligible-limb omission), so that the blocks are the contiguous ones of
+    ``alg2.plan``."""
+    with env(ARBGPU_INNER_ORDER="0", ARBGPU_OMIT="0"):
+        yield
 
 
 def jump_case(seed, M, K, N, jumps, p, nl=1, rad=None):
@@ -171,7 +166,8 @@ def test_several_blocks_with_basecase(arb, contiguous):
     h, blocks = alg2.plan(A, B, M, K, N, p)
     assert any(b[2] for b in blocks) and any(not b[2] for b in blocks)
     out, names = run_mm(arb, A, B, M, K, N, p, arb.ALG_BLOCK, trace=True)
-    assert "accumulate" in names and "dot_tile" in names and "plan" in names
+    assert "accumulate" in names and "plan" in names
+    assert "dot_tile" in names or "dot_fused" in names  # (tiles only when they fill the SMs)
     check_bounds(out, A, B, M, K, N, p, [(i, j) for i in range(M) for j in range(N)])
 
 
@@ -330,7 +326,7 @@ def test_complex_3m_exact_inputs_and_zero_part(arb):
                   [(int(a), int(b)) for a, b in zip(rng2.integers(0, M, 30), rng2.integers(0, N, 30))])
 
 
-def test_complex_3m_falls_back_to_4m_for_several_blocks(arb):
+def test_complex_3m_falls_back_to_4m_for_several_blocks(arb, contiguous):
     """When the shared scaling needs several blocks (Laplace exponents along the inner index), the
     flag leaves the four-product path in place and the result is still rigorous."""
     from synth.workloads import complex_matmul_laplace
@@ -345,7 +341,7 @@ def test_complex_3m_falls_back_to_4m_for_several_blocks(arb):
 
 
 @pytest.mark.parametrize("structured", [True, False])
-def test_complex_laplace_small(arb, structured):
+def test_complex_laplace_small(arb, contiguous, structured):
     """The complex Laplace(40) workload at N = 128: structured (blocks along the inner index) and
     literal (i.i.d. exponents: mostly basecase blocks)."""
     from synth.workloads import complex_matmul_laplace
@@ -359,20 +355,13 @@ def test_complex_laplace_small(arb, structured):
 
 
 def _run_engine(arb, engine, A, B, M, K, N, prec, cplx=False):
-    import os
-    old = os.environ.get("ARBGPU_ENGINE")
-    os.environ["ARBGPU_ENGINE"] = engine
-    try:
+    # (the omission of negligible limbs always takes the multimodular engine: kept off here)
+    with env(ARBGPU_ENGINE=engine, ARBGPU_OMIT="0"):
         if cplx:
             outs, names = run_cmm(arb, A, B, M, K, N, prec, arb.ALG_BLOCK, trace=True)
         else:
             out, names = run_mm(arb, A, B, M, K, N, prec, arb.ALG_BLOCK, trace=True)
             outs = [out]
-    finally:
-        if old is None:
-            del os.environ["ARBGPU_ENGINE"]
-        else:
-            os.environ["ARBGPU_ENGINE"] = old
     return outs, names
 
 
@@ -511,7 +500,6 @@ def test_basecase_dots_tiled_equal_lane_groups(arb, cplx):
     """The basecase blocks of Algorithm 2 through the tiled dot kernel equal, in every output
     field, the group-of-lanes kernel (ARBGPU_DOT_TILE=0): the tagged index lists, the complex
     combinations and the accumulated blocks as `initial` term."""
-    import os
     from synth.workloads import complex_matmul_laplace
     if cplx:  # tiles of 32 x 32 entries: enough of them to fill the SMs
         case = complex_matmul_laplace(n=448, structured=False)
@@ -521,9 +509,8 @@ def test_basecase_dots_tiled_equal_lane_groups(arb, cplx):
         M, K, N, p = 640, 100, 320, 64
     outs = []
     for tile in ("1", "0"):
-        old = os.environ.get("ARBGPU_DOT_TILE")
-        os.environ["ARBGPU_DOT_TILE"] = tile
-        try:
+        # every input bit kept, so that basecase blocks remain
+        with env(ARBGPU_DOT_TILE=tile, ARBGPU_OMIT="0"):
             if cplx:
                 o, names = run_cmm(arb, A, B, M, K, N, p, arb.ALG_BLOCK, trace=True)
             else:
@@ -531,11 +518,6 @@ def test_basecase_dots_tiled_equal_lane_groups(arb, cplx):
                 o = [o1]
             assert ("dot_tile" in names) == (tile == "1")
             outs.append(o)
-        finally:
-            if old is None:
-                del os.environ["ARBGPU_DOT_TILE"]
-            else:
-                os.environ["ARBGPU_DOT_TILE"] = old
     for a, b in zip(outs[0], outs[1]):
         for f in ("limbs", "exp", "flags", "rad_man", "rad_exp"):
             assert np.array_equal(getattr(a, f), getattr(b, f)), f

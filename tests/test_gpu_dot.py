@@ -296,9 +296,9 @@ def test_matmul_by_dots_p256_sampled(arb):
         assert mismatch(out, int(e), ref) is None
 
 
-@pytest.mark.parametrize("M,K,N,prec,cplx", [(330, 70, 450, 128, False), (170, 129, 400, 256, False),
+@pytest.mark.parametrize("M,K,N,prec,cplx", [(330, 70, 450, 128, False), (200, 129, 400, 256, False),
                                              (90, 40, 700, 512, False), (200, 33, 360, 1024, False),
-                                             (310, 50, 330, 64, True), (400, 17, 80, 192, True)])
+                                             (310, 50, 330, 64, True), (400, 17, 130, 192, True)])
 def test_tiled_matrix_dots_equal_the_lane_group_kernel(arb, M, K, N, prec, cplx):
     """The classical product through the shared-memory tiled dot kernel equals, in every output
     field, the group-of-lanes kernel (ARBGPU_DOT_TILE=0) and the Algorithm 1 restatement."""

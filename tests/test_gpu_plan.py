@@ -17,6 +17,7 @@ from synth import random_balls
 from synth.workloads import complex_matmul_laplace
 from tests.test_gpu_block import (band_case, check_bounds, check_complex, check_entries,
                                   jump_case, run_cmm, run_mm)
+from tests.gpu_util import env
 from tests.test_oracle_alg2 import TALL_PLANS, _greedy_case, _tall_case
 
 pytestmark = pytest.mark.gpu
@@ -73,13 +74,9 @@ def _sample(M, N, count, seed):
 
 @pytest.fixture
 def contiguous():
-    old = os.environ.get("ARBGPU_INNER_ORDER")
-    os.environ["ARBGPU_INNER_ORDER"] = "0"
-    yield
-    if old is None:
-        del os.environ["ARBGPU_INNER_ORDER"]
-    else:
-        os.environ["ARBGPU_INNER_ORDER"] = old
+    """The inner index in its own order, every input bit kept (no negligible-limb omission)."""
+    with env(ARBGPU_INNER_ORDER="0", ARBGPU_OMIT="0"):
+        yield
 
 
 @pytest.mark.parametrize("kind", sorted(TALL_PLANS) + ["jump", "band", "drift", "iid",
@@ -134,13 +131,9 @@ def test_device_plan_of_the_complex_product_by_eq2(arb):
 
 @pytest.fixture
 def ordered():
-    old = os.environ.get("ARBGPU_INNER_ORDER")
-    os.environ["ARBGPU_INNER_ORDER"] = "1"
-    yield
-    if old is None:
-        del os.environ["ARBGPU_INNER_ORDER"]
-    else:
-        os.environ["ARBGPU_INNER_ORDER"] = old
+    """The inner ordering on, every input bit kept (no negligible-limb omission)."""
+    with env(ARBGPU_INNER_ORDER="1", ARBGPU_OMIT="0"):
+        yield
 
 
 def _expected_ordered(A, B, M, K, N, p):
@@ -179,6 +172,11 @@ def test_inner_ordering_is_the_default(arb):
     """Without the environment variable the inner ordering runs for products that need several
     blocks (the structured real product: one full block over the order, exactly rounded)."""
     assert os.environ.get("ARBGPU_INNER_ORDER") is None
+    with env(ARBGPU_OMIT="0"):
+        _inner_ordering_default(arb)
+
+
+def _inner_ordering_default(arb):
     A, B, M, K, N, p = _case("structured")
     want = _expected_ordered(A, B, M, K, N, p)
     out, names = run_mm(arb, A, B, M, K, N, p, arb.ALG_BLOCK, trace=True)
