@@ -121,6 +121,26 @@ class ClockSampler:
 
 IMAD_PER_CLK_PER_SM = 64  # 32-bit integer multiply(-add) issue rate per SM per clock
 SMS = 152
+# the device's measured 32-bit multiply-add rate (arbgpu_calibrate), set once per run
+MEASURED_ALU = {}
+
+
+def measure_alu(ctx):
+    """Run the library's calibration kernels once; their IMAD rate becomes the ALU peak."""
+    try:
+        MEASURED_ALU.update(ctx.calibrate())
+    except Exception as e:  # the derived figure stands in, and the line says so
+        MEASURED_ALU["error"] = str(e)
+    return dict(MEASURED_ALU)
+
+
+def alu_peak_of(sm_mhz):
+    """(peak in T 32-bit multiply-adds/s, where it comes from): the rate arbgpu_calibrate measured
+    on this device, else unit counts x the sampled SM clock."""
+    if MEASURED_ALU.get("imad_tops"):
+        return MEASURED_ALU["imad_tops"], "measured: arbgpu_calibrate mad.lo.u32 rate"
+    return (SMS * IMAD_PER_CLK_PER_SM * sm_mhz * 1e6 / 1e12,
+            f"derived: {SMS} SMs x {IMAD_PER_CLK_PER_SM} IMAD/clk x {sm_mhz:.0f} MHz")
 
 
 def kernel_summary(recs, step_ms_total):
@@ -141,14 +161,13 @@ def roofline_of(name, k, peaks, sm_mhz, limb_n=None):
     per term."""
     avg_s = k["ms_total"] / k["launches"] * 1e-3
     units = k["units"] / k["launches"]
-    alu_peak = SMS * IMAD_PER_CLK_PER_SM * sm_mhz * 1e6 / 1e12
+    alu_peak, alu_source = alu_peak_of(sm_mhz)
     if name in ("dot_fused", "dot_tile") and limb_n:
         achieved = 4 * limb_n * limb_n * units / avg_s / 1e12
         return {"bound": "alu", "kernel": name, "achieved": achieved, "peak": alu_peak,
                 "unit": "T int32-mul/s", "frac": achieved / alu_peak, "traffic": None,
                 "work": f"{units:.4g} terms per launch x {4 * limb_n * limb_n} 32-bit multiplies",
-                "peak_source": f"derived: {SMS} SMs x {IMAD_PER_CLK_PER_SM} IMAD/clk x "
-                               f"{sm_mhz:.0f} MHz"}
+                "peak_source": alu_source}
     if name in ("crt_gemm", "digit_gemm", "digit_gemm_mid", "digit_gemm_rad"):
         achieved = 2.0 * units / avg_s / 1e12
         peak = peaks.get("bf16_tflops", 1900.0)
@@ -167,8 +186,7 @@ def roofline_of(name, k, peaks, sm_mhz, limb_n=None):
         achieved = units / avg_s / 1e12
         return {"bound": "alu", "kernel": name, "achieved": achieved, "peak": alu_peak,
                 "unit": "T int32-mul/s", "frac": achieved / alu_peak, "traffic": None,
-                "peak_source": f"derived: {SMS} SMs x {IMAD_PER_CLK_PER_SM} IMAD/clk x "
-                               f"{sm_mhz:.0f} MHz",
+                "peak_source": alu_source,
                 "work": "CRT sums (block_round) / residue chunks (residues): 32-bit "
                         "multiply-adds per launch"}
     return {"kernel": name, "ms_avg": avg_s * 1e3}
@@ -206,7 +224,7 @@ def dot_roofline(kernels, work, calls, peaks, sm_mhz):
     t_all = t_eval + t_set
     if t_all <= 0:
         return None
-    alu_peak = SMS * IMAD_PER_CLK_PER_SM * sm_mhz * 1e6 / 1e12
+    alu_peak, alu_source = alu_peak_of(sm_mhz)
     hbm_peak = peaks.get("hbm_gbs", 6800.0)
     t_hbm = work["bytes"] / (hbm_peak * 1e9)
     t_alu = work["mults"] / (alu_peak * 1e12)
@@ -224,8 +242,7 @@ def dot_roofline(kernels, work, calls, peaks, sm_mhz):
         base.update({"bound": "alu", "achieved": achieved, "peak": alu_peak,
                      "unit": "T int32-mul/s", "frac": achieved / alu_peak,
                      "mults_per_call": work["mults"],
-                     "peak_source": f"derived: {SMS} SMs x {IMAD_PER_CLK_PER_SM} IMAD/clk x "
-                                    f"{sm_mhz:.0f} MHz"})
+                     "peak_source": alu_source})
     return base
 
 
@@ -355,6 +372,7 @@ def run_workload(args):
     torch.cuda.set_device(0)
     ctx = arb.default_context(0)
     peaks = load_peaks()
+    calibration = measure_alu(ctx)
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     wl = args.workload
     cpu_fn = None
@@ -575,7 +593,8 @@ def run_workload(args):
             "gpu_launches": launches, "roofline": roofline, "kernels": kernels,
             "cpu_baseline": {"value": r / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
                              "sample": sample},
-            "io_bytes": {"in": inbytes, "out": outbytes}, "clocks": clocks}
+            "io_bytes": {"in": inbytes, "out": outbytes}, "clocks": clocks,
+            "calibration": calibration}
     if graph:
         line["us_per_call"] = ms / args.steps * 1e3
         line["graph_replay"] = graph
@@ -638,6 +657,7 @@ def main():
     dev = f"cuda:{local}"
     ctx = arb.default_context(local)
     peaks = load_peaks()
+    calibration = measure_alu(ctx)
     algs = {"auto": arb.ALG_AUTO, "dot": arb.ALG_DOT, "block": arb.ALG_BLOCK}
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
@@ -858,7 +878,8 @@ def main():
                 "gpu_launches": launches, "roofline": roofline, "tensor_core": tensor,
                 "kernels": kernels,
                 "cpu_baseline": cpu,
-                "clocks": clocks, "compare": compare, "peaks_source": peaks["_source"]}
+                "clocks": clocks, "compare": compare, "peaks_source": peaks["_source"],
+                "calibration": calibration}
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()

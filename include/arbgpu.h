@@ -88,6 +88,29 @@ arbgpu_status arbgpu_destroy(arbgpu_ctx *ctx);
  * nothing.  Call it before capturing matrix products in a CUDA graph.  max_prec in [2, 1024]. */
 arbgpu_status arbgpu_reserve(arbgpu_ctx *ctx, int32_t max_prec, int64_t max_inner);
 
+/* Calibration (host-side, synchronous, on the legacy default stream of ctx's device; a few tens
+ * of milliseconds): measured throughput of the arithmetic units the two exact-product carriers of
+ * Section III-D / IV-A would run on, by three micro-kernels of 4 x 256-thread CTAs per SM with
+ * independent dependency chains:
+ *   imad_tops       tera 32-bit multiply-adds per second (mad.lo.u32), the CUDA-core rate that
+ *                   bounds Algorithm 1's limb products;
+ *   imad_wide_tops  tera 32x32+64 -> 64-bit multiply-adds per second (mad.wide.u32);
+ *   mma_s8_tops     tera integer operations per second (2 per multiply-add) of the warp-level
+ *                   8-bit tensor MMA mma.sync m16n8k32 s8.s8.s32 (the tcgen05 8-bit kind is not
+ *                   available on sm_103a), the alternative carrier to the BF16 digit products;
+ *   sm_count, max_clock_mhz  the device's SM count and maximum SM clock.
+ * Allocates and frees a small device buffer and two events.  ARBGPU_ERR_CUDA on any CUDA
+ * failure (the fields are then zero). */
+typedef struct {
+  double imad_tops;
+  double imad_wide_tops;
+  double mma_s8_tops;
+  int32_t sm_count;
+  double max_clock_mhz;
+} arbgpu_calibration;
+
+arbgpu_status arbgpu_calibrate(arbgpu_ctx *ctx, arbgpu_calibration *out);
+
 /* Synchronises `stream`, returns the first device-side error recorded since the previous call
  * (ARBGPU_OK if none) and clears it. */
 arbgpu_status arbgpu_get_status(arbgpu_ctx *ctx, void *stream);

@@ -169,6 +169,15 @@ class Context:
         if rc != 0:
             raise ArbgpuError(rc, "arbgpu_reserve")
 
+    def calibrate(self):
+        """Measured integer and 8-bit tensor throughput of the device (``arbgpu_calibrate``):
+        dict with imad_tops, imad_wide_tops, mma_s8_tops, sm_count, max_clock_mhz."""
+        out = _lib.CCalibration()
+        rc = _lib.lib().arbgpu_calibrate(self.handle, C.byref(out))
+        if rc != 0:
+            raise ArbgpuError(rc, "arbgpu_calibrate")
+        return {k: getattr(out, k) for k, _ in _lib.CCalibration._fields_}
+
     def last_plans(self):
         """The block plans of the last matrix-product call (``arbgpu_last_plans``), one dict per
         real product: kind, h, K, blocks [(start, stop, basecase)], and for kind 1 the inner
