@@ -567,6 +567,10 @@ struct CrtTables {
   const uint16_t *wtab;  // reconstruction on the tensor cores: [NQP][128] BF16 weights
   const float *mbytes;   // [NQ] balanced bytes of M
   int NQ, NQP;
+  // reconstruction on the 8-bit warp-level MMA: [NQ8][K8] balanced bytes of the Q_t
+  const int8_t *w8 = nullptr;
+  int K8 = 0, NQ8 = 0;
+  const uint32_t *c32 = nullptr;  // [2 NMW + 2] words of 32896 sum_t Q_t
 };
 
 // One exact integer product.  kind 0: digit + carry form of T itself.  kind 1 (multimodular): for
@@ -624,7 +628,7 @@ __device__ int crt_assemble(const IntProduct &p, int64_t i, int64_t j, int64_t M
       const uint32_t *row = c.Q32 + (int64_t)t * c.NW32P;
 #pragma unroll
       for (int u = 0; u < 16; ++u)
-        if (l0 + u < c.NW32P) acc[u] += z * __ldg(row + l0 + u);
+        if (l0 + u < c.NW32P) mad_wide(acc[u], (uint32_t)z, __ldg(row + l0 + u));
     }
 #pragma unroll
     for (int u = 0; u < 16; u += 2) {
@@ -837,6 +841,7 @@ static void launch_residues(int nch, int64_t n, cudaStream_t s, const BallsView 
   else if (nch <= 18) ARB_RES(18, 1);
   else if (nch <= 24) ARB_RES(24, 1);
   else if (nch <= 34) ARB_RES(34, 1);
+  else if (nch <= 40) ARB_RES(40, 1);
   else ARB_RES(CRT_MAX_CHUNKS32, 1);
 #undef ARB_RES
 }
@@ -1949,6 +1954,384 @@ __global__ void __launch_bounds__(128, 6) block_round_regs_kernel(const RoundArg
   round_store_regs<NW>(T, sigma, 0, rad, a.prec, a.C, i * a.ldc + j);
 }
 
+// ------------------------------------------------------------------------- wide epilogue
+//
+// The epilogue for products too long for the register kernels (p >= 512: T of 20 to 48 limbs),
+// one entry per thread on the CUDA cores.  The multimodular engine's Chinese-remainder sum
+// T = sum_t z_t Q_t - q M is formed sixteen 32-bit words at a time in 64-bit register
+// accumulators, every thread of the CTA reading the same row of Q from shared memory (a
+// broadcast) for its own z_t; the limbs of T go to shared memory, limb-major ([k][thread], so a
+// warp's accesses are conflict-free); the rounding then reads only the NWIN limbs at the top of
+// |T| plus a sticky bit, as round_store_window does in registers.
+constexpr int RW_ROWS = 128;  // entries (threads) per CTA
+
+// Shared-memory bytes of the wide epilogue: the Q rows and M padded to L32P words, 1 / m_t, and
+// the limbs of T.
+__host__ __device__ inline int rw_l32p(int nw) { return (2 * nw + 15) / 16 * 16; }
+static size_t rw_smem_bytes(const IntProduct &p, int nw) {
+  size_t b = (size_t)nw * RW_ROWS * 8;
+  if (p.kind == 1) b += ((size_t)p.crt.NM + 1) * rw_l32p(nw) * 4 + (size_t)p.crt.NM * 4;
+  return b;
+}
+
+// Round T (two's complement, nw limbs at sT[k RS]) times 2^sigma to p bits and store it into
+// entry oi of C with radius >= |rounded - T 2^sigma| + rad; prec + 66 <= 64 NWIN.  T is clobbered
+// (replaced by |T|).
+template <int NWIN, int RS = RW_ROWS>
+__device__ __forceinline__ void round_store_smem(uint64_t *sT, int nw, int64_t sigma, Mag rad,
+                                                 int prec, const BallsOut &C, int64_t oi) {
+  const bool neg = (sT[(nw - 1) * RS] >> 63) != 0;
+  int top = -1;
+  {
+    const uint64_t flip = neg ? ~(uint64_t)0 : 0;
+    u128 cc = neg ? 1 : 0;
+    for (int k = 0; k < nw; ++k) {
+      cc += (u128)(sT[k * RS] ^ flip);
+      const uint64_t v = (uint64_t)cc;
+      cc >>= 64;
+      sT[k * RS] = v;
+      if (v) top = k;
+    }
+  }
+  uint64_t ta[NWIN + 1];
+  if (top < 0) {
+#pragma unroll
+    for (int k = 0; k <= NWIN; ++k) ta[k] = 0;
+    store_rounded<NWIN + 1, 1>(C, oi, 0, true, neg, ta, sigma, rad);
+    return;
+  }
+  const int L = 64 * top + bitlen64(sT[top * RS]);
+  uint64_t w[NWIN];
+  int sh = L - 64 * NWIN;  // the window is |T| >> sh (sh <= 0: all of |T|)
+  bool sticky = false;
+  if (sh <= 0) {
+    sh = 0;
+#pragma unroll
+    for (int k = 0; k < NWIN; ++k) w[k] = k <= top ? sT[k * RS] : 0;
+  } else {
+    const int q = sh >> 6, r = sh & 63;  // q + NWIN - 1 <= top
+    for (int k = 0; k < q; ++k) sticky |= sT[k * RS] != 0;
+    sticky |= (sT[q * RS] & ((((uint64_t)1) << r) - 1)) != 0;
+#pragma unroll
+    for (int k = 0; k < NWIN; ++k) {
+      const uint64_t lo = sT[(q + k) * RS];
+      const uint64_t hi = q + k + 1 <= top ? sT[(q + k + 1) * RS] : 0;
+      w[k] = r ? ((lo >> r) | (hi << (64 - r))) : lo;
+    }
+    w[0] |= sticky ? 1u : 0u;
+  }
+  int LW = L - sh;
+  Mag r1{0u, 0};
+  round_abs_regs<NWIN>(w, LW, prec, sticky ? 1u : 0u, sigma + sh, ta, r1);
+  store_rounded<NWIN + 1, 1>(C, oi, 0, false, neg, ta, sigma + sh + LW, mag_add_up(r1, rad));
+}
+
+template <int NWIN>
+__global__ void __launch_bounds__(RW_ROWS) block_round_wide_kernel(const RoundArgs a, int nw) {
+  extern __shared__ uint4 smem_u4[];
+  uint64_t *sT = (uint64_t *)smem_u4 + threadIdx.x;  // limb k at sT[k RW_ROWS]
+  const int L32P = rw_l32p(nw);
+  uint32_t *sQ = (uint32_t *)((uint64_t *)smem_u4 + (size_t)nw * RW_ROWS);
+  const IntProduct &p = a.mid;
+  if (p.kind == 1) {
+    const CrtTables &c = p.crt;
+    for (int k = threadIdx.x; k < (c.NM + 1) * L32P; k += blockDim.x) {
+      const int t = k / L32P, l = k - t * L32P;
+      const uint32_t *src = t < c.NM ? c.Q32 + (int64_t)t * c.NW32P : c.M32;
+      sQ[k] = l < c.NW32P ? __ldg(src + l) : 0u;
+    }
+    float *sr = (float *)(sQ + (size_t)(c.NM + 1) * L32P);
+    for (int k = threadIdx.x; k < c.NM; k += blockDim.x) sr[k] = __ldg(c.rinv + k);
+    __syncthreads();
+  }
+  pdl_wait();  // the block products come from the GEMM kernel before this one
+  const int64_t idx = (int64_t)blockIdx.x * RW_ROWS + threadIdx.x;
+  if (idx >= a.M * a.N) return;
+  const int64_t i = idx / a.N, j = idx - i * a.N;
+  const int64_t pl = a.Mp * a.Np, o = i * a.Np + j;
+  if (p.kind == 1) {
+    // T = sum_t z_t Q_t - q M, q = rint(sum_t z_t / m_t)
+    const CrtTables &c = p.crt;
+    const int NM = c.NM;
+    const uint32_t *sM = sQ + (size_t)NM * L32P;
+    const float *sr = (const float *)(sM + L32P);
+    const uint16_t *zp = (const uint16_t *)p.digits + o;
+    float qs = 0.f;
+    for (int t = 0; t < NM; ++t) qs = fmaf((float)__ldg(zp + (int64_t)t * pl), sr[t], qs);
+    const int64_t q = (int64_t)rintf(qs);
+    int64_t carry = 0;
+    for (int l0 = 0; l0 < 2 * nw; l0 += 16) {
+      uint64_t acc[16];
+#pragma unroll
+      for (int u = 0; u < 16; ++u) acc[u] = 0;
+      const uint4 *qrow = (const uint4 *)(sQ + l0);
+      for (int t0 = 0; t0 < NM; t0 += 8) {
+        // the residues of eight moduli are requested together
+        uint32_t zb[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) zb[u] = t0 + u < NM ? __ldg(zp + (int64_t)(t0 + u) * pl) : 0u;
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          if (t0 + u >= NM) break;
+          const uint32_t z = zb[u];
+          const uint4 *w4 = qrow + (size_t)(t0 + u) * (L32P / 4);
+#pragma unroll
+          for (int q4 = 0; q4 < 4; ++q4) {
+            const uint4 w = w4[q4];
+            mad_wide(acc[4 * q4 + 0], z, w.x);
+            mad_wide(acc[4 * q4 + 1], z, w.y);
+            mad_wide(acc[4 * q4 + 2], z, w.z);
+            mad_wide(acc[4 * q4 + 3], z, w.w);
+          }
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < 16; u += 2) {
+        const int l = l0 + u;
+        const int64_t v0 = (int64_t)acc[u] - q * (int64_t)sM[l] + carry;
+        carry = v0 >> 32;
+        const int64_t v1 = (int64_t)acc[u + 1] - q * (int64_t)sM[l + 1] + carry;
+        carry = v1 >> 32;
+        if ((l >> 1) < nw)
+          sT[(l >> 1) * RW_ROWS] = (uint64_t)(uint32_t)v0 | ((uint64_t)(uint32_t)v1 << 32);
+      }
+    }
+  } else {
+    // T from its digits (eight per limb) and the carries of the digit groups
+    const uint8_t *dp = p.digits + o;
+    for (int k = 0; k < nw; ++k) {
+      uint64_t w = 0;
+#pragma unroll
+      for (int b = 0; b < 8; ++b)
+        if (8 * k + b < p.ND) w |= (uint64_t)__ldg(dp + (int64_t)(8 * k + b) * pl) << (8 * b);
+      sT[k * RW_ROWS] = w;
+    }
+    for (int g = 0; g < p.groups; ++g) {
+      const int64_t cg = __ldg(p.carries + ((int64_t)g * a.Mp + i) * a.Np + j);
+      if (cg == 0) continue;
+      const int pos = 8 * p.ends.e[g];
+      const int li = pos >> 6, bi = pos & 63;
+      const uint64_t lo = (uint64_t)cg << bi;
+      const uint64_t hi = bi ? (uint64_t)(cg >> (64 - bi)) : (uint64_t)(cg < 0 ? -1 : 0);
+      const uint64_t ext = cg < 0 ? ~(uint64_t)0 : 0;
+      u128 s = 0;
+      for (int k = li; k < nw; ++k) {
+        const uint64_t add = k == li ? lo : (k == li + 1 ? hi : ext);
+        s += (u128)sT[k * RW_ROWS] + add;
+        sT[k * RW_ROWS] = (uint64_t)s;
+        s >>= 64;
+      }
+    }
+  }
+  const bool rowz = a.rtop[i] == INT64_MIN, colz = a.ctop[j] == INT64_MIN;
+  const int64_t sigma = (rowz ? 0 : a.rbot[i]) + (colz ? 0 : a.cbot[j]);  // T * 2^sigma
+  const Mag rad = with_extra_radius(
+      a, i, j, block_radius_regs(a.rp1, a.rp2, a.rtop, a.rrad, a.crad, a.cplus, i, j, a.Mp, a.Np));
+  round_store_smem<NWIN>(sT, nw, sigma, rad, a.prec, a.C, i * a.ldc + j);
+}
+
+// ------------------------------------------------------------------------- MMA epilogue
+//
+// The Chinese-remainder sum of the multimodular engine on the 8-bit warp-level MMA
+// (mma.sync m16n8k32, signed bytes into s32), for products beyond the TMEM epilogue (more than
+// 64 moduli or 16 limbs).  With z_t = l_t + 256 h_t (bytes l, h), l' = l - 128, h' = h - 128 and
+// Q_t = sum_n q_{t,n} 256^n (balanced bytes),
+//
+//     sum_t z_t Q_t = sum_n 256^n S_n + 32896 sum_t Q_t,   S_n = sum_t (l'_t q_{t,n} + h'_t q_{t,n-1}),
+//
+// S the product of the signed byte matrix [entries][2 NM] and the table w8 [2 NM][NQ]; |S_n| <=
+// 2 NM 128 128 < 2^31, so the s32 sums are exact.  A warp takes 32 entries (two row tiles of 16) and the
+// columns 32 at a time; the sums pass through shared memory to the lane of their entry, which
+// carries them into the 32-bit words of T = sum_n 256^n S_n - q M (q = rint(sum_t z_t / m_t), as
+// in crt_assemble).  The limbs of T go to shared memory and round_store_smem rounds them.
+constexpr int RM_MAX_KS = 12;  // k-steps of 32 bytes: NM <= 192
+
+__device__ __forceinline__ void mma_s8s8(int32_t (&d)[4], const uint32_t (&a)[4], uint32_t b0,
+                                         uint32_t b1) {
+  asm("mma.sync.aligned.m16n8k32.row.col.s32.s8.s8.s32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, "
+      "{%8, %9}, {%0, %1, %2, %3};"
+      : "+r"(d[0]), "+r"(d[1]), "+r"(d[2]), "+r"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+// Shared-memory bytes of the MMA epilogue with `warps` warps: the limbs of T, the column staging,
+// M and the offset term in 32-bit words, 1 / m_t and the byte table (rows padded by 16 bytes).
+static size_t rm_smem_bytes(const CrtTables &c, int nw, int warps) {
+  const size_t rows = 32 * (size_t)warps;
+  return (size_t)nw * rows * 8 + (size_t)warps * 32 * 33 * 4 + (size_t)(2 * nw + 3) / 4 * 32 +
+         (size_t)(c.NM + 3) / 4 * 16 + (size_t)c.NQ8 * (c.K8 + 16);
+}
+
+template <int NWIN, int WARPS, int KSM>
+__global__ void __launch_bounds__(32 * WARPS) crt_round_mma_kernel(const RoundArgs a, int nw) {
+  constexpr int ROWS = 32 * WARPS;
+  extern __shared__ uint4 smem_u4[];
+  const CrtTables &c = a.mid.crt;
+  const int NM = c.NM, KS = c.K8 / 32, WS = c.K8 + 16, L32 = 2 * nw;
+  uint64_t *sT = (uint64_t *)smem_u4;                                  // [nw][ROWS]
+  int32_t *sC = (int32_t *)(sT + (size_t)nw * ROWS);                     // [WARPS][32][33]
+  uint32_t *sM = (uint32_t *)(sC + WARPS * 32 * 33);                     // [L32] words of M
+  uint32_t *sO = sM + (L32 + 3) / 4 * 4;                                 // [L32] offset term
+  float *sr = (float *)(sO + (L32 + 3) / 4 * 4);                         // [NM] 1 / m_t
+  uint8_t *sW = (uint8_t *)(sr + (NM + 3) / 4 * 4);                      // [NQ8][WS] bytes
+  for (int q = threadIdx.x; q < L32; q += blockDim.x) {
+    sM[q] = q < c.NW32P ? __ldg(c.M32 + q) : 0u;
+    sO[q] = __ldg(c.c32 + q);  // (2 NMW + 2 = L32 words)
+  }
+  for (int q = threadIdx.x; q < NM; q += blockDim.x) sr[q] = __ldg(c.rinv + q);
+  {
+    const int c16 = c.K8 / 16;
+    for (int q = threadIdx.x; q < c.NQ8 * c16; q += blockDim.x) {
+      const int n = q / c16, u = q - n * c16;
+      *(uint4 *)(sW + (size_t)n * WS + 16 * u) = __ldg((const uint4 *)(c.w8 + (size_t)n * c.K8) + u);
+    }
+  }
+  __syncthreads();
+  pdl_wait();  // the residues z come from the GEMM kernel before this one
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, tig = lane & 3;
+  const int64_t MN = a.M * a.N, pl = a.Mp * a.Np, ntile = (MN + 31) / 32;
+  const uint16_t *zbase = (const uint16_t *)a.mid.digits;
+  auto z_off = [&](int64_t e) -> int64_t {  // offset of entry e in a residue plane, -1 past MN
+    if (e >= MN) return -1;
+    const int64_t i = e / a.N;
+    return i * a.Np + (e - i * a.N);
+  };
+  int32_t *sCw = sC + warp * 32 * 33;
+  uint32_t *sT32 = (uint32_t *)(sT + threadIdx.x);  // word w of T at sT32[(w >> 1) 2 ROWS + (w & 1)]
+  const int nchunks = c.NQ8 / 32;
+  // persistent: every warp takes tiles of 32 consecutive entries, a grid's warps apart
+  for (int64_t tile = (int64_t)blockIdx.x * WARPS + warp; tile < ntile;
+       tile += (int64_t)gridDim.x * WARPS) {
+    const int64_t e0 = 32 * tile;
+    // A fragments of the tile's two row tiles for every k-step: register r of row tile mt holds
+    // the bytes of z_t, z_(t+1) (t = 16 ks + 8 (r >> 1) + 2 tig) of row 16 mt + g + 8 (r & 1)
+    uint32_t af[KSM][2][4];
+    {
+      int64_t orow[2][2];
+#pragma unroll
+      for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+        for (int h = 0; h < 2; ++h) orow[mt][h] = z_off(e0 + 16 * mt + 8 * h + g);
+#pragma unroll
+      for (int ks = 0; ks < KSM; ++ks)
+#pragma unroll
+        for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+          for (int r = 0; r < 4; ++r) {
+            uint32_t v = 0;
+            const int t = 16 * ks + 8 * (r >> 1) + 2 * tig;
+            const int64_t o = orow[mt][r & 1];
+            if (ks < KS && o >= 0) {
+              if (t < NM) v = __ldg(zbase + (int64_t)t * pl + o);
+              if (t + 1 < NM) v |= (uint32_t)__ldg(zbase + (int64_t)(t + 1) * pl + o) << 16;
+            }
+            af[ks][mt][r] = v;
+          }
+    }
+    // q = rint(sum_t z_t / m_t) of the lane's entry (row `lane` of the tile): partial sums over
+    // this lane's moduli for its four rows, summed over the four lanes of its group (the same
+    // value in each), then fetched from the group that holds the row
+    float qp[2][2] = {{0.f, 0.f}, {0.f, 0.f}};
+#pragma unroll
+    for (int ks = 0; ks < KSM; ++ks)
+#pragma unroll
+      for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+          const int t = 16 * ks + 8 * (r >> 1) + 2 * tig;
+          if (ks < KS && t < NM) {
+            const uint32_t v = af[ks][mt][r];
+            float s = qp[mt][r & 1];
+            s = fmaf((float)(v & 0xFFFFu), sr[t], s);
+            if (t + 1 < NM) s = fmaf((float)(v >> 16), sr[t + 1], s);
+            qp[mt][r & 1] = s;
+          }
+        }
+    float qs = 0.f;
+#pragma unroll
+    for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        float v = qp[mt][h];
+        v += __shfl_xor_sync(0xffffffffu, v, 1);
+        v += __shfl_xor_sync(0xffffffffu, v, 2);
+        v = __shfl_sync(0xffffffffu, v, 4 * (lane & 7));
+        if ((lane >> 4) == mt && ((lane >> 3) & 1) == h) qs = v;
+      }
+    const int64_t q = (int64_t)rintf(qs);
+    // the bytes as signed bytes offset by -128
+#pragma unroll
+    for (int ks = 0; ks < KSM; ++ks)
+#pragma unroll
+      for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+        for (int r = 0; r < 4; ++r) af[ks][mt][r] ^= 0x80808080u;
+    int64_t carry = 0;
+    for (int nc = 0; nc < nchunks; ++nc) {
+      int32_t acc[2][4][4];
+#pragma unroll
+      for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+        for (int nt = 0; nt < 4; ++nt)
+#pragma unroll
+          for (int r = 0; r < 4; ++r) acc[mt][nt][r] = 0;
+#pragma unroll
+      for (int ks = 0; ks < KSM; ++ks) {
+        if (ks < KS) {
+#pragma unroll
+          for (int nt = 0; nt < 4; ++nt) {
+            const uint8_t *wrow = sW + (size_t)(32 * nc + 8 * nt + g) * WS + 32 * ks + 4 * tig;
+            const uint32_t b0 = *(const uint32_t *)wrow, b1 = *(const uint32_t *)(wrow + 16);
+            mma_s8s8(acc[0][nt], af[ks][0], b0, b1);
+            mma_s8s8(acc[1][nt], af[ks][1], b0, b1);
+          }
+        }
+      }
+      // column sums of rows 16 mt + g (+ 8) to the staging rows, then each lane carries its row
+#pragma unroll
+      for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+        for (int nt = 0; nt < 4; ++nt) {
+          int32_t *r0 = sCw + (16 * mt + g) * 33 + 8 * nt + 2 * tig;
+          r0[0] = acc[mt][nt][0];
+          r0[1] = acc[mt][nt][1];
+          r0[8 * 33] = acc[mt][nt][2];
+          r0[8 * 33 + 1] = acc[mt][nt][3];
+        }
+      __syncwarp();
+      const int32_t *mine = sCw + lane * 33;
+#pragma unroll
+      for (int wq = 0; wq < 8; ++wq) {
+        const int w = 8 * nc + wq;
+        const int64_t v = (int64_t)mine[4 * wq] + (int64_t)mine[4 * wq + 1] * 256 +
+                          (int64_t)mine[4 * wq + 2] * 65536 +
+                          (int64_t)mine[4 * wq + 3] * 16777216 + carry +
+                          (w < L32 ? (int64_t)sO[w] - q * (int64_t)sM[w] : 0);
+        carry = v >> 32;
+        if (w < L32) sT32[(size_t)(w >> 1) * 2 * ROWS + (w & 1)] = (uint32_t)v;
+      }
+      __syncwarp();
+    }
+    for (int w = 8 * nchunks; w < L32; ++w) {  // words past the table's columns: M's and the sign
+      const int64_t v = carry + (int64_t)sO[w] - q * (int64_t)sM[w];
+      carry = v >> 32;
+      sT32[(size_t)(w >> 1) * 2 * ROWS + (w & 1)] = (uint32_t)v;
+    }
+    const int64_t e = e0 + lane;
+    if (e < MN) {
+      const int64_t i = e / a.N, j = e - i * a.N;
+      const bool rowz = a.rtop[i] == INT64_MIN, colz = a.ctop[j] == INT64_MIN;
+      const int64_t sigma = (rowz ? 0 : a.rbot[i]) + (colz ? 0 : a.cbot[j]);  // T * 2^sigma
+      const Mag rad = with_extra_radius(a, i, j,
+                                        block_radius_regs(a.rp1, a.rp2, a.rtop, a.rrad, a.crad,
+                                                          a.cplus, i, j, a.Mp, a.Np));
+      round_store_smem<NWIN, ROWS>(sT + threadIdx.x, nw, sigma, rad, a.prec, a.C,
+                                   i * a.ldc + j);
+    }
+    __syncwarp();
+  }
+}
+
 // Limbs of the assembled product of `p` (two's complement, including the sign).
 static int product_limbs(const IntProduct &p) {
   return p.kind == 1 ? p.crt.NMW + 1 : (8 * p.ND + 32 + 63) / 64 + 1;
@@ -2279,8 +2662,93 @@ static bool launch_crt_round_tc(arbgpu_ctx *ctx, const RoundArgs &ra, cudaStream
   return true;
 }
 
+// The wide epilogue with the smallest rounding window that holds prec + 66 bits; false when the
+// product or the precision is beyond it (ARBGPU_ROUND_WIDE=0 also declines).
+static bool launch_block_round_wide(arbgpu_ctx *ctx, const RoundArgs &ra, int nw, unsigned blocks,
+                                    cudaStream_t s) {
+  const char *e = getenv("ARBGPU_ROUND_WIDE");
+  if ((e && !strcmp(e, "0")) || ra.mid.kind > 1 || nw < 1 || nw > RD_MAXW) return false;
+  const size_t smem = rw_smem_bytes(ra.mid, nw);
+  if (smem > RT_SMEM_MAX) return false;
+  const int dev = ctx->device & 255;
+#define ARB_RW(NWIN_)                                                                         \
+  do {                                                                                        \
+    static bool attr_done[256] = {};                                                          \
+    if (!attr_done[dev]) {                                                                    \
+      if (cudaFuncSetAttribute(block_round_wide_kernel<NWIN_>,                                \
+                               cudaFuncAttributeMaxDynamicSharedMemorySize,                   \
+                               (int)RT_SMEM_MAX) != cudaSuccess)                              \
+        return false;                                                                         \
+      attr_done[dev] = true;                                                                  \
+    }                                                                                         \
+    launch_pdl(block_round_wide_kernel<NWIN_>, dim3(blocks), dim3(RW_ROWS), smem, s, ra, nw); \
+  } while (0)
+  if (ra.prec + 66 <= 64 * 6)
+    ARB_RW(6);
+  else if (ra.prec + 66 <= 64 * 10)
+    ARB_RW(10);
+  else if (ra.prec + 66 <= 64 * 18)
+    ARB_RW(18);
+  else
+    return false;
+#undef ARB_RW
+  return true;
+}
+
+// The MMA epilogue (multimodular products): persistent CTAs of eight warps, one per SM, the
+// fragment set sized for at most 6 or 12 k-steps; false when the product or its tables are beyond
+// it (ARBGPU_ROUND_MMA=0 also declines).
+static bool launch_crt_round_mma(arbgpu_ctx *ctx, const RoundArgs &ra, int nw, cudaStream_t s) {
+  const char *e = getenv("ARBGPU_ROUND_MMA");
+  if (e && !strcmp(e, "0")) return false;
+  const CrtTables &c = ra.mid.crt;
+  if (ra.mid.kind != 1 || !c.w8 || !c.c32 || c.K8 < 32 || c.K8 > 32 * RM_MAX_KS || c.NQ8 < 32 || nw < 1 ||
+      nw > RD_MAXW)
+    return false;
+  constexpr int W = 8;
+  const size_t smem = rm_smem_bytes(c, nw, W);
+  if (smem > RT_SMEM_MAX) return false;
+  const int64_t ntile = (ra.M * ra.N + 31) / 32;
+  const bool small = c.K8 <= 32 * 6;
+  int64_t grid = (ntile + W - 1) / W;
+  if (grid > (int64_t)ctx->sm_count) grid = ctx->sm_count;
+  if (grid < 1) return true;
+  const int dev = ctx->device & 255;
+#define ARB_RM(NWIN_, KSM_)                                                                   \
+  do {                                                                                        \
+    static bool attr_done[256] = {};                                                          \
+    if (!attr_done[dev]) {                                                                    \
+      if (cudaFuncSetAttribute(crt_round_mma_kernel<NWIN_, W, KSM_>,                          \
+                               cudaFuncAttributeMaxDynamicSharedMemorySize,                   \
+                               (int)RT_SMEM_MAX) != cudaSuccess)                              \
+        return false;                                                                         \
+      attr_done[dev] = true;                                                                  \
+    }                                                                                         \
+    launch_pdl(crt_round_mma_kernel<NWIN_, W, KSM_>, dim3((unsigned)grid), dim3(32 * W), smem, \
+               s, ra, nw);                                                                    \
+  } while (0)
+#define ARB_RM_K(NWIN_)  \
+  do {                   \
+    if (small)           \
+      ARB_RM(NWIN_, 6);  \
+    else                 \
+      ARB_RM(NWIN_, 12); \
+  } while (0)
+  if (ra.prec + 66 <= 64 * 6)
+    ARB_RM_K(6);
+  else if (ra.prec + 66 <= 64 * 10)
+    ARB_RM_K(10);
+  else if (ra.prec + 66 <= 64 * 18)
+    ARB_RM_K(18);
+  else
+    return false;
+#undef ARB_RM_K
+#undef ARB_RM
+  return true;
+}
+
 // The rounding epilogue of one block: the register kernel of the smallest size that holds the
-// product, else the general one.
+// product, else the MMA kernel, else the wide kernel, else the general one.
 static void launch_block_round(arbgpu_ctx *ctx, const RoundArgs &ra, cudaStream_t s) {
   arbgpu_status tc_st;
   if (launch_crt_round_tc(ctx, ra, s, &tc_st)) return;  // (launch errors surface at the caller)
@@ -2295,7 +2763,8 @@ static void launch_block_round(arbgpu_ctx *ctx, const RoundArgs &ra, cudaStream_
   else if (crt_smem_bytes(ra.mid, 16) <= 48 * 1024 && ra.prec < 64 * 16 && nw <= 16)
     launch_pdl(block_round_regs_kernel<16>, dim3(blocks), dim3(128), crt_smem_bytes(ra.mid, 16),
                s, ra);
-  else
+  else if (!launch_crt_round_mma(ctx, ra, nw, s) &&
+           !launch_block_round_wide(ctx, ra, nw, blocks, s))
     block_round_kernel<<<blocks, 128, 0, s>>>(ra);
 }
 
@@ -3162,6 +3631,10 @@ static arbgpu_status run_block(arbgpu_ctx *ctx, const BlockWs &w, uint8_t *ws, c
     CrtTables ct{dt.Q32,         dt.M32,     dt.y,      dt.rinv,  plan->NM, plan->NMW,
                  plan->NW32P,    dt.crt_wtab, dt.mbytes, plan->NQ, plan->NQP};
     if (plan->NM > 64) ct.wtab = nullptr;  // (the table is built for NM <= 64 only)
+    ct.w8 = dt.w8;
+    ct.K8 = plan->K8;
+    ct.NQ8 = plan->NQ8;
+    ct.c32 = dt.c32;
     __nv_bfloat16 *resA = (__nv_bfloat16 *)(ws + w.resA), *resB = (__nv_bfloat16 *)(ws + w.resB);
     // with radii, the two radius products ride in the same GEMM as items NM and NM + 1: their
     // operand planes follow the residue planes, and their exact values come out as int64
@@ -3727,7 +4200,9 @@ static arbgpu_status run_3m(arbgpu_ctx *ctx, const BlockWs &w, uint8_t *ws, cons
   // (the tensor-core reconstruction's weight table exists for NM <= 64)
   const CrtTables ct{dt.Q32,        dt.M32,                      dt.y,      dt.rinv,
                      NM,            p.plan->NMW,                 p.plan->NW32P,
-                     NM <= 64 ? dt.crt_wtab : nullptr, dt.mbytes, p.plan->NQ, p.plan->NQP};
+                     NM <= 64 ? dt.crt_wtab : nullptr, dt.mbytes, p.plan->NQ, p.plan->NQP,
+                     dt.w8,         p.plan->K8,                  p.plan->NQ8,
+                     dt.c32};
   // residue planes [re | im | re + im] of each side, 2 NM planes each
   __nv_bfloat16 *xr = (__nv_bfloat16 *)(ws + w.r3A), *yr = (__nv_bfloat16 *)(ws + w.r3B);
   const size_t setA = (size_t)2 * NM * M * Kp, setB = (size_t)2 * NM * N * Kp;

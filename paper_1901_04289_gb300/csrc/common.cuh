@@ -83,6 +83,11 @@ __device__ __forceinline__ uint64_t shl_funnel(uint64_t hi, uint64_t lo, int b) 
 
 __device__ __forceinline__ int bitlen64(uint64_t v) { return v ? 64 - __clzll((long long)v) : 0; }
 
+// acc += a * b for 32-bit a, b and a 64-bit acc, as one widening multiply-add (mad.wide.u32).
+__device__ __forceinline__ void mad_wide(uint64_t &acc, uint32_t a, uint32_t b) {
+  asm("mad.wide.u32 %0, %1, %2, %0;" : "+l"(acc) : "r"(a), "r"(b));
+}
+
 // 30-bit radius value man * 2^(exp - 30), man = 0 (zero) or 2^29 <= man < 2^30.
 struct Mag {
   uint32_t man;

@@ -177,22 +177,47 @@ std::unique_ptr<CrtPlan> build_plan(int NM) {
       u += 0x7FFFu + ((u >> 16) & 1u);
       return (uint16_t)(u >> 16);
     };
-    if (NM <= 64) {
-      for (int t = 0; t < NM; ++t) {
-        std::vector<uint64_t> Q(P->NMW, 0);
-        for (int k = 0; k < P->NMW; ++k)
-          Q[k] = (uint64_t)P->Q32[(size_t)t * P->NW32P + 2 * k] |
-                 ((uint64_t)P->Q32[(size_t)t * P->NW32P + 2 * k + 1] << 32);
-        const std::vector<int> qb = balanced_bytes(Q, NB);
-        for (int n = 0; n < P->NQ; ++n) {
-          const int lo = n < NB ? qb[n] : 0, hi = (n >= 1 && n - 1 < NB) ? qb[n - 1] : 0;
+    // the same bytes as 8-bit integers for the warp-level MMA reconstruction (every NM): row n
+    // of w8 [NQ8][K8] holds byte n of Q_t in column 2t and byte n - 1 in column 2t + 1
+    P->K8 = (2 * NM + 31) / 32 * 32;
+    P->NQ8 = (P->NQ + 31) / 32 * 32;
+    P->w8.assign((size_t)P->NQ8 * P->K8, 0);
+    // the z bytes enter the MMA offset by -128 (signed): c32 = 32896 sum_t Q_t puts them back
+    std::vector<uint64_t> qsum(P->NMW + 1, 0);
+    for (int t = 0; t < NM; ++t) {
+      std::vector<uint64_t> Q(P->NMW, 0);
+      for (int k = 0; k < P->NMW; ++k)
+        Q[k] = (uint64_t)P->Q32[(size_t)t * P->NW32P + 2 * k] |
+               ((uint64_t)P->Q32[(size_t)t * P->NW32P + 2 * k + 1] << 32);
+      u128 cq = 0;
+      for (int k = 0; k <= P->NMW; ++k) {
+        cq += (u128)qsum[k] + (k < P->NMW ? Q[k] : 0);
+        qsum[k] = (uint64_t)cq;
+        cq >>= 64;
+      }
+      const std::vector<int> qb = balanced_bytes(Q, NB);
+      for (int n = 0; n < P->NQ; ++n) {
+        const int lo = n < NB ? qb[n] : 0, hi = (n >= 1 && n - 1 < NB) ? qb[n - 1] : 0;
+        P->w8[(size_t)n * P->K8 + 2 * t] = (int8_t)lo;
+        P->w8[(size_t)n * P->K8 + 2 * t + 1] = (int8_t)hi;
+        if (NM <= 64) {
           P->crt_wtab[(size_t)n * 128 + 2 * t] = bf16_of((float)lo);
           P->crt_wtab[(size_t)n * 128 + 2 * t + 1] = bf16_of((float)hi);
         }
+      }
+      if (NM <= 64) {
         P->crt_wtab[(size_t)P->NQ * 128 + 2 * t] = bf16_of((float)(1.0 / (double)P->mods[t]));
         P->crt_wtab[(size_t)P->NQ * 128 + 2 * t + 1] =
             bf16_of((float)(256.0 / (double)P->mods[t]));
       }
+    }
+    mul_small(qsum, 32896u);
+    P->c32.assign((size_t)2 * P->NMW + 2, 0);
+    for (int k = 0; k < (int)qsum.size() && 2 * k + 1 < (int)P->c32.size(); ++k) {
+      P->c32[2 * k] = (uint32_t)qsum[k];
+      P->c32[2 * k + 1] = (uint32_t)(qsum[k] >> 32);
+    }
+    if (NM <= 64) {
       const std::vector<int> mb = balanced_bytes(P->M, NB);
       for (int n = 0; n < NB; ++n) P->mbytes[n] = (float)mb[n];
     }
@@ -220,7 +245,9 @@ arbgpu_status crt_device_tables(arbgpu_ctx *ctx, const CrtPlan *P, CrtDevTables 
   const size_t ow = oi + al(8 * P->inv.size());
   const size_t ocw = ow + al(2 * P->wtab.size());
   const size_t omb = ocw + al(2 * P->crt_wtab.size());
-  const size_t total = omb + al(4 * P->mbytes.size());
+  const size_t ow8 = omb + al(4 * P->mbytes.size());
+  const size_t oc32 = ow8 + al(P->w8.size());
+  const size_t total = oc32 + al(4 * P->c32.size());
   auto it = ctx->crt_tables.find(P->NM);
   uint8_t *base = nullptr;
   if (it != ctx->crt_tables.end()) {
@@ -238,6 +265,8 @@ arbgpu_status crt_device_tables(arbgpu_ctx *ctx, const CrtPlan *P, CrtDevTables 
     memcpy(h.data() + ow, P->wtab.data(), 2 * P->wtab.size());
     memcpy(h.data() + ocw, P->crt_wtab.data(), 2 * P->crt_wtab.size());
     memcpy(h.data() + omb, P->mbytes.data(), 4 * P->mbytes.size());
+    memcpy(h.data() + ow8, P->w8.data(), P->w8.size());
+    memcpy(h.data() + oc32, P->c32.data(), 4 * P->c32.size());
     if (cudaMemcpy(base, h.data(), total, cudaMemcpyHostToDevice) != cudaSuccess) {
       cudaFree(base);
       return ARBGPU_ERR_CUDA;
@@ -254,6 +283,8 @@ arbgpu_status crt_device_tables(arbgpu_ctx *ctx, const CrtPlan *P, CrtDevTables 
   out->wtab = (const uint16_t *)(base + ow);
   out->crt_wtab = (const uint16_t *)(base + ocw);
   out->mbytes = (const float *)(base + omb);
+  out->w8 = (const int8_t *)(base + ow8);
+  out->c32 = (const uint32_t *)(base + oc32);
   return ARBGPU_OK;
 }
 

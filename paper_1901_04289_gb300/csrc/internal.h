@@ -207,6 +207,14 @@ struct CrtPlan {
   int NQ, NQP;
   std::vector<uint16_t> crt_wtab;
   std::vector<float> mbytes;
+  // The same bytes as 8-bit integers for the warp-level MMA reconstruction (every NM): w8
+  // [NQ8][K8], row n holding byte n of Q_t in column 2t and byte n - 1 in column 2t + 1 (zero
+  // padded: K8 = 2 NM and NQ8 = NQ rounded up to multiples of 32).
+  int K8, NQ8;
+  std::vector<int8_t> w8;
+  // The z bytes enter that product offset by -128 (as signed bytes): c32 [2 NMW + 2] holds
+  // 32896 sum_t Q_t in 32-bit words, the term that puts the offset back.
+  std::vector<uint32_t> c32;
 };
 int crt_moduli_for_bits(int bits);
 const CrtPlan *crt_plan(int NM);
@@ -218,6 +226,8 @@ struct CrtDevTables {
   const uint16_t *crt_wtab;
   const float *mbytes;
   const uint64_t *inv;
+  const int8_t *w8;
+  const uint32_t *c32;
 };
 arbgpu_status crt_device_tables(arbgpu_ctx *ctx, const CrtPlan *plan, CrtDevTables *out);
 

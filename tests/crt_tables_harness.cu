@@ -47,5 +47,10 @@ int main(int argc, char **argv) {
   put("wtab", P->wtab);
   put("crt_wtab", P->crt_wtab);
   put_f("mbytes", P->mbytes);
+  printf("dims8 %d %d\n", P->K8, P->NQ8);
+  printf("w8");
+  for (int8_t x : P->w8) printf(" %d", (int)x);
+  printf("\n");
+  put("c32", P->c32);
   return 0;
 }

@@ -7,7 +7,8 @@ count.  Every table is checked against what it must satisfy, not against a retyp
 * the Barrett reciprocals and the GEMM item tables repeat for three products per modulus;
 * 2^(32c) mod m_t is right;
 * the residue weights' balanced bytes give 2^(8d) (times y_t) mod m_t;
-* the reconstruction weights' balanced bytes sum back to Q_t and M;
+* the reconstruction weights' balanced bytes sum back to Q_t and M, in BF16 (NM <= 64) and as the
+  signed bytes of the warp-MMA reconstruction (every NM), whose offset term is 32896 sum_t Q_t;
 * the modulus count covers the requested bits.
 """
 from __future__ import annotations
@@ -71,7 +72,7 @@ def balanced_sum(digits):
     return sum(int(d) * 256 ** n for n, d in enumerate(digits))
 
 
-@pytest.mark.parametrize("NM", [5, 39, 64, 100])
+@pytest.mark.parametrize("NM", [5, 39, 64, 100, 143])
 def test_crt_tables(harness, NM):
     t = tables(harness, NM)
     nm, NMW, NCHP, NW32P, NPAD, NQ, NQP = t["dims"]
@@ -134,6 +135,21 @@ def test_crt_tables(harness, NM):
             assert w256 == 256 * w1
             err += m * abs(w1 - Fraction(1, m))
         assert err < Fraction(1, 4)
+    # the signed-byte table of the warp-MMA reconstruction: column 2t holds the balanced bytes
+    # of Q_t, column 2t + 1 the same bytes one place up (the high byte of z_t), zero elsewhere
+    K8, NQ8 = t["dims8"]
+    w8 = t["w8"]
+    assert K8 % 32 == 0 and 2 * NM <= K8 < 2 * NM + 32 and NQ8 % 32 == 0 and NQ <= NQ8
+    assert len(w8) == K8 * NQ8 and all(-128 <= v <= 127 for v in w8)
+    for k, m in enumerate(mods):
+        lo = [w8[n * K8 + 2 * k] for n in range(NQ8)]
+        hi = [w8[n * K8 + 2 * k + 1] for n in range(NQ8)]
+        assert balanced_sum(lo) == M // m
+        assert hi == [0] + lo[:-1]
+    assert all(w8[n * K8 + c] == 0 for n in range(NQ8) for c in range(2 * NM, K8))
+    # with the z bytes offset by -128, sum_t z_t Q_t = S + 32896 sum_t Q_t
+    assert from_limbs(t["c32"], 32) == 32896 * sum(M // m for m in mods)
+    assert len(t["c32"]) == 2 * NMW + 2
 
 
 def test_modulus_count_covers_the_bits(harness):
