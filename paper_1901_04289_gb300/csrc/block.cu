@@ -846,6 +846,230 @@ static void launch_residues(int nch, int64_t n, cudaStream_t s, const BallsView 
 #undef ARB_RES
 }
 
+// ---- Residues on the 8-bit warp-level MMA, for operands beyond the tensor-core residue kernel
+// (more moduli, chunks or shared memory than it takes).  With the bytes x_d of the scaled |X|
+// (d < 32 KS, zero past |X|) and the unsigned bytes l, h of w_{t,d} = 2^(8d) mod m_t (times y_t
+// for B), X mod m_t = (S_l + 256 S_h) mod m_t with S_b = sum_d x_d (byte b of w_{t,d}): an
+// unsigned byte product on mma.sync m16n8k32 whose s32 sums are exact (|S| <= 224 255 255).  A
+// warp takes 32 consecutive entries of the [rows][Kp] layout: each lane cuts its entry into
+// 32-bit chunks (residue_chunks32) and writes its radius operands as residue_split_kernel does,
+// the chunks reach the A fragments through shared memory, and each lane reduces the column pairs
+// (2t, 2t + 1) it holds for two rows to balanced residues and stores their bytes.
+constexpr int RQ_WARPS = 8;
+constexpr size_t RQ_SMEM_MAX = 227 * 1024;  // opt-in shared memory of one CTA
+constexpr float RQ_MAGIC = 12582912.0f;     // 1.5 * 2^23: adding it rounds |v| < 2^22 to an integer
+
+__device__ __forceinline__ void mma_u8u8(int32_t (&d)[4], const uint32_t (&a)[4], uint32_t b0,
+                                         uint32_t b1) {
+  asm("mma.sync.aligned.m16n8k32.row.col.s32.u8.u8.s32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, "
+      "{%8, %9}, {%0, %1, %2, %3};"
+      : "+r"(d[0]), "+r"(d[1]), "+r"(d[2]), "+r"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+template <int NCH>
+constexpr int rq_ks() {
+  return (4 * NCH + 31) / 32;
+}
+
+// Shared-memory bytes of residue_mma_kernel<NCH> for NM moduli.
+template <int NCH>
+static size_t rq_smem_bytes(int NM) {
+  constexpr int KS = rq_ks<NCH>();
+  const size_t N2 = (size_t)(2 * NM + 31) / 32 * 32;
+  return N2 * (32 * KS + 16) + (size_t)(NM + 3) / 4 * 32 +
+         (size_t)RQ_WARPS * 32 * (8 * KS + 1) * 4 + (size_t)RQ_WARPS * 32 * 4;
+}
+
+template <int NCH>
+__global__ void __launch_bounds__(32 * RQ_WARPS) residue_mma_kernel(
+    const BallsView X, bool is_b, int64_t rows, int64_t k0, int64_t K, int64_t Kp, int64_t ld,
+    const int64_t *bot, int NM, const uint8_t *w8r, int KR, const float *rinv,
+    __nv_bfloat16 *out, SplitOut ro, const int64_t *top, const int64_t *radtop,
+    const int64_t *plustop) {
+  constexpr int KS = rq_ks<NCH>();
+  constexpr int CW = 8 * KS + 1;  // chunk row stride in words (odd: conflict-free columns)
+  const int N2 = (2 * NM + 31) / 32 * 32, WS = 32 * KS + 16;
+  extern __shared__ uint4 smem_u4[];
+  uint8_t *sW = (uint8_t *)smem_u4;                           // [N2][WS] weight bytes
+  uint32_t *sMod = (uint32_t *)(sW + (size_t)N2 * WS);        // [NM] m_t
+  float *sR = (float *)(sMod + (NM + 3) / 4 * 4);             // [NM] 1 / m_t
+  uint32_t *sCh = (uint32_t *)(sR + (NM + 3) / 4 * 4);        // [warps][32][CW] chunks
+  uint32_t *sFl = sCh + RQ_WARPS * 32 * CW;                   // [warps][32] 1: live, 2: negative
+  {
+    const int c16 = 2 * KS;  // 16-byte pieces of a row's 32 KS bytes
+    for (int q = threadIdx.x; q < N2 * c16; q += blockDim.x) {
+      const int n = q / c16, u = q - n * c16;
+      *(uint4 *)(sW + (size_t)n * WS + 16 * u) = __ldg((const uint4 *)(w8r + (size_t)n * KR) + u);
+    }
+    for (int t = threadIdx.x; t < NM; t += blockDim.x) {
+      sMod[t] = c_mods[t];
+      sR[t] = __ldg(rinv + t);
+    }
+  }
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, tig = lane & 3;
+  uint32_t *sChw = sCh + warp * 32 * CW;
+  uint32_t *sFlw = sFl + warp * 32;
+  const int64_t n = rows * Kp, plane = rows * Kp, ntile = (n + 31) / 32;
+  const int nchunks = N2 / 32;
+  for (int64_t tile = (int64_t)blockIdx.x * RQ_WARPS + warp; tile < ntile;
+       tile += (int64_t)gridDim.x * RQ_WARPS) {
+    // this lane's entry: chunks, sign, radius operands
+    {
+      const int64_t L = 32 * tile + lane;
+      uint32_t ch[NCH];
+#pragma unroll
+      for (int c = 0; c < NCH; ++c) ch[c] = 0;
+      uint32_t fl_out = 0;
+      if (L < n) {
+        const int64_t r = L / Kp, k = L - r * Kp;
+        Mag absm{0u, 0}, rad{0u, 0};
+        if (k < K) {
+          const int64_t e = is_b ? ((k0 + k) * ld + r) : (r * ld + k0 + k);
+          const uint32_t fl = __ldg(X.flags + e);
+          const int64_t ex = __ldg(X.exp + e);
+          if (!(fl & (ARBGPU_FLAG_ZERO | SPECIAL_MASK))) {
+            fl_out = 1u | ((fl & ARBGPU_FLAG_SIGN) ? 2u : 0u);
+            const int64_t sh = ex - 64LL * X.nlimbs - bot[r];
+            residue_chunks32<NCH>(X, e, sh, ch);
+            if (ro.r1 || ro.r2) absm = mid_upper(X, e, ex);
+          }
+          if (ro.r1 || ro.r2) rad = Mag{__ldg(X.rad_man + e), __ldg(X.rad_exp + e)};
+        }
+        if (ro.r1 || ro.r2) {
+          const int64_t off = r * Kp + k;
+          if (!is_b) {
+            if (ro.r1) put_small_digits(window_up(absm.man, absm.exp, top[r]), ro.r1 + off, plane);
+            if (ro.r2) put_small_digits(window_up(rad.man, rad.exp, radtop[r]), ro.r2 + off, plane);
+          } else {
+            if (ro.r1) put_small_digits(window_up(rad.man, rad.exp, radtop[r]), ro.r1 + off, plane);
+            if (ro.r2) {
+              const Mag plus = mag_add_up(absm, rad);
+              put_small_digits(window_up(plus.man, plus.exp, plustop[r]), ro.r2 + off, plane);
+            }
+          }
+        }
+      }
+#pragma unroll
+      for (int c = 0; c < 8 * KS; ++c) sChw[lane * CW + c] = (c < NCH && (fl_out & 1u)) ? ch[c] : 0u;
+      sFlw[lane] = fl_out;
+    }
+    __syncwarp();
+    // A fragments: register r of row tile mt holds chunk 8 ks + tig + 4 (r >> 1) (bytes
+    // 32 ks + 4 tig .. (+16)) of row 16 mt + g + 8 (r & 1)
+    uint32_t af[KS][2][4];
+#pragma unroll
+    for (int ks = 0; ks < KS; ++ks)
+#pragma unroll
+      for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+        for (int r = 0; r < 4; ++r)
+          af[ks][mt][r] = sChw[(16 * mt + g + 8 * (r & 1)) * CW + 8 * ks + tig + 4 * (r >> 1)];
+    uint32_t rfl[2][2];
+#pragma unroll
+    for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+      for (int h = 0; h < 2; ++h) rfl[mt][h] = sFlw[16 * mt + 8 * h + g];
+    __syncwarp();
+    for (int nc = 0; nc < nchunks; ++nc) {
+      int32_t acc[2][4][4];
+#pragma unroll
+      for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+        for (int nt = 0; nt < 4; ++nt)
+#pragma unroll
+          for (int r = 0; r < 4; ++r) acc[mt][nt][r] = 0;
+#pragma unroll
+      for (int ks = 0; ks < KS; ++ks)
+#pragma unroll
+        for (int nt = 0; nt < 4; ++nt) {
+          const uint8_t *wrow = sW + (size_t)(32 * nc + 8 * nt + g) * WS + 32 * ks + 4 * tig;
+          const uint32_t b0 = *(const uint32_t *)wrow, b1 = *(const uint32_t *)(wrow + 16);
+          mma_u8u8(acc[0][nt], af[ks][0], b0, b1);
+          mma_u8u8(acc[1][nt], af[ks][1], b0, b1);
+        }
+      // columns 2t, 2t + 1 of rows 16 mt + g (+ 8): t = 16 nc + 4 nt + tig.  With 0 <= S_b <
+      // 2^24 (exact in FP32): r_h = S_h mod m (|r_h| <= m, one FMA, exact), x = 256 r_h + S_l
+      // (|x| < 2^25), then x mod m from a float quotient off by at most one, balanced.
+#pragma unroll
+      for (int nt = 0; nt < 4; ++nt) {
+        const int t = 16 * nc + 4 * nt + tig;
+        if (t >= NM) continue;
+        const int32_t m = (int32_t)sMod[t], hm = m >> 1;
+        const float mf = (float)m, rm = sR[t];
+        __nv_bfloat16 *o0 = out + (int64_t)(2 * t) * plane + 32 * tile;
+#pragma unroll
+        for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            const int row = 16 * mt + 8 * h + g;
+            if (32 * tile + row >= n) continue;
+            const float fh = (float)acc[mt][nt][2 * h + 1];
+            const float qh = __fadd_rn(__fmaf_rn(fh, rm, RQ_MAGIC), -RQ_MAGIC);
+            const int32_t x = 256 * (int32_t)__fmaf_rn(-qh, mf, fh) + acc[mt][nt][2 * h];
+            const float q = __fadd_rn(__fmaf_rn((float)x, rm, RQ_MAGIC), -RQ_MAGIC);
+            int32_t res = x - (int32_t)q * m;
+            if (res > hm) res -= m;
+            if (res > hm) res -= m;
+            if (res < -hm) res += m;
+            if (res < -hm) res += m;
+            if (rfl[mt][h] & 2u) res = -res;
+            if (!(rfl[mt][h] & 1u)) res = 0;
+            const int32_t lo = ((res + 128) & 255) - 128;
+            const int32_t hi = (res - lo) >> 8;
+            o0[row] = __float2bfloat16_rn((float)lo);
+            o0[plane + row] = __float2bfloat16_rn((float)hi);
+          }
+      }
+    }
+  }
+}
+
+// The MMA residue kernel for nch chunks; false when it does not take the operand
+// (ARBGPU_RESIDUE_MMA=0 also declines).
+static bool launch_residues_mma(arbgpu_ctx *ctx, int nch, cudaStream_t s, const BallsView &X,
+                                bool is_b, int64_t rows, int64_t k0, int64_t K, int64_t Kp,
+                                int64_t ld, const int64_t *bot, int NM, const uint8_t *w8r, int KR,
+                                const float *rinv, __nv_bfloat16 *out, const SplitOut &ro,
+                                const int64_t *top, const int64_t *radtop,
+                                const int64_t *plustop) {
+  const char *e = getenv("ARBGPU_RESIDUE_MMA");
+  if ((e && !strcmp(e, "0")) || !w8r || NM < 1 || NM > CRT_MAX_MODULI || nch > CRT_MAX_CHUNKS32)
+    return false;
+  const int64_t ntile = (rows * Kp + 31) / 32;
+  int64_t grid = (ntile + RQ_WARPS - 1) / RQ_WARPS;
+  if (grid > 2LL * ctx->sm_count) grid = 2LL * ctx->sm_count;
+  if (grid < 1) return true;
+  const int dev = ctx->device & 255;
+#define ARB_RQ(NCH_)                                                                          \
+  do {                                                                                        \
+    if (32 * rq_ks<NCH_>() > KR) return false;                                                \
+    const size_t smem = rq_smem_bytes<NCH_>(NM);                                              \
+    if (smem > RQ_SMEM_MAX) return false;                                                     \
+    static bool attr_done[256] = {};                                                          \
+    if (!attr_done[dev]) {                                                                    \
+      if (cudaFuncSetAttribute(residue_mma_kernel<NCH_>,                                      \
+                               cudaFuncAttributeMaxDynamicSharedMemorySize,                   \
+                               (int)RQ_SMEM_MAX) != cudaSuccess)                              \
+        return false;                                                                         \
+      attr_done[dev] = true;                                                                  \
+    }                                                                                         \
+    residue_mma_kernel<NCH_><<<(unsigned)grid, 32 * RQ_WARPS, smem, s>>>(                     \
+        X, is_b, rows, k0, K, Kp, ld, bot, NM, w8r, KR, rinv, out, ro, top, radtop, plustop); \
+  } while (0)
+  if (nch <= 24)
+    ARB_RQ(24);
+  else if (nch <= 32)
+    ARB_RQ(32);
+  else if (nch <= 40)
+    ARB_RQ(40);
+  else
+    ARB_RQ(CRT_MAX_CHUNKS32);
+#undef ARB_RQ
+  return true;
+}
+
 // ---- Residues on the tensor cores.  With the signed base-256 digits x_d = ±(byte d of |X|)
 // (d < 4 NCH, the sign of X on every digit),
 //
@@ -3669,13 +3893,19 @@ static arbgpu_status run_block(arbgpu_ctx *ctx, const BlockWs &w, uint8_t *ws, c
       if (omitted) return ARBGPU_ERR_LIMIT;
       {
         LaunchScope sc(ctx, s, "residues_a", M * Kp * NM * nchA);
-        launch_residues(nchA, M * Kp, s, Av, false, M, k0, Kb, Kp, lda, ln.rbot, NM, dt.pow32,
-                        plan->NCHP, nullptr, resA, roA, ln.rtop, ln.rrad, nullptr);
+        if (!launch_residues_mma(ctx, nchA, s, Av, false, M, k0, Kb, Kp, lda, ln.rbot, NM,
+                                 dt.w8r, plan->KR, dt.rinv, resA, roA, ln.rtop, ln.rrad,
+                                 nullptr))
+          launch_residues(nchA, M * Kp, s, Av, false, M, k0, Kb, Kp, lda, ln.rbot, NM, dt.pow32,
+                          plan->NCHP, nullptr, resA, roA, ln.rtop, ln.rrad, nullptr);
       }
       {
         LaunchScope sc(ctx, s, "residues_b", N * Kp * NM * nchB);
-        launch_residues(nchB, N * Kp, s, Bv, true, N, k0, Kb, Kp, ldb, ln.cbot, NM, dt.pow32,
-                        plan->NCHP, dt.y, resB, roB, ln.ctop, ln.crad, ln.cplus);
+        if (!launch_residues_mma(ctx, nchB, s, Bv, true, N, k0, Kb, Kp, ldb, ln.cbot, NM,
+                                 dt.w8r + (size_t)plan->N2 * plan->KR, plan->KR, dt.rinv, resB,
+                                 roB, ln.ctop, ln.crad, ln.cplus))
+          launch_residues(nchB, N * Kp, s, Bv, true, N, k0, Kb, Kp, ldb, ln.cbot, NM, dt.pow32,
+                          plan->NCHP, dt.y, resB, roB, ln.ctop, ln.crad, ln.cplus);
       }
     }
     if (cudaGetLastError() != cudaSuccess) return ARBGPU_ERR_CUDA;

@@ -149,6 +149,23 @@ std::unique_ptr<CrtPlan> build_plan(int NM) {
         v = (v << 8) % m;
       }
     }
+  // the same weights as unsigned bytes for the warp-level MMA residue step (every NM): side o,
+  // column n = 2t + b holds byte b of 2^(8d) mod m_t (times y_t for side 1) in row d < KR
+  P->N2 = (2 * NM + 31) / 32 * 32;
+  P->KR = (4 * CRT_MAX_CHUNKS32 + 31) / 32 * 32;
+  P->w8r.assign((size_t)2 * P->N2 * P->KR, 0);
+  for (int side = 0; side < 2; ++side)
+    for (int t = 0; t < NM; ++t) {
+      const uint64_t m = P->mods[t];
+      uint64_t v = 1;  // 2^(8d) mod m
+      for (int d = 0; d < P->KR; ++d) {
+        const uint64_t w = side ? v * P->y[t] % m : v;
+        uint8_t *col = P->w8r.data() + ((size_t)side * P->N2 + 2 * t) * P->KR;
+        col[d] = (uint8_t)(w & 255);
+        col[P->KR + d] = (uint8_t)(w >> 8);
+        v = (v << 8) % m;
+      }
+    }
   // reconstruction weights (used when NM <= 64)
   {
     auto balanced_bytes = [](const std::vector<uint64_t> &x, int nb) {
@@ -247,7 +264,8 @@ arbgpu_status crt_device_tables(arbgpu_ctx *ctx, const CrtPlan *P, CrtDevTables 
   const size_t omb = ocw + al(2 * P->crt_wtab.size());
   const size_t ow8 = omb + al(4 * P->mbytes.size());
   const size_t oc32 = ow8 + al(P->w8.size());
-  const size_t total = oc32 + al(4 * P->c32.size());
+  const size_t ow8r = oc32 + al(4 * P->c32.size());
+  const size_t total = ow8r + al(P->w8r.size());
   auto it = ctx->crt_tables.find(P->NM);
   uint8_t *base = nullptr;
   if (it != ctx->crt_tables.end()) {
@@ -267,6 +285,7 @@ arbgpu_status crt_device_tables(arbgpu_ctx *ctx, const CrtPlan *P, CrtDevTables 
     memcpy(h.data() + omb, P->mbytes.data(), 4 * P->mbytes.size());
     memcpy(h.data() + ow8, P->w8.data(), P->w8.size());
     memcpy(h.data() + oc32, P->c32.data(), 4 * P->c32.size());
+    memcpy(h.data() + ow8r, P->w8r.data(), P->w8r.size());
     if (cudaMemcpy(base, h.data(), total, cudaMemcpyHostToDevice) != cudaSuccess) {
       cudaFree(base);
       return ARBGPU_ERR_CUDA;
@@ -285,6 +304,7 @@ arbgpu_status crt_device_tables(arbgpu_ctx *ctx, const CrtPlan *P, CrtDevTables 
   out->mbytes = (const float *)(base + omb);
   out->w8 = (const int8_t *)(base + ow8);
   out->c32 = (const uint32_t *)(base + oc32);
+  out->w8r = (const uint8_t *)(base + ow8r);
   return ARBGPU_OK;
 }
 

@@ -215,6 +215,11 @@ struct CrtPlan {
   // The z bytes enter that product offset by -128 (as signed bytes): c32 [2 NMW + 2] holds
   // 32896 sum_t Q_t in 32-bit words, the term that puts the offset back.
   std::vector<uint32_t> c32;
+  // Residue weights as unsigned bytes for the warp-level MMA residue step (every NM): w8r
+  // [2][N2][KR], side o, column n = 2t + b holding byte b of 2^(8d) mod m_t (times y_t for side
+  // 1) in row d (N2 = 2 NM rounded up to 32, KR = 4 CRT_MAX_CHUNKS32 rounded up to 32).
+  int N2, KR;
+  std::vector<uint8_t> w8r;
 };
 int crt_moduli_for_bits(int bits);
 const CrtPlan *crt_plan(int NM);
@@ -228,6 +233,7 @@ struct CrtDevTables {
   const uint64_t *inv;
   const int8_t *w8;
   const uint32_t *c32;
+  const uint8_t *w8r;
 };
 arbgpu_status crt_device_tables(arbgpu_ctx *ctx, const CrtPlan *plan, CrtDevTables *out);
 

@@ -52,5 +52,7 @@ int main(int argc, char **argv) {
   for (int8_t x : P->w8) printf(" %d", (int)x);
   printf("\n");
   put("c32", P->c32);
+  printf("dimsr %d %d\n", P->N2, P->KR);
+  put("w8r", P->w8r);
   return 0;
 }

@@ -6,7 +6,8 @@ count.  Every table is checked against what it must satisfy, not against a retyp
 * M and its cofactors Q_t = M / m_t are right, and y_t Q_t = 1 (mod m_t);
 * the Barrett reciprocals and the GEMM item tables repeat for three products per modulus;
 * 2^(32c) mod m_t is right;
-* the residue weights' balanced bytes give 2^(8d) (times y_t) mod m_t;
+* the residue weights' balanced bytes give 2^(8d) (times y_t) mod m_t, and so do the unsigned
+  bytes of the warp-MMA residue step;
 * the reconstruction weights' balanced bytes sum back to Q_t and M, in BF16 (NM <= 64) and as the
   signed bytes of the warp-MMA reconstruction (every NM), whose offset term is 32896 sum_t Q_t;
 * the modulus count covers the requested bits.
@@ -150,6 +151,20 @@ def test_crt_tables(harness, NM):
     # with the z bytes offset by -128, sum_t z_t Q_t = S + 32896 sum_t Q_t
     assert from_limbs(t["c32"], 32) == 32896 * sum(M // m for m in mods)
     assert len(t["c32"]) == 2 * NMW + 2
+    # unsigned residue weights of the warp-MMA residue step: column 2t (+1) of side o holds the
+    # low (high) byte of 2^(8d) mod m_t (times y_t for o = 1) in row d, zero past 2 NM
+    N2, KR = t["dimsr"]
+    w8r = t["w8r"]
+    assert N2 % 32 == 0 and 2 * NM <= N2 < 2 * NM + 32 and KR % 32 == 0 and KR >= 200
+    assert len(w8r) == 2 * N2 * KR and all(0 <= v <= 255 for v in w8r)
+    for side in (0, 1):
+        for k, m in enumerate(mods):
+            base = (side * N2 + 2 * k) * KR
+            for d in range(0, KR, 7 if NM > 64 else 1):
+                v = w8r[base + d] + 256 * w8r[base + KR + d]
+                assert v == pow(2, 8 * d, m) * (t["y"][k] if side else 1) % m
+        assert not any(w8r[(side * N2 + c) * KR:(side * N2 + c + 1) * KR] != [0] * KR
+                       for c in range(2 * NM, N2))
 
 
 def test_modulus_count_covers_the_bits(harness):

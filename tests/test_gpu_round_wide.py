@@ -53,3 +53,25 @@ def test_long_epilogues_match_general_and_oracle(arb, M, K, N, prec, spread, nl,
     rng2 = np.random.default_rng(7)
     entries = [(int(a), int(b)) for a, b in zip(rng2.integers(0, M, 16), rng2.integers(0, N, 16))]
     check_entries(out, A, B, M, K, N, prec, entries, (prec + 63) // 64)
+
+
+@pytest.mark.parametrize("M,K,N,prec,spread,nl", CASES)
+def test_residue_mma_matches_cuda_core_residues(arb, M, K, N, prec, spread, nl):
+    """The operands these products take beyond the tensor-core residue kernel get their residues
+    from the 8-bit warp-MMA kernel; the CUDA-core residue kernel (ARBGPU_RESIDUE_MMA=0) gives the
+    same balls bit for bit, with radii on both sides (the radius operands are written alongside)."""
+    rng = np.random.default_rng(3 * prec + spread)
+    A = random_balls(rng, M * K, nl, 64 * nl - 2, -spread, spread, rad_bits=prec - 8,
+                     rad_zero_frac=0.4, zero_frac=0.05)
+    B = random_balls(rng, K * N, nl, 64 * nl - 2, -spread, spread, rad_bits=prec - 8,
+                     rad_zero_frac=0.4, zero_frac=0.05)
+    with env(ARBGPU_ENGINE="crt", ARBGPU_OMIT="0"):
+        out, names = run_mm(arb, A, B, M, K, N, prec, arb.ALG_BLOCK, trace=True)
+        with env(ARBGPU_RESIDUE_MMA="0"):
+            ref, _ = run_mm(arb, A, B, M, K, N, prec, arb.ALG_BLOCK)
+    assert "residues_a" in names and "residues_b" in names
+    for f in ("limbs", "exp", "flags", "rad_man", "rad_exp"):
+        assert np.array_equal(getattr(out, f), getattr(ref, f)), f
+    rng2 = np.random.default_rng(11)
+    entries = [(int(a), int(b)) for a, b in zip(rng2.integers(0, M, 12), rng2.integers(0, N, 12))]
+    check_entries(out, A, B, M, K, N, prec, entries, (prec + 63) // 64)
