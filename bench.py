@@ -195,10 +195,11 @@ def roofline_of(name, k, peaks, sm_mhz, limb_n=None):
 DOT_KERNELS = ("dot_setup", "dot_eval", "dot_fused", "dot_tile")
 
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the headline workload's
-# kernels (N = 512, p = 256), from the ncu capture summarised in
+# kernels (N = 512, p = 256: residue_tc_kernel, crt_gemm_kernel and crt_round_tc_kernel, the last
+# traced as block_round), from the ncu capture summarised in
 # profiles/multimodular_n512_p256_full.md; valid only for that workload and for kernels unchanged
-# since that capture (the reconstruction kernel has changed since, so its traffic is not given).
-TRAFFIC_N512_P256 = {"crt_gemm": 88.21e6, "residues": 58.84e6}
+# since that capture.
+TRAFFIC_N512_P256 = {"crt_gemm": 88.24e6, "residues": 58.76e6, "block_round": 24.28e6}
 
 
 def dot_work(terms_by_n, unique_bytes=None):
@@ -485,6 +486,8 @@ def run_workload(args):
             return terms / dt, f"{done} series x {length} coefficients in {dt:.1f} s", dt
     else:  # grouped
         cases = grouped_matmuls()
+        if args.items:  # a subset of the batch (e.g. one item for a profiler capture)
+            cases = [cases[int(t)] for t in args.items.split(",")]
         items = []
         inbytes = outbytes = 0
         for c in cases:
@@ -500,6 +503,8 @@ def run_workload(args):
         prec = 1024
         name = ("grouped batch of 256 real ball matmuls, N U[16,512], p in {64..1024}, "
                 "exponents U[-50,50], radii 2^-(p-8)")
+        if args.items:
+            name = f"items {args.items} of the " + name
 
         def cpu_fn(limit):
             rng = np.random.default_rng(0)
@@ -545,7 +550,7 @@ def run_workload(args):
         step()
     t1.record(stream)
     torch.cuda.synchronize()
-    recs = ctx.trace_read()
+    recs = ctx.trace_read(max_entries=1 << 18)
     ctx.trace(False)
     ctx.check()
     kernels = kernel_summary(recs, t0.elapsed_time(t1))
@@ -629,6 +634,9 @@ def main():
     ap.add_argument("--no-compare", action="store_true", help="skip the p=128 / dot-path lines")
     ap.add_argument("--ref-entries", type=int, default=48)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--items", default="",
+                    help="grouped workload only: comma-separated item indices to run instead of "
+                         "the whole batch")
     ap.add_argument("--workload", default="n512",
                     choices=["n512", "n32dots", "dots", "complex2048", "complex2048_literal",
                              "series", "grouped"],
@@ -709,7 +717,7 @@ def main():
         if world > 1:
             dist.barrier()
         launches = ctx.launch_count() - l0
-        recs = ctx.trace_read() if trace else []
+        recs = ctx.trace_read(max_entries=1 << 18) if trace else []
         ctx.trace(False)
         ctx.check()
         ms = sum(a.elapsed_time(b) for a, b in evs)
