@@ -294,9 +294,10 @@ __device__ __forceinline__ LineAcc line_shfl_xor(const LineAcc &a, int o) {
   return b;
 }
 
-// Both whole-range scans in one launch of 1024-thread CTAs: CTAs [0, ceil(M / 4)) take four rows
-// of A (256 threads along each row), the others four columns of B (256 k-slices; a warp reads
-// eight rows of four neighbouring entries, one 32-byte sector each).  Each CTA finishes its lines.
+// Both whole-range scans in one launch of 1024-thread CTAs: CTAs [0, ceil(M / 8)) take eight rows
+// of A (128 threads along each row), the others eight columns of B (128 k-slices; a warp reads
+// four rows of eight neighbouring entries).  Each CTA finishes its lines.  (At N = 512 the 128
+// CTAs run in one wave, each thread with four entries' loads in flight.)
 // Publication of the statistics to the host: the last CTA of the launch to finish copies `n`
 // BlockStats from `src` into mapped pinned host memory `dst` (as 32-bit words), then writes `seq`
 // into the word after them (system-scope fences between), so that the host can poll for `seq`
@@ -335,21 +336,21 @@ __global__ void __launch_bounds__(1024) scan_full_kernel(
     const BallsView A, const BallsView B, int64_t M, int64_t K, int64_t N, int64_t lda,
     int64_t ldb, int64_t *rtop, int64_t *rbot, int64_t *rrad, BlockStats *st_rows, int64_t *ctop,
     int64_t *cbot, int64_t *crad, int64_t *cplus, BlockStats *st_cols, const StatsPublish pub) {
-  __shared__ LineAcc s_acc[32][4];
+  __shared__ LineAcc s_acc[32][8];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int64_t row_ctas = (M + 3) / 4;
+  const int64_t row_ctas = (M + 7) / 8;
   LineAcc a{INT64_MIN, INT64_MAX, INT64_MIN, 0, 0};
   if ((int64_t)blockIdx.x < row_ctas) {
-    const int r = threadIdx.x >> 8, tk = threadIdx.x & 255;  // row of the group, k-slice
-    const int64_t i = (int64_t)blockIdx.x * 4 + r;
+    const int r = threadIdx.x >> 7, tk = threadIdx.x & 127;  // row of the group, k-slice
+    const int64_t i = (int64_t)blockIdx.x * 8 + r;
     if (i < M)
-      for (int64_t k = tk; k < K; k += 256) line_fold(a, scan_entry(A, i * lda + k));
+      for (int64_t k = tk; k < K; k += 128) line_fold(a, scan_entry(A, i * lda + k));
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) line_merge(a, line_shfl_xor(a, o));
     if (lane == 0) s_acc[warp][0] = a;
     __syncthreads();
-    if (tk == 0 && i < M) {  // warps 8r .. 8r + 7 hold row r
-      for (int w = 1; w < 8; ++w) line_merge(a, s_acc[8 * r + w][0]);
+    if (tk == 0 && i < M) {  // warps 4r .. 4r + 3 hold row r
+      for (int w = 1; w < 4; ++w) line_merge(a, s_acc[4 * r + w][0]);
       rtop[i] = a.top;
       rbot[i] = a.bot;
       rrad[i] = a.rad;
@@ -361,17 +362,16 @@ __global__ void __launch_bounds__(1024) scan_full_kernel(
     if (pub.dst) publish_stats(pub, tk == 0);
     return;
   }
-  const int tx = threadIdx.x & 3, ty = threadIdx.x >> 2;  // column of the group, k-slice
-  const int64_t j = ((int64_t)blockIdx.x - row_ctas) * 4 + tx;
+  const int tx = threadIdx.x & 7, ty = threadIdx.x >> 3;  // column of the group, k-slice
+  const int64_t j = ((int64_t)blockIdx.x - row_ctas) * 8 + tx;
   if (j < N)
-    for (int64_t k = ty; k < K; k += 256) line_fold(a, scan_entry(B, k * ldb + j));
-  // lanes 4 apart hold the same column
-  line_merge(a, line_shfl_xor(a, 4));
+    for (int64_t k = ty; k < K; k += 128) line_fold(a, scan_entry(B, k * ldb + j));
+  // lanes 8 apart hold the same column
   line_merge(a, line_shfl_xor(a, 8));
   line_merge(a, line_shfl_xor(a, 16));
-  if (lane < 4) s_acc[warp][lane] = a;
+  if (lane < 8) s_acc[warp][lane] = a;
   __syncthreads();
-  if (threadIdx.x < 4 && j < N) {
+  if (threadIdx.x < 8 && j < N) {
     for (int w = 1; w < 32; ++w) line_merge(a, s_acc[w][tx]);
     ctop[j] = a.top;
     cbot[j] = a.bot;
@@ -383,7 +383,7 @@ __global__ void __launch_bounds__(1024) scan_full_kernel(
     if (a.flags & 1) atomicOr(&st_cols->special, 1);
     if (a.flags & 2) atomicOr(&st_cols->radB, 1);
   }
-  if (pub.dst) publish_stats(pub, threadIdx.x < 4);
+  if (pub.dst) publish_stats(pub, threadIdx.x < 8);
 }
 
 // Scans of the rows of X (M x K) and the columns of Y (K x N) over the whole inner range
@@ -4682,7 +4682,7 @@ arbgpu_status block_scan_launch(arbgpu_ctx *ctx, const arbgpu_balls *A, const ar
       if (pub.seq == 0) pub.seq = ++ctx->pub_seq;  // (0 is the words' initial value)
     }
     LaunchScope sc(ctx, s, "scans", M * K + K * N);
-    scan_full_kernel<<<(unsigned)((M + 3) / 4 + (N + 3) / 4), 1024, 0, s>>>(
+    scan_full_kernel<<<(unsigned)((M + 7) / 8 + (N + 7) / 8), 1024, 0, s>>>(
         view_of(A[q]), view_of(B[q]), M, K, N, lda, ldb, sr.rtop[q], sr.rbot[q], sr.rrad[q],
         sr.pst + q, sr.ctop[q], sr.cbot[q], sr.crad[q], sr.cplus[q], sr.pst + 2 + q, pub);
     if (cudaGetLastError() != cudaSuccess) return ARBGPU_ERR_CUDA;
