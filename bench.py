@@ -374,6 +374,7 @@ def run_workload(args):
     ctx = arb.default_context(0)
     peaks = load_peaks()
     calibration = measure_alu(ctx)
+    ctx.set_autotune(args.autotune)
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     wl = args.workload
     cpu_fn = None
@@ -599,7 +600,7 @@ def run_workload(args):
             "cpu_baseline": {"value": r / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
                              "sample": sample},
             "io_bytes": {"in": inbytes, "out": outbytes}, "clocks": clocks,
-            "calibration": calibration}
+            "calibration": calibration, "autotune": dict(ctx.autotune_stats(), on=args.autotune)}
     if graph:
         line["us_per_call"] = ms / args.steps * 1e3
         line["graph_replay"] = graph
@@ -634,6 +635,8 @@ def main():
     ap.add_argument("--no-compare", action="store_true", help="skip the p=128 / dot-path lines")
     ap.add_argument("--ref-entries", type=int, default=48)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--autotune", action="store_true",
+                    help="turn on the library's engine autotuner (the warm-up steps decide)")
     ap.add_argument("--items", default="",
                     help="grouped workload only: comma-separated item indices to run instead of "
                          "the whole batch")
@@ -666,6 +669,7 @@ def main():
     ctx = arb.default_context(local)
     peaks = load_peaks()
     calibration = measure_alu(ctx)
+    ctx.set_autotune(args.autotune)
     algs = {"auto": arb.ALG_AUTO, "dot": arb.ALG_DOT, "block": arb.ALG_BLOCK}
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
@@ -887,7 +891,8 @@ def main():
                 "kernels": kernels,
                 "cpu_baseline": cpu,
                 "clocks": clocks, "compare": compare, "peaks_source": peaks["_source"],
-                "calibration": calibration}
+                "calibration": calibration,
+                "autotune": dict(ctx.autotune_stats(), on=args.autotune)}
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()

@@ -111,6 +111,24 @@ typedef struct {
 
 arbgpu_status arbgpu_calibrate(arbgpu_ctx *ctx, arbgpu_calibration *out);
 
+/* Engine autotuner for the block algorithm's exact integer products (Section IV-A).  The
+ * library has two exact carriers for them: S_A x S_B products of balanced 8-bit digit slices, or
+ * 4 NM products of residues modulo NM 16-bit primes followed by a Chinese-remainder
+ * reconstruction.  Both give the same integers bit for bit, so the choice only changes the time.
+ * By default a cost model with per-unit constants measured on GB300 chooses.  With the autotuner
+ * on (enable != 0), the first block product of each size bucket (the digit counts, the modulus
+ * count, and M, N and the padded inner length rounded up to powers of two) that both engines can
+ * take runs on both, once untimed and once timed with CUDA events (four products in all).  That
+ * call synchronises its stream. The faster engine
+ * is kept for the bucket, for the context's lifetime, and later products of the bucket use it.
+ * While the stream is being captured into a CUDA graph, no timing runs: undecided buckets use the
+ * cost model.  Outputs never depend on the setting.
+ * arbgpu_autotune_stats: buckets decided so far, products run for the timings, and how many of
+ * the decided buckets chose the multimodular engine (any pointer may be null). */
+arbgpu_status arbgpu_set_autotune(arbgpu_ctx *ctx, int enable);
+arbgpu_status arbgpu_autotune_stats(arbgpu_ctx *ctx, int64_t *buckets, int64_t *timing_runs,
+                                    int64_t *crt_buckets);
+
 /* Synchronises `stream`, returns the first device-side error recorded since the previous call
  * (ARBGPU_OK if none) and clears it. */
 arbgpu_status arbgpu_get_status(arbgpu_ctx *ctx, void *stream);

@@ -169,6 +169,20 @@ class Context:
         if rc != 0:
             raise ArbgpuError(rc, "arbgpu_reserve")
 
+    def set_autotune(self, enable=True):
+        """Turn the block path's engine autotuner on or off (``arbgpu_set_autotune``)."""
+        rc = _lib.lib().arbgpu_set_autotune(self.handle, 1 if enable else 0)
+        if rc != 0:
+            raise ArbgpuError(rc, "arbgpu_set_autotune")
+
+    def autotune_stats(self):
+        """dict(buckets, timing_runs, crt_buckets) of the engine autotuner."""
+        b, t, c = C.c_int64(0), C.c_int64(0), C.c_int64(0)
+        rc = _lib.lib().arbgpu_autotune_stats(self.handle, C.byref(b), C.byref(t), C.byref(c))
+        if rc != 0:
+            raise ArbgpuError(rc, "arbgpu_autotune_stats")
+        return dict(buckets=b.value, timing_runs=t.value, crt_buckets=c.value)
+
     def calibrate(self):
         """Measured integer and 8-bit tensor throughput of the device (``arbgpu_calibrate``):
         dict with imad_tops, imad_wide_tops, mma_s8_tops, sm_count, max_clock_mhz."""

@@ -110,6 +110,9 @@ def lib():
         L.arbgpu_last_plans.argtypes = [vp, vp, i64, C.POINTER(C.c_int64)]
         L.arbgpu_reserve.argtypes = [vp, i32, i64]
         L.arbgpu_calibrate.argtypes = [vp, C.POINTER(CCalibration)]
+        L.arbgpu_set_autotune.argtypes = [vp, C.c_int]
+        L.arbgpu_autotune_stats.argtypes = [vp, C.POINTER(C.c_int64), C.POINTER(C.c_int64),
+                                            C.POINTER(C.c_int64)]
         L.arbgpu_series_exp.argtypes = [vp, P, P, i64, i64, i32, vp, sz, vp]
         L.arbgpu_series_exp_workspace_size.argtypes = [vp, i64, i64, i32, C.POINTER(C.c_size_t)]
         L.arbgpu_launch_count.argtypes = [vp, C.POINTER(C.c_int64)]
@@ -117,6 +120,7 @@ def lib():
         L.arbgpu_trace_read.argtypes = [vp, C.POINTER(CTrace), i32, C.POINTER(C.c_int32)]
         for name in ("arbgpu_launch_count", "arbgpu_trace_enable", "arbgpu_trace_read",
                      "arbgpu_last_plans", "arbgpu_reserve", "arbgpu_calibrate",
+                     "arbgpu_set_autotune", "arbgpu_autotune_stats",
                      "arbgpu_series_exp",
                      "arbgpu_series_exp_workspace_size",
                      "arbgpu_create", "arbgpu_destroy", "arbgpu_get_status", "arbgpu_dot",
@@ -144,4 +148,5 @@ def exported_symbols():
             "arbgpu_int_mat_mul", "arbgpu_int_mat_mul_workspace_size",
             "arbgpu_int_mat_mul_noalloc", "arbgpu_mat_mul_batched",
             "arbgpu_mat_mul_batched_workspace_size", "arbgpu_last_plans", "arbgpu_reserve",
-            "arbgpu_series_exp", "arbgpu_series_exp_workspace_size", "arbgpu_calibrate"]
+            "arbgpu_series_exp", "arbgpu_series_exp_workspace_size", "arbgpu_calibrate",
+            "arbgpu_set_autotune", "arbgpu_autotune_stats"]

@@ -109,6 +109,23 @@ arbgpu_status arbgpu_trace_read(arbgpu_ctx *ctx, arbgpu_trace_entry *out, int32_
   return ARBGPU_OK;
 }
 
+arbgpu_status arbgpu_set_autotune(arbgpu_ctx *ctx, int enable) {
+  if (!ctx) return ARBGPU_ERR_INVALID;
+  ctx->autotune = enable != 0;
+  return ARBGPU_OK;
+}
+
+arbgpu_status arbgpu_autotune_stats(arbgpu_ctx *ctx, int64_t *buckets, int64_t *timing_runs,
+                                    int64_t *crt_buckets) {
+  if (!ctx) return ARBGPU_ERR_INVALID;
+  int64_t crt = 0;
+  for (const auto &kv : ctx->engine_tuned) crt += kv.second ? 1 : 0;
+  if (buckets) *buckets = (int64_t)ctx->engine_tuned.size();
+  if (timing_runs) *timing_runs = ctx->tune_runs;
+  if (crt_buckets) *crt_buckets = crt;
+  return ARBGPU_OK;
+}
+
 int arbgpu_version(void) { return 100; }
 
 const char *arbgpu_status_string(arbgpu_status s) {

@@ -3751,13 +3751,14 @@ static int bit_length(int64_t v) {
 // (per output entry), a 16-bit multiply-add of the residue kernel (per input entry), and a digit
 // byte of the digit epilogue (per output entry).
 static bool choose_crt(int SA, int SB, int NM, int64_t M, int64_t N, int64_t Kp, int64_t hA,
-                       int64_t hB) {
+                       int64_t hB, int engine = -1) {
   const char *e = getenv("ARBGPU_ENGINE");
   if (e && !strcmp(e, "digits")) return false;
   if (e && !strcmp(e, "crt")) return true;
-  // seconds per unit, measured on a GB300 (N = 512, p = 256): the reconstruction runs on the
-  // tensor cores for NM <= 64 and on the CUDA cores above
-  const double t_mma = 2.6e-15, t_crt = NM <= 64 ? 2.1e-13 : 7e-13, t_res = 2.4e-13,
+  if (engine >= 0) return engine == 1;  // the autotuner's choice
+  // seconds per unit, measured on a GB300 (N = 512, p = 256; and N = 388, p = 1024 for the
+  // reconstruction above 64 moduli, on the 8-bit warp MMA: 0.344 ms for 1.58e9 units)
+  const double t_mma = 2.6e-15, t_crt = NM <= 64 ? 2.1e-13 : 2.2e-13, t_res = 2.4e-13,
                t_dig = 4e-12;
   const double MN = (double)M * (double)N;
   const double nw32 = 2.0 * ((16.0 * NM + 63) / 64 + 1);
@@ -3801,11 +3802,28 @@ static arbgpu_status radius_gemm(arbgpu_ctx *ctx, const BlockWs &w, uint8_t *ws,
 // Split the block [k0, k0 + Kb) and run its products: T = (E A)(B F), and the radius products
 // P1 = U(|A|) V(R_B) (when B has radii), P2 = U(R_A) V(|B| + R_B) (when A has radii).  hA, hB: the
 // largest row / column heights in the block.
-static arbgpu_status run_block(arbgpu_ctx *ctx, const BlockWs &w, uint8_t *ws, const BallsView &Av,
-                               const BallsView &Bv, int64_t M, int64_t N, int64_t lda,
-                               int64_t ldb, int64_t k0, int64_t Kb, int64_t hA, int64_t hB,
-                               bool radA, bool radB, const Lines &ln, cudaStream_t s,
-                               IntProduct *mid, IntProduct *rp1, IntProduct *rp2) {
+// Which engines can take a block product of heights hA, hB over Kb inner indices.
+static void block_engines(const BlockWs &w, int64_t Kb, int64_t hA, int64_t hB, bool *crt_ok,
+                          bool *digits_ok) {
+  const int64_t Kp = (Kb + TG_BK - 1) / TG_BK * TG_BK;
+  const int SA = digits_for_height(hA), SB = digits_for_height(hB);
+  const int NM = crt_moduli_for_bits((int)((hA > 0 ? hA : 0) + (hB > 0 ? hB : 0) +
+                                           bit_length(Kb) + 2));
+  const int nch32 = (int)(((hA > hB ? hA : hB) + 2 + 31) / 32) + 1;
+  const size_t res_smem = (size_t)NM * ((nch32 + 3) / 4 * 4) * 4;
+  const CrtPlan *plan = NM <= w.NMmax && res_smem <= 48 * 1024 ? crt_plan(NM) : nullptr;
+  *crt_ok = plan && plan->NMW + 1 <= RD_MAXW;
+  *digits_ok = SA <= w.Smax && SB <= w.Smax && digit_gemm_fits(SA, SB, Kp);
+}
+
+// engine: -1 lets the cost model choose, 0 asks for the digit engine, 1 for the multimodular one
+// (when it can take the product).
+static arbgpu_status run_block_engine(arbgpu_ctx *ctx, const BlockWs &w, uint8_t *ws,
+                                      const BallsView &Av, const BallsView &Bv, int64_t M,
+                                      int64_t N, int64_t lda, int64_t ldb, int64_t k0, int64_t Kb,
+                                      int64_t hA, int64_t hB, bool radA, bool radB,
+                                      const Lines &ln, cudaStream_t s, IntProduct *mid,
+                                      IntProduct *rp1, IntProduct *rp2, int engine) {
   const int64_t Kp = (Kb + TG_BK - 1) / TG_BK * TG_BK;
   const int SA = digits_for_height(hA), SB = digits_for_height(hB);
   const int NM = crt_moduli_for_bits((int)((hA > 0 ? hA : 0) + (hB > 0 ? hB : 0) +
@@ -3815,7 +3833,7 @@ static arbgpu_status run_block(arbgpu_ctx *ctx, const BlockWs &w, uint8_t *ws, c
   const size_t res_smem = (size_t)NM * ((nch32 + 3) / 4 * 4) * 4;  // residue kernel's table
   const bool omitted = ln.rtrunc || ln.ctrunc;  // only the tensor-core residue kernel adds the
                                                  // omission's radius
-  if ((omitted || choose_crt(SA, SB, NM, M, N, Kp, hA, hB)) && NM <= w.NMmax &&
+  if ((omitted || choose_crt(SA, SB, NM, M, N, Kp, hA, hB, engine)) && NM <= w.NMmax &&
       res_smem <= 48 * 1024) {
     plan = crt_plan(NM);
     if (plan && plan->NMW + 1 > RD_MAXW) plan = nullptr;
@@ -3940,6 +3958,73 @@ static arbgpu_status run_block(arbgpu_ctx *ctx, const BlockWs &w, uint8_t *ws, c
     digit_gemm_group_ends(SA, SB, G, mid->ends.e);
   }
   return radius_gemm(ctx, w, ws, M, N, Kp, radA, radB, s, rp1, rp2);
+}
+
+// The integer product of one block (Section IV-A) on the engine the cost model picks, or, with
+// the context's autotuner on, on the engine measured faster for the product's size bucket: the
+// first product of a bucket that both engines can take runs on both (once untimed, then timed
+// with CUDA events, the stream synchronised; never while it is being captured), the faster is
+// kept for the bucket, and the product is left as the faster engine computed it.  Both engines
+// give the same integers.
+static int ceil_log2(int64_t v) {
+  int b = 0;
+  while (((int64_t)1 << b) < v && b < 62) ++b;
+  return b;
+}
+
+static arbgpu_status run_block(arbgpu_ctx *ctx, const BlockWs &w, uint8_t *ws, const BallsView &Av,
+                               const BallsView &Bv, int64_t M, int64_t N, int64_t lda,
+                               int64_t ldb, int64_t k0, int64_t Kb, int64_t hA, int64_t hB,
+                               bool radA, bool radB, const Lines &ln, cudaStream_t s,
+                               IntProduct *mid, IntProduct *rp1, IntProduct *rp2) {
+  auto run = [&](int engine) {
+    return run_block_engine(ctx, w, ws, Av, Bv, M, N, lda, ldb, k0, Kb, hA, hB, radA, radB, ln, s,
+                            mid, rp1, rp2, engine);
+  };
+  if (!ctx->autotune || getenv("ARBGPU_ENGINE") || ln.rtrunc || ln.ctrunc) return run(-1);
+  bool crt_ok = false, digits_ok = false;
+  block_engines(w, Kb, hA, hB, &crt_ok, &digits_ok);
+  if (!crt_ok || !digits_ok) return run(-1);
+  const int64_t Kp = (Kb + TG_BK - 1) / TG_BK * TG_BK;
+  const uint64_t SA = (uint64_t)digits_for_height(hA), SB = (uint64_t)digits_for_height(hB);
+  const uint64_t NM = (uint64_t)crt_moduli_for_bits((int)((hA > 0 ? hA : 0) +
+                                                          (hB > 0 ? hB : 0) + bit_length(Kb) + 2));
+  const uint64_t key = (SA & 1023) | (SB & 1023) << 10 | (NM & 1023) << 20 |
+                       (uint64_t)ceil_log2(M) << 30 | (uint64_t)ceil_log2(N) << 36 |
+                       (uint64_t)ceil_log2(Kp) << 42;
+  const auto it = ctx->engine_tuned.find(key);
+  if (it != ctx->engine_tuned.end()) return run(it->second ? 1 : 0);
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(s, &cap) != cudaSuccess || cap != cudaStreamCaptureStatusNone)
+    return run(-1);
+  cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
+  for (auto &e : ev)
+    if (cudaEventCreate(&e) != cudaSuccess) {
+      for (auto &f : ev)
+        if (f) cudaEventDestroy(f);
+      return run(-1);
+    }
+  // one untimed run of each engine first: first-use work (table uploads, kernel attributes)
+  // stays out of the timings
+  arbgpu_status st = run(1);
+  if (st == ARBGPU_OK) st = run(0);
+  float t_crt = 0.f, t_dig = 0.f;
+  if (st == ARBGPU_OK && cudaEventRecord(ev[0], s) != cudaSuccess) st = ARBGPU_ERR_CUDA;
+  if (st == ARBGPU_OK) st = run(1);
+  if (st == ARBGPU_OK && cudaEventRecord(ev[1], s) != cudaSuccess) st = ARBGPU_ERR_CUDA;
+  if (st == ARBGPU_OK) st = run(0);
+  if (st == ARBGPU_OK && (cudaEventRecord(ev[2], s) != cudaSuccess ||
+                          cudaEventSynchronize(ev[2]) != cudaSuccess ||
+                          cudaEventElapsedTime(&t_crt, ev[0], ev[1]) != cudaSuccess ||
+                          cudaEventElapsedTime(&t_dig, ev[1], ev[2]) != cudaSuccess))
+    st = ARBGPU_ERR_CUDA;
+  for (auto &e : ev) cudaEventDestroy(e);
+  if (st != ARBGPU_OK) return st;
+  ctx->tune_runs += 4;
+  const bool crt_faster = t_crt < t_dig;
+  ctx->engine_tuned[key] = crt_faster;
+  // the digit engine ran last: its product is the one in the workspace
+  return crt_faster ? run(1) : ARBGPU_OK;
 }
 
 // Radius products alone (their operands by the digit split, then radius_gemm): those of the

@@ -37,6 +37,11 @@ struct arbgpu_ctx {
   void *pub = nullptr;
   void *pub_dev = nullptr;
   uint32_t pub_seq = 0;
+  // engine autotuner (arbgpu_set_autotune): per size bucket of a block product, whether the
+  // multimodular engine measured faster than the digit engine; products run for the timings
+  bool autotune = false;
+  std::map<uint64_t, bool> engine_tuned;
+  int64_t tune_runs = 0;
 };
 
 namespace arbgpu {
