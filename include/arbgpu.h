@@ -292,8 +292,12 @@ arbgpu_status arbgpu_mat_mul(arbgpu_ctx *ctx, const arbgpu_balls *C, const arbgp
  * item).  `descs` is a HOST array of `count` descriptors (device pointers inside).  Items that use
  * the classical algorithm (ARBGPU_ALG_DOT, or ARBGPU_ALG_AUTO below the block size) run together
  * in ONE launch of the dot kernel over a device work list (one warp per output entry, each item at
- * its own precision); the other items run the block algorithm one after the other on `stream`,
- * sharing the workspace.  Workspace: arbgpu_mat_mul_batched_workspace_size().
+ * its own precision).  The other items run the block algorithm: their scans on `stream`, one
+ * read-back of all their statistics, then the products on up to four internal streams of the
+ * context side by side (created on the first batched call that needs them; forked from `stream`
+ * and joined back into it, so work queued on `stream` afterwards sees every output).  Each
+ * internal stream has its own share of the workspace; items keep their order within a stream.
+ * Workspace: arbgpu_mat_mul_batched_workspace_size() (it covers the internal streams' shares).
  */
 typedef struct {
   arbgpu_balls C[2], A[2], B[2]; /* [1] is the imaginary part when complex_mode */

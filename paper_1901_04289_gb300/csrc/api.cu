@@ -200,6 +200,11 @@ arbgpu_status arbgpu_destroy(arbgpu_ctx *ctx) {
   for (auto &t : ctx->crt_tables) cudaFree(t.second);
   if (ctx->mapped) cudaFreeHost(ctx->mapped);
   if (ctx->pub) cudaFreeHost(ctx->pub);
+  for (int l = 0; l < arbgpu_ctx::kLanes; ++l) {
+    if (ctx->lanes[l]) cudaStreamDestroy(ctx->lanes[l]);
+    if (ctx->lane_done[l]) cudaEventDestroy(ctx->lane_done[l]);
+  }
+  if (ctx->lane_fork) cudaEventDestroy(ctx->lane_fork);
   cudaFree(ctx->status);
   delete ctx;
   return ARBGPU_OK;
@@ -407,7 +412,10 @@ arbgpu_status arbgpu_mat_mul_batched_workspace_size(arbgpu_ctx *ctx,
     blk = b > blk ? b : blk;
     scans += al256(block_scan_bytes(d.M, d.N, d.complex_mode != 0));
   }
-  *bytes = grouped + scans + blk;
+  int nblock = 0;
+  for (int32_t q = 0; q < count; ++q) nblock += item_uses_block(descs[q]) ? 1 : 0;
+  const size_t lanes = nblock < arbgpu_ctx::kLanes ? (size_t)nblock : (size_t)arbgpu_ctx::kLanes;
+  *bytes = grouped + scans + (lanes > 1 ? lanes * al256(blk) : blk);
   return ARBGPU_OK;
 }
 
@@ -511,20 +519,59 @@ arbgpu_status arbgpu_mat_mul_batched(arbgpu_ctx *ctx, const arbgpu_matmul_desc *
     std::vector<BlockStats> hstats(4 * nb);
     st = read_stats(ctx, dstats, hstats.data(), 4 * nb, s);
     if (st != ARBGPU_OK) return st;
+    // the products themselves on up to kLanes streams side by side, each with its own share of
+    // the workspace, forked from and joined back into `s`: in item order, each item goes to the
+    // lane with the least work so far (estimated as M N K (p / 64)^2)
+    const int lanes = nb < (size_t)arbgpu_ctx::kLanes ? (int)nb : arbgpu_ctx::kLanes;
+    size_t lane_bytes = ws_bytes - prod_off;
+    if (lanes > 1) {
+      lane_bytes = (ws_bytes - prod_off) / (size_t)lanes / 256 * 256;
+      if (!ctx->lane_fork && cudaEventCreateWithFlags(&ctx->lane_fork, cudaEventDisableTiming) !=
+                                 cudaSuccess)
+        return ARBGPU_ERR_CUDA;
+      for (int l = 0; l < lanes; ++l) {
+        if (!ctx->lanes[l] &&
+            (cudaStreamCreateWithFlags(&ctx->lanes[l], cudaStreamNonBlocking) != cudaSuccess ||
+             cudaEventCreateWithFlags(&ctx->lane_done[l], cudaEventDisableTiming) != cudaSuccess))
+          return ARBGPU_ERR_CUDA;
+      }
+      if (cudaEventRecord(ctx->lane_fork, s) != cudaSuccess) return ARBGPU_ERR_CUDA;
+      for (int l = 0; l < lanes; ++l)
+        if (cudaStreamWaitEvent(ctx->lanes[l], ctx->lane_fork, 0) != cudaSuccess)
+          return ARBGPU_ERR_CUDA;
+    }
+    arbgpu_status first = ARBGPU_OK;
+    double load[arbgpu_ctx::kLanes] = {};
     for (size_t i = 0; i < nb; ++i) {
       const arbgpu_matmul_desc &d = descs[block_items[i]];
+      int l = 0;
+      for (int c = 1; c < lanes; ++c)
+        if (load[c] < load[l]) l = c;
+      const double w64 = (d.prec + 63) / 64;
+      load[l] += (double)d.M * (double)d.N * (double)d.K * w64 * w64;
+      cudaStream_t ls = lanes > 1 ? ctx->lanes[l] : s;
       bool used = false;
       st = ARBGPU_ERR_LIMIT;
       if (scanned[i])
         st = block_finish(ctx, d.C, d.A, d.B, d.M, d.K, d.N, d.lda, d.ldb, d.ldc, d.prec,
                           d.complex_mode != 0, (d.flags & ARBGPU_MM_COMPLEX_3M) != 0,
                           ws + region[i], hstats.data() + 4 * i,
-                          ws + prod_off, ws_bytes - prod_off, s, &used);
+                          ws + prod_off + (size_t)l * lane_bytes, lane_bytes, ls, &used);
       if (!used && st == ARBGPU_ERR_LIMIT)
         st = launch_matmul_dot(ctx, d.C, d.A, d.B, d.M, d.K, d.N, d.lda, d.ldb, d.ldc, d.prec,
-                               d.complex_mode, s);
-      if (st != ARBGPU_OK) return st;
+                               d.complex_mode, ls);
+      if (st != ARBGPU_OK) {
+        first = st;
+        break;
+      }
     }
+    if (lanes > 1) {  // join (also after an error, so that `s` orders everything launched)
+      for (int l = 0; l < lanes; ++l)
+        if (cudaEventRecord(ctx->lane_done[l], ctx->lanes[l]) != cudaSuccess ||
+            cudaStreamWaitEvent(s, ctx->lane_done[l], 0) != cudaSuccess)
+          return ARBGPU_ERR_CUDA;
+    }
+    if (first != ARBGPU_OK) return first;
   }
   return ARBGPU_OK;
 }

@@ -42,6 +42,12 @@ struct arbgpu_ctx {
   bool autotune = false;
   std::map<uint64_t, bool> engine_tuned;
   int64_t tune_runs = 0;
+  // streams on which arbgpu_mat_mul_batched runs its block items side by side, forked from and
+  // joined back into the caller's stream (created on the first batched call that needs them)
+  static constexpr int kLanes = 4;
+  cudaStream_t lanes[kLanes] = {};
+  cudaEvent_t lane_done[kLanes] = {};
+  cudaEvent_t lane_fork = nullptr;
 };
 
 namespace arbgpu {
