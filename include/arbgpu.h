@@ -355,7 +355,14 @@ arbgpu_status arbgpu_mat_mul_workspace_size(arbgpu_ctx *ctx, int64_t M, int64_t 
  *   prec     working and output precision in bits, 2..1024
  *   workspace  device memory of at least arbgpu_series_exp_workspace_size() bytes
  * Every output ball contains the exact coefficient of the exponential of every series whose
- * coefficients lie in the input balls.  2 (len - 1) + 1 batched dot launches on `stream`.
+ * coefficients lie in the input balls.  2 (len - 1) + 1 batched dot calls, each one launch of the
+ * dot kernel (setup and evaluation fused: the dots of a call share one precision).
+ * The first call with a given set of arguments (pointers, sizes, precision, workspace) records its
+ * launches as a CUDA graph, on a private stream of the context (host time of a few milliseconds
+ * for long series), and replays it on `stream`; later calls with the same arguments only replay
+ * it.  The context keeps the four most recent graphs.  While tracing is on, while `stream` is
+ * itself being captured, or with ARBGPU_SERIES_GRAPH=0, the launches go to `stream` directly.
+ * The outputs are the same either way.
  */
 arbgpu_status arbgpu_series_exp(arbgpu_ctx *ctx, const arbgpu_balls *res, const arbgpu_balls *a,
                                 int64_t len, int64_t batch, int32_t prec, void *workspace,

@@ -205,6 +205,8 @@ arbgpu_status arbgpu_destroy(arbgpu_ctx *ctx) {
     if (ctx->lane_done[l]) cudaEventDestroy(ctx->lane_done[l]);
   }
   if (ctx->lane_fork) cudaEventDestroy(ctx->lane_fork);
+  for (auto &g : ctx->series_graphs) cudaGraphExecDestroy(g.exec);
+  if (ctx->capture_stream) cudaStreamDestroy(ctx->capture_stream);
   cudaFree(ctx->status);
   delete ctx;
   return ARBGPU_OK;

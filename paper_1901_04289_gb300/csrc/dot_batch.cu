@@ -16,7 +16,7 @@ arbgpu_status launch_batched_dot(arbgpu_ctx *ctx, const arbgpu_balls *res,
                                  const arbgpu_balls *y, const int64_t *yoff, const int64_t *ystep,
                                  const int64_t *len, const int32_t *prec, int64_t batch,
                                  int32_t prec_max, int64_t len_max, int complex_mode,
-                                 cudaStream_t stream, bool approx, bool reduce) {
+                                 cudaStream_t stream, bool approx, bool reduce, bool fused) {
   const int parts = complex_mode ? 2 : 1;
   BatchDotSrc s{};
   int maxnl = 1;
@@ -52,6 +52,11 @@ arbgpu_status launch_batched_dot(arbgpu_ctx *ctx, const arbgpu_balls *res,
   s.ndots_host = s.cplx ? 2 * batch : batch;
   const int cmax = dot_class_for_problem(prec_max, terms_max + 1, maxnl);
   if (cmax < 0) return ARBGPU_ERR_INVALID;
+  // fused: setup and evaluation of every dot in one launch of class cmax (dots of one precision,
+  // where the classes hardly differ: fewer launches for short chains of dependent calls)
+  if (fused)
+    return launch_dot_fused(ctx, s, s.cplx ? 2 * batch : batch, cmax, dot_group_batched(terms_max),
+                            stream);
   return launch_dot_src(ctx, s, s.cplx ? 2 * batch : batch, cmax, dot_group_batched(terms_max), stream);
 }
 

@@ -48,6 +48,15 @@ struct arbgpu_ctx {
   cudaStream_t lanes[kLanes] = {};
   cudaEvent_t lane_done[kLanes] = {};
   cudaEvent_t lane_fork = nullptr;
+  // arbgpu_series_exp's recurrence recorded as CUDA graphs, keyed by the call's arguments (the
+  // graphs bake the pointers in), most recent last; the private stream they are captured on
+  struct SeriesGraph {
+    std::vector<uintptr_t> key;
+    cudaGraphExec_t exec;
+    int64_t kernels;
+  };
+  std::vector<SeriesGraph> series_graphs;
+  cudaStream_t capture_stream = nullptr;
 };
 
 namespace arbgpu {
@@ -76,7 +85,8 @@ arbgpu_status launch_batched_dot(arbgpu_ctx *ctx, const arbgpu_balls *res,
                                  const arbgpu_balls *y, const int64_t *yoff, const int64_t *ystep,
                                  const int64_t *len, const int32_t *prec, int64_t batch,
                                  int32_t prec_max, int64_t len_max, int complex_mode,
-                                 cudaStream_t stream, bool approx = false, bool reduce = false);
+                                 cudaStream_t stream, bool approx = false, bool reduce = false,
+                                 bool fused = false);
 
 // Kernel (a) over rows x columns: the classical matrix product, one warp per output entry.
 arbgpu_status launch_matmul_dot(arbgpu_ctx *ctx, const arbgpu_balls *C, const arbgpu_balls *A,

@@ -209,23 +209,14 @@ arbgpu_status arbgpu_series_exp_workspace_size(arbgpu_ctx *ctx, int64_t len, int
   return ARBGPU_OK;
 }
 
-arbgpu_status arbgpu_series_exp(arbgpu_ctx *ctx, const arbgpu_balls *res, const arbgpu_balls *a,
-                                int64_t len, int64_t batch, int32_t prec, void *workspace,
-                                size_t ws_bytes, void *stream) {
-  if (!ctx || !res || !a || len < 0 || batch < 0 || prec < 2 || prec > 1024)
-    return ARBGPU_ERR_INVALID;
-  if (len == 0 || batch == 0) return ARBGPU_OK;
-  if ((int64_t)res->nlimbs * 64 < prec || res->count < len * batch || a->count < len * batch ||
-      res->limb_stride < res->count || a->limb_stride < a->count || !res->limbs || !a->limbs ||
-      !balls_ok(*res) || !balls_ok(*a) || balls_alias(*res, *a))
-    return ARBGPU_ERR_INVALID;
-  if (len > ((int64_t)1 << 24) || len * batch > ((int64_t)1 << 34)) return ARBGPU_ERR_LIMIT;
-  const int nl = (prec + 63) / 64 + 1;  // working balls: one guard limb over the output
-  const SeriesWs w = series_ws(len, batch, nl);
-  if (!workspace || ws_bytes < w.total) return ARBGPU_ERR_WORKSPACE;
-  if (cudaSetDevice(ctx->device) != cudaSuccess) return ARBGPU_ERR_CUDA;
-  cudaStream_t s = (cudaStream_t)stream;
-  uint8_t *ws = (uint8_t *)workspace;
+}  // extern "C"
+
+namespace {
+
+// The launches of one exponential call (checked arguments) on stream s.
+arbgpu_status series_exp_launches(arbgpu_ctx *ctx, const arbgpu_balls *res, const arbgpu_balls *a,
+                                  int64_t len, int64_t batch, int32_t prec, uint8_t *ws,
+                                  const SeriesWs &w, int nl, cudaStream_t s) {
   const int64_t n = len * batch;
   const unsigned gn = (unsigned)((n + 255) / 256), gl = (unsigned)((len + 255) / 256);
   arbgpu_balls ap = ball_at(ws + w.ap, n, nl), jb = ball_at(ws + w.jb, len, 1);
@@ -266,7 +257,8 @@ arbgpu_status arbgpu_series_exp(arbgpu_ctx *ctx, const arbgpu_balls *res, const 
   for (int64_t k = 1; k < len; ++k) {
     const int64_t o = k * batch;
     st = launch_batched_dot(ctx, &c, nullptr, nullptr, &ap, d.xoff + o, d.xstep + o, res,
-                            d.yoff + o, d.ystep + o, d.len + o, d.prec + o, batch, prec, k, 0, s);
+                            d.yoff + o, d.ystep + o, d.len + o, d.prec + o, batch, prec, k, 0, s,
+                            false, false, true);
     if (st != ARBGPU_OK) return st;
     arbgpu_balls rk = *res;  // coefficient k of every series: indices [k batch, (k + 1) batch)
     rk.limbs += o;
@@ -276,9 +268,86 @@ arbgpu_status arbgpu_series_exp(arbgpu_ctx *ctx, const arbgpu_balls *res, const 
     rk.rad_exp += o;
     rk.count = batch;
     st = launch_batched_dot(ctx, &rk, nullptr, nullptr, &c, d.cxoff + o, d.zero + o, &inv,
-                            d.cyoff + o, d.zero + o, d.one + o, d.prec + o, batch, prec, 1, 0, s);
+                            d.cyoff + o, d.zero + o, d.one + o, d.prec + o, batch, prec, 1, 0, s,
+                            false, false, true);
     if (st != ARBGPU_OK) return st;
   }
+  return ARBGPU_OK;
+}
+
+constexpr size_t SERIES_GRAPHS_KEPT = 4;
+
+}  // namespace
+
+extern "C" {
+
+arbgpu_status arbgpu_series_exp(arbgpu_ctx *ctx, const arbgpu_balls *res, const arbgpu_balls *a,
+                                int64_t len, int64_t batch, int32_t prec, void *workspace,
+                                size_t ws_bytes, void *stream) {
+  if (!ctx || !res || !a || len < 0 || batch < 0 || prec < 2 || prec > 1024)
+    return ARBGPU_ERR_INVALID;
+  if (len == 0 || batch == 0) return ARBGPU_OK;
+  if ((int64_t)res->nlimbs * 64 < prec || res->count < len * batch || a->count < len * batch ||
+      res->limb_stride < res->count || a->limb_stride < a->count || !res->limbs || !a->limbs ||
+      !balls_ok(*res) || !balls_ok(*a) || balls_alias(*res, *a))
+    return ARBGPU_ERR_INVALID;
+  if (len > ((int64_t)1 << 24) || len * batch > ((int64_t)1 << 34)) return ARBGPU_ERR_LIMIT;
+  const int nl = (prec + 63) / 64 + 1;  // working balls: one guard limb over the output
+  const SeriesWs w = series_ws(len, batch, nl);
+  if (!workspace || ws_bytes < w.total) return ARBGPU_ERR_WORKSPACE;
+  if (cudaSetDevice(ctx->device) != cudaSuccess) return ARBGPU_ERR_CUDA;
+  cudaStream_t s = (cudaStream_t)stream;
+  uint8_t *ws = (uint8_t *)workspace;
+  // Replay of the recorded launches when this call's arguments were seen before; direct launches
+  // while tracing, while `s` is itself being captured, or with ARBGPU_SERIES_GRAPH=0.
+  const char *e = getenv("ARBGPU_SERIES_GRAPH");
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (ctx->trace || (e && !strcmp(e, "0")) || cudaStreamIsCapturing(s, &cap) != cudaSuccess ||
+      cap != cudaStreamCaptureStatusNone)
+    return series_exp_launches(ctx, res, a, len, batch, prec, ws, w, nl, s);
+  const std::vector<uintptr_t> key{
+      (uintptr_t)res->limbs, (uintptr_t)res->exp,     (uintptr_t)res->flags,
+      (uintptr_t)res->rad_man, (uintptr_t)res->rad_exp, (uintptr_t)res->limb_stride,
+      (uintptr_t)res->nlimbs, (uintptr_t)a->limbs,     (uintptr_t)a->exp,
+      (uintptr_t)a->flags,   (uintptr_t)a->rad_man,   (uintptr_t)a->rad_exp,
+      (uintptr_t)a->limb_stride, (uintptr_t)a->nlimbs, (uintptr_t)len,
+      (uintptr_t)batch,      (uintptr_t)prec,         (uintptr_t)workspace};
+  auto &gs = ctx->series_graphs;
+  for (size_t q = 0; q < gs.size(); ++q)
+    if (gs[q].key == key) {
+      if (cudaGraphLaunch(gs[q].exec, s) != cudaSuccess) return ARBGPU_ERR_CUDA;
+      ctx->launches += gs[q].kernels;
+      return ARBGPU_OK;
+    }
+  // record: the launches on a private stream under capture, then one replay on `s`
+  if (!ctx->capture_stream &&
+      cudaStreamCreateWithFlags(&ctx->capture_stream, cudaStreamNonBlocking) != cudaSuccess)
+    return ARBGPU_ERR_CUDA;
+  cudaStream_t cs = ctx->capture_stream;
+  if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+    return ARBGPU_ERR_CUDA;
+  const int64_t l0 = ctx->launches;
+  const arbgpu_status st = series_exp_launches(ctx, res, a, len, batch, prec, ws, w, nl, cs);
+  cudaGraph_t graph = nullptr;
+  const cudaError_t ce = cudaStreamEndCapture(cs, &graph);
+  const int64_t kernels = ctx->launches - l0;
+  ctx->launches = l0;  // counted when the graph runs
+  if (st != ARBGPU_OK || ce != cudaSuccess || !graph) {
+    if (graph) cudaGraphDestroy(graph);
+    cudaGetLastError();
+    return st != ARBGPU_OK ? st : ARBGPU_ERR_CUDA;
+  }
+  cudaGraphExec_t exec = nullptr;
+  const cudaError_t ie = cudaGraphInstantiate(&exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (ie != cudaSuccess) return ARBGPU_ERR_CUDA;
+  if (gs.size() >= SERIES_GRAPHS_KEPT) {
+    cudaGraphExecDestroy(gs.front().exec);
+    gs.erase(gs.begin());
+  }
+  gs.push_back({key, exec, kernels});
+  if (cudaGraphLaunch(exec, s) != cudaSuccess) return ARBGPU_ERR_CUDA;
+  ctx->launches += kernels;
   return ARBGPU_OK;
 }
 

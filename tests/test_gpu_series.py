@@ -89,3 +89,33 @@ def test_series_exp_argument_errors(arb):
         arb.series_exp(arb.Balls.empty(10, 1), A, 5, 2, 128)  # output narrower than prec
     with pytest.raises(_lib.ArbgpuError):
         arb.series_exp(A, A, 5, 2, 128)  # aliasing
+
+
+def test_series_graph_replay_matches_direct_launches(arb):
+    """The recurrence's launches are recorded as a CUDA graph on the first call with given buffers
+    and replayed by later identical calls: the replays write the same balls, bit for bit, as
+    direct launches (ARBGPU_SERIES_GRAPH=0), and count the same kernels."""
+    import contextlib
+
+    from tests.gpu_util import env
+    rng = np.random.default_rng(4242)
+    prec, length, batch = 128, 30, 64
+    A = random_balls(rng, length * batch, 2, 128, -3, 1, rad_bits=120, rad_zero_frac=0.5)
+    ctx = arb.Context(0)
+    a = arb.Balls.from_raw(A)
+    res = arb.Balls.empty(length * batch, 2)
+    outs, counts = [], []
+    for mode in ("record", "replay", "direct"):
+        for t in (res.limbs, res.exp, res.flags, res.rad_man, res.rad_exp):
+            t.fill_(7)  # stale contents: each call must write every output
+        n0 = ctx.launch_count()
+        with (env(ARBGPU_SERIES_GRAPH="0") if mode == "direct" else contextlib.nullcontext()):
+            arb.series_exp(res, a, length, batch, prec, ctx=ctx)
+        assert ctx.status() == 0
+        counts.append(ctx.launch_count() - n0)
+        outs.append(to_raw(res))
+    assert counts[0] == counts[1] == counts[2] > 2 * length
+    for o in outs[1:]:
+        for f in ("limbs", "exp", "flags", "rad_man", "rad_exp"):
+            assert np.array_equal(getattr(o, f), getattr(outs[0], f)), f
+    _check(outs[0], A, length, batch, prec, range(0, batch, 9), 12)
