@@ -367,7 +367,7 @@ def run_workload(args):
     from oracle import exact as X
     from synth import SEED_BASE
     from synth.workloads import (batched_dots, complex_matmul_laplace, dot_matmul_n32_p128,
-                                 grouped_matmuls)
+                                 grouped_matmuls, matmul_uniform)
     from tests.gpu_util import batch_tensors
 
     torch.cuda.set_device(0)
@@ -422,7 +422,7 @@ def run_workload(args):
                 terms += int(bt.length[b])
             dt = time.perf_counter() - t0
             return terms / dt, f"{done} dots ({terms} terms) in {dt:.1f} s", dt
-    elif wl.startswith("complex2048"):
+    elif wl in ("complex2048", "complex2048_literal"):
         case = complex_matmul_laplace(structured=(wl == "complex2048"))
         n = case.N
         A = [arb.Balls.from_raw(a) for a in case.A]
@@ -447,6 +447,42 @@ def run_workload(args):
                                              [k * n + j for k in range(n)])
                 X.result_exact(re, 128, 2)
                 X.result_exact(im, 128, 2)
+                done += 1
+            dt = time.perf_counter() - t0
+            return done * n / dt, f"{done} complex entries x {n} terms in {dt:.1f} s", dt
+    elif wl == "complex2048_uniform":
+        # complex N = 2048, p = 128, uniform exponents: the parts' shared scaling fits one block,
+        # so --complex-3m takes eq. 2 (three real products) instead of four
+        n, prec = 2048, 128
+        parts = [matmul_uniform(SEED_BASE + 6 + q, n, prec, -20, 20, rad_bits=120)
+                 for q in range(2)]
+        cA = [parts[0].A[0], parts[1].A[0]]
+        cB = [parts[0].B[0], parts[1].B[0]]
+        A = [arb.Balls.from_raw(a) for a in cA]
+        B = [arb.Balls.from_raw(b) for b in cB]
+        C = [arb.Balls.empty(n * n, 2), arb.Balls.empty(n * n, 2)]
+        mflags = arb.MM_COMPLEX_3M if args.complex_3m else 0
+        need = arb.mat_mul_workspace_size(n, n, n, prec, 2, 2, True, arb.ALG_AUTO, mflags)
+        ws = torch.empty(max(need, 1), dtype=torch.uint8, device="cuda")
+
+        def step():
+            arb.mat_mul(C, A, B, n, n, n, prec, flags=mflags, workspace=ws, ctx=ctx)
+        macs = n ** 3
+        name = (f"complex ball matmul N=2048 p=128, uniform exponents U[-20,20], radii 2^-120 "
+                f"relative, {'eq. 2 (3M)' if args.complex_3m else 'four real products (4M)'}")
+        inbytes = sum(b.nbytes() for b in A + B)
+        outbytes = sum(c.nbytes() for c in C)
+
+        def cpu_fn(limit):
+            rng = np.random.default_rng(0)
+            done = 0
+            t0 = time.perf_counter()
+            while time.perf_counter() - t0 < limit:
+                i, j = int(rng.integers(n)), int(rng.integers(n))
+                re, im = X.complex_dot_terms(cA, [i * n + k for k in range(n)], cB,
+                                             [k * n + j for k in range(n)])
+                X.result_exact(re, prec, 2)
+                X.result_exact(im, prec, 2)
                 done += 1
             dt = time.perf_counter() - t0
             return done * n / dt, f"{done} complex entries x {n} terms in {dt:.1f} s", dt
@@ -635,6 +671,9 @@ def main():
     ap.add_argument("--no-compare", action="store_true", help="skip the p=128 / dot-path lines")
     ap.add_argument("--ref-entries", type=int, default=48)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--complex-3m", action="store_true",
+                    help="complex2048_uniform only: the complex product by eq. 2 (three real "
+                         "products)")
     ap.add_argument("--autotune", action="store_true",
                     help="turn on the library's engine autotuner (the warm-up steps decide)")
     ap.add_argument("--items", default="",
@@ -642,7 +681,7 @@ def main():
                          "the whole batch")
     ap.add_argument("--workload", default="n512",
                     choices=["n512", "n32dots", "dots", "complex2048", "complex2048_literal",
-                             "series", "grouped"],
+                             "complex2048_uniform", "series", "grouped"],
                     help="n512 (default): the headline; the others are the remaining synthetic "
                          "workloads, one JSON line each")
     args = ap.parse_args()
