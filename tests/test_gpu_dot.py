@@ -104,6 +104,22 @@ def test_batched_dots_bit_exact_vs_alg1(arb, k):
     assert not bad, f"{len(bad)} mismatches, first: {bad[:2]}"
 
 
+@pytest.mark.parametrize("k", [0, 1, 2, 6])
+def test_fused_launch_agrees_with_class_launches(arb, k):
+    """Batches whose largest size class is small run setup and evaluation in one fused launch;
+    the setup launch plus one launch per class (ARBGPU_DOT_FUSED=0) gives the same balls, bit for
+    bit, and the same status."""
+    from tests.gpu_util import env
+    batch = small_batch(**SMALL[k])
+    nl_out = (int(batch.prec.max()) + 63) // 64
+    fused, st1 = run_batch(arb, batch, nl_out)
+    with env(ARBGPU_DOT_FUSED="0"):
+        split, st2 = run_batch(arb, batch, nl_out)
+    assert st1 == st2 == 0
+    for f in ("limbs", "exp", "flags", "rad_man", "rad_exp"):
+        assert np.array_equal(getattr(fused, f), getattr(split, f)), f
+
+
 @pytest.mark.parametrize("k", [1, 2, 4, 5])
 def test_reduced_precision_dots_bit_exact_vs_alg1(arb, k):
     """ARBGPU_DOT_REDUCE_PREC (Section III-C, "optimize p"): every output field equals the Algorithm 1
