@@ -236,9 +236,15 @@ arbgpu_status arbgpu_approx_dot(arbgpu_ctx *ctx, const arbgpu_balls *res,
 /* Complex midpoints by eq. 2 (Section IV-C): when one exponent per row of A and per column of B,
  * shared by the real and imaginary parts, scales both parts to integers within one block of
  * Algorithm 2, Re = Ar Br - Ai Bi and Im = (Ar + Ai)(Br + Bi) - Ar Br - Ai Bi are formed exactly
- * from three integer products instead of four; radii come from the four real radius products as
- * without the flag.  Otherwise (several blocks, or the dot path) the flag changes nothing.  Any
- * other flag bit is ARBGPU_ERR_INVALID. */
+ * from three integer products instead of four and rounded once; radii come from the four real
+ * radius products as without the flag.  When the shared scaling needs several blocks, the inner
+ * range is cut once for both parts (Section IV-C's second suggestion: the greedy extraction on
+ * the larger top and the smaller bottom of each entry's two parts, over an inner order and
+ * scaling shared by the parts when the inner ordering is on); each full block's Re and Im come
+ * from three exact products and are added into the parts' window accumulators, the basecase
+ * blocks become complex dot products.  Blocks the tensor-core residue kernel cannot take (more
+ * than 32 chunks or 128 moduli) leave the four real products in place, and the dot path ignores
+ * the flag.  Any other flag bit is ARBGPU_ERR_INVALID. */
 #define ARBGPU_MM_COMPLEX_3M 1u
 
 /*
@@ -322,14 +328,18 @@ arbgpu_status arbgpu_mat_mul_batched_workspace_size(arbgpu_ctx *ctx,
  * that ran the block algorithm, in the order they ran (a complex product by four real products
  * gives Ar Br, Ai Bi, Ar Bi, Ai Br; batched items in item order):
  *   kind   0: blocks over the inner index in its own order; 1: over the inner ordering (the
- *          block positions index the order listed after the triples); 2: the one block of a
- *          complex product by eq. 2 (ARBGPU_MM_COMPLEX_3M) shared by both parts; 3: one block
- *          of the operands with their negligible limbs omitted (see arbgpu_mat_mul)
+ *          block positions index the order listed after the triples); 2: the blocks of a
+ *          complex product by eq. 2 (ARBGPU_MM_COMPLEX_3M) shared by both parts, planned on
+ *          the larger top and smaller bottom of each entry's two parts (Section IV-C; one record
+ *          for the whole complex product); 3: one block of the operands with their negligible
+ *          limbs omitted (see arbgpu_mat_mul); 4: the shared blocks of kind 2 over an inner
+ *          order and scaling shared by both parts (listed as for kind 1)
  *   h      the height bound, floor(1.25 min(p, max(p_A, p_B))) + 192
  *   K      the inner dimension
  *   nb     the number of blocks, then nb triples (start, stop, basecase): [start, stop) covers
  *          positions of the inner index; basecase = 1 for a block done by dot products
- *   kind 1 only: K positions' inner indices (the order), then K inner scaling exponents g_k
+ *   kinds 1 and 4 only: K positions' inner indices (the order), then K inner scaling
+ *          exponents g_k
  * `words` receives the first min(n, max_words) words; *n_words is set to n.  A call that took
  * the classical algorithm leaves no record.
  */

@@ -194,8 +194,8 @@ class Context:
 
     def last_plans(self):
         """The block plans of the last matrix-product call (``arbgpu_last_plans``), one dict per
-        real product: kind, h, K, blocks [(start, stop, basecase)], and for kind 1 the inner
-        order and the scaling exponents."""
+        real product: kind, h, K, blocks [(start, stop, basecase)], and for kinds 1 and 4 the
+        inner order and the scaling exponents."""
         n = C.c_int64(0)
         rc = _lib.lib().arbgpu_last_plans(self.handle, None, 0, C.byref(n))
         if rc != 0:
@@ -212,7 +212,7 @@ class Context:
             blocks = [(w[q + 3 * b], w[q + 3 * b + 1], bool(w[q + 3 * b + 2])) for b in range(nb)]
             q += 3 * nb
             rec = dict(kind=kind, h=h, K=K, blocks=blocks)
-            if kind == 1:
+            if kind in (1, 4):
                 rec["order"] = w[q:q + K]
                 rec["g"] = w[q + K:q + 2 * K]
                 q += 2 * K

@@ -2994,15 +2994,22 @@ static void launch_block_round(arbgpu_ctx *ctx, const RoundArgs &ra, cudaStream_
 
 // ------------------------------------------------------------------------- several blocks
 
-// Per-entry top / bottom exponents (INT64_MIN / INT64_MAX for zeros) for the planner.
+// Per-entry top / bottom exponents (INT64_MIN / INT64_MAX for zeros) for the planner.  With
+// `merge`, the larger top and the smaller bottom of this operand's and the values already in
+// top / bot (the other part of a complex operand: both parts of an entry share one scaling).
 __global__ void entry_tb_kernel(const BallsView X, int64_t rows, int64_t cols, int64_t ld,
-                                int64_t *top, int64_t *bot) {
+                                int64_t *top, int64_t *bot, int merge) {
   const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= rows * cols) return;
   const int64_t r = idx / cols, c = idx - (idx / cols) * cols;
   EntryScan e = scan_entry(X, r * ld + c);
-  top[idx] = e.nz ? e.top : INT64_MIN;
-  bot[idx] = e.nz ? e.bot : INT64_MAX;
+  int64_t t = e.nz ? e.top : INT64_MIN, b = e.nz ? e.bot : INT64_MAX;
+  if (merge) {
+    t = max((long long)t, (long long)top[idx]);
+    b = min((long long)b, (long long)bot[idx]);
+  }
+  top[idx] = t;
+  bot[idx] = b;
 }
 
 // The same per-entry exponents of a K x N operand, written transposed ([N][K]: column j of the
@@ -3010,7 +3017,7 @@ __global__ void entry_tb_kernel(const BallsView X, int64_t rows, int64_t cols, i
 // planner walks -- a row of A or a column of B -- is contiguous.
 __global__ void __launch_bounds__(256) entry_tb_t_kernel(const BallsView X, int64_t K, int64_t N,
                                                          int64_t ld, int64_t *topT,
-                                                         int64_t *botT) {
+                                                         int64_t *botT, int merge) {
   __shared__ int64_t st[32][33], sb[32][33];
   const int64_t tiles_n = (N + 31) / 32;
   const int64_t k0 = ((int64_t)blockIdx.x / tiles_n) * 32, j0 = ((int64_t)blockIdx.x % tiles_n) * 32;
@@ -3032,8 +3039,13 @@ __global__ void __launch_bounds__(256) entry_tb_t_kernel(const BallsView X, int6
   for (int r = ty; r < 32; r += 8) {
     const int64_t j = j0 + r, k = k0 + tx;
     if (j < N && k < K) {
-      topT[j * K + k] = st[tx][r];
-      botT[j * K + k] = sb[tx][r];
+      int64_t t = st[tx][r], b = sb[tx][r];
+      if (merge) {
+        t = max((long long)t, (long long)topT[j * K + k]);
+        b = min((long long)b, (long long)botT[j * K + k]);
+      }
+      topT[j * K + k] = t;
+      botT[j * K + k] = b;
     }
   }
 }
@@ -3404,12 +3416,17 @@ __global__ void acc_to_ball_kernel(const AccView v, BallsOut I, int64_t M, int64
 // The shared scaling of a complex operand's two parts: eq. 2 forms X_re + X_im, so both parts of a
 // row of A (a column of B) take one exponent.  Line tops are the larger, bottoms the smaller of
 // the parts' (an empty line has top INT64_MIN and bottom INT64_MAX); st receives the largest row
-// height (hA) and column height (hB), INT64_MIN when every line is empty.  One CTA.
+// height (hA) and column height (hB), INT64_MIN when every line is empty.  One CTA per block of a
+// plan: CTA b merges the lines of block b (rows at b M, columns at b N) into st[b].
 __global__ void __launch_bounds__(1024) merge_parts_kernel(
     const int64_t *rtop0, const int64_t *rbot0, const int64_t *rtop1, const int64_t *rbot1,
     int64_t M, int64_t *rtop, int64_t *rbot, const int64_t *ctop0, const int64_t *cbot0,
     const int64_t *ctop1, const int64_t *cbot1, int64_t N, int64_t *ctop, int64_t *cbot,
     BlockStats *st) {
+  const int64_t oM = (int64_t)blockIdx.x * M, oN = (int64_t)blockIdx.x * N;
+  rtop0 += oM, rbot0 += oM, rtop1 += oM, rbot1 += oM, rtop += oM, rbot += oM;
+  ctop0 += oN, cbot0 += oN, ctop1 += oN, cbot1 += oN, ctop += oN, cbot += oN;
+  st += blockIdx.x;
   __shared__ long long s_h[2];
   if (threadIdx.x < 2) s_h[threadIdx.x] = INT64_MIN;
   __syncthreads();
@@ -3589,8 +3606,13 @@ struct BlockWs {
   size_t eprod, om_rbot, om_rrad, om_rtrunc, om_cbot, om_crad, om_cplus, om_ctrunc, om_stats;
   // multimodular engine: residue planes, residue products, tables
   size_t resA, resB, cdig, ccar, craw;
-  // complex product by eq. 2: residue planes of the parts and their sum, three residue products
+  // complex product by eq. 2: residue planes of the parts and their sum, three residue products;
+  // over several blocks, the imaginary parts' per-block lines (the real parts' take the
+  // b* arrays), the lines shared by both parts, the per-block statistics of the imaginary parts
+  // and of the shared lines, and (inner order) the reordered imaginary parts
   size_t r3A, r3B, z3;
+  size_t e2rtop, e2rbot, e2rrad, e2ctop, e2cbot, e2crad, e2cplus;
+  size_t e2srtop, e2srbot, e2sctop, e2scbot, e2stats, e2mstats, oA2, oB2;
   // inner ordering (Section IV-B): per-index tops, the order and scaling, the reordered operands,
   // the range flag of the scaled exponents
   size_t ia, ib, iord, ig, oA, oB, irange;
@@ -3697,6 +3719,24 @@ static BlockWs block_ws(arbgpu_ctx *ctx, int64_t M, int64_t K, int64_t N, int pr
     w.r3A = take((size_t)3 * 2 * w.NMmax * M * w.Kp * 2);
     w.r3B = take((size_t)3 * 2 * w.NMmax * N * w.Kp * 2);
     w.z3 = take((size_t)3 * w.NMmax * w.Mp * w.Np * 2);
+    const size_t bm = 8 * (size_t)w.maxb * M, bn = 8 * (size_t)w.maxb * N;
+    w.e2rtop = take(bm);
+    w.e2rbot = take(bm);
+    w.e2rrad = take(bm);
+    w.e2ctop = take(bn);
+    w.e2cbot = take(bn);
+    w.e2crad = take(bn);
+    w.e2cplus = take(bn);
+    w.e2srtop = take(bm);
+    w.e2srbot = take(bm);
+    w.e2sctop = take(bn);
+    w.e2scbot = take(bn);
+    w.e2stats = take(sizeof(BlockStats) * (size_t)w.maxb);
+    w.e2mstats = take(sizeof(BlockStats) * (size_t)w.maxb);
+    if (w.oA) {
+      w.oA2 = take(ball_array_bytes(M * K, nlA < 1 || nlA > BL_MAX_NL ? BL_MAX_NL : nlA));
+      w.oB2 = take(ball_array_bytes(K * N, nlB < 1 || nlB > BL_MAX_NL ? BL_MAX_NL : nlB));
+    }
   }
   w.total = off;
   return w;
@@ -4082,11 +4122,12 @@ static int64_t height_bound(int prec, const BlockStats &hs) {
 static arbgpu_status entry_tops(arbgpu_ctx *ctx, const BallsView &Xv, const BallsView &Yv,
                                 int64_t M, int64_t K, int64_t N, int64_t ldx, int64_t ldy,
                                 int64_t *tA, int64_t *bA, int64_t *tBT, int64_t *bBT,
-                                cudaStream_t s) {
+                                cudaStream_t s, bool merge = false) {
   LaunchScope sc(ctx, s, "entry_tb", M * K + K * N);
-  entry_tb_kernel<<<(unsigned)((M * K + 255) / 256), 256, 0, s>>>(Xv, M, K, ldx, tA, bA);
+  entry_tb_kernel<<<(unsigned)((M * K + 255) / 256), 256, 0, s>>>(Xv, M, K, ldx, tA, bA,
+                                                                    merge ? 1 : 0);
   const int64_t tiles = ((K + 31) / 32) * ((N + 31) / 32);
-  entry_tb_t_kernel<<<(unsigned)tiles, 256, 0, s>>>(Yv, K, N, ldy, tBT, bBT);
+  entry_tb_t_kernel<<<(unsigned)tiles, 256, 0, s>>>(Yv, K, N, ldy, tBT, bBT, merge ? 1 : 0);
   return cudaGetLastError() == cudaSuccess ? ARBGPU_OK : ARBGPU_ERR_CUDA;
 }
 
@@ -4266,6 +4307,43 @@ struct DirectRound {
 // Add (-1)^negate X Y to the accumulator by Algorithm 2: plan the blocks of this product, run the
 // products of the full blocks and accumulate them; append the basecase indices, tagged with
 // `combo`, to `basek`.
+// The greedy extraction of Algorithm 2 on the per-entry tops and bottoms in the workspace (tA / bA
+// for the rows of X, tB / bB for the columns of Y, from entry_tops): one cooperative launch, then
+// the [start, stop, basecase] triples read back into hb (the plan stays at w.blocks).
+static arbgpu_status plan_blocks(arbgpu_ctx *ctx, const BlockWs &w, uint8_t *ws, int64_t M,
+                                 int64_t K, int64_t N, int64_t h, cudaStream_t s,
+                                 std::vector<int32_t> &hb) {
+  int64_t *tA = (int64_t *)(ws + w.tA), *bA = (int64_t *)(ws + w.bA);
+  int64_t *tBT = (int64_t *)(ws + w.tB), *bBT = (int64_t *)(ws + w.bB);
+  int32_t *blocks = (int32_t *)(ws + w.blocks), *nblocks = (int32_t *)(ws + w.nblocks);
+  {
+    int *state = (int *)(nblocks + 2);
+    unsigned *bar = (unsigned *)(nblocks + 4);
+    int *failed = (int *)(nblocks + 6);
+    int64_t hh = h;
+    int maxb = w.maxb;
+    int *status = ctx->status;
+    void *args[] = {&tA, &bA, &tBT, &bBT, &M, &K, &N, &hh, &blocks, &nblocks, &maxb,
+                    &state, &bar, &failed, &status};
+    const int grid = plan_coop_grid(ctx->device, M + N);
+    if (grid < 1 || cudaMemsetAsync(nblocks, 0, 32, s) != cudaSuccess) return ARBGPU_ERR_CUDA;
+    LaunchScope sc(ctx, s, "plan", M + N);
+    if (cudaLaunchCooperativeKernel((const void *)plan_coop_kernel, dim3(grid), dim3(256), args,
+                                    0, s) != cudaSuccess)
+      return ARBGPU_ERR_CUDA;
+  }
+  int32_t nb = 0;
+  if (cudaMemcpyAsync(&nb, nblocks, 4, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess)
+    return ARBGPU_ERR_CUDA;
+  if (nb < 1 || nb > w.maxb) return ARBGPU_ERR_LIMIT;
+  hb.assign(3 * (size_t)nb, 0);
+  if (cudaMemcpyAsync(hb.data(), blocks, 12 * (size_t)nb, cudaMemcpyDeviceToHost, s) !=
+      cudaSuccess)
+    return ARBGPU_ERR_CUDA;
+  return ARBGPU_OK;
+}
+
 static arbgpu_status accumulate_product(arbgpu_ctx *ctx, const BlockWs &w, uint8_t *ws,
                                         const BallsView &Xv, const BallsView &Yv, int64_t M,
                                         int64_t K, int64_t N, int64_t ldx, int64_t ldy, int prec,
@@ -4289,40 +4367,18 @@ static arbgpu_status accumulate_product(arbgpu_ctx *ctx, const BlockWs &w, uint8
     hbs = {hs};
     log_plan(ctx, plan_kind, h, K, hb);
   } else {
-    int64_t *tA = (int64_t *)(ws + w.tA), *bA = (int64_t *)(ws + w.bA);
-    int64_t *tBT = (int64_t *)(ws + w.tB), *bBT = (int64_t *)(ws + w.bB);
-    int32_t *blocks = (int32_t *)(ws + w.blocks), *nblocks = (int32_t *)(ws + w.nblocks);
-    const arbgpu_status est = entry_tops(ctx, Xv, Yv, M, K, N, ldx, ldy, tA, bA, tBT, bBT, s);
+    const arbgpu_status est = entry_tops(ctx, Xv, Yv, M, K, N, ldx, ldy, (int64_t *)(ws + w.tA),
+                                         (int64_t *)(ws + w.bA), (int64_t *)(ws + w.tB),
+                                         (int64_t *)(ws + w.bB), s);
     if (est != ARBGPU_OK) return est;
-    {
-      int *state = (int *)(nblocks + 2);
-      unsigned *bar = (unsigned *)(nblocks + 4);
-      int *failed = (int *)(nblocks + 6);
-      int64_t hh = h;
-      int maxb = w.maxb;
-      int *status = ctx->status;
-      void *args[] = {&tA, &bA, &tBT, &bBT, &M, &K, &N, &hh, &blocks, &nblocks, &maxb,
-                      &state, &bar, &failed, &status};
-      const int grid = plan_coop_grid(ctx->device, M + N);
-      if (grid < 1 || cudaMemsetAsync(nblocks, 0, 32, s) != cudaSuccess) return ARBGPU_ERR_CUDA;
-      LaunchScope sc(ctx, s, "plan", M + N);
-      if (cudaLaunchCooperativeKernel((const void *)plan_coop_kernel, dim3(grid), dim3(256), args,
-                                      0, s) != cudaSuccess)
-        return ARBGPU_ERR_CUDA;
-    }
-    int32_t nb = 0;
-    if (cudaMemcpyAsync(&nb, nblocks, 4, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
-        cudaStreamSynchronize(s) != cudaSuccess)
-      return ARBGPU_ERR_CUDA;
-    if (nb < 1 || nb > w.maxb) return ARBGPU_ERR_LIMIT;
-    hnb = nb;
-    hb.assign(3 * (size_t)hnb, 0);
+    const arbgpu_status pst = plan_blocks(ctx, w, ws, M, K, N, h, s, hb);
+    if (pst != ARBGPU_OK) return pst;
+    hnb = (int)(hb.size() / 3);
     hbs.assign((size_t)hnb, init);
     BlockStats *bst = (BlockStats *)(ws + w.bstats);
-    if (cudaMemcpyAsync(hb.data(), blocks, 12 * (size_t)hnb, cudaMemcpyDeviceToHost, s) !=
-            cudaSuccess ||
-        cudaMemcpyAsync(bst, hbs.data(), sizeof(BlockStats) * hnb, cudaMemcpyHostToDevice, s) !=
-            cudaSuccess)
+    const int32_t *blocks = (const int32_t *)(ws + w.blocks);
+    if (cudaMemcpyAsync(bst, hbs.data(), sizeof(BlockStats) * hnb, cudaMemcpyHostToDevice, s) !=
+        cudaSuccess)
       return ARBGPU_ERR_CUDA;
     per = Lines{(int64_t *)(ws + w.brtop), (int64_t *)(ws + w.brbot), (int64_t *)(ws + w.brrad),
                 (int64_t *)(ws + w.bctop), (int64_t *)(ws + w.bcbot), (int64_t *)(ws + w.bcrad),
@@ -4450,6 +4506,7 @@ static arbgpu_status accumulate_product(arbgpu_ctx *ctx, const BlockWs &w, uint8
 // The radii are the four real radius products of the 4M path.
 struct Plan3M {
   bool ok;
+  bool several;  // the shared scaling needs several blocks (accumulate_eq2)
   int64_t hA, hB;
   int NM, nch;
   const CrtPlan *plan;
@@ -4464,6 +4521,7 @@ static arbgpu_status plan_3m(arbgpu_ctx *ctx, const BlockWs &w, uint8_t *ws, con
                              const Lines *colsL, const BlockStats *hst, int64_t M, int64_t K,
                              int64_t N, int prec, cudaStream_t s, Plan3M *p) {
   p->ok = false;
+  p->several = false;
   if (!w.r3A) return ARBGPU_OK;
   p->rtop = (int64_t *)(ws + w.brtop);
   p->rbot = (int64_t *)(ws + w.brbot);
@@ -4486,7 +4544,10 @@ static arbgpu_status plan_3m(arbgpu_ctx *ctx, const BlockWs &w, uint8_t *ws, con
   hs.pA = hst[0].pA > hst[1].pA ? hst[0].pA : hst[1].pA;
   hs.pB = hst[2].pB > hst[3].pB ? hst[2].pB : hst[3].pB;
   const int64_t h = height_bound(prec, hs);
-  if (hm.hA > h || hm.hB > h) return ARBGPU_OK;
+  if (hm.hA > h || hm.hB > h) {
+    p->several = true;
+    return ARBGPU_OK;
+  }
   p->hA = hm.hA;
   p->hB = hm.hB;
   p->NM = crt_moduli_for_bits((int)(p->hA + p->hB + bit_length(K) + 3));
@@ -4500,40 +4561,42 @@ static arbgpu_status plan_3m(arbgpu_ctx *ctx, const BlockWs &w, uint8_t *ws, con
   return ARBGPU_OK;
 }
 
-// Run the planned eq. 2 product: the radius bounds of each part summed into av[q].rman / rexp
-// (zeroed by the caller), then Re and Im reconstructed and rounded straight into C[0], C[1].
-static arbgpu_status run_3m(arbgpu_ctx *ctx, const BlockWs &w, uint8_t *ws, const Plan3M &p,
-                            const arbgpu_balls *C, const BallsView *Av, const BallsView *Bv,
-                            const Lines *rowsL, const Lines *colsL, const BlockStats *hst,
-                            int64_t M, int64_t K, int64_t N, int64_t lda, int64_t ldb,
-                            int64_t ldc, int prec, const AccView *av, cudaStream_t s) {
-  const int NM = p.NM;
-  const int64_t Kp = w.Kp;
+// The three residue products of eq. 2 over the inner range [k0, k0 + Kb) under lines shared by
+// both parts (rtop / rbot: rows of A, ctop / cbot: columns of B; radius windows of part q in
+// pl[q]): the residues of each part, those of X_re + X_im and Y_re + Y_im, the 3 NM residue
+// products, then Re = P1 - P2 and Im = P3 - P1 - P2 in place of P1 and P2 (z3m_kernel).  *z
+// receives Re's NM planes of Mp x Np (Im's follow), *ct the tables to reconstruct them.
+static arbgpu_status eq2_products(arbgpu_ctx *ctx, const BlockWs &w, uint8_t *ws, int NM,
+                                  const CrtPlan *plan, int nch, const RtLayout &L,
+                                  const BallsView *Av, const BallsView *Bv, int64_t M, int64_t N,
+                                  int64_t lda, int64_t ldb, int64_t k0, int64_t Kb,
+                                  const int64_t *rtop, const int64_t *rbot, const int64_t *ctop,
+                                  const int64_t *cbot, const Lines *pl, cudaStream_t s,
+                                  uint16_t **z, CrtTables *ct) {
+  const int64_t Kp = (Kb + TG_BK - 1) / TG_BK * TG_BK;
   if (ensure_crt_constants(ctx->device) != ARBGPU_OK) return ARBGPU_ERR_CUDA;
   CrtDevTables dt{};
-  if (crt_device_tables(ctx, p.plan, &dt) != ARBGPU_OK) return ARBGPU_ERR_CUDA;
+  if (crt_device_tables(ctx, plan, &dt) != ARBGPU_OK) return ARBGPU_ERR_CUDA;
   // (the tensor-core reconstruction's weight table exists for NM <= 64)
-  const CrtTables ct{dt.Q32,        dt.M32,                      dt.y,      dt.rinv,
-                     NM,            p.plan->NMW,                 p.plan->NW32P,
-                     NM <= 64 ? dt.crt_wtab : nullptr, dt.mbytes, p.plan->NQ, p.plan->NQP,
-                     dt.w8,         p.plan->K8,                  p.plan->NQ8,
-                     dt.c32};
+  *ct = CrtTables{dt.Q32,        dt.M32,                    dt.y,      dt.rinv,
+                  NM,            plan->NMW,                 plan->NW32P,
+                  NM <= 64 ? dt.crt_wtab : nullptr, dt.mbytes, plan->NQ, plan->NQP,
+                  dt.w8,         plan->K8,                  plan->NQ8,
+                  dt.c32};
   // residue planes [re | im | re + im] of each side, 2 NM planes each
   __nv_bfloat16 *xr = (__nv_bfloat16 *)(ws + w.r3A), *yr = (__nv_bfloat16 *)(ws + w.r3B);
   const size_t setA = (size_t)2 * NM * M * Kp, setB = (size_t)2 * NM * N * Kp;
   for (int q = 0; q < 2; ++q) {
     LaunchScope sc(ctx, s, "residues",
                    (M * (8 * (int64_t)Av[q].nlimbs + 24) + N * (8 * (int64_t)Bv[q].nlimbs + 24)) *
-                           K +
-                       (int64_t)p.L.NPL * (M + N) * Kp * 2);
+                           Kb +
+                       (int64_t)L.NPL * (M + N) * Kp * 2);
     RtArgs ra{};
-    ra.side[0] = RtSide{Av[q], M,         lda, p.rbot, p.rtop, rowsL[q].rrad, nullptr,
-                        SplitOut{}, dt.wtab};
-    ra.side[1] = RtSide{Bv[q], N, ldb, p.cbot, p.ctop, colsL[q].crad, colsL[q].cplus,
-                        SplitOut{}, dt.wtab + (size_t)p.plan->NPAD * 128};
-    ra.k0 = 0, ra.K = K, ra.Kp = Kp, ra.NM = NM, ra.rinv = dt.rinv;
-    const arbgpu_status st = launch_residues_tc(ctx, p.L, p.nch, s, ra, xr + q * setA,
-                                                yr + q * setB);
+    ra.side[0] = RtSide{Av[q], M, lda, rbot, rtop, pl[q].rrad, nullptr, SplitOut{}, dt.wtab};
+    ra.side[1] = RtSide{Bv[q],      N,         ldb, cbot, ctop, pl[q].crad, pl[q].cplus,
+                        SplitOut{}, dt.wtab + (size_t)plan->NPAD * 128};
+    ra.k0 = k0, ra.K = Kb, ra.Kp = Kp, ra.NM = NM, ra.rinv = dt.rinv;
+    const arbgpu_status st = launch_residues_tc(ctx, L, nch, s, ra, xr + q * setA, yr + q * setB);
     if (st != ARBGPU_OK) return st;
   }
   {
@@ -4543,21 +4606,40 @@ static arbgpu_status run_3m(arbgpu_ctx *ctx, const BlockWs &w, uint8_t *ws, cons
         xr, xr + setA, xr + 2 * setA, M * Kp, yr, yr + setB, yr + 2 * setB, N * Kp, NM);
     if (cudaGetLastError() != cudaSuccess) return ARBGPU_ERR_CUDA;
   }
-  uint16_t *z = (uint16_t *)(ws + w.z3);
+  *z = (uint16_t *)(ws + w.z3);
   DigitGemmArgs g{xr, yr, (int)M, (int)N, Kp, 2, 2, 1, ws + w.z3, (int32_t *)(ws + w.ccar),
                   "crt_gemm", 3 * NM};
-  g.zout = z;
+  g.zout = *z;
   g.ztab = dt.ztab;
   g.zinv = dt.inv;
   arbgpu_status stg = launch_digit_gemm(ctx, g, s);
   if (stg != ARBGPU_OK) return stg;
   const int64_t plane = w.Mp * w.Np;
-  {
-    const int64_t nv = (int64_t)NM * (plane / 8);
-    LaunchScope sc(ctx, s, "z3m", nv * 8);
-    z3m_kernel<<<(unsigned)((nv + 255) / 256), 256, 0, s>>>(z, NM, plane);
-    if (cudaGetLastError() != cudaSuccess) return ARBGPU_ERR_CUDA;
-  }
+  const int64_t nv = (int64_t)NM * (plane / 8);
+  LaunchScope sc(ctx, s, "z3m", nv * 8);
+  z3m_kernel<<<(unsigned)((nv + 255) / 256), 256, 0, s>>>(*z, NM, plane);
+  return cudaGetLastError() == cudaSuccess ? ARBGPU_OK : ARBGPU_ERR_CUDA;
+}
+
+// Run the planned eq. 2 product: the radius bounds of each part summed into av[q].rman / rexp
+// (zeroed by the caller), then Re and Im reconstructed and rounded straight into C[0], C[1].
+static arbgpu_status run_3m(arbgpu_ctx *ctx, const BlockWs &w, uint8_t *ws, const Plan3M &p,
+                            const arbgpu_balls *C, const BallsView *Av, const BallsView *Bv,
+                            const Lines *rowsL, const Lines *colsL, const BlockStats *hst,
+                            int64_t M, int64_t K, int64_t N, int64_t lda, int64_t ldb,
+                            int64_t ldc, int prec, const AccView *av, cudaStream_t s) {
+  const int NM = p.NM;
+  const Lines pl[2] = {Lines{nullptr, nullptr, rowsL[0].rrad, nullptr, nullptr, colsL[0].crad,
+                             colsL[0].cplus},
+                       Lines{nullptr, nullptr, rowsL[1].rrad, nullptr, nullptr, colsL[1].crad,
+                             colsL[1].cplus}};
+  uint16_t *z = nullptr;
+  CrtTables ct{};
+  const arbgpu_status pst = eq2_products(ctx, w, ws, NM, p.plan, p.nch, p.L, Av, Bv, M, N, lda,
+                                         ldb, 0, K, p.rtop, p.rbot, p.ctop, p.cbot, pl, s, &z,
+                                         &ct);
+  if (pst != ARBGPU_OK) return pst;
+  const int64_t plane = w.Mp * w.Np;
   // radii: Re from A_re B_re and A_im B_im, Im from A_re B_im and A_im B_re, summed per entry
   const int pairs[4][3] = {{0, 0, 0}, {0, 1, 1}, {1, 0, 1}, {1, 1, 0}};
   for (const auto &pr : pairs) {
@@ -4682,6 +4764,288 @@ static arbgpu_status accumulate_product_ordered(arbgpu_ctx *ctx, const BlockWs &
   if (st == ARBGPU_OK && rec < ctx->plan_log.size()) {
     // the record covers positions of the order: mark it and append the order and the scaling
     ctx->plan_log[rec] = 1;
+    for (int64_t k = 0; k < K; ++k) ctx->plan_log.push_back(ord[(size_t)k]);
+    for (int64_t k = 0; k < K; ++k) ctx->plan_log.push_back(g[(size_t)k]);
+  }
+  return st;
+}
+
+// ---- eq. 2 over several blocks (Section IV-C's second suggestion: one splitting of the inner
+// range planned for the real and imaginary parts together).  The greedy extraction of Section
+// IV-A runs on entries whose top is the larger and whose bottom the smaller of the two parts'
+// (entry_tops with merge), so each full block admits one scaling per row of A and per column of
+// B shared by both parts: the per-block scans of each part, merged line by line
+// (merge_parts_kernel, one CTA per block).  Under it X_re + X_im and Y_re + Y_im are integers and
+// the block's Re and Im come from three exact products (eq2_products).  Each part's exact block
+// value goes into that part's window accumulator (one addition per block), and its radius bound
+// comes from the part's two real radius products over the block; basecase blocks become
+// complex dot products (both real products of each part, with the accumulated blocks as their
+// initial term).  kmap: the caller's inner index of each position (inner order), or null.
+// *done = false on return means nothing was accumulated (a block the tensor-core residue kernel
+// cannot take): the caller then runs four real products.
+static arbgpu_status accumulate_eq2(arbgpu_ctx *ctx, const BlockWs &w, uint8_t *ws,
+                                    const BallsView *Xv, const BallsView *Yv, int64_t M,
+                                    int64_t K, int64_t N, int64_t ldx, int64_t ldy, int prec,
+                                    const BlockStats *hst, const AccView *av, cudaStream_t s,
+                                    std::vector<int32_t> *basek, const std::vector<int32_t> *kmap,
+                                    const std::function<arbgpu_status()> &prepare, bool *done) {
+  *done = false;
+  BlockStats hs{};
+  hs.pA = hst[0].pA > hst[1].pA ? hst[0].pA : hst[1].pA;
+  hs.pB = hst[2].pB > hst[3].pB ? hst[2].pB : hst[3].pB;
+  const int64_t h = height_bound(prec, hs);
+  int64_t *tA = (int64_t *)(ws + w.tA), *bA = (int64_t *)(ws + w.bA);
+  int64_t *tBT = (int64_t *)(ws + w.tB), *bBT = (int64_t *)(ws + w.bB);
+  for (int q = 0; q < 2; ++q) {
+    const arbgpu_status est =
+        entry_tops(ctx, Xv[q], Yv[q], M, K, N, ldx, ldy, tA, bA, tBT, bBT, s, q == 1);
+    if (est != ARBGPU_OK) return est;
+  }
+  std::vector<int32_t> hb;
+  const arbgpu_status pst = plan_blocks(ctx, w, ws, M, K, N, h, s, hb);
+  if (pst != ARBGPU_OK) return pst;
+  const int nb = (int)(hb.size() / 3);
+  const int32_t *blocks = (const int32_t *)(ws + w.blocks);
+  // per-block lines: part 0 in the b* arrays, part 1 in the e2* arrays, shared in e2s*
+  int64_t *L0[7] = {(int64_t *)(ws + w.brtop), (int64_t *)(ws + w.brbot),
+                    (int64_t *)(ws + w.brrad), (int64_t *)(ws + w.bctop),
+                    (int64_t *)(ws + w.bcbot), (int64_t *)(ws + w.bcrad),
+                    (int64_t *)(ws + w.bcplus)};
+  int64_t *L1[7] = {(int64_t *)(ws + w.e2rtop), (int64_t *)(ws + w.e2rbot),
+                    (int64_t *)(ws + w.e2rrad), (int64_t *)(ws + w.e2ctop),
+                    (int64_t *)(ws + w.e2cbot), (int64_t *)(ws + w.e2crad),
+                    (int64_t *)(ws + w.e2cplus)};
+  int64_t *srtop = (int64_t *)(ws + w.e2srtop), *srbot = (int64_t *)(ws + w.e2srbot);
+  int64_t *sctop = (int64_t *)(ws + w.e2sctop), *scbot = (int64_t *)(ws + w.e2scbot);
+  BlockStats *bst[2] = {(BlockStats *)(ws + w.bstats), (BlockStats *)(ws + w.e2stats)};
+  BlockStats *mst = (BlockStats *)(ws + w.e2mstats);
+  BlockStats init{};
+  init.hA = init.hB = INT64_MIN;
+  std::vector<BlockStats> hbs[2], hms((size_t)nb);
+  for (int q = 0; q < 2; ++q) {
+    hbs[q].assign((size_t)nb, init);
+    if (cudaMemcpyAsync(bst[q], hbs[q].data(), sizeof(BlockStats) * nb, cudaMemcpyHostToDevice,
+                        s) != cudaSuccess)
+      return ARBGPU_ERR_CUDA;
+    int64_t *const *L = q ? L1 : L0;
+    const arbgpu_status sst = run_scans(ctx, s, Xv[q], M, K, ldx, Yv[q], N, ldy, blocks, nb, K,
+                                        L[0], L[1], L[2], L[3], L[4], L[5], L[6], bst[q], bst[q]);
+    if (sst != ARBGPU_OK) return sst;
+  }
+  {
+    LaunchScope sc(ctx, s, "merge_parts", (M + N) * nb);
+    merge_parts_kernel<<<(unsigned)nb, 1024, 0, s>>>(L0[0], L0[1], L1[0], L1[1], M, srtop, srbot,
+                                                     L0[3], L0[4], L1[3], L1[4], N, sctop, scbot,
+                                                     mst);
+  }
+  if (cudaGetLastError() != cudaSuccess ||
+      cudaMemcpyAsync(hbs[0].data(), bst[0], sizeof(BlockStats) * nb, cudaMemcpyDeviceToHost,
+                      s) != cudaSuccess ||
+      cudaMemcpyAsync(hbs[1].data(), bst[1], sizeof(BlockStats) * nb, cudaMemcpyDeviceToHost,
+                      s) != cudaSuccess ||
+      cudaMemcpyAsync(hms.data(), mst, sizeof(BlockStats) * nb, cudaMemcpyDeviceToHost, s) !=
+          cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess)
+    return ARBGPU_ERR_CUDA;
+  // every full block with a nonzero midpoint product must fit the tensor-core residue kernel
+  struct BlockPlan {
+    int NM, nch;
+    const CrtPlan *plan;
+    RtLayout L;
+  };
+  std::vector<BlockPlan> bp((size_t)nb);
+  for (int b = 0; b < nb; ++b) {
+    bp[b] = BlockPlan{0, 0, nullptr, {}};
+    const int64_t hA = hms[b].hA, hB = hms[b].hB;
+    if (hb[3 * b + 2] || hA == INT64_MIN || hB == INT64_MIN) continue;
+    const int64_t kc = hb[3 * b + 1] - hb[3 * b], Kpb = (kc + TG_BK - 1) / TG_BK * TG_BK;
+    BlockPlan &q = bp[b];
+    q.NM = crt_moduli_for_bits((int)(hA + hB + bit_length(kc) + 3));
+    if (q.NM > w.NMmax) return ARBGPU_OK;
+    q.plan = crt_plan(q.NM);
+    if (!q.plan || q.plan->NMW + 1 > RD_MAXW) return ARBGPU_OK;
+    q.nch = (int)(((hA > hB ? hA : hB) + 2 + 31) / 32) + 1;
+    if (!residue_tc_layout(q.nch, q.NM, false, (M > N ? M : N) * Kpb, &q.L)) return ARBGPU_OK;
+  }
+  *done = true;
+  log_plan(ctx, 2, h, K, hb);
+  const arbgpu_status prs = prepare();  // the accumulators' window bounds
+  if (prs != ARBGPU_OK) return prs;
+  const int64_t plane = w.Mp * w.Np;
+  for (int b = 0; b < nb; ++b) {
+    const int64_t k0 = hb[3 * b], k1 = hb[3 * b + 1];
+    if (hb[3 * b + 2]) {
+      // both real products of each part over these indices (combos as in the four-product path)
+      for (int64_t k = k0; k < k1; ++k) {
+        const int32_t kk = (int32_t)((kmap ? (int64_t)(*kmap)[k] : k) << 2);
+        basek[0].push_back(kk | 0);
+        basek[0].push_back(kk | 1);
+        basek[1].push_back(kk | 2);
+        basek[1].push_back(kk | 3);
+      }
+      continue;
+    }
+    const int64_t oM = (int64_t)b * M, oN = (int64_t)b * N;
+    const Lines pl[2] = {Lines{L0[0] + oM, L0[1] + oM, L0[2] + oM, L0[3] + oN, L0[4] + oN,
+                               L0[5] + oN, L0[6] + oN},
+                         Lines{L1[0] + oM, L1[1] + oM, L1[2] + oM, L1[3] + oN, L1[4] + oN,
+                               L1[5] + oN, L1[6] + oN}};
+    if (bp[b].plan) {
+      uint16_t *z = nullptr;
+      CrtTables ct{};
+      const arbgpu_status st =
+          eq2_products(ctx, w, ws, bp[b].NM, bp[b].plan, bp[b].nch, bp[b].L, Xv, Yv, M, N, ldx,
+                       ldy, k0, k1 - k0, srtop + oM, srbot + oM, sctop + oN, scbot + oN, pl, s,
+                       &z, &ct);
+      if (st != ARBGPU_OK) return st;
+      for (int q = 0; q < 2; ++q) {
+        RoundArgs ra{};
+        ra.mid = IntProduct{(const uint8_t *)(z + (size_t)q * bp[b].NM * plane), nullptr, 3, 1,
+                            {}, 1, ct};
+        ra.mid.ends.e[0] = 3;
+        ra.rtop = srtop + oM;
+        ra.rbot = srbot + oM;
+        ra.rrad = pl[q].rrad;
+        ra.ctop = sctop + oN;
+        ra.cbot = scbot + oN;
+        ra.crad = pl[q].crad;
+        ra.cplus = pl[q].cplus;
+        ra.M = M;
+        ra.N = N;
+        ra.Mp = w.Mp;
+        ra.Np = w.Np;
+        ra.prec = prec;
+        ra.acc = av[q];
+        LaunchScope sc(ctx, s, "accumulate", M * N);
+        arbgpu_status tst = ARBGPU_OK;
+        if (launch_crt_round_tc(ctx, ra, s, &tst, true)) {
+          if (tst != ARBGPU_OK) return tst;
+          continue;
+        }
+        AccArgs aa{};
+        aa.mid = ra.mid;
+        aa.rtop = ra.rtop;
+        aa.rbot = ra.rbot;
+        aa.rrad = ra.rrad;
+        aa.ctop = ra.ctop;
+        aa.cbot = ra.cbot;
+        aa.crad = ra.crad;
+        aa.cplus = ra.cplus;
+        aa.v = av[q];
+        aa.M = M;
+        aa.N = N;
+        aa.Mp = w.Mp;
+        aa.Np = w.Np;
+        aa.skip_rad = 1;
+        accumulate_kernel<<<(unsigned)((M * N + 127) / 128), 128, 0, s>>>(aa);
+      }
+    }
+    // radii: Re from X_re Y_re and X_im Y_im, Im from X_re Y_im and X_im Y_re, over this block
+    const int pairs[4][3] = {{0, 0, 0}, {0, 1, 1}, {1, 0, 1}, {1, 1, 0}};
+    for (const auto &pr : pairs) {
+      const int part = pr[0], xa = pr[1], yb = pr[2];
+      const bool radA = hbs[xa][b].radA != 0, radB = hbs[yb][b].radB != 0;
+      if (!radA && !radB) continue;
+      const Lines ln{pl[xa].rtop, pl[xa].rbot, pl[xa].rrad, pl[yb].ctop,
+                     pl[yb].cbot, pl[yb].crad, pl[yb].cplus};
+      AccArgs aa{};
+      const arbgpu_status st = run_radius(ctx, w, ws, Xv[xa], Yv[yb], M, N, ldx, ldy, k0,
+                                          k1 - k0, radA, radB, ln, s, &aa.rp1, &aa.rp2);
+      if (st != ARBGPU_OK) return st;
+      aa.rtop = ln.rtop;
+      aa.rbot = ln.rbot;
+      aa.rrad = ln.rrad;
+      aa.ctop = ln.ctop;
+      aa.cbot = ln.cbot;
+      aa.crad = ln.crad;
+      aa.cplus = ln.cplus;
+      aa.v = av[part];
+      aa.M = M;
+      aa.N = N;
+      aa.Mp = w.Mp;
+      aa.Np = w.Np;
+      aa.skip_mid = 1;
+      LaunchScope sc(ctx, s, "accumulate", M * N);
+      accumulate_kernel<<<(unsigned)((M * N + 127) / 128), 128, 0, s>>>(aa);
+    }
+  }
+  return cudaGetLastError() == cudaSuccess ? ARBGPU_OK : ARBGPU_ERR_CUDA;
+}
+
+// accumulate_eq2 over an inner order shared by the parts (the two suggestions of Sections IV-B and
+// IV-C together): a_k = largest top over column k of both parts of A, b_k over row k of both parts
+// of B, then the order and scaling of the real case (inner_order_host), reordered and scaled
+// copies of all four operand parts, and accumulate_eq2 on the copies.  The plan record (kind 4)
+// lists the order and the scaling after its blocks.
+static arbgpu_status accumulate_eq2_ordered(arbgpu_ctx *ctx, const BlockWs &w, uint8_t *ws,
+                                            const BallsView *Xv, const BallsView *Yv, int64_t M,
+                                            int64_t K, int64_t N, int64_t ldx, int64_t ldy,
+                                            int prec, const BlockStats *hst, const AccView *av,
+                                            cudaStream_t s, std::vector<int32_t> *basek,
+                                            const std::function<arbgpu_status()> &prepare,
+                                            bool *done) {
+  *done = false;
+  for (int q = 0; q < 2; ++q)
+    if (Xv[q].nlimbs > BL_MAX_NL || Yv[q].nlimbs > BL_MAX_NL) return ARBGPU_OK;
+  int64_t *tA = (int64_t *)(ws + w.tA), *bA = (int64_t *)(ws + w.bA);
+  int64_t *tBT = (int64_t *)(ws + w.tB), *bBT = (int64_t *)(ws + w.bB);
+  int64_t *da = (int64_t *)(ws + w.ia), *db = (int64_t *)(ws + w.ib);
+  for (int q = 0; q < 2; ++q) {
+    const arbgpu_status est =
+        entry_tops(ctx, Xv[q], Yv[q], M, K, N, ldx, ldy, tA, bA, tBT, bBT, s, q == 1);
+    if (est != ARBGPU_OK) return est;
+  }
+  {
+    LaunchScope sc(ctx, s, "inner_tops", M * K + K * N);
+    colmax_kernel<<<(unsigned)((K + 31) / 32), 256, 0, s>>>(tA, M, K, da);
+    colmax_kernel<<<(unsigned)((K + 31) / 32), 256, 0, s>>>(tBT, N, K, db);
+  }
+  std::vector<int64_t> a((size_t)K), b((size_t)K), g;
+  std::vector<int32_t> ord;
+  if (cudaGetLastError() != cudaSuccess ||
+      cudaMemcpyAsync(a.data(), da, 8 * (size_t)K, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaMemcpyAsync(b.data(), db, 8 * (size_t)K, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess)
+    return ARBGPU_ERR_CUDA;
+  inner_order_host(a, b, ord, g);
+  int32_t *dord = (int32_t *)(ws + w.iord);
+  int64_t *dg = (int64_t *)(ws + w.ig);
+  if (cudaMemcpyAsync(dord, ord.data(), 4 * (size_t)K, cudaMemcpyHostToDevice, s) !=
+          cudaSuccess ||
+      cudaMemcpyAsync(dg, g.data(), 8 * (size_t)K, cudaMemcpyHostToDevice, s) != cudaSuccess)
+    return ARBGPU_ERR_CUDA;
+  BallsView Xo[2], Yo[2];
+  int *drange = (int *)(ws + w.irange);
+  int hrange = 0;
+  if (cudaMemsetAsync(drange, 0, 4, s) != cudaSuccess) return ARBGPU_ERR_CUDA;
+  {
+    LaunchScope sc(ctx, s, "gather_inner", 2 * (M * K + K * N));
+    for (int q = 0; q < 2; ++q) {
+      const BallsOut oX = ball_array_at(ws + (q ? w.oA2 : w.oA), M * K, Xv[q].nlimbs);
+      const BallsOut oY = ball_array_at(ws + (q ? w.oB2 : w.oB), K * N, Yv[q].nlimbs);
+      gather_inner_kernel<<<(unsigned)((M * K + 255) / 256), 256, 0, s>>>(Xv[q], ldx, false, M,
+                                                                          K, N, dord, dg, oX,
+                                                                          drange);
+      gather_inner_kernel<<<(unsigned)((K * N + 255) / 256), 256, 0, s>>>(Yv[q], ldy, true, M,
+                                                                          K, N, dord, dg, oY,
+                                                                          drange);
+      Xo[q] = BallsView{oX.limbs, oX.stride, oX.nlimbs, oX.exp, oX.flags, oX.rad_man, oX.rad_exp};
+      Yo[q] = BallsView{oY.limbs, oY.stride, oY.nlimbs, oY.exp, oY.flags, oY.rad_man, oY.rad_exp};
+    }
+    if (cudaGetLastError() != cudaSuccess ||
+        cudaMemcpyAsync(&hrange, drange, 4, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+      return ARBGPU_ERR_CUDA;
+  }
+  if (hrange)  // a scaled exponent would leave the fast path's range: keep the original order
+    return accumulate_eq2(ctx, w, ws, Xv, Yv, M, K, N, ldx, ldy, prec, hst, av, s, basek,
+                          nullptr, prepare, done);
+  const size_t rec = ctx->plan_log.size();
+  const arbgpu_status st = accumulate_eq2(ctx, w, ws, Xo, Yo, M, K, N, K, N, prec, hst, av, s,
+                                          basek, &ord, prepare, done);
+  if (cudaStreamSynchronize(s) != cudaSuccess) return ARBGPU_ERR_CUDA;
+  if (st == ARBGPU_OK && *done && rec < ctx->plan_log.size()) {
+    ctx->plan_log[rec] = 4;
     for (int64_t k = 0; k < K; ++k) ctx->plan_log.push_back(ord[(size_t)k]);
     for (int64_t k = 0; k < K; ++k) ctx->plan_log.push_back(g[(size_t)k]);
   }
@@ -5008,9 +5372,24 @@ arbgpu_status block_finish(arbgpu_ctx *ctx, const arbgpu_balls *C, const arbgpu_
     *used_block = true;
     return ARBGPU_OK;
   }
+  // eq. 2 over several blocks shared by both parts (over their shared inner order when the
+  // inner ordering is on)
+  bool eq2 = false;
+  if (p3.several) {
+    const std::function<arbgpu_status()> prep2 = [&etop_of]() {
+      const arbgpu_status e0 = etop_of(0);
+      return e0 != ARBGPU_OK ? e0 : etop_of(1);
+    };
+    const arbgpu_status se =
+        w.oA2 ? accumulate_eq2_ordered(ctx, w, ws, Av, Bv, M, K, N, lda, ldb, prec, hst, av, s,
+                                       basek, prep2, &eq2)
+              : accumulate_eq2(ctx, w, ws, Av, Bv, M, K, N, lda, ldb, prec, hst, av, s, basek,
+                               nullptr, prep2, &eq2);
+    if (se != ARBGPU_OK) return se;
+  }
   bool rounded[2] = {false, false};
   const DirectRound direct{out_of(C[0]), ldc};
-  for (int t = 0; t < (p3.ok ? 0 : nprods); ++t) {
+  for (int t = 0; t < (eq2 ? 0 : nprods); ++t) {
     const Prod &pr = prods[t];
     const BlockStats hs = merge_stats(hst[pr.xa], hst[2 + pr.yb]);
     const int64_t hb = height_bound(prec, hs);

@@ -326,14 +326,18 @@ def test_complex_3m_exact_inputs_and_zero_part(arb):
                   [(int(a), int(b)) for a, b in zip(rng2.integers(0, M, 30), rng2.integers(0, N, 30))])
 
 
-def test_complex_3m_falls_back_to_4m_for_several_blocks(arb, contiguous):
+def test_complex_3m_plans_several_blocks_for_both_parts(arb, contiguous):
     """When the shared scaling needs several blocks (Laplace exponents along the inner index), the
-    flag leaves the four-product path in place and the result is still rigorous."""
+    flag cuts the inner range once for both parts (Section IV-C's second suggestion): one plan
+    record, the greedy blocks of the merged entry heights (here every block is a basecase range of
+    complex dots), and the result is still rigorous."""
     from synth.workloads import complex_matmul_laplace
     case = complex_matmul_laplace(n=128, structured=True)
     outs, names = run_cmm(arb, case.A, case.B, 128, 128, 128, 128, arb.ALG_BLOCK, trace=True,
                           flags=arb.MM_COMPLEX_3M)
-    assert "z3m" not in names and "plan" in names
+    h, blocks = alg2.plan_complex_shared(case.A, case.B, 128, 128, 128, 128)
+    assert arb.default_context().last_plans() == [dict(kind=2, h=h, K=128, blocks=blocks)]
+    assert len(blocks) > 1 and "plan" in names
     rng2 = np.random.default_rng(8)
     check_complex(outs, case.A, case.B, 128, 128, 128, 128,
                   [(int(a), int(b)) for a, b in zip(rng2.integers(0, 128, 30),

@@ -127,6 +127,47 @@ def test_device_plan_of_the_complex_product_by_eq2(arb):
     check_complex(outs, A2, B2, M, K, N, p, _sample(M, N, 30, 6))
 
 
+def complex_bands(seed, M, K, N, bands, nl=2, rad=120):
+    """Complex operands: the columns lo..hi-1 of A's real part (first range) and of its imaginary
+    part (second range) sit 2^900 higher than the rest; B is uniformly scaled."""
+    rng = np.random.default_rng(seed)
+    A2, B2 = [], []
+    for lo, hi in bands:
+        ea = rng.integers(-5, 5, size=M * K)
+        for k in range(lo, hi):
+            ea[np.arange(M) * K + k] += 900
+        A2.append(random_balls(rng, M * K, nl, 64 * nl, exps=ea, rad_bits=rad, rad_zero_frac=0.5))
+        B2.append(random_balls(rng, K * N, nl, 64 * nl, -5, 5, rad_bits=rad, rad_zero_frac=0.5))
+    return A2, B2
+
+
+EQ2_BANDS = {
+    "same": ((60, 120), (60, 120)),  # three full blocks shared by the parts
+    "apart": ((35, 36), (70, 71)),   # a merged entry taller than h in each part: basecase ranges
+    "overlap": ((40, 90), (60, 110)),  # full blocks, forced single indices, basecase ranges
+}
+
+
+@pytest.mark.parametrize("kind", sorted(EQ2_BANDS))
+def test_device_plan_of_eq2_over_several_blocks(arb, contiguous, kind):
+    """Eq. 2 over several blocks (Section IV-C's second suggestion): the device plans the inner
+    range once on the merged entry heights of both parts and the record equals
+    ``plan_complex_shared`` element by element; every full block's Re and Im come from three
+    exact products (z3m), and every sampled ball of both parts contains the exact complex
+    product within the accuracy bound."""
+    M, K, N, p = 40, 180, 36, 128
+    A2, B2 = complex_bands(31 + len(kind), M, K, N, EQ2_BANDS[kind])
+    outs, names = run_cmm(arb, A2, B2, M, K, N, p, arb.ALG_BLOCK, trace=True,
+                          flags=arb.MM_COMPLEX_3M)
+    h, blocks = alg2.plan_complex_shared(A2, B2, M, K, N, p)
+    assert len(blocks) > 1
+    assert arb.default_context().last_plans() == [dict(kind=2, h=h, K=K, blocks=blocks)]
+    assert ("z3m" in names) == any(not b[2] for b in blocks)
+    if any(b[2] for b in blocks):
+        assert "dot_tile" in names or "dot_fused" in names
+    check_complex(outs, A2, B2, M, K, N, p, _sample(M, N, 60, 9))
+
+
 # ------------------------------------------------------------------ inner ordering (Section IV-B)
 
 @pytest.fixture
@@ -196,3 +237,24 @@ def test_inner_ordered_complex_product(arb, ordered):
     for rec, (xa, yb) in zip(plans, ((0, 0), (1, 1), (0, 1), (1, 0))):
         assert rec == _expected_ordered(case.A[xa], case.B[yb], n, n, n, p)
     check_complex(outs, case.A, case.B, n, n, n, p, _sample(n, n, 40, 8))
+
+
+@pytest.mark.parametrize("kind", ["structured", "overlap"])
+def test_inner_ordered_eq2_plan_equals_oracle(arb, ordered, kind):
+    """Both suggestions together: eq. 2 over blocks planned for both parts at once, over an inner
+    order and scaling shared by the parts.  The record (kind 4) equals ``plan_complex_ordered``:
+    blocks, order and scaling exponents; the sampled balls contain the exact product within the
+    accuracy bound."""
+    if kind == "structured":
+        case = complex_matmul_laplace(n=128, structured=True)
+        A2, B2, M, K, N, p = case.A, case.B, 128, 128, 128, 128
+    else:
+        M, K, N, p = 40, 180, 36, 128
+        A2, B2 = complex_bands(38, M, K, N, EQ2_BANDS[kind])
+    outs, names = run_cmm(arb, A2, B2, M, K, N, p, arb.ALG_BLOCK, trace=True,
+                          flags=arb.MM_COMPLEX_3M)
+    h, order, g, blocks = alg2.plan_complex_ordered(A2, B2, M, K, N, p)
+    assert arb.default_context().last_plans() == [
+        dict(kind=4, h=h, K=K, blocks=blocks, order=order, g=g)]
+    assert any(not b[2] for b in blocks) and "z3m" in names
+    check_complex(outs, A2, B2, M, K, N, p, _sample(M, N, 60, 10))

@@ -41,7 +41,7 @@ def _inputs(arb, seed, M, K, N, p, parts, lo, hi):
     return A, B
 
 
-@pytest.mark.parametrize("kind", ["block", "several", "dot", "complex3m"])
+@pytest.mark.parametrize("kind", ["block", "several", "dot", "complex3m", "complex3m_several"])
 def test_repeated_calls_are_bitwise_identical(arb, kind):
     if kind == "block":
         M, K, N, p, parts, lo, hi, alg, flags = 96, 96, 96, 128, 1, -10, 10, arb.ALG_BLOCK, 0
@@ -49,8 +49,11 @@ def test_repeated_calls_are_bitwise_identical(arb, kind):
         M, K, N, p, parts, lo, hi, alg, flags = 48, 120, 40, 64, 1, -400, 400, arb.ALG_BLOCK, 0
     elif kind == "dot":
         M, K, N, p, parts, lo, hi, alg, flags = 40, 40, 40, 192, 1, -30, 30, arb.ALG_DOT, 0
-    else:
+    elif kind == "complex3m":
         M, K, N, p, parts, lo, hi, alg, flags = (64, 64, 64, 128, 2, -10, 10, arb.ALG_BLOCK,
+                                                 arb.MM_COMPLEX_3M)
+    else:  # eq. 2 over several blocks shared by the parts
+        M, K, N, p, parts, lo, hi, alg, flags = (48, 120, 40, 64, 2, -400, 400, arb.ALG_BLOCK,
                                                  arb.MM_COMPLEX_3M)
     A, B = _inputs(arb, 90, M, K, N, p, parts, lo, hi)
     nl = (p + 63) // 64
