@@ -428,12 +428,16 @@ def run_workload(args):
         A = [arb.Balls.from_raw(a) for a in case.A]
         B = [arb.Balls.from_raw(b) for b in case.B]
         C = [arb.Balls.empty(n * n, 2), arb.Balls.empty(n * n, 2)]
-        need = arb.mat_mul_workspace_size(n, n, n, 128, 2, 2, True, arb.ALG_AUTO)
+        # --complex-3m: eq. 2 over blocks shared by both parts (over their shared inner order)
+        mflags = arb.MM_COMPLEX_3M if args.complex_3m else 0
+        need = arb.mat_mul_workspace_size(n, n, n, 128, 2, 2, True, arb.ALG_AUTO, mflags)
         ws = torch.empty(max(need, 1), dtype=torch.uint8, device="cuda")
 
         def step():
-            arb.mat_mul(C, A, B, n, n, n, 128, workspace=ws, ctx=ctx)
-        macs, prec, name = n ** 3, 128, case.name
+            arb.mat_mul(C, A, B, n, n, n, 128, flags=mflags, workspace=ws, ctx=ctx)
+        macs, prec = n ** 3, 128
+        name = case.name + (", eq. 2 over blocks shared by both parts (3M)" if args.complex_3m
+                            else "")
         inbytes = sum(b.nbytes() for b in A + B)
         outbytes = sum(c.nbytes() for c in C)
 

@@ -29,7 +29,10 @@ scaling of the columns of A_s against the rows of B_s, combined with a permutati
 index); its reading is given above ``inner_order``.  ``plan_complex_shared`` /
 ``scaled_block_complex`` / ``eq2_block_products`` restate Section IV-C's complex product by eq. 2
 over blocks planned for both parts together; ``plan_complex_ordered`` /
-``scaled_block_complex_ordered`` combine that with the inner ordering.
+``scaled_block_complex_ordered`` combine that with the inner ordering.  ``omission_thresholds``
+/ ``omitted_product`` restate the negligible-limb omission of Section IV-B's last paragraph for a
+real product, ``omission_thresholds_complex`` / ``omitted_product_complex`` for the two parts of a
+complex product by eq. 2 under thresholds shared by the parts.
 """
 from __future__ import annotations
 
@@ -445,3 +448,58 @@ def omitted_product(A, B, M, K, N, tau, sigma):
         return Fraction(v[0]) * Fraction(2) ** v[1]
     return [[sum(val(a[i][k]) * val(b[k][j]) for k in range(K)) for j in range(N)]
             for i in range(M)]
+
+
+# ---- the omission for eq. 2 (Section IV-B's last paragraph with Section IV-C's shared scaling).
+# Reading: both parts of a row of A (a column of B) drop their bits below one threshold, so the
+# truncated parts still take one scaling per line shared by both parts.  With E_q,ij the largest
+# product exponent of output part q at (i, j) (q = 0: a_re b_re and a_im b_im; q = 1: a_re b_im
+# and a_im b_re), rtop_i / ctop_j the line tops over both parts, and G = bc(K) + 9,
+#     tau_i = min_{q, j} (E_q,ij - ctop_j) - p - G,   sigma_j = min_{q, i} (E_q,ij - rtop_i) - p - G
+# (minima over the (q, i, j) with a nonzero product).  Each of part q's 2 K products then changes
+# by less than 2^(tau_i + ctop_j) + 2^(rtop_i + sigma_j) <= 2 2^(E_q,ij - p - G), so part q changes
+# by less than 4 K 2^(E_q,ij - p - G) < 2^(E_q,ij - 2) 2^-p / 32 <= (1/32) 2^-p times the sum of
+# |a b| over part q's terms: one bit more of G than a real product takes, for the two products
+# each part sums.  The bound of each part is its own: a threshold taken from the larger part's E
+# alone would drop bits that matter to the smaller part.
+
+def omission_thresholds_complex(A, B, M, K, N, prec):
+    """``(tau, sigma)`` shared by both parts of ``A = (A_re, A_im)`` and ``B = (B_re, B_im)`` (None
+    for a line left as it is)."""
+    G = bc(K) + 9
+    ta = [[[top_bottom(A[q], i * K + k) for k in range(K)] for i in range(M)] for q in (0, 1)]
+    tb = [[[top_bottom(B[q], k * N + j) for j in range(N)] for k in range(K)] for q in (0, 1)]
+    rtop = [max((t[0] for q in (0, 1) for t in ta[q][i] if t is not None), default=None)
+            for i in range(M)]
+    ctop = [max((tb[q][k][j][0] for q in (0, 1) for k in range(K) if tb[q][k][j] is not None),
+                default=None) for j in range(N)]
+    products = (((0, 0), (1, 1)), ((0, 1), (1, 0)))  # (A part, B part) of Re, then of Im
+    E = [[[None] * N for _ in range(M)] for _ in products]
+    for part, pairs in enumerate(products):
+        for i in range(M):
+            for j in range(N):
+                for x, y in pairs:
+                    for k in range(K):
+                        a, b = ta[x][i][k], tb[y][k][j]
+                        if a is not None and b is not None:
+                            v = a[0] + b[0]
+                            e = E[part][i][j]
+                            E[part][i][j] = v if e is None else max(e, v)
+    tau = []
+    for i in range(M):
+        d = [E[q][i][j] - ctop[j] for q in (0, 1) for j in range(N) if E[q][i][j] is not None]
+        tau.append(min(d) - prec - G if d else None)
+    sigma = []
+    for j in range(N):
+        d = [E[q][i][j] - rtop[i] for q in (0, 1) for i in range(M) if E[q][i][j] is not None]
+        sigma.append(min(d) - prec - G if d else None)
+    return tau, sigma
+
+
+def omitted_product_complex(A, B, M, K, N, tau, sigma):
+    """``(Re, Im)`` of the exact complex product of the truncated parts, entry by entry, as
+    Fractions."""
+    P = {(x, y): omitted_product(A[x], B[y], M, K, N, tau, sigma) for x in (0, 1) for y in (0, 1)}
+    re = [[P[0, 0][i][j] - P[1, 1][i][j] for j in range(N)] for i in range(M)]
+    im = [[P[0, 1][i][j] + P[1, 0][i][j] for j in range(N)] for i in range(M)]
+    return re, im

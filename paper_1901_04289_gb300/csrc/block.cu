@@ -4304,9 +4304,6 @@ struct DirectRound {
   int64_t ldc;
 };
 
-// Add (-1)^negate X Y to the accumulator by Algorithm 2: plan the blocks of this product, run the
-// products of the full blocks and accumulate them; append the basecase indices, tagged with
-// `combo`, to `basek`.
 // The greedy extraction of Algorithm 2 on the per-entry tops and bottoms in the workspace (tA / bA
 // for the rows of X, tB / bB for the columns of Y, from entry_tops): one cooperative launch, then
 // the [start, stop, basecase] triples read back into hb (the plan stays at w.blocks).
@@ -4344,6 +4341,9 @@ static arbgpu_status plan_blocks(arbgpu_ctx *ctx, const BlockWs &w, uint8_t *ws,
   return ARBGPU_OK;
 }
 
+// Add (-1)^negate X Y to the accumulator by Algorithm 2: plan the blocks of this product, run the
+// products of the full blocks and accumulate them; append the basecase indices, tagged with
+// `combo`, to `basek`.
 static arbgpu_status accumulate_product(arbgpu_ctx *ctx, const BlockWs &w, uint8_t *ws,
                                         const BallsView &Xv, const BallsView &Yv, int64_t M,
                                         int64_t K, int64_t N, int64_t ldx, int64_t ldy, int prec,

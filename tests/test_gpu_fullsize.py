@@ -2,8 +2,9 @@
 
 * the complex N = 2048, p = 128 product with Laplace(40) exponents, both the structured variant
   (exponent blocks along the inner index) and the literal one (i.i.d. exponents): containment of
-  the exact product and the accuracy bound |m - S| <= 2^-p sum |a b| on every sampled entry, and
-  for the structured variant midpoints exactly RNE_p where the product ran as one exact block;
+  the exact product and the accuracy bound |m - S| <= 2^-p sum |a b| on every sampled entry, by
+  four real products with their negligible limbs omitted, and with ARBGPU_MM_COMPLEX_3M by eq. 2
+  over blocks shared by both parts (over their shared inner order);
 * the grouped batch of 256 real products (N in [16, 512], p in {64, ..., 1024}) in one
   arbgpu_mat_mul_batched call: block items (one exponent block each) bit-exact RNE_p of the exact
   sum, or within the bound where negligible limbs were omitted, classical items bit-exact against
@@ -30,20 +31,32 @@ def arb():
 
 
 @pytest.mark.parametrize("structured", [True, False])
-def test_complex2048_sampled(arb, structured):
+@pytest.mark.parametrize("m3", [False, True])
+def test_complex2048_sampled(arb, structured, m3):
     case = complex_matmul_laplace(structured=structured)
     n, p = case.N, case.prec
     A = [arb.Balls.from_raw(a) for a in case.A]
     B = [arb.Balls.from_raw(b) for b in case.B]
     C = [arb.Balls.empty(n * n, 2), arb.Balls.empty(n * n, 2)]
-    need = arb.mat_mul_workspace_size(n, n, n, p, 2, 2, True, arb.ALG_AUTO)
+    flags = arb.MM_COMPLEX_3M if m3 else 0
+    need = arb.mat_mul_workspace_size(n, n, n, p, 2, 2, True, arb.ALG_AUTO, flags)
     import torch
     ws = torch.empty(max(need, 1), dtype=torch.uint8, device="cuda")
     ctx = arb.default_context()
-    arb.mat_mul(C, A, B, n, n, n, p, workspace=ws, ctx=ctx)
+    arb.mat_mul(C, A, B, n, n, n, p, flags=flags, workspace=ws, ctx=ctx)
     assert ctx.status() == 0
-    # with the negligible limbs omitted, each real product of this workload is one block
-    assert [r["kind"] for r in ctx.last_plans()] == [3, 3, 3, 3]
+    plans = ctx.last_plans()
+    if m3:
+        # eq. 2 over blocks shared by both parts, over their shared inner order: one record whose
+        # blocks tile the inner range
+        assert len(plans) == 1 and plans[0]["kind"] == 4
+        bl = plans[0]["blocks"]
+        assert bl[0][0] == 0 and bl[-1][1] == n
+        assert all(a[1] == b[0] for a, b in zip(bl, bl[1:]))
+        assert sorted(plans[0]["order"]) == list(range(n))
+    else:
+        # with the negligible limbs omitted, each real product of this workload is one block
+        assert [r["kind"] for r in plans] == [3, 3, 3, 3]
     outs = [to_raw(c) for c in C]
     rng = np.random.default_rng(2048 + structured)
     entries = [(int(a), int(b)) for a, b in zip(rng.integers(0, n, 100), rng.integers(0, n, 100))]

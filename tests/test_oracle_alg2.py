@@ -800,3 +800,122 @@ def test_planted_omission_slip_is_caught(monkeypatch):
     monkeypatch.setattr(alg2, "omission_thresholds", coarse)
     with pytest.raises(AssertionError):
         test_omission_keeps_the_accuracy_bound(2, 5, 9, 4, 128, 200, 60)
+
+
+# ------------------------------------------------------------------ omission for eq. 2
+# (thresholds shared by both parts, in the reading of ``oracle.alg2.omission_thresholds_complex``)
+
+# (A part, B part, sign) of the two products of each output part: Re, then Im
+_PART_PRODUCTS = (((0, 0, 1), (1, 1, -1)), ((0, 1, 1), (1, 0, 1)))
+
+
+def _complex_wide_case(seed, M, K, N, bits, spread, lopsided=False):
+    """Complex operands with `bits`-bit mantissas; lopsided: A_re and B_im sit 2^200 lower than
+    A_im and B_re, so every term of Re is about 2^-200 times the largest terms of Im."""
+    rng = np.random.default_rng(seed)
+    nl = (bits + 63) // 64
+    lo = -200 if lopsided else 0
+    A = [random_balls(rng, M * K, nl, bits, -spread + (lo if q == 0 else 0),
+                      spread + (lo if q == 0 else 0)) for q in (0, 1)]
+    B = [random_balls(rng, K * N, nl, bits, -spread + (lo if q == 1 else 0),
+                      spread + (lo if q == 1 else 0)) for q in (0, 1)]
+    return A, B
+
+
+def _check_complex_omission(A, B, M, K, N, p, tau, sigma):
+    """Each part of the truncated operands' product within (1/32) 2^-p sum |a b| of the exact part
+    (the bound the reading derives); every dropped part below 2^tau (2^sigma); True when
+    something was dropped."""
+    re, im = alg2.omitted_product_complex(A, B, M, K, N, tau, sigma)
+    ex = {(x, y): exact_product(A[x], B[y], M, K, N) for x in (0, 1) for y in (0, 1)}
+    for part, got in enumerate((re, im)):
+        for i in range(M):
+            for j in range(N):
+                S = sum(sg * ex[x, y][i][j] for x, y, sg in _PART_PRODUCTS[part])
+                sabs = sum(abs(ball_values(A[x], i * K + k)[0] * ball_values(B[y], k * N + j)[0])
+                           for x, y, _ in _PART_PRODUCTS[part] for k in range(K))
+                assert abs(got[i][j] - S) <= Fraction(1, 32) * sabs / Fraction(2) ** p, \
+                    (part, i, j)
+    dropped = False
+    for q in (0, 1):
+        for i in range(M):
+            for k in range(K):
+                tb = alg2.top_bottom(A[q], i * K + k)
+                if tb is None:
+                    continue
+                v, e = alg2.truncate_value(tb, tau[i])
+                d = abs(Fraction(tb[2]) * Fraction(2) ** tb[3] - Fraction(v) * Fraction(2) ** e)
+                assert tau[i] is not None or d == 0
+                assert d == 0 or d < Fraction(2) ** tau[i]
+                dropped = dropped or d > 0
+    return dropped
+
+
+@pytest.mark.parametrize("seed,M,K,N,p,bits,spread,lopsided", [
+    (1, 4, 10, 3, 64, 512, 5, False), (2, 3, 8, 4, 128, 256, 60, False),
+    (3, 3, 9, 3, 64, 320, 5, True)])
+def test_complex_omission_keeps_the_accuracy_bound(seed, M, K, N, p, bits, spread, lopsided):
+    A, B = _complex_wide_case(seed, M, K, N, bits, spread, lopsided)
+    tau, sigma = alg2.omission_thresholds_complex(A, B, M, K, N, p)
+    assert _check_complex_omission(A, B, M, K, N, p, tau, sigma)
+
+
+def _thresholds_by_definition(A, B, M, K, N, p, larger_part_only=False):
+    """tau_i and sigma_j evaluated directly from the exponent fields (2^(exp - 1) <= |x| < 2^exp):
+    E per output part, or (larger_part_only) the larger of the two parts' E for both."""
+    val = lambda raw, i: None if int(raw.flags[i]) & X.FLAG_ZERO else int(raw.exp[i])  # noqa
+    G = alg2.bc(K) + 9
+
+    def E(part, i, j):
+        v = [val(A[x], i * K + k) + val(B[y], k * N + j) for x, y, _ in _PART_PRODUCTS[part]
+             for k in range(K) if val(A[x], i * K + k) is not None
+             and val(B[y], k * N + j) is not None]
+        return max(v) if v else None
+
+    def Es(i, j):
+        e = [E(q, i, j) for q in (0, 1)]
+        if larger_part_only:
+            live = [v for v in e if v is not None]
+            return [max(live)] if live else []
+        return [v for v in e if v is not None]
+    ctop = [max([val(B[q], k * N + j) for q in (0, 1) for k in range(K)
+                 if val(B[q], k * N + j) is not None], default=None) for j in range(N)]
+    rtop = [max([val(A[q], i * K + k) for q in (0, 1) for k in range(K)
+                 if val(A[q], i * K + k) is not None], default=None) for i in range(M)]
+    tau = []
+    for i in range(M):
+        cand = [e - ctop[j] for j in range(N) for e in Es(i, j)]
+        tau.append(min(cand) - p - G if cand else None)
+    sigma = []
+    for j in range(N):
+        cand = [e - rtop[i] for i in range(M) for e in Es(i, j)]
+        sigma.append(min(cand) - p - G if cand else None)
+    return tau, sigma
+
+
+def test_complex_omission_thresholds_by_brute_force():
+    """The shared thresholds against a direct evaluation of their definition, on a lopsided case
+    with zero entries and a row of A that is zero in both parts."""
+    rng = np.random.default_rng(9)
+    M, K, N, p = 4, 6, 5, 64
+    A = [random_balls(rng, M * K, 2, 128, -40 + (-90 if q == 0 else 0), 40, zero_frac=0.3)
+         for q in (0, 1)]
+    B = [random_balls(rng, K * N, 2, 128, -40, 40, zero_frac=0.3) for q in (0, 1)]
+    for q in (0, 1):  # row 0 of A zero in both parts: no product, no truncation
+        A[q].flags[0:K] = X.FLAG_ZERO
+        A[q].limbs[:, 0:K] = 0
+    tau, sigma = alg2.omission_thresholds_complex(A, B, M, K, N, p)
+    assert (tau, sigma) == _thresholds_by_definition(A, B, M, K, N, p)
+    assert tau[0] is None
+
+
+def test_planted_complex_omission_slip_is_caught():
+    """Thresholds taken from the larger part's bound for both parts (Im here) drop bits that
+    matter to Re, about 2^-200 times smaller: the accuracy pin fails."""
+    M, K, N, p = 3, 9, 3, 64
+    A, B = _complex_wide_case(3, M, K, N, 320, 5, True)
+    good = _thresholds_by_definition(A, B, M, K, N, p)
+    assert good == alg2.omission_thresholds_complex(A, B, M, K, N, p)
+    bad = _thresholds_by_definition(A, B, M, K, N, p, larger_part_only=True)
+    with pytest.raises(AssertionError):
+        _check_complex_omission(A, B, M, K, N, p, *bad)
