@@ -237,14 +237,19 @@ arbgpu_status arbgpu_approx_dot(arbgpu_ctx *ctx, const arbgpu_balls *res,
  * shared by the real and imaginary parts, scales both parts to integers within one block of
  * Algorithm 2, Re = Ar Br - Ai Bi and Im = (Ar + Ai)(Br + Bi) - Ar Br - Ai Bi are formed exactly
  * from three integer products instead of four and rounded once; radii come from the four real
- * radius products as without the flag.  When the shared scaling needs several blocks, the inner
- * range is cut once for both parts (Section IV-C's second suggestion: the greedy extraction on
- * the larger top and the smaller bottom of each entry's two parts, over an inner order and
- * scaling shared by the parts when the inner ordering is on); each full block's Re and Im come
- * from three exact products and are added into the parts' window accumulators, the basecase
- * blocks become complex dot products.  Blocks the tensor-core residue kernel cannot take (more
- * than 32 chunks or 128 moduli) leave the four real products in place, and the dot path ignores
- * the flag.  Any other flag bit is ARBGPU_ERR_INVALID. */
+ * radius products as without the flag.  When the shared scaling needs several blocks and the
+ * negligible-limb omission is on (ARBGPU_OMIT, see arbgpu_mat_mul), both parts drop their bits
+ * below thresholds shared by the parts (each part's error stays within (1/32) 2^-p times the sum
+ * of |a b| over its own terms); when the truncated parts fit one shared block, eq. 2 runs on them
+ * and each part is rounded once, and otherwise four real products, each with its own omission,
+ * run instead.  With the omission off, the inner range is cut once for both parts (Section IV-C's
+ * second suggestion: the greedy extraction on the larger top and the smaller bottom of each
+ * entry's two parts, over an inner order and scaling shared by the parts when the inner ordering
+ * is on); each full block's Re and Im come from three exact products and are added into the
+ * parts' window accumulators, the basecase blocks become complex dot products.  Blocks the
+ * tensor-core residue kernel cannot take (more than 32 chunks or 128 moduli) leave the four real
+ * products in place, and the dot path ignores the flag.  Any other flag bit is
+ * ARBGPU_ERR_INVALID. */
 #define ARBGPU_MM_COMPLEX_3M 1u
 
 /*
@@ -333,7 +338,9 @@ arbgpu_status arbgpu_mat_mul_batched_workspace_size(arbgpu_ctx *ctx,
  *          the larger top and smaller bottom of each entry's two parts (Section IV-C; one record
  *          for the whole complex product); 3: one block of the operands with their negligible
  *          limbs omitted (see arbgpu_mat_mul); 4: the shared blocks of kind 2 over an inner
- *          order and scaling shared by both parts (listed as for kind 1)
+ *          order and scaling shared by both parts (listed as for kind 1); 5: one block shared by
+ *          both parts of a complex product by eq. 2 after both parts' negligible limbs were
+ *          omitted under thresholds shared by the parts
  *   h      the height bound, floor(1.25 min(p, max(p_A, p_B))) + 192
  *   K      the inner dimension
  *   nb     the number of blocks, then nb triples (start, stop, basecase): [start, stop) covers

@@ -505,9 +505,12 @@ struct SplitOut {
 //   A: mid = E A; r1 = U(|A|) under rowtop; r2 = U(R_A) under rowrad.
 //   B: mid = B F; r1 = V(R_B) under colrad; r2 = V(|B| + R_B) under colplus.
 //   Columns [k0, k0 + K) of the operand form the block; columns K..Kp of the planes are zero.
+//   trunc (or null): per line, the exponent below which the line's bits were dropped (INT64_MIN:
+//   none); every nonzero entry of such a line carries 2^trunc more radius.
 __global__ void split_kernel(const BallsView X, bool is_b, int64_t rows, int64_t k0, int64_t K,
                              int64_t Kp, int64_t ld, int S, const int64_t *bot, const int64_t *top,
-                             const int64_t *radtop, const int64_t *plustop, SplitOut o) {
+                             const int64_t *radtop, const int64_t *plustop, SplitOut o,
+                             const int64_t *trunc) {
   const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= rows * Kp) return;
   const int64_t r = idx / Kp, k = idx - (idx / Kp) * Kp;
@@ -530,7 +533,8 @@ __global__ void split_kernel(const BallsView X, bool is_b, int64_t rows, int64_t
   } else {
     for (int t = 0; t < S; ++t) o.mid[(int64_t)t * plane + off] = z;
   }
-  const Mag rad{__ldg(X.rad_man + e), __ldg(X.rad_exp + e)};
+  Mag rad{__ldg(X.rad_man + e), __ldg(X.rad_exp + e)};
+  if (trunc && nz && trunc[r] != INT64_MIN) rad = mag_add_up(rad, Mag{1u << 29, trunc[r] + 1});
   const Mag absm = nz ? mid_upper(X, e, ex) : Mag{0u, 0};
   if (!is_b) {
     if (o.r1) put_small_digits(window_up(absm.man, absm.exp, top[r]), o.r1 + off, plane);
@@ -3894,7 +3898,7 @@ static arbgpu_status run_block_engine(arbgpu_ctx *ctx, const BlockWs &w, uint8_t
     LaunchScope sc(ctx, s, "split_a", n);
     split_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(Av, false, M, k0, Kb, Kp, lda,
                                                              plan ? 0 : SA, ln.rbot, ln.rtop,
-                                                             ln.rrad, nullptr, o);
+                                                             ln.rrad, nullptr, o, ln.rtrunc);
   }
   if (!plan) {
     const int64_t n = N * Kp;
@@ -3902,7 +3906,7 @@ static arbgpu_status run_block_engine(arbgpu_ctx *ctx, const BlockWs &w, uint8_t
     LaunchScope sc(ctx, s, "split_b", n);
     split_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(Bv, true, N, k0, Kb, Kp, ldb,
                                                              plan ? 0 : SB, ln.cbot, ln.ctop,
-                                                             ln.crad, ln.cplus, o);
+                                                             ln.crad, ln.cplus, o, ln.ctrunc);
   }
   if (cudaGetLastError() != cudaSuccess) return ARBGPU_ERR_CUDA;
   if (plan) {
@@ -4085,7 +4089,8 @@ static arbgpu_status run_radius(arbgpu_ctx *ctx, const BlockWs &w, uint8_t *ws,
     SplitOut o{nullptr, radB ? rA1 : nullptr, radA ? rA2 : nullptr};
     LaunchScope sc(ctx, s, "split_a", n);
     split_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(Av, false, M, k0, Kb, Kp, lda, 0,
-                                                             ln.rbot, ln.rtop, ln.rrad, nullptr, o);
+                                                             ln.rbot, ln.rtop, ln.rrad, nullptr, o,
+                                                             ln.rtrunc);
   }
   {
     const int64_t n = N * Kp;
@@ -4093,7 +4098,7 @@ static arbgpu_status run_radius(arbgpu_ctx *ctx, const BlockWs &w, uint8_t *ws,
     LaunchScope sc(ctx, s, "split_b", n);
     split_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(Bv, true, N, k0, Kb, Kp, ldb, 0,
                                                              ln.cbot, ln.ctop, ln.crad, ln.cplus,
-                                                             o);
+                                                             o, ln.ctrunc);
   }
   if (cudaGetLastError() != cudaSuccess) return ARBGPU_ERR_CUDA;
   return radius_gemm(ctx, w, ws, M, N, Kp, radA, radB, s, rp1, rp2);
@@ -4296,6 +4301,94 @@ static arbgpu_status omit_product(arbgpu_ctx *ctx, const BlockWs &w, uint8_t *ws
   out->hs = os;
   out->ok = true;
   return ARBGPU_OK;
+}
+
+// ---- the omission for eq. 2 (Section IV-B's last paragraph under Section IV-C's shared scaling).
+// Reading: both parts of a row of A (a column of B) drop their bits below one threshold, so the
+// truncated parts keep one scaling per line shared by both parts.  With E_q the per-entry bound
+// of output part q (its two real products, maxplus_top_kernel) and the shared line tops,
+// tau_i = min_{q, j} (E_q,ij - ctop_j) - p - G and sigma_j = min_{q, i} (E_q,ij - rtop_i) - p - G,
+// G = bc(K) + 9: part q changes by less than 4 K 2^(E_q,ij - p - G) <= (1/32) 2^-p times the sum
+// of |a b| over its terms.  Every nonzero entry of a truncated line, in either part, carries
+// 2^tau (2^sigma) more radius (split_kernel adds it to the radius operands).
+
+// Rows: one warp per row of A.  Writes the shared truncated bottoms and tau (INT64_MIN: none), each
+// part's radius line (rrad_q raised to tau + 1 where part q's row is nonzero), and folds the shared
+// row heights into st[0].hA and each part's radius flag into st[1 + q].radA.
+__global__ void __launch_bounds__(256) omission_eq2_rows_kernel(
+    const int64_t *E0, const int64_t *E1, int64_t M, int64_t N, const int64_t *rtop,
+    const int64_t *rbot, const int64_t *ctop, const int64_t *rtop0, const int64_t *rtop1,
+    const int64_t *rrad0, const int64_t *rrad1, int64_t off, int64_t *obot, int64_t *otrunc,
+    int64_t *orad0, int64_t *orad1, BlockStats *st) {
+  const int lane = threadIdx.x & 31;
+  const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (i >= M) return;
+  long long m = INT64_MAX;
+  for (int64_t j = lane; j < N; j += 32) {
+    const int64_t e0 = E0[i * N + j], e1 = E1[i * N + j];
+    if (e0 != INT64_MIN) m = min(m, (long long)(e0 - ctop[j]));
+    if (e1 != INT64_MIN) m = min(m, (long long)(e1 - ctop[j]));
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m = min(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if (lane != 0) return;
+  int64_t bot = rbot[i], t = INT64_MIN;
+  if (m != INT64_MAX && rtop[i] != INT64_MIN && bot < m - off) {
+    t = m - off;
+    bot = t;
+  }
+  obot[i] = bot;
+  otrunc[i] = t;
+  const int64_t *pt[2] = {rtop0, rtop1}, *pr[2] = {rrad0, rrad1};
+  int64_t *po[2] = {orad0, orad1};
+  for (int q = 0; q < 2; ++q) {
+    int64_t rr = pr[q][i];
+    if (t != INT64_MIN && pt[q][i] != INT64_MIN) rr = rr > t + 1 ? rr : t + 1;
+    po[q][i] = rr;
+    if (rr != INT64_MIN) atomicOr(&st[1 + q].radA, 1);
+  }
+  if (rtop[i] != INT64_MIN) atomic_max_i64(&st[0].hA, rtop[i] - bot);
+}
+
+// Columns: 32 columns x 8 row slices per CTA, the slices' minima combined in shared memory; the
+// same outputs for the columns of B (radius and |y| + r_y lines of each part, flags in radB).
+__global__ void __launch_bounds__(256) omission_eq2_cols_kernel(
+    const int64_t *E0, const int64_t *E1, int64_t M, int64_t N, const int64_t *rtop,
+    const int64_t *ctop, const int64_t *cbot, const int64_t *ctop0, const int64_t *ctop1,
+    const int64_t *crad0, const int64_t *crad1, int64_t off, int64_t *obot, int64_t *otrunc,
+    int64_t *orad0, int64_t *orad1, int64_t *oplus0, int64_t *oplus1, BlockStats *st) {
+  __shared__ long long s_m[8][32];
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  const int64_t j = (int64_t)blockIdx.x * 32 + tx;
+  long long m = INT64_MAX;
+  if (j < N)
+    for (int64_t i = ty; i < M; i += 8) {
+      const int64_t e0 = E0[i * N + j], e1 = E1[i * N + j];
+      if (e0 != INT64_MIN) m = min(m, (long long)(e0 - rtop[i]));
+      if (e1 != INT64_MIN) m = min(m, (long long)(e1 - rtop[i]));
+    }
+  s_m[ty][tx] = m;
+  __syncthreads();
+  if (ty != 0 || j >= N) return;
+  for (int q = 1; q < 8; ++q) m = min(m, s_m[q][tx]);
+  int64_t bot = cbot[j], t = INT64_MIN;
+  if (m != INT64_MAX && ctop[j] != INT64_MIN && bot < m - off) {
+    t = m - off;
+    bot = t;
+  }
+  obot[j] = bot;
+  otrunc[j] = t;
+  const int64_t *pt[2] = {ctop0, ctop1}, *pr[2] = {crad0, crad1};
+  int64_t *po[2] = {orad0, orad1}, *pp[2] = {oplus0, oplus1};
+  for (int q = 0; q < 2; ++q) {
+    int64_t rr = pr[q][j];
+    if (t != INT64_MIN && pt[q][j] != INT64_MIN) rr = rr > t + 1 ? rr : t + 1;
+    po[q][j] = rr;
+    const int64_t mx = pt[q][j] > rr ? pt[q][j] : rr;  // |y| + r_y < 2^(max(top, rexp) + 1)
+    pp[q][j] = mx == INT64_MIN ? INT64_MIN : mx + 1;
+    if (rr != INT64_MIN) atomicOr(&st[1 + q].radB, 1);
+  }
+  if (ctop[j] != INT64_MIN) atomic_max_i64(&st[0].hB, ctop[j] - bot);
 }
 
 // Output of a real product that may be rounded straight from one exact block.
@@ -4544,12 +4637,12 @@ static arbgpu_status plan_3m(arbgpu_ctx *ctx, const BlockWs &w, uint8_t *ws, con
   hs.pA = hst[0].pA > hst[1].pA ? hst[0].pA : hst[1].pA;
   hs.pB = hst[2].pB > hst[3].pB ? hst[2].pB : hst[3].pB;
   const int64_t h = height_bound(prec, hs);
+  p->hA = hm.hA;  // (the shared heights, also when they need several blocks)
+  p->hB = hm.hB;
   if (hm.hA > h || hm.hB > h) {
     p->several = true;
     return ARBGPU_OK;
   }
-  p->hA = hm.hA;
-  p->hB = hm.hB;
   p->NM = crt_moduli_for_bits((int)(p->hA + p->hB + bit_length(K) + 3));
   if (p->NM > w.NMmax) return ARBGPU_OK;
   p->plan = crt_plan(p->NM);
@@ -4646,8 +4739,9 @@ static arbgpu_status run_3m(arbgpu_ctx *ctx, const BlockWs &w, uint8_t *ws, cons
     const int part = pr[0], xa = pr[1], yb = pr[2];
     const bool radA = hst[xa].radA != 0, radB = hst[2 + yb].radB != 0;
     if (!radA && !radB) continue;
-    const Lines ln{rowsL[xa].rtop, rowsL[xa].rbot, rowsL[xa].rrad, colsL[yb].ctop,
-                   colsL[yb].cbot, colsL[yb].crad, colsL[yb].cplus};
+    const Lines ln{rowsL[xa].rtop,  rowsL[xa].rbot, rowsL[xa].rrad,   colsL[yb].ctop,
+                   colsL[yb].cbot,  colsL[yb].crad, colsL[yb].cplus,  rowsL[xa].rtrunc,
+                   colsL[yb].ctrunc};
     AccArgs aa{};
     const arbgpu_status st = run_radius(ctx, w, ws, Av[xa], Bv[yb], M, N, lda, ldb, 0, K, radA,
                                         radB, ln, s, &aa.rp1, &aa.rp2);
@@ -4694,6 +4788,71 @@ static arbgpu_status run_3m(arbgpu_ctx *ctx, const BlockWs &w, uint8_t *ws, cons
     launch_block_round(ctx, ra, s);
   }
   return cudaGetLastError() == cudaSuccess ? ARBGPU_OK : ARBGPU_ERR_CUDA;
+}
+
+// The omission for eq. 2 under p3's shared lines (E_0, E_1 already at w.etop): the thresholds,
+// the truncated shared bottoms, each part's radius lines carrying the thresholds (rows_o[q],
+// cols_o[q]) and hst_o (hst with the truncated parts' radius flags).  *po is planned as one block
+// when the truncated shared heights fit h and the tensor-core residue kernel takes them (one
+// statistics read-back); otherwise po->ok stays false.
+static arbgpu_status omit_eq2(arbgpu_ctx *ctx, const BlockWs &w, uint8_t *ws, const Plan3M &p3,
+                              const Lines *rowsL, const Lines *colsL, const BlockStats *hst,
+                              int64_t M, int64_t K, int64_t N, int prec, cudaStream_t s,
+                              Plan3M *po, Lines *rows_o, Lines *cols_o, BlockStats *hst_o) {
+  *po = Plan3M{};
+  const int64_t off = (int64_t)prec + bit_length(K) + 9;
+  const int64_t *E0 = (const int64_t *)(ws + w.etop[0]), *E1 = (const int64_t *)(ws + w.etop[1]);
+  int64_t *rb = (int64_t *)(ws + w.om_rbot), *rt = (int64_t *)(ws + w.om_rtrunc);
+  int64_t *rr[2] = {(int64_t *)(ws + w.om_rrad), (int64_t *)(ws + w.e2rrad)};
+  int64_t *cb = (int64_t *)(ws + w.om_cbot), *ct = (int64_t *)(ws + w.om_ctrunc);
+  int64_t *cr[2] = {(int64_t *)(ws + w.om_crad), (int64_t *)(ws + w.e2crad)};
+  int64_t *cp[2] = {(int64_t *)(ws + w.om_cplus), (int64_t *)(ws + w.e2cplus)};
+  BlockStats *st = (BlockStats *)(ws + w.e2mstats);  // [3]: shared heights, part 0, part 1
+  if (cudaMemsetAsync(st, 0, 3 * sizeof(BlockStats), s) != cudaSuccess) return ARBGPU_ERR_CUDA;
+  {
+    LaunchScope sc(ctx, s, "omission", M * N);
+    omission_eq2_rows_kernel<<<(unsigned)((M + 7) / 8), 256, 0, s>>>(
+        E0, E1, M, N, p3.rtop, p3.rbot, p3.ctop, rowsL[0].rtop, rowsL[1].rtop, rowsL[0].rrad,
+        rowsL[1].rrad, off, rb, rt, rr[0], rr[1], st);
+    omission_eq2_cols_kernel<<<(unsigned)((N + 31) / 32), 256, 0, s>>>(
+        E0, E1, M, N, p3.rtop, p3.ctop, p3.cbot, colsL[0].ctop, colsL[1].ctop, colsL[0].crad,
+        colsL[1].crad, off, cb, ct, cr[0], cr[1], cp[0], cp[1], st);
+    if (cudaGetLastError() != cudaSuccess) return ARBGPU_ERR_CUDA;
+  }
+  BlockStats os[3];
+  const arbgpu_status rs = read_stats(ctx, st, os, 3, s);
+  if (rs != ARBGPU_OK) return rs;
+  BlockStats hs{};
+  hs.pA = hst[0].pA > hst[1].pA ? hst[0].pA : hst[1].pA;
+  hs.pB = hst[2].pB > hst[3].pB ? hst[2].pB : hst[3].pB;
+  const int64_t h = height_bound(prec, hs);
+  if (os[0].hA > h || os[0].hB > h) return ARBGPU_OK;
+  Plan3M &p = *po;
+  p.hA = os[0].hA;
+  p.hB = os[0].hB;
+  p.NM = crt_moduli_for_bits((int)((p.hA > 0 ? p.hA : 0) + (p.hB > 0 ? p.hB : 0) +
+                                   bit_length(K) + 3));
+  if (p.NM > w.NMmax) return ARBGPU_OK;
+  p.plan = crt_plan(p.NM);
+  if (!p.plan || p.plan->NMW + 1 > RD_MAXW) return ARBGPU_OK;
+  p.nch = (int)(((p.hA > p.hB ? p.hA : p.hB) + 2 + 31) / 32) + 1;
+  if (!residue_tc_layout(p.nch, p.NM, false, (M > N ? M : N) * w.Kp, &p.L)) return ARBGPU_OK;
+  p.rtop = p3.rtop;
+  p.rbot = rb;
+  p.ctop = p3.ctop;
+  p.cbot = cb;
+  for (int q = 0; q < 2; ++q) {
+    rows_o[q] = Lines{rowsL[q].rtop, rowsL[q].rbot, rr[q], nullptr, nullptr, nullptr, nullptr,
+                      rt, nullptr};
+    cols_o[q] = Lines{nullptr, nullptr, nullptr, colsL[q].ctop, colsL[q].cbot, cr[q], cp[q],
+                      nullptr, ct};
+    hst_o[q] = hst[q];
+    hst_o[q].radA = os[1 + q].radA;
+    hst_o[2 + q] = hst[2 + q];
+    hst_o[2 + q].radB = os[1 + q].radB;
+  }
+  p.ok = true;
+  return ARBGPU_OK;
 }
 
 // accumulate_product over the inner order (see "inner ordering" above): the order and scaling
@@ -5372,10 +5531,43 @@ arbgpu_status block_finish(arbgpu_ctx *ctx, const arbgpu_balls *C, const arbgpu_
     *used_block = true;
     return ARBGPU_OK;
   }
+  // eq. 2 after the negligible limbs of both parts were omitted under shared thresholds, when the
+  // truncated parts fit one shared block: one rounding per part, as for the one-block case.  When
+  // they do not, four real products, each with its own omission (per-product thresholds drop more
+  // bits than thresholds shared by the parts), do less work than eq. 2 over several blocks; eq. 2
+  // over several blocks runs when the omission is not wanted (or switched off).
+  bool several_eq2 = p3.several;
+  if (p3.several) {
+    BlockStats hm{};
+    hm.hA = p3.hA;
+    hm.hB = p3.hB;
+    if (omission_wanted(prec, K, hm, false)) {
+      arbgpu_status so = etop_of(0);
+      if (so == ARBGPU_OK) so = etop_of(1);
+      if (so != ARBGPU_OK) return so;
+      Plan3M po{};
+      Lines ro[2], co[2];
+      BlockStats ho[4];
+      so = omit_eq2(ctx, w, ws, p3, rowsL, colsL, hst, M, K, N, prec, s, &po, ro, co, ho);
+      if (so != ARBGPU_OK) return so;
+      if (po.ok) {
+        BlockStats hs{};
+        hs.pA = hst[0].pA > hst[1].pA ? hst[0].pA : hst[1].pA;
+        hs.pB = hst[2].pB > hst[3].pB ? hst[2].pB : hst[3].pB;
+        log_plan(ctx, 5, height_bound(prec, hs), K, {0, (int32_t)K, 0});
+        const arbgpu_status s3 = run_3m(ctx, w, ws, po, C, Av, Bv, ro, co, ho, M, K, N, lda,
+                                        ldb, ldc, prec, av, s);
+        if (s3 != ARBGPU_OK) return s3;
+        *used_block = true;
+        return ARBGPU_OK;
+      }
+      several_eq2 = false;
+    }
+  }
   // eq. 2 over several blocks shared by both parts (over their shared inner order when the
   // inner ordering is on)
   bool eq2 = false;
-  if (p3.several) {
+  if (several_eq2) {
     const std::function<arbgpu_status()> prep2 = [&etop_of]() {
       const arbgpu_status e0 = etop_of(0);
       return e0 != ARBGPU_OK ? e0 : etop_of(1);

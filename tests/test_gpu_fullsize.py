@@ -4,7 +4,8 @@
   (exponent blocks along the inner index) and the literal one (i.i.d. exponents): containment of
   the exact product and the accuracy bound |m - S| <= 2^-p sum |a b| on every sampled entry, by
   four real products with their negligible limbs omitted, and with ARBGPU_MM_COMPLEX_3M by eq. 2
-  over blocks shared by both parts (over their shared inner order);
+  on both parts truncated under shared thresholds (or four products where those leave several
+  blocks);
 * the grouped batch of 256 real products (N in [16, 512], p in {64, ..., 1024}) in one
   arbgpu_mat_mul_batched call: block items (one exponent block each) bit-exact RNE_p of the exact
   sum, or within the bound where negligible limbs were omitted, classical items bit-exact against
@@ -46,14 +47,12 @@ def test_complex2048_sampled(arb, structured, m3):
     arb.mat_mul(C, A, B, n, n, n, p, flags=flags, workspace=ws, ctx=ctx)
     assert ctx.status() == 0
     plans = ctx.last_plans()
-    if m3:
-        # eq. 2 over blocks shared by both parts, over their shared inner order: one record whose
-        # blocks tile the inner range
-        assert len(plans) == 1 and plans[0]["kind"] == 4
-        bl = plans[0]["blocks"]
-        assert bl[0][0] == 0 and bl[-1][1] == n
-        assert all(a[1] == b[0] for a, b in zip(bl, bl[1:]))
-        assert sorted(plans[0]["order"]) == list(range(n))
+    if m3 and len(plans) == 1:
+        # eq. 2 on the parts truncated under thresholds shared by both parts: one shared block
+        assert plans[0]["kind"] == 5 and plans[0]["blocks"] == [(0, n, False)]
+    elif m3:
+        # the shared thresholds left several blocks: four real products, each with its omission
+        assert [r["kind"] for r in plans] == [3, 3, 3, 3]
     else:
         # with the negligible limbs omitted, each real product of this workload is one block
         assert [r["kind"] for r in plans] == [3, 3, 3, 3]

@@ -93,3 +93,84 @@ def test_omission_off_keeps_every_bit(arb):
     assert "omission" in names
     check_bounds(off, A, B, M, K, N, p, ents)
     check_bounds(on, A, B, M, K, N, p, ents)
+
+
+# ---- eq. 2 with the omission under thresholds shared by both parts
+# (``oracle.alg2.omission_thresholds_complex``)
+
+def _eq2_case(kind):
+    from synth.workloads import complex_matmul_laplace
+    if kind == "wide":  # 1024-bit entries at p = 64
+        rng = np.random.default_rng(31)
+        n, p = 40, 64
+        mk = lambda: random_balls(rng, n * n, 16, 1024, -6, 6, rad_bits=1000,  # noqa
+                                  rad_zero_frac=0.5)
+        return [mk(), mk()], [mk(), mk()], n, p
+    if kind == "lopsided":  # A_re and B_im 2^200 below A_im and B_re: Re ~ 2^-200 Im
+        rng = np.random.default_rng(32)
+        n, p = 36, 128
+
+        def mk(low):
+            d = -200 if low else 0
+            return random_balls(rng, n * n, 8, 512, -5 + d, 5 + d, rad_bits=500,
+                                rad_zero_frac=0.5)
+        return [mk(True), mk(False)], [mk(False), mk(True)], n, p
+    case = complex_matmul_laplace(n=64, structured=(kind == "laplace"))
+    return case.A, case.B, 64, case.prec
+
+
+def _truncated_part(A2, B2, K, N, tau, sigma, part, i, j):
+    """Part `part` of entry (i, j) of the exact complex product of the truncated operands."""
+    from fractions import Fraction
+
+    def val(raw, idx, t):
+        v, e = alg2.truncate_value(alg2.top_bottom(raw, idx), t)
+        return Fraction(v) * Fraction(2) ** e
+    pairs = (((0, 0, 1), (1, 1, -1)), ((0, 1, 1), (1, 0, 1)))[part]
+    return sum(sg * val(A2[x], i * K + k, tau[i]) * val(B2[y], k * N + j, sigma[j])
+               for x, y, sg in pairs for k in range(K))
+
+
+@pytest.mark.parametrize("kind", ["wide", "lopsided", "laplace"])
+def test_eq2_omitted_single_block_is_rne_of_the_truncated_product(arb, kind):
+    """Eq. 2 with ARBGPU_MM_COMPLEX_3M where the parts' shared scaling needs several blocks: both
+    parts drop their bits below thresholds shared by the parts and the truncated parts form one
+    shared block (record kind 5), so every sampled midpoint of Re and Im is exactly RNE_p of the
+    oracle's truncated complex product, and every ball contains the exact product within the
+    accuracy bound (per part: the lopsided case fails it if the thresholds follow the larger
+    part's bound alone)."""
+    A2, B2, n, p = _eq2_case(kind)
+    h, blocks = alg2.plan_complex_shared(A2, B2, n, n, n, p)
+    assert len(blocks) > 1  # several shared blocks without the omission
+    outs, names = run_cmm(arb, A2, B2, n, n, n, p, arb.ALG_BLOCK, trace=True,
+                          flags=arb.MM_COMPLEX_3M)
+    assert "omission" in names and "z3m" in names and "plan" not in names
+    assert arb.default_context().last_plans() == [dict(kind=5, h=h, K=n,
+                                                       blocks=[(0, n, False)])]
+    tau, sigma = alg2.omission_thresholds_complex(A2, B2, n, n, n, p)
+    onl = (p + 63) // 64
+    rng2 = np.random.default_rng(5)
+    ents = [(int(a), int(b)) for a, b in zip(rng2.integers(0, n, 40), rng2.integers(0, n, 40))]
+    for i, j in ents:
+        idx = i * n + j
+        for part in (0, 1):
+            T = _truncated_part(A2, B2, n, n, tau, sigma, part, i, j)
+            out = outs[part]
+            got = ([int(out.limbs[k, idx]) for k in range(onl)], int(out.exp[idx]),
+                   int(out.flags[idx]))
+            assert got == _rne(T, p, onl), (kind, part, i, j)
+    check_complex(outs, A2, B2, n, n, n, p, ents)
+
+
+def test_eq2_falls_back_to_four_products_when_the_shared_omission_leaves_several_blocks(arb):
+    """The literal Laplace workload at N = 64: thresholds shared by the parts leave rows taller
+    than h, so the flag runs four real products, each with its own omission; the balls stay
+    rigorous."""
+    A2, B2, n, p = _eq2_case("laplace_literal")
+    outs, names = run_cmm(arb, A2, B2, n, n, n, p, arb.ALG_BLOCK, trace=True,
+                          flags=arb.MM_COMPLEX_3M)
+    plans = arb.default_context().last_plans()
+    assert len(plans) == 4 and "z3m" not in names
+    rng2 = np.random.default_rng(6)
+    check_complex(outs, A2, B2, n, n, n, p, [(int(a), int(b)) for a, b in
+                                             zip(rng2.integers(0, n, 40), rng2.integers(0, n, 40))])
