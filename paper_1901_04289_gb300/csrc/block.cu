@@ -3239,10 +3239,17 @@ constexpr int ACC_MAX = 24;
 constexpr int MP_T = 128, MP_K = 32, MP_PAD = 4;
 constexpr int32_t MP_FLOOR = -(1 << 30);
 
+// The same product on 16-bit halves (maxplus16_top_kernel), two outputs per instruction, when
+// every nonzero entry of both operands lies within 2^13 - 1 of its line's top: live relative tops
+// are then in [-8191, 0], zeros take -16384, so a sum with a zero (<= -16384) stays below every
+// sum of two live entries (>= -16382) and no sum leaves int16.  The live maxima, hence the bound
+// of every entry with a nonzero product, are those of the int32 kernel.
+constexpr int32_t MP16_LIVE = 8191, MP16_ZERO = -16384;
+
 // rel[r * cols + c] = top(X[r * ld + c]) - ref, ref = rt[r] (by_row) or rt[c], clamped; zeros and
-// empty lines give the floor.
+// empty lines give the floor.  *wide is set when a nonzero entry lies below -MP16_LIVE.
 __global__ void rel_tops_kernel(const BallsView X, int64_t ld, int64_t rows, int64_t cols,
-                                const int64_t *rt, bool by_row, int32_t *rel) {
+                                const int64_t *rt, bool by_row, int32_t *rel, int *wide) {
   const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= rows * cols) return;
   const int64_t r = idx / cols, c = idx - (idx / cols) * cols;
@@ -3253,14 +3260,98 @@ __global__ void rel_tops_kernel(const BallsView X, int64_t ld, int64_t rows, int
   if (!(fl & ARBGPU_FLAG_ZERO) && ref != INT64_MIN) {
     const int64_t d = __ldg(X.exp + e) - ref;
     v = d < MP_FLOOR ? MP_FLOOR : (int32_t)d;
+    if (d < -MP16_LIVE) atomicOr(wide, 1);
   }
   rel[idx] = v;
 }
 
+// One operand value as the 16-bit half of maxplus16_top_kernel.
+__device__ __forceinline__ uint32_t mp16_half(int32_t v) {
+  return (uint32_t)(uint16_t)(int16_t)(v == MP_FLOOR ? MP16_ZERO : v);
+}
+
+// maxplus_top_kernel on 16-bit halves: the same tiles, A staged as (a, a) and B as (b_j, b_j+1)
+// pairs, each __viaddmax_s16x2 giving max(a + b, acc) for two columns.  Returns at once when
+// either operand's `wide` flag is set (the int32 kernel then runs).
+__global__ void __launch_bounds__(256) maxplus16_top_kernel(
+    const int32_t *dX, const int32_t *dY, const int *wideX, const int *wideY, const int64_t *rt,
+    const int64_t *ct, int64_t M, int64_t K, int64_t N, int64_t *etop, int first) {
+  if (*wideX | *wideY) return;
+  __shared__ __align__(16) uint32_t sa[MP_K][MP_T + MP_PAD];
+  __shared__ __align__(16) uint32_t sb[MP_K][MP_T / 2 + MP_PAD];
+  const int64_t i0 = (int64_t)blockIdx.y * MP_T, j0 = (int64_t)blockIdx.x * MP_T;
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  uint32_t acc[8][4];
+#pragma unroll
+  for (int a = 0; a < 8; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) acc[a][b] = 0x80008000u;  // -32768 in both halves
+  // this thread's 16 loads of each tile: A rows r = t / 32 (kk = t % 32); B column c = t % 128
+  // (the same for every u), rows kb = t / 128
+  int32_t ra[16], rb[16];
+  auto load = [&](int64_t k0) {
+#pragma unroll
+    for (int u = 0; u < 16; ++u) {
+      const int t = threadIdx.x + 256 * u;
+      const int kk = t % MP_K, r = t / MP_K;
+      const int64_t i = i0 + r, k = k0 + kk;
+      ra[u] = (i < M && k < K) ? __ldg(dX + i * K + k) : MP_FLOOR;
+      const int c = t % MP_T, kb = t / MP_T;
+      const int64_t j = j0 + c, k2 = k0 + kb;
+      rb[u] = (j < N && k2 < K) ? __ldg(dY + k2 * N + j) : MP_FLOOR;
+    }
+  };
+  load(0);
+  const int c = threadIdx.x % MP_T;  // this thread's B column in the tile (even: it packs a pair)
+  for (int64_t k0 = 0; k0 < K; k0 += MP_K) {
+#pragma unroll
+    for (int u = 0; u < 16; ++u) {
+      const int t = threadIdx.x + 256 * u;
+      const uint32_t ha = mp16_half(ra[u]);
+      sa[t % MP_K][t / MP_K] = ha | (ha << 16);
+      const uint32_t hb = mp16_half(rb[u]);
+      const uint32_t hn = __shfl_xor_sync(0xffffffffu, hb, 1);  // column c ^ 1
+      if (!(c & 1)) sb[t / MP_T][c >> 1] = hb | (hn << 16);
+    }
+    __syncthreads();
+    if (k0 + MP_K < K) load(k0 + MP_K);
+#pragma unroll 4
+    for (int kk = 0; kk < MP_K; ++kk) {
+      const uint4 a0 = *(const uint4 *)&sa[kk][8 * ty], a1 = *(const uint4 *)&sa[kk][8 * ty + 4];
+      const uint4 b0 = *(const uint4 *)&sb[kk][4 * tx];
+      const uint32_t av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+      const uint32_t bv[4] = {b0.x, b0.y, b0.z, b0.w};
+#pragma unroll
+      for (int a = 0; a < 8; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) acc[a][b] = __viaddmax_s16x2(av[a], bv[b], acc[a][b]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int a = 0; a < 8; ++a) {
+    const int64_t i = i0 + 8 * ty + a;
+    if (i >= M) continue;
+#pragma unroll
+    for (int b = 0; b < 8; ++b) {
+      const int64_t j = j0 + 8 * tx + b;
+      if (j >= N) continue;
+      const int32_t v = (int32_t)(int16_t)(uint16_t)(acc[a][b >> 1] >> (16 * (b & 1)));
+      const bool live = rt[i] != INT64_MIN && ct[j] != INT64_MIN;
+      const int64_t e = live ? rt[i] + ct[j] + (int64_t)v : INT64_MIN;
+      int64_t *o = etop + i * N + j;
+      if (first || e > *o) *o = e;
+    }
+  }
+}
+
+// (wideX / wideY null: always runs; otherwise only when one of the flags is set)
 __global__ void __launch_bounds__(256) maxplus_top_kernel(const int32_t *dX, const int32_t *dY,
+                                                          const int *wideX, const int *wideY,
                                                           const int64_t *rt, const int64_t *ct,
                                                           int64_t M, int64_t K, int64_t N,
                                                           int64_t *etop, int first) {
+  if (wideX && !(*wideX | *wideY)) return;
   __shared__ __align__(16) int32_t sa[MP_K][MP_T + MP_PAD];
   __shared__ __align__(16) int32_t sb[MP_K][MP_T + MP_PAD];
   const int64_t i0 = (int64_t)blockIdx.y * MP_T, j0 = (int64_t)blockIdx.x * MP_T;
@@ -3321,6 +3412,25 @@ __global__ void __launch_bounds__(256) maxplus_top_kernel(const int32_t *dX, con
       if (first || e > *o) *o = e;
     }
   }
+}
+
+// The max-plus bound of X Y into E (first: overwrite, else raise): the 16-bit kernel, and the
+// int32 kernel for operands whose `wide` flag rel_tops_kernel set (each returns at once where the
+// other applies).  ARBGPU_MAXPLUS16=0 keeps the int32 kernel alone.
+static void launch_maxplus(arbgpu_ctx *ctx, cudaStream_t s, const int32_t *dX, const int32_t *dY,
+                           const int *wideX, const int *wideY, const int64_t *rt,
+                           const int64_t *ct, int64_t M, int64_t K, int64_t N, int64_t *E,
+                           int first) {
+  const char *env16 = getenv("ARBGPU_MAXPLUS16");
+  const bool use16 = !(env16 && !strcmp(env16, "0"));
+  LaunchScope sc(ctx, s, "maxplus_top", M * K * N);
+  const dim3 grid((unsigned)((N + MP_T - 1) / MP_T), (unsigned)((M + MP_T - 1) / MP_T));
+  if (!use16) {
+    maxplus_top_kernel<<<grid, 256, 0, s>>>(dX, dY, nullptr, nullptr, rt, ct, M, K, N, E, first);
+    return;
+  }
+  maxplus16_top_kernel<<<grid, 256, 0, s>>>(dX, dY, wideX, wideY, rt, ct, M, K, N, E, first);
+  maxplus_top_kernel<<<grid, 256, 0, s>>>(dX, dY, wideX, wideY, rt, ct, M, K, N, E, first);
 }
 
 // acc += T_s 2^sigma_s (bits below the window truncated toward zero, one ulp each time),
@@ -3606,6 +3716,7 @@ struct BlockWs {
   size_t acc[2], err[2], rman[2], rexp[2], ilimbs[2], iexp[2], iflags[2], irman[2], irexp[2], bk[2];
   size_t etop[2];  // per-entry exponent bound of the accumulated products (maxplus_top_kernel)
   size_t relA[2], relB[2];  // tops of A's and B's parts relative to their lines (int32)
+  size_t relwide;           // their `wide` flags (A0, A1, B0, B1): see maxplus16_top_kernel
   // negligible-limb omission: one product's E, its truncated lines and their statistics
   size_t eprod, om_rbot, om_rrad, om_rtrunc, om_cbot, om_crad, om_cplus, om_ctrunc, om_stats;
   // multimodular engine: residue planes, residue products, tables
@@ -3694,6 +3805,7 @@ static BlockWs block_ws(arbgpu_ctx *ctx, int64_t M, int64_t K, int64_t N, int pr
     w.relA[q] = take(4 * (size_t)M * K);
     w.relB[q] = take(4 * (size_t)K * N);
   }
+  w.relwide = take(4 * sizeof(int));
   w.eprod = take(8 * MN);
   w.om_rbot = take(8 * (size_t)M);
   w.om_rrad = take(8 * (size_t)M);
@@ -4251,19 +4363,16 @@ struct Omitted {
 // block of height <= h (h of the untruncated operands' precisions) and the tensor-core residue
 // kernel takes them; otherwise nothing is used.
 static arbgpu_status omit_product(arbgpu_ctx *ctx, const BlockWs &w, uint8_t *ws,
-                                  const int32_t *dX, const int32_t *dY, int64_t M, int64_t K,
-                                  int64_t N, int prec, const Lines &full, const BlockStats &hs,
-                                  cudaStream_t s, Omitted *out) {
+                                  const int32_t *dX, const int32_t *dY, const int *wideX,
+                                  const int *wideY, int64_t M, int64_t K, int64_t N, int prec,
+                                  const Lines &full, const BlockStats &hs, cudaStream_t s,
+                                  Omitted *out) {
   out->ok = false;
   int bk = 0;
   for (int64_t v = K; v > 0; v >>= 1) ++bk;
   const int64_t off = (int64_t)prec + bk + 8;
   int64_t *E = (int64_t *)(ws + w.eprod);
-  {
-    LaunchScope sc(ctx, s, "maxplus_top", M * K * N);
-    const dim3 grid((unsigned)((N + MP_T - 1) / MP_T), (unsigned)((M + MP_T - 1) / MP_T));
-    maxplus_top_kernel<<<grid, 256, 0, s>>>(dX, dY, full.rtop, full.ctop, M, K, N, E, 1);
-  }
+  launch_maxplus(ctx, s, dX, dY, wideX, wideY, full.rtop, full.ctop, M, K, N, E, 1);
   int64_t *rb = (int64_t *)(ws + w.om_rbot), *rr = (int64_t *)(ws + w.om_rrad);
   int64_t *rt = (int64_t *)(ws + w.om_rtrunc);
   int64_t *cb = (int64_t *)(ws + w.om_cbot), *cr = (int64_t *)(ws + w.om_crad);
@@ -5355,18 +5464,25 @@ arbgpu_status block_finish(arbgpu_ctx *ctx, const arbgpu_balls *C, const arbgpu_
 
   // the operands' tops relative to their lines (rel_tops_kernel), once per operand part per call:
   // the max-plus bound of the accumulator's window and the negligible-limb omission use them
+  // (with a `wide` flag per operand part, zeroed before the first of them: the max-plus kernel
+  // they feed runs on 16-bit halves unless a flag is set)
   bool rel_done[4] = {false, false, false, false};  // A0, A1, B0, B1
+  int *wide = (int *)(ws + w.relwide);
+  auto wide_of = [&](int q) -> const int * { return wide + q; };
   auto ensure_rel = [&](int xa, int yb) -> arbgpu_status {
+    if (!rel_done[0] && !rel_done[1] && !rel_done[2] && !rel_done[3] &&
+        cudaMemsetAsync(wide, 0, 4 * sizeof(int), s) != cudaSuccess)
+      return ARBGPU_ERR_CUDA;
     if (!rel_done[xa]) {
       LaunchScope sc(ctx, s, "rel_tops", M * K);
       rel_tops_kernel<<<(unsigned)((M * K + 255) / 256), 256, 0, s>>>(
-          Av[xa], lda, M, K, rowsL[xa].rtop, true, (int32_t *)(ws + w.relA[xa]));
+          Av[xa], lda, M, K, rowsL[xa].rtop, true, (int32_t *)(ws + w.relA[xa]), wide + xa);
       rel_done[xa] = true;
     }
     if (!rel_done[2 + yb]) {
       LaunchScope sc(ctx, s, "rel_tops", K * N);
       rel_tops_kernel<<<(unsigned)((K * N + 255) / 256), 256, 0, s>>>(
-          Bv[yb], ldb, K, N, colsL[yb].ctop, false, (int32_t *)(ws + w.relB[yb]));
+          Bv[yb], ldb, K, N, colsL[yb].ctop, false, (int32_t *)(ws + w.relB[yb]), wide + 2 + yb);
       rel_done[2 + yb] = true;
     }
     return cudaGetLastError() == cudaSuccess ? ARBGPU_OK : ARBGPU_ERR_CUDA;
@@ -5382,8 +5498,8 @@ arbgpu_status block_finish(arbgpu_ctx *ctx, const arbgpu_balls *C, const arbgpu_
       if (so != ARBGPU_OK) return so;
       Omitted om{};
       so = omit_product(ctx, w, ws, (const int32_t *)(ws + w.relA[0]),
-                        (const int32_t *)(ws + w.relB[0]), M, K, N, prec, lines_of(0, 0), hs, s,
-                        &om);
+                        (const int32_t *)(ws + w.relB[0]), wide_of(0), wide_of(2), M, K, N, prec,
+                        lines_of(0, 0), hs, s, &om);
       if (so != ARBGPU_OK) return so;
       if (om.ok) {
         RoundArgs ra{};
@@ -5511,10 +5627,8 @@ arbgpu_status block_finish(arbgpu_ctx *ctx, const arbgpu_balls *C, const arbgpu_
       if (rs != ARBGPU_OK) return rs;
       const int32_t *dX = (const int32_t *)(ws + w.relA[pr.xa]);
       const int32_t *dY = (const int32_t *)(ws + w.relB[pr.yb]);
-      LaunchScope sc(ctx, s, "maxplus_top", M * K * N);
-      const dim3 grid((unsigned)((N + MP_T - 1) / MP_T), (unsigned)((M + MP_T - 1) / MP_T));
-      maxplus_top_kernel<<<grid, 256, 0, s>>>(dX, dY, rowsL[pr.xa].rtop, colsL[pr.yb].ctop, M, K,
-                                               N, et, first ? 1 : 0);
+      launch_maxplus(ctx, s, dX, dY, wide_of(pr.xa), wide_of(2 + pr.yb), rowsL[pr.xa].rtop,
+                     colsL[pr.yb].ctop, M, K, N, et, first ? 1 : 0);
       first = false;
     }
     return cudaGetLastError() == cudaSuccess ? ARBGPU_OK : ARBGPU_ERR_CUDA;
@@ -5593,8 +5707,8 @@ arbgpu_status block_finish(arbgpu_ctx *ctx, const arbgpu_balls *C, const arbgpu_
       if (so != ARBGPU_OK) return so;
       Omitted om{};
       so = omit_product(ctx, w, ws, (const int32_t *)(ws + w.relA[pr.xa]),
-                        (const int32_t *)(ws + w.relB[pr.yb]), M, K, N, prec,
-                        lines_of(pr.xa, pr.yb), hs, s, &om);
+                        (const int32_t *)(ws + w.relB[pr.yb]), wide_of(pr.xa),
+                        wide_of(2 + pr.yb), M, K, N, prec, lines_of(pr.xa, pr.yb), hs, s, &om);
       if (so != ARBGPU_OK) return so;
       if (om.ok) {
         so = accumulate_product(ctx, w, ws, Av[pr.xa], Bv[pr.yb], M, K, N, lda, ldb, prec,

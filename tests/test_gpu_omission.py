@@ -174,3 +174,45 @@ def test_eq2_falls_back_to_four_products_when_the_shared_omission_leaves_several
     rng2 = np.random.default_rng(6)
     check_complex(outs, A2, B2, n, n, n, p, [(int(a), int(b)) for a, b in
                                              zip(rng2.integers(0, n, 40), rng2.integers(0, n, 40))])
+
+
+# ---- the max-plus bound on 16-bit halves (maxplus16_top_kernel) against the int32 kernel
+
+def _wide_rows_case():
+    """Complex 512-bit entries at p = 64 whose rows of A span more than 2^13 bits of exponent
+    (column 0 sits 2^9000 above the rest): the int32 max-plus kernel runs there."""
+    rng = np.random.default_rng(77)
+    n, p = 40, 64
+    A2, B2 = [], []
+    for _ in "ri":
+        ea = rng.integers(-6, 6, size=n * n)
+        ea[np.arange(n) * n] += 9000
+        A2.append(random_balls(rng, n * n, 8, 512, exps=ea, rad_bits=500, rad_zero_frac=0.5))
+        B2.append(random_balls(rng, n * n, 8, 512, -6, 6, rad_bits=500, rad_zero_frac=0.5))
+    return A2, B2, n, p
+
+
+@pytest.mark.parametrize("kind,m3", [("laplace", False), ("laplace", True),
+                                     ("laplace_literal", True), ("lopsided", True),
+                                     ("wide_rows", False)])
+def test_maxplus16_gives_the_int32_results(arb, kind, m3):
+    """The window bound and the omission thresholds from the 16-bit max-plus kernel equal those of
+    the int32 kernel wherever a product is nonzero, so every output field is bit-identical with
+    ARBGPU_MAXPLUS16=0; rows wider than 2^13 bits take the int32 kernel (and the balls stay
+    rigorous)."""
+    from tests.gpu_util import env
+    A2, B2, n, p = _wide_rows_case() if kind == "wide_rows" else _eq2_case(kind)
+    flags = arb.MM_COMPLEX_3M if m3 else 0
+    runs = []
+    for v in ("1", "0"):
+        with env(ARBGPU_MAXPLUS16=v):
+            outs, names = run_cmm(arb, A2, B2, n, n, n, p, arb.ALG_BLOCK, trace=True, flags=flags)
+        assert "maxplus_top" in names
+        runs.append(outs)
+    for a, b in zip(*runs):
+        for f in ("limbs", "exp", "flags", "rad_man", "rad_exp"):
+            assert np.array_equal(getattr(a, f), getattr(b, f)), (kind, f)
+    rng2 = np.random.default_rng(12)
+    check_complex(runs[0], A2, B2, n, n, n, p, [(int(a), int(b)) for a, b in
+                                                zip(rng2.integers(0, n, 30),
+                                                    rng2.integers(0, n, 30))])
