@@ -3433,6 +3433,15 @@ static void launch_maxplus(arbgpu_ctx *ctx, cudaStream_t s, const int32_t *dX, c
   maxplus_top_kernel<<<grid, 256, 0, s>>>(dX, dY, wideX, wideY, rt, ct, M, K, N, E, first);
 }
 
+// The window bound of an output part from its products' bounds: out = max(a, b) entry by entry
+// (b null: a copy); INT64_MIN marks an entry without a nonzero product.
+__global__ void etop_max_kernel(const int64_t *a, const int64_t *b, int64_t *out, int64_t n) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const long long v = a[i];
+  out[i] = b ? max(v, (long long)b[i]) : v;
+}
+
 // acc += T_s 2^sigma_s (bits below the window truncated toward zero, one ulp each time),
 // rad += this block's radius bound.
 __global__ void accumulate_kernel(const AccArgs a) {
@@ -3718,7 +3727,7 @@ struct BlockWs {
   size_t relA[2], relB[2];  // tops of A's and B's parts relative to their lines (int32)
   size_t relwide;           // their `wide` flags (A0, A1, B0, B1): see maxplus16_top_kernel
   // negligible-limb omission: one product's E, its truncated lines and their statistics
-  size_t eprod, om_rbot, om_rrad, om_rtrunc, om_cbot, om_crad, om_cplus, om_ctrunc, om_stats;
+  size_t eprod /* [products][M N] */, om_rbot, om_rrad, om_rtrunc, om_cbot, om_crad, om_cplus, om_ctrunc, om_stats;
   // multimodular engine: residue planes, residue products, tables
   size_t resA, resB, cdig, ccar, craw;
   // complex product by eq. 2: residue planes of the parts and their sum, three residue products;
@@ -3806,7 +3815,7 @@ static BlockWs block_ws(arbgpu_ctx *ctx, int64_t M, int64_t K, int64_t N, int pr
     w.relB[q] = take(4 * (size_t)K * N);
   }
   w.relwide = take(4 * sizeof(int));
-  w.eprod = take(8 * MN);
+  w.eprod = take(8 * MN * (size_t)(cplx ? 4 : 1));  // E of each real product
   w.om_rbot = take(8 * (size_t)M);
   w.om_rrad = take(8 * (size_t)M);
   w.om_rtrunc = take(8 * (size_t)M);
@@ -4357,22 +4366,19 @@ struct Omitted {
   BlockStats hs;
 };
 
-// The omission for X Y under the whole-range lines `full` (dX, dY: the operands' tops relative to
-// those lines, rel_tops_kernel): E, the thresholds, the truncated lines in the workspace and
-// their statistics (one read-back).  ok when the truncated operands fit one
+// The omission for X Y under the whole-range lines `full`, from E = its max-plus bound
+// (launch_maxplus): the thresholds, the truncated lines in the workspace and their statistics
+// (one read-back).  ok when the truncated operands fit one
 // block of height <= h (h of the untruncated operands' precisions) and the tensor-core residue
 // kernel takes them; otherwise nothing is used.
 static arbgpu_status omit_product(arbgpu_ctx *ctx, const BlockWs &w, uint8_t *ws,
-                                  const int32_t *dX, const int32_t *dY, const int *wideX,
-                                  const int *wideY, int64_t M, int64_t K, int64_t N, int prec,
+                                  const int64_t *E, int64_t M, int64_t K, int64_t N, int prec,
                                   const Lines &full, const BlockStats &hs, cudaStream_t s,
                                   Omitted *out) {
   out->ok = false;
   int bk = 0;
   for (int64_t v = K; v > 0; v >>= 1) ++bk;
   const int64_t off = (int64_t)prec + bk + 8;
-  int64_t *E = (int64_t *)(ws + w.eprod);
-  launch_maxplus(ctx, s, dX, dY, wideX, wideY, full.rtop, full.ctop, M, K, N, E, 1);
   int64_t *rb = (int64_t *)(ws + w.om_rbot), *rr = (int64_t *)(ws + w.om_rrad);
   int64_t *rt = (int64_t *)(ws + w.om_rtrunc);
   int64_t *cb = (int64_t *)(ws + w.om_cbot), *cr = (int64_t *)(ws + w.om_crad);
@@ -5487,6 +5493,21 @@ arbgpu_status block_finish(arbgpu_ctx *ctx, const arbgpu_balls *C, const arbgpu_
     }
     return cudaGetLastError() == cudaSuccess ? ARBGPU_OK : ARBGPU_ERR_CUDA;
   };
+  // The max-plus bound E_t of real product t (A_xa B_yb; t as in the product lists below),
+  // computed once per call: the omission's thresholds and the window bound of the product's
+  // output part both read it.
+  bool e_done[4] = {false, false, false, false};
+  auto E_of = [&](int t) { return (int64_t *)(ws + w.eprod) + (size_t)t * M * N; };
+  auto ensure_E = [&](int t, int xa, int yb) -> arbgpu_status {
+    if (e_done[t]) return ARBGPU_OK;
+    const arbgpu_status rs = ensure_rel(xa, yb);
+    if (rs != ARBGPU_OK) return rs;
+    launch_maxplus(ctx, s, (const int32_t *)(ws + w.relA[xa]), (const int32_t *)(ws + w.relB[yb]),
+                   wide_of(xa), wide_of(2 + yb), rowsL[xa].rtop, colsL[yb].ctop, M, K, N,
+                   E_of(t), 1);
+    e_done[t] = true;
+    return cudaGetLastError() == cudaSuccess ? ARBGPU_OK : ARBGPU_ERR_CUDA;
+  };
 
   if (!cplx) {
     const BlockStats hs = merge_stats(hst[0], hst[2]);
@@ -5494,12 +5515,10 @@ arbgpu_status block_finish(arbgpu_ctx *ctx, const arbgpu_balls *C, const arbgpu_
     const bool one = hs.hA <= h && hs.hB <= h;
     if (omission_wanted(prec, K, hs, one)) {
       // ---- negligible limbs omitted: one block of the truncated operands, rounded once
-      arbgpu_status so = ensure_rel(0, 0);
+      arbgpu_status so = ensure_E(0, 0, 0);
       if (so != ARBGPU_OK) return so;
       Omitted om{};
-      so = omit_product(ctx, w, ws, (const int32_t *)(ws + w.relA[0]),
-                        (const int32_t *)(ws + w.relB[0]), wide_of(0), wide_of(2), M, K, N, prec,
-                        lines_of(0, 0), hs, s, &om);
+      so = omit_product(ctx, w, ws, E_of(0), M, K, N, prec, lines_of(0, 0), hs, s, &om);
       if (so != ARBGPU_OK) return so;
       if (om.ok) {
         RoundArgs ra{};
@@ -5619,18 +5638,17 @@ arbgpu_status block_finish(arbgpu_ctx *ctx, const arbgpu_balls *C, const arbgpu_
     if (etop_done[q]) return ARBGPU_OK;
     etop_done[q] = true;
     int64_t *et = (int64_t *)(ws + w.etop[q]);
-    bool first = true;
+    const int64_t *src[2] = {nullptr, nullptr};
+    int n = 0;
     for (int t = 0; t < nprods; ++t) {
       const Prod &pr = prods[t];
       if (pr.part != q) continue;
-      const arbgpu_status rs = ensure_rel(pr.xa, pr.yb);
+      const arbgpu_status rs = ensure_E(t, pr.xa, pr.yb);
       if (rs != ARBGPU_OK) return rs;
-      const int32_t *dX = (const int32_t *)(ws + w.relA[pr.xa]);
-      const int32_t *dY = (const int32_t *)(ws + w.relB[pr.yb]);
-      launch_maxplus(ctx, s, dX, dY, wide_of(pr.xa), wide_of(2 + pr.yb), rowsL[pr.xa].rtop,
-                     colsL[pr.yb].ctop, M, K, N, et, first ? 1 : 0);
-      first = false;
+      src[n++] = E_of(t);
     }
+    LaunchScope sc(ctx, s, "etop_max", M * N);
+    etop_max_kernel<<<(unsigned)((M * N + 255) / 256), 256, 0, s>>>(src[0], src[1], et, M * N);
     return cudaGetLastError() == cudaSuccess ? ARBGPU_OK : ARBGPU_ERR_CUDA;
   };
   if (!p3.ok)
@@ -5703,12 +5721,10 @@ arbgpu_status block_finish(arbgpu_ctx *ctx, const arbgpu_balls *C, const arbgpu_
     if (cplx && omission_wanted(prec, K, hs, hs.hA <= hb && hs.hB <= hb)) {
       // negligible limbs omitted: when the truncated operands fit one block, that block is
       // accumulated (a real product tried this before reaching the loop)
-      arbgpu_status so = ensure_rel(pr.xa, pr.yb);
+      arbgpu_status so = ensure_E(t, pr.xa, pr.yb);
       if (so != ARBGPU_OK) return so;
       Omitted om{};
-      so = omit_product(ctx, w, ws, (const int32_t *)(ws + w.relA[pr.xa]),
-                        (const int32_t *)(ws + w.relB[pr.yb]), wide_of(pr.xa),
-                        wide_of(2 + pr.yb), M, K, N, prec, lines_of(pr.xa, pr.yb), hs, s, &om);
+      so = omit_product(ctx, w, ws, E_of(t), M, K, N, prec, lines_of(pr.xa, pr.yb), hs, s, &om);
       if (so != ARBGPU_OK) return so;
       if (om.ok) {
         so = accumulate_product(ctx, w, ws, Av[pr.xa], Bv[pr.yb], M, K, N, lda, ldb, prec,
