@@ -3,9 +3,9 @@
 * the complex N = 2048, p = 128 product with Laplace(40) exponents, both the structured variant
   (exponent blocks along the inner index) and the literal one (i.i.d. exponents): containment of
   the exact product and the accuracy bound |m - S| <= 2^-p sum |a b| on every sampled entry, by
-  four real products with their negligible limbs omitted, and with ARBGPU_MM_COMPLEX_3M by eq. 2
-  on both parts truncated under shared thresholds (or four products where those leave several
-  blocks);
+  four real products with their negligible limbs omitted, with ARBGPU_MM_COMPLEX_3M by eq. 2 on
+  both parts truncated under shared thresholds, and with the omission off by eq. 2 over several
+  blocks shared by both parts (over their shared inner order);
 * the grouped batch of 256 real products (N in [16, 512], p in {64, ..., 1024}) in one
   arbgpu_mat_mul_batched call: block items (one exponent block each) bit-exact RNE_p of the exact
   sum, or within the bound where negligible limbs were omitted, classical items bit-exact against
@@ -32,27 +32,36 @@ def arb():
 
 
 @pytest.mark.parametrize("structured", [True, False])
-@pytest.mark.parametrize("m3", [False, True])
-def test_complex2048_sampled(arb, structured, m3):
+@pytest.mark.parametrize("mode", ["4m", "3m", "3m_several"])
+def test_complex2048_sampled(arb, structured, mode):
+    from tests.gpu_util import env
     case = complex_matmul_laplace(structured=structured)
     n, p = case.N, case.prec
     A = [arb.Balls.from_raw(a) for a in case.A]
     B = [arb.Balls.from_raw(b) for b in case.B]
     C = [arb.Balls.empty(n * n, 2), arb.Balls.empty(n * n, 2)]
-    flags = arb.MM_COMPLEX_3M if m3 else 0
+    flags = 0 if mode == "4m" else arb.MM_COMPLEX_3M
     need = arb.mat_mul_workspace_size(n, n, n, p, 2, 2, True, arb.ALG_AUTO, flags)
     import torch
     ws = torch.empty(max(need, 1), dtype=torch.uint8, device="cuda")
     ctx = arb.default_context()
-    arb.mat_mul(C, A, B, n, n, n, p, flags=flags, workspace=ws, ctx=ctx)
+    # 3m_several: the omission off, so eq. 2 runs over several blocks shared by both parts
+    import contextlib
+    with env(ARBGPU_OMIT="0") if mode == "3m_several" else contextlib.nullcontext():
+        arb.mat_mul(C, A, B, n, n, n, p, flags=flags, workspace=ws, ctx=ctx)
     assert ctx.status() == 0
     plans = ctx.last_plans()
-    if m3 and len(plans) == 1:
+    if mode == "3m":
         # eq. 2 on the parts truncated under thresholds shared by both parts: one shared block
-        assert plans[0]["kind"] == 5 and plans[0]["blocks"] == [(0, n, False)]
-    elif m3:
-        # the shared thresholds left several blocks: four real products, each with its omission
-        assert [r["kind"] for r in plans] == [3, 3, 3, 3]
+        assert len(plans) == 1 and plans[0]["kind"] == 5
+        assert plans[0]["blocks"] == [(0, n, False)]
+    elif mode == "3m_several":
+        # one record over the inner order shared by the parts; its blocks tile the inner range
+        assert len(plans) == 1 and plans[0]["kind"] == 4
+        bl = plans[0]["blocks"]
+        assert len(bl) > 1 and bl[0][0] == 0 and bl[-1][1] == n
+        assert all(a[1] == b[0] for a, b in zip(bl, bl[1:]))
+        assert sorted(plans[0]["order"]) == list(range(n))
     else:
         # with the negligible limbs omitted, each real product of this workload is one block
         assert [r["kind"] for r in plans] == [3, 3, 3, 3]
