@@ -641,7 +641,8 @@ def run_workload(args):
             "cpu_baseline": {"value": r / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
                              "sample": sample},
             "io_bytes": {"in": inbytes, "out": outbytes}, "clocks": clocks,
-            "calibration": calibration, "autotune": dict(ctx.autotune_stats(), on=args.autotune)}
+            "calibration": calibration, "autotune": dict(ctx.autotune_stats(), on=args.autotune,
+                                                        algorithm=ctx.autotune_alg_stats())}
     if graph:
         line["us_per_call"] = ms / args.steps * 1e3
         line["graph_replay"] = graph
@@ -936,7 +937,8 @@ def main():
                 "cpu_baseline": cpu,
                 "clocks": clocks, "compare": compare, "peaks_source": peaks["_source"],
                 "calibration": calibration,
-                "autotune": dict(ctx.autotune_stats(), on=args.autotune)}
+                "autotune": dict(ctx.autotune_stats(), on=args.autotune,
+                                 algorithm=ctx.autotune_alg_stats())}
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()

@@ -122,12 +122,29 @@ arbgpu_status arbgpu_calibrate(arbgpu_ctx *ctx, arbgpu_calibration *out);
  * call synchronises its stream. The faster engine
  * is kept for the bucket, for the context's lifetime, and later products of the bucket use it.
  * While the stream is being captured into a CUDA graph, no timing runs: undecided buckets use the
- * cost model.  Outputs never depend on the setting.
+ * cost model.  Outputs never depend on the engine choice.
  * arbgpu_autotune_stats: buckets decided so far, products run for the timings, and how many of
- * the decided buckets chose the multimodular engine (any pointer may be null). */
+ * the decided buckets chose the multimodular engine (any pointer may be null).
+ *
+ * The same switch times the algorithm of ARBGPU_ALG_AUTO matrix products near the crossover
+ * between the classical dots and Algorithm 2 (the paper finds it at N = 40..60, Section V):
+ * for 8 <= M, N <= 512 and 30 <= K <= 512, the first AUTO product of a size bucket (M, K, N
+ * rounded up to powers of two, the precision in limbs, complex, eq. 2) runs both algorithms once
+ * untimed and once timed (four products; the call synchronises its stream), keeps the faster for
+ * the bucket and leaves its result in C; arbgpu_mat_mul_batched times such items alone before
+ * the batch.  Outside that range, with the autotuner off, or while the stream is captured, the
+ * fixed rule (Algorithm 2 for M, N, K >= 48) applies.  The two algorithms give different balls
+ * (both contain the exact product within the accuracy bound), so with the autotuner on an AUTO
+ * product's result depends on the measured choice.  The workspace size queries count the block
+ * algorithm's workspace for the products the autotuner may give it: query them after
+ * arbgpu_set_autotune.
+ * arbgpu_autotune_alg_stats: AUTO buckets decided, products run for their timings, and how many
+ * chose Algorithm 2 (any pointer may be null). */
 arbgpu_status arbgpu_set_autotune(arbgpu_ctx *ctx, int enable);
 arbgpu_status arbgpu_autotune_stats(arbgpu_ctx *ctx, int64_t *buckets, int64_t *timing_runs,
                                     int64_t *crt_buckets);
+arbgpu_status arbgpu_autotune_alg_stats(arbgpu_ctx *ctx, int64_t *buckets, int64_t *timing_runs,
+                                        int64_t *block_buckets);
 
 /* Synchronises `stream`, returns the first device-side error recorded since the previous call
  * (ARBGPU_OK if none) and clears it. */

@@ -170,7 +170,8 @@ class Context:
             raise ArbgpuError(rc, "arbgpu_reserve")
 
     def set_autotune(self, enable=True):
-        """Turn the block path's engine autotuner on or off (``arbgpu_set_autotune``)."""
+        """Turn the autotuner on or off (``arbgpu_set_autotune``): the block path's integer engine,
+        and the dot / block choice of ALG_AUTO products near the crossover."""
         rc = _lib.lib().arbgpu_set_autotune(self.handle, 1 if enable else 0)
         if rc != 0:
             raise ArbgpuError(rc, "arbgpu_set_autotune")
@@ -182,6 +183,15 @@ class Context:
         if rc != 0:
             raise ArbgpuError(rc, "arbgpu_autotune_stats")
         return dict(buckets=b.value, timing_runs=t.value, crt_buckets=c.value)
+
+    def autotune_alg_stats(self):
+        """dict(buckets, timing_runs, block_buckets) of the ALG_AUTO dot / block choice."""
+        b, t, k = C.c_int64(0), C.c_int64(0), C.c_int64(0)
+        rc = _lib.lib().arbgpu_autotune_alg_stats(self.handle, C.byref(b), C.byref(t),
+                                                  C.byref(k))
+        if rc != 0:
+            raise ArbgpuError(rc, "arbgpu_autotune_alg_stats")
+        return dict(buckets=b.value, timing_runs=t.value, block_buckets=k.value)
 
     def calibrate(self):
         """Measured integer and 8-bit tensor throughput of the device (``arbgpu_calibrate``):

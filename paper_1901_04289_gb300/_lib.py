@@ -113,6 +113,8 @@ def lib():
         L.arbgpu_set_autotune.argtypes = [vp, C.c_int]
         L.arbgpu_autotune_stats.argtypes = [vp, C.POINTER(C.c_int64), C.POINTER(C.c_int64),
                                             C.POINTER(C.c_int64)]
+        L.arbgpu_autotune_alg_stats.argtypes = [vp, C.POINTER(C.c_int64), C.POINTER(C.c_int64),
+                                                C.POINTER(C.c_int64)]
         L.arbgpu_series_exp.argtypes = [vp, P, P, i64, i64, i32, vp, sz, vp]
         L.arbgpu_series_exp_workspace_size.argtypes = [vp, i64, i64, i32, C.POINTER(C.c_size_t)]
         L.arbgpu_launch_count.argtypes = [vp, C.POINTER(C.c_int64)]
@@ -121,7 +123,7 @@ def lib():
         for name in ("arbgpu_launch_count", "arbgpu_trace_enable", "arbgpu_trace_read",
                      "arbgpu_last_plans", "arbgpu_reserve", "arbgpu_calibrate",
                      "arbgpu_set_autotune", "arbgpu_autotune_stats",
-                     "arbgpu_series_exp",
+                     "arbgpu_autotune_alg_stats", "arbgpu_series_exp",
                      "arbgpu_series_exp_workspace_size",
                      "arbgpu_create", "arbgpu_destroy", "arbgpu_get_status", "arbgpu_dot",
                      "arbgpu_approx_dot", "arbgpu_dot_ex",
@@ -149,4 +151,4 @@ def exported_symbols():
             "arbgpu_int_mat_mul_noalloc", "arbgpu_mat_mul_batched",
             "arbgpu_mat_mul_batched_workspace_size", "arbgpu_last_plans", "arbgpu_reserve",
             "arbgpu_series_exp", "arbgpu_series_exp_workspace_size", "arbgpu_calibrate",
-            "arbgpu_set_autotune", "arbgpu_autotune_stats"]
+            "arbgpu_set_autotune", "arbgpu_autotune_stats", "arbgpu_autotune_alg_stats"]

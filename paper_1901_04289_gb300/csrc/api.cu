@@ -126,6 +126,17 @@ arbgpu_status arbgpu_autotune_stats(arbgpu_ctx *ctx, int64_t *buckets, int64_t *
   return ARBGPU_OK;
 }
 
+arbgpu_status arbgpu_autotune_alg_stats(arbgpu_ctx *ctx, int64_t *buckets, int64_t *timing_runs,
+                                        int64_t *block_buckets) {
+  if (!ctx) return ARBGPU_ERR_INVALID;
+  int64_t blk = 0;
+  for (const auto &kv : ctx->alg_tuned) blk += kv.second ? 1 : 0;
+  if (buckets) *buckets = (int64_t)ctx->alg_tuned.size();
+  if (timing_runs) *timing_runs = ctx->alg_tune_runs;
+  if (block_buckets) *block_buckets = blk;
+  return ARBGPU_OK;
+}
+
 int arbgpu_version(void) { return 100; }
 
 const char *arbgpu_status_string(arbgpu_status s) {
@@ -295,6 +306,115 @@ static bool auto_uses_block(int64_t M, int64_t K, int64_t N) {
   return M >= 48 && N >= 48 && K >= 48;
 }
 
+// AUTO with the autotuner on: around the crossover (both algorithms apply and neither dominates
+// by construction) the choice is timed once per size bucket: M, K and N rounded up to powers of
+// two, the precision in limbs, complex and eq. 2.
+static bool auto_tunable(int64_t M, int64_t K, int64_t N) {
+  return K >= 30 && M >= 8 && N >= 8 && M <= 512 && N <= 512 && K <= 512;
+}
+
+static int clog2(int64_t v) {
+  int b = 0;
+  while (((int64_t)1 << b) < v) ++b;
+  return b;
+}
+
+static uint64_t alg_bucket(int64_t M, int64_t K, int64_t N, int prec, bool cplx, bool m3) {
+  return (uint64_t)clog2(M) | (uint64_t)clog2(K) << 8 | (uint64_t)clog2(N) << 16 |
+         (uint64_t)((prec + 63) / 64) << 24 | (uint64_t)(cplx ? 1 : 0) << 40 |
+         (uint64_t)(m3 ? 1 : 0) << 41;
+}
+
+// The AUTO choice: 1 block, 0 classical dots, -1 a bucket the autotuner has yet to time.
+static int auto_choice(const arbgpu_ctx *ctx, int64_t M, int64_t K, int64_t N, int prec,
+                       bool cplx, bool m3) {
+  if (ctx->autotune && auto_tunable(M, K, N)) {
+    const auto it = ctx->alg_tuned.find(alg_bucket(M, K, N, prec, cplx, m3));
+    return it == ctx->alg_tuned.end() ? -1 : (it->second ? 1 : 0);
+  }
+  return auto_uses_block(M, K, N) ? 1 : 0;
+}
+
+// Whether an AUTO product may run the block algorithm (so its workspace must hold it).
+static bool auto_may_use_block(const arbgpu_ctx *ctx, int64_t M, int64_t K, int64_t N) {
+  return auto_uses_block(M, K, N) || (ctx->autotune && auto_tunable(M, K, N));
+}
+
+// One product by the block algorithm (*used: it ran; false with ARBGPU_ERR_LIMIT when the
+// inputs need the classical one) or by the classical dots.
+static arbgpu_status run_matmul_alg(arbgpu_ctx *ctx, bool block, const arbgpu_balls *C,
+                                    const arbgpu_balls *A, const arbgpu_balls *B, int64_t M,
+                                    int64_t K, int64_t N, int64_t lda, int64_t ldb, int64_t ldc,
+                                    int32_t prec, int complex_mode, uint32_t flags,
+                                    void *workspace, size_t ws_bytes, cudaStream_t s,
+                                    bool *used) {
+  *used = false;
+  if (block) {
+    const arbgpu_status st =
+        block_matmul(ctx, C, A, B, M, K, N, lda, ldb, ldc, prec, complex_mode != 0,
+                     (flags & ARBGPU_MM_COMPLEX_3M) != 0, workspace, ws_bytes, s, used);
+    if (*used || st != ARBGPU_ERR_LIMIT) return st;
+  }
+  return launch_matmul_dot(ctx, C, A, B, M, K, N, lda, ldb, ldc, prec, complex_mode, s);
+}
+
+// The first AUTO product of an undecided bucket: both algorithms once untimed, then once each
+// timed with CUDA events on `s` (which this synchronises); the faster is kept for the bucket and
+// its result is the one left in C.  No timing while `s` is being captured, nor when the block
+// algorithm does not take these inputs (the fixed rule, or the dots, decide then).
+static arbgpu_status tune_auto(arbgpu_ctx *ctx, const arbgpu_balls *C, const arbgpu_balls *A,
+                               const arbgpu_balls *B, int64_t M, int64_t K, int64_t N,
+                               int64_t lda, int64_t ldb, int64_t ldc, int32_t prec,
+                               int complex_mode, uint32_t flags, void *workspace,
+                               size_t ws_bytes, cudaStream_t s) {
+  auto run = [&](bool block, bool *used) {
+    return run_matmul_alg(ctx, block, C, A, B, M, K, N, lda, ldb, ldc, prec, complex_mode, flags,
+                          workspace, ws_bytes, s, used);
+  };
+  bool used = false;
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(s, &cap) != cudaSuccess || cap != cudaStreamCaptureStatusNone)
+    return run(auto_uses_block(M, K, N), &used);
+  arbgpu_status st = run(true, &used);
+  if (st == ARBGPU_ERR_WORKSPACE) return run(false, &used);  // (a workspace sized without it)
+  if (st != ARBGPU_OK) return st;
+  const uint64_t key =
+      alg_bucket(M, K, N, prec, complex_mode != 0, (flags & ARBGPU_MM_COMPLEX_3M) != 0);
+  if (!used) {  // the inputs took the classical algorithm inside the block call
+    ctx->alg_tuned[key] = false;
+    ctx->alg_tune_runs += 1;
+    return ARBGPU_OK;
+  }
+  cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
+  for (auto &e : ev)
+    if (cudaEventCreate(&e) != cudaSuccess) {
+      for (auto &f : ev)
+        if (f) cudaEventDestroy(f);
+      return ARBGPU_ERR_CUDA;
+    }
+  bool u2 = false;
+  float t_blk = 0.f, t_dot = 0.f;
+  st = run(false, &u2);
+  if (st == ARBGPU_OK && cudaEventRecord(ev[0], s) != cudaSuccess) st = ARBGPU_ERR_CUDA;
+  if (st == ARBGPU_OK) st = run(true, &u2);
+  if (st == ARBGPU_OK && cudaEventRecord(ev[1], s) != cudaSuccess) st = ARBGPU_ERR_CUDA;
+  if (st == ARBGPU_OK) st = run(false, &u2);
+  if (st == ARBGPU_OK && (cudaEventRecord(ev[2], s) != cudaSuccess ||
+                          cudaEventSynchronize(ev[2]) != cudaSuccess ||
+                          cudaEventElapsedTime(&t_blk, ev[0], ev[1]) != cudaSuccess ||
+                          cudaEventElapsedTime(&t_dot, ev[1], ev[2]) != cudaSuccess))
+    st = ARBGPU_ERR_CUDA;
+  for (auto &e : ev) cudaEventDestroy(e);
+  if (st != ARBGPU_OK) return st;
+  const bool block_faster = t_blk < t_dot;
+  ctx->alg_tuned[key] = block_faster;
+  ctx->alg_tune_runs += 4;
+  // the dots ran last; a block choice runs once more so that its result (and plan) is the one
+  // the call leaves
+  ctx->plan_log.clear();
+  return block_faster ? run(true, &u2) : ARBGPU_OK;
+}
+
 arbgpu_status arbgpu_mat_mul_workspace_size(arbgpu_ctx *ctx, int64_t M, int64_t K, int64_t N,
                                             int32_t prec, int32_t a_nlimbs, int32_t b_nlimbs,
                                             int complex_mode, int alg, uint32_t flags,
@@ -306,7 +426,7 @@ arbgpu_status arbgpu_mat_mul_workspace_size(arbgpu_ctx *ctx, int64_t M, int64_t 
   *bytes = 0;
   if (alg == ARBGPU_ALG_DOT) return ARBGPU_OK;
   if (alg != ARBGPU_ALG_BLOCK && alg != ARBGPU_ALG_AUTO) return ARBGPU_ERR_INVALID;
-  if (alg == ARBGPU_ALG_AUTO && !auto_uses_block(M, K, N)) return ARBGPU_OK;
+  if (alg == ARBGPU_ALG_AUTO && !auto_may_use_block(ctx, M, K, N)) return ARBGPU_OK;
   *bytes = block_workspace_size(ctx, M, K, N, prec, complex_mode != 0,
                                 (flags & ARBGPU_MM_COMPLEX_3M) != 0, a_nlimbs, b_nlimbs);
   return ARBGPU_OK;
@@ -337,18 +457,20 @@ arbgpu_status arbgpu_mat_mul(arbgpu_ctx *ctx, const arbgpu_balls *C, const arbgp
   if (alg != ARBGPU_ALG_DOT && alg != ARBGPU_ALG_BLOCK && alg != ARBGPU_ALG_AUTO)
     return ARBGPU_ERR_INVALID;
   ctx->plan_log.clear();
-  const bool try_block =
-      alg == ARBGPU_ALG_BLOCK || (alg == ARBGPU_ALG_AUTO && auto_uses_block(M, K, N));
-  if (try_block && K > 0) {
-    bool used = false;
-    arbgpu_status st = block_matmul(ctx, C, A, B, M, K, N, lda, ldb, ldc, prec, complex_mode != 0,
-                                    (flags & ARBGPU_MM_COMPLEX_3M) != 0, workspace, ws_bytes,
-                                    (cudaStream_t)stream, &used);
-    if (used || st != ARBGPU_ERR_LIMIT) return st;
-    // not a single exponent block (or special values): the classical algorithm handles it
-  }
-  return launch_matmul_dot(ctx, C, A, B, M, K, N, lda, ldb, ldc, prec, complex_mode,
-                           (cudaStream_t)stream);
+  const int choice =
+      alg == ARBGPU_ALG_BLOCK
+          ? 1
+          : alg == ARBGPU_ALG_DOT
+                ? 0
+                : auto_choice(ctx, M, K, N, prec, complex_mode != 0,
+                              (flags & ARBGPU_MM_COMPLEX_3M) != 0);
+  if (choice < 0 && K > 0)
+    return tune_auto(ctx, C, A, B, M, K, N, lda, ldb, ldc, prec, complex_mode, flags, workspace,
+                     ws_bytes, (cudaStream_t)stream);
+  // (the block call hands inputs it cannot take -- special values, limits -- to the dots)
+  bool used = false;
+  return run_matmul_alg(ctx, choice == 1 && K > 0, C, A, B, M, K, N, lda, ldb, ldc, prec,
+                        complex_mode, flags, workspace, ws_bytes, (cudaStream_t)stream, &used);
 }
 
 arbgpu_status arbgpu_last_plans(arbgpu_ctx *ctx, int64_t *words, int64_t max_words,
@@ -384,9 +506,23 @@ bool matmul_args_ok(const arbgpu_balls *C, const arbgpu_balls *A, const arbgpu_b
   return true;
 }
 
-bool item_uses_block(const arbgpu_matmul_desc &d) {
+// The item's AUTO choice (1 block, 0 dots, -1 to be timed), as for arbgpu_mat_mul.
+int item_choice(const arbgpu_ctx *ctx, const arbgpu_matmul_desc &d) {
+  if (d.M == 0 || d.N == 0 || d.K == 0) return 0;
+  if (d.alg != ARBGPU_ALG_AUTO) return d.alg == ARBGPU_ALG_BLOCK ? 1 : 0;
+  return auto_choice(ctx, d.M, d.K, d.N, d.prec, d.complex_mode != 0,
+                     (d.flags & ARBGPU_MM_COMPLEX_3M) != 0);
+}
+
+bool item_uses_block(const arbgpu_ctx *ctx, const arbgpu_matmul_desc &d) {
+  return item_choice(ctx, d) == 1;
+}
+
+// Whether the item may run the block algorithm (its share of the workspace must hold it).
+bool item_may_use_block(const arbgpu_ctx *ctx, const arbgpu_matmul_desc &d) {
   if (d.M == 0 || d.N == 0 || d.K == 0) return false;
-  return d.alg == ARBGPU_ALG_BLOCK || (d.alg == ARBGPU_ALG_AUTO && auto_uses_block(d.M, d.K, d.N));
+  if (d.alg != ARBGPU_ALG_AUTO) return d.alg == ARBGPU_ALG_BLOCK;
+  return auto_may_use_block(ctx, d.M, d.K, d.N);
 }
 
 size_t al256(size_t v) { return (v + 255) / 256 * 256; }
@@ -403,7 +539,7 @@ arbgpu_status arbgpu_mat_mul_batched_workspace_size(arbgpu_ctx *ctx,
   size_t blk = 0, scans = al256(sizeof(BlockStats) * 4 * (size_t)count);
   for (int32_t q = 0; q < count; ++q) {
     const arbgpu_matmul_desc &d = descs[q];
-    if (!item_uses_block(d)) continue;
+    if (!item_may_use_block(ctx, d)) continue;
     int nlA = d.A[0].nlimbs, nlB = d.B[0].nlimbs;
     if (d.complex_mode) {
       nlA = d.A[1].nlimbs > nlA ? d.A[1].nlimbs : nlA;
@@ -415,7 +551,7 @@ arbgpu_status arbgpu_mat_mul_batched_workspace_size(arbgpu_ctx *ctx,
     scans += al256(block_scan_bytes(d.M, d.N, d.complex_mode != 0));
   }
   int nblock = 0;
-  for (int32_t q = 0; q < count; ++q) nblock += item_uses_block(descs[q]) ? 1 : 0;
+  for (int32_t q = 0; q < count; ++q) nblock += item_may_use_block(ctx, descs[q]) ? 1 : 0;
   const size_t lanes = nblock < arbgpu_ctx::kLanes ? (size_t)nblock : (size_t)arbgpu_ctx::kLanes;
   *bytes = grouped + scans + (lanes > 1 ? lanes * al256(blk) : blk);
   return ARBGPU_OK;
@@ -445,6 +581,17 @@ arbgpu_status arbgpu_mat_mul_batched(arbgpu_ctx *ctx, const arbgpu_matmul_desc *
   uint8_t *ws = (uint8_t *)workspace;
   const size_t items_off = 0, ends_off = al256(sizeof(GroupItem) * (size_t)count);
   const size_t blk_off = ends_off + al256(8 * (size_t)count);
+  // 0. AUTO items of buckets the autotuner has yet to time: each alone, as arbgpu_mat_mul would
+  //    (its product is then computed again below, by the chosen algorithm), in the workspace past
+  //    the grouped arrays (at least one item's block workspace)
+  for (int32_t q = 0; q < count; ++q) {
+    const arbgpu_matmul_desc &d = descs[q];
+    if (item_choice(ctx, d) >= 0) continue;
+    st = tune_auto(ctx, d.C, d.A, d.B, d.M, d.K, d.N, d.lda, d.ldb, d.ldc, d.prec,
+                   d.complex_mode, d.flags, ws + blk_off, ws_bytes - blk_off, s);
+    if (st != ARBGPU_OK) return st;
+  }
+  ctx->plan_log.clear();
   // 1. every classical item in one launch of the dot kernel
   std::vector<GroupItem> items;
   std::vector<int64_t> ends;
@@ -454,7 +601,7 @@ arbgpu_status arbgpu_mat_mul_batched(arbgpu_ctx *ctx, const arbgpu_matmul_desc *
   for (int32_t q = 0; q < count; ++q) {
     const arbgpu_matmul_desc &d = descs[q];
     if (d.M == 0 || d.N == 0) continue;
-    if (item_uses_block(d)) {
+    if (item_uses_block(ctx, d)) {
       block_items.push_back(q);
       continue;
     }

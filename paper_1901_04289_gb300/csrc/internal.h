@@ -42,6 +42,10 @@ struct arbgpu_ctx {
   bool autotune = false;
   std::map<uint64_t, bool> engine_tuned;
   int64_t tune_runs = 0;
+  // and, for ARBGPU_ALG_AUTO products near the crossover, per size bucket whether Algorithm 2
+  // measured faster than the classical dots; products run for those timings
+  std::map<uint64_t, bool> alg_tuned;
+  int64_t alg_tune_runs = 0;
   // streams on which arbgpu_mat_mul_batched runs its block items side by side, forked from and
   // joined back into the caller's stream (created on the first batched call that needs them)
   static constexpr int kLanes = 4;
