@@ -380,11 +380,9 @@ static arbgpu_status tune_auto(arbgpu_ctx *ctx, const arbgpu_balls *C, const arb
   if (st != ARBGPU_OK) return st;
   const uint64_t key =
       alg_bucket(M, K, N, prec, complex_mode != 0, (flags & ARBGPU_MM_COMPLEX_3M) != 0);
-  if (!used) {  // the inputs took the classical algorithm inside the block call
-    ctx->alg_tuned[key] = false;
-    ctx->alg_tune_runs += 1;
-    return ARBGPU_OK;
-  }
+  // the inputs (special values, limits), not the sizes, sent this product to the classical
+  // algorithm inside the block call: nothing to time, the bucket stays undecided
+  if (!used) return ARBGPU_OK;
   cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
   for (auto &e : ev)
     if (cudaEventCreate(&e) != cudaSuccess) {
