@@ -103,9 +103,21 @@ class Balls:
         return sum(t.numel() * t.element_size() for t in self.tensors())
 
     def cstruct(self) -> CBalls:
-        return CBalls(self.limbs.data_ptr(), self.count, self.nlimbs, self.exp.data_ptr(),
-                      self.flags.data_ptr(), self.rad_man.data_ptr(), self.rad_exp.data_ptr(),
-                      self.count)
+        """The ``arbgpu_balls`` struct of this array.  Kept between calls and rebuilt whenever a
+        field's data pointer, the count or the limb count differs from the kept one."""
+        key = (self.limbs.data_ptr(), self.exp.data_ptr(), self.flags.data_ptr(),
+               self.rad_man.data_ptr(), self.rad_exp.data_ptr(), self.count, self.nlimbs)
+        kept = self.__dict__.get("_cstruct")
+        if kept is not None and kept[0] == key:
+            return kept[1]
+        cs = CBalls(key[0], self.count, self.nlimbs, key[1], key[2], key[3], key[4], self.count)
+        self._cstruct = (key, cs, (CBalls * 1)(cs))
+        return cs
+
+    def carray(self):
+        """A one-element ``arbgpu_balls`` array holding ``cstruct()`` (the C calls take arrays)."""
+        self.cstruct()
+        return self._cstruct[2]
 
 
 class Context:
@@ -265,6 +277,13 @@ def _arr(structs):
     return A(*structs)
 
 
+def _carr(balls):
+    """The ``arbgpu_balls`` array argument for a list of one (real) or two (complex) arrays."""
+    if len(balls) == 1:
+        return balls[0].carray()
+    return _arr([b.cstruct() for b in balls])
+
+
 def _ptr(t):
     return None if t is None else C.c_void_p(t.data_ptr())
 
@@ -282,9 +301,8 @@ def dot(res, x, y, xoff, xstep, yoff, ystep, length, prec, *, prec_max, len_max,
     batch = int(length.shape[0])
     options = (1 if approx else 0) | (2 if reduce_prec else 0)
     rc = _lib.lib().arbgpu_dot_ex(
-        ctx.handle, _arr([b.cstruct() for b in r]),
-        _arr([b.cstruct() for b in init]) if init else None, _ptr(sub),
-        _arr([b.cstruct() for b in xs]), _ptr(xoff), _ptr(xstep), _arr([b.cstruct() for b in ys]),
+        ctx.handle, _carr(r), _carr(init) if init else None, _ptr(sub),
+        _carr(xs), _ptr(xoff), _ptr(xstep), _carr(ys),
         _ptr(yoff), _ptr(ystep), _ptr(length), _ptr(prec), batch, int(prec_max), int(len_max),
         1 if cplx else 0, options, None, 0, _stream_ptr(stream))
     if rc != 0:
@@ -319,16 +337,15 @@ def mat_mul(C_out, A, B, M, K, N, prec, *, alg=ALG_AUTO, flags=0, lda=None, ldb=
     lda = K if lda is None else lda
     ldb = N if ldb is None else ldb
     ldc = N if ldc is None else ldc
-    if workspace is None:
+    if workspace is None and alg != ALG_DOT:  # (the classical algorithm needs none)
         need = mat_mul_workspace_size(M, K, N, prec, max(a.nlimbs for a in As),
                                       max(b.nlimbs for b in Bs), cplx, alg, flags, ctx)
         workspace = ctx.workspace(need)
     wsp = _ptr(workspace)
     wsb = 0 if workspace is None else workspace.numel() * workspace.element_size()
-    rc = _lib.lib().arbgpu_mat_mul(ctx.handle, _arr([b.cstruct() for b in cs]),
-                                   _arr([b.cstruct() for b in As]), _arr([b.cstruct() for b in Bs]),
-                                   M, K, N, lda, ldb, ldc, prec, 1 if cplx else 0, alg, flags, wsp,
-                                   wsb, _stream_ptr(stream))
+    rc = _lib.lib().arbgpu_mat_mul(ctx.handle, _carr(cs), _carr(As), _carr(Bs), M, K, N, lda, ldb,
+                                   ldc, prec, 1 if cplx else 0, alg, flags, wsp, wsb,
+                                   _stream_ptr(stream))
     if rc != 0:
         raise ArbgpuError(rc, "arbgpu_mat_mul")
 
