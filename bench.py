@@ -427,7 +427,7 @@ def run_workload(args):
             dt = time.perf_counter() - t0
             return terms / dt, f"{done} dots ({terms} terms) in {dt:.1f} s", dt
     elif wl in ("complex2048", "complex2048_literal"):
-        case = complex_matmul_laplace(structured=(wl == "complex2048"))
+        case = complex_matmul_laplace(n=args.complex_n, structured=(wl == "complex2048"))
         n = case.N
         A = [arb.Balls.from_raw(a) for a in case.A]
         B = [arb.Balls.from_raw(b) for b in case.B]
@@ -682,8 +682,10 @@ def main():
     ap.add_argument("--ref-entries", type=int, default=48)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--complex-3m", action="store_true",
-                    help="complex2048_uniform only: the complex product by eq. 2 (three real "
-                         "products)")
+                    help="complex workloads: the complex product by eq. 2 (three real products)")
+    ap.add_argument("--complex-n", type=int, default=2048,
+                    help="complex2048 / complex2048_literal: the matrix size (2048: the workload; "
+                         "smaller for profiling captures)")
     ap.add_argument("--autotune", action="store_true",
                     help="turn on the library's engine autotuner (the warm-up steps decide)")
     ap.add_argument("--items", default="",
